@@ -1,0 +1,261 @@
+"""FP64 CPU oracle of the bond-based peridynamic time step (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library never calls it.
+
+The arithmetic lives in ``oracle.c`` (plain C, FP64, OpenMP over nodes,
+ascending neighbour order).  This wrapper only marshals numpy arrays.
+
+What pins each function (tests in ``tests/test_oracle_pins.py``):
+
+* ``micromodulus`` (Eq. 5): the printed worked value c = 2.32e18 of the
+  optimised-parameters table (Section 6) from E = 37.0 GPa, nu = 1/4,
+  delta = 15.7 mm; and the continuum strain-energy identity behind it
+  (W = 9/2 K eps^2 under uniform dilation) via the lattice quadrature ratio,
+  which tends to 1 as delta/dx grows.
+* ``family_*`` (Eq. 9): brute force equals the cell grid; interior nodes have
+  the 122 offsets with |o|^2 <= 9; directed-bond totals equal closed-form
+  counts of lattice offset pairs.
+* ``step`` (Eqs. 4-6, 10-11, damped Euler-Cromer reading): zero force under
+  rigid translation, near-zero under rotation; antisymmetry (sum V_i F_i = 0);
+  momentum decays by exactly (1 - dt eta / rho) per step; forces equal minus
+  the energy gradient (finite differences of ``energy_density``); a two-node
+  bond reproduces the closed-form linear recurrence and breaks at the
+  analytic step; displacement BCs follow the prescribed ramp.
+* ``damage`` (Eq. 8): zero at the start, in [0, 1], monotone, and equal to the
+  fraction of crossing offsets for a node next to a full planar cut.
+* ``splitmix64``: the published reference outputs of the generator.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "_liboracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into an in-tree shared library (gcc, FP64, OpenMP).
+
+    ``-ffp-contract=off`` keeps results identical on x86-64 and aarch64."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+class _Model(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64), ("x", ctypes.c_void_p), ("vol", ctypes.c_void_p),
+        ("rows", ctypes.c_void_p), ("nrows", ctypes.c_int64),
+        ("off", ctypes.c_void_p), ("idx", ctypes.c_void_p),
+        ("c", ctypes.c_double), ("c_bond", ctypes.c_void_p),
+        ("sc", ctypes.c_double), ("sc_mode", ctypes.c_int32), ("pad0", ctypes.c_int32),
+        ("sc_seed", ctypes.c_uint64), ("sc_lo", ctypes.c_double), ("sc_hi", ctypes.c_double),
+        ("no_fail", ctypes.c_void_p), ("bc_type", ctypes.c_void_p),
+        ("bc_disp", ctypes.c_void_p), ("bc_force", ctypes.c_void_p),
+        ("disp_rate", ctypes.c_double), ("load", ctypes.c_double),
+        ("dt", ctypes.c_double), ("damping", ctypes.c_double), ("density", ctypes.c_double),
+    ]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        L = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        L.or_micromodulus.restype = ctypes.c_double
+        L.or_micromodulus.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.or_critical_stretch_3d.restype = ctypes.c_double
+        L.or_critical_stretch_3d.argtypes = [ctypes.c_double] * 3
+        L.or_splitmix64.restype = ctypes.c_uint64
+        L.or_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        L.or_sc_bond.restype = ctypes.c_double
+        L.or_sc_bond.argtypes = [ctypes.c_uint64, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_int64, ctypes.c_int64]
+        for name in ("or_family_bruteforce", "or_family_cells"):
+            f = getattr(L, name)
+            f.restype = ctypes.c_int64
+            f.argtypes = [P, ctypes.c_int64, ctypes.c_double, P, ctypes.c_int64, P, P]
+        L.or_cut_crosses.restype = ctypes.c_int
+        L.or_cut_crosses.argtypes = [P, P, P]
+        L.or_apply_cuts.restype = None
+        L.or_apply_cuts.argtypes = [P, P, ctypes.c_int64, P, P, P, ctypes.c_int64, P]
+        L.or_step.restype = None
+        L.or_step.argtypes = [ctypes.POINTER(_Model), ctypes.c_int64, P, P, P, P, P, P, P]
+        L.or_run.restype = None
+        L.or_run.argtypes = [ctypes.POINTER(_Model), ctypes.c_int64, ctypes.c_int64, P, P, P, P]
+        L.or_damage.restype = None
+        L.or_damage.argtypes = [ctypes.POINTER(_Model), P, P]
+        L.or_energy_density.restype = None
+        L.or_energy_density.argtypes = [ctypes.POINTER(_Model), P, P, P]
+        _lib = L
+    return _lib
+
+
+def _p(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data
+
+
+def _c64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def micromodulus(K: float, delta: float) -> float:
+    return lib().or_micromodulus(K, delta)
+
+
+def critical_stretch_3d(G_F: float, E: float, delta: float) -> float:
+    return lib().or_critical_stretch_3d(G_F, E, delta)
+
+
+def splitmix64(seed: int, m: int) -> int:
+    return int(lib().or_splitmix64(seed, m))
+
+
+def sc_bond(seed: int, lo: float, hi: float, i: int, j: int) -> float:
+    return lib().or_sc_bond(seed, lo, hi, i, j)
+
+
+def family(coords: np.ndarray, delta: float, rows: Optional[np.ndarray] = None,
+           method: str = "cells"):
+    """CSR family (Eq. 9) of ``rows`` (default all nodes): (off int64, idx int32)."""
+    x = _c64(coords)
+    n = x.shape[0]
+    r = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    nrows = n if r is None else r.shape[0]
+    off = np.zeros(nrows + 1, dtype=np.int64)
+    f = lib().or_family_bruteforce if method == "brute" else lib().or_family_cells
+    total = f(x.ctypes.data, n, delta, _p(r), nrows, off.ctypes.data, None)
+    idx = np.zeros(max(int(total), 1), dtype=np.int32)
+    f(x.ctypes.data, n, delta, _p(r), nrows, off.ctypes.data, idx.ctypes.data)
+    return off, idx[:total]
+
+
+def cut_keep(coords, off, idx, cuts, rows=None):
+    """uint8 mask over family entries: 0 where the bond crosses a notch rectangle."""
+    x = _c64(coords)
+    cuts = _c64(np.asarray(cuts, dtype=np.float64).reshape(-1, 6))
+    r = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    nrows = x.shape[0] if r is None else r.shape[0]
+    keep = np.ones(idx.shape[0], dtype=np.uint8)
+    if cuts.shape[0] and idx.shape[0]:
+        lib().or_apply_cuts(x.ctypes.data, _p(r), nrows, off.ctypes.data, idx.ctypes.data,
+                            cuts.ctypes.data, cuts.shape[0], keep.ctypes.data)
+    return keep
+
+
+def cut_family(coords, delta, cuts, rows=None, method="cells"):
+    """Family after the initial notch removal (Section 6)."""
+    off, idx = family(coords, delta, rows, method)
+    keep = cut_keep(coords, off, idx, cuts, rows)
+    if keep.all():
+        return off, idx
+    cum = np.zeros(idx.shape[0] + 1, dtype=np.int64)
+    np.cumsum(keep, out=cum[1:])
+    return cum[off], idx[keep.astype(bool)]
+
+
+class Model:
+    """Arguments of the oracle step, kept alive for the C side."""
+
+    def __init__(self, coords, volumes, off, idx, *, c, sc=None, sc_hash=None,
+                 c_bond=None, no_fail=None, bc_type=None, bc_disp=None, bc_force=None,
+                 disp_rate=0.0, load=0.0, dt=1e-7, damping=0.0, density=1.0, rows=None):
+        self.x = _c64(coords)
+        n = self.x.shape[0]
+        self.vol = _c64(volumes)
+        self.rows = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+        self.off = np.ascontiguousarray(off, dtype=np.int64)
+        self.idx = np.ascontiguousarray(idx, dtype=np.int32)
+        self.c_bond = None if c_bond is None else _c64(c_bond)
+        self.no_fail = None if no_fail is None else np.ascontiguousarray(no_fail, np.uint8)
+        self.bc_type = (np.zeros((n, 3), np.uint8) if bc_type is None
+                        else np.ascontiguousarray(bc_type, np.uint8))
+        self.bc_disp = np.zeros((n, 3)) if bc_disp is None else _c64(bc_disp)
+        self.bc_force = None if bc_force is None else _c64(bc_force)
+        m = _Model()
+        m.n = n
+        m.x = self.x.ctypes.data
+        m.vol = self.vol.ctypes.data
+        m.rows = _p(self.rows)
+        m.nrows = n if self.rows is None else self.rows.shape[0]
+        m.off = self.off.ctypes.data
+        m.idx = self.idx.ctypes.data
+        m.c = float(c)
+        m.c_bond = _p(self.c_bond)
+        if sc_hash is not None:
+            m.sc_mode = 1
+            m.sc_seed, m.sc_lo, m.sc_hi = int(sc_hash[0]), float(sc_hash[1]), float(sc_hash[2])
+            m.sc = 0.0
+        else:
+            m.sc_mode = 0
+            m.sc = float(sc)
+        m.no_fail = _p(self.no_fail)
+        m.bc_type = self.bc_type.ctypes.data
+        m.bc_disp = self.bc_disp.ctypes.data
+        m.bc_force = _p(self.bc_force)
+        m.disp_rate, m.load = float(disp_rate), float(load)
+        m.dt, m.damping, m.density = float(dt), float(damping), float(density)
+        self.m = m
+        self.nrows = m.nrows
+        self.nbonds = int(self.off[-1])
+
+    @classmethod
+    def from_workload(cls, w, off, idx, c=None, rows=None, c_bond=None):
+        if c is None:
+            c = micromodulus(w.bulk_modulus, w.horizon)
+        return cls(w.coords, w.volumes, off, idx, c=c, sc=w.sc, sc_hash=w.sc_hash,
+                   c_bond=c_bond, no_fail=w.no_fail, bc_type=w.bc_type, bc_disp=w.bc_disp,
+                   bc_force=w.bc_force, disp_rate=w.disp_rate, load=w.load, dt=w.dt,
+                   damping=w.damping, density=w.density, rows=rows)
+
+    def step(self, step_index, u, v, mu, margin=None, want_force=False):
+        """One step; returns (u_out, v_out[, F]) per row.  mu/margin updated in place."""
+        u = _c64(u)
+        v = _c64(v)
+        uo = np.empty((self.nrows, 3))
+        vo = np.empty((self.nrows, 3))
+        F = np.empty((self.nrows, 3)) if want_force else None
+        lib().or_step(ctypes.byref(self.m), int(step_index), u.ctypes.data, v.ctypes.data,
+                      mu.ctypes.data, _p(margin), uo.ctypes.data, vo.ctypes.data, _p(F))
+        return (uo, vo, F) if want_force else (uo, vo)
+
+    def run(self, first_step, nsteps, u, v, mu, margin=None):
+        """``nsteps`` steps over all nodes; u, v, mu (and margin) updated in place."""
+        assert self.rows is None
+        assert u.dtype == np.float64 and u.flags.c_contiguous
+        assert v.dtype == np.float64 and v.flags.c_contiguous
+        lib().or_run(ctypes.byref(self.m), int(first_step), int(nsteps), u.ctypes.data,
+                     v.ctypes.data, mu.ctypes.data, _p(margin))
+
+    def damage(self, mu):
+        phi = np.empty(self.nrows)
+        lib().or_damage(ctypes.byref(self.m), mu.ctypes.data, phi.ctypes.data)
+        return phi
+
+    def energy_density(self, u, mu):
+        u = _c64(u)
+        W = np.empty(self.nrows)
+        lib().or_energy_density(ctypes.byref(self.m), u.ctypes.data, mu.ctypes.data,
+                                W.ctypes.data)
+        return W
+
+    def fresh_bonds(self):
+        return np.ones(self.nbonds, dtype=np.uint8)

@@ -1,0 +1,412 @@
+/*
+ * FP64 CPU oracle for the bond-based (PMB) peridynamic explicit time step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file; only the test-suite, the smoke check and the CPU-baseline leg
+ * of the benchmark do.  It shares no code, header, table or helper with the
+ * CUDA library.
+ *
+ * Written from the paper ("PeriPy - A High Performance OpenCL Peridynamics
+ * Package", arXiv 2105.04150), plain and slow on purpose:
+ *   - family            Eq. (9), Section 2.3
+ *   - stretch           Eq. (4), Section 2.2
+ *   - PMB force, c      Eq. (5), Section 2.2 (c = 18K / (pi delta^4))
+ *   - breaking (mu)     Eq. (6), Section 2.2, and Algorithm "bond_index"
+ *                       (the break check comes before the force, a bond that
+ *                       breaks contributes nothing in that step)
+ *   - discrete EoM      Eqs. (10)-(11), Section 2.3 (beta = 1, no corrections)
+ *   - damage            Eq. (8), Section 2.2
+ *   - initial notch     Section 6 (bonds crossing the void broken at start)
+ *   - damped Euler-Cromer: named only (Section 3.6); read as
+ *       v^{n+1} = v^n + dt (F(u^n) - eta v^n) / rho,  u^{n+1} = u^n + dt v^{n+1}
+ *   - displacement BC:  u = g * rate * (n+1) after the update, and the velocity
+ *       of that component is the prescribed rate g * rate / dt.
+ * Per node the bonds are visited in ascending neighbour id; each node owns its
+ * row of bond flags, so the node loop may run in parallel without races.
+ *
+ * Per-bond critical stretch (an input the paper does not fix): a counter-based
+ * SplitMix64 draw (Steele, Lea & Flood 2014) keyed on the unordered pair of
+ * caller node ids, mapped to U[lo, hi) with 53 bits.
+ *
+ * Every function here is pinned by CPU tests against closed forms, invariants
+ * or brute force (see the module docstring of oracle/__init__.py for the list).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* Eq. (5): constant micromodulus of the PMB model, c = 18 K / (pi delta^4). */
+double or_micromodulus(double bulk_modulus, double delta)
+{
+    double d4 = delta * delta * delta * delta;
+    return 18.0 * bulk_modulus / (M_PI * d4);
+}
+
+/* Eq. (7), 3D case: s_c = sqrt(5 G_F / (6 E delta)). */
+double or_critical_stretch_3d(double G_F, double E, double delta)
+{
+    return sqrt(5.0 * G_F / (6.0 * E * delta));
+}
+
+/* SplitMix64: the m-th output (m >= 1) of the generator seeded with `seed`. */
+uint64_t or_splitmix64(uint64_t seed, uint64_t m)
+{
+    uint64_t z = seed + m * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* Critical stretch of the bond {i, j}: U[lo, hi) from output (key + 1), where
+ * key = min(i,j) * 2^32 + max(i,j).  Symmetric in i and j by construction. */
+double or_sc_bond(uint64_t seed, double lo, double hi, int64_t i, int64_t j)
+{
+    uint64_t a = (uint64_t)(i < j ? i : j);
+    uint64_t b = (uint64_t)(i < j ? j : i);
+    uint64_t key = (a << 32) | b;
+    uint64_t h = or_splitmix64(seed, key + 1ULL);
+    double unit = (double)(h >> 11) * (1.0 / 9007199254740992.0);
+    return lo + (hi - lo) * unit;
+}
+
+static double dist2(const double* a, const double* b)
+{
+    double dx = b[0] - a[0], dy = b[1] - a[1], dz = b[2] - a[2];
+    return dx * dx + dy * dy + dz * dz;
+}
+
+/* ------------------------------------------------------------------ */
+/* Eq. (9): H_i = { j != i : |x_i - x_j| <= delta }, by brute force, O(n^2).
+ * Rows `rows[r]` (or 0..n-1 when rows == NULL).  First call with idx == NULL
+ * fills off[0..nrows] (returns total count); the second call fills idx. */
+int64_t or_family_bruteforce(const double* x, int64_t n, double delta,
+                             const int64_t* rows, int64_t nrows,
+                             int64_t* off, int32_t* idx)
+{
+    double d2 = delta * delta;
+    if (idx == NULL) {
+        off[0] = 0;
+        for (int64_t r = 0; r < nrows; ++r) {
+            int64_t i = rows ? rows[r] : r;
+            int64_t cnt = 0;
+            for (int64_t j = 0; j < n; ++j)
+                if (j != i && dist2(x + 3 * i, x + 3 * j) <= d2) ++cnt;
+            off[r + 1] = off[r] + cnt;
+        }
+        return off[nrows];
+    }
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t r = 0; r < nrows; ++r) {
+        int64_t i = rows ? rows[r] : r;
+        int64_t p = off[r];
+        for (int64_t j = 0; j < n; ++j)
+            if (j != i && dist2(x + 3 * i, x + 3 * j) <= d2) idx[p++] = (int32_t)j;
+    }
+    return off[nrows];
+}
+
+/* Same set through a uniform cell grid (cell edge = delta), an independent
+ * second route used for large inputs.  Each row is sorted ascending. */
+typedef struct {
+    double lo[3];
+    double h;
+    int64_t dim[3];
+    int64_t* start; /* ncell+1 */
+    int64_t* items; /* node ids grouped by cell, ascending inside a cell */
+} or_grid;
+
+static int64_t cell_coord(double v, double lo, double h, int64_t dim)
+{
+    int64_t c = (int64_t)floor((v - lo) / h);
+    if (c < 0) c = 0;
+    if (c >= dim) c = dim - 1;
+    return c;
+}
+
+static void grid_build(or_grid* g, const double* x, int64_t n, double delta)
+{
+    double hi[3];
+    for (int a = 0; a < 3; ++a) { g->lo[a] = x[a]; hi[a] = x[a]; }
+    for (int64_t i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            if (x[3 * i + a] < g->lo[a]) g->lo[a] = x[3 * i + a];
+            if (x[3 * i + a] > hi[a]) hi[a] = x[3 * i + a];
+        }
+    g->h = delta;
+    for (int a = 0; a < 3; ++a) g->dim[a] = (int64_t)floor((hi[a] - g->lo[a]) / delta) + 1;
+    int64_t ncell = g->dim[0] * g->dim[1] * g->dim[2];
+    g->start = (int64_t*)calloc((size_t)ncell + 1, sizeof(int64_t));
+    g->items = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int64_t* cell = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t c0 = cell_coord(x[3 * i], g->lo[0], g->h, g->dim[0]);
+        int64_t c1 = cell_coord(x[3 * i + 1], g->lo[1], g->h, g->dim[1]);
+        int64_t c2 = cell_coord(x[3 * i + 2], g->lo[2], g->h, g->dim[2]);
+        cell[i] = (c0 * g->dim[1] + c1) * g->dim[2] + c2;
+        g->start[cell[i] + 1]++;
+    }
+    for (int64_t c = 0; c < ncell; ++c) g->start[c + 1] += g->start[c];
+    int64_t* fill = (int64_t*)malloc((size_t)ncell * sizeof(int64_t) + 8);
+    memcpy(fill, g->start, (size_t)ncell * sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) g->items[fill[cell[i]]++] = i; /* ascending i */
+    free(fill);
+    free(cell);
+}
+
+static int cmp_i32(const void* a, const void* b)
+{
+    int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+    return (x > y) - (x < y);
+}
+
+/* Visit the candidates of node i in the 27 surrounding cells. */
+static int64_t grid_row(const or_grid* g, const double* x, int64_t i, double d2, int32_t* out)
+{
+    int64_t c[3];
+    for (int a = 0; a < 3; ++a) c[a] = cell_coord(x[3 * i + a], g->lo[a], g->h, g->dim[a]);
+    int64_t cnt = 0;
+    for (int64_t a = c[0] - 1; a <= c[0] + 1; ++a) {
+        if (a < 0 || a >= g->dim[0]) continue;
+        for (int64_t b = c[1] - 1; b <= c[1] + 1; ++b) {
+            if (b < 0 || b >= g->dim[1]) continue;
+            for (int64_t d = c[2] - 1; d <= c[2] + 1; ++d) {
+                if (d < 0 || d >= g->dim[2]) continue;
+                int64_t cell = (a * g->dim[1] + b) * g->dim[2] + d;
+                for (int64_t p = g->start[cell]; p < g->start[cell + 1]; ++p) {
+                    int64_t j = g->items[p];
+                    if (j != i && dist2(x + 3 * i, x + 3 * j) <= d2) {
+                        if (out) out[cnt] = (int32_t)j;
+                        ++cnt;
+                    }
+                }
+            }
+        }
+    }
+    if (out) qsort(out, (size_t)cnt, sizeof(int32_t), cmp_i32);
+    return cnt;
+}
+
+int64_t or_family_cells(const double* x, int64_t n, double delta,
+                        const int64_t* rows, int64_t nrows,
+                        int64_t* off, int32_t* idx)
+{
+    or_grid g;
+    grid_build(&g, x, n, delta);
+    double d2 = delta * delta;
+    if (idx == NULL) {
+        int64_t* cnt = (int64_t*)malloc((size_t)(nrows > 0 ? nrows : 1) * sizeof(int64_t));
+#pragma omp parallel for schedule(dynamic, 256)
+        for (int64_t r = 0; r < nrows; ++r)
+            cnt[r] = grid_row(&g, x, rows ? rows[r] : r, d2, NULL);
+        off[0] = 0;
+        for (int64_t r = 0; r < nrows; ++r) off[r + 1] = off[r] + cnt[r];
+        free(cnt);
+    } else {
+#pragma omp parallel for schedule(dynamic, 256)
+        for (int64_t r = 0; r < nrows; ++r)
+            grid_row(&g, x, rows ? rows[r] : r, d2, idx + off[r]);
+    }
+    free(g.start);
+    free(g.items);
+    return off[nrows];
+}
+
+/* ------------------------------------------------------------------ */
+/* Initial notch (Section 6): the bond x_i -> x_j is absent when its segment
+ * crosses the plane x[axis] = pos at a point inside the rectangle
+ * lo_a <= x[a] <= hi_a, lo_b <= x[b] <= hi_b ((a, b) = other axes, ascending).
+ * cut = {axis, pos, lo_a, hi_a, lo_b, hi_b}. */
+int or_cut_crosses(const double* xi, const double* xj, const double* cut)
+{
+    int ax = (int)cut[0];
+    double pos = cut[1];
+    double di = xi[ax] - pos, dj = xj[ax] - pos;
+    if (!(di * dj < 0.0)) return 0;
+    double t = di / (di - dj);
+    int a = (ax == 0) ? 1 : 0;
+    int b = (ax == 2) ? 1 : 2;
+    double pa = xi[a] + t * (xj[a] - xi[a]);
+    double pb = xi[b] + t * (xj[b] - xi[b]);
+    return pa >= cut[2] && pa <= cut[3] && pb >= cut[4] && pb <= cut[5];
+}
+
+/* keep[k] = 0 for every bond of the CSR family that crosses any cut, else 1. */
+void or_apply_cuts(const double* x, const int64_t* rows, int64_t nrows,
+                   const int64_t* off, const int32_t* idx,
+                   const double* cuts, int64_t ncuts, uint8_t* keep)
+{
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t r = 0; r < nrows; ++r) {
+        int64_t i = rows ? rows[r] : r;
+        for (int64_t k = off[r]; k < off[r + 1]; ++k) {
+            int64_t j = idx[k];
+            uint8_t ok = 1;
+            for (int64_t c = 0; c < ncuts && ok; ++c)
+                if (or_cut_crosses(x + 3 * i, x + 3 * j, cuts + 6 * c)) ok = 0;
+            keep[k] = ok;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int64_t n;               /* number of nodes */
+    const double* x;         /* 3n reference coordinates */
+    const double* vol;       /* n nodal volumes */
+    const int64_t* rows;     /* nrows node ids the family rows belong to, or NULL = 0..n-1 */
+    int64_t nrows;
+    const int64_t* off;      /* nrows+1 CSR offsets of the family (after notch removal) */
+    const int32_t* idx;      /* neighbour ids, ascending within each row */
+    double c;                /* micromodulus when c_bond == NULL */
+    const double* c_bond;    /* per family entry, or NULL */
+    double sc;               /* critical stretch when sc_mode == 0 */
+    int32_t sc_mode;         /* 0 constant, 1 per-bond U[sc_lo, sc_hi) draw */
+    int32_t pad0;
+    uint64_t sc_seed;
+    double sc_lo, sc_hi;
+    const uint8_t* no_fail;  /* n flags or NULL: bonds touching such a node never break */
+    const uint8_t* bc_type;  /* 3n: 1 = displacement-controlled component */
+    const double* bc_disp;   /* 3n: prescribed displacement per unit scale */
+    const double* bc_force;  /* 3n body-force density per unit load, or NULL */
+    double disp_rate;        /* displacement scale after step k = disp_rate * k */
+    double load;             /* body-force scale */
+    double dt, damping, density;
+} or_model;
+
+static double bond_sc(const or_model* m, int64_t i, int64_t j)
+{
+    if (m->sc_mode == 1) return or_sc_bond(m->sc_seed, m->sc_lo, m->sc_hi, i, j);
+    return m->sc;
+}
+
+/* Internal force density of row r (Eq. (10) sum with beta = 1) and the bond
+ * updates of Algorithm bond_index: for every intact bond compute the stretch
+ * (Eq. (4)); if s >= s_c the bond breaks for good (Eq. (6)) and adds nothing;
+ * else it adds c s V_j (xi+eta)/|xi+eta| (Eq. (5)). */
+static void row_force(const or_model* m, int64_t r, const double* u, uint8_t* mu,
+                      double* margin, double F[3])
+{
+    int64_t i = m->rows ? m->rows[r] : r;
+    F[0] = F[1] = F[2] = 0.0;
+    for (int64_t k = m->off[r]; k < m->off[r + 1]; ++k) {
+        if (!mu[k]) continue;
+        int64_t j = m->idx[k];
+        double xi[3], eta[3], y[3];
+        for (int a = 0; a < 3; ++a) {
+            xi[a] = m->x[3 * j + a] - m->x[3 * i + a];
+            eta[a] = u[3 * j + a] - u[3 * i + a];
+            y[a] = xi[a] + eta[a];
+        }
+        double L = sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
+        double rr = sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+        double s = (rr - L) / L;
+        double sc = bond_sc(m, i, j);
+        if (margin) {
+            double d = fabs(s - sc);
+            if (d < margin[k]) margin[k] = d;
+        }
+        int nofail = m->no_fail && (m->no_fail[i] || m->no_fail[j]);
+        if (s >= sc && !nofail) {
+            mu[k] = 0;
+            continue;
+        }
+        double cij = m->c_bond ? m->c_bond[k] : m->c;
+        double f = cij * s * m->vol[j] / rr;
+        for (int a = 0; a < 3; ++a) F[a] += f * y[a];
+    }
+    if (m->bc_force)
+        for (int a = 0; a < 3; ++a) F[a] += m->load * m->bc_force[3 * i + a];
+}
+
+/* One damped Euler-Cromer step from (u, v) at step index `step` (t = step*dt)
+ * for the rows of the model.  mu (per family entry) is updated in place;
+ * margin (per family entry, or NULL) keeps min |s - s_c| over intact bonds.
+ * Outputs are per row: u_out, v_out (3 per row) and, if F_out != NULL, the
+ * force density F_i of Eq. (11) before integration. */
+void or_step(const or_model* m, int64_t step, const double* u, const double* v,
+             uint8_t* mu, double* margin, double* u_out, double* v_out, double* F_out)
+{
+    double a_damp = m->damping, rho = m->density, dt = m->dt;
+    double s_now = m->disp_rate * (double)step;
+    double s_next = m->disp_rate * (double)(step + 1);
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t r = 0; r < m->nrows; ++r) {
+        int64_t i = m->rows ? m->rows[r] : r;
+        double F[3];
+        row_force(m, r, u, mu, margin, F);
+        for (int a = 0; a < 3; ++a) {
+            double vi = v[3 * i + a];
+            double vn = vi + dt * (F[a] - a_damp * vi) / rho;
+            double un = u[3 * i + a] + dt * vn;
+            if (m->bc_type[3 * i + a] == 1) {
+                double g = m->bc_disp[3 * i + a];
+                un = g * s_next;
+                vn = g * (s_next - s_now) / dt;
+            }
+            u_out[3 * r + a] = un;
+            v_out[3 * r + a] = vn;
+            if (F_out) F_out[3 * r + a] = F[a];
+        }
+    }
+}
+
+/* Run `nsteps` steps over all nodes (rows must be NULL): u, v in/out, mu in/out. */
+void or_run(const or_model* m, int64_t first_step, int64_t nsteps, double* u, double* v,
+            uint8_t* mu, double* margin)
+{
+    int64_t n3 = 3 * m->n;
+    double* u2 = (double*)malloc((size_t)n3 * sizeof(double) + 8);
+    double* v2 = (double*)malloc((size_t)n3 * sizeof(double) + 8);
+    for (int64_t k = 0; k < nsteps; ++k) {
+        or_step(m, first_step + k, u, v, mu, margin, u2, v2, NULL);
+        memcpy(u, u2, (size_t)n3 * sizeof(double));
+        memcpy(v, v2, (size_t)n3 * sizeof(double));
+    }
+    free(u2);
+    free(v2);
+}
+
+/* Eq. (8) with volume weights: phi_i = 1 - sum_j mu_ij V_j / sum_j V_j over the
+ * family of i (after the initial notch removal). */
+void or_damage(const or_model* m, const uint8_t* mu, double* phi)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < m->nrows; ++r) {
+        double num = 0.0, den = 0.0;
+        for (int64_t k = m->off[r]; k < m->off[r + 1]; ++k) {
+            double vj = m->vol[m->idx[k]];
+            den += vj;
+            if (mu[k]) num += vj;
+        }
+        phi[r] = den > 0.0 ? 1.0 - num / den : 0.0;
+    }
+}
+
+/* Elastic energy density of each row: W_i = 1/2 sum_j mu_ij w(eta, xi) V_j with
+ * the micropotential of Eq. (4) read as w = c s^2 |xi| / 2 (the factor 1/2
+ * shares each bond's energy between its two end nodes). */
+void or_energy_density(const or_model* m, const double* u, const uint8_t* mu, double* W)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < m->nrows; ++r) {
+        int64_t i = m->rows ? m->rows[r] : r;
+        double acc = 0.0;
+        for (int64_t k = m->off[r]; k < m->off[r + 1]; ++k) {
+            if (!mu[k]) continue;
+            int64_t j = m->idx[k];
+            double xi[3], y[3];
+            for (int a = 0; a < 3; ++a) {
+                xi[a] = m->x[3 * j + a] - m->x[3 * i + a];
+                y[a] = xi[a] + u[3 * j + a] - u[3 * i + a];
+            }
+            double L = sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
+            double rr = sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+            double s = (rr - L) / L;
+            double cij = m->c_bond ? m->c_bond[k] : m->c;
+            acc += 0.5 * (0.5 * cij * s * s * L) * m->vol[j];
+        }
+        W[r] = acc;
+    }
+}
