@@ -1,0 +1,197 @@
+/*
+ * pd.h - C ABI of the GB300-native bond-based peridynamic time stepper.
+ *
+ * The library advances the explicit, damped time step of a bond-based (PMB)
+ * peridynamic model over a fixed neighbour family (arXiv 2105.04150,
+ * "PeriPy"): per node it evaluates every intact bond (stretch, Eq. 4), breaks
+ * bonds irreversibly at the critical stretch (Eq. 6), reduces the pairwise
+ * forces (Eq. 5, Eq. 10), adds the body force, integrates with damped
+ * Euler-Cromer (Eq. 11) and applies displacement boundary conditions, and
+ * writes the damage (Eq. 8).  All of it runs on one GPU in CUDA kernels.
+ *
+ * Conventions for every entry point:
+ *  - Node ids in and out are the caller's ids 0..n-1; the library keeps its
+ *    own spatial order internally and never exposes it.
+ *  - "Family" arrays are CSR over the caller's nodes (off[n+1] int64,
+ *    idx[off[n]] int32), rows sorted ascending; per-bond arrays
+ *    (stiffness, bond flags) follow that CSR order ("canonical order").
+ *  - Vectors are row-major n x 3 (x, y, z per node), double unless stated.
+ *  - The library copies every input; the caller owns every buffer it passes.
+ *  - Pointers documented as "host or device" are classified with
+ *    cudaPointerGetAttributes; all other pointers are host pointers.
+ *  - Every call returns a pd_status; nothing aborts, traps or exits.  On
+ *    error pd_last_error() returns a message (thread-local, valid until the
+ *    next call from the same thread).
+ *  - Work is queued on the handle's stream (pd_config.stream, or a stream the
+ *    library creates); calls that return data to the host synchronise it.
+ */
+#ifndef PD_H
+#define PD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pd_handle pd_handle;
+
+typedef enum {
+    PD_OK = 0,
+    PD_ERR_ARG = 1,               /* invalid argument (message says which) */
+    PD_ERR_CUDA = 2,              /* a CUDA runtime call failed */
+    PD_ERR_OOM = 3,               /* device or host allocation failed */
+    PD_ERR_NONFINITE = 4,         /* a displacement became NaN/Inf during stepping */
+    PD_ERR_UNSTABLE_DT = 5,       /* dt exceeds the explicit stability bound */
+    PD_ERR_FAMILY_TOO_LARGE = 6,  /* a family exceeds PD_MAX_FAMILY members */
+    PD_ERR_TIMEOUT = 7,           /* reserved for bounded device waits */
+    PD_ERR_STATE = 8              /* call not valid in the handle's current state */
+} pd_status;
+
+#define PD_PREC_F64 64   /* FP64 throughout */
+#define PD_PREC_F32 32   /* FP32 bond arithmetic; FP64 displacement accumulation and
+                            an FP64 re-test of bonds whose stretch is near s_c */
+#define PD_MAX_FAMILY 1024
+#define PD_MAX_BC_CLASSES 256
+
+typedef struct {
+    int32_t precision;    /* PD_PREC_F64 or PD_PREC_F32 */
+    int32_t graph_steps;  /* steps per captured CUDA graph; 0 = direct launches */
+    double dt;            /* time step, s */
+    double damping;       /* eta of Eq. 11, kg m^-3 s^-1 */
+    double density;       /* rho, kg m^-3 */
+    int32_t check_dt;     /* 1 = refuse a dt above the bound of Silling & Askari (2005) */
+    int32_t device;       /* CUDA device ordinal */
+    void* stream;         /* cudaStream_t to queue work on; NULL = library-owned stream */
+    int32_t block_threads;/* threads per block of the step kernel; 0 = default (256) */
+    int32_t blocks_per_sm;/* resident blocks per SM for the step grid; 0 = default */
+} pd_config;
+
+typedef struct {
+    double c;             /* micromodulus, Eq. 5 (see pd_micromodulus) */
+    double sc;            /* critical stretch, used when sc_mode == 0 */
+    int32_t sc_mode;      /* 0 = constant sc; 1 = per-bond draw U[sc_lo, sc_hi) */
+    int32_t reserved;
+    uint64_t sc_seed;     /* sc_mode 1: SplitMix64 seed; bond {i,j} uses output
+                             min(i,j)*2^32 + max(i,j) + 1 of the stream (caller ids) */
+    double sc_lo, sc_hi;
+} pd_material;
+
+typedef struct {
+    const uint8_t* type;   /* n*3: 1 = displacement-controlled component, 0 = free */
+    const double* disp;    /* n*3: prescribed displacement per unit scale (NULL = 0) */
+    const double* force;   /* n*3: body-force density per unit load, N m^-3 (NULL = 0) */
+    const uint8_t* no_fail;/* n: bonds touching a flagged node never break (NULL = none) */
+    double disp_rate;      /* displacement scale after step k is disp_rate * k */
+    double load;           /* body-force scale */
+} pd_bc;
+
+typedef struct {
+    int64_t n;            /* nodes */
+    int64_t n_bonds;      /* directed bonds in the family after the initial cuts */
+    int64_t step;         /* steps taken so far (index of the next step) */
+    int32_t precision;
+    int32_t ell_width;    /* padded family width used on the device (multiple of 32) */
+    int64_t device_bytes; /* device memory held by the handle */
+} pd_info_t;
+
+/*
+ * pd_micromodulus - c = 18 K / (pi delta^4) (Eq. 5, Section 2.2).
+ * K: bulk modulus (Pa), delta: horizon (m).  PD_ERR_ARG unless both > 0.
+ */
+pd_status pd_micromodulus(double K, double delta, double* c_out);
+
+/*
+ * pd_create - build a model and upload it to the GPU.
+ *  n        nodes (>= 1, < 2^31)
+ *  coords   host, n*3 reference positions x_i (m)
+ *  volumes  host, n nodal volumes dV_i (> 0)
+ *  horizon  delta (m) of the family H_i = { j != i : |x_i - x_j| <= delta } (Eq. 9)
+ *  fam_off, fam_idx  host CSR family in canonical order, or both NULL to let
+ *           the library search it (uniform cell grid, inclusive distance test)
+ *  cuts     host, n_cuts*6 doubles {axis, pos, lo_a, hi_a, lo_b, hi_b}: planar
+ *           rectangles x[axis] = pos, lo_a <= x[a] <= hi_a, lo_b <= x[b] <= hi_b
+ *           ((a, b) = the other axes ascending).  A bond whose segment crosses a
+ *           rectangle is removed before the first step (initial notch, Section 6).
+ *  mat, bc, cfg  see the structs; all required.
+ *  out      receives the handle.
+ * Returns PD_ERR_ARG for invalid sizes, non-finite inputs, non-positive volumes,
+ * more than PD_MAX_BC_CLASSES distinct (type, disp, force, no_fail) tuples;
+ * PD_ERR_FAMILY_TOO_LARGE when a family exceeds PD_MAX_FAMILY;
+ * PD_ERR_UNSTABLE_DT when cfg->check_dt is set and dt is too large;
+ * PD_ERR_OOM / PD_ERR_CUDA on allocation or runtime failure (nothing leaks).
+ * The initial state is u = v = 0 with every bond of the family intact, step 0.
+ */
+pd_status pd_create(int64_t n, const double* coords, const double* volumes, double horizon,
+                    const int64_t* fam_off, const int32_t* fam_idx,
+                    const double* cuts, int32_t n_cuts,
+                    const pd_material* mat, const pd_bc* bc, const pd_config* cfg,
+                    pd_handle** out);
+
+/* pd_destroy - release every resource of the handle (NULL is ignored). */
+void pd_destroy(pd_handle* h);
+
+/* pd_last_error - message of the last failed call on this thread ("" if none). */
+const char* pd_last_error(void);
+
+/* pd_get_info - sizes and step counter of the handle. */
+pd_status pd_get_info(pd_handle* h, pd_info_t* out);
+
+/*
+ * pd_get_family - the family after the initial cuts, canonical CSR order.
+ * off: host int64[n+1]; idx: host int32[n_bonds] (idx may be NULL to get off only).
+ */
+pd_status pd_get_family(pd_handle* h, int64_t* off, int32_t* idx);
+
+/*
+ * pd_step - advance n_steps damped Euler-Cromer steps (Eqs. 4-6, 8, 10-11):
+ * per step one fused kernel evaluates all intact bonds, breaks those with
+ * s >= s_c for good (no force from a bond in the step it breaks, Algorithm
+ * bond_index), reduces F_i, adds load * force_i, updates
+ * v <- v + dt (F - eta v) / rho and u <- u + dt v, overwrites controlled
+ * components with u = disp * disp_rate * (k+1), v = disp * disp_rate / dt,
+ * and writes the damage.  Asynchronous on the handle's stream; a non-finite
+ * displacement is reported by the next synchronising call (PD_ERR_NONFINITE).
+ * n_steps >= 0.
+ */
+pd_status pd_step(pd_handle* h, int64_t n_steps);
+
+/* pd_sync - wait for queued work and report device-side errors. */
+pd_status pd_sync(pd_handle* h);
+
+/*
+ * pd_get_state / pd_set_state - displacement and velocity (n*3 doubles each,
+ * host or device, either may be NULL) and the step counter (host, may be NULL).
+ * pd_set_state also accepts step < 0 to keep the current counter.
+ */
+pd_status pd_get_state(pd_handle* h, double* u, double* v, int64_t* step);
+pd_status pd_set_state(pd_handle* h, const double* u, const double* v, int64_t step);
+
+/*
+ * pd_get_bonds / pd_set_bonds - bond flags mu (1 intact, 0 broken), one byte per
+ * directed bond in canonical order (host).  pd_set_bonds rejects values other than 0/1.
+ */
+pd_status pd_get_bonds(pd_handle* h, uint8_t* mu);
+pd_status pd_set_bonds(pd_handle* h, const uint8_t* mu);
+
+/*
+ * pd_damage - phi_i = 1 - sum_j mu_ij V_j / sum_j V_j over the family after the
+ * initial cuts (Eq. 8), for the current state.  phi: n doubles, host or device.
+ */
+pd_status pd_damage(pd_handle* h, double* phi);
+
+/*
+ * pd_set_params - change material and load without rebuilding the model
+ * (Section 3.6, "Running simulations").  c > 0, sc > 0, load and disp_rate
+ * finite.  sc applies to sc_mode 0.  c_bond: host, per directed bond in
+ * canonical order (> 0, symmetric between i->j and j->i), or NULL for the
+ * constant c.
+ */
+pd_status pd_set_params(pd_handle* h, double c, double sc, double load, double disp_rate,
+                        const double* c_bond);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PD_H */

@@ -1,0 +1,327 @@
+"""GB300-native bond-based peridynamic time stepper (arXiv 2105.04150).
+
+Thin ctypes binding over the C ABI of ``include/pd.h``: the functions keep the
+C names (``pd_create``, ``pd_step``, ...) and only marshal arguments.  Every
+step of the computation runs in the CUDA library ``_libpd.so`` built for
+sm_103a; there is no CPU fallback, and importing the binding raises when the
+library has not been built.
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); they must
+be C-contiguous with the documented dtype.  PyTorch is only used by callers
+for device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Any, Optional, Sequence
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "PdError", "build", "lib", "pd_micromodulus", "pd_create", "pd_destroy", "pd_last_error",
+    "pd_get_info", "pd_get_family", "pd_step", "pd_sync", "pd_get_state", "pd_set_state",
+    "pd_get_bonds", "pd_set_bonds", "pd_damage", "pd_set_params", "Model",
+    "PD_PREC_F32", "PD_PREC_F64",
+]
+
+PD_PREC_F64 = 64
+PD_PREC_F32 = 32
+_STATUS = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_CUDA", 3: "PD_ERR_OOM",
+           4: "PD_ERR_NONFINITE", 5: "PD_ERR_UNSTABLE_DT", 6: "PD_ERR_FAMILY_TOO_LARGE",
+           7: "PD_ERR_TIMEOUT", 8: "PD_ERR_STATE"}
+
+
+class PdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.name = _STATUS.get(status, str(status))
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("graph_steps", ctypes.c_int32),
+                ("dt", ctypes.c_double), ("damping", ctypes.c_double),
+                ("density", ctypes.c_double), ("check_dt", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+
+
+class _Material(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_double), ("sc", ctypes.c_double), ("sc_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("sc_seed", ctypes.c_uint64),
+                ("sc_lo", ctypes.c_double), ("sc_hi", ctypes.c_double)]
+
+
+class _Bc(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_void_p), ("disp", ctypes.c_void_p),
+                ("force", ctypes.c_void_p), ("no_fail", ctypes.c_void_p),
+                ("disp_rate", ctypes.c_double), ("load", ctypes.c_double)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_bonds", ctypes.c_int64), ("step", ctypes.c_int64),
+                ("precision", ctypes.c_int32), ("ell_width", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the CUDA library in-tree (sm_103a)."""
+    return _build.build(force=force)
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise ImportError(
+                f"CUDA library {_build.LIB} is missing: run paper_2105_04150_gb300.build()")
+        L = ctypes.CDLL(_build.LIB)
+        P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        sig = {
+            "pd_micromodulus": [D, D, P],
+            "pd_create": [I64, P, P, D, P, P, P, I32, P, P, P, P],
+            "pd_get_info": [P, P],
+            "pd_get_family": [P, P, P],
+            "pd_step": [P, I64],
+            "pd_sync": [P],
+            "pd_get_state": [P, P, P, P],
+            "pd_set_state": [P, P, P, I64],
+            "pd_get_bonds": [P, P],
+            "pd_set_bonds": [P, P],
+            "pd_damage": [P, P],
+            "pd_set_params": [P, D, D, D, D, P],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.pd_destroy.argtypes = [P]
+        L.pd_destroy.restype = None
+        L.pd_last_error.argtypes = []
+        L.pd_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def pd_last_error() -> str:
+    return lib().pd_last_error().decode()
+
+
+def _check(st: int):
+    if st != 0:
+        raise PdError(st, pd_last_error())
+
+
+def _ptr(a: Any, dtype, count: Optional[int] = None, writable: bool = False):
+    """(address, keep-alive) of a numpy array or torch tensor; None -> (None, None)."""
+    if a is None:
+        return None, None
+    mod = type(a).__module__
+    if mod.startswith("torch"):
+        import torch
+        tdt = {np.float64: torch.float64, np.int64: torch.int64, np.int32: torch.int32,
+               np.uint8: torch.uint8, np.float32: torch.float32}[dtype]
+        if a.dtype != tdt or not a.is_contiguous():
+            raise TypeError(f"tensor must be contiguous {tdt}")
+        if count is not None and a.numel() != count:
+            raise ValueError(f"expected {count} elements, got {a.numel()}")
+        return a.data_ptr(), a
+    arr = np.asarray(a)
+    if writable:
+        if arr.dtype != dtype or not arr.flags.c_contiguous or not arr.flags.writeable:
+            raise TypeError(f"output array must be writable C-contiguous {np.dtype(dtype)}")
+    else:
+        arr = np.ascontiguousarray(arr, dtype=dtype)
+    if count is not None and arr.size != count:
+        raise ValueError(f"expected {count} elements, got {arr.size}")
+    return arr.ctypes.data, arr
+
+
+def pd_micromodulus(K: float, delta: float) -> float:
+    c = ctypes.c_double()
+    _check(lib().pd_micromodulus(float(K), float(delta), ctypes.byref(c)))
+    return c.value
+
+
+def pd_create(coords, volumes, horizon: float, *, c: float, sc: float = 0.0,
+              sc_hash=None, fam_off=None, fam_idx=None, cuts=None, bc_type=None, bc_disp=None,
+              bc_force=None, no_fail=None, disp_rate: float = 0.0, load: float = 0.0,
+              dt: float, damping: float, density: float, precision: int = PD_PREC_F64,
+              graph_steps: int = 0, check_dt: bool = False, device: int = 0, stream=None,
+              block_threads: int = 0, blocks_per_sm: int = 0) -> int:
+    """Create a model; returns an opaque handle (int).  See pd.h for the semantics."""
+    x, kx = _ptr(coords, np.float64)
+    n = (kx.numel() if hasattr(kx, "numel") else kx.size) // 3
+    vol, kv = _ptr(volumes, np.float64, n)
+    fo, kfo = _ptr(fam_off, np.int64, n + 1 if fam_off is not None else None)
+    fi, kfi = _ptr(fam_idx, np.int32)
+    if cuts is not None and len(cuts):
+        cuts_arr = np.ascontiguousarray(np.asarray(cuts, dtype=np.float64).reshape(-1, 6))
+    else:
+        cuts_arr = None
+    cp, kc = _ptr(cuts_arr, np.float64)
+    ncut = 0 if cuts_arr is None else cuts_arr.shape[0]
+    if bc_type is None:
+        bc_type = np.zeros((n, 3), np.uint8)
+    bt, kbt = _ptr(bc_type, np.uint8, 3 * n)
+    bd, kbd = _ptr(bc_disp, np.float64, 3 * n if bc_disp is not None else None)
+    bf, kbf = _ptr(bc_force, np.float64, 3 * n if bc_force is not None else None)
+    nf, knf = _ptr(no_fail, np.uint8, n if no_fail is not None else None)
+    mat = _Material(c=float(c), sc=float(sc), sc_mode=0)
+    if sc_hash is not None:
+        mat.sc_mode = 1
+        mat.sc_seed, mat.sc_lo, mat.sc_hi = int(sc_hash[0]), float(sc_hash[1]), float(sc_hash[2])
+    bc = _Bc(type=bt, disp=bd, force=bf, no_fail=nf, disp_rate=float(disp_rate),
+             load=float(load))
+    cfg = _Config(precision=int(precision), graph_steps=int(graph_steps), dt=float(dt),
+                  damping=float(damping), density=float(density), check_dt=int(bool(check_dt)),
+                  device=int(device), stream=stream, block_threads=int(block_threads),
+                  blocks_per_sm=int(blocks_per_sm))
+    h = ctypes.c_void_p()
+    _check(lib().pd_create(n, x, vol, float(horizon), fo, fi, cp, ncut, ctypes.byref(mat),
+                           ctypes.byref(bc), ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def pd_destroy(h: int) -> None:
+    if h:
+        lib().pd_destroy(h)
+
+
+def pd_get_info(h: int) -> dict:
+    info = _Info()
+    _check(lib().pd_get_info(h, ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in _Info._fields_}
+
+
+def pd_get_family(h: int):
+    info = pd_get_info(h)
+    off = np.empty(info["n"] + 1, np.int64)
+    idx = np.empty(max(info["n_bonds"], 1), np.int32)
+    _check(lib().pd_get_family(h, off.ctypes.data, idx.ctypes.data))
+    return off, idx[: info["n_bonds"]]
+
+
+def pd_step(h: int, n_steps: int) -> None:
+    _check(lib().pd_step(h, int(n_steps)))
+
+
+def pd_sync(h: int) -> None:
+    _check(lib().pd_sync(h))
+
+
+def pd_get_state(h: int, u=None, v=None) -> int:
+    """Fill u and/or v (n*3 float64, host or device); returns the step counter."""
+    n = pd_get_info(h)["n"]
+    up, ku = _ptr(u, np.float64, 3 * n, writable=True)
+    vp, kv = _ptr(v, np.float64, 3 * n, writable=True)
+    step = ctypes.c_int64()
+    _check(lib().pd_get_state(h, up, vp, ctypes.byref(step)))
+    return step.value
+
+
+def pd_set_state(h: int, u=None, v=None, step: int = -1) -> None:
+    n = pd_get_info(h)["n"]
+    up, ku = _ptr(u, np.float64, 3 * n)
+    vp, kv = _ptr(v, np.float64, 3 * n)
+    _check(lib().pd_set_state(h, up, vp, int(step)))
+
+
+def pd_get_bonds(h: int) -> np.ndarray:
+    nb = pd_get_info(h)["n_bonds"]
+    mu = np.empty(max(nb, 1), np.uint8)
+    _check(lib().pd_get_bonds(h, mu.ctypes.data))
+    return mu[:nb]
+
+
+def pd_set_bonds(h: int, mu) -> None:
+    nb = pd_get_info(h)["n_bonds"]
+    p, k = _ptr(mu, np.uint8, nb)
+    if nb == 0:
+        return
+    _check(lib().pd_set_bonds(h, p))
+
+
+def pd_damage(h: int, phi=None):
+    """Damage per node (Eq. 8) into phi (n float64, host or device) or a new numpy array."""
+    n = pd_get_info(h)["n"]
+    if phi is None:
+        phi = np.empty(n, np.float64)
+    p, k = _ptr(phi, np.float64, n, writable=True)
+    _check(lib().pd_damage(h, p))
+    return phi
+
+
+def pd_set_params(h: int, c: float, sc: float, load: float, disp_rate: float,
+                  c_bond=None) -> None:
+    nb = pd_get_info(h)["n_bonds"]
+    p, k = _ptr(c_bond, np.float64, nb if c_bond is not None else None)
+    _check(lib().pd_set_params(h, float(c), float(sc), float(load), float(disp_rate), p))
+
+
+class Model:
+    """Owning wrapper of one handle (calls the pd_* functions above)."""
+
+    def __init__(self, **kw):
+        self.h = pd_create(**kw)
+
+    @classmethod
+    def from_workload(cls, w, precision=PD_PREC_F64, c=None, **kw):
+        if c is None:
+            c = pd_micromodulus(w.bulk_modulus, w.horizon)
+        return cls(coords=w.coords, volumes=w.volumes, horizon=w.horizon, c=c, sc=w.sc,
+                   sc_hash=w.sc_hash, cuts=w.cuts_array(), bc_type=w.bc_type, bc_disp=w.bc_disp,
+                   bc_force=w.bc_force, no_fail=w.no_fail, disp_rate=w.disp_rate, load=w.load,
+                   dt=w.dt, damping=w.damping, density=w.density, precision=precision, **kw)
+
+    def close(self):
+        if self.h:
+            pd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        return pd_get_info(self.h)
+
+    def step(self, n):
+        pd_step(self.h, n)
+
+    def sync(self):
+        pd_sync(self.h)
+
+    def state(self):
+        n = self.info()["n"]
+        u = np.empty((n, 3))
+        v = np.empty((n, 3))
+        pd_get_state(self.h, u, v)
+        return u, v
+
+    def set_state(self, u=None, v=None, step=-1):
+        pd_set_state(self.h, u, v, step)
+
+    def bonds(self):
+        return pd_get_bonds(self.h)
+
+    def set_bonds(self, mu):
+        pd_set_bonds(self.h, mu)
+
+    def damage(self, phi=None):
+        return pd_damage(self.h, phi)
+
+    def family(self):
+        return pd_get_family(self.h)
+
+    def set_params(self, c, sc, load, disp_rate, c_bond=None):
+        pd_set_params(self.h, c, sc, load, disp_rate, c_bond)

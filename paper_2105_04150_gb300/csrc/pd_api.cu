@@ -1,0 +1,760 @@
+// C ABI of the peridynamic step library: handle lifecycle, step orchestration
+// (direct launches or captured CUDA graphs of `graph_steps` steps driven by a
+// device step counter), state transfer and parameter updates.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pd.h"
+#include "pd_internal.h"
+#include "pd_prep.h"
+
+using namespace pd;
+
+namespace {
+
+thread_local std::string g_err;
+
+pd_status fail(pd_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+pd_status cuda_fail(cudaError_t e, const char* what)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(PD_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(PD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define PD_CUDA(call, what)                      \
+    do {                                         \
+        cudaError_t e_ = (call);                 \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+bool is_device_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct pd_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int precision = 64;
+    int Q = 1;
+    int64_t n = 0, n_bonds = 0;
+    double delta = 0, dt = 0, eta = 0, rho = 0;
+    double c = 0, sc = 0, sc_lo = 0, sc_hi = 0;
+    int sc_mode = 0;
+    uint64_t sc_seed = 0;
+    double disp_rate = 0, load = 0;
+    bool has_nofail = false;
+    bool per_bond_c = false;
+    int64_t step = 0;
+    int graph_steps = 0;
+    cudaGraphExec_t graph = nullptr;
+    int grid = 0, block = 256;
+    bool damage_fresh = false;
+
+    std::vector<int64_t> off;   // canonical family after cuts
+    std::vector<int32_t> idx;
+    std::vector<int32_t> perm, inv, cnt;
+
+    std::vector<void*> allocs;
+    int64_t device_bytes = 0;
+    void* rec[2] = {nullptr, nullptr};
+    double* u64[2] = {nullptr, nullptr};
+    void* v = nullptr;
+    int32_t* nbr = nullptr;
+    uint32_t* bits = nullptr;
+    void* cbond = nullptr;
+    uint8_t* bcc = nullptr;
+    BcClass* bct = nullptr;
+    int32_t* gid = nullptr;
+    int32_t* fam_cnt = nullptr;
+    double* x64 = nullptr;
+    double* vol = nullptr;
+    void* wsum_inv = nullptr;
+    void* damage = nullptr;
+    int* err = nullptr;
+    int64_t* step_ctr = nullptr;
+    double* staging = nullptr;  // 3n doubles for host transfers
+
+    template <class T>
+    cudaError_t alloc(T** p, size_t count)
+    {
+        void* q = nullptr;
+        const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+        cudaError_t e = cudaMalloc(&q, bytes);
+        if (e != cudaSuccess) return e;
+        allocs.push_back(q);
+        device_bytes += (int64_t)bytes;
+        *p = (T*)q;
+        return cudaSuccess;
+    }
+
+    void release()
+    {
+        if (graph) cudaGraphExecDestroy(graph);
+        graph = nullptr;
+        for (void* p : allocs) cudaFree(p);
+        allocs.clear();
+        if (own_stream && stream) cudaStreamDestroy(stream);
+        stream = nullptr;
+    }
+
+    void drop_graph()
+    {
+        if (graph) cudaGraphExecDestroy(graph);
+        graph = nullptr;
+    }
+};
+
+namespace {
+
+StepArgsF32 args_f32(pd_handle* h, int k)
+{
+    StepArgsF32 a{};
+    a.rec[0] = (const float4*)h->rec[0];
+    a.rec[1] = (const float4*)h->rec[1];
+    a.u64[0] = h->u64[0];
+    a.u64[1] = h->u64[1];
+    a.v = (float*)h->v;
+    a.nbr = h->nbr;
+    a.bits = h->bits;
+    a.cbond = h->per_bond_c ? (const float*)h->cbond : nullptr;
+    a.bcc = h->bcc;
+    a.bct = h->bct;
+    a.gid = h->gid;
+    a.x64 = h->x64;
+    a.wsum_inv = (const float*)h->wsum_inv;
+    a.damage = (float*)h->damage;
+    a.err = h->err;
+    a.step_ctr = h->step_ctr;
+    a.n = h->n;
+    a.k = k;
+    a.q_rt = h->Q;
+    a.has_nofail = h->has_nofail ? 1 : 0;
+    a.sc_f = (float)h->sc;
+    a.sc_lo_f = (float)h->sc_lo;
+    a.guard = 5e-4f;
+    a.sc = h->sc;
+    a.sc_lo = h->sc_lo;
+    a.sc_hi = h->sc_hi;
+    a.sc_seed = h->sc_seed;
+    a.dt = h->dt;
+    a.eta = h->eta;
+    a.rho = h->rho;
+    a.disp_rate = h->disp_rate;
+    a.load = h->load;
+    a.inv_delta = 1.0 / h->delta;
+    return a;
+}
+
+StepArgsF64 args_f64(pd_handle* h, int k)
+{
+    StepArgsF64 a{};
+    a.rec[0] = (const double*)h->rec[0];
+    a.rec[1] = (const double*)h->rec[1];
+    a.v = (double*)h->v;
+    a.nbr = h->nbr;
+    a.bits = h->bits;
+    a.cbond = h->per_bond_c ? (const double*)h->cbond : nullptr;
+    a.bcc = h->bcc;
+    a.bct = h->bct;
+    a.gid = h->gid;
+    a.wsum_inv = (const double*)h->wsum_inv;
+    a.damage = (double*)h->damage;
+    a.err = h->err;
+    a.step_ctr = h->step_ctr;
+    a.n = h->n;
+    a.k = k;
+    a.q_rt = h->Q;
+    a.has_nofail = h->has_nofail ? 1 : 0;
+    a.sc = h->sc;
+    a.sc_lo = h->sc_lo;
+    a.sc_hi = h->sc_hi;
+    a.sc_seed = h->sc_seed;
+    a.dt = h->dt;
+    a.eta = h->eta;
+    a.rho = h->rho;
+    a.disp_rate = h->disp_rate;
+    a.load = h->load;
+    return a;
+}
+
+cudaError_t launch_one(pd_handle* h, int k)
+{
+    if (h->precision == 32)
+        return launch_step_f32(args_f32(h, k), h->Q, h->sc_mode, h->grid, h->block, h->stream);
+    return launch_step_f64(args_f64(h, k), h->Q, h->sc_mode, h->grid, h->block, h->stream);
+}
+
+pd_status choose_grid(pd_handle* h, int blocks_per_sm)
+{
+    int sms = 0;
+    PD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "sm count");
+    const void* fn = h->precision == 32 ? step_f32_kernel(h->Q, h->sc_mode)
+                                        : step_f64_kernel(h->Q, h->sc_mode);
+    int occ = 0;
+    PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, h->block, 0), "occupancy");
+    if (occ < 1) occ = 1;
+    if (blocks_per_sm > 0) occ = std::min(occ, blocks_per_sm);
+    const int64_t groups = (h->n + 31) / 32;
+    const int64_t warps_per_block = h->block / 32;
+    const int64_t need = (groups + warps_per_block - 1) / warps_per_block;
+    h->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * occ, need));
+    return PD_OK;
+}
+
+pd_status upload_weights(pd_handle* h)
+{
+    const double wscale = h->per_bond_c ? 1.0 : h->c;
+    PD_CUDA(launch_set_weights(h->precision, h->rec[0], h->rec[1], h->vol, h->nbr, h->fam_cnt,
+                               h->n, h->Q, wscale, h->wsum_inv, h->stream),
+            "set weights");
+    return PD_OK;
+}
+
+pd_status check_dev_err(pd_handle* h)
+{
+    int e = 0;
+    PD_CUDA(cudaMemcpyAsync(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream),
+            "read error flag");
+    PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
+    if (e & PD_DEVERR_NONFINITE)
+        return fail(PD_ERR_NONFINITE, "a displacement became non-finite (check dt and loads)");
+    return PD_OK;
+}
+
+bool finite_all(const double* p, int64_t m)
+{
+    for (int64_t i = 0; i < m; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pd_last_error(void) { return g_err.c_str(); }
+
+pd_status pd_micromodulus(double K, double delta, double* c_out)
+{
+    if (!c_out) return fail(PD_ERR_ARG, "c_out is NULL");
+    if (!(K > 0.0) || !(delta > 0.0) || !std::isfinite(K) || !std::isfinite(delta))
+        return fail(PD_ERR_ARG, "K and delta must be finite and > 0");
+    const double d4 = delta * delta * delta * delta;
+    *c_out = 18.0 * K / (M_PI * d4);
+    return PD_OK;
+}
+
+pd_status pd_create(int64_t n, const double* coords, const double* volumes, double horizon,
+                    const int64_t* fam_off, const int32_t* fam_idx, const double* cuts,
+                    int32_t n_cuts, const pd_material* mat, const pd_bc* bc,
+                    const pd_config* cfg, pd_handle** out)
+{
+    g_err.clear();
+    if (!out) return fail(PD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n >= (int64_t)1 << 31) return fail(PD_ERR_ARG, "n must be in [1, 2^31)");
+    if (!coords || !volumes || !mat || !bc || !cfg)
+        return fail(PD_ERR_ARG, "coords, volumes, mat, bc and cfg are required");
+    if (!bc->type) return fail(PD_ERR_ARG, "bc->type is required");
+    if ((fam_off == nullptr) != (fam_idx == nullptr))
+        return fail(PD_ERR_ARG, "fam_off and fam_idx must both be given or both be NULL");
+    if (n_cuts < 0 || (n_cuts > 0 && !cuts)) return fail(PD_ERR_ARG, "invalid cuts");
+    if (cfg->precision != PD_PREC_F32 && cfg->precision != PD_PREC_F64)
+        return fail(PD_ERR_ARG, "precision must be 32 or 64");
+    if (!(horizon > 0.0) || !std::isfinite(horizon)) return fail(PD_ERR_ARG, "horizon must be > 0");
+    if (!(cfg->dt > 0.0) || !(cfg->density > 0.0) || !(cfg->damping >= 0.0) ||
+        !std::isfinite(cfg->dt) || !std::isfinite(cfg->density) || !std::isfinite(cfg->damping))
+        return fail(PD_ERR_ARG, "dt and density must be > 0, damping >= 0");
+    if (!(mat->c > 0.0) || !std::isfinite(mat->c)) return fail(PD_ERR_ARG, "c must be > 0");
+    if (mat->sc_mode == 0) {
+        if (!(mat->sc > 0.0) || !std::isfinite(mat->sc)) return fail(PD_ERR_ARG, "sc must be > 0");
+    } else if (mat->sc_mode == 1) {
+        if (!(mat->sc_lo > 0.0) || !(mat->sc_hi > mat->sc_lo) || !std::isfinite(mat->sc_hi))
+            return fail(PD_ERR_ARG, "need 0 < sc_lo < sc_hi");
+    } else {
+        return fail(PD_ERR_ARG, "sc_mode must be 0 or 1");
+    }
+    if (!std::isfinite(bc->disp_rate) || !std::isfinite(bc->load))
+        return fail(PD_ERR_ARG, "disp_rate and load must be finite");
+    if (cfg->graph_steps < 0 || cfg->graph_steps > 4096)
+        return fail(PD_ERR_ARG, "graph_steps must be in [0, 4096]");
+    if (cfg->block_threads != 0 &&
+        (cfg->block_threads < 32 || cfg->block_threads > 256 || cfg->block_threads % 32))
+        return fail(PD_ERR_ARG, "block_threads must be a multiple of 32 in [32, 256]");
+    if (!finite_all(coords, 3 * n)) return fail(PD_ERR_ARG, "non-finite coordinates");
+    for (int64_t i = 0; i < n; ++i)
+        if (!(volumes[i] > 0.0) || !std::isfinite(volumes[i]))
+            return fail(PD_ERR_ARG, "volumes must be finite and > 0");
+
+    pd_handle* h = new (std::nothrow) pd_handle();
+    if (!h) return fail(PD_ERR_OOM, "host allocation");
+    auto bail = [&](pd_status st) {
+        h->release();
+        delete h;
+        return st;
+    };
+
+    // ---- family, notch, order, layout (host)
+    std::string msg;
+    if (fam_off) {
+        msg = check_family(n, fam_off, fam_idx);
+        if (!msg.empty()) return bail(fail(PD_ERR_ARG, "%s", msg.c_str()));
+        h->off.assign(fam_off, fam_off + n + 1);
+        h->idx.assign(fam_idx, fam_idx + fam_off[n]);
+    } else {
+        msg = search_family(n, coords, horizon, h->off, h->idx);
+        if (!msg.empty()) return bail(fail(PD_ERR_ARG, "%s", msg.c_str()));
+    }
+    apply_cuts(n, coords, cuts, n_cuts, h->off, h->idx);
+    int64_t maxfam = 0;
+    for (int64_t i = 0; i < n; ++i) maxfam = std::max(maxfam, h->off[i + 1] - h->off[i]);
+    if (maxfam > PD_MAX_FAMILY)
+        return bail(fail(PD_ERR_FAMILY_TOO_LARGE, "largest family has %lld members (max %d)",
+                         (long long)maxfam, PD_MAX_FAMILY));
+    h->Q = (int)std::max<int64_t>(1, (maxfam + 31) / 32);
+    h->n = n;
+    h->n_bonds = h->off[n];
+    h->precision = cfg->precision;
+    h->delta = horizon;
+    h->dt = cfg->dt;
+    h->eta = cfg->damping;
+    h->rho = cfg->density;
+    h->c = mat->c;
+    h->sc = mat->sc_mode == 0 ? mat->sc : 0.5 * (mat->sc_lo + mat->sc_hi);
+    h->sc_mode = mat->sc_mode;
+    h->sc_seed = mat->sc_seed;
+    h->sc_lo = mat->sc_mode == 1 ? mat->sc_lo : mat->sc;
+    h->sc_hi = mat->sc_mode == 1 ? mat->sc_hi : mat->sc;
+    h->disp_rate = bc->disp_rate;
+    h->load = bc->load;
+    h->graph_steps = cfg->graph_steps;
+    h->block = cfg->block_threads ? cfg->block_threads : 256;
+    h->device = cfg->device;
+
+    if (cfg->check_dt) {
+        const double dtc = stable_dt(n, coords, volumes, h->off, h->idx, h->c, h->rho);
+        if (h->dt > dtc)
+            return bail(fail(PD_ERR_UNSTABLE_DT, "dt = %g exceeds the stable bound %g", h->dt, dtc));
+    }
+
+    std::vector<BcClass> table;
+    std::vector<uint8_t> cls;
+    msg = bc_classes(n, bc->type, bc->disp, bc->force, bc->no_fail, table, cls, h->has_nofail);
+    if (!msg.empty()) return bail(fail(PD_ERR_ARG, "%s", msg.c_str()));
+
+    spatial_order(n, coords, horizon, h->perm, h->inv);
+    std::vector<int32_t> nbr;
+    std::vector<uint32_t> bits;
+    build_layout(n, h->off, h->idx, h->perm, h->inv, h->Q, nbr, bits, h->cnt);
+
+    // ---- device
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaSetDevice"));
+    if (cfg->stream) {
+        h->stream = (cudaStream_t)cfg->stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "stream create"));
+        h->own_stream = true;
+    }
+    const int64_t W = 32LL * h->Q;
+    const bool f32 = h->precision == 32;
+    const size_t recb = f32 ? 32 : 64;
+#define ALLOC(ptr, type, count)                                     \
+    do {                                                            \
+        e = h->alloc((type**)&(ptr), (size_t)(count));              \
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc " #ptr)); \
+    } while (0)
+    ALLOC(h->rec[0], uint8_t, recb * n);
+    ALLOC(h->rec[1], uint8_t, recb * n);
+    if (f32) {
+        ALLOC(h->u64[0], double, 3 * n);
+        ALLOC(h->u64[1], double, 3 * n);
+        ALLOC(h->v, float, 3 * n);
+        ALLOC(h->wsum_inv, float, n);
+        ALLOC(h->damage, float, n);
+    } else {
+        ALLOC(h->v, double, 3 * n);
+        ALLOC(h->wsum_inv, double, n);
+        ALLOC(h->damage, double, n);
+    }
+    ALLOC(h->nbr, int32_t, n * W);
+    ALLOC(h->bits, uint32_t, n * h->Q);
+    ALLOC(h->bcc, uint8_t, n);
+    ALLOC(h->bct, BcClass, table.size());
+    ALLOC(h->gid, int32_t, n);
+    ALLOC(h->fam_cnt, int32_t, n);
+    ALLOC(h->x64, double, 3 * n);
+    ALLOC(h->vol, double, n);
+    ALLOC(h->err, int, 1);
+    ALLOC(h->step_ctr, int64_t, 1);
+    ALLOC(h->staging, double, 3 * n);
+#undef ALLOC
+
+    // node records in spatial order
+    double lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) lo[a] = hi[a] = coords[a];
+    for (int64_t i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], coords[3 * i + a]);
+            hi[a] = std::max(hi[a], coords[3 * i + a]);
+        }
+    double ctr[3];
+    for (int a = 0; a < 3; ++a) ctr[a] = 0.5 * (lo[a] + hi[a]);
+    std::vector<double> xs(3 * n), vs(n);
+    std::vector<uint8_t> clsp(n);
+    for (int64_t p = 0; p < n; ++p) {
+        const int64_t i = h->perm[p];
+        for (int a = 0; a < 3; ++a) xs[3 * p + a] = coords[3 * i + a];
+        vs[p] = volumes[i];
+        clsp[p] = cls[i];
+    }
+    auto up = [&](void* dst, const void* src, size_t bytes, const char* what) -> pd_status {
+        cudaError_t ee = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->stream);
+        if (ee != cudaSuccess) return cuda_fail(ee, what);
+        return PD_OK;
+    };
+    pd_status st;
+    if (f32) {
+        std::vector<float4> r(2 * n);
+        for (int64_t p = 0; p < n; ++p) {
+            r[2 * p] = make_float4((float)((xs[3 * p] - ctr[0]) / horizon),
+                                   (float)((xs[3 * p + 1] - ctr[1]) / horizon),
+                                   (float)((xs[3 * p + 2] - ctr[2]) / horizon), 0.0f);
+            r[2 * p + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if ((st = up(h->rec[0], r.data(), 32 * n, "upload records")) ||
+            (st = up(h->rec[1], r.data(), 32 * n, "upload records")))
+            return bail(st);
+        cudaStreamSynchronize(h->stream);
+        e = cudaMemsetAsync(h->u64[0], 0, 24 * n, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->u64[1], 0, 24 * n, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->v, 0, 12 * n, h->stream);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "memset"));
+    } else {
+        std::vector<double> r(8 * n, 0.0);
+        for (int64_t p = 0; p < n; ++p)
+            for (int a = 0; a < 3; ++a) r[8 * p + a] = xs[3 * p + a];
+        if ((st = up(h->rec[0], r.data(), 64 * n, "upload records")) ||
+            (st = up(h->rec[1], r.data(), 64 * n, "upload records")))
+            return bail(st);
+        cudaStreamSynchronize(h->stream);
+        e = cudaMemsetAsync(h->v, 0, 24 * n, h->stream);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "memset"));
+    }
+    if ((st = up(h->nbr, nbr.data(), nbr.size() * 4, "upload family")) ||
+        (st = up(h->bits, bits.data(), bits.size() * 4, "upload bond flags")) ||
+        (st = up(h->bcc, clsp.data(), n, "upload bc classes")) ||
+        (st = up(h->bct, table.data(), table.size() * sizeof(BcClass), "upload bc table")) ||
+        (st = up(h->gid, h->perm.data(), 4 * n, "upload ids")) ||
+        (st = up(h->fam_cnt, h->cnt.data(), 4 * n, "upload counts")) ||
+        (st = up(h->x64, xs.data(), 24 * n, "upload coordinates")) ||
+        (st = up(h->vol, vs.data(), 8 * n, "upload volumes")))
+        return bail(st);
+    e = cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->step_ctr, 0, sizeof(int64_t), h->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "memset"));
+    if ((st = upload_weights(h)) != PD_OK) return bail(st);
+    if ((st = choose_grid(h, cfg->blocks_per_sm)) != PD_OK) return bail(st);
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "synchronize"));
+    *out = h;
+    return PD_OK;
+}
+
+void pd_destroy(pd_handle* h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    h->release();
+    delete h;
+}
+
+pd_status pd_get_info(pd_handle* h, pd_info_t* out)
+{
+    if (!h || !out) return fail(PD_ERR_ARG, "NULL argument");
+    out->n = h->n;
+    out->n_bonds = h->n_bonds;
+    out->step = h->step;
+    out->precision = h->precision;
+    out->ell_width = 32 * h->Q;
+    out->device_bytes = h->device_bytes;
+    return PD_OK;
+}
+
+pd_status pd_get_family(pd_handle* h, int64_t* off, int32_t* idx)
+{
+    if (!h || !off) return fail(PD_ERR_ARG, "NULL argument");
+    std::memcpy(off, h->off.data(), sizeof(int64_t) * (h->n + 1));
+    if (idx) std::memcpy(idx, h->idx.data(), sizeof(int32_t) * h->n_bonds);
+    return PD_OK;
+}
+
+pd_status pd_step(pd_handle* h, int64_t n_steps)
+{
+    if (!h) return fail(PD_ERR_ARG, "NULL handle");
+    if (n_steps < 0) return fail(PD_ERR_ARG, "n_steps must be >= 0");
+    if (n_steps == 0) return PD_OK;
+    PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    int64_t left = n_steps;
+    const int G = h->graph_steps;
+    if (G > 0 && left >= G) {
+        if (!h->graph) {
+            cudaGraph_t g = nullptr;
+            PD_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal),
+                    "begin capture");
+            cudaError_t e = cudaSuccess;
+            for (int k = 0; k < G && e == cudaSuccess; ++k) e = launch_one(h, k);
+            if (e == cudaSuccess) e = launch_advance(h->step_ctr, G, h->stream);
+            cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return cuda_fail(e != cudaSuccess ? e : e2, "graph capture");
+            }
+            e = cudaGraphInstantiate(&h->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                h->graph = nullptr;
+                return cuda_fail(e, "graph instantiate");
+            }
+        }
+        while (left >= G) {
+            PD_CUDA(cudaGraphLaunch(h->graph, h->stream), "graph launch");
+            left -= G;
+            h->step += G;
+        }
+    }
+    for (int64_t k = 0; k < left; ++k) PD_CUDA(launch_one(h, (int)k), "step launch");
+    if (left > 0) {
+        PD_CUDA(launch_advance(h->step_ctr, left, h->stream), "advance");
+        h->step += left;
+    }
+    h->damage_fresh = true;
+    return PD_OK;
+}
+
+pd_status pd_sync(pd_handle* h)
+{
+    if (!h) return fail(PD_ERR_ARG, "NULL handle");
+    PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    return check_dev_err(h);
+}
+
+pd_status pd_get_state(pd_handle* h, double* u, double* v, int64_t* step)
+{
+    if (!h) return fail(PD_ERR_ARG, "NULL handle");
+    PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    const int cur = (int)(h->step & 1);
+    double* outs[2] = {u, v};
+    for (int w = 0; w < 2; ++w) {
+        double* o = outs[w];
+        if (!o) continue;
+        const bool dev = is_device_ptr(o);
+        double* dst = dev ? o : h->staging;
+        double* uo = w == 0 ? dst : nullptr;
+        double* vo = w == 1 ? dst : nullptr;
+        if (h->precision == 32)
+            PD_CUDA(launch_get_state_f32(h->u64[cur], (const float*)h->v, h->gid, h->n, uo, vo,
+                                         h->stream),
+                    "get state");
+        else
+            PD_CUDA(launch_get_state_f64((const double*)h->rec[cur], (const double*)h->v, h->gid,
+                                         h->n, uo, vo, h->stream),
+                    "get state");
+        if (!dev)
+            PD_CUDA(cudaMemcpyAsync(o, h->staging, 24 * h->n, cudaMemcpyDeviceToHost, h->stream),
+                    "copy state to host");
+    }
+    if (step) *step = h->step;
+    return check_dev_err(h);
+}
+
+pd_status pd_set_state(pd_handle* h, const double* u, const double* v, int64_t step)
+{
+    if (!h) return fail(PD_ERR_ARG, "NULL handle");
+    PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    if (step >= 0 && step != h->step) {
+        h->step = step;
+        PD_CUDA(cudaMemcpyAsync(h->step_ctr, &h->step, sizeof(int64_t), cudaMemcpyHostToDevice,
+                                h->stream),
+                "set step");
+        PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
+    }
+    const int cur = (int)(h->step & 1);
+    const double* ins[2] = {u, v};
+    for (int w = 0; w < 2; ++w) {
+        const double* in = ins[w];
+        if (!in) continue;
+        const double* src = in;
+        if (!is_device_ptr(in)) {
+            if (!finite_all(in, 3 * h->n)) return fail(PD_ERR_ARG, "non-finite state");
+            PD_CUDA(cudaMemcpyAsync(h->staging, in, 24 * h->n, cudaMemcpyHostToDevice, h->stream),
+                    "copy state to device");
+            src = h->staging;
+        }
+        const double* ui = w == 0 ? src : nullptr;
+        const double* vi = w == 1 ? src : nullptr;
+        if (h->precision == 32)
+            PD_CUDA(launch_set_state_f32(ui, vi, h->gid, h->n, 1.0 / h->delta, h->u64[cur],
+                                         (float4*)h->rec[cur], (float*)h->v, h->stream),
+                    "set state");
+        else
+            PD_CUDA(launch_set_state_f64(ui, vi, h->gid, h->n, (double*)h->rec[cur],
+                                         (double*)h->v, h->stream),
+                    "set state");
+        if (src == h->staging) PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
+    }
+    PD_CUDA(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream), "clear error flag");
+    h->damage_fresh = false;
+    return PD_OK;
+}
+
+pd_status pd_get_bonds(pd_handle* h, uint8_t* mu)
+{
+    if (!h || !mu) return fail(PD_ERR_ARG, "NULL argument");
+    PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    std::vector<uint32_t> bits((size_t)(h->n * h->Q));
+    PD_CUDA(cudaMemcpyAsync(bits.data(), h->bits, bits.size() * 4, cudaMemcpyDeviceToHost,
+                            h->stream),
+            "copy bond flags");
+    PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
+    std::vector<int32_t> nbr((size_t)(h->n * 32 * h->Q));
+    PD_CUDA(cudaMemcpy(nbr.data(), h->nbr, nbr.size() * 4, cudaMemcpyDeviceToHost), "copy family");
+    std::vector<int64_t> pos;
+    slot_to_canonical(h->n, h->off, h->idx, h->perm, nbr, h->cnt, h->Q, pos);
+    const int64_t W = 32LL * h->Q;
+    for (int64_t p = 0; p < h->n; ++p)
+        for (int64_t m = 0; m < h->cnt[p]; ++m)
+            mu[pos[p * W + m]] = (bits[p * h->Q + (m >> 5)] >> (m & 31)) & 1u;
+    return PD_OK;
+}
+
+pd_status pd_set_bonds(pd_handle* h, const uint8_t* mu)
+{
+    if (!h || !mu) return fail(PD_ERR_ARG, "NULL argument");
+    for (int64_t k = 0; k < h->n_bonds; ++k)
+        if (mu[k] > 1) return fail(PD_ERR_ARG, "bond flags must be 0 or 1");
+    PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    std::vector<int32_t> nbr((size_t)(h->n * 32 * h->Q));
+    PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
+    PD_CUDA(cudaMemcpy(nbr.data(), h->nbr, nbr.size() * 4, cudaMemcpyDeviceToHost), "copy family");
+    std::vector<int64_t> pos;
+    slot_to_canonical(h->n, h->off, h->idx, h->perm, nbr, h->cnt, h->Q, pos);
+    const int64_t W = 32LL * h->Q;
+    std::vector<uint32_t> bits((size_t)(h->n * h->Q), 0u);
+    for (int64_t p = 0; p < h->n; ++p)
+        for (int64_t m = 0; m < h->cnt[p]; ++m)
+            if (mu[pos[p * W + m]]) bits[p * h->Q + (m >> 5)] |= 1u << (m & 31);
+    PD_CUDA(cudaMemcpy(h->bits, bits.data(), bits.size() * 4, cudaMemcpyHostToDevice),
+            "upload bond flags");
+    h->damage_fresh = false;
+    return PD_OK;
+}
+
+pd_status pd_damage(pd_handle* h, double* phi)
+{
+    if (!h || !phi) return fail(PD_ERR_ARG, "NULL argument");
+    PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    const bool dev = is_device_ptr(phi);
+    double* dst = dev ? phi : h->staging;
+    const int cur = (int)(h->step & 1);
+    if (h->damage_fresh)  // written by the last step kernel (fused)
+        PD_CUDA(launch_gather_damage(h->precision, h->damage, h->gid, h->n, dst, h->stream),
+                "damage");
+    else
+        PD_CUDA(launch_damage(h->precision, h->rec[cur], h->nbr, h->bits, h->wsum_inv, h->gid,
+                              h->n, h->Q, dst, h->stream),
+                "damage");
+    if (!dev)
+        PD_CUDA(cudaMemcpyAsync(phi, h->staging, 8 * h->n, cudaMemcpyDeviceToHost, h->stream),
+                "copy damage");
+    return check_dev_err(h);
+}
+
+pd_status pd_set_params(pd_handle* h, double c, double sc, double load, double disp_rate,
+                        const double* c_bond)
+{
+    if (!h) return fail(PD_ERR_ARG, "NULL handle");
+    if (!(c > 0.0) || !std::isfinite(c)) return fail(PD_ERR_ARG, "c must be > 0");
+    if (!(sc > 0.0) || !std::isfinite(sc)) return fail(PD_ERR_ARG, "sc must be > 0");
+    if (!std::isfinite(load) || !std::isfinite(disp_rate))
+        return fail(PD_ERR_ARG, "load and disp_rate must be finite");
+    PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    if (c_bond) {
+        for (int64_t k = 0; k < h->n_bonds; ++k)
+            if (!(c_bond[k] > 0.0) || !std::isfinite(c_bond[k]))
+                return fail(PD_ERR_ARG, "c_bond must be finite and > 0");
+        std::vector<int32_t> nbr((size_t)(h->n * 32 * h->Q));
+        PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
+        PD_CUDA(cudaMemcpy(nbr.data(), h->nbr, nbr.size() * 4, cudaMemcpyDeviceToHost),
+                "copy family");
+        std::vector<int64_t> pos;
+        slot_to_canonical(h->n, h->off, h->idx, h->perm, nbr, h->cnt, h->Q, pos);
+        const size_t slots = nbr.size();
+        if (!h->cbond) {
+            cudaError_t e = h->alloc((uint8_t**)&h->cbond, slots * (h->precision == 32 ? 4 : 8));
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc c_bond");
+        }
+        if (h->precision == 32) {
+            std::vector<float> cb(slots, 0.0f);
+            for (size_t s = 0; s < slots; ++s)
+                if (pos[s] >= 0) cb[s] = (float)c_bond[pos[s]];
+            PD_CUDA(cudaMemcpy(h->cbond, cb.data(), slots * 4, cudaMemcpyHostToDevice),
+                    "upload c_bond");
+        } else {
+            std::vector<double> cb(slots, 0.0);
+            for (size_t s = 0; s < slots; ++s)
+                if (pos[s] >= 0) cb[s] = c_bond[pos[s]];
+            PD_CUDA(cudaMemcpy(h->cbond, cb.data(), slots * 8, cudaMemcpyHostToDevice),
+                    "upload c_bond");
+        }
+    }
+    const bool pbc = c_bond != nullptr;
+    const bool reweight = pbc != h->per_bond_c || (!pbc && c != h->c);
+    h->per_bond_c = pbc;
+    h->c = c;
+    if (h->sc_mode == 0) {
+        h->sc = sc;
+        h->sc_lo = h->sc_hi = sc;
+    }
+    h->load = load;
+    h->disp_rate = disp_rate;
+    h->drop_graph();
+    if (reweight) {
+        pd_status st = upload_weights(h);
+        if (st != PD_OK) return st;
+    }
+    PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
+    h->damage_fresh = false;
+    return PD_OK;
+}
+
+}  // extern "C"

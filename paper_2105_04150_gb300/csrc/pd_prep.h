@@ -1,0 +1,41 @@
+// Host-side model preparation (library internal).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "pd_internal.h"
+
+namespace pd {
+
+// Family of Eq. 9 by a uniform cell grid (edge = delta), rows ascending.
+// Returns "" on success, else an error message.
+std::string search_family(int64_t n, const double* x, double delta, std::vector<int64_t>& off,
+                          std::vector<int32_t>& idx);
+// Validate a caller-supplied canonical CSR family.
+std::string check_family(int64_t n, const int64_t* off, const int32_t* idx);
+// Remove bonds whose segment crosses a cut rectangle (initial notch, Section 6).
+void apply_cuts(int64_t n, const double* x, const double* cuts, int32_t ncuts,
+                std::vector<int64_t>& off, std::vector<int32_t>& idx);
+// perm[p] = caller id of spatial position p; inv = inverse.
+void spatial_order(int64_t n, const double* x, double delta, std::vector<int32_t>& perm,
+                   std::vector<int32_t>& inv);
+// Padded q-major family (W = 32 Q slots per node), intact-bond bits and counts.
+void build_layout(int64_t n, const std::vector<int64_t>& off, const std::vector<int32_t>& idx,
+                  const std::vector<int32_t>& perm, const std::vector<int32_t>& inv, int Q,
+                  std::vector<int32_t>& nbr, std::vector<uint32_t>& bits,
+                  std::vector<int32_t>& cnt);
+// Canonical CSR position of every device slot (-1 for padding).
+void slot_to_canonical(int64_t n, const std::vector<int64_t>& off, const std::vector<int32_t>& idx,
+                       const std::vector<int32_t>& perm, const std::vector<int32_t>& nbr,
+                       const std::vector<int32_t>& cnt, int Q, std::vector<int64_t>& pos);
+// Deduplicate per-node (type, disp, force, no_fail) tuples into <= 256 classes.
+std::string bc_classes(int64_t n, const uint8_t* type, const double* disp, const double* force,
+                       const uint8_t* no_fail, std::vector<BcClass>& table,
+                       std::vector<uint8_t>& cls, bool& has_nofail);
+// Largest stable explicit time step (Silling & Askari 2005).
+double stable_dt(int64_t n, const double* x, const double* vol, const std::vector<int64_t>& off,
+                 const std::vector<int32_t>& idx, double c, double rho);
+
+}  // namespace pd

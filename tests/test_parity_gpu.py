@@ -1,0 +1,385 @@
+"""GPU parity: the CUDA step (called through the C ABI) against the FP64 oracle.
+
+Tolerances (written here, derived from the arithmetic):
+  FP64 path   u and v within 1e-10 relative (max node error / max node value);
+              broken-bond set identical except bonds the oracle saw within
+              1e-9 (absolute stretch) of s_c at some step.
+  FP32 path   u within 1e-4 relative; broken-bond sets differ in < 0.1 % of bonds.
+Relative error = max_i |a_i - b_i| / max_i |b_i| over all node components.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2105_04150_gb300 as pdgb
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+F64, F32 = pdgb.PD_PREC_F64, pdgb.PD_PREC_F32
+BAND = 1e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pdgb.build()
+    oracle.build()
+
+
+def rel(a, b):
+    den = np.abs(b).max()
+    return np.abs(a - b).max() / (den if den > 0 else 1.0)
+
+
+def oracle_run(w, steps, c=None, c_bond=None, u0=None, v0=None, off_idx=None):
+    off, idx = off_idx if off_idx is not None else oracle.cut_family(
+        w.coords, w.horizon, w.cuts_array())
+    m = oracle.Model.from_workload(w, off, idx, c=c, c_bond=c_bond)
+    u = np.zeros((w.n, 3)) if u0 is None else u0.copy()
+    v = np.zeros((w.n, 3)) if v0 is None else v0.copy()
+    mu = m.fresh_bonds()
+    margin = np.full(m.nbonds, np.inf)
+    m.run(0, steps, u, v, mu, margin)
+    return dict(u=u, v=v, mu=mu, margin=margin, phi=m.damage(mu), off=off, idx=idx)
+
+
+def gpu_run(w, steps, precision, c=None, c_bond=None, u0=None, v0=None, **kw):
+    if c is None:
+        c = oracle.micromodulus(w.bulk_modulus, w.horizon)
+    m = pdgb.Model.from_workload(w, precision=precision, c=c, **kw)
+    if c_bond is not None:
+        m.set_params(c, w.sc, w.load, w.disp_rate, c_bond)
+    if u0 is not None or v0 is not None:
+        m.set_state(u0, v0)
+    m.step(steps)
+    m.sync()
+    u, v = m.state()
+    out = dict(u=u, v=v, mu=m.bonds(), phi=m.damage(), fam=m.family(), info=m.info())
+    m.close()
+    return out
+
+
+def check_f64(g, o, tol=1e-10):
+    assert np.array_equal(g["fam"][0], o["off"]) and np.array_equal(g["fam"][1], o["idx"])
+    assert rel(g["u"], o["u"]) <= tol, rel(g["u"], o["u"])
+    assert rel(g["v"], o["v"]) <= tol * 10, rel(g["v"], o["v"])
+    diff = g["mu"] != o["mu"]
+    assert np.all(o["margin"][diff] < BAND), int(diff.sum())
+    assert np.abs(g["phi"] - o["phi"]).max() <= 1e-12 + 2.0 * diff.sum() / max(len(diff), 1)
+
+
+def check_f32(g, o, tol=1e-4):
+    assert np.array_equal(g["fam"][0], o["off"]) and np.array_equal(g["fam"][1], o["idx"])
+    assert rel(g["u"], o["u"]) <= tol, rel(g["u"], o["u"])
+    frac = (g["mu"] != o["mu"]).mean() if len(o["mu"]) else 0.0
+    assert frac < 1e-3, frac
+
+
+# ------------------------------------------------------------------ tensile bar
+@pytest.fixture(scope="module")
+def bar():
+    w = workloads.tensile_bar()
+    return w, oracle_run(w, w.steps)
+
+
+def test_tensile_bar_fp64_matches_oracle(bar):
+    w, o = bar
+    assert o["off"][-1] == 370728
+    g = gpu_run(w, w.steps, F64, graph_steps=50)
+    check_f64(g, o)
+    assert g["info"]["step"] == w.steps
+
+
+def test_tensile_bar_fp32_matches_oracle(bar):
+    w, o = bar
+    g = gpu_run(w, w.steps, F32, graph_steps=50)
+    check_f32(g, o)
+
+
+def test_tensile_bar_breaks_bonds(bar):
+    w, o = bar
+    # the run must exercise the break path, else the parity above says little about it
+    assert (o["mu"] == 0).sum() > 0
+
+
+# ------------------------------------------------------------------ notched beam (hashed s_c)
+@pytest.fixture(scope="module")
+def beam():
+    w = workloads.notched_beam(48, 10, 12, length=0.08, rate=1e-7, steps=400)
+    return w, oracle_run(w, w.steps)
+
+
+def test_notched_beam_fp64_matches_oracle(beam):
+    w, o = beam
+    assert (o["mu"] == 0).sum() > 0
+    g = gpu_run(w, w.steps, F64)
+    check_f64(g, o)
+
+
+def test_notched_beam_fp32_matches_oracle(beam):
+    w, o = beam
+    g = gpu_run(w, w.steps, F32, graph_steps=25)
+    check_f32(g, o)
+
+
+# ------------------------------------------------------------------ irregular / runtime width
+def test_jittered_lattice_wide_family_fp64_fp32():
+    w = workloads.tensile_bar(14, 9, 8, rate=5e-7, steps=150)
+    w.coords = workloads.lattice(14, 9, 8, w.dx, jitter=0.25, seed=11)
+    w.horizon = 3.9 * w.dx  # max family 255: runtime-width kernel (Q = 8)
+    rng = np.random.default_rng(2)
+    w.volumes = w.volumes * rng.uniform(0.7, 1.3, w.n)
+    u0, v0 = workloads.random_state(w.n, 4, 1e-7, 1e-2)
+    o = oracle_run(w, w.steps, u0=u0, v0=v0)
+    g = gpu_run(w, w.steps, F64, u0=u0, v0=v0)
+    assert g["info"]["ell_width"] == 256
+    check_f64(g, o)
+    g = gpu_run(w, w.steps, F32, u0=u0, v0=v0)
+    check_f32(g, o)
+
+
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_q5_family_width(prec):
+    w = workloads.tensile_bar(12, 8, 8, rate=5e-7, steps=60)
+    w.coords = workloads.lattice(12, 8, 8, w.dx, jitter=0.2, seed=5)
+    w.horizon = 3.2 * w.dx
+    o = oracle_run(w, w.steps)
+    g = gpu_run(w, w.steps, prec, graph_steps=7)
+    assert g["info"]["ell_width"] in (160, 192)
+    (check_f64 if prec == F64 else check_f32)(g, o)
+
+
+# ------------------------------------------------------------------ edge cases
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_ragged_sizes_and_degenerate_bodies(prec):
+    for shape in ((1, 1, 1), (2, 1, 1), (11, 3, 1), (37, 11, 9)):
+        w = workloads.tensile_bar(*shape, rate=1e-6, slab=1, steps=30)
+        u0, v0 = workloads.random_state(w.n, 1, 1e-6, 1e-1)
+        o = oracle_run(w, w.steps, u0=u0, v0=v0)
+        g = gpu_run(w, w.steps, prec, u0=u0, v0=v0)
+        if prec == F64:
+            check_f64(g, o)
+        else:
+            check_f32(g, o, tol=2e-4 if w.n < 8 else 1e-4)
+
+
+def test_graph_and_direct_launch_agree_bitwise():
+    w = workloads.notched_beam(40, 8, 10, length=0.06, rate=4e-7, steps=100)
+    for prec in (F64, F32):
+        a = gpu_run(w, 100, prec, graph_steps=0)
+        b = gpu_run(w, 100, prec, graph_steps=16)   # 6 graph replays + 4 direct steps
+        c = gpu_run(w, 100, prec, graph_steps=16)
+        for k in ("u", "v", "mu", "phi"):
+            assert np.array_equal(a[k], b[k]) and np.array_equal(b[k], c[k]), k
+
+
+def test_step_in_chunks_equals_one_call():
+    w = workloads.tensile_bar(20, 6, 6, rate=2e-6, steps=90)
+    c = oracle.micromodulus(w.bulk_modulus, w.horizon)
+    for prec in (F64, F32):
+        a = pdgb.Model.from_workload(w, precision=prec, c=c, graph_steps=10)
+        b = pdgb.Model.from_workload(w, precision=prec, c=c, graph_steps=10)
+        a.step(90)
+        for k in (3, 17, 40, 30):
+            b.step(k)
+        ua, va = a.state()
+        ub, vb = b.state()
+        assert np.array_equal(ua, ub) and np.array_equal(va, vb)
+        assert np.array_equal(a.bonds(), b.bonds())
+        a.close()
+        b.close()
+
+
+def test_state_transfer_host_and_device_pointers():
+    import torch
+    w = workloads.tensile_bar(16, 5, 5, rate=1e-6, steps=20)
+    c = oracle.micromodulus(w.bulk_modulus, w.horizon)
+    u0, v0 = workloads.random_state(w.n, 3, 1e-6, 1e-1)
+    for prec in (F64, F32):
+        m = pdgb.Model.from_workload(w, precision=prec, c=c)
+        m.set_state(torch.tensor(u0, device="cuda"), torch.tensor(v0, device="cuda"), step=5)
+        uh, vh = m.state()
+        ud = torch.empty((w.n, 3), dtype=torch.float64, device="cuda")
+        vd = torch.empty_like(ud)
+        assert pdgb.pd_get_state(m.h, ud, vd) == 5
+        assert np.array_equal(ud.cpu().numpy(), uh) and np.array_equal(vd.cpu().numpy(), vh)
+        assert np.array_equal(uh, u0)
+        if prec == F64:
+            assert np.array_equal(vh, v0)
+        else:
+            assert np.array_equal(vh, v0.astype(np.float32).astype(np.float64))
+        phid = torch.empty(w.n, dtype=torch.float64, device="cuda")
+        pdgb.pd_damage(m.h, phid)
+        assert np.array_equal(phid.cpu().numpy(), m.damage())
+        m.close()
+
+
+def test_restart_from_intermediate_state_matches_continuous_run():
+    # Section 3.6: simulate can restart from a supplied state and first_step.
+    w = workloads.tensile_bar(24, 6, 6, rate=2e-6, steps=80)
+    c = oracle.micromodulus(w.bulk_modulus, w.horizon)
+    a = pdgb.Model.from_workload(w, precision=F64, c=c)
+    a.step(80)
+    ua, va = a.state()
+    b = pdgb.Model.from_workload(w, precision=F64, c=c)
+    b.step(30)
+    u1, v1 = b.state()
+    mu1 = b.bonds()
+    b.close()
+    r = pdgb.Model.from_workload(w, precision=F64, c=c)
+    r.set_state(u1, v1, step=30)
+    r.set_bonds(mu1)
+    r.step(50)
+    ur, vr = r.state()
+    assert np.array_equal(ua, ur) and np.array_equal(va, vr)
+    assert np.array_equal(a.bonds(), r.bonds())
+    a.close()
+    r.close()
+
+
+def test_fused_damage_equals_recomputed_damage(beam):
+    w, o = beam
+    c = oracle.micromodulus(w.bulk_modulus, w.horizon)
+    for prec in (F64, F32):
+        m = pdgb.Model.from_workload(w, precision=prec, c=c)
+        m.step(w.steps)
+        fused = m.damage()
+        m.set_bonds(m.bonds())   # invalidates the per-step array -> recompute from bits
+        again = m.damage()
+        assert np.array_equal(fused, again)
+        assert np.all(fused >= 0) and np.all(fused <= 1) and fused.max() > 0
+        m.close()
+
+
+# ------------------------------------------------------------------ parameters
+def test_per_bond_stiffness_and_load_parameters():
+    w = workloads.cracked_plate_force(30, 16, 4, load=2e11, steps=120)
+    off, idx = oracle.cut_family(w.coords, w.horizon, w.cuts_array())
+    c0 = oracle.micromodulus(w.bulk_modulus, w.horizon)
+    om, ph = workloads.grf_params(2105041505, 5 * w.dx)
+    rows = np.repeat(np.arange(w.n), np.diff(off))
+    mid = 0.5 * (w.coords[rows] + w.coords[idx])
+    cb = c0 * (1.0 + 0.1 * workloads.grf_eval(mid, om, ph))
+    o = oracle_run(w, w.steps, c=c0, c_bond=cb, off_idx=(off, idx))
+    assert np.abs(o["u"]).max() > 0
+    g = gpu_run(w, w.steps, F64, c=c0, c_bond=cb)
+    check_f64(g, o)
+    g = gpu_run(w, w.steps, F32, c=c0, c_bond=cb)
+    check_f32(g, o)
+
+
+def test_set_params_changes_material_without_rebuild():
+    w = workloads.tensile_bar(20, 6, 6, rate=2e-6, steps=60)
+    c = oracle.micromodulus(w.bulk_modulus, w.horizon)
+    w2 = workloads.tensile_bar(20, 6, 6, rate=3e-6, steps=60, sc=2e-3)
+    o = oracle_run(w2, 60, c=1.5 * c)
+    for prec in (F64, F32):
+        m = pdgb.Model.from_workload(w, precision=prec, c=c, graph_steps=8)
+        m.step(8)  # capture a graph with the old parameters
+        m.set_state(np.zeros((w.n, 3)), np.zeros((w.n, 3)), step=0)
+        m.set_bonds(np.ones(m.info()["n_bonds"], np.uint8))
+        m.set_params(1.5 * c, 2e-3, 0.0, 3e-6)
+        m.step(60)
+        u, v = m.state()
+        tol = 1e-10 if prec == F64 else 1e-4
+        assert rel(u, o["u"]) <= tol
+        m.close()
+
+
+def test_no_fail_nodes_keep_their_bonds():
+    w = workloads.tensile_bar(20, 6, 6, rate=4e-6, steps=100)
+    nf = np.zeros(w.n, np.uint8)
+    nf[w.bc_type[:, 0] == 1] = 1
+    w.no_fail = nf
+    o = oracle_run(w, w.steps)
+    off = o["off"]
+    rows = np.repeat(np.arange(w.n), np.diff(off))
+    touching = (nf[rows] == 1) | (nf[o["idx"]] == 1)
+    assert o["mu"][touching].all() and (o["mu"] == 0).any()
+    for prec in (F64, F32):
+        g = gpu_run(w, w.steps, prec)
+        assert g["mu"][touching].all()
+        (check_f64 if prec == F64 else check_f32)(g, o)
+
+
+def test_nonfinite_state_is_reported():
+    import torch
+    w = workloads.tensile_bar(10, 4, 4, steps=3)
+    c = oracle.micromodulus(w.bulk_modulus, w.horizon)
+    for prec in (F64, F32):
+        m = pdgb.Model.from_workload(w, precision=prec, c=c)
+        bad = np.zeros((w.n, 3))
+        bad[7, 1] = np.nan
+        with pytest.raises(pdgb.PdError) as e:
+            m.set_state(bad, None)        # host input is validated
+        assert e.value.name == "PD_ERR_ARG"
+        m.set_state(torch.tensor(bad, device="cuda"), None)  # device input is not
+        m.step(2)
+        with pytest.raises(pdgb.PdError) as e:
+            m.sync()
+        assert e.value.name == "PD_ERR_NONFINITE"
+        m.close()
+
+
+def test_deterministic_repeat():
+    w = workloads.notched_beam(40, 8, 10, length=0.06, rate=4e-7, steps=80)
+    for prec in (F64, F32):
+        a = gpu_run(w, 80, prec)
+        b = gpu_run(w, 80, prec)
+        assert np.array_equal(a["u"], b["u"]) and np.array_equal(a["mu"], b["mu"])
+
+
+# ------------------------------------------------------------------ full size, sampled
+@pytest.mark.parametrize("prec", [F32, F64])
+def test_full_size_notched_beam_sampled_one_step(prec):
+    """1,009,200-node beam in the benchmark's launch configuration: from a common
+    state with broken bonds, one GPU step is compared with the oracle's step of
+    2000 sampled nodes computed one by one."""
+    w = workloads.notched_beam()
+    c = oracle.micromodulus(w.bulk_modulus, w.horizon)
+    m = pdgb.Model.from_workload(w, precision=prec, c=c, graph_steps=20)
+    info = m.info()
+    assert info["n"] == 1009200 and info["ell_width"] == 128
+    rng = np.random.default_rng(7)
+    # a smooth stretch plus noise: s around 1e-4 so that part of the bonds break
+    u0 = 1.0e-4 * (w.coords - w.coords.mean(axis=0)) * np.array([1.0, 0.3, 0.5])
+    u0 += rng.normal(0.0, 2e-8, size=u0.shape)
+    v0 = rng.normal(0.0, 1e-3, size=u0.shape)
+    m.set_state(u0, v0, step=40)
+    m.step(3)
+    m.sync()
+    u_s, v_s = m.state()
+    mu_all = m.bonds()
+    m.step(1)
+    u_g, v_g = m.state()
+    mu_g = m.bonds()
+    off_g, idx_g = m.family()
+    m.close()
+
+    rows = np.sort(rng.choice(w.n, 2000, replace=False))
+    # include notch-face and load/support nodes
+    rows = np.unique(np.concatenate([rows, np.nonzero(w.bc_type.any(axis=1))[0][:50],
+                                     np.arange(149 * 58 * 58, 149 * 58 * 58 + 40)]))
+    off_r, idx_r = oracle.cut_family(w.coords, w.horizon, w.cuts_array(), rows=rows)
+    sel = np.concatenate([np.arange(off_g[i], off_g[i + 1]) for i in rows])
+    assert np.array_equal(idx_g[sel], idx_r)
+    assert np.array_equal(np.diff(off_r), off_g[rows + 1] - off_g[rows])
+    mu = mu_all[sel].copy()
+    assert (mu == 0).any()
+    om = oracle.Model.from_workload(w, off_r, idx_r, c=c, rows=rows)
+    margin = np.full(len(mu), np.inf)
+    uo, vo = om.step(43, u_s, v_s, mu, margin)
+    du_o = uo - u_s[rows]
+    du_g = u_g[rows] - u_s[rows]
+    diff = mu != mu_g[sel]
+    if prec == F64:
+        assert rel(u_g[rows], uo) <= 1e-12
+        assert rel(du_g, du_o) <= 1e-9
+        assert np.all(margin[diff] < BAND)
+    else:
+        assert rel(u_g[rows], uo) <= 1e-6
+        assert rel(du_g, du_o) <= 1e-3
+        assert diff.mean() < 1e-3
