@@ -1,0 +1,372 @@
+"""Benchmark of the fused peridynamic step (bond updates per second).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload beam|plate|bar] [--precision 32|64]
+
+Default workload: the notched three-point-bend beam, 300 x 58 x 58 = 1,009,200
+nodes, delta = pi dx, 117.7M directed bonds, per-bond critical stretch, FP32
+bulk arithmetic.  A step is one pass of the whole method over the model (one
+fused kernel launch).  Inputs are resident in HBM when the timed region starts;
+the 517 MB padded family index streamed every step is larger than L2, so no
+flush is needed between steps.  Rank 0 prints one JSON line.
+
+Under torchrun (N > 1) every rank advances its own replica of the workload
+(the method has no exchange step on one model: replicas only, weak scaling);
+the time is the maximum over ranks and the value counts all ranks' bonds.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+project) on the host cores, on a row sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+# Algorithmic bytes of one step (what the method must move, padding excluded):
+# per directed bond a 4-byte neighbour id and one state bit; per node (FP32 bulk)
+# position+weight 16 B read, FP64 displacement 24 B read + 24 B written, FP32
+# velocity 12 B read + 12 B written, damage 4 B written, BC class 1 B.
+BYTES_PER_BOND = 4.125
+BYTES_PER_NODE = {32: 93.0, 64: 136.0}
+STEP_SRC = {32: "pd_step_f32.cu", 64: "pd_step_f64.cu"}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="beam", choices=["beam", "plate", "bar"])
+    p.add_argument("--precision", type=int, default=32, choices=[32, 64])
+    p.add_argument("--graph-steps", type=int, default=50)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def make_workload(name):
+    if name == "beam":
+        return workloads.notched_beam()
+    if name == "plate":
+        return workloads.plate()
+    return workloads.tensile_bar()
+
+
+def describe(w, n_bonds, precision):
+    return {
+        "workload": f"{w.name}: {w.n:,} nodes, {n_bonds:,} directed bonds, "
+                    f"delta = {w.horizon / w.dx:.4g} dx, "
+                    + ("per-bond s_c ~ U[9e-5, 1.1e-4)" if w.sc_hash else f"s_c = {w.sc:g}"),
+        "precision": "fp32 bonds, fp64 displacement" if precision == 32 else "fp64",
+        "n_nodes": w.n,
+        "n_bonds": int(n_bonds),
+        "l2_policy": "inputs larger than L2 (padded family index > 129 MB streamed per step)",
+    }
+
+
+# --------------------------------------------------------------------------- peaks, clocks
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0=None, t1=None):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        picked = [l for t, l in self.lines if (t0 is None or t >= t0) and (t1 is None or t <= t1)]
+        if not picked:  # timed region shorter than one sample period: nearest samples
+            picked = [l for _, l in self.lines[-3:]]
+        for line in picked:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- multi-rank
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    group = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+        group = dist
+    return world, rank, local, group
+
+
+def barrier(group, device_sync):
+    if device_sync is not None:
+        device_sync()
+    if group is not None:
+        group.barrier()
+
+
+def aggregate_max(value: float, group) -> float:
+    """Maximum of a per-rank scalar over all ranks (identity without a group)."""
+    if group is None:
+        return value
+    import torch
+    dev = "cuda" if group.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    group.all_reduce(t, op=group.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job(units_per_rank: float, ms_max: float, world: int) -> float:
+    """Units processed by all ranks divided by the slowest rank's time."""
+    return units_per_rank * world / (ms_max * 1e-3)
+
+
+# --------------------------------------------------------------------------- traffic
+def profiled_traffic(precision, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel source (matched by hash); else None."""
+    src = os.path.join(ROOT, "paper_2105_04150_gb300", "csrc", STEP_SRC[precision])
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", f"step_f{precision}_{workload}_traffic.txt")
+    try:
+        kv = dict(l.split(None, 1) for l in open(path) if l.strip() and not l.startswith("#"))
+        if kv.get("kernel_source_sha256_16", "").strip() == sha:
+            return float(kv["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+# --------------------------------------------------------------------------- oracle timing
+def oracle_sample(w, c, budget_s, steps=None, warmup=0):
+    """Time the FP64 oracle step on a row sample of the workload (host cores)."""
+    import oracle
+    off_all = None
+    rng = np.random.default_rng(0)
+    # estimate the full-step cost from a 2% row sample
+    probe_rows = np.sort(rng.choice(w.n, max(1, w.n // 50), replace=False))
+    off, idx = oracle.cut_family(w.coords, w.horizon, w.cuts_array(), rows=probe_rows)
+    m = oracle.Model.from_workload(w, off, idx, c=c, rows=probe_rows)
+    u, v = workloads.random_state(w.n, 1, 1e-9, 1e-4)
+    t = time.perf_counter()
+    m.step(0, u, v, m.fresh_bonds())
+    t_probe = time.perf_counter() - t
+    per_bond = t_probe / max(1, m.nbonds)
+    n_steps = steps if steps is not None else 5
+    bonds_budget = budget_s / max(per_bond, 1e-12) / max(1, n_steps)
+    frac = min(1.0, bonds_budget / max(1, w.n * (m.nbonds / len(probe_rows))))
+    rows = np.sort(rng.choice(w.n, max(1, int(frac * w.n)), replace=False)) if frac < 1 else None
+    off, idx = oracle.cut_family(w.coords, w.horizon, w.cuts_array(), rows=rows)
+    m = oracle.Model.from_workload(w, off, idx, c=c, rows=rows)
+    mu = m.fresh_bonds()
+    for _ in range(warmup):
+        m.step(0, u, v, mu)
+    t = time.perf_counter()
+    for k in range(n_steps):
+        m.step(k, u, v, mu)
+    el = time.perf_counter() - t
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {
+        "value": m.nbonds * n_steps / el, "unit": "bond updates/s", "cores": cores,
+        "kind": "oracle", "seconds": el, "steps": n_steps,
+        "sample": f"{n_steps} oracle FP64 steps over {m.nrows:,} of {w.n:,} rows "
+                  f"({m.nbonds:,} bonds each) of the same workload, OpenMP on {cores} host threads",
+    }
+
+
+def run_reference(args):
+    world, rank, local, group = dist_setup(args)
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    w = make_workload(args.workload)
+    c = oracle.micromodulus(w.bulk_modulus, w.horizon)
+    # each timed step is a row sample sized so the whole run takes about a minute
+    res = oracle_sample(w, c, budget_s=60.0, steps=args.steps, warmup=args.warmup)
+    line = {
+        "impl": "reference", "metric": "bond updates/s", "value": res["value"],
+        "unit": "bond updates/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["seconds"] * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w.name, "sample": res["sample"]},
+        "cpu_baseline": {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": {"value": res["value"], "unit": "bond updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    world, rank, local, group = dist_setup(args)
+    import paper_2105_04150_gb300 as pdgb
+    pdgb.lib()
+    torch.cuda.set_device(local)
+    dev_sync = torch.cuda.synchronize
+    w = make_workload(args.workload)
+    c = pdgb.pd_micromodulus(w.bulk_modulus, w.horizon)
+    stream = torch.cuda.Stream(device=local)
+    G = max(0, min(args.graph_steps, args.steps))
+    m = pdgb.Model.from_workload(w, precision=args.precision, c=c, graph_steps=G,
+                                 stream=stream.cuda_stream, device=local)
+    info = m.info()
+    n_bonds = info["n_bonds"]
+    # warm-up: W steps (also captures the graph)
+    m.step(args.warmup)
+    m.sync()
+    barrier(group, dev_sync)
+    with torch.cuda.stream(stream):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            time.sleep(0.5)  # let the sampler start
+            barrier(group, dev_sync)
+            t_on = time.time()
+            e0.record(stream)
+            m.step(args.steps)
+            e1.record(stream)
+            e1.synchronize()
+            t_off = time.time()
+            barrier(group, dev_sync)
+            time.sleep(0.25)
+    m.sync()
+    ms = e0.elapsed_time(e1)
+    ms_max = aggregate_max(ms, group)
+    n_graph = args.steps // G if G > 0 else 0
+    rem = args.steps - n_graph * G
+    launches = args.steps + n_graph + (1 if rem > 0 else 0)
+
+    # end to end through the public API with pinned host buffers: every step uploads
+    # the state (u, v), advances one step and reads the new state back.
+    e2e = None
+    if not args.no_e2e:
+        uh = torch.empty((w.n, 3), dtype=torch.float64).pin_memory()
+        vh = torch.empty((w.n, 3), dtype=torch.float64).pin_memory()
+        pdgb.pd_get_state(m.h, uh, vh)
+        k_e2e = max(3, min(args.steps, 50))
+        for _ in range(2):
+            pdgb.pd_set_state(m.h, uh, vh)
+            m.step(1)
+            pdgb.pd_get_state(m.h, uh, vh)
+        barrier(group, dev_sync)
+        t = time.perf_counter()
+        for _ in range(k_e2e):
+            pdgb.pd_set_state(m.h, uh, vh)
+            m.step(1)
+            pdgb.pd_get_state(m.h, uh, vh)
+        dev_sync()
+        el = aggregate_max(time.perf_counter() - t, group)
+        e2e = {"value": whole_job(n_bonds * k_e2e, el * 1e3, world), "unit": "bond updates/s",
+               "h2d_bytes_per_step": 2 * uh.numel() * 8, "d2h_bytes_per_step": 2 * uh.numel() * 8,
+               "steps": k_e2e}
+    m.close()
+
+    if rank != 0:
+        barrier(group, None)
+        return
+    ms_step = ms_max / args.steps
+    value = whole_job(n_bonds * args.steps, ms_max, world)
+    alg_bytes = n_bonds * BYTES_PER_BOND + w.n * BYTES_PER_NODE[args.precision]
+    peak, peak_kind = hbm_peak()
+    achieved = alg_bytes / (ms_step * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": profiled_traffic(args.precision, args.workload),
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s", "algorithmic_bytes_per_launch": alg_bytes,
+                "kernel": f"k_step_f{args.precision}"}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cb = oracle_sample(w, oracle.micromodulus(w.bulk_modulus, w.horizon), budget_s=15.0)
+        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    line = {
+        "metric": "bond updates/s", "value": value, "unit": "bond updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "time_steps_per_s": 1e3 / ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision == 32 else "f64",
+        "data": "synthetic", "config": describe(w, n_bonds, args.precision),
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk.summary(t_on, t_off),
+    }
+    print(json.dumps(line), flush=True)
+    if group is not None:
+        group.barrier()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

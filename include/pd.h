@@ -65,6 +65,9 @@ typedef struct {
     void* stream;         /* cudaStream_t to queue work on; NULL = library-owned stream */
     int32_t block_threads;/* threads per block of the step kernel; 0 = default (256) */
     int32_t blocks_per_sm;/* resident blocks per SM for the step grid; 0 = default */
+    int32_t reorder;      /* 0 = keep the caller's node order (best for lattices given
+                             row-major); 1 = sort nodes by horizon-sized cells */
+    int32_t reserved0;
 } pd_config;
 
 typedef struct {

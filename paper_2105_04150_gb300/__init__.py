@@ -46,7 +46,8 @@ class _Config(ctypes.Structure):
                 ("dt", ctypes.c_double), ("damping", ctypes.c_double),
                 ("density", ctypes.c_double), ("check_dt", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
-                ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+                ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("reorder", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
 
 class _Material(ctypes.Structure):
@@ -155,7 +156,7 @@ def pd_create(coords, volumes, horizon: float, *, c: float, sc: float = 0.0,
               bc_force=None, no_fail=None, disp_rate: float = 0.0, load: float = 0.0,
               dt: float, damping: float, density: float, precision: int = PD_PREC_F64,
               graph_steps: int = 0, check_dt: bool = False, device: int = 0, stream=None,
-              block_threads: int = 0, blocks_per_sm: int = 0) -> int:
+              block_threads: int = 0, blocks_per_sm: int = 0, reorder: int = 0) -> int:
     """Create a model; returns an opaque handle (int).  See pd.h for the semantics."""
     x, kx = _ptr(coords, np.float64)
     n = (kx.numel() if hasattr(kx, "numel") else kx.size) // 3
@@ -183,7 +184,7 @@ def pd_create(coords, volumes, horizon: float, *, c: float, sc: float = 0.0,
     cfg = _Config(precision=int(precision), graph_steps=int(graph_steps), dt=float(dt),
                   damping=float(damping), density=float(density), check_dt=int(bool(check_dt)),
                   device=int(device), stream=stream, block_threads=int(block_threads),
-                  blocks_per_sm=int(blocks_per_sm))
+                  blocks_per_sm=int(blocks_per_sm), reorder=int(reorder))
     h = ctypes.c_void_p()
     _check(lib().pd_create(n, x, vol, float(horizon), fo, fi, cp, ncut, ctypes.byref(mat),
                            ctypes.byref(bc), ctypes.byref(cfg), ctypes.byref(h)))

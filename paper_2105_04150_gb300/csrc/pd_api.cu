@@ -39,9 +39,9 @@ pd_status cuda_fail(cudaError_t e, const char* what)
     return fail(PD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define PD_CUDA(call, what)                      \
-    do {                                         \
-        cudaError_t e_ = (call);                 \
+#define PD_CUDA(call, what)                                \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
         if (e_ != cudaSuccess) return cuda_fail(e_, what); \
     } while (0)
 
@@ -56,6 +56,13 @@ bool is_device_ptr(const void* p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+bool finite_all(const double* p, int64_t m)
+{
+    for (int64_t i = 0; i < m; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
 }  // namespace
 
 struct pd_handle {
@@ -64,7 +71,7 @@ struct pd_handle {
     bool own_stream = false;
     int precision = 64;
     int Q = 1;
-    int64_t n = 0, n_bonds = 0;
+    int64_t n = 0, n_pad = 0, n_slices = 0, n_bonds = 0;
     double delta = 0, dt = 0, eta = 0, rho = 0;
     double c = 0, sc = 0, sc_lo = 0, sc_hi = 0;
     int sc_mode = 0;
@@ -78,22 +85,25 @@ struct pd_handle {
     int grid = 0, block = 256;
     bool damage_fresh = false;
 
-    std::vector<int64_t> off;   // canonical family after cuts
+    std::vector<int64_t> off;  // canonical family after cuts
     std::vector<int32_t> idx;
     std::vector<int32_t> perm, inv, cnt;
 
     std::vector<void*> allocs;
     int64_t device_bytes = 0;
-    void* rec[2] = {nullptr, nullptr};
-    double* u64[2] = {nullptr, nullptr};
+    // FP32 path: 3 float4 per node; FP64 path: 8 doubles per node
+    float4* rec32[2] = {nullptr, nullptr};
+    double* rec[2] = {nullptr, nullptr};
+    // both
     void* v = nullptr;
     int32_t* nbr = nullptr;
     uint32_t* bits = nullptr;
+    uint32_t* bits0 = nullptr;  // bond flags after the initial cuts
+    int32_t* sw = nullptr;
     void* cbond = nullptr;
     uint8_t* bcc = nullptr;
     BcClass* bct = nullptr;
     int32_t* gid = nullptr;
-    int32_t* fam_cnt = nullptr;
     double* x64 = nullptr;
     double* vol = nullptr;
     void* wsum_inv = nullptr;
@@ -106,19 +116,20 @@ struct pd_handle {
     cudaError_t alloc(T** p, size_t count)
     {
         void* q = nullptr;
-        const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+        const size_t bytes = std::max<size_t>(count * sizeof(T), 256);
         cudaError_t e = cudaMalloc(&q, bytes);
         if (e != cudaSuccess) return e;
         allocs.push_back(q);
         device_bytes += (int64_t)bytes;
         *p = (T*)q;
-        return cudaSuccess;
+        return cudaMemsetAsync(q, 0, bytes, stream);
     }
 
     void release()
     {
         if (graph) cudaGraphExecDestroy(graph);
         graph = nullptr;
+        if (stream) cudaStreamSynchronize(stream);
         for (void* p : allocs) cudaFree(p);
         allocs.clear();
         if (own_stream && stream) cudaStreamDestroy(stream);
@@ -130,6 +141,11 @@ struct pd_handle {
         if (graph) cudaGraphExecDestroy(graph);
         graph = nullptr;
     }
+
+    const void* wrec() const
+    {
+        return precision == 32 ? (const void*)rec32[0] : (const void*)rec[0];
+    }
 };
 
 namespace {
@@ -137,13 +153,12 @@ namespace {
 StepArgsF32 args_f32(pd_handle* h, int k)
 {
     StepArgsF32 a{};
-    a.rec[0] = (const float4*)h->rec[0];
-    a.rec[1] = (const float4*)h->rec[1];
-    a.u64[0] = h->u64[0];
-    a.u64[1] = h->u64[1];
+    a.rec[0] = h->rec32[0];
+    a.rec[1] = h->rec32[1];
     a.v = (float*)h->v;
     a.nbr = h->nbr;
     a.bits = h->bits;
+    a.sw = h->sw;
     a.cbond = h->per_bond_c ? (const float*)h->cbond : nullptr;
     a.bcc = h->bcc;
     a.bct = h->bct;
@@ -155,11 +170,12 @@ StepArgsF32 args_f32(pd_handle* h, int k)
     a.step_ctr = h->step_ctr;
     a.n = h->n;
     a.k = k;
-    a.q_rt = h->Q;
+    a.Q = h->Q;
     a.has_nofail = h->has_nofail ? 1 : 0;
+    a.guard = 5e-4f;
     a.sc_f = (float)h->sc;
     a.sc_lo_f = (float)h->sc_lo;
-    a.guard = 5e-4f;
+    a.fast_lo = (float)((1.0 - 2.0 * a.guard) * h->sc_lo);
     a.sc = h->sc;
     a.sc_lo = h->sc_lo;
     a.sc_hi = h->sc_hi;
@@ -169,6 +185,7 @@ StepArgsF32 args_f32(pd_handle* h, int k)
     a.rho = h->rho;
     a.disp_rate = h->disp_rate;
     a.load = h->load;
+    a.delta = h->delta;
     a.inv_delta = 1.0 / h->delta;
     return a;
 }
@@ -176,11 +193,12 @@ StepArgsF32 args_f32(pd_handle* h, int k)
 StepArgsF64 args_f64(pd_handle* h, int k)
 {
     StepArgsF64 a{};
-    a.rec[0] = (const double*)h->rec[0];
-    a.rec[1] = (const double*)h->rec[1];
+    a.rec[0] = h->rec[0];
+    a.rec[1] = h->rec[1];
     a.v = (double*)h->v;
     a.nbr = h->nbr;
     a.bits = h->bits;
+    a.sw = h->sw;
     a.cbond = h->per_bond_c ? (const double*)h->cbond : nullptr;
     a.bcc = h->bcc;
     a.bct = h->bct;
@@ -191,7 +209,7 @@ StepArgsF64 args_f64(pd_handle* h, int k)
     a.step_ctr = h->step_ctr;
     a.n = h->n;
     a.k = k;
-    a.q_rt = h->Q;
+    a.Q = h->Q;
     a.has_nofail = h->has_nofail ? 1 : 0;
     a.sc = h->sc;
     a.sc_lo = h->sc_lo;
@@ -208,23 +226,24 @@ StepArgsF64 args_f64(pd_handle* h, int k)
 cudaError_t launch_one(pd_handle* h, int k)
 {
     if (h->precision == 32)
-        return launch_step_f32(args_f32(h, k), h->Q, h->sc_mode, h->grid, h->block, h->stream);
-    return launch_step_f64(args_f64(h, k), h->Q, h->sc_mode, h->grid, h->block, h->stream);
+        return launch_step_f32(args_f32(h, k), h->sc_mode, h->grid, h->block, h->stream);
+    return launch_step_f64(args_f64(h, k), h->sc_mode, h->grid, h->block, h->stream);
 }
 
 pd_status choose_grid(pd_handle* h, int blocks_per_sm)
 {
     int sms = 0;
     PD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "sm count");
-    const void* fn = h->precision == 32 ? step_f32_kernel(h->Q, h->sc_mode)
-                                        : step_f64_kernel(h->Q, h->sc_mode);
+    const void* fn = h->precision == 32 ? step_f32_kernel(h->sc_mode) : step_f64_kernel(h->sc_mode);
+    // no shared memory is used: give the unified L1/shared array to L1
+    PD_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 0),
+            "carveout");
     int occ = 0;
     PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, h->block, 0), "occupancy");
     if (occ < 1) occ = 1;
     if (blocks_per_sm > 0) occ = std::min(occ, blocks_per_sm);
-    const int64_t groups = (h->n + 31) / 32;
     const int64_t warps_per_block = h->block / 32;
-    const int64_t need = (groups + warps_per_block - 1) / warps_per_block;
+    const int64_t need = (h->n_slices + warps_per_block - 1) / warps_per_block;
     h->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * occ, need));
     return PD_OK;
 }
@@ -232,8 +251,10 @@ pd_status choose_grid(pd_handle* h, int blocks_per_sm)
 pd_status upload_weights(pd_handle* h)
 {
     const double wscale = h->per_bond_c ? 1.0 : h->c;
-    PD_CUDA(launch_set_weights(h->precision, h->rec[0], h->rec[1], h->vol, h->nbr, h->fam_cnt,
-                               h->n, h->Q, wscale, h->wsum_inv, h->stream),
+    void* w0 = h->precision == 32 ? (void*)h->rec32[0] : (void*)h->rec[0];
+    void* w1 = h->precision == 32 ? (void*)h->rec32[1] : (void*)h->rec[1];
+    PD_CUDA(launch_set_weights(h->precision, w0, w1, h->vol, h->nbr, h->bits0, h->sw, h->n, h->Q,
+                               wscale, h->wsum_inv, h->stream),
             "set weights");
     return PD_OK;
 }
@@ -249,11 +270,14 @@ pd_status check_dev_err(pd_handle* h)
     return PD_OK;
 }
 
-bool finite_all(const double* p, int64_t m)
+// canonical position of every SELL slot, computed on demand from the device family
+pd_status canonical_slots(pd_handle* h, std::vector<int64_t>& pos)
 {
-    for (int64_t i = 0; i < m; ++i)
-        if (!std::isfinite(p[i])) return false;
-    return true;
+    std::vector<int32_t> nbr((size_t)(h->n_slices * 32 * h->Q * 32));
+    PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
+    PD_CUDA(cudaMemcpy(nbr.data(), h->nbr, nbr.size() * 4, cudaMemcpyDeviceToHost), "copy family");
+    slot_to_canonical(h->n, h->off, h->idx, h->perm, nbr, h->cnt, h->Q, pos);
+    return PD_OK;
 }
 
 }  // namespace
@@ -309,6 +333,7 @@ pd_status pd_create(int64_t n, const double* coords, const double* volumes, doub
     if (cfg->block_threads != 0 &&
         (cfg->block_threads < 32 || cfg->block_threads > 256 || cfg->block_threads % 32))
         return fail(PD_ERR_ARG, "block_threads must be a multiple of 32 in [32, 256]");
+    if (cfg->reorder != 0 && cfg->reorder != 1) return fail(PD_ERR_ARG, "reorder must be 0 or 1");
     if (!finite_all(coords, 3 * n)) return fail(PD_ERR_ARG, "non-finite coordinates");
     for (int64_t i = 0; i < n; ++i)
         if (!(volumes[i] > 0.0) || !std::isfinite(volumes[i]))
@@ -341,6 +366,8 @@ pd_status pd_create(int64_t n, const double* coords, const double* volumes, doub
                          (long long)maxfam, PD_MAX_FAMILY));
     h->Q = (int)std::max<int64_t>(1, (maxfam + 31) / 32);
     h->n = n;
+    h->n_slices = (n + 31) / 32;
+    h->n_pad = 32 * h->n_slices;
     h->n_bonds = h->off[n];
     h->precision = cfg->precision;
     h->delta = horizon;
@@ -348,8 +375,8 @@ pd_status pd_create(int64_t n, const double* coords, const double* volumes, doub
     h->eta = cfg->damping;
     h->rho = cfg->density;
     h->c = mat->c;
-    h->sc = mat->sc_mode == 0 ? mat->sc : 0.5 * (mat->sc_lo + mat->sc_hi);
     h->sc_mode = mat->sc_mode;
+    h->sc = mat->sc_mode == 0 ? mat->sc : 0.5 * (mat->sc_lo + mat->sc_hi);
     h->sc_seed = mat->sc_seed;
     h->sc_lo = mat->sc_mode == 1 ? mat->sc_lo : mat->sc;
     h->sc_hi = mat->sc_mode == 1 ? mat->sc_hi : mat->sc;
@@ -370,10 +397,10 @@ pd_status pd_create(int64_t n, const double* coords, const double* volumes, doub
     msg = bc_classes(n, bc->type, bc->disp, bc->force, bc->no_fail, table, cls, h->has_nofail);
     if (!msg.empty()) return bail(fail(PD_ERR_ARG, "%s", msg.c_str()));
 
-    spatial_order(n, coords, horizon, h->perm, h->inv);
-    std::vector<int32_t> nbr;
+    spatial_order(n, coords, horizon, cfg->reorder, h->perm, h->inv);
+    std::vector<int32_t> nbr, sw;
     std::vector<uint32_t> bits;
-    build_layout(n, h->off, h->idx, h->perm, h->inv, h->Q, nbr, bits, h->cnt);
+    build_layout(n, h->off, h->idx, h->perm, h->inv, h->Q, nbr, bits, sw, h->cnt);
 
     // ---- device
     cudaError_t e = cudaSetDevice(h->device);
@@ -385,41 +412,41 @@ pd_status pd_create(int64_t n, const double* coords, const double* volumes, doub
         if (e != cudaSuccess) return bail(cuda_fail(e, "stream create"));
         h->own_stream = true;
     }
-    const int64_t W = 32LL * h->Q;
+    const int64_t np = h->n_pad;
     const bool f32 = h->precision == 32;
-    const size_t recb = f32 ? 32 : 64;
-#define ALLOC(ptr, type, count)                                     \
-    do {                                                            \
-        e = h->alloc((type**)&(ptr), (size_t)(count));              \
+#define ALLOC(ptr, type, count)                                              \
+    do {                                                                     \
+        e = h->alloc((type**)&(ptr), (size_t)(count));                       \
         if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc " #ptr)); \
     } while (0)
-    ALLOC(h->rec[0], uint8_t, recb * n);
-    ALLOC(h->rec[1], uint8_t, recb * n);
     if (f32) {
-        ALLOC(h->u64[0], double, 3 * n);
-        ALLOC(h->u64[1], double, 3 * n);
-        ALLOC(h->v, float, 3 * n);
-        ALLOC(h->wsum_inv, float, n);
-        ALLOC(h->damage, float, n);
+        ALLOC(h->rec32[0], float4, 3 * np);
+        ALLOC(h->rec32[1], float4, 3 * np);
+        ALLOC(h->v, float, 3 * np);
+        ALLOC(h->wsum_inv, float, np);
+        ALLOC(h->damage, float, np);
     } else {
-        ALLOC(h->v, double, 3 * n);
-        ALLOC(h->wsum_inv, double, n);
-        ALLOC(h->damage, double, n);
+        ALLOC(h->rec[0], double, 8 * np);
+        ALLOC(h->rec[1], double, 8 * np);
+        ALLOC(h->v, double, 3 * np);
+        ALLOC(h->wsum_inv, double, np);
+        ALLOC(h->damage, double, np);
     }
-    ALLOC(h->nbr, int32_t, n * W);
-    ALLOC(h->bits, uint32_t, n * h->Q);
-    ALLOC(h->bcc, uint8_t, n);
+    ALLOC(h->nbr, int32_t, nbr.size());
+    ALLOC(h->bits, uint32_t, bits.size());
+    ALLOC(h->bits0, uint32_t, bits.size());
+    ALLOC(h->sw, int32_t, sw.size());
+    ALLOC(h->bcc, uint8_t, np);
     ALLOC(h->bct, BcClass, table.size());
-    ALLOC(h->gid, int32_t, n);
-    ALLOC(h->fam_cnt, int32_t, n);
-    ALLOC(h->x64, double, 3 * n);
-    ALLOC(h->vol, double, n);
+    ALLOC(h->gid, int32_t, np);
+    ALLOC(h->x64, double, 3 * np);
+    ALLOC(h->vol, double, np);
     ALLOC(h->err, int, 1);
     ALLOC(h->step_ctr, int64_t, 1);
     ALLOC(h->staging, double, 3 * n);
 #undef ALLOC
 
-    // node records in spatial order
+    // node data in the library's order (padding nodes: zero volume, class 0)
     double lo[3], hi[3];
     for (int a = 0; a < 3; ++a) lo[a] = hi[a] = coords[a];
     for (int64_t i = 0; i < n; ++i)
@@ -429,13 +456,15 @@ pd_status pd_create(int64_t n, const double* coords, const double* volumes, doub
         }
     double ctr[3];
     for (int a = 0; a < 3; ++a) ctr[a] = 0.5 * (lo[a] + hi[a]);
-    std::vector<double> xs(3 * n), vs(n);
-    std::vector<uint8_t> clsp(n);
+    std::vector<double> xs(3 * np, 0.0), vs(np, 0.0);
+    std::vector<uint8_t> clsp(np, 0);
+    std::vector<int32_t> gids(np, 0);
     for (int64_t p = 0; p < n; ++p) {
         const int64_t i = h->perm[p];
         for (int a = 0; a < 3; ++a) xs[3 * p + a] = coords[3 * i + a];
         vs[p] = volumes[i];
         clsp[p] = cls[i];
+        gids[p] = (int32_t)i;
     }
     auto up = [&](void* dst, const void* src, size_t bytes, const char* what) -> pd_status {
         cudaError_t ee = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->stream);
@@ -443,45 +472,35 @@ pd_status pd_create(int64_t n, const double* coords, const double* volumes, doub
         return PD_OK;
     };
     pd_status st;
+    std::vector<float4> r32;
+    std::vector<double> r64;
     if (f32) {
-        std::vector<float4> r(2 * n);
-        for (int64_t p = 0; p < n; ++p) {
-            r[2 * p] = make_float4((float)((xs[3 * p] - ctr[0]) / horizon),
-                                   (float)((xs[3 * p + 1] - ctr[1]) / horizon),
-                                   (float)((xs[3 * p + 2] - ctr[2]) / horizon), 0.0f);
-            r[2 * p + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        if ((st = up(h->rec[0], r.data(), 32 * n, "upload records")) ||
-            (st = up(h->rec[1], r.data(), 32 * n, "upload records")))
-            return bail(st);
-        cudaStreamSynchronize(h->stream);
-        e = cudaMemsetAsync(h->u64[0], 0, 24 * n, h->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->u64[1], 0, 24 * n, h->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->v, 0, 12 * n, h->stream);
-        if (e != cudaSuccess) return bail(cuda_fail(e, "memset"));
-    } else {
-        std::vector<double> r(8 * n, 0.0);
+        r32.assign(3 * np, make_float4(0.f, 0.f, 0.f, 0.f));
         for (int64_t p = 0; p < n; ++p)
-            for (int a = 0; a < 3; ++a) r[8 * p + a] = xs[3 * p + a];
-        if ((st = up(h->rec[0], r.data(), 64 * n, "upload records")) ||
-            (st = up(h->rec[1], r.data(), 64 * n, "upload records")))
+            r32[3 * p] = make_float4((float)((xs[3 * p] - ctr[0]) / horizon),
+                                     (float)((xs[3 * p + 1] - ctr[1]) / horizon),
+                                     (float)((xs[3 * p + 2] - ctr[2]) / horizon), 0.0f);
+        if ((st = up(h->rec32[0], r32.data(), 48 * np, "upload records")) ||
+            (st = up(h->rec32[1], r32.data(), 48 * np, "upload records")))
             return bail(st);
-        cudaStreamSynchronize(h->stream);
-        e = cudaMemsetAsync(h->v, 0, 24 * n, h->stream);
-        if (e != cudaSuccess) return bail(cuda_fail(e, "memset"));
+    } else {
+        r64.assign(8 * np, 0.0);
+        for (int64_t p = 0; p < n; ++p)
+            for (int a = 0; a < 3; ++a) r64[8 * p + a] = xs[3 * p + a];
+        if ((st = up(h->rec[0], r64.data(), 64 * np, "upload records")) ||
+            (st = up(h->rec[1], r64.data(), 64 * np, "upload records")))
+            return bail(st);
     }
     if ((st = up(h->nbr, nbr.data(), nbr.size() * 4, "upload family")) ||
         (st = up(h->bits, bits.data(), bits.size() * 4, "upload bond flags")) ||
-        (st = up(h->bcc, clsp.data(), n, "upload bc classes")) ||
+        (st = up(h->bits0, bits.data(), bits.size() * 4, "upload bond flags")) ||
+        (st = up(h->sw, sw.data(), sw.size() * 4, "upload slice widths")) ||
+        (st = up(h->bcc, clsp.data(), np, "upload bc classes")) ||
         (st = up(h->bct, table.data(), table.size() * sizeof(BcClass), "upload bc table")) ||
-        (st = up(h->gid, h->perm.data(), 4 * n, "upload ids")) ||
-        (st = up(h->fam_cnt, h->cnt.data(), 4 * n, "upload counts")) ||
-        (st = up(h->x64, xs.data(), 24 * n, "upload coordinates")) ||
-        (st = up(h->vol, vs.data(), 8 * n, "upload volumes")))
+        (st = up(h->gid, gids.data(), 4 * np, "upload ids")) ||
+        (st = up(h->x64, xs.data(), 24 * np, "upload coordinates")) ||
+        (st = up(h->vol, vs.data(), 8 * np, "upload volumes")))
         return bail(st);
-    e = cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->step_ctr, 0, sizeof(int64_t), h->stream);
-    if (e != cudaSuccess) return bail(cuda_fail(e, "memset"));
     if ((st = upload_weights(h)) != PD_OK) return bail(st);
     if ((st = choose_grid(h, cfg->blocks_per_sm)) != PD_OK) return bail(st);
     e = cudaStreamSynchronize(h->stream);
@@ -493,7 +512,6 @@ pd_status pd_create(int64_t n, const double* coords, const double* volumes, doub
 void pd_destroy(pd_handle* h)
 {
     if (!h) return;
-    if (h->stream) cudaStreamSynchronize(h->stream);
     h->release();
     delete h;
 }
@@ -582,12 +600,12 @@ pd_status pd_get_state(pd_handle* h, double* u, double* v, int64_t* step)
         double* uo = w == 0 ? dst : nullptr;
         double* vo = w == 1 ? dst : nullptr;
         if (h->precision == 32)
-            PD_CUDA(launch_get_state_f32(h->u64[cur], (const float*)h->v, h->gid, h->n, uo, vo,
-                                         h->stream),
+            PD_CUDA(launch_get_state_f32(h->rec32[cur], (const float*)h->v, h->gid, h->n,
+                                         h->delta, uo, vo, h->stream),
                     "get state");
         else
-            PD_CUDA(launch_get_state_f64((const double*)h->rec[cur], (const double*)h->v, h->gid,
-                                         h->n, uo, vo, h->stream),
+            PD_CUDA(launch_get_state_f64(h->rec[cur], (const double*)h->v, h->gid, h->n, uo, vo,
+                                         h->stream),
                     "get state");
         if (!dev)
             PD_CUDA(cudaMemcpyAsync(o, h->staging, 24 * h->n, cudaMemcpyDeviceToHost, h->stream),
@@ -623,12 +641,12 @@ pd_status pd_set_state(pd_handle* h, const double* u, const double* v, int64_t s
         const double* ui = w == 0 ? src : nullptr;
         const double* vi = w == 1 ? src : nullptr;
         if (h->precision == 32)
-            PD_CUDA(launch_set_state_f32(ui, vi, h->gid, h->n, 1.0 / h->delta, h->u64[cur],
-                                         (float4*)h->rec[cur], (float*)h->v, h->stream),
+            PD_CUDA(launch_set_state_f32(ui, vi, h->gid, h->n, 1.0 / h->delta, h->rec32[cur],
+                                         (float*)h->v, h->stream),
                     "set state");
         else
-            PD_CUDA(launch_set_state_f64(ui, vi, h->gid, h->n, (double*)h->rec[cur],
-                                         (double*)h->v, h->stream),
+            PD_CUDA(launch_set_state_f64(ui, vi, h->gid, h->n, h->rec[cur], (double*)h->v,
+                                         h->stream),
                     "set state");
         if (src == h->staging) PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
     }
@@ -641,19 +659,18 @@ pd_status pd_get_bonds(pd_handle* h, uint8_t* mu)
 {
     if (!h || !mu) return fail(PD_ERR_ARG, "NULL argument");
     PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
-    std::vector<uint32_t> bits((size_t)(h->n * h->Q));
-    PD_CUDA(cudaMemcpyAsync(bits.data(), h->bits, bits.size() * 4, cudaMemcpyDeviceToHost,
-                            h->stream),
-            "copy bond flags");
-    PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
-    std::vector<int32_t> nbr((size_t)(h->n * 32 * h->Q));
-    PD_CUDA(cudaMemcpy(nbr.data(), h->nbr, nbr.size() * 4, cudaMemcpyDeviceToHost), "copy family");
     std::vector<int64_t> pos;
-    slot_to_canonical(h->n, h->off, h->idx, h->perm, nbr, h->cnt, h->Q, pos);
+    pd_status st = canonical_slots(h, pos);
+    if (st != PD_OK) return st;
+    std::vector<uint32_t> bits((size_t)(h->n_slices * h->Q * 32));
+    PD_CUDA(cudaMemcpy(bits.data(), h->bits, bits.size() * 4, cudaMemcpyDeviceToHost),
+            "copy bond flags");
     const int64_t W = 32LL * h->Q;
-    for (int64_t p = 0; p < h->n; ++p)
+    for (int64_t p = 0; p < h->n; ++p) {
+        const int64_t g = p / 32, l = p % 32;
         for (int64_t m = 0; m < h->cnt[p]; ++m)
-            mu[pos[p * W + m]] = (bits[p * h->Q + (m >> 5)] >> (m & 31)) & 1u;
+            mu[pos[(g * W + m) * 32 + l]] = (bits[(g * h->Q + (m >> 5)) * 32 + l] >> (m & 31)) & 1u;
+    }
     return PD_OK;
 }
 
@@ -663,16 +680,16 @@ pd_status pd_set_bonds(pd_handle* h, const uint8_t* mu)
     for (int64_t k = 0; k < h->n_bonds; ++k)
         if (mu[k] > 1) return fail(PD_ERR_ARG, "bond flags must be 0 or 1");
     PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
-    std::vector<int32_t> nbr((size_t)(h->n * 32 * h->Q));
-    PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
-    PD_CUDA(cudaMemcpy(nbr.data(), h->nbr, nbr.size() * 4, cudaMemcpyDeviceToHost), "copy family");
     std::vector<int64_t> pos;
-    slot_to_canonical(h->n, h->off, h->idx, h->perm, nbr, h->cnt, h->Q, pos);
+    pd_status st = canonical_slots(h, pos);
+    if (st != PD_OK) return st;
     const int64_t W = 32LL * h->Q;
-    std::vector<uint32_t> bits((size_t)(h->n * h->Q), 0u);
-    for (int64_t p = 0; p < h->n; ++p)
+    std::vector<uint32_t> bits((size_t)(h->n_slices * h->Q * 32), 0u);
+    for (int64_t p = 0; p < h->n; ++p) {
+        const int64_t g = p / 32, l = p % 32;
         for (int64_t m = 0; m < h->cnt[p]; ++m)
-            if (mu[pos[p * W + m]]) bits[p * h->Q + (m >> 5)] |= 1u << (m & 31);
+            if (mu[pos[(g * W + m) * 32 + l]]) bits[(g * h->Q + (m >> 5)) * 32 + l] |= 1u << (m & 31);
+    }
     PD_CUDA(cudaMemcpy(h->bits, bits.data(), bits.size() * 4, cudaMemcpyHostToDevice),
             "upload bond flags");
     h->damage_fresh = false;
@@ -685,13 +702,12 @@ pd_status pd_damage(pd_handle* h, double* phi)
     PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
     const bool dev = is_device_ptr(phi);
     double* dst = dev ? phi : h->staging;
-    const int cur = (int)(h->step & 1);
     if (h->damage_fresh)  // written by the last step kernel (fused)
         PD_CUDA(launch_gather_damage(h->precision, h->damage, h->gid, h->n, dst, h->stream),
                 "damage");
     else
-        PD_CUDA(launch_damage(h->precision, h->rec[cur], h->nbr, h->bits, h->wsum_inv, h->gid,
-                              h->n, h->Q, dst, h->stream),
+        PD_CUDA(launch_damage(h->precision, h->wrec(), h->nbr, h->bits, h->sw, h->wsum_inv,
+                              h->gid, h->n, h->Q, dst, h->stream),
                 "damage");
     if (!dev)
         PD_CUDA(cudaMemcpyAsync(phi, h->staging, 8 * h->n, cudaMemcpyDeviceToHost, h->stream),
@@ -712,13 +728,10 @@ pd_status pd_set_params(pd_handle* h, double c, double sc, double load, double d
         for (int64_t k = 0; k < h->n_bonds; ++k)
             if (!(c_bond[k] > 0.0) || !std::isfinite(c_bond[k]))
                 return fail(PD_ERR_ARG, "c_bond must be finite and > 0");
-        std::vector<int32_t> nbr((size_t)(h->n * 32 * h->Q));
-        PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
-        PD_CUDA(cudaMemcpy(nbr.data(), h->nbr, nbr.size() * 4, cudaMemcpyDeviceToHost),
-                "copy family");
         std::vector<int64_t> pos;
-        slot_to_canonical(h->n, h->off, h->idx, h->perm, nbr, h->cnt, h->Q, pos);
-        const size_t slots = nbr.size();
+        pd_status st = canonical_slots(h, pos);
+        if (st != PD_OK) return st;
+        const size_t slots = pos.size();
         if (!h->cbond) {
             cudaError_t e = h->alloc((uint8_t**)&h->cbond, slots * (h->precision == 32 ? 4 : 8));
             if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc c_bond");

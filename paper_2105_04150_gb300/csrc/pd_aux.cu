@@ -1,5 +1,5 @@
 // Auxiliary kernels: step counter, state transfer between the caller's node
-// order and the library's spatial order, damage from the bond flags (Eq. 8),
+// order and the library's node order, damage from the bond flags (Eq. 8),
 // and the per-node bond weights w = c V.
 #include <cuda_runtime.h>
 
@@ -8,46 +8,55 @@
 namespace pd {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-
 __global__ void k_advance(int64_t* ctr, int64_t k)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) *ctr += k;
 }
 
-__global__ void k_get_state_f32(const double* __restrict__ u64, const float* __restrict__ v32,
-                                const int32_t* __restrict__ gid, int64_t n,
+#define GRID_STRIDE(var, count)                                                   \
+    for (int64_t var = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; var < (count); \
+         var += (int64_t)gridDim.x * blockDim.x)
+
+__global__ void k_get_state_f32(const float4* __restrict__ rec, const float* __restrict__ v32,
+                                const int32_t* __restrict__ gid, int64_t n, double delta,
                                 double* __restrict__ u_out, double* __restrict__ v_out)
 {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 3 * n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = e / 3;
-        const int c = (int)(e - 3 * p);
+    GRID_STRIDE(p, n)
+    {
         const int64_t g = gid[p];
-        if (u_out) u_out[3 * g + c] = u64[e];
-        if (v_out) v_out[3 * g + c] = (double)v32[e];
+        if (u_out) {
+            const float4 h = rec[3 * p + 1];
+            const float4 l = rec[3 * p + 2];
+            u_out[3 * g] = ((double)h.x + (double)h.w) * delta;
+            u_out[3 * g + 1] = ((double)h.y + (double)l.x) * delta;
+            u_out[3 * g + 2] = ((double)h.z + (double)l.y) * delta;
+        }
+        if (v_out)
+            for (int c = 0; c < 3; ++c) v_out[3 * g + c] = (double)v32[3 * p + c];
     }
+}
+
+__device__ __forceinline__ void split(double x, float& h, float& l)
+{
+    h = (float)x;
+    l = (float)(x - (double)h);
 }
 
 __global__ void k_set_state_f32(const double* __restrict__ u_in, const double* __restrict__ v_in,
                                 const int32_t* __restrict__ gid, int64_t n, double inv_delta,
-                                double* __restrict__ u64, float4* __restrict__ rec,
-                                float* __restrict__ v32)
+                                float4* __restrict__ rec, float* __restrict__ v32)
 {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x) {
+    GRID_STRIDE(p, n)
+    {
         const int64_t g = gid[p];
         if (u_in) {
-            const double ux = u_in[3 * g], uy = u_in[3 * g + 1], uz = u_in[3 * g + 2];
-            u64[3 * p] = ux;
-            u64[3 * p + 1] = uy;
-            u64[3 * p + 2] = uz;
-            rec[2 * p + 1] = make_float4((float)(ux * inv_delta), (float)(uy * inv_delta),
-                                         (float)(uz * inv_delta), 0.0f);
+            float h[3], l[3];
+            for (int c = 0; c < 3; ++c) split(u_in[3 * g + c] * inv_delta, h[c], l[c]);
+            rec[3 * p + 1] = make_float4(h[0], h[1], h[2], l[0]);
+            rec[3 * p + 2] = make_float4(l[1], l[2], 0.0f, 0.0f);
         }
-        if (v_in) {
+        if (v_in)
             for (int c = 0; c < 3; ++c) v32[3 * p + c] = (float)v_in[3 * g + c];
-        }
     }
 }
 
@@ -55,8 +64,8 @@ __global__ void k_get_state_f64(const double* __restrict__ rec, const double* __
                                 const int32_t* __restrict__ gid, int64_t n,
                                 double* __restrict__ u_out, double* __restrict__ v_out)
 {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 3 * n;
-         e += (int64_t)gridDim.x * blockDim.x) {
+    GRID_STRIDE(e, 3 * n)
+    {
         const int64_t p = e / 3;
         const int c = (int)(e - 3 * p);
         const int64_t g = gid[p];
@@ -69,8 +78,8 @@ __global__ void k_set_state_f64(const double* __restrict__ u_in, const double* _
                                 const int32_t* __restrict__ gid, int64_t n,
                                 double* __restrict__ rec, double* __restrict__ v64)
 {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 3 * n;
-         e += (int64_t)gridDim.x * blockDim.x) {
+    GRID_STRIDE(e, 3 * n)
+    {
         const int64_t p = e / 3;
         const int c = (int)(e - 3 * p);
         const int64_t g = gid[p];
@@ -80,71 +89,49 @@ __global__ void k_set_state_f64(const double* __restrict__ u_in, const double* _
 }
 
 template <typename T>
-__device__ __forceinline__ T rec_w(const void* rec, int64_t p);
+__device__ __forceinline__ T node_w(const void* wrec, int64_t p);
 template <>
-__device__ __forceinline__ float rec_w<float>(const void* rec, int64_t p)
+__device__ __forceinline__ float node_w<float>(const void* wrec, int64_t p)
 {
-    return reinterpret_cast<const float4*>(rec)[2 * p].w;
+    return reinterpret_cast<const float4*>(wrec)[3 * p].w;
 }
 template <>
-__device__ __forceinline__ double rec_w<double>(const void* rec, int64_t p)
+__device__ __forceinline__ double node_w<double>(const void* wrec, int64_t p)
 {
-    return reinterpret_cast<const double*>(rec)[8 * p + 3];
+    return reinterpret_cast<const double*>(wrec)[8 * p + 3];
 }
 
-// phi = 1 - sum_{intact j} w_j / sum_{family j} w_j  (Eq. 8), warp per node.
+// sum over the set bits of `bits` of w_j, lane per node, in slot order (the
+// same order as the step kernels, so the result is bit-identical to theirs).
 template <typename T>
-__global__ void k_damage(const void* __restrict__ rec, const int32_t* __restrict__ nbr,
-                         const uint32_t* __restrict__ bits, const T* __restrict__ wsum_inv,
-                         const int32_t* __restrict__ gid, int64_t n, int Q,
-                         double* __restrict__ phi)
+__device__ __forceinline__ T masked_wsum(const void* wrec, const int32_t* __restrict__ nbr,
+                                         const uint32_t* __restrict__ bits, int64_t g, int lane,
+                                         int Wg, int Q)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n; p += nw) {
-        T acc = 0;
-        for (int q = 0; q < Q; ++q) {
-            const uint32_t w = bits[p * Q + q];
-            if ((w >> lane) & 1u) acc += rec_w<T>(rec, nbr[p * 32 * Q + q * 32 + lane]);
-        }
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-        if (lane == 0) phi[gid[p]] = (double)(1 - acc * wsum_inv[p]);
+    const int64_t W = 32LL * Q;
+    T acc = 0;
+    for (int q = 0; q * 32 < Wg; ++q) {
+        const uint32_t word = bits[(g * Q + q) * 32 + lane];
+        const int mend = min(32, Wg - q * 32);
+        for (int b = 0; b < mend; ++b)
+            if ((word >> b) & 1u) acc += node_w<T>(wrec, nbr[(g * W + q * 32 + b) * 32 + lane]);
     }
+    return acc;
 }
 
 template <typename T>
-__global__ void k_set_w(void* rec0, void* rec1, const double* __restrict__ vol, int64_t n,
-                        double wscale)
+__global__ void k_damage(const void* __restrict__ wrec, const int32_t* __restrict__ nbr,
+                         const uint32_t* __restrict__ bits, const int32_t* __restrict__ sw,
+                         const T* __restrict__ wsum_inv, const int32_t* __restrict__ gid,
+                         int64_t n, int Q, double* __restrict__ phi)
 {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const T w = (T)(wscale * vol[p]);
-        if (sizeof(T) == 4) {
-            reinterpret_cast<float4*>(rec0)[2 * p].w = (float)w;
-            reinterpret_cast<float4*>(rec1)[2 * p].w = (float)w;
-        } else {
-            reinterpret_cast<double*>(rec0)[8 * p + 3] = (double)w;
-            reinterpret_cast<double*>(rec1)[8 * p + 3] = (double)w;
-        }
-    }
-}
-
-template <typename T>
-__global__ void k_wsum(const void* __restrict__ rec, const int32_t* __restrict__ nbr,
-                       const int32_t* __restrict__ fam_cnt, int64_t n, int Q,
-                       T* __restrict__ wsum_inv)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n; p += nw) {
-        T acc = 0;
-        const int cnt = fam_cnt[p];
-        for (int q = 0; q < Q; ++q) {
-            const int m = q * 32 + lane;
-            if (m < cnt) acc += rec_w<T>(rec, nbr[p * 32 * Q + m]);
-        }
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-        if (lane == 0) wsum_inv[p] = acc > 0 ? (T)1 / acc : (T)0;
+    GRID_STRIDE(p, ((n + 31) >> 5) << 5)
+    {
+        const int64_t g = p >> 5;
+        const int lane = (int)(p & 31);
+        const T acc = masked_wsum<T>(wrec, nbr, bits, g, lane, sw[g], Q);
+        // a node without family has no damage (the integral ratio of Eq. 8 is 0/0)
+        if (p < n) phi[gid[p]] = wsum_inv[p] > 0 ? (double)((T)1 - acc * wsum_inv[p]) : 0.0;
     }
 }
 
@@ -152,9 +139,37 @@ template <typename T>
 __global__ void k_gather_damage(const T* __restrict__ dmg, const int32_t* __restrict__ gid,
                                 int64_t n, double* __restrict__ phi)
 {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x)
-        phi[gid[p]] = (double)dmg[p];
+    GRID_STRIDE(p, n) phi[gid[p]] = (double)dmg[p];
+}
+
+template <typename T>
+__global__ void k_set_w(void* wrec0, void* wrec1, const double* __restrict__ vol, int64_t n,
+                        double wscale)
+{
+    GRID_STRIDE(p, n)
+    {
+        if (sizeof(T) == 4) {
+            reinterpret_cast<float4*>(wrec0)[3 * p].w = (float)(wscale * vol[p]);
+            reinterpret_cast<float4*>(wrec1)[3 * p].w = (float)(wscale * vol[p]);
+        } else {
+            reinterpret_cast<double*>(wrec0)[8 * p + 3] = wscale * vol[p];
+            reinterpret_cast<double*>(wrec1)[8 * p + 3] = wscale * vol[p];
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_wsum(const void* __restrict__ wrec, const int32_t* __restrict__ nbr,
+                       const uint32_t* __restrict__ bits0, const int32_t* __restrict__ sw,
+                       int64_t n, int Q, T* __restrict__ wsum_inv)
+{
+    GRID_STRIDE(p, ((n + 31) >> 5) << 5)
+    {
+        const int64_t g = p >> 5;
+        const int lane = (int)(p & 31);
+        const T acc = masked_wsum<T>(wrec, nbr, bits0, g, lane, sw[g], Q);
+        wsum_inv[p] = acc > 0 ? (T)1 / acc : (T)0;
+    }
 }
 
 int grid_for(int64_t work, int block)
@@ -173,19 +188,19 @@ cudaError_t launch_advance(int64_t* step_ctr, int64_t k, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_get_state_f32(const double* u64, const float* v32, const int32_t* gid,
-                                 int64_t n, double* u_out, double* v_out, cudaStream_t s)
+cudaError_t launch_get_state_f32(const float4* rec, const float* v32, const int32_t* gid,
+                                 int64_t n, double delta, double* u_out, double* v_out,
+                                 cudaStream_t s)
 {
-    k_get_state_f32<<<grid_for(3 * n, 256), 256, 0, s>>>(u64, v32, gid, n, u_out, v_out);
+    k_get_state_f32<<<grid_for(n, 256), 256, 0, s>>>(rec, v32, gid, n, delta, u_out, v_out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_set_state_f32(const double* u_in, const double* v_in, const int32_t* gid,
-                                 int64_t n, double inv_delta, double* u64, float4* rec,
-                                 float* v32, cudaStream_t s)
+                                 int64_t n, double inv_delta, float4* rec, float* v32,
+                                 cudaStream_t s)
 {
-    k_set_state_f32<<<grid_for(n, 256), 256, 0, s>>>(u_in, v_in, gid, n, inv_delta, u64, rec,
-                                                     v32);
+    k_set_state_f32<<<grid_for(n, 256), 256, 0, s>>>(u_in, v_in, gid, n, inv_delta, rec, v32);
     return cudaGetLastError();
 }
 
@@ -203,17 +218,17 @@ cudaError_t launch_set_state_f64(const double* u_in, const double* v_in, const i
     return cudaGetLastError();
 }
 
-cudaError_t launch_damage(int precision, const void* rec, const int32_t* nbr,
-                          const uint32_t* bits, const void* wsum_inv, const int32_t* gid,
-                          int64_t n, int Q, double* phi_out, cudaStream_t s)
+cudaError_t launch_damage(int precision, const void* wrec, const int32_t* nbr,
+                          const uint32_t* bits, const int32_t* sw, const void* wsum_inv,
+                          const int32_t* gid, int64_t n, int Q, double* phi_out, cudaStream_t s)
 {
-    const int g = grid_for(32 * n, 256);
+    const int g = grid_for(n, 256);
     if (precision == 32)
-        k_damage<float><<<g, 256, 0, s>>>(rec, nbr, bits, (const float*)wsum_inv, gid, n, Q,
+        k_damage<float><<<g, 256, 0, s>>>(wrec, nbr, bits, sw, (const float*)wsum_inv, gid, n, Q,
                                           phi_out);
     else
-        k_damage<double><<<g, 256, 0, s>>>(rec, nbr, bits, (const double*)wsum_inv, gid, n, Q,
-                                           phi_out);
+        k_damage<double><<<g, 256, 0, s>>>(wrec, nbr, bits, sw, (const double*)wsum_inv, gid, n,
+                                           Q, phi_out);
     return cudaGetLastError();
 }
 
@@ -228,18 +243,18 @@ cudaError_t launch_gather_damage(int precision, const void* dmg, const int32_t* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_set_weights(int precision, void* rec0, void* rec1, const double* vol,
-                               const int32_t* nbr, const int32_t* fam_cnt, int64_t n, int Q,
-                               double wscale, void* wsum_inv, cudaStream_t s)
+cudaError_t launch_set_weights(int precision, void* wrec0, void* wrec1, const double* vol,
+                               const int32_t* nbr, const uint32_t* init_bits, const int32_t* sw,
+                               int64_t n, int Q, double wscale, void* wsum_inv, cudaStream_t s)
 {
     if (precision == 32) {
-        k_set_w<float><<<grid_for(n, 256), 256, 0, s>>>(rec0, rec1, vol, n, wscale);
-        k_wsum<float><<<grid_for(32 * n, 256), 256, 0, s>>>(rec0, nbr, fam_cnt, n, Q,
-                                                            (float*)wsum_inv);
+        k_set_w<float><<<grid_for(n, 256), 256, 0, s>>>(wrec0, wrec1, vol, n, wscale);
+        k_wsum<float><<<grid_for(n, 256), 256, 0, s>>>(wrec0, nbr, init_bits, sw, n, Q,
+                                                       (float*)wsum_inv);
     } else {
-        k_set_w<double><<<grid_for(n, 256), 256, 0, s>>>(rec0, rec1, vol, n, wscale);
-        k_wsum<double><<<grid_for(32 * n, 256), 256, 0, s>>>(rec0, nbr, fam_cnt, n, Q,
-                                                             (double*)wsum_inv);
+        k_set_w<double><<<grid_for(n, 256), 256, 0, s>>>(wrec0, wrec1, vol, n, wscale);
+        k_wsum<double><<<grid_for(n, 256), 256, 0, s>>>(wrec0, nbr, init_bits, sw, n, Q,
+                                                        (double*)wsum_inv);
     }
     return cudaGetLastError();
 }

@@ -170,16 +170,19 @@ void apply_cuts(int64_t n, const double* x, const double* cuts, int32_t ncuts,
     off.swap(noff);
 }
 
-void spatial_order(int64_t n, const double* x, double delta, std::vector<int32_t>& perm,
-                   std::vector<int32_t>& inv)
+void spatial_order(int64_t n, const double* x, double delta, int reorder,
+                   std::vector<int32_t>& perm, std::vector<int32_t>& inv)
 {
-    // Nodes sorted by the cell (edge = horizon) they fall in, cells in
-    // lexicographic order, ties by caller id: a warp's 32 nodes and a block's
-    // few hundred are spatial neighbours and share most of their families.
+    // reorder == 0 keeps the caller's order (a row-major lattice is already the
+    // best order for the sliced layout: the 32 nodes of a slice are translates
+    // of each other, so slot m of all of them points to the same offset and the
+    // neighbour gathers are contiguous).  reorder == 1 sorts nodes by the cell
+    // (edge = horizon) they fall in, cells in lexicographic order, ties by
+    // caller id, for point sets given in no particular order.
     Grid g;
     perm.resize(n);
     inv.resize(n);
-    if (!build_grid(g, n, x, delta)) {
+    if (reorder == 0 || !build_grid(g, n, x, delta)) {
         std::iota(perm.begin(), perm.end(), 0);
     } else {
         std::copy(g.items.begin(), g.items.end(), perm.begin());
@@ -190,22 +193,37 @@ void spatial_order(int64_t n, const double* x, double delta, std::vector<int32_t
 void build_layout(int64_t n, const std::vector<int64_t>& off, const std::vector<int32_t>& idx,
                   const std::vector<int32_t>& perm, const std::vector<int32_t>& inv, int Q,
                   std::vector<int32_t>& nbr, std::vector<uint32_t>& bits,
-                  std::vector<int32_t>& cnt)
+                  std::vector<int32_t>& sw, std::vector<int32_t>& cnt)
 {
+    // Sliced ELL, slice height 32 (one warp): member m of node p = 32g + l at
+    // nbr[(g*W + m)*32 + l]; bond flag word q at bits[(g*Q + q)*32 + l].
     const int64_t W = 32LL * Q;
-    nbr.resize((size_t)(n * W));
-    bits.assign((size_t)(n * Q), 0u);
-    cnt.resize(n);
+    const int64_t ns = (n + 31) / 32;
+    nbr.resize((size_t)(ns * W * 32));
+    bits.assign((size_t)(ns * Q * 32), 0u);
+    sw.assign((size_t)ns, 0);
+    cnt.assign((size_t)(ns * 32), 0);
 #pragma omp parallel for schedule(static)
-    for (int64_t p = 0; p < n; ++p) {
-        const int64_t i = perm[p];
-        const int64_t m = off[i + 1] - off[i];
-        int32_t* row = nbr.data() + p * W;
-        for (int64_t k = 0; k < m; ++k) row[k] = inv[idx[off[i] + k]];
-        std::sort(row, row + m);
-        for (int64_t k = m; k < W; ++k) row[k] = (int32_t)p;
-        for (int64_t k = 0; k < m; ++k) bits[p * Q + (k >> 5)] |= 1u << (k & 31);
-        cnt[p] = (int32_t)m;
+    for (int64_t g = 0; g < ns; ++g) {
+        std::vector<int32_t> row;
+        int32_t width = 0;
+        for (int l = 0; l < 32; ++l) {
+            const int64_t p = g * 32 + l;
+            row.clear();
+            if (p < n) {
+                const int64_t i = perm[p];
+                for (int64_t k = off[i]; k < off[i + 1]; ++k) row.push_back(inv[idx[k]]);
+                std::sort(row.begin(), row.end());
+            }
+            const int64_t m = (int64_t)row.size();
+            for (int64_t k = 0; k < W; ++k)
+                nbr[(g * W + k) * 32 + l] = k < m ? row[k] : (int32_t)p;
+            for (int64_t k = 0; k < m; ++k)
+                bits[(g * Q + (k >> 5)) * 32 + l] |= 1u << (k & 31);
+            cnt[p] = (int32_t)m;
+            width = std::max<int32_t>(width, (int32_t)m);
+        }
+        sw[g] = width;
     }
 }
 
@@ -213,17 +231,20 @@ void slot_to_canonical(int64_t n, const std::vector<int64_t>& off, const std::ve
                        const std::vector<int32_t>& perm, const std::vector<int32_t>& nbr,
                        const std::vector<int32_t>& cnt, int Q, std::vector<int64_t>& pos)
 {
-    // pos[p*W + m] = canonical CSR position of member m of node p (or -1 for padding)
+    // pos[slot] = canonical CSR position of the bond in that SELL slot (-1 if unused)
     const int64_t W = 32LL * Q;
-    pos.assign((size_t)(n * W), -1);
+    const int64_t ns = (n + 31) / 32;
+    pos.assign((size_t)(ns * W * 32), -1);
 #pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < n; ++p) {
+        const int64_t g = p / 32, l = p % 32;
         const int64_t i = perm[p];
         const int32_t* b = idx.data() + off[i];
         const int32_t* e = idx.data() + off[i + 1];
         for (int64_t m = 0; m < cnt[p]; ++m) {
-            const int32_t j = perm[nbr[p * W + m]];
-            pos[p * W + m] = off[i] + (std::lower_bound(b, e, j) - b);
+            const int64_t slot = (g * W + m) * 32 + l;
+            const int32_t j = perm[nbr[slot]];
+            pos[slot] = off[i] + (std::lower_bound(b, e, j) - b);
         }
     }
 }

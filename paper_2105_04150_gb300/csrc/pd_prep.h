@@ -18,15 +18,16 @@ std::string check_family(int64_t n, const int64_t* off, const int32_t* idx);
 // Remove bonds whose segment crosses a cut rectangle (initial notch, Section 6).
 void apply_cuts(int64_t n, const double* x, const double* cuts, int32_t ncuts,
                 std::vector<int64_t>& off, std::vector<int32_t>& idx);
-// perm[p] = caller id of spatial position p; inv = inverse.
-void spatial_order(int64_t n, const double* x, double delta, std::vector<int32_t>& perm,
-                   std::vector<int32_t>& inv);
-// Padded q-major family (W = 32 Q slots per node), intact-bond bits and counts.
+// perm[p] = caller id of node position p; inv = inverse (reorder: 0 keep, 1 cells).
+void spatial_order(int64_t n, const double* x, double delta, int reorder,
+                   std::vector<int32_t>& perm, std::vector<int32_t>& inv);
+// Sliced ELL (slice height 32, W = 32 Q slots), intact-bond bits, per-slice
+// widths and per-node counts (padded to a multiple of 32 nodes).
 void build_layout(int64_t n, const std::vector<int64_t>& off, const std::vector<int32_t>& idx,
                   const std::vector<int32_t>& perm, const std::vector<int32_t>& inv, int Q,
                   std::vector<int32_t>& nbr, std::vector<uint32_t>& bits,
-                  std::vector<int32_t>& cnt);
-// Canonical CSR position of every device slot (-1 for padding).
+                  std::vector<int32_t>& sw, std::vector<int32_t>& cnt);
+// Canonical CSR position of every device slot (-1 for unused slots).
 void slot_to_canonical(int64_t n, const std::vector<int64_t>& off, const std::vector<int32_t>& idx,
                        const std::vector<int32_t>& perm, const std::vector<int32_t>& nbr,
                        const std::vector<int32_t>& cnt, int Q, std::vector<int64_t>& pos);

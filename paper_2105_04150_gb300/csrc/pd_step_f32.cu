@@ -1,30 +1,36 @@
 // Fused FP32-bulk peridynamic step kernel for sm_103a.
 //
-// One launch = one explicit time step (bond kinematics, irreversible breaking,
-// force reduction, body force, damped Euler-Cromer update, displacement BCs,
-// damage), i.e. the bond-force + reduction kernel and the integrator kernel of
-// the paper (Algorithm bond_index, Algorithm reduction, Section 3.3) fused
-// into one pass.  The paper keeps integration in a second kernel because an
-// in-place update would race with neighbours still reading u^n (Section 3.3);
-// here every array that neighbours read (node records, FP64 displacement) is
-// double-buffered, so step k reads buffer k&1 and writes buffer (k+1)&1.
+// One launch = one explicit time step: bond kinematics (Eq. 4), irreversible
+// breaking (Eq. 6), pairwise PMB force (Eq. 5) reduced onto the node
+// (Eq. 10), body force, damped Euler-Cromer update (Eq. 11), displacement
+// BCs and damage (Eq. 8).  The paper splits this into a bond kernel and an
+// integrator kernel because an in-place update would race with neighbours
+// still reading u^n (Section 3.3); here the displacement that neighbours read
+// is double-buffered (step k reads buffer k&1, writes (k+1)&1), so the whole
+// step is one kernel and every node's data crosses HBM once per step.
 //
-// Work decomposition: a warp owns a group of 32 consecutive nodes (spatial
-// order).  For each node of the group, lane l evaluates the family members
-// q*32+l (q < Q) - one coalesced 128-byte load of neighbour ids per q - and the
-// four partial sums (force x/y/z and intact-bond weight) are reduced with a
-// shuffle butterfly; lane t keeps node t's totals.  The group's integration
-// then runs lane-parallel (lane t integrates node t) with coalesced node loads
-// and stores.  Bond flags are bits: word q of a node is exactly the ballot of
-// its lanes' "still intact" predicates for round q.
+// Work decomposition ("lane per node" over a sliced ELL): a warp owns a slice
+// of 32 consecutive nodes and walks their families in lockstep, slot m of all
+// 32 nodes per iteration - one coalesced 128-byte load of neighbour ids - so
+// each lane accumulates its own node's force in registers: no shared-memory
+// reduction, no shuffles, no barriers.  Bond flags are the lane's own 32-bit
+// words.  The slot loop is branch-free: slots beyond a lane's family or of
+// broken bonds are evaluated and masked (the paper's thread-divergence
+// trade-off, Section 3.5, resolved in favour of no divergence at all, with the
+// padding bounded per slice instead of per power of two).  The slice's
+// neighbour-id block is requested from HBM with one bulk L2 prefetch when the
+// warp starts it, so the stream does not wait for the warp's own loads.
+// Each node's gather data is one 48-byte record {x~, w | h | l}.
 //
-// Precision: bond arithmetic is FP32 in units of the horizon, using the
+// Precision: bond arithmetic is FP32 in units of the horizon with the
 // cancellation-free stretch s = eta.(2 xi + eta) / (|xi| (|xi| + |xi+eta|)).
-// It is exactly antisymmetric: bond j->i sees -xi, -eta and computes the same
-// bits as i->j, so both directions break together.  A bond whose FP32 stretch
-// lies within a relative band `guard` of s_c is re-tested with the literal
-// FP64 stretch of Eq. 4 from FP64 positions and displacements, so the break
-// decision is the FP64 one.  Displacements accumulate in FP64.
+// The displacement is an unevaluated float-float sum h + l (48-bit
+// significand): it is accumulated exactly enough by two-sum updates and gives
+// eta = (h_j - h_i) + (l_j - l_i) to FP32 relative accuracy even when |u| is
+// far larger than |eta|.  The arithmetic is exactly antisymmetric (bond j->i
+// sees -xi, -eta and produces the same bits), so both directions of a bond
+// break together.  A bond whose FP32 stretch lies within a relative band of
+// s_c is re-tested with the literal FP64 stretch of Eq. 4.
 #include <cuda_runtime.h>
 
 #include "pd_internal.h"
@@ -32,7 +38,13 @@
 namespace pd {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
+#ifndef PD_F32_UNROLL
+#define PD_F32_UNROLL 4
+#endif
+#ifndef PD_F32_MIN_BLOCKS
+#define PD_F32_MIN_BLOCKS 3
+#endif
+constexpr int kUnroll = PD_F32_UNROLL;  // family slots in flight per lane
 
 // SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output m of the stream seeded
 // with `seed`.  Used as a counter-based draw of the per-bond critical stretch.
@@ -53,234 +65,253 @@ __device__ __forceinline__ double sc_draw(uint64_t seed, double lo, double hi, i
     return lo + (hi - lo) * ((double)(h >> 11) * 0x1.0p-53);
 }
 
-// Literal FP64 stretch of Eq. 4 for the bond i->j and the break test of Eq. 6.
-__device__ __noinline__ bool retest_f64(const double* __restrict__ x64,
-                                        const double* __restrict__ u, int64_t i, int64_t j,
-                                        double sc)
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes)
 {
-    double xi[3], y[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        xi[c] = x64[3 * j + c] - x64[3 * i + c];
-        y[c] = xi[c] + (u[3 * j + c] - u[3 * i + c]);
-    }
-    const double L = sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
-    const double r = sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
-    return (r - L) / L >= sc;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-__device__ __noinline__ bool pair_no_fail(const uint8_t* __restrict__ bcc,
-                                          const BcClass* __restrict__ bct, int64_t i, int64_t j)
+// (s, e) = exact sum of a and b (Knuth's two-sum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 {
-    return ((bct[bcc[i]].mask | bct[bcc[j]].mask) & 8u) != 0u;
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
 }
 
-// Break decision for an intact bond with FP32 stretch num/den (den > 0).
+// h + l += d, keeping |l| <= ulp(h)/2.
+__device__ __forceinline__ void ff_add(float& h, float& l, float d)
+{
+    float s, e;
+    two_sum(h, d, s, e);
+    e += l;
+    h = s + e;
+    l = e - (h - s);
+}
+
+__device__ __forceinline__ void ff_set(double x, float& h, float& l)
+{
+    h = (float)x;
+    l = (float)(x - (double)h);
+}
+
+// FP32 bond kinematics in horizon units: y = xi + eta, num = eta.(2 xi + eta)
+// = |y|^2 - |xi|^2 (no cancellation), den = |xi| (|xi| + |y|), so s = num / den.
+struct BondF32 {
+    float yx, yy, yz, num, den, y2;
+};
+
+__device__ __forceinline__ BondF32 bond_f32(const float4 xi, const float4 hi, const float2 li,
+                                            const float4 xj, const float4 hj, const float2 lj)
+{
+    BondF32 r;
+    const float ex = xj.x - xi.x, ey = xj.y - xi.y, ez = xj.z - xi.z;
+    const float hx = (hj.x - hi.x) + (hj.w - hi.w);
+    const float hy = (hj.y - hi.y) + (lj.x - li.x);
+    const float hz = (hj.z - hi.z) + (lj.y - li.y);
+    r.yx = ex + hx;
+    r.yy = ey + hy;
+    r.yz = ez + hz;
+    const float xx = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+    r.num = fmaf(hx, ex + r.yx, fmaf(hy, ey + r.yy, hz * (ez + r.yz)));
+    r.y2 = xx + r.num;
+    const float p = xx * r.y2;
+    r.den = xx + p * rsqrtf(p);
+    return r;
+}
+
+// c V_j s / |y| = w num / (den |y|)
+__device__ __forceinline__ float bond_coef(const BondF32& b, float w)
+{
+    return w * b.num * rsqrtf(b.den * b.den * b.y2);
+}
+
+// A bond whose FP32 stretch reached the band just below the smallest s_c: the
+// break test is decided in FP32 when s is clearly away from the bond's s_c and
+// otherwise with the literal FP64 stretch of Eq. 4 (FP64 positions, float-float
+// displacement); the no-fail rule applies last.  Returns the bond's force
+// contribution {fx, fy, fz, w}, all zero when it breaks (*broken = true).
 template <int SCM>
-__device__ __forceinline__ bool decide_break(const StepArgsF32& a, const double* __restrict__ uin,
-                                             int64_t i, int64_t j, float num, float den)
+__device__ __noinline__ float4 resolve_bond(const StepArgsF32& a, int cur, int64_t i, int64_t j,
+                                            int64_t slot, bool* broken)
 {
-    if (SCM == 0) {
-        const float r = fmaf(-a.sc_f, den, num);  // sign of s - s_c
-        if (fabsf(r) > a.guard * a.sc_f * den) return r >= 0.0f;
-        return retest_f64(a.x64, uin, i, j, a.sc);
-    } else {
-        // s_c in [sc_lo, sc_hi): most bonds are clearly below sc_lo.
-        const float rlo = fmaf(-a.sc_lo_f, den, num);
-        if (rlo < -a.guard * a.sc_lo_f * den) return false;
-        const double sc = sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i], a.gid[j]);
-        const float scf = (float)sc;
-        const float r = fmaf(-scf, den, num);
-        if (fabsf(r) > a.guard * scf * den) return r >= 0.0f;
-        return retest_f64(a.x64, uin, i, j, sc);
+    const float4* __restrict__ R = a.rec[cur];
+    const float4 xi = R[3 * i], hi = R[3 * i + 1], xj = R[3 * j], hj = R[3 * j + 1];
+    const float2 li = *reinterpret_cast<const float2*>(R + 3 * i + 2);
+    const float2 lj = *reinterpret_cast<const float2*>(R + 3 * j + 2);
+    const BondF32 b = bond_f32(xi, hi, li, xj, hj, lj);
+    double sc = a.sc;
+    float scf = a.sc_f;
+    if (SCM == 1) {
+        sc = sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i], a.gid[j]);
+        scf = (float)sc;
     }
+    const float r = fmaf(-scf, b.den, b.num);  // den * (s - s_c)
+    bool brk;
+    if (fabsf(r) > a.guard * scf * b.den) {
+        brk = r >= 0.0f;
+    } else {
+        const double ui[3] = {(double)hi.x + (double)hi.w, (double)hi.y + (double)li.x,
+                              (double)hi.z + (double)li.y};
+        const double uj[3] = {(double)hj.x + (double)hj.w, (double)hj.y + (double)lj.x,
+                              (double)hj.z + (double)lj.y};
+        double xv[3], y[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            xv[c] = a.x64[3 * j + c] - a.x64[3 * i + c];
+            y[c] = xv[c] + (uj[c] - ui[c]) * a.delta;
+        }
+        const double L = sqrt(xv[0] * xv[0] + xv[1] * xv[1] + xv[2] * xv[2]);
+        const double Rr = sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+        brk = (Rr - L) / L >= sc;
+    }
+    if (brk && a.has_nofail) brk = ((a.bct[a.bcc[i]].mask | a.bct[a.bcc[j]].mask) & 8u) == 0u;
+    *broken = brk;
+    if (brk) return make_float4(0.f, 0.f, 0.f, 0.f);
+    float w = xj.w;
+    if (a.cbond != nullptr) w *= a.cbond[slot];
+    const float coef = bond_coef(b, w);
+    return make_float4(coef * b.yx, coef * b.yy, coef * b.yz, xj.w);
 }
 
-template <int QT, int SCM>
-__global__ void __launch_bounds__(256) k_step_f32(const StepArgsF32 a)
+template <int SCM>
+__global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS) k_step_f32(const __grid_constant__ StepArgsF32 a)
 {
-    const int Q = (QT > 0) ? QT : a.q_rt;
-    const int W = 32 * Q;
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t step = *a.step_ctr + a.k;
     const int cur = (int)(step & 1);
-    const float4* __restrict__ rin = a.rec[cur];
-    float4* __restrict__ rout = const_cast<float4*>(a.rec[cur ^ 1]);
-    const double* __restrict__ uin = a.u64[cur];
-    double* __restrict__ uout = a.u64[cur ^ 1];
+    const int Q = a.Q;
+    const int64_t W = 32LL * Q;
+    const int64_t nslices = (a.n + 31) >> 5;
+    const float4* __restrict__ R = a.rec[cur];
+    float4* __restrict__ Rout = const_cast<float4*>(a.rec[cur ^ 1]);
     const float* __restrict__ cb = a.cbond;
-    const int64_t ngroups = (a.n + 31) >> 5;
+    const float fast_lo = a.fast_lo;
 
-    for (int64_t g = wid; g < ngroups; g += nwarps) {
-        const int64_t base = g << 5;
-        const int cnt = (int)min((int64_t)32, a.n - base);
-        float kx = 0.f, ky = 0.f, kz = 0.f, kw = 0.f;
+    for (int64_t g = wid; g < nslices; g += nwarps) {
+        const int Wg = a.sw[g];
+        const int32_t* __restrict__ col = a.nbr + g * W * 32 + lane;
+        if (lane == 0) prefetch_l2(col, (uint32_t)(((Wg + 3) & ~3) * 128));
+        const int64_t i = (g << 5) + lane;
+        const float4 xi = __ldg(R + 3 * i);
+        const float4 hi = __ldg(R + 3 * i + 1);
+        const float2 li = __ldg(reinterpret_cast<const float2*>(R + 3 * i + 2));
+        uint32_t* bw = a.bits + g * Q * 32 + lane;
+        float fx = 0.f, fy = 0.f, fz = 0.f, ws = 0.f;
 
-        for (int t = 0; t < cnt; ++t) {
-            const int64_t i = base + t;
-            const float4 xi = __ldg(rin + 2 * i);
-            const float4 ui = __ldg(rin + 2 * i + 1);
-            const int32_t* __restrict__ row = a.nbr + i * W;
-            uint32_t* brow = a.bits + i * Q;
-            float fx = 0.f, fy = 0.f, fz = 0.f, ws = 0.f;
-
-            for (int q0 = 0; q0 < Q; q0 += 4) {
-                uint32_t w[4];
-                int32_t jj[4];
-                bool al[4];
-                float4 xa[4], ua[4];
+        for (int q = 0; q * 32 < Wg; ++q) {
+            const uint32_t word = bw[q * 32];
+            uint32_t nword = word;
+            uint32_t pend = 0u;  // members in the near-s_c band, resolved below
+            const int mend = min(32, Wg - q * 32);
+            const int32_t* __restrict__ cq = col + (int64_t)q * 32 * 32;
+            for (int b0 = 0; b0 < mend; b0 += kUnroll) {
+                // every slot is evaluated; slots that are broken or unused (their
+                // id is the node itself) are masked out with selects, so the warp
+                // never diverges in this loop
+                int32_t jj[kUnroll];
+                float4 xa[kUnroll], ha[kUnroll];
+                float2 la[kUnroll];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int q = q0 + c;
-                    al[c] = false;
-                    w[c] = 0u;
-                    jj[c] = 0;
-                    if (q < Q) {
-                        w[c] = brow[q];
-                        jj[c] = __ldg(row + q * 32 + lane);
-                        al[c] = (w[c] >> lane) & 1u;
-                    }
+                for (int u = 0; u < kUnroll; ++u) jj[u] = __ldg(cq + (b0 + u) * 32);
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    const float4* rj = R + 3 * (int64_t)jj[u];
+                    xa[u] = __ldg(rj);
+                    ha[u] = __ldg(rj + 1);
+                    la[u] = __ldg(reinterpret_cast<const float2*>(rj + 2));
                 }
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    if (al[c]) {
-                        xa[c] = __ldg(rin + 2 * (int64_t)jj[c]);
-                        ua[c] = __ldg(rin + 2 * (int64_t)jj[c] + 1);
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    if (al[c]) {
-                        const float ex = xa[c].x - xi.x, ey = xa[c].y - xi.y, ez = xa[c].z - xi.z;
-                        const float hx = ua[c].x - ui.x, hy = ua[c].y - ui.y, hz = ua[c].z - ui.z;
-                        const float yx = ex + hx, yy = ey + hy, yz = ez + hz;
-                        const float xx = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                        // eta . (2 xi + eta) = |y|^2 - |xi|^2 without cancellation
-                        const float num = fmaf(hx, ex + yx, fmaf(hy, ey + yy, hz * (ez + yz)));
-                        const float y2 = xx + num;
-                        const float p = xx * y2;
-                        const float lxly = p * rsqrtf(p);           // |xi| |y|
-                        const float den = xx + lxly;                 // |xi| (|xi| + |y|)
-                        bool brk = decide_break<SCM>(a, uin, i, jj[c], num, den);
-                        if (brk && a.has_nofail) brk = !pair_no_fail(a.bcc, a.bct, i, jj[c]);
-                        if (brk) {
-                            al[c] = false;
-                        } else {
-                            // c V_j s / |y| = w_j num / (den |y|)
-                            float wj = xa[c].w;
-                            if (cb != nullptr) wj *= __ldg(cb + i * W + (q0 + c) * 32 + lane);
-                            const float coef = wj * num * rsqrtf(den * den * y2);
-                            fx = fmaf(coef, yx, fx);
-                            fy = fmaf(coef, yy, fy);
-                            fz = fmaf(coef, yz, fz);
-                            ws += xa[c].w;
-                        }
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    if (q0 + c < Q) {
-                        const uint32_t nw = __ballot_sync(kFull, al[c]);
-                        if (lane == 0 && nw != w[c]) brow[q0 + c] = nw;
-                    }
+                for (int u = 0; u < kUnroll; ++u) {
+                    const bool alive = (word >> (b0 + u)) & 1u;
+                    const BondF32 bd = bond_f32(xi, hi, li, xa[u], ha[u], la[u]);
+                    const bool cand = alive && (bd.num >= fast_lo * bd.den);
+                    const bool take = alive && !cand;
+                    pend |= cand ? (1u << (b0 + u)) : 0u;
+                    float wj = xa[u].w;
+                    if (cb != nullptr) wj *= __ldg(cb + (g * W + q * 32 + b0 + u) * 32 + lane);
+                    float coef = bond_coef(bd, wj);
+                    coef = take ? coef : 0.0f;
+                    fx = fmaf(coef, bd.yx, fx);
+                    fy = fmaf(coef, bd.yy, fy);
+                    fz = fmaf(coef, bd.yz, fz);
+                    ws += take ? xa[u].w : 0.0f;
                 }
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                fx += __shfl_xor_sync(kFull, fx, o);
-                fy += __shfl_xor_sync(kFull, fy, o);
-                fz += __shfl_xor_sync(kFull, fz, o);
-                ws += __shfl_xor_sync(kFull, ws, o);
+            while (pend) {
+                const int b = __ffs(pend) - 1;
+                pend &= pend - 1u;
+                const int64_t slot = (g * W + q * 32 + b) * 32 + lane;
+                bool broken;
+                const float4 f = resolve_bond<SCM>(a, cur, i, cq[b * 32], slot, &broken);
+                if (broken) {
+                    nword &= ~(1u << b);
+                } else {
+                    fx += f.x;
+                    fy += f.y;
+                    fz += f.z;
+                    ws += f.w;
+                }
             }
-            if (lane == t) {
-                kx = fx;
-                ky = fy;
-                kz = fz;
-                kw = ws;
-            }
+            if (nword != word) bw[q * 32] = nword;
         }
 
-        // ---- lane-parallel integration of the group (Eq. 11, damped Euler-Cromer)
-        if (lane < cnt) {
-            const int64_t i = base + lane;
+        // ---- integration of the lane's node (Eq. 11, damped Euler-Cromer)
+        if (i < a.n) {
             const uint32_t cls = a.bcc[i];
             uint32_t mask = 0u;
-            double gdisp[3] = {0.0, 0.0, 0.0};
-            float F[3] = {kx, ky, kz};
+            const BcClass* bc = nullptr;
+            float F[3] = {fx, fy, fz};
             if (cls != 0u) {
-                const BcClass& bc = a.bct[cls];
-                mask = bc.mask;
+                bc = a.bct + cls;
+                mask = bc->mask;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    gdisp[c] = bc.disp[c];
-                    F[c] += (float)(a.load * bc.force[c]);
-                }
+                for (int c = 0; c < 3; ++c) F[c] += (float)(a.load * bc->force[c]);
             }
-            const double s_now = a.disp_rate * (double)step;
-            const double s_next = a.disp_rate * (double)(step + 1);
             const float dtf = (float)a.dt, etaf = (float)a.eta, rhof = (float)a.rho;
-            double un[3];
+            const float dtd = (float)(a.dt * a.inv_delta);
+            float H[3] = {hi.x, hi.y, hi.z};
+            float L[3] = {hi.w, li.x, li.y};
             bool finite = true;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const float vi = a.v[3 * i + c];
                 float vn = vi + dtf * (F[c] - etaf * vi) / rhof;
-                double u = uin[3 * i + c] + a.dt * (double)vn;
+                ff_add(H[c], L[c], vn * dtd);
                 if (mask & (1u << c)) {
-                    u = gdisp[c] * s_next;
-                    vn = (float)(gdisp[c] * (s_next - s_now) / a.dt);
+                    const double s_now = a.disp_rate * (double)step;
+                    const double s_next = a.disp_rate * (double)(step + 1);
+                    ff_set(bc->disp[c] * s_next * a.inv_delta, H[c], L[c]);
+                    vn = (float)(bc->disp[c] * (s_next - s_now) / a.dt);
                 }
-                finite = finite && isfinite(u);
-                un[c] = u;
+                finite = finite && isfinite(H[c]);
                 a.v[3 * i + c] = vn;
-                uout[3 * i + c] = u;
             }
-            rout[2 * i] = __ldg(rin + 2 * i);
-            rout[2 * i + 1] = make_float4((float)(un[0] * a.inv_delta), (float)(un[1] * a.inv_delta),
-                                          (float)(un[2] * a.inv_delta), 0.0f);
-            a.damage[i] = 1.0f - kw * a.wsum_inv[i];
+            Rout[3 * i] = xi;
+            Rout[3 * i + 1] = make_float4(H[0], H[1], H[2], L[0]);
+            Rout[3 * i + 2] = make_float4(L[1], L[2], 0.0f, 0.0f);
+            const float wi = a.wsum_inv[i];
+            a.damage[i] = wi > 0.0f ? 1.0f - ws * wi : 0.0f;
             if (!finite) atomicOr(a.err, PD_DEVERR_NONFINITE);
         }
     }
 }
 
-template <int QT>
-cudaError_t launch_q(const StepArgsF32& a, int sc_mode, int grid, int block, cudaStream_t s)
+}  // namespace
+
+cudaError_t launch_step_f32(const StepArgsF32& a, int sc_mode, int grid, int block, cudaStream_t s)
 {
     if (sc_mode == 0)
-        k_step_f32<QT, 0><<<grid, block, 0, s>>>(a);
+        k_step_f32<0><<<grid, block, 0, s>>>(a);
     else
-        k_step_f32<QT, 1><<<grid, block, 0, s>>>(a);
+        k_step_f32<1><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int QT>
-const void* kernel_ptr(int sc_mode)
+const void* step_f32_kernel(int sc_mode)
 {
-    return sc_mode == 0 ? (const void*)k_step_f32<QT, 0> : (const void*)k_step_f32<QT, 1>;
-}
-
-}  // namespace
-
-cudaError_t launch_step_f32(const StepArgsF32& a, int Q, int sc_mode, int grid, int block,
-                            cudaStream_t s)
-{
-    switch (Q) {
-        case 4: return launch_q<4>(a, sc_mode, grid, block, s);
-        case 5: return launch_q<5>(a, sc_mode, grid, block, s);
-        default: return launch_q<0>(a, sc_mode, grid, block, s);
-    }
-}
-
-const void* step_f32_kernel(int Q, int sc_mode)
-{
-    switch (Q) {
-        case 4: return kernel_ptr<4>(sc_mode);
-        case 5: return kernel_ptr<5>(sc_mode);
-        default: return kernel_ptr<0>(sc_mode);
-    }
+    return sc_mode == 0 ? (const void*)k_step_f32<0> : (const void*)k_step_f32<1>;
 }
 
 }  // namespace pd

@@ -1,11 +1,12 @@
 // Fused FP64 peridynamic step kernel for sm_103a (the parity path).
 //
-// Same decomposition as the FP32-bulk kernel (warp per 32-node group, lane
-// per family member, shuffle reduction, lane-parallel integration, bit-packed
-// bond flags, double-buffered node records), but every quantity is FP64 and
-// the stretch is the literal one of Eq. 4, s = (|xi+eta| - |xi|) / |xi|, so
-// the break decisions are FP64 decisions.  Node record: 8 doubles
-// {x, y, z, w, ux, uy, uz, 0} with w = c V_j (or V_j with per-bond c).
+// Same decomposition as the FP32-bulk kernel (lane per node over the sliced
+// family layout, double-buffered displacement, bond flags as the lane's own
+// bit words, integration and damage in the same pass), but every quantity is
+// FP64 and the stretch is the literal one of Eq. 4,
+// s = (|xi + eta| - |xi|) / |xi|, so break decisions are FP64 decisions.
+// Node record: 8 doubles {x, y, z, w, ux, uy, uz, 0}, w = c V (or V with
+// per-bond stiffness).
 #include <cuda_runtime.h>
 
 #include "pd_internal.h"
@@ -13,7 +14,7 @@
 namespace pd {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
+constexpr int kUnroll = 2;
 
 __device__ __forceinline__ uint64_t splitmix_out(uint64_t seed, uint64_t m)
 {
@@ -38,117 +39,86 @@ __device__ __noinline__ bool pair_no_fail(const uint8_t* __restrict__ bcc,
     return ((bct[bcc[i]].mask | bct[bcc[j]].mask) & 8u) != 0u;
 }
 
-template <int QT, int SCM>
+template <int SCM>
 __global__ void __launch_bounds__(256) k_step_f64(const StepArgsF64 a)
 {
-    const int Q = (QT > 0) ? QT : a.q_rt;
-    const int W = 32 * Q;
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t step = *a.step_ctr + a.k;
     const int cur = (int)(step & 1);
+    const int Q = a.Q;
+    const int64_t W = 32LL * Q;
+    const int64_t nslices = (a.n + 31) >> 5;
     const double2* __restrict__ rin = reinterpret_cast<const double2*>(a.rec[cur]);
     double2* __restrict__ rout = reinterpret_cast<double2*>(const_cast<double*>(a.rec[cur ^ 1]));
     const double* __restrict__ cb = a.cbond;
-    const int64_t ngroups = (a.n + 31) >> 5;
 
-    for (int64_t g = wid; g < ngroups; g += nwarps) {
-        const int64_t base = g << 5;
-        const int cnt = (int)min((int64_t)32, a.n - base);
-        double kx = 0.0, ky = 0.0, kz = 0.0, kw = 0.0;
+    for (int64_t g = wid; g < nslices; g += nwarps) {
+        const int64_t i = (g << 5) + lane;
+        const int Wg = a.sw[g];
+        const double2 x01 = __ldg(rin + 4 * i), x23 = __ldg(rin + 4 * i + 1);
+        const double2 u01 = __ldg(rin + 4 * i + 2), u23 = __ldg(rin + 4 * i + 3);
+        const int32_t* __restrict__ col = a.nbr + g * W * 32 + lane;
+        uint32_t* bw = a.bits + g * Q * 32 + lane;
+        double fx = 0.0, fy = 0.0, fz = 0.0, ws = 0.0;
 
-        for (int t = 0; t < cnt; ++t) {
-            const int64_t i = base + t;
-            const double2 x01 = __ldg(rin + 4 * i), x23 = __ldg(rin + 4 * i + 1);
-            const double2 u01 = __ldg(rin + 4 * i + 2), u23 = __ldg(rin + 4 * i + 3);
-            const int32_t* __restrict__ row = a.nbr + i * W;
-            uint32_t* brow = a.bits + i * Q;
-            double fx = 0.0, fy = 0.0, fz = 0.0, ws = 0.0;
-
-            for (int q0 = 0; q0 < Q; q0 += 2) {
-                uint32_t w[2];
-                int32_t jj[2];
-                bool al[2];
-                double2 ra[2][4];
+        for (int q = 0; q * 32 < Wg; ++q) {
+            const uint32_t word = bw[q * 32];
+            uint32_t nword = word;
+            const int mend = min(32, Wg - q * 32);
+            for (int b0 = 0; b0 < mend; b0 += kUnroll) {
+                int32_t jj[kUnroll];
+                bool al[kUnroll];
+                double2 ra[kUnroll][4];
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const int q = q0 + c;
-                    al[c] = false;
-                    w[c] = 0u;
-                    jj[c] = 0;
-                    if (q < Q) {
-                        w[c] = brow[q];
-                        jj[c] = __ldg(row + q * 32 + lane);
-                        al[c] = (w[c] >> lane) & 1u;
-                    }
+                for (int u = 0; u < kUnroll; ++u) {
+                    const int b = b0 + u;
+                    al[u] = (b < mend) && ((word >> b) & 1u);
+                    jj[u] = al[u] ? __ldg(col + (int64_t)(q * 32 + b) * 32) : 0;
                 }
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    if (al[c]) {
+                for (int u = 0; u < kUnroll; ++u)
+                    if (al[u])
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) ra[c][e] = __ldg(rin + 4 * (int64_t)jj[c] + e);
-                    }
-                }
+                        for (int e = 0; e < 4; ++e) ra[u][e] = __ldg(rin + 4 * (int64_t)jj[u] + e);
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    if (al[c]) {
-                        const double ex = ra[c][0].x - x01.x, ey = ra[c][0].y - x01.y;
-                        const double ez = ra[c][1].x - x23.x;
-                        const double yx = ex + (ra[c][2].x - u01.x);
-                        const double yy = ey + (ra[c][2].y - u01.y);
-                        const double yz = ez + (ra[c][3].x - u23.x);
-                        const double L = sqrt(ex * ex + ey * ey + ez * ez);
-                        const double r = sqrt(yx * yx + yy * yy + yz * yz);
-                        const double s = (r - L) / L;
-                        const double sc = (SCM == 0)
-                                              ? a.sc
-                                              : sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i],
-                                                        a.gid[jj[c]]);
-                        bool brk = s >= sc;
-                        if (brk && a.has_nofail) brk = !pair_no_fail(a.bcc, a.bct, i, jj[c]);
-                        if (brk) {
-                            al[c] = false;
-                        } else {
-                            double wj = ra[c][1].y;
-                            if (cb != nullptr) wj *= __ldg(cb + i * W + (q0 + c) * 32 + lane);
-                            const double f = wj * s / r;
-                            fx += f * yx;
-                            fy += f * yy;
-                            fz += f * yz;
-                            ws += ra[c][1].y;
-                        }
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    if (q0 + c < Q) {
-                        const uint32_t nw = __ballot_sync(kFull, al[c]);
-                        if (lane == 0 && nw != w[c]) brow[q0 + c] = nw;
+                for (int u = 0; u < kUnroll; ++u) {
+                    if (!al[u]) continue;
+                    const double ex = ra[u][0].x - x01.x, ey = ra[u][0].y - x01.y;
+                    const double ez = ra[u][1].x - x23.x;
+                    const double yx = ex + (ra[u][2].x - u01.x);
+                    const double yy = ey + (ra[u][2].y - u01.y);
+                    const double yz = ez + (ra[u][3].x - u23.x);
+                    const double L = sqrt(ex * ex + ey * ey + ez * ez);
+                    const double r = sqrt(yx * yx + yy * yy + yz * yz);
+                    const double s = (r - L) / L;
+                    const double sc = (SCM == 0) ? a.sc
+                                                 : sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i],
+                                                           a.gid[jj[u]]);
+                    bool brk = s >= sc;
+                    if (brk && a.has_nofail) brk = !pair_no_fail(a.bcc, a.bct, i, jj[u]);
+                    if (brk) {
+                        nword &= ~(1u << (b0 + u));
+                    } else {
+                        double wj = ra[u][1].y;
+                        if (cb != nullptr) wj *= __ldg(cb + (g * W + q * 32 + b0 + u) * 32 + lane);
+                        const double f = wj * s / r;
+                        fx += f * yx;
+                        fy += f * yy;
+                        fz += f * yz;
+                        ws += ra[u][1].y;
                     }
                 }
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                fx += __shfl_xor_sync(kFull, fx, o);
-                fy += __shfl_xor_sync(kFull, fy, o);
-                fz += __shfl_xor_sync(kFull, fz, o);
-                ws += __shfl_xor_sync(kFull, ws, o);
-            }
-            if (lane == t) {
-                kx = fx;
-                ky = fy;
-                kz = fz;
-                kw = ws;
-            }
+            if (nword != word) bw[q * 32] = nword;
         }
 
-        if (lane < cnt) {
-            const int64_t i = base + lane;
+        if (i < a.n) {
             const uint32_t cls = a.bcc[i];
             uint32_t mask = 0u;
             double gdisp[3] = {0.0, 0.0, 0.0};
-            double F[3] = {kx, ky, kz};
+            double F[3] = {fx, fy, fz};
             if (cls != 0u) {
                 const BcClass& bc = a.bct[cls];
                 mask = bc.mask;
@@ -160,9 +130,7 @@ __global__ void __launch_bounds__(256) k_step_f64(const StepArgsF64 a)
             }
             const double s_now = a.disp_rate * (double)step;
             const double s_next = a.disp_rate * (double)(step + 1);
-            const double2 r01 = __ldg(rin + 4 * i), r23 = __ldg(rin + 4 * i + 1);
-            const double2 q01 = __ldg(rin + 4 * i + 2), q23 = __ldg(rin + 4 * i + 3);
-            const double uo[3] = {q01.x, q01.y, q23.x};
+            const double uo[3] = {u01.x, u01.y, u23.x};
             double un[3];
             bool finite = true;
 #pragma unroll
@@ -178,49 +146,31 @@ __global__ void __launch_bounds__(256) k_step_f64(const StepArgsF64 a)
                 un[c] = u;
                 a.v[3 * i + c] = vn;
             }
-            rout[4 * i] = r01;
-            rout[4 * i + 1] = r23;
+            rout[4 * i] = x01;
+            rout[4 * i + 1] = x23;
             rout[4 * i + 2] = make_double2(un[0], un[1]);
             rout[4 * i + 3] = make_double2(un[2], 0.0);
-            a.damage[i] = 1.0 - kw * a.wsum_inv[i];
+            const double wi = a.wsum_inv[i];
+            a.damage[i] = wi > 0.0 ? 1.0 - ws * wi : 0.0;
             if (!finite) atomicOr(a.err, PD_DEVERR_NONFINITE);
         }
     }
 }
 
-template <int QT>
-cudaError_t launch_q(const StepArgsF64& a, int sc_mode, int grid, int block, cudaStream_t s)
+}  // namespace
+
+cudaError_t launch_step_f64(const StepArgsF64& a, int sc_mode, int grid, int block, cudaStream_t s)
 {
     if (sc_mode == 0)
-        k_step_f64<QT, 0><<<grid, block, 0, s>>>(a);
+        k_step_f64<0><<<grid, block, 0, s>>>(a);
     else
-        k_step_f64<QT, 1><<<grid, block, 0, s>>>(a);
+        k_step_f64<1><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int QT>
-const void* kernel_ptr(int sc_mode)
+const void* step_f64_kernel(int sc_mode)
 {
-    return sc_mode == 0 ? (const void*)k_step_f64<QT, 0> : (const void*)k_step_f64<QT, 1>;
-}
-
-}  // namespace
-
-cudaError_t launch_step_f64(const StepArgsF64& a, int Q, int sc_mode, int grid, int block,
-                            cudaStream_t s)
-{
-    switch (Q) {
-        case 4: return launch_q<4>(a, sc_mode, grid, block, s);
-        default: return launch_q<0>(a, sc_mode, grid, block, s);
-    }
-}
-
-const void* step_f64_kernel(int Q, int sc_mode)
-{
-    switch (Q) {
-        case 4: return kernel_ptr<4>(sc_mode);
-        default: return kernel_ptr<0>(sc_mode);
-    }
+    return sc_mode == 0 ? (const void*)k_step_f64<0> : (const void*)k_step_f64<1>;
 }
 
 }  // namespace pd
