@@ -82,7 +82,7 @@ struct pd_handle {
     int64_t step = 0;
     int graph_steps = 0;
     cudaGraphExec_t graph = nullptr;
-    int grid = 0, block = 256;
+    int grid = 0, block = 256, blocks_per_sm = 0;
     bool damage_fresh = false;
 
     std::vector<int64_t> off;  // canonical family after cuts
@@ -91,8 +91,12 @@ struct pd_handle {
 
     std::vector<void*> allocs;
     int64_t device_bytes = 0;
-    // FP32 path: 3 float4 per node; FP64 path: 8 doubles per node
+    // FP32 path: 2 float4 per node (+ owner-private lo, weights); FP64: 8 doubles per node
     float4* rec32[2] = {nullptr, nullptr};
+    float4* lo32 = nullptr;
+    float* w32 = nullptr;
+    bool uniform_vol = false;
+    double vol0 = 0.0;
     double* rec[2] = {nullptr, nullptr};
     // both
     void* v = nullptr;
@@ -144,7 +148,7 @@ struct pd_handle {
 
     const void* wrec() const
     {
-        return precision == 32 ? (const void*)rec32[0] : (const void*)rec[0];
+        return precision == 32 ? (const void*)w32 : (const void*)rec[0];
     }
 };
 
@@ -155,6 +159,10 @@ StepArgsF32 args_f32(pd_handle* h, int k)
     StepArgsF32 a{};
     a.rec[0] = h->rec32[0];
     a.rec[1] = h->rec32[1];
+    a.lo32 = h->lo32;
+    a.w = h->w32;
+    a.uniform_w = h->uniform_vol ? 1 : 0;
+    a.w_const = (float)((h->per_bond_c ? 1.0 : h->c) * h->vol0);
     a.v = (float*)h->v;
     a.nbr = h->nbr;
     a.bits = h->bits;
@@ -234,7 +242,8 @@ pd_status choose_grid(pd_handle* h, int blocks_per_sm)
 {
     int sms = 0;
     PD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "sm count");
-    const void* fn = h->precision == 32 ? step_f32_kernel(h->sc_mode) : step_f64_kernel(h->sc_mode);
+    const void* fn = h->precision == 32 ? step_f32_kernel(h->sc_mode, h->uniform_vol, h->per_bond_c)
+                                        : step_f64_kernel(h->sc_mode);
     // no shared memory is used: give the unified L1/shared array to L1
     PD_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 0),
             "carveout");
@@ -251,8 +260,8 @@ pd_status choose_grid(pd_handle* h, int blocks_per_sm)
 pd_status upload_weights(pd_handle* h)
 {
     const double wscale = h->per_bond_c ? 1.0 : h->c;
-    void* w0 = h->precision == 32 ? (void*)h->rec32[0] : (void*)h->rec[0];
-    void* w1 = h->precision == 32 ? (void*)h->rec32[1] : (void*)h->rec[1];
+    void* w0 = h->precision == 32 ? (void*)h->w32 : (void*)h->rec[0];
+    void* w1 = h->precision == 32 ? nullptr : (void*)h->rec[1];
     PD_CUDA(launch_set_weights(h->precision, w0, w1, h->vol, h->nbr, h->bits0, h->sw, h->n, h->Q,
                                wscale, h->wsum_inv, h->stream),
             "set weights");
@@ -385,6 +394,9 @@ pd_status pd_create(int64_t n, const double* coords, const double* volumes, doub
     h->graph_steps = cfg->graph_steps;
     h->block = cfg->block_threads ? cfg->block_threads : 256;
     h->device = cfg->device;
+    h->vol0 = volumes[0];
+    h->uniform_vol = true;
+    for (int64_t i = 1; i < n && h->uniform_vol; ++i) h->uniform_vol = volumes[i] == volumes[0];
 
     if (cfg->check_dt) {
         const double dtc = stable_dt(n, coords, volumes, h->off, h->idx, h->c, h->rho);
@@ -420,8 +432,10 @@ pd_status pd_create(int64_t n, const double* coords, const double* volumes, doub
         if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc " #ptr)); \
     } while (0)
     if (f32) {
-        ALLOC(h->rec32[0], float4, 3 * np);
-        ALLOC(h->rec32[1], float4, 3 * np);
+        ALLOC(h->rec32[0], float4, 2 * np);
+        ALLOC(h->rec32[1], float4, 2 * np);
+        ALLOC(h->lo32, float4, np);
+        ALLOC(h->w32, float, np);
         ALLOC(h->v, float, 3 * np);
         ALLOC(h->wsum_inv, float, np);
         ALLOC(h->damage, float, np);
@@ -475,13 +489,13 @@ pd_status pd_create(int64_t n, const double* coords, const double* volumes, doub
     std::vector<float4> r32;
     std::vector<double> r64;
     if (f32) {
-        r32.assign(3 * np, make_float4(0.f, 0.f, 0.f, 0.f));
+        r32.assign(2 * np, make_float4(0.f, 0.f, 0.f, 0.f));
         for (int64_t p = 0; p < n; ++p)
-            r32[3 * p] = make_float4((float)((xs[3 * p] - ctr[0]) / horizon),
+            r32[2 * p] = make_float4((float)((xs[3 * p] - ctr[0]) / horizon),
                                      (float)((xs[3 * p + 1] - ctr[1]) / horizon),
                                      (float)((xs[3 * p + 2] - ctr[2]) / horizon), 0.0f);
-        if ((st = up(h->rec32[0], r32.data(), 48 * np, "upload records")) ||
-            (st = up(h->rec32[1], r32.data(), 48 * np, "upload records")))
+        if ((st = up(h->rec32[0], r32.data(), 32 * np, "upload records")) ||
+            (st = up(h->rec32[1], r32.data(), 32 * np, "upload records")))
             return bail(st);
     } else {
         r64.assign(8 * np, 0.0);
@@ -502,7 +516,8 @@ pd_status pd_create(int64_t n, const double* coords, const double* volumes, doub
         (st = up(h->vol, vs.data(), 8 * np, "upload volumes")))
         return bail(st);
     if ((st = upload_weights(h)) != PD_OK) return bail(st);
-    if ((st = choose_grid(h, cfg->blocks_per_sm)) != PD_OK) return bail(st);
+    h->blocks_per_sm = cfg->blocks_per_sm;
+    if ((st = choose_grid(h, h->blocks_per_sm)) != PD_OK) return bail(st);
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return bail(cuda_fail(e, "synchronize"));
     *out = h;
@@ -600,8 +615,8 @@ pd_status pd_get_state(pd_handle* h, double* u, double* v, int64_t* step)
         double* uo = w == 0 ? dst : nullptr;
         double* vo = w == 1 ? dst : nullptr;
         if (h->precision == 32)
-            PD_CUDA(launch_get_state_f32(h->rec32[cur], (const float*)h->v, h->gid, h->n,
-                                         h->delta, uo, vo, h->stream),
+            PD_CUDA(launch_get_state_f32(h->rec32[cur], h->lo32, (const float*)h->v, h->gid,
+                                         h->n, h->delta, uo, vo, h->stream),
                     "get state");
         else
             PD_CUDA(launch_get_state_f64(h->rec[cur], (const double*)h->v, h->gid, h->n, uo, vo,
@@ -642,7 +657,7 @@ pd_status pd_set_state(pd_handle* h, const double* u, const double* v, int64_t s
         const double* vi = w == 1 ? src : nullptr;
         if (h->precision == 32)
             PD_CUDA(launch_set_state_f32(ui, vi, h->gid, h->n, 1.0 / h->delta, h->rec32[cur],
-                                         (float*)h->v, h->stream),
+                                         h->lo32, (float*)h->v, h->stream),
                     "set state");
         else
             PD_CUDA(launch_set_state_f64(ui, vi, h->gid, h->n, h->rec[cur], (double*)h->v,
@@ -761,6 +776,10 @@ pd_status pd_set_params(pd_handle* h, double c, double sc, double load, double d
     h->load = load;
     h->disp_rate = disp_rate;
     h->drop_graph();
+    {  // the kernel variant depends on per-bond stiffness
+        pd_status st = choose_grid(h, h->blocks_per_sm);
+        if (st != PD_OK) return st;
+    }
     if (reweight) {
         pd_status st = upload_weights(h);
         if (st != PD_OK) return st;

@@ -1,6 +1,7 @@
 // Auxiliary kernels: step counter, state transfer between the caller's node
 // order and the library's node order, damage from the bond flags (Eq. 8),
 // and the per-node bond weights w = c V.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "pd_internal.h"
@@ -17,19 +18,19 @@ __global__ void k_advance(int64_t* ctr, int64_t k)
     for (int64_t var = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; var < (count); \
          var += (int64_t)gridDim.x * blockDim.x)
 
-__global__ void k_get_state_f32(const float4* __restrict__ rec, const float* __restrict__ v32,
-                                const int32_t* __restrict__ gid, int64_t n, double delta,
-                                double* __restrict__ u_out, double* __restrict__ v_out)
+__global__ void k_get_state_f32(const float4* __restrict__ rec, const float4* __restrict__ lo32,
+                                const float* __restrict__ v32, const int32_t* __restrict__ gid,
+                                int64_t n, double delta, double* __restrict__ u_out,
+                                double* __restrict__ v_out)
 {
     GRID_STRIDE(p, n)
     {
         const int64_t g = gid[p];
         if (u_out) {
-            const float4 h = rec[3 * p + 1];
-            const float4 l = rec[3 * p + 2];
-            u_out[3 * g] = ((double)h.x + (double)h.w) * delta;
-            u_out[3 * g + 1] = ((double)h.y + (double)l.x) * delta;
-            u_out[3 * g + 2] = ((double)h.z + (double)l.y) * delta;
+            const float4 a = rec[2 * p], b = rec[2 * p + 1], l = lo32[p];
+            u_out[3 * g] = ((double)a.w + (double)l.x) * delta;
+            u_out[3 * g + 1] = ((double)b.x + (double)l.y) * delta;
+            u_out[3 * g + 2] = ((double)b.y + (double)l.z) * delta;
         }
         if (v_out)
             for (int c = 0; c < 3; ++c) v_out[3 * g + c] = (double)v32[3 * p + c];
@@ -42,9 +43,16 @@ __device__ __forceinline__ void split(double x, float& h, float& l)
     l = (float)(x - (double)h);
 }
 
+__device__ __forceinline__ float bf16_pair(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return __uint_as_float(*reinterpret_cast<const uint32_t*>(&v));
+}
+
 __global__ void k_set_state_f32(const double* __restrict__ u_in, const double* __restrict__ v_in,
                                 const int32_t* __restrict__ gid, int64_t n, double inv_delta,
-                                float4* __restrict__ rec, float* __restrict__ v32)
+                                float4* __restrict__ rec, float4* __restrict__ lo32,
+                                float* __restrict__ v32)
 {
     GRID_STRIDE(p, n)
     {
@@ -52,8 +60,11 @@ __global__ void k_set_state_f32(const double* __restrict__ u_in, const double* _
         if (u_in) {
             float h[3], l[3];
             for (int c = 0; c < 3; ++c) split(u_in[3 * g + c] * inv_delta, h[c], l[c]);
-            rec[3 * p + 1] = make_float4(h[0], h[1], h[2], l[0]);
-            rec[3 * p + 2] = make_float4(l[1], l[2], 0.0f, 0.0f);
+            float4 a = rec[2 * p];
+            a.w = h[0];
+            rec[2 * p] = a;
+            rec[2 * p + 1] = make_float4(h[1], h[2], bf16_pair(l[0], l[1]), bf16_pair(l[2], 0.0f));
+            lo32[p] = make_float4(l[0], l[1], l[2], 0.0f);
         }
         if (v_in)
             for (int c = 0; c < 3; ++c) v32[3 * p + c] = (float)v_in[3 * g + c];
@@ -93,7 +104,7 @@ __device__ __forceinline__ T node_w(const void* wrec, int64_t p);
 template <>
 __device__ __forceinline__ float node_w<float>(const void* wrec, int64_t p)
 {
-    return reinterpret_cast<const float4*>(wrec)[3 * p].w;
+    return reinterpret_cast<const float*>(wrec)[p];
 }
 template <>
 __device__ __forceinline__ double node_w<double>(const void* wrec, int64_t p)
@@ -131,7 +142,8 @@ __global__ void k_damage(const void* __restrict__ wrec, const int32_t* __restric
         const int lane = (int)(p & 31);
         const T acc = masked_wsum<T>(wrec, nbr, bits, g, lane, sw[g], Q);
         // a node without family has no damage (the integral ratio of Eq. 8 is 0/0)
-        if (p < n) phi[gid[p]] = wsum_inv[p] > 0 ? (double)((T)1 - acc * wsum_inv[p]) : 0.0;
+        if (p < n)
+            phi[gid[p]] = wsum_inv[p] > 0 ? (double)fmax((T)0, (T)1 - acc * wsum_inv[p]) : 0.0;
     }
 }
 
@@ -149,8 +161,7 @@ __global__ void k_set_w(void* wrec0, void* wrec1, const double* __restrict__ vol
     GRID_STRIDE(p, n)
     {
         if (sizeof(T) == 4) {
-            reinterpret_cast<float4*>(wrec0)[3 * p].w = (float)(wscale * vol[p]);
-            reinterpret_cast<float4*>(wrec1)[3 * p].w = (float)(wscale * vol[p]);
+            reinterpret_cast<float*>(wrec0)[p] = (float)(wscale * vol[p]);
         } else {
             reinterpret_cast<double*>(wrec0)[8 * p + 3] = wscale * vol[p];
             reinterpret_cast<double*>(wrec1)[8 * p + 3] = wscale * vol[p];
@@ -188,19 +199,21 @@ cudaError_t launch_advance(int64_t* step_ctr, int64_t k, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_get_state_f32(const float4* rec, const float* v32, const int32_t* gid,
-                                 int64_t n, double delta, double* u_out, double* v_out,
-                                 cudaStream_t s)
+cudaError_t launch_get_state_f32(const float4* rec, const float4* lo32, const float* v32,
+                                 const int32_t* gid, int64_t n, double delta, double* u_out,
+                                 double* v_out, cudaStream_t s)
 {
-    k_get_state_f32<<<grid_for(n, 256), 256, 0, s>>>(rec, v32, gid, n, delta, u_out, v_out);
+    k_get_state_f32<<<grid_for(n, 256), 256, 0, s>>>(rec, lo32, v32, gid, n, delta, u_out,
+                                                     v_out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_set_state_f32(const double* u_in, const double* v_in, const int32_t* gid,
-                                 int64_t n, double inv_delta, float4* rec, float* v32,
-                                 cudaStream_t s)
+                                 int64_t n, double inv_delta, float4* rec, float4* lo32,
+                                 float* v32, cudaStream_t s)
 {
-    k_set_state_f32<<<grid_for(n, 256), 256, 0, s>>>(u_in, v_in, gid, n, inv_delta, rec, v32);
+    k_set_state_f32<<<grid_for(n, 256), 256, 0, s>>>(u_in, v_in, gid, n, inv_delta, rec, lo32,
+                                                     v32);
     return cudaGetLastError();
 }
 

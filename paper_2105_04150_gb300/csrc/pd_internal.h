@@ -19,11 +19,12 @@
 //   step_ctr  int64 device step counter (read by every step kernel)
 //   err       int32 device error bits (PD_DEVERR_*)
 // FP32-bulk path (all lengths in units of the horizon, positions centred):
-//   rec[2] 48-byte node records, 3 float4 per node, double buffered:
-//          {x~, y~, z~, w}  reference position; w = c V (constant c) or V
-//          {hx, hy, hz, lx} {ly, lz, 0, 0}: the displacement as an unevaluated
-//          float-float sum u~ = h + l (48-bit significand); it is both the
-//          integrator's state and what neighbours gather
+//   rec[2] 32-byte node records (one sector), double buffered:
+//          {x~, y~, z~, hx | hy, hz, bf16(lx, ly), bf16(lz, 0)}: reference position
+//          and the displacement u~ = h + l as published to neighbours
+//   lo32   float4 {lx, ly, lz, 0}: the owner's full-precision l (the float-float
+//          pair h + l has a 48-bit significand and is the integrator's state)
+//   w      float per node: c V (constant c) or V (per-bond c)
 //   v      float velocity, 3 per node, updated in place by its owner
 // FP64 path:
 //   rec[2] 8 doubles per node {x, y, z, w, ux, uy, uz, 0}, double buffered
@@ -45,7 +46,11 @@ struct BcClass {
 };
 
 struct StepArgsF32 {
-    const float4* rec[2];
+    const float4* rec[2];      // 2 float4 (32 B) per node
+    float4* lo32;              // owner-private full-precision l, 1 float4 per node
+    const float* w;            // per-node weight w = c V (or V with per-bond c)
+    float w_const;             // the common weight when uniform_w
+    int32_t uniform_w;         // all w equal: w_const is used, damage by bit counts
     float* v;
     const int32_t* nbr;
     uint32_t* bits;
@@ -102,18 +107,18 @@ cudaError_t launch_step_f32(const StepArgsF32& a, int sc_mode, int grid, int blo
                             cudaStream_t s);
 cudaError_t launch_step_f64(const StepArgsF64& a, int sc_mode, int grid, int block,
                             cudaStream_t s);
-const void* step_f32_kernel(int sc_mode);
+const void* step_f32_kernel(int sc_mode, bool uniform_w, bool per_bond_c);
 const void* step_f64_kernel(int sc_mode);
 
 // ---- helper kernels (pd_aux.cu) ---------------------------------------------
 cudaError_t launch_advance(int64_t* step_ctr, int64_t k, cudaStream_t s);
 // caller-order FP64 (u, v) <-> internal state; u_out/v_out/u_in/v_in may be null
-cudaError_t launch_get_state_f32(const float4* rec, const float* v32, const int32_t* gid,
-                                 int64_t n, double delta, double* u_out, double* v_out,
-                                 cudaStream_t s);
+cudaError_t launch_get_state_f32(const float4* rec, const float4* lo32, const float* v32,
+                                 const int32_t* gid, int64_t n, double delta, double* u_out,
+                                 double* v_out, cudaStream_t s);
 cudaError_t launch_set_state_f32(const double* u_in, const double* v_in, const int32_t* gid,
-                                 int64_t n, double inv_delta, float4* rec, float* v32,
-                                 cudaStream_t s);
+                                 int64_t n, double inv_delta, float4* rec, float4* lo32,
+                                 float* v32, cudaStream_t s);
 cudaError_t launch_get_state_f64(const double* rec64, const double* v64, const int32_t* gid,
                                  int64_t n, double* u_out, double* v_out, cudaStream_t s);
 cudaError_t launch_set_state_f64(const double* u_in, const double* v_in, const int32_t* gid,
@@ -125,8 +130,8 @@ cudaError_t launch_damage(int precision, const void* wrec, const int32_t* nbr,
 // damage written by the last step -> caller order
 cudaError_t launch_gather_damage(int precision, const void* dmg, const int32_t* gid, int64_t n,
                                  double* phi_out, cudaStream_t s);
-// node weights w = wscale * V in both record buffers, and wsum_inv
-// (a slot is a real family member iff its bit in init_bits is set)
+// node weights w = wscale * V (FP32: the w array, passed as wrec0; FP64: both
+// record buffers) and wsum_inv (a slot is a real member iff its init_bits bit is set)
 cudaError_t launch_set_weights(int precision, void* wrec0, void* wrec1, const double* vol,
                                const int32_t* nbr, const uint32_t* init_bits, const int32_t* sw,
                                int64_t n, int Q, double wscale, void* wsum_inv, cudaStream_t s);

@@ -5,8 +5,8 @@
 // (Eq. 10), body force, damped Euler-Cromer update (Eq. 11), displacement
 // BCs and damage (Eq. 8).  The paper splits this into a bond kernel and an
 // integrator kernel because an in-place update would race with neighbours
-// still reading u^n (Section 3.3); here the displacement that neighbours read
-// is double-buffered (step k reads buffer k&1, writes (k+1)&1), so the whole
+// still reading u^n (Section 3.3); here the node records that neighbours read
+// are double-buffered (step k reads buffer k&1, writes (k+1)&1), so the whole
 // step is one kernel and every node's data crosses HBM once per step.
 //
 // Work decomposition ("lane per node" over a sliced ELL): a warp owns a slice
@@ -20,17 +20,23 @@
 // padding bounded per slice instead of per power of two).  The slice's
 // neighbour-id block is requested from HBM with one bulk L2 prefetch when the
 // warp starts it, so the stream does not wait for the warp's own loads.
-// Each node's gather data is one 48-byte record {x~, w | h | l}.
 //
-// Precision: bond arithmetic is FP32 in units of the horizon with the
-// cancellation-free stretch s = eta.(2 xi + eta) / (|xi| (|xi| + |xi+eta|)).
-// The displacement is an unevaluated float-float sum h + l (48-bit
-// significand): it is accumulated exactly enough by two-sum updates and gives
-// eta = (h_j - h_i) + (l_j - l_i) to FP32 relative accuracy even when |u| is
-// far larger than |eta|.  The arithmetic is exactly antisymmetric (bond j->i
-// sees -xi, -eta and produces the same bits), so both directions of a bond
-// break together.  A bond whose FP32 stretch lies within a relative band of
-// s_c is re-tested with the literal FP64 stretch of Eq. 4.
+// Node record: 32 bytes, one L1/L2 sector, read with one 256-bit load:
+//   {x~, y~, z~, h_x | h_y, h_z, bf16(l_x, l_y), bf16(l_z, 0)}
+// (lengths in units of the horizon, positions centred).  The displacement is
+// an unevaluated float-float sum u/delta = h + l: the owner keeps l in full
+// FP32 (private array, exact two-sum updates, 48-bit significand) and
+// publishes it rounded to bf16 in the record; eta = (h_j - h_i) + (l_j - l_i)
+// is then accurate to ~2^-33 |u/delta|, i.e. to FP32 relative accuracy of eta
+// even when |u| is far larger than |eta|.
+//
+// Precision: bond arithmetic is FP32 with the cancellation-free stretch
+// s = eta.(2 xi + eta) / (|xi| (|xi| + |xi+eta|)).  Both directions of a bond
+// read the same records and the arithmetic is exactly antisymmetric (j->i sees
+// -xi, -eta and produces the same bits), so both break together.  A bond whose
+// FP32 stretch is within a relative band of s_c is re-tested with the literal
+// FP64 stretch of Eq. 4.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "pd_internal.h"
@@ -42,7 +48,7 @@ namespace {
 #define PD_F32_UNROLL 4
 #endif
 #ifndef PD_F32_MIN_BLOCKS
-#define PD_F32_MIN_BLOCKS 3
+#define PD_F32_MIN_BLOCKS 2
 #endif
 constexpr int kUnroll = PD_F32_UNROLL;  // family slots in flight per lane
 
@@ -70,6 +76,43 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// One 32-byte record with a single 256-bit non-coherent load.
+__device__ __forceinline__ void ld_rec(const float4* p, float4& a, float4& b)
+{
+    asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z),
+                   "=f"(b.w)
+                 : "l"(p));
+}
+
+__device__ __forceinline__ void st_rec(float4* p, const float4& a, const float4& b)
+{
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(a.x),
+                 "f"(a.y), "f"(a.z), "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ float ld_f32(const float* p)
+{
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ float bf_lo(float packed)
+{
+    return __uint_as_float(__float_as_uint(packed) << 16);
+}
+__device__ __forceinline__ float bf_hi(float packed)
+{
+    return __uint_as_float(__float_as_uint(packed) & 0xffff0000u);
+}
+__device__ __forceinline__ float bf_pack(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return __uint_as_float(*reinterpret_cast<const uint32_t*>(&v));
+}
+
 // (s, e) = exact sum of a and b (Knuth's two-sum).
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 {
@@ -94,20 +137,39 @@ __device__ __forceinline__ void ff_set(double x, float& h, float& l)
     l = (float)(x - (double)h);
 }
 
+// A node as seen by its neighbours: position and published displacement.
+struct NodeF32 {
+    float x, y, z, hx, hy, hz, lx, ly, lz;
+};
+
+__device__ __forceinline__ NodeF32 unpack(const float4 a, const float4 b)
+{
+    NodeF32 r;
+    r.x = a.x;
+    r.y = a.y;
+    r.z = a.z;
+    r.hx = a.w;
+    r.hy = b.x;
+    r.hz = b.y;
+    r.lx = bf_lo(b.z);
+    r.ly = bf_hi(b.z);
+    r.lz = bf_lo(b.w);
+    return r;
+}
+
 // FP32 bond kinematics in horizon units: y = xi + eta, num = eta.(2 xi + eta)
 // = |y|^2 - |xi|^2 (no cancellation), den = |xi| (|xi| + |y|), so s = num / den.
 struct BondF32 {
     float yx, yy, yz, num, den, y2;
 };
 
-__device__ __forceinline__ BondF32 bond_f32(const float4 xi, const float4 hi, const float2 li,
-                                            const float4 xj, const float4 hj, const float2 lj)
+__device__ __forceinline__ BondF32 bond_f32(const NodeF32& i, const NodeF32& j)
 {
     BondF32 r;
-    const float ex = xj.x - xi.x, ey = xj.y - xi.y, ez = xj.z - xi.z;
-    const float hx = (hj.x - hi.x) + (hj.w - hi.w);
-    const float hy = (hj.y - hi.y) + (lj.x - li.x);
-    const float hz = (hj.z - hi.z) + (lj.y - li.y);
+    const float ex = j.x - i.x, ey = j.y - i.y, ez = j.z - i.z;
+    const float hx = (j.hx - i.hx) + (j.lx - i.lx);
+    const float hy = (j.hy - i.hy) + (j.ly - i.ly);
+    const float hz = (j.hz - i.hz) + (j.lz - i.lz);
     r.yx = ex + hx;
     r.yy = ey + hy;
     r.yz = ez + hz;
@@ -125,20 +187,28 @@ __device__ __forceinline__ float bond_coef(const BondF32& b, float w)
     return w * b.num * rsqrtf(b.den * b.den * b.y2);
 }
 
+template <bool UW>
+__device__ __forceinline__ float node_w(const StepArgsF32& a, int64_t j)
+{
+    return UW ? a.w_const : __ldg(a.w + j);
+}
+
 // A bond whose FP32 stretch reached the band just below the smallest s_c: the
 // break test is decided in FP32 when s is clearly away from the bond's s_c and
-// otherwise with the literal FP64 stretch of Eq. 4 (FP64 positions, float-float
-// displacement); the no-fail rule applies last.  Returns the bond's force
-// contribution {fx, fy, fz, w}, all zero when it breaks (*broken = true).
-template <int SCM>
+// otherwise with the literal FP64 stretch of Eq. 4 (FP64 positions, published
+// float-float displacement, read identically by both directions); the no-fail
+// rule applies last.  Returns the bond's force contribution {fx, fy, fz, w},
+// all zero when it breaks (*broken = true).
+template <int SCM, bool UW>
 __device__ __noinline__ float4 resolve_bond(const StepArgsF32& a, int cur, int64_t i, int64_t j,
                                             int64_t slot, bool* broken)
 {
     const float4* __restrict__ R = a.rec[cur];
-    const float4 xi = R[3 * i], hi = R[3 * i + 1], xj = R[3 * j], hj = R[3 * j + 1];
-    const float2 li = *reinterpret_cast<const float2*>(R + 3 * i + 2);
-    const float2 lj = *reinterpret_cast<const float2*>(R + 3 * j + 2);
-    const BondF32 b = bond_f32(xi, hi, li, xj, hj, lj);
+    float4 ai, bi, aj, bj;
+    ld_rec(R + 2 * i, ai, bi);
+    ld_rec(R + 2 * j, aj, bj);
+    const NodeF32 ni = unpack(ai, bi), nj = unpack(aj, bj);
+    const BondF32 b = bond_f32(ni, nj);
     double sc = a.sc;
     float scf = a.sc_f;
     if (SCM == 1) {
@@ -150,10 +220,10 @@ __device__ __noinline__ float4 resolve_bond(const StepArgsF32& a, int cur, int64
     if (fabsf(r) > a.guard * scf * b.den) {
         brk = r >= 0.0f;
     } else {
-        const double ui[3] = {(double)hi.x + (double)hi.w, (double)hi.y + (double)li.x,
-                              (double)hi.z + (double)li.y};
-        const double uj[3] = {(double)hj.x + (double)hj.w, (double)hj.y + (double)lj.x,
-                              (double)hj.z + (double)lj.y};
+        const double ui[3] = {(double)ni.hx + (double)ni.lx, (double)ni.hy + (double)ni.ly,
+                              (double)ni.hz + (double)ni.lz};
+        const double uj[3] = {(double)nj.hx + (double)nj.lx, (double)nj.hy + (double)nj.ly,
+                              (double)nj.hz + (double)nj.lz};
         double xv[3], y[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -167,14 +237,16 @@ __device__ __noinline__ float4 resolve_bond(const StepArgsF32& a, int cur, int64
     if (brk && a.has_nofail) brk = ((a.bct[a.bcc[i]].mask | a.bct[a.bcc[j]].mask) & 8u) == 0u;
     *broken = brk;
     if (brk) return make_float4(0.f, 0.f, 0.f, 0.f);
-    float w = xj.w;
+    const float wv = node_w<UW>(a, j);
+    float w = wv;
     if (a.cbond != nullptr) w *= a.cbond[slot];
     const float coef = bond_coef(b, w);
-    return make_float4(coef * b.yx, coef * b.yy, coef * b.yz, xj.w);
+    return make_float4(coef * b.yx, coef * b.yy, coef * b.yz, wv);
 }
 
-template <int SCM>
-__global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS) k_step_f32(const __grid_constant__ StepArgsF32 a)
+template <int SCM, bool UW>
+__global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS)
+    k_step_f32(const __grid_constant__ StepArgsF32 a)
 {
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -194,68 +266,84 @@ __global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS) k_step_f32(const __gri
         const int32_t* __restrict__ col = a.nbr + g * W * 32 + lane;
         if (lane == 0) prefetch_l2(col, (uint32_t)(((Wg + 3) & ~3) * 128));
         const int64_t i = (g << 5) + lane;
-        const float4 xi = __ldg(R + 3 * i);
-        const float4 hi = __ldg(R + 3 * i + 1);
-        const float2 li = __ldg(reinterpret_cast<const float2*>(R + 3 * i + 2));
+        float4 ai, bi;
+        ld_rec(R + 2 * i, ai, bi);
+        const NodeF32 ni = unpack(ai, bi);
         uint32_t* bw = a.bits + g * Q * 32 + lane;
         float fx = 0.f, fy = 0.f, fz = 0.f, ws = 0.f;
+        int alive_count = 0;
 
-        for (int q = 0; q * 32 < Wg; ++q) {
-            const uint32_t word = bw[q * 32];
-            uint32_t nword = word;
-            uint32_t pend = 0u;  // members in the near-s_c band, resolved below
-            const int mend = min(32, Wg - q * 32);
-            const int32_t* __restrict__ cq = col + (int64_t)q * 32 * 32;
-            for (int b0 = 0; b0 < mend; b0 += kUnroll) {
-                // every slot is evaluated; slots that are broken or unused (their
-                // id is the node itself) are masked out with selects, so the warp
-                // never diverges in this loop
-                int32_t jj[kUnroll];
-                float4 xa[kUnroll], ha[kUnroll];
-                float2 la[kUnroll];
+        // Slots are visited in chunks of kUnroll; the neighbour ids of the next
+        // chunk are loaded while the current chunk's records are gathered and
+        // evaluated, so the id stream's latency overlaps the arithmetic.  Every
+        // slot is evaluated; slots of broken bonds or beyond a lane's family (id =
+        // the node itself) are masked with selects, so the warp never diverges.
+        const int nch = (Wg + kUnroll - 1) / kUnroll;
+        int32_t jn[kUnroll];
 #pragma unroll
-                for (int u = 0; u < kUnroll; ++u) jj[u] = __ldg(cq + (b0 + u) * 32);
-#pragma unroll
-                for (int u = 0; u < kUnroll; ++u) {
-                    const float4* rj = R + 3 * (int64_t)jj[u];
-                    xa[u] = __ldg(rj);
-                    ha[u] = __ldg(rj + 1);
-                    la[u] = __ldg(reinterpret_cast<const float2*>(rj + 2));
-                }
-#pragma unroll
-                for (int u = 0; u < kUnroll; ++u) {
-                    const bool alive = (word >> (b0 + u)) & 1u;
-                    const BondF32 bd = bond_f32(xi, hi, li, xa[u], ha[u], la[u]);
-                    const bool cand = alive && (bd.num >= fast_lo * bd.den);
-                    const bool take = alive && !cand;
-                    pend |= cand ? (1u << (b0 + u)) : 0u;
-                    float wj = xa[u].w;
-                    if (cb != nullptr) wj *= __ldg(cb + (g * W + q * 32 + b0 + u) * 32 + lane);
-                    float coef = bond_coef(bd, wj);
-                    coef = take ? coef : 0.0f;
-                    fx = fmaf(coef, bd.yx, fx);
-                    fy = fmaf(coef, bd.yy, fy);
-                    fz = fmaf(coef, bd.yz, fz);
-                    ws += take ? xa[u].w : 0.0f;
-                }
+        for (int u = 0; u < kUnroll; ++u) jn[u] = __ldg(col + u * 32);
+        uint32_t word = 0u, nword = 0u, pend = 0u;
+        for (int c = 0; c < nch; ++c) {
+            const int m0 = c * kUnroll;
+            const int q = m0 >> 5, b0 = m0 & 31;
+            if (b0 == 0) {
+                word = bw[q * 32];
+                nword = word;
+                pend = 0u;  // members in the near-s_c band, resolved at the word's end
             }
-            while (pend) {
-                const int b = __ffs(pend) - 1;
-                pend &= pend - 1u;
-                const int64_t slot = (g * W + q * 32 + b) * 32 + lane;
-                bool broken;
-                const float4 f = resolve_bond<SCM>(a, cur, i, cq[b * 32], slot, &broken);
-                if (broken) {
-                    nword &= ~(1u << b);
-                } else {
-                    fx += f.x;
-                    fy += f.y;
-                    fz += f.z;
-                    ws += f.w;
-                }
+            int32_t jj[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) jj[u] = jn[u];
+            if (c + 1 < nch) {
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) jn[u] = __ldg(col + (m0 + kUnroll + u) * 32);
             }
-            if (nword != word) bw[q * 32] = nword;
+            float4 ra[kUnroll], rb[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) ld_rec(R + 2 * (int64_t)jj[u], ra[u], rb[u]);
+            const uint32_t wb = word >> b0;
+            uint32_t pc = 0u;
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const bool alive = (wb >> u) & 1u;
+                const NodeF32 nj = unpack(ra[u], rb[u]);
+                const BondF32 bd = bond_f32(ni, nj);
+                const bool cand = alive && (bd.num >= fast_lo * bd.den);
+                const bool take = alive && !cand;
+                pc |= cand ? (1u << u) : 0u;
+                float wj = node_w<UW>(a, jj[u]);
+                const float wv = wj;
+                if (cb != nullptr) wj *= ld_f32(cb + (g * W + m0 + u) * 32 + lane);
+                float coef = bond_coef(bd, wj);
+                coef = take ? coef : 0.0f;
+                fx = fmaf(coef, bd.yx, fx);
+                fy = fmaf(coef, bd.yy, fy);
+                fz = fmaf(coef, bd.yz, fz);
+                if (!UW) ws += take ? wv : 0.0f;
+            }
+            pend |= pc << b0;
+            if (b0 + kUnroll == 32 || c + 1 == nch) {  // end of bond-flag word q
+                while (pend) {
+                    const int b = __ffs(pend) - 1;
+                    pend &= pend - 1u;
+                    const int64_t slot = (g * W + q * 32 + b) * 32 + lane;
+                    bool broken;
+                    const float4 f = resolve_bond<SCM, UW>(a, cur, i, col[(int64_t)(q * 32 + b) * 32],
+                                                           slot, &broken);
+                    if (broken) {
+                        nword &= ~(1u << b);
+                    } else {
+                        fx += f.x;
+                        fy += f.y;
+                        fz += f.z;
+                        if (!UW) ws += f.w;
+                    }
+                }
+                if (nword != word) bw[q * 32] = nword;
+                alive_count += __popc(nword);
+            }
         }
+        if (UW) ws = a.w_const * (float)alive_count;
 
         // ---- integration of the lane's node (Eq. 11, damped Euler-Cromer)
         if (i < a.n) {
@@ -271,8 +359,9 @@ __global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS) k_step_f32(const __gri
             }
             const float dtf = (float)a.dt, etaf = (float)a.eta, rhof = (float)a.rho;
             const float dtd = (float)(a.dt * a.inv_delta);
-            float H[3] = {hi.x, hi.y, hi.z};
-            float L[3] = {hi.w, li.x, li.y};
+            const float4 lo = a.lo32[i];
+            float H[3] = {ni.hx, ni.hy, ni.hz};
+            float L[3] = {lo.x, lo.y, lo.z};
             bool finite = true;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -288,30 +377,39 @@ __global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS) k_step_f32(const __gri
                 finite = finite && isfinite(H[c]);
                 a.v[3 * i + c] = vn;
             }
-            Rout[3 * i] = xi;
-            Rout[3 * i + 1] = make_float4(H[0], H[1], H[2], L[0]);
-            Rout[3 * i + 2] = make_float4(L[1], L[2], 0.0f, 0.0f);
+            st_rec(Rout + 2 * i, make_float4(ni.x, ni.y, ni.z, H[0]),
+                   make_float4(H[1], H[2], bf_pack(L[0], L[1]), bf_pack(L[2], 0.0f)));
+            a.lo32[i] = make_float4(L[0], L[1], L[2], 0.0f);
             const float wi = a.wsum_inv[i];
-            a.damage[i] = wi > 0.0f ? 1.0f - ws * wi : 0.0f;
+            // clamp: ws * (1 / sum w) can round to 1 + 1 ulp for an intact family
+            a.damage[i] = wi > 0.0f ? fmaxf(0.0f, 1.0f - ws * wi) : 0.0f;
             if (!finite) atomicOr(a.err, PD_DEVERR_NONFINITE);
         }
     }
 }
 
+template <int SCM, bool UW>
+cudaError_t launch_v(const StepArgsF32& a, int grid, int block, cudaStream_t s)
+{
+    k_step_f32<SCM, UW><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+// per_bond_c selects no separate variant (it is a uniform run-time branch)
+const void* step_f32_kernel(int sc_mode, bool uniform_w, bool /*per_bond_c*/)
+{
+    if (sc_mode == 0)
+        return uniform_w ? (const void*)k_step_f32<0, true> : (const void*)k_step_f32<0, false>;
+    return uniform_w ? (const void*)k_step_f32<1, true> : (const void*)k_step_f32<1, false>;
+}
 
 cudaError_t launch_step_f32(const StepArgsF32& a, int sc_mode, int grid, int block, cudaStream_t s)
 {
     if (sc_mode == 0)
-        k_step_f32<0><<<grid, block, 0, s>>>(a);
-    else
-        k_step_f32<1><<<grid, block, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-const void* step_f32_kernel(int sc_mode)
-{
-    return sc_mode == 0 ? (const void*)k_step_f32<0> : (const void*)k_step_f32<1>;
+        return a.uniform_w ? launch_v<0, true>(a, grid, block, s) : launch_v<0, false>(a, grid, block, s);
+    return a.uniform_w ? launch_v<1, true>(a, grid, block, s) : launch_v<1, false>(a, grid, block, s);
 }
 
 }  // namespace pd

@@ -151,7 +151,8 @@ __global__ void __launch_bounds__(256) k_step_f64(const StepArgsF64 a)
             rout[4 * i + 2] = make_double2(un[0], un[1]);
             rout[4 * i + 3] = make_double2(un[2], 0.0);
             const double wi = a.wsum_inv[i];
-            a.damage[i] = wi > 0.0 ? 1.0 - ws * wi : 0.0;
+            // clamp: ws * (1 / sum w) can round to 1 + 1 ulp for an intact family
+            a.damage[i] = wi > 0.0 ? fmax(0.0, 1.0 - ws * wi) : 0.0;
             if (!finite) atomicOr(a.err, PD_DEVERR_NONFINITE);
         }
     }

@@ -261,8 +261,8 @@ def test_fused_damage_equals_recomputed_damage(beam):
         again = m.damage()
         if prec == F64:
             assert np.array_equal(fused, again)
-        else:  # near-s_c bonds are summed after the others in the fused kernel
-            assert np.abs(fused - again).max() <= 1e-6
+        else:  # FP32 sums of ~120 weights in different orders / as count * w
+            assert np.abs(fused - again).max() <= 1e-5
         assert np.all(fused >= 0) and np.all(fused <= 1) and fused.max() > 0
         m.close()
 
