@@ -63,7 +63,8 @@ __global__ void k_set_state_f32(const double* __restrict__ u_in, const double* _
             float4 a = rec[2 * p];
             a.w = h[0];
             rec[2 * p] = a;
-            rec[2 * p + 1] = make_float4(h[1], h[2], bf16_pair(l[0], l[1]), bf16_pair(l[2], 0.0f));
+            // same packing as the step kernel: {bf16(l_x) | bf16(l_y)}, {bf16(l_z) | 0}
+            rec[2 * p + 1] = make_float4(h[1], h[2], bf16_pair(l[1], l[0]), bf16_pair(0.0f, l[2]));
             lo32[p] = make_float4(l[0], l[1], l[2], 0.0f);
         }
         if (v_in)

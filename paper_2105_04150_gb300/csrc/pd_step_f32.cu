@@ -151,9 +151,12 @@ __device__ __forceinline__ NodeF32 unpack(const float4 a, const float4 b)
     r.hx = a.w;
     r.hy = b.x;
     r.hz = b.y;
-    r.lx = bf_lo(b.z);
-    r.ly = bf_hi(b.z);
-    r.lz = bf_lo(b.w);
+    // b.z = {bf16(l_x) high half, bf16(l_y) low half}: read as a float it is
+    // l_x up to a relative 2^-7 of l_x itself (< 2^-31 |h|), so only l_y needs
+    // a shift; b.w = {bf16(l_z), 0} is l_z exactly.
+    r.lx = b.z;
+    r.ly = bf_lo(b.z);
+    r.lz = b.w;
     return r;
 }
 
@@ -308,20 +311,22 @@ __global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS)
                 const bool alive = (wb >> u) & 1u;
                 const NodeF32 nj = unpack(ra[u], rb[u]);
                 const BondF32 bd = bond_f32(ni, nj);
-                const bool cand = alive && (bd.num >= fast_lo * bd.den);
-                const bool take = alive && !cand;
+                // near-s_c candidates; unused/broken slots are dropped from the
+                // pending set once per chunk (pc & wb below)
+                const bool cand = bd.num >= fast_lo * bd.den;
                 pc |= cand ? (1u << u) : 0u;
                 float wj = node_w<UW>(a, jj[u]);
                 const float wv = wj;
                 if (cb != nullptr) wj *= ld_f32(cb + (g * W + m0 + u) * 32 + lane);
                 float coef = bond_coef(bd, wj);
-                coef = take ? coef : 0.0f;
+                coef = cand ? 0.0f : coef;
+                coef = alive ? coef : 0.0f;
                 fx = fmaf(coef, bd.yx, fx);
                 fy = fmaf(coef, bd.yy, fy);
                 fz = fmaf(coef, bd.yz, fz);
-                if (!UW) ws += take ? wv : 0.0f;
+                if (!UW) ws += (alive && !cand) ? wv : 0.0f;
             }
-            pend |= pc << b0;
+            pend |= (pc & wb) << b0;
             if (b0 + kUnroll == 32 || c + 1 == nch) {  // end of bond-flag word q
                 while (pend) {
                     const int b = __ffs(pend) - 1;
@@ -378,7 +383,7 @@ __global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS)
                 a.v[3 * i + c] = vn;
             }
             st_rec(Rout + 2 * i, make_float4(ni.x, ni.y, ni.z, H[0]),
-                   make_float4(H[1], H[2], bf_pack(L[0], L[1]), bf_pack(L[2], 0.0f)));
+                   make_float4(H[1], H[2], bf_pack(L[1], L[0]), bf_pack(0.0f, L[2])));
             a.lo32[i] = make_float4(L[0], L[1], L[2], 0.0f);
             const float wi = a.wsum_inv[i];
             // clamp: ws * (1 / sum w) can round to 1 + 1 ulp for an intact family
