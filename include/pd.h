@@ -193,6 +193,50 @@ pd_status pd_damage(pd_handle* h, double* phi);
 pd_status pd_set_params(pd_handle* h, double c, double sc, double load, double disp_rate,
                         const double* c_bond);
 
+/* ---------------------------------------------------------------------------
+ * Batched multi-instance form (outer-loop use: sensitivity, uncertainty
+ * quantification, optimisation; Section 3.6 "Running simulations").
+ */
+typedef struct {
+    int64_t n;               /* nodes of this instance (>= 1) */
+    const double* coords;    /* host, n*3 */
+    const double* volumes;   /* host, n */
+    double horizon;          /* delta of this instance (its family is searched alone) */
+    const double* cuts;      /* host, n_cuts*6 (see pd_create), or NULL */
+    int32_t n_cuts;
+    int32_t reserved;
+    pd_material mat;         /* c and critical stretch of this instance */
+    pd_bc bc;                /* BCs of this instance; disp_rate and load must be equal
+                                across the batch (they are handle-wide) */
+} pd_instance;
+
+/*
+ * pd_batch_create - n_inst independent models advanced together: one handle,
+ * one fused launch per step over all instances (no bond joins two instances).
+ * Node k of instance b has the batch-wide id node_offset[b] + k in every other
+ * call (pd_get_state, pd_damage, pd_get_bonds, ...), node offsets being the
+ * prefix sums of the instances' n.  The per-bond s_c draw of an instance with
+ * sc_mode 1 is keyed on its own node ids, so an instance behaves exactly as
+ * the same model created alone.  dt, damping, density, precision and graph
+ * settings come from cfg and are shared.  pd_set_params is not available on a
+ * batch handle (PD_ERR_STATE).  Errors as pd_create, plus PD_ERR_ARG when
+ * instances disagree on disp_rate/load, or n_inst < 1.
+ */
+pd_status pd_batch_create(int32_t n_inst, const pd_instance* inst, const pd_config* cfg,
+                          pd_handle** out);
+
+/* pd_batch_offsets - node_offset[n_inst+1] (host) of a batch handle (or [0, n] otherwise). */
+pd_status pd_batch_offsets(pd_handle* h, int32_t* n_inst, int64_t* node_offset);
+
+/*
+ * pd_autotune - time `trial_steps` steps for each candidate launch shape
+ * (threads per block, resident blocks per SM) and keep the fastest.  The model
+ * state (u, v, bond flags, step counter) is saved before and restored after,
+ * so the simulation is unchanged.  trial_steps in [1, 1000].
+ */
+pd_status pd_autotune(pd_handle* h, int32_t trial_steps, int32_t* block_threads,
+                      int32_t* blocks_per_sm);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,8 @@ from . import _build
 __all__ = [
     "PdError", "build", "lib", "pd_micromodulus", "pd_create", "pd_destroy", "pd_last_error",
     "pd_get_info", "pd_get_family", "pd_step", "pd_sync", "pd_get_state", "pd_set_state",
-    "pd_get_bonds", "pd_set_bonds", "pd_damage", "pd_set_params", "Model",
+    "pd_get_bonds", "pd_set_bonds", "pd_damage", "pd_set_params", "pd_batch_create",
+    "pd_batch_offsets", "pd_autotune", "instance_from_workload", "Model",
     "PD_PREC_F32", "PD_PREC_F64",
 ]
 
@@ -62,6 +63,12 @@ class _Bc(ctypes.Structure):
                 ("disp_rate", ctypes.c_double), ("load", ctypes.c_double)]
 
 
+class _Instance(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("coords", ctypes.c_void_p), ("volumes", ctypes.c_void_p),
+                ("horizon", ctypes.c_double), ("cuts", ctypes.c_void_p), ("n_cuts", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("mat", _Material), ("bc", _Bc)]
+
+
 class _Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("n_bonds", ctypes.c_int64), ("step", ctypes.c_int64),
                 ("precision", ctypes.c_int32), ("ell_width", ctypes.c_int32),
@@ -98,6 +105,9 @@ def lib():
             "pd_set_bonds": [P, P],
             "pd_damage": [P, P],
             "pd_set_params": [P, D, D, D, D, P],
+            "pd_batch_create": [I32, P, P, P],
+            "pd_batch_offsets": [P, P, P],
+            "pd_autotune": [P, I32, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -267,11 +277,96 @@ def pd_set_params(h: int, c: float, sc: float, load: float, disp_rate: float,
     _check(lib().pd_set_params(h, float(c), float(sc), float(load), float(disp_rate), p))
 
 
+def _config(precision, graph_steps, dt, damping, density, check_dt, device, stream,
+            block_threads, blocks_per_sm, reorder):
+    return _Config(precision=int(precision), graph_steps=int(graph_steps), dt=float(dt),
+                   damping=float(damping), density=float(density), check_dt=int(bool(check_dt)),
+                   device=int(device), stream=stream, block_threads=int(block_threads),
+                   blocks_per_sm=int(blocks_per_sm), reorder=int(reorder))
+
+
+def pd_batch_create(instances, *, dt: float, damping: float, density: float,
+                    precision: int = PD_PREC_F64, graph_steps: int = 0, check_dt: bool = False,
+                    device: int = 0, stream=None, block_threads: int = 0,
+                    blocks_per_sm: int = 0, reorder: int = 0) -> int:
+    """Create a batch handle from a list of dicts with the keys of ``pd_create``'s
+    body arguments: coords, volumes, horizon, c, sc / sc_hash, cuts, bc_type,
+    bc_disp, bc_force, no_fail, disp_rate, load."""
+    keep = []
+    arr = (_Instance * len(instances))()
+    for k, I in enumerate(instances):
+        x, kx = _ptr(I["coords"], np.float64)
+        n = kx.size // 3
+        vol, kv = _ptr(I["volumes"], np.float64, n)
+        cuts = I.get("cuts")
+        ca = (np.ascontiguousarray(np.asarray(cuts, np.float64).reshape(-1, 6))
+              if cuts is not None and len(cuts) else None)
+        cp, kc = _ptr(ca, np.float64)
+        bt, kbt = _ptr(I["bc_type"], np.uint8, 3 * n)
+        bd, kbd = _ptr(I.get("bc_disp"), np.float64, 3 * n if I.get("bc_disp") is not None else None)
+        bf, kbf = _ptr(I.get("bc_force"), np.float64, 3 * n if I.get("bc_force") is not None else None)
+        nf, knf = _ptr(I.get("no_fail"), np.uint8, n if I.get("no_fail") is not None else None)
+        keep += [kx, kv, kc, kbt, kbd, kbf, knf]
+        mat = _Material(c=float(I["c"]), sc=float(I.get("sc", 0.0)), sc_mode=0)
+        if I.get("sc_hash") is not None:
+            s = I["sc_hash"]
+            mat.sc_mode, mat.sc_seed, mat.sc_lo, mat.sc_hi = 1, int(s[0]), float(s[1]), float(s[2])
+        arr[k] = _Instance(n=n, coords=x, volumes=vol, horizon=float(I["horizon"]), cuts=cp,
+                           n_cuts=0 if ca is None else ca.shape[0], mat=mat,
+                           bc=_Bc(type=bt, disp=bd, force=bf, no_fail=nf,
+                                  disp_rate=float(I.get("disp_rate", 0.0)),
+                                  load=float(I.get("load", 0.0))))
+    cfg = _config(precision, graph_steps, dt, damping, density, check_dt, device, stream,
+                  block_threads, blocks_per_sm, reorder)
+    h = ctypes.c_void_p()
+    _check(lib().pd_batch_create(len(instances), arr, ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def pd_batch_offsets(h: int) -> np.ndarray:
+    k = ctypes.c_int32()
+    _check(lib().pd_batch_offsets(h, ctypes.byref(k), None))
+    off = np.empty(k.value + 1, np.int64)
+    _check(lib().pd_batch_offsets(h, ctypes.byref(k), off.ctypes.data))
+    return off
+
+
+def pd_autotune(h: int, trial_steps: int = 20):
+    """Pick the fastest (threads per block, blocks per SM); the state is unchanged."""
+    b, s = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().pd_autotune(h, int(trial_steps), ctypes.byref(b), ctypes.byref(s)))
+    return b.value, s.value
+
+
+def instance_from_workload(w, c=None) -> dict:
+    """pd_batch_create instance dict of a workloads.Workload."""
+    if c is None:
+        c = pd_micromodulus(w.bulk_modulus, w.horizon)
+    return dict(coords=w.coords, volumes=w.volumes, horizon=w.horizon, c=c, sc=w.sc,
+                sc_hash=w.sc_hash, cuts=w.cuts_array(), bc_type=w.bc_type, bc_disp=w.bc_disp,
+                bc_force=w.bc_force, no_fail=w.no_fail, disp_rate=w.disp_rate, load=w.load)
+
+
 class Model:
     """Owning wrapper of one handle (calls the pd_* functions above)."""
 
-    def __init__(self, **kw):
-        self.h = pd_create(**kw)
+    def __init__(self, handle=None, **kw):
+        self.h = handle if handle is not None else pd_create(**kw)
+
+    @classmethod
+    def batch(cls, workload_list, precision=PD_PREC_F64, c_list=None, **kw):
+        """One handle advancing every workload of the list together."""
+        insts = [instance_from_workload(w, None if c_list is None else c_list[k])
+                 for k, w in enumerate(workload_list)]
+        w0 = workload_list[0]
+        return cls(handle=pd_batch_create(insts, dt=w0.dt, damping=w0.damping,
+                                          density=w0.density, precision=precision, **kw))
+
+    def offsets(self):
+        return pd_batch_offsets(self.h)
+
+    def autotune(self, trial_steps=20):
+        return pd_autotune(self.h, trial_steps)
 
     @classmethod
     def from_workload(cls, w, precision=PD_PREC_F64, c=None, **kw):

@@ -21,6 +21,9 @@ namespace {
 
 thread_local std::string g_err;
 
+// relative band around s_c within which the FP32 path re-tests bonds in FP64
+constexpr double kGuard = 5e-4;
+
 pd_status fail(pd_status st, const char* fmt, ...)
 {
     char buf[512];
@@ -115,6 +118,12 @@ struct pd_handle {
     int* err = nullptr;
     int64_t* step_ctr = nullptr;
     double* staging = nullptr;  // 3n doubles for host transfers
+    // batches: instance of each node, instance-local ids, per-instance s_c table
+    bool batch = false;
+    std::vector<int64_t> inst_off;
+    int32_t* inst = nullptr;
+    int32_t* hid = nullptr;
+    InstParams* itab = nullptr;
 
     template <class T>
     cudaError_t alloc(T** p, size_t count)
@@ -157,6 +166,9 @@ namespace {
 StepArgsF32 args_f32(pd_handle* h, int k)
 {
     StepArgsF32 a{};
+    a.inst = h->inst;
+    a.itab = h->itab;
+    a.hid = h->hid;
     a.rec[0] = h->rec32[0];
     a.rec[1] = h->rec32[1];
     a.lo32 = h->lo32;
@@ -180,7 +192,7 @@ StepArgsF32 args_f32(pd_handle* h, int k)
     a.k = k;
     a.Q = h->Q;
     a.has_nofail = h->has_nofail ? 1 : 0;
-    a.guard = 5e-4f;
+    a.guard = (float)kGuard;
     a.sc_f = (float)h->sc;
     a.sc_lo_f = (float)h->sc_lo;
     a.fast_lo = (float)((1.0 - 2.0 * a.guard) * h->sc_lo);
@@ -201,6 +213,9 @@ StepArgsF32 args_f32(pd_handle* h, int k)
 StepArgsF64 args_f64(pd_handle* h, int k)
 {
     StepArgsF64 a{};
+    a.inst = h->inst;
+    a.itab = h->itab;
+    a.hid = h->hid;
     a.rec[0] = h->rec[0];
     a.rec[1] = h->rec[1];
     a.v = (double*)h->v;
@@ -305,27 +320,28 @@ pd_status pd_micromodulus(double K, double delta, double* c_out)
     return PD_OK;
 }
 
-pd_status pd_create(int64_t n, const double* coords, const double* volumes, double horizon,
-                    const int64_t* fam_off, const int32_t* fam_idx, const double* cuts,
-                    int32_t n_cuts, const pd_material* mat, const pd_bc* bc,
-                    const pd_config* cfg, pd_handle** out)
+}  // extern "C"
+
+namespace {
+
+pd_status check_cfg(const pd_config* cfg)
 {
-    g_err.clear();
-    if (!out) return fail(PD_ERR_ARG, "out is NULL");
-    *out = nullptr;
-    if (n < 1 || n >= (int64_t)1 << 31) return fail(PD_ERR_ARG, "n must be in [1, 2^31)");
-    if (!coords || !volumes || !mat || !bc || !cfg)
-        return fail(PD_ERR_ARG, "coords, volumes, mat, bc and cfg are required");
-    if (!bc->type) return fail(PD_ERR_ARG, "bc->type is required");
-    if ((fam_off == nullptr) != (fam_idx == nullptr))
-        return fail(PD_ERR_ARG, "fam_off and fam_idx must both be given or both be NULL");
-    if (n_cuts < 0 || (n_cuts > 0 && !cuts)) return fail(PD_ERR_ARG, "invalid cuts");
     if (cfg->precision != PD_PREC_F32 && cfg->precision != PD_PREC_F64)
         return fail(PD_ERR_ARG, "precision must be 32 or 64");
-    if (!(horizon > 0.0) || !std::isfinite(horizon)) return fail(PD_ERR_ARG, "horizon must be > 0");
     if (!(cfg->dt > 0.0) || !(cfg->density > 0.0) || !(cfg->damping >= 0.0) ||
         !std::isfinite(cfg->dt) || !std::isfinite(cfg->density) || !std::isfinite(cfg->damping))
         return fail(PD_ERR_ARG, "dt and density must be > 0, damping >= 0");
+    if (cfg->graph_steps < 0 || cfg->graph_steps > 4096)
+        return fail(PD_ERR_ARG, "graph_steps must be in [0, 4096]");
+    if (cfg->block_threads != 0 &&
+        (cfg->block_threads < 32 || cfg->block_threads > 256 || cfg->block_threads % 32))
+        return fail(PD_ERR_ARG, "block_threads must be a multiple of 32 in [32, 256]");
+    if (cfg->reorder != 0 && cfg->reorder != 1) return fail(PD_ERR_ARG, "reorder must be 0 or 1");
+    return PD_OK;
+}
+
+pd_status check_material(const pd_material* mat)
+{
     if (!(mat->c > 0.0) || !std::isfinite(mat->c)) return fail(PD_ERR_ARG, "c must be > 0");
     if (mat->sc_mode == 0) {
         if (!(mat->sc > 0.0) || !std::isfinite(mat->sc)) return fail(PD_ERR_ARG, "sc must be > 0");
@@ -335,101 +351,101 @@ pd_status pd_create(int64_t n, const double* coords, const double* volumes, doub
     } else {
         return fail(PD_ERR_ARG, "sc_mode must be 0 or 1");
     }
+    return PD_OK;
+}
+
+pd_status check_body(int64_t n, const double* coords, const double* volumes, double horizon,
+                     const double* cuts, int32_t n_cuts, const pd_bc* bc)
+{
+    if (n < 1 || n >= (int64_t)1 << 31) return fail(PD_ERR_ARG, "n must be in [1, 2^31)");
+    if (!coords || !volumes || !bc) return fail(PD_ERR_ARG, "coords, volumes and bc are required");
+    if (!bc->type) return fail(PD_ERR_ARG, "bc->type is required");
+    if (n_cuts < 0 || (n_cuts > 0 && !cuts)) return fail(PD_ERR_ARG, "invalid cuts");
+    if (!(horizon > 0.0) || !std::isfinite(horizon)) return fail(PD_ERR_ARG, "horizon must be > 0");
     if (!std::isfinite(bc->disp_rate) || !std::isfinite(bc->load))
         return fail(PD_ERR_ARG, "disp_rate and load must be finite");
-    if (cfg->graph_steps < 0 || cfg->graph_steps > 4096)
-        return fail(PD_ERR_ARG, "graph_steps must be in [0, 4096]");
-    if (cfg->block_threads != 0 &&
-        (cfg->block_threads < 32 || cfg->block_threads > 256 || cfg->block_threads % 32))
-        return fail(PD_ERR_ARG, "block_threads must be a multiple of 32 in [32, 256]");
-    if (cfg->reorder != 0 && cfg->reorder != 1) return fail(PD_ERR_ARG, "reorder must be 0 or 1");
     if (!finite_all(coords, 3 * n)) return fail(PD_ERR_ARG, "non-finite coordinates");
     for (int64_t i = 0; i < n; ++i)
         if (!(volumes[i] > 0.0) || !std::isfinite(volumes[i]))
             return fail(PD_ERR_ARG, "volumes must be finite and > 0");
+    return PD_OK;
+}
 
-    pd_handle* h = new (std::nothrow) pd_handle();
-    if (!h) return fail(PD_ERR_OOM, "host allocation");
-    auto bail = [&](pd_status st) {
-        h->release();
-        delete h;
-        return st;
-    };
+// Host description of a model whose family (h->off, h->idx, after the cuts)
+// and material scalars are already in the handle.
+struct ModelDesc {
+    int64_t n = 0;
+    const double* coords = nullptr;   // 3n
+    const double* wvol = nullptr;     // n: w = c * wvol (batches fold c into wvol)
+    const uint8_t* type = nullptr;    // 3n
+    const double* disp = nullptr;     // 3n or null
+    const double* force = nullptr;    // 3n or null
+    const uint8_t* no_fail = nullptr; // n or null
+    const double* centre = nullptr;   // 3n per-node origin of the FP32 positions, or null
+    double unit = 1.0;                // FP32 length unit (the horizon)
+    double horizon = 1.0;             // cell size of the optional node reordering
+    int uniform_w = -1;               // batches: 1 if every instance has uniform weights
+    std::vector<int32_t> inst, hid;   // batches only
+    std::vector<InstParams> itab;
+};
 
-    // ---- family, notch, order, layout (host)
-    std::string msg;
-    if (fam_off) {
-        msg = check_family(n, fam_off, fam_idx);
-        if (!msg.empty()) return bail(fail(PD_ERR_ARG, "%s", msg.c_str()));
-        h->off.assign(fam_off, fam_off + n + 1);
-        h->idx.assign(fam_idx, fam_idx + fam_off[n]);
-    } else {
-        msg = search_family(n, coords, horizon, h->off, h->idx);
-        if (!msg.empty()) return bail(fail(PD_ERR_ARG, "%s", msg.c_str()));
-    }
-    apply_cuts(n, coords, cuts, n_cuts, h->off, h->idx);
+pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
+{
+    const int64_t n = d.n;
     int64_t maxfam = 0;
     for (int64_t i = 0; i < n; ++i) maxfam = std::max(maxfam, h->off[i + 1] - h->off[i]);
     if (maxfam > PD_MAX_FAMILY)
-        return bail(fail(PD_ERR_FAMILY_TOO_LARGE, "largest family has %lld members (max %d)",
-                         (long long)maxfam, PD_MAX_FAMILY));
+        return fail(PD_ERR_FAMILY_TOO_LARGE, "largest family has %lld members (max %d)",
+                    (long long)maxfam, PD_MAX_FAMILY);
     h->Q = (int)std::max<int64_t>(1, (maxfam + 31) / 32);
     h->n = n;
     h->n_slices = (n + 31) / 32;
     h->n_pad = 32 * h->n_slices;
     h->n_bonds = h->off[n];
     h->precision = cfg->precision;
-    h->delta = horizon;
+    h->delta = d.unit;
     h->dt = cfg->dt;
     h->eta = cfg->damping;
     h->rho = cfg->density;
-    h->c = mat->c;
-    h->sc_mode = mat->sc_mode;
-    h->sc = mat->sc_mode == 0 ? mat->sc : 0.5 * (mat->sc_lo + mat->sc_hi);
-    h->sc_seed = mat->sc_seed;
-    h->sc_lo = mat->sc_mode == 1 ? mat->sc_lo : mat->sc;
-    h->sc_hi = mat->sc_mode == 1 ? mat->sc_hi : mat->sc;
-    h->disp_rate = bc->disp_rate;
-    h->load = bc->load;
     h->graph_steps = cfg->graph_steps;
     h->block = cfg->block_threads ? cfg->block_threads : 256;
     h->device = cfg->device;
-    h->vol0 = volumes[0];
+    h->vol0 = d.wvol[0];
     h->uniform_vol = true;
-    for (int64_t i = 1; i < n && h->uniform_vol; ++i) h->uniform_vol = volumes[i] == volumes[0];
+    for (int64_t i = 1; i < n && h->uniform_vol; ++i) h->uniform_vol = d.wvol[i] == d.wvol[0];
+    if (d.uniform_w >= 0) h->uniform_vol = d.uniform_w == 1;
 
     if (cfg->check_dt) {
-        const double dtc = stable_dt(n, coords, volumes, h->off, h->idx, h->c, h->rho);
-        if (h->dt > dtc)
-            return bail(fail(PD_ERR_UNSTABLE_DT, "dt = %g exceeds the stable bound %g", h->dt, dtc));
+        const double dtc = stable_dt(n, d.coords, d.wvol, h->off, h->idx, h->c, h->rho);
+        if (h->dt > dtc) return fail(PD_ERR_UNSTABLE_DT, "dt = %g exceeds the stable bound %g", h->dt, dtc);
     }
 
     std::vector<BcClass> table;
     std::vector<uint8_t> cls;
-    msg = bc_classes(n, bc->type, bc->disp, bc->force, bc->no_fail, table, cls, h->has_nofail);
-    if (!msg.empty()) return bail(fail(PD_ERR_ARG, "%s", msg.c_str()));
+    std::string msg = bc_classes(n, d.type, d.disp, d.force, d.no_fail, table, cls, h->has_nofail);
+    if (!msg.empty()) return fail(PD_ERR_ARG, "%s", msg.c_str());
 
-    spatial_order(n, coords, horizon, cfg->reorder, h->perm, h->inv);
+    spatial_order(n, d.coords, d.horizon, cfg->reorder, h->perm, h->inv);
     std::vector<int32_t> nbr, sw;
     std::vector<uint32_t> bits;
     build_layout(n, h->off, h->idx, h->perm, h->inv, h->Q, nbr, bits, sw, h->cnt);
 
     // ---- device
     cudaError_t e = cudaSetDevice(h->device);
-    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaSetDevice"));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     if (cfg->stream) {
         h->stream = (cudaStream_t)cfg->stream;
     } else {
         e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
-        if (e != cudaSuccess) return bail(cuda_fail(e, "stream create"));
+        if (e != cudaSuccess) return cuda_fail(e, "stream create");
         h->own_stream = true;
     }
     const int64_t np = h->n_pad;
     const bool f32 = h->precision == 32;
-#define ALLOC(ptr, type, count)                                              \
-    do {                                                                     \
-        e = h->alloc((type**)&(ptr), (size_t)(count));                       \
-        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc " #ptr)); \
+#define ALLOC(ptr, type, count)                                      \
+    do {                                                             \
+        e = h->alloc((type**)&(ptr), (size_t)(count));               \
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc " #ptr); \
     } while (0)
     if (f32) {
         ALLOC(h->rec32[0], float4, 2 * np);
@@ -458,27 +474,45 @@ pd_status pd_create(int64_t n, const double* coords, const double* volumes, doub
     ALLOC(h->err, int, 1);
     ALLOC(h->step_ctr, int64_t, 1);
     ALLOC(h->staging, double, 3 * n);
+    if (!d.inst.empty()) {
+        ALLOC(h->inst, int32_t, np);
+        ALLOC(h->hid, int32_t, np);
+        ALLOC(h->itab, InstParams, d.itab.size());
+    }
 #undef ALLOC
 
     // node data in the library's order (padding nodes: zero volume, class 0)
-    double lo[3], hi[3];
-    for (int a = 0; a < 3; ++a) lo[a] = hi[a] = coords[a];
-    for (int64_t i = 0; i < n; ++i)
-        for (int a = 0; a < 3; ++a) {
-            lo[a] = std::min(lo[a], coords[3 * i + a]);
-            hi[a] = std::max(hi[a], coords[3 * i + a]);
-        }
-    double ctr[3];
-    for (int a = 0; a < 3; ++a) ctr[a] = 0.5 * (lo[a] + hi[a]);
-    std::vector<double> xs(3 * np, 0.0), vs(np, 0.0);
+    double gctr[3];
+    {
+        double lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) lo[a] = hi[a] = d.coords[a];
+        for (int64_t i = 0; i < n; ++i)
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = std::min(lo[a], d.coords[3 * i + a]);
+                hi[a] = std::max(hi[a], d.coords[3 * i + a]);
+            }
+        for (int a = 0; a < 3; ++a) gctr[a] = 0.5 * (lo[a] + hi[a]);
+    }
+    std::vector<double> xs(3 * np, 0.0), vs(np, 0.0), cs(3 * np, 0.0);
     std::vector<uint8_t> clsp(np, 0);
-    std::vector<int32_t> gids(np, 0);
+    std::vector<int32_t> gids(np, 0), insts, hids;
+    if (!d.inst.empty()) {
+        insts.assign(np, 0);
+        hids.assign(np, 0);
+    }
     for (int64_t p = 0; p < n; ++p) {
         const int64_t i = h->perm[p];
-        for (int a = 0; a < 3; ++a) xs[3 * p + a] = coords[3 * i + a];
-        vs[p] = volumes[i];
+        for (int a = 0; a < 3; ++a) {
+            xs[3 * p + a] = d.coords[3 * i + a];
+            cs[3 * p + a] = d.centre ? d.centre[3 * i + a] : gctr[a];
+        }
+        vs[p] = d.wvol[i];
         clsp[p] = cls[i];
         gids[p] = (int32_t)i;
+        if (!d.inst.empty()) {
+            insts[p] = d.inst[i];
+            hids[p] = d.hid[i];
+        }
     }
     auto up = [&](void* dst, const void* src, size_t bytes, const char* what) -> pd_status {
         cudaError_t ee = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->stream);
@@ -491,19 +525,19 @@ pd_status pd_create(int64_t n, const double* coords, const double* volumes, doub
     if (f32) {
         r32.assign(2 * np, make_float4(0.f, 0.f, 0.f, 0.f));
         for (int64_t p = 0; p < n; ++p)
-            r32[2 * p] = make_float4((float)((xs[3 * p] - ctr[0]) / horizon),
-                                     (float)((xs[3 * p + 1] - ctr[1]) / horizon),
-                                     (float)((xs[3 * p + 2] - ctr[2]) / horizon), 0.0f);
+            r32[2 * p] = make_float4((float)((xs[3 * p] - cs[3 * p]) / d.unit),
+                                     (float)((xs[3 * p + 1] - cs[3 * p + 1]) / d.unit),
+                                     (float)((xs[3 * p + 2] - cs[3 * p + 2]) / d.unit), 0.0f);
         if ((st = up(h->rec32[0], r32.data(), 32 * np, "upload records")) ||
             (st = up(h->rec32[1], r32.data(), 32 * np, "upload records")))
-            return bail(st);
+            return st;
     } else {
         r64.assign(8 * np, 0.0);
         for (int64_t p = 0; p < n; ++p)
             for (int a = 0; a < 3; ++a) r64[8 * p + a] = xs[3 * p + a];
         if ((st = up(h->rec[0], r64.data(), 64 * np, "upload records")) ||
             (st = up(h->rec[1], r64.data(), 64 * np, "upload records")))
-            return bail(st);
+            return st;
     }
     if ((st = up(h->nbr, nbr.data(), nbr.size() * 4, "upload family")) ||
         (st = up(h->bits, bits.data(), bits.size() * 4, "upload bond flags")) ||
@@ -514,15 +548,209 @@ pd_status pd_create(int64_t n, const double* coords, const double* volumes, doub
         (st = up(h->gid, gids.data(), 4 * np, "upload ids")) ||
         (st = up(h->x64, xs.data(), 24 * np, "upload coordinates")) ||
         (st = up(h->vol, vs.data(), 8 * np, "upload volumes")))
-        return bail(st);
-    if ((st = upload_weights(h)) != PD_OK) return bail(st);
+        return st;
+    if (!d.inst.empty()) {
+        if ((st = up(h->inst, insts.data(), 4 * np, "upload instance ids")) ||
+            (st = up(h->hid, hids.data(), 4 * np, "upload local ids")) ||
+            (st = up(h->itab, d.itab.data(), d.itab.size() * sizeof(InstParams),
+                     "upload instance table")))
+            return st;
+    }
+    if ((st = upload_weights(h)) != PD_OK) return st;
     h->blocks_per_sm = cfg->blocks_per_sm;
-    if ((st = choose_grid(h, h->blocks_per_sm)) != PD_OK) return bail(st);
+    if ((st = choose_grid(h, h->blocks_per_sm)) != PD_OK) return st;
     e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return bail(cuda_fail(e, "synchronize"));
+    if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+    return PD_OK;
+}
+
+void set_material(pd_handle* h, const pd_material* mat, const pd_bc* bc)
+{
+    h->c = mat->c;
+    h->sc_mode = mat->sc_mode;
+    h->sc = mat->sc_mode == 0 ? mat->sc : 0.5 * (mat->sc_lo + mat->sc_hi);
+    h->sc_seed = mat->sc_seed;
+    h->sc_lo = mat->sc_mode == 1 ? mat->sc_lo : mat->sc;
+    h->sc_hi = mat->sc_mode == 1 ? mat->sc_hi : mat->sc;
+    h->disp_rate = bc->disp_rate;
+    h->load = bc->load;
+}
+
+}  // namespace
+
+extern "C" {
+
+pd_status pd_create(int64_t n, const double* coords, const double* volumes, double horizon,
+                    const int64_t* fam_off, const int32_t* fam_idx, const double* cuts,
+                    int32_t n_cuts, const pd_material* mat, const pd_bc* bc,
+                    const pd_config* cfg, pd_handle** out)
+{
+    g_err.clear();
+    if (!out) return fail(PD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!mat || !cfg) return fail(PD_ERR_ARG, "mat and cfg are required");
+    pd_status st;
+    if ((st = check_body(n, coords, volumes, horizon, cuts, n_cuts, bc)) != PD_OK) return st;
+    if ((st = check_cfg(cfg)) != PD_OK || (st = check_material(mat)) != PD_OK) return st;
+    if ((fam_off == nullptr) != (fam_idx == nullptr))
+        return fail(PD_ERR_ARG, "fam_off and fam_idx must both be given or both be NULL");
+
+    pd_handle* h = new (std::nothrow) pd_handle();
+    if (!h) return fail(PD_ERR_OOM, "host allocation");
+    std::string msg;
+    if (fam_off) {
+        msg = check_family(n, fam_off, fam_idx);
+        if (msg.empty()) {
+            h->off.assign(fam_off, fam_off + n + 1);
+            h->idx.assign(fam_idx, fam_idx + fam_off[n]);
+        }
+    } else {
+        msg = search_family(n, coords, horizon, h->off, h->idx);
+    }
+    if (!msg.empty()) {
+        delete h;
+        return fail(PD_ERR_ARG, "%s", msg.c_str());
+    }
+    apply_cuts(n, coords, cuts, n_cuts, h->off, h->idx);
+    set_material(h, mat, bc);
+    ModelDesc d;
+    d.n = n;
+    d.coords = coords;
+    d.wvol = volumes;
+    d.type = bc->type;
+    d.disp = bc->disp;
+    d.force = bc->force;
+    d.no_fail = bc->no_fail;
+    d.unit = horizon;
+    d.horizon = horizon;
+    if ((st = build_device(h, d, cfg)) != PD_OK) {
+        h->release();
+        delete h;
+        return st;
+    }
+    h->inst_off = {0, n};
     *out = h;
     return PD_OK;
 }
+
+pd_status pd_batch_create(int32_t n_inst, const pd_instance* inst, const pd_config* cfg,
+                          pd_handle** out)
+{
+    g_err.clear();
+    if (!out) return fail(PD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_inst < 1 || !inst || !cfg) return fail(PD_ERR_ARG, "need n_inst >= 1, inst and cfg");
+    pd_status st;
+    if ((st = check_cfg(cfg)) != PD_OK) return st;
+    int64_t n = 0;
+    double unit = 0.0;
+    bool any_nofail = false;
+    for (int32_t b = 0; b < n_inst; ++b) {
+        const pd_instance& I = inst[b];
+        if ((st = check_body(I.n, I.coords, I.volumes, I.horizon, I.cuts, I.n_cuts, &I.bc)) != PD_OK ||
+            (st = check_material(&I.mat)) != PD_OK)
+            return fail(st, "instance %d: %s", b, g_err.c_str());
+        if (I.bc.disp_rate != inst[0].bc.disp_rate || I.bc.load != inst[0].bc.load)
+            return fail(PD_ERR_ARG, "instance %d: disp_rate and load must equal instance 0's", b);
+        n += I.n;
+        unit = std::max(unit, I.horizon);
+        any_nofail = any_nofail || I.bc.no_fail != nullptr;
+    }
+    if (n >= (int64_t)1 << 31) return fail(PD_ERR_ARG, "batch has 2^31 nodes or more");
+
+    pd_handle* h = new (std::nothrow) pd_handle();
+    if (!h) return fail(PD_ERR_OOM, "host allocation");
+    std::vector<double> x(3 * n), wv(n), disp(3 * n, 0.0), force(3 * n, 0.0), centre(3 * n);
+    std::vector<uint8_t> type(3 * n), nofail(any_nofail ? n : 0, 0);
+    ModelDesc d;
+    d.inst.resize(n);
+    d.hid.resize(n);
+    d.itab.resize(n_inst);
+    h->off.assign(1, 0);
+    h->inst_off.assign(1, 0);
+    bool uniform_all = true;  // every instance has uniform volumes
+    for (int32_t b = 0; b < n_inst; ++b) {
+        const pd_instance& I = inst[b];
+        const int64_t o = h->inst_off.back();
+        std::vector<int64_t> off;
+        std::vector<int32_t> idx;
+        std::string msg = search_family(I.n, I.coords, I.horizon, off, idx);
+        if (!msg.empty()) {
+            delete h;
+            return fail(PD_ERR_ARG, "instance %d: %s", b, msg.c_str());
+        }
+        apply_cuts(I.n, I.coords, I.cuts, I.n_cuts, off, idx);
+        for (int64_t i = 0; i < I.n; ++i) h->off.push_back(h->off.back() + (off[i + 1] - off[i]));
+        for (int32_t j : idx) h->idx.push_back((int32_t)(j + o));
+        double lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) lo[a] = hi[a] = I.coords[a];
+        for (int64_t i = 0; i < I.n; ++i)
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = std::min(lo[a], I.coords[3 * i + a]);
+                hi[a] = std::max(hi[a], I.coords[3 * i + a]);
+            }
+        for (int64_t i = 0; i < I.n; ++i) {
+            const int64_t k = o + i;
+            for (int a = 0; a < 3; ++a) {
+                x[3 * k + a] = I.coords[3 * i + a];
+                centre[3 * k + a] = 0.5 * (lo[a] + hi[a]);
+                type[3 * k + a] = I.bc.type[3 * i + a];
+                if (I.bc.disp) disp[3 * k + a] = I.bc.disp[3 * i + a];
+                if (I.bc.force) force[3 * k + a] = I.bc.force[3 * i + a];
+            }
+            wv[k] = I.mat.c * I.volumes[i];
+            if (I.bc.no_fail) nofail[k] = I.bc.no_fail[i];
+            d.inst[k] = b;
+            d.hid[k] = (int32_t)i;
+        }
+        InstParams& ip = d.itab[b];
+        ip.sc_mode = I.mat.sc_mode;
+        ip.sc = I.mat.sc_mode == 0 ? I.mat.sc : 0.5 * (I.mat.sc_lo + I.mat.sc_hi);
+        ip.sc_lo = I.mat.sc_mode == 1 ? I.mat.sc_lo : I.mat.sc;
+        ip.sc_hi = I.mat.sc_mode == 1 ? I.mat.sc_hi : I.mat.sc;
+        ip.sc_seed = I.mat.sc_seed;
+        ip.fast_lo = (float)((1.0 - 2.0 * kGuard) * ip.sc_lo);
+        ip.w_const = (float)(I.mat.c * I.volumes[0]);
+        for (int64_t i = 1; i < I.n && uniform_all; ++i) uniform_all = I.volumes[i] == I.volumes[0];
+        h->inst_off.push_back(o + I.n);
+    }
+    // weights carry each instance's micromodulus: w = 1 * (c_b V)
+    pd_material m0 = inst[0].mat;
+    m0.c = 1.0;
+    set_material(h, &m0, &inst[0].bc);
+    h->batch = true;
+    d.n = n;
+    d.coords = x.data();
+    d.wvol = wv.data();
+    d.type = type.data();
+    d.disp = disp.data();
+    d.force = force.data();
+    d.no_fail = any_nofail ? nofail.data() : nullptr;
+    d.centre = centre.data();
+    d.unit = unit;
+    d.horizon = unit;
+    d.uniform_w = uniform_all ? 1 : 0;
+    if ((st = build_device(h, d, cfg)) != PD_OK) {
+        h->release();
+        delete h;
+        return st;
+    }
+    *out = h;
+    return PD_OK;
+}
+
+pd_status pd_batch_offsets(pd_handle* h, int32_t* n_inst, int64_t* node_offset)
+{
+    if (!h) return fail(PD_ERR_ARG, "NULL handle");
+    const int32_t k = (int32_t)h->inst_off.size() - 1;
+    if (n_inst) *n_inst = k;
+    if (node_offset) std::memcpy(node_offset, h->inst_off.data(), sizeof(int64_t) * (k + 1));
+    return PD_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
 
 void pd_destroy(pd_handle* h)
 {
@@ -730,10 +958,106 @@ pd_status pd_damage(pd_handle* h, double* phi)
     return check_dev_err(h);
 }
 
+pd_status pd_autotune(pd_handle* h, int32_t trial_steps, int32_t* block_threads,
+                      int32_t* blocks_per_sm)
+{
+    if (!h) return fail(PD_ERR_ARG, "NULL handle");
+    if (trial_steps < 1 || trial_steps > 1000) return fail(PD_ERR_ARG, "trial_steps in [1, 1000]");
+    PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
+    // save everything a step writes: displacement records and low parts, velocity,
+    // bond flags, damage and the step counter
+    struct Buf {
+        void* dev;
+        size_t bytes;
+        std::vector<uint8_t> keep;
+    };
+    const int64_t np = h->n_pad;
+    std::vector<Buf> bufs;
+    if (h->precision == 32) {
+        bufs.push_back({h->rec32[0], (size_t)(32 * np), {}});
+        bufs.push_back({h->rec32[1], (size_t)(32 * np), {}});
+        bufs.push_back({h->lo32, (size_t)(16 * np), {}});
+        bufs.push_back({h->v, (size_t)(12 * np), {}});
+        bufs.push_back({h->damage, (size_t)(4 * np), {}});
+    } else {
+        bufs.push_back({h->rec[0], (size_t)(64 * np), {}});
+        bufs.push_back({h->rec[1], (size_t)(64 * np), {}});
+        bufs.push_back({h->v, (size_t)(24 * np), {}});
+        bufs.push_back({h->damage, (size_t)(8 * np), {}});
+    }
+    bufs.push_back({h->bits, (size_t)(4 * h->n_slices * h->Q * 32), {}});
+    bufs.push_back({h->step_ctr, sizeof(int64_t), {}});
+    bufs.push_back({h->err, sizeof(int), {}});
+    for (Buf& b : bufs) {
+        b.keep.resize(b.bytes);
+        PD_CUDA(cudaMemcpy(b.keep.data(), b.dev, b.bytes, cudaMemcpyDeviceToHost), "save state");
+    }
+    auto restore = [&]() -> pd_status {
+        for (Buf& b : bufs)
+            PD_CUDA(cudaMemcpy(b.dev, b.keep.data(), b.bytes, cudaMemcpyHostToDevice),
+                    "restore state");
+        return PD_OK;
+    };
+    const int old_block = h->block, old_bps = h->blocks_per_sm;
+    const int64_t step0 = h->step;
+    cudaEvent_t e0, e1;
+    PD_CUDA(cudaEventCreate(&e0), "event");
+    PD_CUDA(cudaEventCreate(&e1), "event");
+    float best = 1e30f;
+    int best_block = old_block, best_bps = old_bps;
+    pd_status st = PD_OK;
+    h->drop_graph();
+    for (int block : {128, 256}) {
+        for (int bps = 1; bps <= 16 && st == PD_OK; ++bps) {
+            h->block = block;
+            if ((st = choose_grid(h, bps)) != PD_OK) break;
+            if ((st = restore()) != PD_OK) break;
+            cudaError_t e = launch_one(h, 0);
+            for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) e = launch_one(h, k + 1);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+            for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) e = launch_one(h, k + 1);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                st = cuda_fail(e, "autotune trial");
+                break;
+            }
+            if (ms < best) {
+                best = ms;
+                best_block = block;
+                best_bps = bps;
+            }
+            int occ = 0;
+            const void* fn = h->precision == 32
+                                 ? step_f32_kernel(h->sc_mode, h->uniform_vol, h->per_bond_c)
+                                 : step_f64_kernel(h->sc_mode);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block, 0);
+            if (bps >= occ) break;  // larger requests are capped to the same grid
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->block = st == PD_OK ? best_block : old_block;
+    h->blocks_per_sm = st == PD_OK ? best_bps : old_bps;
+    pd_status st2 = choose_grid(h, h->blocks_per_sm);
+    pd_status st3 = restore();
+    h->step = step0;
+    if (st != PD_OK) return st;
+    if (st2 != PD_OK) return st2;
+    if (st3 != PD_OK) return st3;
+    if (block_threads) *block_threads = h->block;
+    if (blocks_per_sm) *blocks_per_sm = h->blocks_per_sm;
+    return PD_OK;
+}
+
 pd_status pd_set_params(pd_handle* h, double c, double sc, double load, double disp_rate,
                         const double* c_bond)
 {
     if (!h) return fail(PD_ERR_ARG, "NULL handle");
+    if (h->batch) return fail(PD_ERR_STATE, "pd_set_params is not available on a batch handle");
     if (!(c > 0.0) || !std::isfinite(c)) return fail(PD_ERR_ARG, "c must be > 0");
     if (!(sc > 0.0) || !std::isfinite(sc)) return fail(PD_ERR_ARG, "sc must be > 0");
     if (!std::isfinite(load) || !std::isfinite(disp_rate))

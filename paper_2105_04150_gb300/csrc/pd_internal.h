@@ -45,7 +45,20 @@ struct BcClass {
     double force[3];   // body-force density per unit load
 };
 
+// Critical-stretch parameters of one instance of a batch.
+struct InstParams {
+    int32_t sc_mode;           // 0 constant, 1 per-bond draw
+    float fast_lo;             // (1 - 2 guard) * sc_lo (FP32 kernel fast path)
+    float w_const;             // c V of the instance when its volumes are uniform
+    float pad;
+    double sc, sc_lo, sc_hi;
+    uint64_t sc_seed;
+};
+
 struct StepArgsF32 {
+    const int32_t* inst;       // batch: instance of each node, or nullptr
+    const InstParams* itab;    // batch: per-instance s_c parameters
+    const int32_t* hid;        // batch: instance-local node id (key of the s_c draw)
     const float4* rec[2];      // 2 float4 (32 B) per node
     float4* lo32;              // owner-private full-precision l, 1 float4 per node
     const float* w;            // per-node weight w = c V (or V with per-bond c)
@@ -79,6 +92,9 @@ struct StepArgsF32 {
 };
 
 struct StepArgsF64 {
+    const int32_t* inst;       // batch: instance of each node, or nullptr
+    const InstParams* itab;
+    const int32_t* hid;
     const double* rec[2];      // 8 doubles per node
     double* v;
     const int32_t* nbr;

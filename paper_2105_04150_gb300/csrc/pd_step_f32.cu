@@ -190,10 +190,17 @@ __device__ __forceinline__ float bond_coef(const BondF32& b, float w)
     return w * b.num * rsqrtf(b.den * b.den * b.y2);
 }
 
+// weight c V of node j; with uniform weights (per instance in a batch: both ends
+// of a bond belong to the same instance) it is the lane's constant wc
 template <bool UW>
-__device__ __forceinline__ float node_w(const StepArgsF32& a, int64_t j)
+__device__ __forceinline__ float node_w(const StepArgsF32& a, int64_t j, float wc)
 {
-    return UW ? a.w_const : __ldg(a.w + j);
+    return UW ? wc : __ldg(a.w + j);
+}
+
+__device__ __forceinline__ float lane_wconst(const StepArgsF32& a, int64_t i)
+{
+    return a.inst != nullptr ? a.itab[a.inst[i]].w_const : a.w_const;
 }
 
 // A bond whose FP32 stretch reached the band just below the smallest s_c: the
@@ -213,11 +220,13 @@ __device__ __noinline__ float4 resolve_bond(const StepArgsF32& a, int cur, int64
     const NodeF32 ni = unpack(ai, bi), nj = unpack(aj, bj);
     const BondF32 b = bond_f32(ni, nj);
     double sc = a.sc;
-    float scf = a.sc_f;
-    if (SCM == 1) {
+    if (a.inst != nullptr) {  // batch: the instance's own parameters, local ids as keys
+        const InstParams& ip = a.itab[a.inst[i]];
+        sc = ip.sc_mode == 1 ? sc_draw(ip.sc_seed, ip.sc_lo, ip.sc_hi, a.hid[i], a.hid[j]) : ip.sc;
+    } else if (SCM == 1) {
         sc = sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i], a.gid[j]);
-        scf = (float)sc;
     }
+    const float scf = (float)sc;
     const float r = fmaf(-scf, b.den, b.num);  // den * (s - s_c)
     bool brk;
     if (fabsf(r) > a.guard * scf * b.den) {
@@ -240,7 +249,7 @@ __device__ __noinline__ float4 resolve_bond(const StepArgsF32& a, int cur, int64
     if (brk && a.has_nofail) brk = ((a.bct[a.bcc[i]].mask | a.bct[a.bcc[j]].mask) & 8u) == 0u;
     *broken = brk;
     if (brk) return make_float4(0.f, 0.f, 0.f, 0.f);
-    const float wv = node_w<UW>(a, j);
+    const float wv = node_w<UW>(a, j, UW ? lane_wconst(a, i) : 0.0f);
     float w = wv;
     if (a.cbond != nullptr) w *= a.cbond[slot];
     const float coef = bond_coef(b, w);
@@ -262,13 +271,16 @@ __global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS)
     const float4* __restrict__ R = a.rec[cur];
     float4* __restrict__ Rout = const_cast<float4*>(a.rec[cur ^ 1]);
     const float* __restrict__ cb = a.cbond;
-    const float fast_lo = a.fast_lo;
 
     for (int64_t g = wid; g < nslices; g += nwarps) {
         const int Wg = a.sw[g];
         const int32_t* __restrict__ col = a.nbr + g * W * 32 + lane;
         if (lane == 0) prefetch_l2(col, (uint32_t)(((Wg + 3) & ~3) * 128));
         const int64_t i = (g << 5) + lane;
+        // band just below the smallest s_c the node's bonds can have (per
+        // instance in a batch; both ends of a bond belong to the same instance)
+        const float fast_lo = a.inst != nullptr ? a.itab[a.inst[i]].fast_lo : a.fast_lo;
+        const float wc = UW ? lane_wconst(a, i) : 0.0f;
         float4 ai, bi;
         ld_rec(R + 2 * i, ai, bi);
         const NodeF32 ni = unpack(ai, bi);
@@ -315,7 +327,7 @@ __global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS)
                 // pending set once per chunk (pc & wb below)
                 const bool cand = bd.num >= fast_lo * bd.den;
                 pc |= cand ? (1u << u) : 0u;
-                float wj = node_w<UW>(a, jj[u]);
+                float wj = node_w<UW>(a, jj[u], wc);
                 const float wv = wj;
                 if (cb != nullptr) wj *= ld_f32(cb + (g * W + m0 + u) * 32 + lane);
                 float coef = bond_coef(bd, wj);
@@ -348,7 +360,7 @@ __global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS)
                 alive_count += __popc(nword);
             }
         }
-        if (UW) ws = a.w_const * (float)alive_count;
+        if (UW) ws = wc * (float)alive_count;
 
         // ---- integration of the lane's node (Eq. 11, damped Euler-Cromer)
         if (i < a.n) {

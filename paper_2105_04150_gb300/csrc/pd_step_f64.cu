@@ -93,9 +93,17 @@ __global__ void __launch_bounds__(256) k_step_f64(const StepArgsF64 a)
                     const double L = sqrt(ex * ex + ey * ey + ez * ez);
                     const double r = sqrt(yx * yx + yy * yy + yz * yz);
                     const double s = (r - L) / L;
-                    const double sc = (SCM == 0) ? a.sc
-                                                 : sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i],
-                                                           a.gid[jj[u]]);
+                    double sc;
+                    if (a.inst != nullptr) {  // batch: instance parameters, local ids as keys
+                        const InstParams& ip = a.itab[a.inst[i]];
+                        sc = ip.sc_mode == 1 ? sc_draw(ip.sc_seed, ip.sc_lo, ip.sc_hi, a.hid[i],
+                                                       a.hid[jj[u]])
+                                             : ip.sc;
+                    } else {
+                        sc = (SCM == 0) ? a.sc
+                                        : sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i],
+                                                  a.gid[jj[u]]);
+                    }
                     bool brk = s >= sc;
                     if (brk && a.has_nofail) brk = !pair_no_fail(a.bcc, a.bct, i, jj[u]);
                     if (brk) {

@@ -119,3 +119,18 @@ def test_binding_fails_loudly_without_library(monkeypatch):
     monkeypatch.setattr(pdgb._build, "LIB", "/nonexistent/_libpd.so")
     with pytest.raises(ImportError):
         pdgb.lib()
+
+
+def test_batch_create_rejects_bad_instances(L):
+    w = workloads.tensile_bar(6, 4, 4)
+    inst = pdgb.instance_from_workload(w, c=1e20)
+    bad = dict(inst, horizon=-1.0)
+    with pytest.raises(pdgb.PdError) as e:
+        pdgb.pd_batch_create([inst, bad], dt=1e-7, damping=0.0, density=2400.0)
+    assert e.value.name == "PD_ERR_ARG" and "instance 1" in str(e.value)
+    other = dict(inst, load=5.0)
+    with pytest.raises(pdgb.PdError) as e:
+        pdgb.pd_batch_create([inst, other], dt=1e-7, damping=0.0, density=2400.0)
+    assert "disp_rate and load" in str(e.value)
+    with pytest.raises(pdgb.PdError):
+        pdgb.pd_batch_create([inst], dt=0.0, damping=0.0, density=2400.0)

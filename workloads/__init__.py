@@ -231,12 +231,12 @@ def batch_instances(count: int = 256, n_lo: int = 2000, n_hi: int = 60000,
         K = float(math.exp(rng.normal(math.log(3e10), 0.2)))
         sc = float(math.exp(rng.normal(math.log(1e-4), 0.15)))
         if k % 2 == 0:
-            a = (target / 16.0) ** (1.0 / 3.0)
+            a = (target / 4.0) ** (1.0 / 3.0)   # 4a x a x a nodes
             nx, ny, nz = max(4, round(4 * a)), max(2, round(a)), max(2, round(a))
             w = tensile_bar(nx, ny, nz, dx=dx, rate=1e-9, slab=min(3, nx // 4), K=K, sc=sc,
                             steps=2000)
         else:
-            a = (target / 25.0) ** (1.0 / 3.0)
+            a = (target / 5.0) ** (1.0 / 3.0)   # 5a x a x a nodes
             nx, ny, nz = max(5, round(5 * a)), max(2, round(a)), max(2, round(a))
             w = notched_beam(nx, ny, nz, length=nx * dx, rate=1e-9, K=K, steps=2000,
                              horizon_factor=3.01)
