@@ -410,3 +410,92 @@ void or_energy_density(const or_model* m, const double* u, const uint8_t* mu, do
         W[r] = acc;
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* Reverse mode of the damped Euler-Cromer recurrence with the bond flags mu
+ * frozen (no bond changes state during the run).  Forward, for free components:
+ *   F^n = sum_j c_ij mu_ij s_ij V_j y_ij/|y_ij| + load * force_i      (Eqs. 5, 10)
+ *   v^{n+1} = v^n + dt (F^n - eta v^n) / rho,  u^{n+1} = u^n + dt v^{n+1}
+ * and controlled components are overwritten by the prescribed ramp.  With
+ * ubar, vbar the adjoints of u^{n+1}, v^{n+1} (controlled components zeroed):
+ *   w = vbar + dt ubar
+ *   ubar^n = ubar + (dt/rho) (J^T w),  vbar^n = (1 - dt eta/rho) w
+ *   (J^T w)_m = sum_{j in H_m} c_mj mu_mj K_mj (V_m w_j - V_j w_m),
+ *   K = (1/L - 1/r) I + y y^T / r^3   (L = |xi|, r = |y|; d/dy of s y/|y|)
+ *   dL/dc[m->j] += (dt/rho) mu s V_j (y/r).w_m   (c of the directed entry m->j,
+ *              which only enters F_m; an undirected bond's sensitivity is the
+ *              sum over its two directed entries)
+ *   dL/dload += (dt/rho) sum_m force_m . w_m
+ * All nodes must be rows (m->rows == NULL).  Stores every u^n (small cases). */
+void or_adjoint(const or_model* m, int64_t first_step, int64_t nsteps, const double* u0,
+                const double* v0, const uint8_t* mu, const double* dLdu, const double* dLdv,
+                double* dLdc, double* dLdload, double* dLdu0, double* dLdv0)
+{
+    const int64_t n = m->n, n3 = 3 * n;
+    double* U = (double*)malloc((size_t)(nsteps + 1) * n3 * sizeof(double) + 8);
+    double* v = (double*)malloc((size_t)n3 * sizeof(double) + 8);
+    double* u2 = (double*)malloc((size_t)n3 * sizeof(double) + 8);
+    double* v2 = (double*)malloc((size_t)n3 * sizeof(double) + 8);
+    uint8_t* muc = (uint8_t*)malloc((size_t)(m->off[n] > 0 ? m->off[n] : 1));
+    memcpy(U, u0, (size_t)n3 * sizeof(double));
+    memcpy(v, v0, (size_t)n3 * sizeof(double));
+    for (int64_t k = 0; k < nsteps; ++k) {
+        memcpy(muc, mu, (size_t)m->off[n]);
+        or_step(m, first_step + k, U + k * n3, v, muc, NULL, u2, v2, NULL);
+        memcpy(U + (k + 1) * n3, u2, (size_t)n3 * sizeof(double));
+        memcpy(v, v2, (size_t)n3 * sizeof(double));
+    }
+    double* ub = (double*)malloc((size_t)n3 * sizeof(double) + 8);
+    double* vb = (double*)malloc((size_t)n3 * sizeof(double) + 8);
+    double* w = (double*)malloc((size_t)n3 * sizeof(double) + 8);
+    memcpy(ub, dLdu, (size_t)n3 * sizeof(double));
+    for (int64_t e = 0; e < n3; ++e) vb[e] = dLdv ? dLdv[e] : 0.0;
+    for (int64_t k = 0; k < m->off[n]; ++k) dLdc[k] = 0.0;
+    double gload = 0.0;
+    const double dr = m->dt / m->density, a = 1.0 - m->dt * m->damping / m->density;
+    for (int64_t k = nsteps - 1; k >= 0; --k) {
+        const double* u = U + k * n3; /* u^k: the state the step k -> k+1 reads */
+        for (int64_t e = 0; e < n3; ++e) {
+            if (m->bc_type[e] == 1) {
+                ub[e] = 0.0;
+                vb[e] = 0.0;
+            }
+            w[e] = vb[e] + m->dt * ub[e];
+        }
+        if (m->bc_force)
+            for (int64_t e = 0; e < n3; ++e) gload += dr * m->bc_force[e] * w[e];
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) {
+            double acc[3] = {0.0, 0.0, 0.0};
+            for (int64_t q = m->off[i]; q < m->off[i + 1]; ++q) {
+                if (!mu[q]) continue;
+                const int64_t j = m->idx[q];
+                double xi[3], y[3], d[3];
+                for (int c = 0; c < 3; ++c) {
+                    xi[c] = m->x[3 * j + c] - m->x[3 * i + c];
+                    y[c] = xi[c] + u[3 * j + c] - u[3 * i + c];
+                    d[c] = m->vol[i] * w[3 * j + c] - m->vol[j] * w[3 * i + c];
+                }
+                const double L = sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
+                const double r = sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+                const double s = (r - L) / L;
+                const double yd = y[0] * d[0] + y[1] * d[1] + y[2] * d[2];
+                const double cij = m->c_bond ? m->c_bond[q] : m->c;
+                for (int c = 0; c < 3; ++c)
+                    acc[c] += cij * ((1.0 / L - 1.0 / r) * d[c] + y[c] * yd / (r * r * r));
+                const double yw = y[0] * w[3 * i] + y[1] * w[3 * i + 1] + y[2] * w[3 * i + 2];
+                dLdc[q] += dr * s * m->vol[j] * yw / r;
+            }
+            for (int c = 0; c < 3; ++c) {
+                u2[3 * i + c] = ub[3 * i + c] + dr * acc[c];
+                v2[3 * i + c] = a * w[3 * i + c];
+            }
+        }
+        memcpy(ub, u2, (size_t)n3 * sizeof(double));
+        memcpy(vb, v2, (size_t)n3 * sizeof(double));
+    }
+    if (dLdload) *dLdload = gload;
+    if (dLdu0) memcpy(dLdu0, ub, (size_t)n3 * sizeof(double));
+    if (dLdv0) memcpy(dLdv0, vb, (size_t)n3 * sizeof(double));
+    free(U); free(v); free(u2); free(v2); free(muc); free(ub); free(vb); free(w);
+}
