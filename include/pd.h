@@ -194,6 +194,32 @@ pd_status pd_set_params(pd_handle* h, double c, double sc, double load, double d
                         const double* c_bond);
 
 /* ---------------------------------------------------------------------------
+ * Sensitivities (outer-loop use, Section 3.6): the gradient of a loss of the
+ * final state with respect to every directed bond's stiffness, the body-force
+ * load and the initial state, by a hand-written reverse sweep of the damped
+ * Euler-Cromer recurrence.  FP64 handles only (PD_ERR_STATE otherwise), not
+ * batch handles.
+ *
+ * pd_adjoint_forward - advance n_steps (>= 1) from the current state with the
+ *   bond flags frozen (no bond breaks, so the run is a smooth function of the
+ *   parameters) and record (u, v) every checkpoint_every steps (0 = ceil(sqrt(
+ *   n_steps))) on the device.  Afterwards the state is u^N, v^N as for pd_step.
+ *   Device memory: ceil(N/C) * 48 B + C * 24 B per node.
+ *
+ * pd_adjoint_backward - given dL/du^N and dL/dv^N (n*3 doubles, host or device;
+ *   dLdv may be NULL = 0) of the last pd_adjoint_forward, run the reverse sweep
+ *   (each segment of C steps is recomputed forward from its checkpoint) and
+ *   write any of: dL_dc (host, per directed bond in canonical order: the
+ *   derivative with respect to the stiffness of the entry i->j, which enters
+ *   only F_i; an undirected bond's sensitivity is the sum of its two entries),
+ *   dL_dload (host scalar), dL_du0 / dL_dv0 (n*3, host or device).  The handle's
+ *   state is left at u^N, v^N.  PD_ERR_STATE without a recorded forward.
+ */
+pd_status pd_adjoint_forward(pd_handle* h, int64_t n_steps, int64_t checkpoint_every);
+pd_status pd_adjoint_backward(pd_handle* h, const double* dLdu, const double* dLdv,
+                              double* dL_dc, double* dL_dload, double* dL_du0, double* dL_dv0);
+
+/* ---------------------------------------------------------------------------
  * Batched multi-instance form (outer-loop use: sensitivity, uncertainty
  * quantification, optimisation; Section 3.6 "Running simulations").
  */

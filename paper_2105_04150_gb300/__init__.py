@@ -24,7 +24,8 @@ __all__ = [
     "PdError", "build", "lib", "pd_micromodulus", "pd_create", "pd_destroy", "pd_last_error",
     "pd_get_info", "pd_get_family", "pd_step", "pd_sync", "pd_get_state", "pd_set_state",
     "pd_get_bonds", "pd_set_bonds", "pd_damage", "pd_set_params", "pd_batch_create",
-    "pd_batch_offsets", "pd_autotune", "instance_from_workload", "Model",
+    "pd_batch_offsets", "pd_autotune", "pd_adjoint_forward", "pd_adjoint_backward",
+    "instance_from_workload", "Model",
     "PD_PREC_F32", "PD_PREC_F64",
 ]
 
@@ -108,6 +109,8 @@ def lib():
             "pd_batch_create": [I32, P, P, P],
             "pd_batch_offsets": [P, P, P],
             "pd_autotune": [P, I32, P, P],
+            "pd_adjoint_forward": [P, I64, I64],
+            "pd_adjoint_backward": [P, P, P, P, P, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -336,6 +339,29 @@ def pd_autotune(h: int, trial_steps: int = 20):
     b, s = ctypes.c_int32(), ctypes.c_int32()
     _check(lib().pd_autotune(h, int(trial_steps), ctypes.byref(b), ctypes.byref(s)))
     return b.value, s.value
+
+
+def pd_adjoint_forward(h: int, n_steps: int, checkpoint_every: int = 0) -> None:
+    """Advance n_steps with frozen bond flags, recording checkpoints for the adjoint."""
+    _check(lib().pd_adjoint_forward(h, int(n_steps), int(checkpoint_every)))
+
+
+def pd_adjoint_backward(h: int, dLdu, dLdv=None, want_c: bool = True):
+    """Reverse sweep of the last pd_adjoint_forward.
+
+    Returns (dL/dc per directed bond in canonical order or None, dL/dload,
+    dL/du0, dL/dv0) as numpy arrays (n x 3 for the state gradients)."""
+    info = pd_get_info(h)
+    n, nb = info["n"], info["n_bonds"]
+    up, ku = _ptr(dLdu, np.float64, 3 * n)
+    vp, kv = _ptr(dLdv, np.float64, 3 * n if dLdv is not None else None)
+    gc = np.zeros(max(nb, 1)) if want_c else None
+    gl = ctypes.c_double()
+    gu = np.empty((n, 3))
+    gv = np.empty((n, 3))
+    _check(lib().pd_adjoint_backward(h, up, vp, None if gc is None else gc.ctypes.data,
+                                     ctypes.byref(gl), gu.ctypes.data, gv.ctypes.data))
+    return (None if gc is None else gc[:nb]), gl.value, gu, gv
 
 
 def instance_from_workload(w, c=None) -> dict:

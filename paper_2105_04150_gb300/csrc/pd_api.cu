@@ -118,6 +118,18 @@ struct pd_handle {
     int* err = nullptr;
     int64_t* step_ctr = nullptr;
     double* staging = nullptr;  // 3n doubles for host transfers
+    // adjoint: frozen bond flags during its forward runs, and the recorded run
+    bool frozen = false;
+    struct Tape {
+        bool valid = false;
+        int64_t N = 0, C = 0, nck = 0, step0 = 0;
+        double *ck_u = nullptr, *ck_v = nullptr, *seg = nullptr, *fin_u = nullptr,
+               *fin_v = nullptr;
+        int64_t cap_ck = 0, cap_seg = 0;
+        double *ub[2] = {nullptr, nullptr}, *vb[2] = {nullptr, nullptr}, *ubm = nullptr,
+               *w = nullptr, *gc = nullptr, *gl = nullptr, *partial = nullptr, *out = nullptr;
+        int n_partial = 0;
+    } tape;
     // batches: instance of each node, instance-local ids, per-instance s_c table
     bool batch = false;
     std::vector<int64_t> inst_off;
@@ -234,6 +246,7 @@ StepArgsF64 args_f64(pd_handle* h, int k)
     a.k = k;
     a.Q = h->Q;
     a.has_nofail = h->has_nofail ? 1 : 0;
+    a.frozen = h->frozen ? 1 : 0;
     a.sc = h->sc;
     a.sc_lo = h->sc_lo;
     a.sc_hi = h->sc_hi;
@@ -955,6 +968,224 @@ pd_status pd_damage(pd_handle* h, double* phi)
     if (!dev)
         PD_CUDA(cudaMemcpyAsync(phi, h->staging, 8 * h->n, cudaMemcpyDeviceToHost, h->stream),
                 "copy damage");
+    return check_dev_err(h);
+}
+
+pd_status pd_adjoint_forward(pd_handle* h, int64_t n_steps, int64_t checkpoint_every)
+{
+    if (!h) return fail(PD_ERR_ARG, "NULL handle");
+    if (h->precision != 64 || h->batch)
+        return fail(PD_ERR_STATE, "the adjoint is available on FP64 single-model handles");
+    if (n_steps < 1 || checkpoint_every < 0)
+        return fail(PD_ERR_ARG, "need n_steps >= 1 and checkpoint_every >= 0");
+    PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    auto& T = h->tape;
+    int64_t C = checkpoint_every > 0 ? std::min(checkpoint_every, n_steps)
+                                     : (int64_t)std::ceil(std::sqrt((double)n_steps));
+    C = std::max<int64_t>(1, C);
+    const int64_t nck = (n_steps + C - 1) / C;
+    const int64_t np3 = 3 * h->n_pad;
+    cudaError_t e;
+    if (T.cap_ck < nck) {
+        if ((e = h->alloc(&T.ck_u, (size_t)(nck * np3))) != cudaSuccess ||
+            (e = h->alloc(&T.ck_v, (size_t)(nck * np3))) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc checkpoints");
+        T.cap_ck = nck;
+    }
+    if (T.cap_seg < C) {
+        if ((e = h->alloc(&T.seg, (size_t)(C * np3))) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc segment");
+        T.cap_seg = C;
+    }
+    if (!T.fin_u) {
+        if ((e = h->alloc(&T.fin_u, (size_t)np3)) != cudaSuccess ||
+            (e = h->alloc(&T.fin_v, (size_t)np3)) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc final state");
+    }
+    T.valid = false;
+    h->frozen = true;
+    h->drop_graph();
+    const int64_t step0 = h->step;
+    for (int64_t k = 0; k < n_steps; k += C) {
+        const int cur = (int)(h->step & 1);
+        PD_CUDA(launch_extract_u(h->rec[cur], h->n_pad, T.ck_u + (k / C) * np3, h->stream),
+                "checkpoint u");
+        PD_CUDA(cudaMemcpyAsync(T.ck_v + (k / C) * np3, h->v, 8 * np3, cudaMemcpyDeviceToDevice,
+                                h->stream),
+                "checkpoint v");
+        pd_status st = pd_step(h, std::min(C, n_steps - k));
+        if (st != PD_OK) {
+            h->frozen = false;
+            h->drop_graph();
+            return st;
+        }
+    }
+    const int cur = (int)(h->step & 1);
+    PD_CUDA(launch_extract_u(h->rec[cur], h->n_pad, T.fin_u, h->stream), "final u");
+    PD_CUDA(cudaMemcpyAsync(T.fin_v, h->v, 8 * np3, cudaMemcpyDeviceToDevice, h->stream),
+            "final v");
+    h->frozen = false;
+    h->drop_graph();
+    T.N = n_steps;
+    T.C = C;
+    T.nck = nck;
+    T.step0 = step0;
+    T.valid = true;
+    return check_dev_err(h);
+}
+
+pd_status pd_adjoint_backward(pd_handle* h, const double* dLdu, const double* dLdv,
+                              double* dL_dc, double* dL_dload, double* dL_du0, double* dL_dv0)
+{
+    if (!h) return fail(PD_ERR_ARG, "NULL handle");
+    auto& T = h->tape;
+    if (!T.valid) return fail(PD_ERR_STATE, "no recorded adjoint forward run");
+    if (!dLdu) return fail(PD_ERR_ARG, "dLdu is required");
+    PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    const int64_t np3 = 3 * h->n_pad;
+    const int64_t slots = h->n_slices * 32LL * h->Q * 32;
+    cudaError_t e;
+    if (!T.w) {
+        if ((e = h->alloc(&T.ub[0], (size_t)np3)) != cudaSuccess ||
+            (e = h->alloc(&T.ub[1], (size_t)np3)) != cudaSuccess ||
+            (e = h->alloc(&T.vb[0], (size_t)np3)) != cudaSuccess ||
+            (e = h->alloc(&T.vb[1], (size_t)np3)) != cudaSuccess ||
+            (e = h->alloc(&T.ubm, (size_t)np3)) != cudaSuccess ||
+            (e = h->alloc(&T.w, (size_t)np3)) != cudaSuccess ||
+            (e = h->alloc(&T.gc, (size_t)slots)) != cudaSuccess ||
+            (e = h->alloc(&T.gl, (size_t)h->n_pad)) != cudaSuccess ||
+            (e = h->alloc(&T.out, 1)) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc adjoint buffers");
+        T.n_partial = sum_partials_needed(h->n);
+        if ((e = h->alloc(&T.partial, (size_t)T.n_partial)) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc reduction scratch");
+    }
+    // seed: dL/du^N, dL/dv^N in library order
+    auto to_lib = [&](const double* src, double* dst) -> pd_status {
+        if (!src) {
+            PD_CUDA(cudaMemsetAsync(dst, 0, 8 * np3, h->stream), "memset");
+            return PD_OK;
+        }
+        const double* s = src;
+        if (!is_device_ptr(src)) {
+            PD_CUDA(cudaMemcpyAsync(h->staging, src, 24 * h->n, cudaMemcpyHostToDevice, h->stream),
+                    "copy gradient to device");
+            s = h->staging;
+        }
+        PD_CUDA(launch_to_lib3(s, h->gid, h->n, dst, h->stream), "reorder");
+        PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
+        return PD_OK;
+    };
+    pd_status st;
+    PD_CUDA(cudaMemsetAsync(T.ub[0], 0, 8 * np3, h->stream), "memset");
+    PD_CUDA(cudaMemsetAsync(T.vb[0], 0, 8 * np3, h->stream), "memset");
+    if ((st = to_lib(dLdu, T.ub[0])) != PD_OK || (st = to_lib(dLdv, T.vb[0])) != PD_OK) return st;
+    PD_CUDA(cudaMemsetAsync(T.gc, 0, 8 * slots, h->stream), "memset");
+    PD_CUDA(cudaMemsetAsync(T.gl, 0, 8 * h->n_pad, h->stream), "memset");
+
+    int sms = 0;
+    PD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "sm count");
+    const int agrid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8,
+                                                                  (h->n_slices + 7) / 8));
+    AdjArgs A{};
+    A.x64 = h->x64;
+    A.nbr = h->nbr;
+    A.bits = h->bits;
+    A.sw = h->sw;
+    A.Q = h->Q;
+    A.vol = h->vol;
+    A.cbond = h->per_bond_c ? (const double*)h->cbond : nullptr;
+    A.c = h->c;
+    A.gc = T.gc;
+    A.gl = T.gl;
+    A.bcc = h->bcc;
+    A.bct = h->bct;
+    A.dt_rho = h->dt / h->rho;
+    A.damp = 1.0 - h->dt * h->eta / h->rho;
+    A.n = h->n;
+
+    h->frozen = true;
+    h->drop_graph();
+    int cb = 0;
+    cudaError_t ke = cudaSuccess;
+    for (int64_t k = T.nck - 1; k >= 0 && ke == cudaSuccess; --k) {
+        const int64_t start = k * T.C;
+        const int64_t len = std::min(T.C, T.N - start);
+        // recompute u^start .. u^{start+len-1} from checkpoint k
+        h->step = T.step0 + start;
+        ke = cudaMemcpyAsync(h->step_ctr, &h->step, sizeof(int64_t), cudaMemcpyHostToDevice,
+                             h->stream);
+        if (ke == cudaSuccess) ke = cudaStreamSynchronize(h->stream);
+        const int cur = (int)(h->step & 1);
+        if (ke == cudaSuccess) ke = launch_insert_u(T.ck_u + k * np3, h->n_pad, h->rec[cur], h->stream);
+        if (ke == cudaSuccess)
+            ke = cudaMemcpyAsync(h->v, T.ck_v + k * np3, 8 * np3, cudaMemcpyDeviceToDevice, h->stream);
+        if (ke == cudaSuccess)
+            ke = cudaMemcpyAsync(T.seg, T.ck_u + k * np3, 8 * np3, cudaMemcpyDeviceToDevice, h->stream);
+        for (int64_t t = 1; t < len && ke == cudaSuccess; ++t) {
+            ke = launch_one(h, 0);
+            if (ke == cudaSuccess) ke = launch_advance(h->step_ctr, 1, h->stream);
+            h->step += 1;
+            if (ke == cudaSuccess)
+                ke = launch_extract_u(h->rec[h->step & 1], h->n_pad, T.seg + t * np3, h->stream);
+        }
+        // reverse through the segment
+        for (int64_t t = len - 1; t >= 0 && ke == cudaSuccess; --t) {
+            ke = launch_adj_mask(T.ub[cb], T.vb[cb], h->bcc, h->bct, h->n_pad, h->dt, T.ubm, T.w,
+                                 h->stream);
+            A.un = T.seg + t * np3;
+            A.w = T.w;
+            A.ubm = T.ubm;
+            A.ub_out = T.ub[cb ^ 1];
+            A.vb_out = T.vb[cb ^ 1];
+            if (ke == cudaSuccess) ke = launch_adj_step(A, agrid, 256, h->stream);
+            cb ^= 1;
+        }
+    }
+    h->frozen = false;
+    h->drop_graph();
+    // restore the final state u^N, v^N
+    h->step = T.step0 + T.N;
+    if (ke == cudaSuccess)
+        ke = cudaMemcpyAsync(h->step_ctr, &h->step, sizeof(int64_t), cudaMemcpyHostToDevice,
+                             h->stream);
+    if (ke == cudaSuccess) ke = cudaStreamSynchronize(h->stream);
+    if (ke == cudaSuccess) ke = launch_insert_u(T.fin_u, h->n_pad, h->rec[h->step & 1], h->stream);
+    if (ke == cudaSuccess)
+        ke = cudaMemcpyAsync(h->v, T.fin_v, 8 * np3, cudaMemcpyDeviceToDevice, h->stream);
+    h->damage_fresh = false;
+    if (ke != cudaSuccess) return cuda_fail(ke, "adjoint sweep");
+
+    // outputs
+    if (dL_dload) {
+        PD_CUDA(launch_sum(T.gl, h->n, A.dt_rho, T.partial, T.n_partial, T.out, h->stream),
+                "load gradient");
+        PD_CUDA(cudaMemcpyAsync(dL_dload, T.out, sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+                "copy load gradient");
+    }
+    auto from_lib = [&](const double* src, double* dst) -> pd_status {
+        if (!dst) return PD_OK;
+        const bool dev = is_device_ptr(dst);
+        double* o = dev ? dst : h->staging;
+        PD_CUDA(launch_from_lib3(src, h->gid, h->n, o, h->stream), "reorder");
+        if (!dev)
+            PD_CUDA(cudaMemcpyAsync(dst, h->staging, 24 * h->n, cudaMemcpyDeviceToHost, h->stream),
+                    "copy gradient to host");
+        PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
+        return PD_OK;
+    };
+    if ((st = from_lib(T.ub[cb], dL_du0)) != PD_OK || (st = from_lib(T.vb[cb], dL_dv0)) != PD_OK)
+        return st;
+    if (dL_dc) {
+        std::vector<double> g((size_t)slots);
+        PD_CUDA(cudaMemcpyAsync(g.data(), T.gc, 8 * slots, cudaMemcpyDeviceToHost, h->stream),
+                "copy stiffness gradient");
+        PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
+        std::vector<int64_t> pos;
+        if ((st = canonical_slots(h, pos)) != PD_OK) return st;
+        for (size_t s = 0; s < pos.size(); ++s)
+            if (pos[s] >= 0) dL_dc[pos[s]] = g[s];
+    }
     return check_dev_err(h);
 }
 

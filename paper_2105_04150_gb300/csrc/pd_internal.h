@@ -100,6 +100,8 @@ struct StepArgsF64 {
     const int32_t* nbr;
     uint32_t* bits;
     const int32_t* sw;
+    int32_t frozen;            // 1: no bond breaks (the adjoint's forward runs)
+    int32_t pad1;
     const double* cbond;
     const uint8_t* bcc;
     const BcClass* bct;
@@ -117,6 +119,47 @@ struct StepArgsF64 {
     uint64_t sc_seed;
     double dt, eta, rho, disp_rate, load;
 };
+
+// Arguments of one reverse step of the FP64 adjoint (pd_adjoint.cu); node arrays
+// in library order, n_pad entries.
+struct AdjArgs {
+    const double* x64;         // reference positions (3 per node)
+    const double* un;          // u^n, the state the forward step n -> n+1 read
+    const double* w;           // vbar + dt ubar (controlled components zeroed)
+    const double* ubm;         // ubar of step n+1, controlled components zeroed
+    double* ub_out;            // ubar^n
+    double* vb_out;            // vbar^n
+    const int32_t* nbr;
+    const uint32_t* bits;      // frozen bond flags
+    const int32_t* sw;
+    int32_t Q;
+    int32_t pad0;
+    const double* vol;         // volumes V
+    const double* cbond;       // per-slot stiffness, or nullptr for the constant c
+    double c;
+    double* gc;                // per-slot dL/dc accumulator
+    double* gl;                // per-node accumulator of force . w
+    const uint8_t* bcc;
+    const BcClass* bct;
+    double dt_rho;             // dt / rho
+    double damp;               // 1 - dt eta / rho
+    int64_t n;
+};
+
+cudaError_t launch_adj_mask(const double* ub, const double* vb, const uint8_t* bcc,
+                            const BcClass* bct, int64_t n, double dt, double* ubm, double* w,
+                            cudaStream_t s);
+cudaError_t launch_adj_step(const AdjArgs& a, int grid, int block, cudaStream_t s);
+cudaError_t launch_extract_u(const double* rec, int64_t n, double* u, cudaStream_t s);
+cudaError_t launch_insert_u(const double* u, int64_t n, double* rec, cudaStream_t s);
+cudaError_t launch_to_lib3(const double* in, const int32_t* gid, int64_t n, double* out,
+                           cudaStream_t s);
+cudaError_t launch_from_lib3(const double* in, const int32_t* gid, int64_t n, double* out,
+                             cudaStream_t s);
+// deterministic two-pass sum: out = scale * sum(x[0..n)); partial holds n_partial doubles
+int sum_partials_needed(int64_t n);
+cudaError_t launch_sum(const double* x, int64_t n, double scale, double* partial, int n_partial,
+                       double* out, cudaStream_t s);
 
 // ---- step kernels (pd_step_f32.cu / pd_step_f64.cu) --------------------------
 cudaError_t launch_step_f32(const StepArgsF32& a, int sc_mode, int grid, int block,

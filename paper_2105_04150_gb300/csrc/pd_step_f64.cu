@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(256) k_step_f64(const StepArgsF64 a)
                                         : sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i],
                                                   a.gid[jj[u]]);
                     }
-                    bool brk = s >= sc;
+                    bool brk = !a.frozen && s >= sc;
                     if (brk && a.has_nofail) brk = !pair_no_fail(a.bcc, a.bct, i, jj[u]);
                     if (brk) {
                         nword &= ~(1u << (b0 + u));
