@@ -219,6 +219,38 @@ pd_status pd_adjoint_forward(pd_handle* h, int64_t n_steps, int64_t checkpoint_e
 pd_status pd_adjoint_backward(pd_handle* h, const double* dLdu, const double* dLdv,
                               double* dL_dc, double* dL_dload, double* dL_du0, double* dL_dv0);
 
+/*
+ * pd_adjoint_backward_static - the same reverse sweep, arguments, outputs and
+ * errors as pd_adjoint_backward (dL_dc may here also be a device pointer), for
+ * callers that cannot allocate device memory when they need the gradient: code
+ * whose device memory is owned by another allocator (a framework's memory pool
+ * that has reserved the device), and code that must not trigger the implicit
+ * device synchronisation that cudaMalloc / cudaFree may cause.  The paper has no
+ * counterpart; it is a deployment variant of the entry point above.
+ *
+ * It allocates nothing: the reverse sweep's working memory (adjoint vectors,
+ * per-slot stiffness gradients, the reduction partials of dL_dload, the
+ * canonical family for the dL_dc scatter) is carved from one file-scope device
+ * array of PD_STATIC_SCRATCH_BYTES (64 MiB) per device, instead of the buffers
+ * pd_adjoint_backward allocates on its first call and keeps in the handle.  The
+ * array occupies that much device memory wherever the library's device code is
+ * loaded.  A model needing more (about 152 B per node + 8 B per SELL slot + 12 B
+ * per directed bond, + 8 B per bond when dL_dc is host memory) gets PD_ERR_ARG
+ * with the required size in pd_last_error().  The recorded forward run
+ * (pd_adjoint_forward, which does allocate) must exist: PD_ERR_STATE otherwise.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and caches it; make that
+ * first call before any stream capture.  Every call, from every handle on the
+ * device, shares the one array: each call clears the part it uses before use,
+ * and calls whose GPU work overlaps (on different streams, or from different
+ * host threads) race on it and give wrong results; serialise them.
+ */
+#define PD_STATIC_SCRATCH_BYTES (64u << 20)
+pd_status pd_adjoint_backward_static(pd_handle* h, const double* dLdu, const double* dLdv,
+                                     double* dL_dc, double* dL_dload, double* dL_du0,
+                                     double* dL_dv0);
+
 /* ---------------------------------------------------------------------------
  * Batched multi-instance form (outer-loop use: sensitivity, uncertainty
  * quantification, optimisation; Section 3.6 "Running simulations").

@@ -25,6 +25,7 @@ __all__ = [
     "pd_get_info", "pd_get_family", "pd_step", "pd_sync", "pd_get_state", "pd_set_state",
     "pd_get_bonds", "pd_set_bonds", "pd_damage", "pd_set_params", "pd_batch_create",
     "pd_batch_offsets", "pd_autotune", "pd_adjoint_forward", "pd_adjoint_backward",
+    "pd_adjoint_backward_static",
     "instance_from_workload", "Model",
     "PD_PREC_F32", "PD_PREC_F64",
 ]
@@ -111,6 +112,7 @@ def lib():
             "pd_autotune": [P, I32, P, P],
             "pd_adjoint_forward": [P, I64, I64],
             "pd_adjoint_backward": [P, P, P, P, P, P, P],
+            "pd_adjoint_backward_static": [P, P, P, P, P, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -361,6 +363,24 @@ def pd_adjoint_backward(h: int, dLdu, dLdv=None, want_c: bool = True):
     gv = np.empty((n, 3))
     _check(lib().pd_adjoint_backward(h, up, vp, None if gc is None else gc.ctypes.data,
                                      ctypes.byref(gl), gu.ctypes.data, gv.ctypes.data))
+    return (None if gc is None else gc[:nb]), gl.value, gu, gv
+
+
+def pd_adjoint_backward_static(h: int, dLdu, dLdv=None, want_c: bool = True):
+    """pd_adjoint_backward through the entry point that allocates no device memory
+    (its working memory is a fixed static device array shared by all calls on a
+    device; models above PD_STATIC_SCRATCH_BYTES of scratch raise PD_ERR_ARG).
+    Same returns as pd_adjoint_backward."""
+    info = pd_get_info(h)
+    n, nb = info["n"], info["n_bonds"]
+    up, ku = _ptr(dLdu, np.float64, 3 * n)
+    vp, kv = _ptr(dLdv, np.float64, 3 * n if dLdv is not None else None)
+    gc = np.zeros(max(nb, 1)) if want_c else None
+    gl = ctypes.c_double()
+    gu = np.empty((n, 3))
+    gv = np.empty((n, 3))
+    _check(lib().pd_adjoint_backward_static(h, up, vp, None if gc is None else gc.ctypes.data,
+                                            ctypes.byref(gl), gu.ctypes.data, gv.ctypes.data))
     return (None if gc is None else gc[:nb]), gl.value, gu, gv
 
 

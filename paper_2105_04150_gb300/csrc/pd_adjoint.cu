@@ -190,6 +190,34 @@ __global__ void __launch_bounds__(kRedBlock) k_sum_final(const double* __restric
     if (threadIdx.x == 0) *out = scale * s;
 }
 
+// canonical position of each used SELL slot of library node p: row gid[p] of
+// the canonical family (sorted ids), found by binary search for the caller id
+// of the slot's neighbour; out[position] = slot value
+__global__ void k_slots_to_canonical(const double* __restrict__ val, const int32_t* __restrict__ nbr,
+                                     const int32_t* __restrict__ gid, const int64_t* __restrict__ off,
+                                     const int32_t* __restrict__ idx, int64_t n, int Q,
+                                     double* __restrict__ out)
+{
+    const int64_t W = 32LL * Q;
+    GRID_STRIDE(p, n)
+    {
+        const int64_t g = p >> 5, l = p & 31;
+        const int64_t i = gid[p];
+        const int64_t b = off[i], cnt = off[i + 1] - b;
+        for (int64_t m = 0; m < cnt; ++m) {
+            const int64_t slot = (g * W + m) * 32 + l;
+            const int32_t j = gid[nbr[slot]];
+            int64_t lo = 0, hi = cnt;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (idx[b + mid] < j) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo < cnt) out[b + lo] = val[slot];
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_adj_mask(const double* ub, const double* vb, const uint8_t* bcc,
@@ -242,6 +270,15 @@ cudaError_t launch_sum(const double* x, int64_t n, double scale, double* partial
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_sum_final<<<1, kRedBlock, 0, s>>>(partial, n_partial, scale, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slots_to_canonical(const double* val, const int32_t* nbr, const int32_t* gid,
+                                      const int64_t* off, const int32_t* idx, int64_t n, int Q,
+                                      double* out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_slots_to_canonical<<<grid_for(n, 128), 128, 0, s>>>(val, nbr, gid, off, idx, n, Q, out);
     return cudaGetLastError();
 }
 

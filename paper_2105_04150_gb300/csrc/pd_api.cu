@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "../../include/pd.h"
@@ -1342,6 +1343,221 @@ pd_status pd_set_params(pd_handle* h, double c, double sc, double load, double d
     PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
     h->damage_fresh = false;
     return PD_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// pd_adjoint_backward_static: the reverse sweep with its working memory in one
+// file-scope device array, for callers that cannot allocate device memory.
+// Calls share the array; overlapping calls race (documented in pd.h).
+
+static __device__ __align__(256) unsigned char pd_static_scratch[PD_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+unsigned char* g_static_ptr[kStaticMaxDevices] = {};
+
+// device address of pd_static_scratch on `device` (current), looked up once
+pd_status static_scratch(int device, unsigned char** out)
+{
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (device < 0 || device >= kStaticMaxDevices)
+        return fail(PD_ERR_ARG, "static scratch: device %d out of range", device);
+    if (!g_static_ptr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, pd_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+        g_static_ptr[device] = (unsigned char*)p;
+    }
+    *out = g_static_ptr[device];
+    return PD_OK;
+}
+
+// the sweep's buffers, carved at 256-byte boundaries from `base` (nullptr: sizing only)
+struct StaticBufs {
+    double *ub[2], *vb[2], *ubm, *w, *gl, *gc, *partial, *out, *dc;
+    int64_t* off;
+    int32_t* idx;
+};
+
+size_t carve_static(unsigned char* base, int64_t np3, int64_t n_pad, int64_t slots, int n_partial,
+                    int64_t n, int64_t n_bonds, bool want_c, bool c_host, StaticBufs& b)
+{
+    size_t used = 0;
+    auto take = [&](size_t bytes) -> unsigned char* {
+        const size_t at = (used + 255) & ~(size_t)255;
+        used = at + std::max<size_t>(bytes, 8);
+        return base ? base + at : nullptr;
+    };
+    for (int k = 0; k < 2; ++k) b.ub[k] = (double*)take(8 * np3);
+    for (int k = 0; k < 2; ++k) b.vb[k] = (double*)take(8 * np3);
+    b.ubm = (double*)take(8 * np3);
+    b.w = (double*)take(8 * np3);
+    b.gl = (double*)take(8 * n_pad);
+    b.gc = (double*)take(8 * slots);
+    b.partial = (double*)take(8 * (size_t)n_partial);
+    b.out = (double*)take(8);
+    b.off = want_c ? (int64_t*)take(8 * (n + 1)) : nullptr;
+    b.idx = want_c ? (int32_t*)take(4 * n_bonds) : nullptr;
+    b.dc = c_host ? (double*)take(8 * n_bonds) : nullptr;
+    return used;
+}
+
+}  // namespace
+
+extern "C" {
+
+pd_status pd_adjoint_backward_static(pd_handle* h, const double* dLdu, const double* dLdv,
+                                     double* dL_dc, double* dL_dload, double* dL_du0,
+                                     double* dL_dv0)
+{
+    if (!h) return fail(PD_ERR_ARG, "NULL handle");
+    auto& T = h->tape;
+    if (!T.valid) return fail(PD_ERR_STATE, "no recorded adjoint forward run");
+    if (!dLdu) return fail(PD_ERR_ARG, "dLdu is required");
+    PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    const int64_t np3 = 3 * h->n_pad;
+    const int64_t slots = h->n_slices * 32LL * h->Q * 32;
+    const int n_partial = sum_partials_needed(h->n);
+    const int64_t n_bonds = h->off[(size_t)h->n];
+    const bool want_c = dL_dc != nullptr;
+    const bool c_host = want_c && !is_device_ptr(dL_dc);
+    StaticBufs b{};
+    const size_t need = carve_static(nullptr, np3, h->n_pad, slots, n_partial, h->n, n_bonds,
+                                     want_c, c_host, b);
+    if (need > (size_t)PD_STATIC_SCRATCH_BYTES)
+        return fail(PD_ERR_ARG,
+                    "pd_adjoint_backward_static: this model needs %zu bytes of scratch, above "
+                    "the static maximum of %zu bytes (use pd_adjoint_backward)",
+                    need, (size_t)PD_STATIC_SCRATCH_BYTES);
+    unsigned char* base = nullptr;
+    pd_status st = static_scratch(h->device, &base);
+    if (st != PD_OK) return st;
+    carve_static(base, np3, h->n_pad, slots, n_partial, h->n, n_bonds, want_c, c_host, b);
+
+    // every buffer starts at zero (gc and gl accumulate; earlier calls leave data)
+    PD_CUDA(cudaMemsetAsync(base, 0, need, h->stream), "clear static scratch");
+    auto to_lib = [&](const double* src, double* dst) -> pd_status {
+        if (!src) return PD_OK;
+        const double* s = src;
+        if (!is_device_ptr(src)) {
+            PD_CUDA(cudaMemcpyAsync(h->staging, src, 24 * h->n, cudaMemcpyHostToDevice, h->stream),
+                    "copy gradient to device");
+            s = h->staging;
+        }
+        PD_CUDA(launch_to_lib3(s, h->gid, h->n, dst, h->stream), "reorder");
+        PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
+        return PD_OK;
+    };
+    if ((st = to_lib(dLdu, b.ub[0])) != PD_OK || (st = to_lib(dLdv, b.vb[0])) != PD_OK) return st;
+
+    int sms = 0;
+    PD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "sm count");
+    const int agrid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8,
+                                                                  (h->n_slices + 7) / 8));
+    AdjArgs A{};
+    A.x64 = h->x64;
+    A.nbr = h->nbr;
+    A.bits = h->bits;
+    A.sw = h->sw;
+    A.Q = h->Q;
+    A.vol = h->vol;
+    A.cbond = h->per_bond_c ? (const double*)h->cbond : nullptr;
+    A.c = h->c;
+    A.gc = b.gc;
+    A.gl = b.gl;
+    A.bcc = h->bcc;
+    A.bct = h->bct;
+    A.dt_rho = h->dt / h->rho;
+    A.damp = 1.0 - h->dt * h->eta / h->rho;
+    A.n = h->n;
+
+    // segments are recomputed with direct launches (no graph is built or used)
+    h->frozen = true;
+    int cb = 0;
+    cudaError_t ke = cudaSuccess;
+    for (int64_t k = T.nck - 1; k >= 0 && ke == cudaSuccess; --k) {
+        const int64_t start = k * T.C;
+        const int64_t len = std::min(T.C, T.N - start);
+        h->step = T.step0 + start;
+        ke = cudaMemcpyAsync(h->step_ctr, &h->step, sizeof(int64_t), cudaMemcpyHostToDevice,
+                             h->stream);
+        if (ke == cudaSuccess) ke = cudaStreamSynchronize(h->stream);
+        const int cur = (int)(h->step & 1);
+        if (ke == cudaSuccess) ke = launch_insert_u(T.ck_u + k * np3, h->n_pad, h->rec[cur], h->stream);
+        if (ke == cudaSuccess)
+            ke = cudaMemcpyAsync(h->v, T.ck_v + k * np3, 8 * np3, cudaMemcpyDeviceToDevice, h->stream);
+        if (ke == cudaSuccess)
+            ke = cudaMemcpyAsync(T.seg, T.ck_u + k * np3, 8 * np3, cudaMemcpyDeviceToDevice, h->stream);
+        for (int64_t t = 1; t < len && ke == cudaSuccess; ++t) {
+            ke = launch_one(h, 0);
+            if (ke == cudaSuccess) ke = launch_advance(h->step_ctr, 1, h->stream);
+            h->step += 1;
+            if (ke == cudaSuccess)
+                ke = launch_extract_u(h->rec[h->step & 1], h->n_pad, T.seg + t * np3, h->stream);
+        }
+        for (int64_t t = len - 1; t >= 0 && ke == cudaSuccess; --t) {
+            ke = launch_adj_mask(b.ub[cb], b.vb[cb], h->bcc, h->bct, h->n_pad, h->dt, b.ubm, b.w,
+                                 h->stream);
+            A.un = T.seg + t * np3;
+            A.w = b.w;
+            A.ubm = b.ubm;
+            A.ub_out = b.ub[cb ^ 1];
+            A.vb_out = b.vb[cb ^ 1];
+            if (ke == cudaSuccess) ke = launch_adj_step(A, agrid, 256, h->stream);
+            cb ^= 1;
+        }
+    }
+    h->frozen = false;
+    h->step = T.step0 + T.N;
+    if (ke == cudaSuccess)
+        ke = cudaMemcpyAsync(h->step_ctr, &h->step, sizeof(int64_t), cudaMemcpyHostToDevice,
+                             h->stream);
+    if (ke == cudaSuccess) ke = cudaStreamSynchronize(h->stream);
+    if (ke == cudaSuccess) ke = launch_insert_u(T.fin_u, h->n_pad, h->rec[h->step & 1], h->stream);
+    if (ke == cudaSuccess)
+        ke = cudaMemcpyAsync(h->v, T.fin_v, 8 * np3, cudaMemcpyDeviceToDevice, h->stream);
+    h->damage_fresh = false;
+    if (ke != cudaSuccess) return cuda_fail(ke, "adjoint sweep");
+
+    if (dL_dload) {
+        PD_CUDA(launch_sum(b.gl, h->n, A.dt_rho, b.partial, n_partial, b.out, h->stream),
+                "load gradient");
+        PD_CUDA(cudaMemcpyAsync(dL_dload, b.out, sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+                "copy load gradient");
+    }
+    auto from_lib = [&](const double* src, double* dst) -> pd_status {
+        if (!dst) return PD_OK;
+        const bool dev = is_device_ptr(dst);
+        double* o = dev ? dst : h->staging;
+        PD_CUDA(launch_from_lib3(src, h->gid, h->n, o, h->stream), "reorder");
+        if (!dev)
+            PD_CUDA(cudaMemcpyAsync(dst, h->staging, 24 * h->n, cudaMemcpyDeviceToHost, h->stream),
+                    "copy gradient to host");
+        PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
+        return PD_OK;
+    };
+    if ((st = from_lib(b.ub[cb], dL_du0)) != PD_OK || (st = from_lib(b.vb[cb], dL_dv0)) != PD_OK)
+        return st;
+    if (want_c) {
+        PD_CUDA(cudaMemcpyAsync(b.off, h->off.data(), 8 * (h->n + 1), cudaMemcpyHostToDevice,
+                                h->stream),
+                "copy family offsets");
+        if (n_bonds > 0)
+            PD_CUDA(cudaMemcpyAsync(b.idx, h->idx.data(), 4 * n_bonds, cudaMemcpyHostToDevice,
+                                    h->stream),
+                    "copy family");
+        PD_CUDA(launch_slots_to_canonical(b.gc, h->nbr, h->gid, b.off, b.idx, h->n, h->Q,
+                                          c_host ? b.dc : dL_dc, h->stream),
+                "stiffness gradient to canonical order");
+        if (c_host && n_bonds > 0)
+            PD_CUDA(cudaMemcpyAsync(dL_dc, b.dc, 8 * n_bonds, cudaMemcpyDeviceToHost, h->stream),
+                    "copy stiffness gradient");
+    }
+    return check_dev_err(h);
 }
 
 }  // extern "C"

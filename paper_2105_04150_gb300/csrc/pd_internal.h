@@ -156,6 +156,11 @@ cudaError_t launch_to_lib3(const double* in, const int32_t* gid, int64_t n, doub
                            cudaStream_t s);
 cudaError_t launch_from_lib3(const double* in, const int32_t* gid, int64_t n, double* out,
                              cudaStream_t s);
+// val (one double per SELL slot) -> out (per directed bond, canonical order);
+// off/idx: the canonical family on the device
+cudaError_t launch_slots_to_canonical(const double* val, const int32_t* nbr, const int32_t* gid,
+                                      const int64_t* off, const int32_t* idx, int64_t n, int Q,
+                                      double* out, cudaStream_t s);
 // deterministic two-pass sum: out = scale * sum(x[0..n)); partial holds n_partial doubles
 int sum_partials_needed(int64_t n);
 cudaError_t launch_sum(const double* x, int64_t n, double scale, double* partial, int n_partial,
