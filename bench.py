@@ -51,7 +51,10 @@ def parse():
     p.add_argument("--steps", type=int, default=2000)
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="beam", choices=["beam", "plate", "bar", "batch"])
+    p.add_argument("--workload", default="beam",
+                   choices=["beam", "plate", "bar", "batch", "adjoint"])
+    p.add_argument("--fd-directions", type=int, default=32)
+    p.add_argument("--checkpoint-every", type=int, default=45)
     p.add_argument("--precision", type=int, default=32, choices=[32, 64])
     p.add_argument("--graph-steps", type=int, default=50)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -423,12 +426,151 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def cmod_loss(u, above, below):
+    """L = CMOD^2 with CMOD = mean u_y above the slit - mean u_y below, at the mouth;
+    returns L and dL/du (n x 3)."""
+    cmod = u[above, 1].mean() - u[below, 1].mean()
+    g = np.zeros_like(u)
+    g[above, 1] = 2.0 * cmod / len(above)
+    g[below, 1] = -2.0 * cmod / len(below)
+    return cmod * cmod, g
+
+
+def run_adjoint(args):
+    """Gradient of the squared crack-mouth opening after N steps of the pre-cracked
+    100k-node plate with respect to every directed bond's stiffness (a 10 %
+    random field) and the edge load: checkpointed forward + reverse sweep (FP64),
+    against the plain forward run, central differences on random directions and
+    the oracle's reverse mode on a bounded number of steps."""
+    import torch
+    import paper_2105_04150_gb300 as pdgb
+    torch.cuda.set_device(0)
+    N, C = args.steps, args.checkpoint_every
+    w = workloads.sensitivity_plate(steps=N)
+    c0 = pdgb.pd_micromodulus(w.bulk_modulus, w.horizon)
+    stream = torch.cuda.Stream()
+    G = max(1, min(args.graph_steps, N))
+    m = pdgb.Model.from_workload(w, precision=64, c=c0, graph_steps=G, stream=stream.cuda_stream)
+    off, idx = m.family()
+    n_bonds = len(idx)
+    cb = workloads.bond_stiffness_grf(w, off, idx, c0)
+    rev = workloads.reverse_bond(w.n, off, idx)
+    above, below = workloads.mouth_nodes(w)
+    zero = np.zeros((w.n, 3))
+
+    def forward_loss(c_bond, load, steps=N):
+        m.set_params(c0, w.sc, load, w.disp_rate, c_bond)
+        m.set_state(zero, zero, step=0)
+        m.step(steps)
+        return cmod_loss(m.state()[0], above, below)[0]
+
+    def gradient(c_bond, load, steps=N, ck=C, times=None):
+        m.set_params(c0, w.sc, load, w.disp_rate, c_bond)
+        m.set_state(zero, zero, step=0)
+        m.sync()
+        t0 = time.perf_counter()
+        pdgb.pd_adjoint_forward(m.h, steps, ck)
+        L, g = cmod_loss(m.state()[0], above, below)
+        t1 = time.perf_counter()
+        gc, gl, _, _ = pdgb.pd_adjoint_backward(m.h, g)
+        m.sync()
+        t2 = time.perf_counter()
+        if times is not None:
+            times.update(forward_ms=(t1 - t0) * 1e3, backward_ms=(t2 - t1) * 1e3)
+        return L, gc, gl
+
+    for _ in range(max(1, min(args.warmup, 3))):
+        forward_loss(cb, w.load)
+        gradient(cb, w.load)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        time.sleep(0.5)
+        t_on = time.time()
+        m.set_params(c0, w.sc, w.load, w.disp_rate, cb)
+        m.set_state(zero, zero, step=0)
+        m.sync()
+        e0.record(stream)
+        m.step(N)
+        e1.record(stream)
+        e1.synchronize()
+        ms_fwd = e0.elapsed_time(e1)
+        parts = {}
+        L0, gc, gl = gradient(cb, w.load, times=parts)
+        ms_grad = parts["forward_ms"] + parts["backward_ms"]
+        t_off = time.time()
+    broken = int((m.bonds() == 0).sum())
+
+    # central differences on random directions in (c_bond, load)
+    rng = np.random.default_rng(2105041506)
+    h = 1e-3  # of a direction whose per-bond entries are 0.1 c0: relative changes ~1e-4
+    worst = 0.0
+    for _ in range(args.fd_directions):
+        r = rng.standard_normal(n_bonds)
+        dc = 0.5 * (r + r[rev]) * 0.1 * c0
+        dl = rng.standard_normal() * 0.1 * w.load
+        fd = (forward_loss(cb + h * dc, w.load + h * dl)
+              - forward_loss(cb - h * dc, w.load - h * dl)) / (2 * h)
+        ana = float(gc @ dc) + gl * dl
+        worst = max(worst, abs(fd - ana) / abs(ana))
+
+    cpu, oracle_check = None, None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        om = oracle.Model.from_workload(w, off, idx, c=c0, c_bond=cb)
+        u1, v1 = zero.copy(), zero.copy()
+        t = time.perf_counter()
+        om.step(0, u1, v1, om.fresh_bonds())
+        per_step = time.perf_counter() - t
+        S = int(max(2, min(N, 15.0 / (3.0 * per_step))))
+        _, gS, _ = gradient(cb, w.load, steps=S, ck=min(C, S))
+        uS, vS = zero.copy(), zero.copy()
+        om.run(0, S, uS, vS, om.fresh_bonds())
+        _, g_u = cmod_loss(uS, above, below)
+        t = time.perf_counter()
+        gc_o, gl_o, _, _ = oracle.adjoint(om, 0, S, zero, zero, om.fresh_bonds(), g_u, None)
+        el = time.perf_counter() - t
+        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        cpu = {"value": n_bonds * S / el, "unit": "bond updates/s", "cores": cores,
+               "kind": "oracle",
+               "sample": f"oracle FP64 reverse mode (all states stored) over {S} steps of the "
+                         f"full plate, {n_bonds:,} bonds, OpenMP on {cores} host threads"}
+        oracle_check = {"steps": S, "checkpoint_every": min(C, S),
+                        "dL_dc_max_rel_err": float(np.abs(gS - gc_o).max() / np.abs(gc_o).max())}
+    m.close()
+    nck = -(-N // C)
+    launches = (N + 2 * nck + 1) + (5 * N - 2 * nck + 9)
+    line = {
+        "metric": "bond updates/s", "value": n_bonds * N / (ms_grad * 1e-3),
+        "unit": "bond updates/s", "n_gpus": 1, "steps": N, "warmup": args.warmup,
+        "ms_per_step": ms_grad / N, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{w.name}: {w.n:,} nodes, {n_bonds:,} directed bonds, "
+                               f"gradient of CMOD^2 after {N} steps w.r.t. per-bond stiffness "
+                               f"and edge load, checkpoint every {C} steps",
+                   "load": w.load},
+        "gradient_ms": ms_grad, "gradient_parts_ms": parts, "forward_ms": ms_fwd,
+        "adjoint_over_forward": ms_grad / ms_fwd, "bonds_broken": broken,
+        "loss": L0, "dL_dload": gl,
+        "fd": {"directions": args.fd_directions, "h_rel": h, "max_rel_err": worst},
+        "oracle_check": oracle_check, "cpu_baseline": cpu,
+        "e2e": {"value": n_bonds * N / (ms_grad * 1e-3), "unit": "bond updates/s",
+                "h2d_bytes_per_step": 2 * 24 * w.n / N, "d2h_bytes_per_step": (24 * w.n * 3 +
+                                                                             8 * n_bonds) / N},
+        "gpu_launches": launches, "clocks": clk.summary(t_on, t_off),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 

@@ -81,19 +81,20 @@ __global__ void __launch_bounds__(256) k_adj_step(const AdjArgs a)
                              y2 = e2 + (a.un[3 * j + 2] - um2);
                 const double L = sqrt(e0 * e0 + e1 * e1 + e2 * e2);
                 const double r = sqrt(y0 * y0 + y1 * y1 + y2 * y2);
-                const double s = (r - L) / L;
+                const double iL = 1.0 / L, ir = 1.0 / r;
+                const double s = (r - L) * iL;
                 const double Vj = a.vol[j];
                 const double d0 = Vm * a.w[3 * j] - Vj * wm0;
                 const double d1 = Vm * a.w[3 * j + 1] - Vj * wm1;
                 const double d2 = Vm * a.w[3 * j + 2] - Vj * wm2;
                 const double yd = y0 * d0 + y1 * d1 + y2 * d2;
                 const double cij = a.cbond != nullptr ? a.cbond[slot] : a.c;
-                const double k1 = 1.0 / L - 1.0 / r, k2 = yd / (r * r * r);
+                const double k1 = iL - ir, k2 = yd * (ir * ir * ir);
                 acc0 += cij * (k1 * d0 + y0 * k2);
                 acc1 += cij * (k1 * d1 + y1 * k2);
                 acc2 += cij * (k1 * d2 + y2 * k2);
                 const double yw = y0 * wm0 + y1 * wm1 + y2 * wm2;
-                a.gc[slot] += a.dt_rho * s * Vj * yw / r;
+                a.gc[slot] += a.dt_rho * s * Vj * yw * ir;
             }
         }
         if (m < a.n) {

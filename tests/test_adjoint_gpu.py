@@ -155,3 +155,63 @@ def test_autograd_function_returns_adjoint_gradients():
     assert float(l_t.grad) == gl
     assert np.array_equal(u_t.grad.numpy(), gu0) and np.array_equal(v_t.grad.numpy(), gv0)
     m.close()
+
+
+def test_sensitivity_plate_full_size():
+    """The 100k-node pre-cracked plate with the 10 % stiffness field: nothing
+    breaks even at half the critical stretch; the gradient equals the oracle's
+    reverse mode over 100 steps (checkpoints every 45: a ragged last segment)
+    and central differences of the full 2000-step run on random directions."""
+    w = workloads.sensitivity_plate()
+    c0 = pdgb.pd_micromodulus(w.bulk_modulus, w.horizon)
+    m = pdgb.Model.from_workload(w, precision=F64, c=c0, graph_steps=50)
+    off, idx = m.family()
+    cb = workloads.bond_stiffness_grf(w, off, idx, c0)
+    rev = workloads.reverse_bond(w.n, off, idx)
+    above, below = workloads.mouth_nodes(w)
+    zero = np.zeros((w.n, 3))
+
+    def cmod2(u):
+        cm = u[above, 1].mean() - u[below, 1].mean()
+        g = np.zeros_like(u)
+        g[above, 1] = 2 * cm / len(above)
+        g[below, 1] = -2 * cm / len(below)
+        return cm * cm, g
+
+    def loss(c_bond, load, steps):
+        m.set_params(c0, w.sc, load, w.disp_rate, c_bond)
+        m.set_state(zero, zero, step=0)
+        m.step(steps)
+        return cmod2(m.state()[0])[0]
+
+    def grad(steps):
+        m.set_params(c0, w.sc, w.load, w.disp_rate, cb)
+        m.set_state(zero, zero, step=0)
+        pdgb.pd_adjoint_forward(m.h, steps, 45)
+        L, g = cmod2(m.state()[0])
+        gc, gl, _, _ = pdgb.pd_adjoint_backward(m.h, g)
+        return g, gc, gl
+
+    m.set_params(c0, 0.5 * w.sc, w.load, w.disp_rate, cb)
+    m.set_state(zero, zero, step=0)
+    m.step(w.steps)
+    assert m.bonds().all()
+
+    S = 100
+    g, gc, gl = grad(S)
+    om = oracle.Model.from_workload(w, off, idx, c=c0, c_bond=cb)
+    gc_o, gl_o, _, _ = oracle.adjoint(om, 0, S, zero, zero, om.fresh_bonds(), g, None)
+    assert rel(gc, gc_o) <= 1e-6 and abs(gl - gl_o) <= 1e-6 * abs(gl_o)
+
+    _, gc, gl = grad(w.steps)
+    rng = np.random.default_rng(2105041506)
+    h = 1e-3
+    for _ in range(4):
+        r = rng.standard_normal(len(idx))
+        dc = 0.5 * (r + r[rev]) * 0.1 * c0
+        dl = rng.standard_normal() * 0.1 * w.load
+        fd = (loss(cb + h * dc, w.load + h * dl, w.steps)
+              - loss(cb - h * dc, w.load - h * dl, w.steps)) / (2 * h)
+        ana = float(gc @ dc) + gl * dl
+        assert abs(fd - ana) <= 1e-6 * abs(ana), (fd, ana)
+    m.close()

@@ -267,6 +267,43 @@ def grf_eval(points: np.ndarray, omega: np.ndarray, phase: np.ndarray) -> np.nda
     return out
 
 
+def sensitivity_plate(load: float = 8e6, steps: int = 2000) -> Workload:
+    """The 250 x 100 x 4 pre-cracked plate of the sensitivity runs (100,000 nodes)
+    with the y-edge body-force density scaled by ``load``.  The largest bond
+    stretch over 2000 steps from rest is about 3.8e-12 per unit load, so the
+    default keeps every bond near 0.3 s_c (s_c = 1e-4): nothing breaks."""
+    return cracked_plate_force(250, 100, 4, load=load, steps=steps)
+
+
+def bond_stiffness_grf(w: Workload, off: np.ndarray, idx: np.ndarray, c0: float,
+                       seed: int = 2105041505, rel: float = 0.1,
+                       corr_dx: float = 5.0) -> np.ndarray:
+    """Per directed bond stiffness c0 (1 + rel g(m_ij)), g a unit-variance random
+    field (correlation length corr_dx * dx) at the bond midpoint m_ij.  The field
+    is evaluated once per distinct midpoint, so (i, j) and (j, i) get the same
+    value exactly."""
+    omega, phase = grf_params(seed, corr_dx * w.dx)
+    rows = np.repeat(np.arange(w.n), np.diff(off))
+    twice = np.rint((w.coords[rows] + w.coords[idx]) / w.dx).astype(np.int64)
+    lo = twice.min(axis=0)
+    span = twice.max(axis=0) - lo + 1
+    t = twice - lo
+    key = (t[:, 0] * span[1] + t[:, 1]) * span[2] + t[:, 2]
+    uniq, inv = np.unique(key, return_inverse=True)
+    pts = np.stack([uniq // (span[1] * span[2]), (uniq // span[2]) % span[1], uniq % span[2]],
+                   axis=1)
+    g = grf_eval(0.5 * (pts + lo) * w.dx, omega, phase)
+    return c0 * (1.0 + rel * g[inv])
+
+
+def reverse_bond(n: int, off: np.ndarray, idx: np.ndarray) -> np.ndarray:
+    """Position of (j, i) for every directed bond (i, j) of a CSR family with
+    ascending rows (for building symmetric per-bond fields)."""
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(off))
+    key = rows * n + idx
+    return np.searchsorted(key, idx.astype(np.int64) * n + rows)
+
+
 def random_state(n: int, seed: int, u_scale: float, v_scale: float):
     """Seeded random displacement and velocity fields (n, 3)."""
     rng = np.random.default_rng(seed)
