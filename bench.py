@@ -250,7 +250,8 @@ def run_reference(args):
     w = make_workload(args.workload)
     c = oracle.micromodulus(w.bulk_modulus, w.horizon)
     # each timed step is a row sample sized so the whole run takes about a minute
-    res = oracle_sample(w, c, budget_s=60.0, steps=args.steps, warmup=args.warmup)
+    budget = float(os.environ.get("BENCH_REFERENCE_BUDGET_S", "60"))
+    res = oracle_sample(w, c, budget_s=budget, steps=args.steps, warmup=args.warmup)
     line = {
         "impl": "reference", "metric": "bond updates/s", "value": res["value"],
         "unit": "bond updates/s", "n_gpus": args.gpus, "steps": args.steps,
