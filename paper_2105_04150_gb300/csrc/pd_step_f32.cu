@@ -36,6 +36,11 @@
 // -xi, -eta and produces the same bits), so both break together.  A bond whose
 // FP32 stretch is within a relative band of s_c is re-tested with the literal
 // FP64 stretch of Eq. 4.
+//
+// The slot loop is instruction-issue bound (about 60 instructions per bond),
+// so the per-bond vector differences run as packed f32x2 operations on the
+// register pairs the 256-bit record load delivers: (x, y), (z, h_x),
+// (h_y, h_z), (l_x, l_z).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -184,6 +189,54 @@ __device__ __forceinline__ BondF32 bond_f32(const NodeF32& i, const NodeF32& j)
     return r;
 }
 
+// The lane's own record, negated and paired as the 256-bit load delivers
+// registers: (x, y), (z, h_x), (h_y, h_z), (l_x, l_z), plus l_y.
+struct LanePairs {
+    float2 xy, zhx, hyz, lxz;
+    float ly;
+};
+
+__device__ __forceinline__ LanePairs lane_pairs(const float4 a, const float4 b)
+{
+    LanePairs p;
+    p.xy = make_float2(-a.x, -a.y);
+    p.zhx = make_float2(-a.z, -a.w);
+    p.hyz = make_float2(-b.x, -b.y);
+    p.lxz = make_float2(-b.z, -b.w);
+    p.ly = -bf_lo(b.z);
+    return p;
+}
+
+// bond_f32 with the vector differences done as packed f32x2 operations on the
+// record's register pairs (the same IEEE operations in the same order per
+// component, so j->i still mirrors i->j bit for bit)
+__device__ __forceinline__ BondF32 bond_f32_pk(const LanePairs& i, const float4 ja, const float4 jb)
+{
+    BondF32 r;
+    const float2 exy = __fadd2_rn(make_float2(ja.x, ja.y), i.xy);
+    const float2 ezhx = __fadd2_rn(make_float2(ja.z, ja.w), i.zhx);
+    const float2 dhyz = __fadd2_rn(make_float2(jb.x, jb.y), i.hyz);
+    const float2 dlxz = __fadd2_rn(make_float2(jb.z, jb.w), i.lxz);
+    const float dly = bf_lo(jb.z) + i.ly;
+    const float2 hxy = make_float2(ezhx.y + dlxz.x, dhyz.x + dly);
+    const float hz = dhyz.y + dlxz.y;
+    const float ez = ezhx.x;
+    const float2 yxy = __fadd2_rn(exy, hxy);
+    const float yz = ez + hz;
+    const float2 sxy = __fadd2_rn(exy, yxy);
+    const float2 e2 = __fmul2_rn(exy, exy);
+    const float xx = fmaf(ez, ez, e2.x + e2.y);
+    const float2 n2 = __fmul2_rn(hxy, sxy);
+    r.num = fmaf(hz, ez + yz, n2.x + n2.y);
+    r.yx = yxy.x;
+    r.yy = yxy.y;
+    r.yz = yz;
+    r.y2 = xx + r.num;
+    const float p = xx * r.y2;
+    r.den = xx + p * rsqrtf(p);
+    return r;
+}
+
 // c V_j s / |y| = w num / (den |y|)
 __device__ __forceinline__ float bond_coef(const BondF32& b, float w)
 {
@@ -284,6 +337,7 @@ __global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS)
         float4 ai, bi;
         ld_rec(R + 2 * i, ai, bi);
         const NodeF32 ni = unpack(ai, bi);
+        const LanePairs pi = lane_pairs(ai, bi);
         uint32_t* bw = a.bits + g * Q * 32 + lane;
         float fx = 0.f, fy = 0.f, fz = 0.f, ws = 0.f;
         int alive_count = 0;
@@ -321,8 +375,7 @@ __global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS)
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
                 const bool alive = (wb >> u) & 1u;
-                const NodeF32 nj = unpack(ra[u], rb[u]);
-                const BondF32 bd = bond_f32(ni, nj);
+                const BondF32 bd = bond_f32_pk(pi, ra[u], rb[u]);
                 // near-s_c candidates; unused/broken slots are dropped from the
                 // pending set once per chunk (pc & wb below)
                 const bool cand = bd.num >= fast_lo * bd.den;
