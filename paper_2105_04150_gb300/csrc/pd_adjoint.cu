@@ -79,10 +79,11 @@ __global__ void __launch_bounds__(256) k_adj_step(const AdjArgs a)
                              e2 = a.x64[3 * j + 2] - xm2;
                 const double y0 = e0 + (a.un[3 * j] - um0), y1 = e1 + (a.un[3 * j + 1] - um1),
                              y2 = e2 + (a.un[3 * j + 2] - um2);
-                const double L = sqrt(e0 * e0 + e1 * e1 + e2 * e2);
-                const double r = sqrt(y0 * y0 + y1 * y1 + y2 * y2);
-                const double iL = 1.0 / L, ir = 1.0 / r;
-                const double s = (r - L) * iL;
+                const double iL = a.ilen[slot];
+                const double yy2 = y0 * y0 + y1 * y1 + y2 * y2;
+                const double ir = rsqrt_nr(yy2);
+                const double r = yy2 * ir;
+                const double s = fma(r, iL, -1.0);
                 const double Vj = a.vol[j];
                 const double d0 = Vm * a.w[3 * j] - Vj * wm0;
                 const double d1 = Vm * a.w[3 * j + 1] - Vj * wm1;

@@ -114,6 +114,7 @@ struct pd_handle {
     int32_t* gid = nullptr;
     double* x64 = nullptr;
     double* vol = nullptr;
+    double* ilen = nullptr;  // FP64: per slot 1 / |xi|
     void* wsum_inv = nullptr;
     void* damage = nullptr;
     int* err = nullptr;
@@ -236,6 +237,7 @@ StepArgsF64 args_f64(pd_handle* h, int k)
     a.bits = h->bits;
     a.sw = h->sw;
     a.cbond = h->per_bond_c ? (const double*)h->cbond : nullptr;
+    a.ilen = h->ilen;
     a.bcc = h->bcc;
     a.bct = h->bct;
     a.gid = h->gid;
@@ -475,6 +477,7 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
         ALLOC(h->v, double, 3 * np);
         ALLOC(h->wsum_inv, double, np);
         ALLOC(h->damage, double, np);
+        ALLOC(h->ilen, double, nbr.size());
     }
     ALLOC(h->nbr, int32_t, nbr.size());
     ALLOC(h->bits, uint32_t, bits.size());
@@ -569,6 +572,10 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
             (st = up(h->itab, d.itab.data(), d.itab.size() * sizeof(InstParams),
                      "upload instance table")))
             return st;
+    }
+    if (!f32) {
+        e = launch_inv_len(h->x64, h->nbr, h->sw, n, h->Q, h->ilen, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "bond lengths");
     }
     if ((st = upload_weights(h)) != PD_OK) return st;
     h->blocks_per_sm = cfg->blocks_per_sm;
@@ -1096,6 +1103,7 @@ pd_status pd_adjoint_backward(pd_handle* h, const double* dLdu, const double* dL
     A.Q = h->Q;
     A.vol = h->vol;
     A.cbond = h->per_bond_c ? (const double*)h->cbond : nullptr;
+    A.ilen = h->ilen;
     A.c = h->c;
     A.gc = T.gc;
     A.gl = T.gl;
@@ -1466,6 +1474,7 @@ pd_status pd_adjoint_backward_static(pd_handle* h, const double* dLdu, const dou
     A.Q = h->Q;
     A.vol = h->vol;
     A.cbond = h->per_bond_c ? (const double*)h->cbond : nullptr;
+    A.ilen = h->ilen;
     A.c = h->c;
     A.gc = b.gc;
     A.gl = b.gl;

@@ -184,6 +184,30 @@ __global__ void k_wsum(const void* __restrict__ wrec, const int32_t* __restrict_
     }
 }
 
+__global__ void k_inv_len(const double* __restrict__ x64, const int32_t* __restrict__ nbr,
+                          const int32_t* __restrict__ sw, int64_t n, int Q,
+                          double* __restrict__ ilen)
+{
+    const int64_t W = 32LL * Q;
+    GRID_STRIDE(p, ((n + 31) >> 5) << 5)
+    {
+        const int64_t g = p >> 5;
+        const int lane = (int)(p & 31);
+        const int Wg = sw[g];
+        for (int m = 0; m < Wg; ++m) {
+            const int64_t slot = (g * W + m) * 32 + lane;
+            const int64_t j = nbr[slot];
+            double v = 0.0;
+            if (j != p) {
+                const double ex = x64[3 * j] - x64[3 * p], ey = x64[3 * j + 1] - x64[3 * p + 1],
+                             ez = x64[3 * j + 2] - x64[3 * p + 2];
+                v = 1.0 / sqrt(ex * ex + ey * ey + ez * ez);
+            }
+            ilen[slot] = v;
+        }
+    }
+}
+
 int grid_for(int64_t work, int block)
 {
     int64_t g = (work + block - 1) / block;
@@ -270,6 +294,13 @@ cudaError_t launch_set_weights(int precision, void* wrec0, void* wrec1, const do
         k_wsum<double><<<grid_for(n, 256), 256, 0, s>>>(wrec0, nbr, init_bits, sw, n, Q,
                                                         (double*)wsum_inv);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inv_len(const double* x64, const int32_t* nbr, const int32_t* sw, int64_t n,
+                           int Q, double* ilen, cudaStream_t s)
+{
+    k_inv_len<<<grid_for(((n + 31) >> 5) << 5, 256), 256, 0, s>>>(x64, nbr, sw, n, Q, ilen);
     return cudaGetLastError();
 }
 

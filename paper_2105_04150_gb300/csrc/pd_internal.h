@@ -103,6 +103,7 @@ struct StepArgsF64 {
     int32_t frozen;            // 1: no bond breaks (the adjoint's forward runs)
     int32_t pad1;
     const double* cbond;
+    const double* ilen;        // per slot 1 / |xi| (reference bond length)
     const uint8_t* bcc;
     const BcClass* bct;
     const int32_t* gid;
@@ -136,6 +137,7 @@ struct AdjArgs {
     int32_t pad0;
     const double* vol;         // volumes V
     const double* cbond;       // per-slot stiffness, or nullptr for the constant c
+    const double* ilen;        // per slot 1 / |xi|
     double c;
     double* gc;                // per-slot dL/dc accumulator
     double* gl;                // per-node accumulator of force . w
@@ -196,6 +198,27 @@ cudaError_t launch_gather_damage(int precision, const void* dmg, const int32_t* 
                                  double* phi_out, cudaStream_t s);
 // node weights w = wscale * V (FP32: the w array, passed as wrec0; FP64: both
 // record buffers) and wsum_inv (a slot is a real member iff its init_bits bit is set)
+// per slot 1 / |x_j - x_i| from the FP64 reference positions (0 for unused slots)
+cudaError_t launch_inv_len(const double* x64, const int32_t* nbr, const int32_t* sw, int64_t n,
+                           int Q, double* ilen, cudaStream_t s);
+// 1/sqrt(x), x > 0, in FP64: the FP32 hardware estimate refined by two
+// Newton-Raphson steps for f(y) = 1/y^2 - x (quadratic convergence: relative
+// error ~2^-22 -> ~2^-43 -> rounding level); residual r = 1 - x y^2 taken with
+// a fused multiply-add, y <- y + (y/2) r.  Outside the FP32 range of the
+// estimate it falls back to 1/sqrt(x).
+#ifdef __CUDACC__
+__device__ __forceinline__ double rsqrt_nr(double x)
+{
+    const float xf = (float)x;
+    if (!(xf > 0.0f) || isinf(xf)) return 1.0 / sqrt(x);
+    double y = (double)rsqrtf(xf);
+    double t = x * y;
+    y = fma(0.5 * y, fma(-t, y, 1.0), y);
+    t = x * y;
+    y = fma(0.5 * y, fma(-t, y, 1.0), y);
+    return y;
+}
+#endif
 cudaError_t launch_set_weights(int precision, void* wrec0, void* wrec1, const double* vol,
                                const int32_t* nbr, const uint32_t* init_bits, const int32_t* sw,
                                int64_t n, int Q, double wscale, void* wsum_inv, cudaStream_t s);

@@ -3,8 +3,14 @@
 // Same decomposition as the FP32-bulk kernel (lane per node over the sliced
 // family layout, double-buffered displacement, bond flags as the lane's own
 // bit words, integration and damage in the same pass), but every quantity is
-// FP64 and the stretch is the literal one of Eq. 4,
-// s = (|xi + eta| - |xi|) / |xi|, so break decisions are FP64 decisions.
+// FP64 and the stretch is that of Eq. 4, s = (|xi + eta| - |xi|) / |xi|, so
+// break decisions are FP64 decisions.  GB300's FP64 rate is a small fraction
+// of its FP32 rate and this kernel is bound by it, so the per-bond square roots
+// and divisions are avoided: 1/|xi| is a per-slot array computed once (8 bytes
+// per bond: memory is not the limit here), and 1/|y| comes from a Newton-
+// refined reciprocal square root; then |y| = |y|^2 / |y|, s = |y| / |xi| - 1
+// (one rounding, an absolute error of a few 1e-16) and the force scale is
+// c V s / |y| with multiplications only.
 // Node record: 8 doubles {x, y, z, w, ux, uy, uz, 0}, w = c V (or V with
 // per-bond stiffness).
 #include <cuda_runtime.h>
@@ -90,9 +96,11 @@ __global__ void __launch_bounds__(256) k_step_f64(const StepArgsF64 a)
                     const double yx = ex + (ra[u][2].x - u01.x);
                     const double yy = ey + (ra[u][2].y - u01.y);
                     const double yz = ez + (ra[u][3].x - u23.x);
-                    const double L = sqrt(ex * ex + ey * ey + ez * ez);
-                    const double r = sqrt(yx * yx + yy * yy + yz * yz);
-                    const double s = (r - L) / L;
+                    const int64_t slot = (g * W + q * 32 + b0 + u) * 32 + lane;
+                    const double y2 = yx * yx + yy * yy + yz * yz;
+                    const double ir = rsqrt_nr(y2);
+                    const double r = y2 * ir;
+                    const double s = fma(r, __ldg(a.ilen + slot), -1.0);
                     double sc;
                     if (a.inst != nullptr) {  // batch: instance parameters, local ids as keys
                         const InstParams& ip = a.itab[a.inst[i]];
@@ -110,8 +118,8 @@ __global__ void __launch_bounds__(256) k_step_f64(const StepArgsF64 a)
                         nword &= ~(1u << (b0 + u));
                     } else {
                         double wj = ra[u][1].y;
-                        if (cb != nullptr) wj *= __ldg(cb + (g * W + q * 32 + b0 + u) * 32 + lane);
-                        const double f = wj * s / r;
+                        if (cb != nullptr) wj *= __ldg(cb + slot);
+                        const double f = wj * s * ir;
                         fx += f * yx;
                         fy += f * yy;
                         fz += f * yz;
