@@ -42,6 +42,15 @@ import workloads  # noqa: E402
 # velocity 12 B read + 12 B written, damage 4 B written, BC class 1 B.
 BYTES_PER_BOND = 4.125
 BYTES_PER_NODE = {32: 93.0, 64: 136.0}
+# The FP64 step is bound by GB300's FP64 arithmetic, not by HBM.  Algorithmic
+# FP64 work per bond (Eqs. 4-5 as written): xi, eta, y (9), |xi|^2 and |y|^2
+# (10), two square roots and the stretch's division (3), c V s / |y| (3), the
+# force accumulation (6 as 3 fused multiply-adds) = 31 flops, counting a square
+# root or a division as one.  Peak: FP64 fused multiply-add throughput measured
+# on a GB300 of this pool with a plain dependent-chain probe, 1.20 TFLOP/s
+# (nominal 1.25).
+FP64_FLOPS_PER_BOND = 31.0
+FP64_PEAK_TFLOPS = 1.20
 STEP_SRC = {32: "pd_step_f32.cu", 64: "pd_step_f64.cu"}
 
 
@@ -344,6 +353,15 @@ def run_ours(args):
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s", "algorithmic_bytes_per_launch": alg_bytes,
                 "kernel": f"k_step_f{args.precision}"}
+    if args.precision == 64:
+        tf = FP64_FLOPS_PER_BOND * n_bonds / (ms_step * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": tf / FP64_PEAK_TFLOPS, "traffic": profiled_traffic(64, args.workload),
+                    "peak_source": "FP64 FMA throughput measured by a probe on this pool's GB300 "
+                                   "(nominal 1.25 TFLOP/s)",
+                    "algorithmic_flops_per_bond": FP64_FLOPS_PER_BOND,
+                    "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak}, "kernel": "k_step_f64"}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         import oracle
