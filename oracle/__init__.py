@@ -25,6 +25,14 @@ What pins each function (tests in ``tests/test_oracle_pins.py``):
 * ``damage`` (Eq. 8): zero at the start, in [0, 1], monotone, and equal to the
   fraction of crossing offsets for a node next to a full planar cut.
 * ``splitmix64``: the published reference outputs of the generator.
+* ``stiffness_factors`` (micromodulus functions, surface correction): the
+  conical function reproduces the lattice quadrature ratio computed directly
+  from the stencil offsets and tends to the continuum W = 9/2 K eps^2; the
+  volume correction is symmetric, 1 between bulk nodes when V0 is the bulk
+  family volume, and equals 2 V0 / (V_i + V_j) with V_i counted directly from
+  the stencil for nodes on a free face (``tests/test_oracle_stiffness.py``).
+* ``adjoint``: central differences of the pinned forward run
+  (``tests/test_oracle_adjoint.py``).
 """
 from __future__ import annotations
 
@@ -105,6 +113,9 @@ def lib():
         L.or_damage.argtypes = [ctypes.POINTER(_Model), P, P]
         L.or_energy_density.restype = None
         L.or_energy_density.argtypes = [ctypes.POINTER(_Model), P, P, P]
+        L.or_stiffness_factors.restype = None
+        L.or_stiffness_factors.argtypes = [P, P, ctypes.c_int64, ctypes.c_double, P, P,
+                                           ctypes.c_int, ctypes.c_double, P]
         _lib = L
     return _lib
 
@@ -170,6 +181,26 @@ def cut_family(coords, delta, cuts, rows=None, method="cells"):
     cum = np.zeros(idx.shape[0] + 1, dtype=np.int64)
     np.cumsum(keep, out=cum[1:])
     return cum[off], idx[keep.astype(bool)]
+
+
+CONICAL, SURFACE = 1, 2
+
+
+def stiffness_factors(coords, volumes, delta, off, idx, flags, v0=0.0):
+    """Per family entry factors multiplying c: conical micromodulus (bit 1) and the
+    volume surface correction 2 V0 / (V_i + V_j) (bit 2); see oracle.c."""
+    x = _c64(coords)
+    vol = _c64(volumes)
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    nrows = off.shape[0] - 1
+    # rows are nodes 0..nrows-1; the volume correction needs every node as a row
+    assert nrows <= x.shape[0] and (not flags & SURFACE or nrows == x.shape[0])
+    out = np.zeros(max(idx.shape[0], 1))
+    lib().or_stiffness_factors(x.ctypes.data, vol.ctypes.data, nrows, delta,
+                               off.ctypes.data, idx.ctypes.data, int(flags), float(v0),
+                               out.ctypes.data)
+    return out[: idx.shape[0]]
 
 
 class Model:

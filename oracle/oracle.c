@@ -412,6 +412,47 @@ void or_energy_density(const or_model* m, const double* u, const uint8_t* mu, do
 }
 
 /* ------------------------------------------------------------------ */
+/* Stiffness corrections as per-bond factors that multiply the constant
+ * micromodulus c of Eq. (5), one per family entry (Section 2.2, micromodulus
+ * functions; "Surface correction factors"):
+ *   bit 0, conical micromodulus c(|xi|) = c1 (1 - |xi|/delta): the strain
+ *     energy density under uniform dilation s = eps,
+ *       W = (eps^2 / 4) int_0^delta c(r) r 4 pi r^2 dr = (eps^2 / 4) c1 pi delta^4 / 5,
+ *     equated to (9/2) K eps^2 gives c1 = 90 K / (pi delta^4) = 5 c, so the
+ *     factor is 5 (1 - |xi| / delta);
+ *   bit 1, volume (surface) correction lambda_ij = 2 V0 / (V_i + V_j) with V_i
+ *     the family volume sum_{j in H_i} V_j of node i (family as given, i.e.
+ *     after the initial notch removal) and V0 the family volume of a node in
+ *     the bulk (an input).
+ * With both bits the factors multiply.  All nodes are rows. */
+void or_stiffness_factors(const double* x, const double* vol, int64_t n, double delta,
+                          const int64_t* off, const int32_t* idx, int flags, double v0,
+                          double* out)
+{
+    double* fv = NULL;
+    if (flags & 2) {
+        fv = (double*)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+        for (int64_t i = 0; i < n; ++i) {
+            double acc = 0.0;
+            for (int64_t k = off[i]; k < off[i + 1]; ++k) acc += vol[idx[k]];
+            fv[i] = acc;
+        }
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = off[i]; k < off[i + 1]; ++k) {
+            int64_t j = idx[k];
+            double f = 1.0;
+            if (flags & 1) {
+                double L = sqrt(dist2(x + 3 * i, x + 3 * j));
+                f *= 5.0 * (1.0 - L / delta);
+            }
+            if (flags & 2) f *= 2.0 * v0 / (fv[i] + fv[j]);
+            out[k] = f;
+        }
+    free(fv);
+}
+
+/* ------------------------------------------------------------------ */
 /* Reverse mode of the damped Euler-Cromer recurrence with the bond flags mu
  * frozen (no bond changes state during the run).  Forward, for free components:
  *   F^n = sum_j c_ij mu_ij s_ij V_j y_ij/|y_ij| + load * force_i      (Eqs. 5, 10)
