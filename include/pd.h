@@ -105,6 +105,30 @@ typedef struct {
 pd_status pd_micromodulus(double K, double delta, double* c_out);
 
 /*
+ * pd_stiffness_factors - stiffness corrections as per-bond factors, one per
+ * directed bond of the family (fam_off[n+1], fam_idx: canonical order, e.g.
+ * from pd_get_family), to pass as c_bond = c * factor to pd_set_params:
+ *   PD_STIFF_CONICAL  conical micromodulus c(|xi|) = c1 (1 - |xi|/delta)
+ *                     (Section 2.2, micromodulus functions); equating the strain
+ *                     energy density under uniform dilation with (9/2) K eps^2
+ *                     gives c1 = 90 K / (pi delta^4) = 5 c, so the factor is
+ *                     5 (1 - |xi|/delta)
+ *   PD_STIFF_SURFACE  volume surface correction lambda_ij = 2 V0 / (V_i + V_j)
+ *                     ("Surface correction factors"), V_i = sum over the family
+ *                     of node i of V_j, and v0 > 0 the family volume of a node in
+ *                     the bulk (on a cubic lattice with delta = 3.01 dx that is
+ *                     122 dx^3)
+ * The flags combine (the factors multiply).  coords n*3, volumes n (host);
+ * factor: host, one double per family entry.  Host-only work.  PD_ERR_ARG on
+ * bad flags, horizon, v0 or family.
+ */
+#define PD_STIFF_CONICAL 1
+#define PD_STIFF_SURFACE 2
+pd_status pd_stiffness_factors(int64_t n, const double* coords, const double* volumes,
+                               double horizon, const int64_t* fam_off, const int32_t* fam_idx,
+                               int32_t flags, double v0, double* factor);
+
+/*
  * pd_create - build a model and upload it to the GPU.
  *  n        nodes (>= 1, < 2^31)
  *  coords   host, n*3 reference positions x_i (m)

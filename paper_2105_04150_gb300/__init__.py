@@ -25,13 +25,16 @@ __all__ = [
     "pd_get_info", "pd_get_family", "pd_step", "pd_sync", "pd_get_state", "pd_set_state",
     "pd_get_bonds", "pd_set_bonds", "pd_damage", "pd_set_params", "pd_batch_create",
     "pd_batch_offsets", "pd_autotune", "pd_adjoint_forward", "pd_adjoint_backward",
-    "pd_adjoint_backward_static",
+    "pd_adjoint_backward_static", "pd_stiffness_factors", "PD_STIFF_CONICAL",
+    "PD_STIFF_SURFACE",
     "instance_from_workload", "Model",
     "PD_PREC_F32", "PD_PREC_F64",
 ]
 
 PD_PREC_F64 = 64
 PD_PREC_F32 = 32
+PD_STIFF_CONICAL = 1
+PD_STIFF_SURFACE = 2
 _STATUS = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_CUDA", 3: "PD_ERR_OOM",
            4: "PD_ERR_NONFINITE", 5: "PD_ERR_UNSTABLE_DT", 6: "PD_ERR_FAMILY_TOO_LARGE",
            7: "PD_ERR_TIMEOUT", 8: "PD_ERR_STATE"}
@@ -113,6 +116,7 @@ def lib():
             "pd_adjoint_forward": [P, I64, I64],
             "pd_adjoint_backward": [P, P, P, P, P, P, P],
             "pd_adjoint_backward_static": [P, P, P, P, P, P, P],
+            "pd_stiffness_factors": [I64, P, P, D, P, P, I32, D, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -382,6 +386,21 @@ def pd_adjoint_backward_static(h: int, dLdu, dLdv=None, want_c: bool = True):
     _check(lib().pd_adjoint_backward_static(h, up, vp, None if gc is None else gc.ctypes.data,
                                             ctypes.byref(gl), gu.ctypes.data, gv.ctypes.data))
     return (None if gc is None else gc[:nb]), gl.value, gu, gv
+
+
+def pd_stiffness_factors(coords, volumes, horizon, off, idx, flags, v0=0.0):
+    """Per directed bond stiffness factors (canonical order) for the conical
+    micromodulus and/or the volume surface correction; c_bond = c * factor."""
+    x = np.ascontiguousarray(coords, dtype=np.float64)
+    vol = np.ascontiguousarray(volumes, dtype=np.float64)
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    n = x.shape[0]
+    out = np.zeros(max(idx.shape[0], 1))
+    _check(lib().pd_stiffness_factors(n, x.ctypes.data, vol.ctypes.data, float(horizon),
+                                      off.ctypes.data, idx.ctypes.data, int(flags), float(v0),
+                                      out.ctypes.data))
+    return out[: idx.shape[0]]
 
 
 def instance_from_workload(w, c=None) -> dict:

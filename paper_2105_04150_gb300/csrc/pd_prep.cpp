@@ -304,6 +304,39 @@ std::string bc_classes(int64_t n, const uint8_t* type, const double* disp, const
     return "";
 }
 
+void stiffness_factors(int64_t n, const double* x, const double* vol, double delta,
+                       const int64_t* off, const int32_t* idx, int flags, double v0,
+                       double* factor)
+{
+    // family volumes first (the correction needs both ends'), then one pass
+    // over the bonds; each bond's factor depends only on its own two nodes
+    std::vector<double> fam;
+    if (flags & 2) {
+        fam.resize((size_t)n);
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) {
+            double v = 0.0;
+            for (int64_t k = off[i]; k < off[i + 1]; ++k) v += vol[idx[k]];
+            fam[(size_t)i] = v;
+        }
+    }
+    const double inv_delta = 1.0 / delta;
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t k = off[i]; k < off[i + 1]; ++k) {
+            const int64_t j = idx[k];
+            double f = 1.0;
+            if (flags & 1) {
+                const double d0 = x[3 * j] - x[3 * i], d1 = x[3 * j + 1] - x[3 * i + 1],
+                             d2 = x[3 * j + 2] - x[3 * i + 2];
+                f = 5.0 * (1.0 - std::sqrt(d0 * d0 + d1 * d1 + d2 * d2) * inv_delta);
+            }
+            if (flags & 2) f *= (2.0 * v0) / (fam[(size_t)i] + fam[(size_t)j]);
+            factor[k] = f;
+        }
+    }
+}
+
 double stable_dt(int64_t n, const double* x, const double* vol, const std::vector<int64_t>& off,
                  const std::vector<int32_t>& idx, double c, double rho)
 {
