@@ -79,6 +79,7 @@ class _Model(ctypes.Structure):
         ("bc_disp", ctypes.c_void_p), ("bc_force", ctypes.c_void_p),
         ("disp_rate", ctypes.c_double), ("load", ctypes.c_double),
         ("dt", ctypes.c_double), ("damping", ctypes.c_double), ("density", ctypes.c_double),
+        ("ramp_steps", ctypes.c_int64),
     ]
 
 
@@ -113,6 +114,11 @@ def lib():
         L.or_damage.argtypes = [ctypes.POINTER(_Model), P, P]
         L.or_energy_density.restype = None
         L.or_energy_density.argtypes = [ctypes.POINTER(_Model), P, P, P]
+        L.or_scale.restype = ctypes.c_double
+        L.or_scale.argtypes = [ctypes.c_double, ctypes.c_int64, ctypes.c_int64]
+        L.or_run_vv.restype = None
+        L.or_run_vv.argtypes = [ctypes.POINTER(_Model), ctypes.c_int64, ctypes.c_int64,
+                                ctypes.c_int, P, P, P, P]
         L.or_stiffness_factors.restype = None
         L.or_stiffness_factors.argtypes = [P, P, ctypes.c_int64, ctypes.c_double, P, P,
                                            ctypes.c_int, ctypes.c_double, P]
@@ -126,6 +132,11 @@ def _p(a: Optional[np.ndarray]):
 
 def _c64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def scale(rate: float, ramp_steps: int, k: int) -> float:
+    """Displacement scale after step k (linear, or the smooth start; see oracle.c)."""
+    return lib().or_scale(rate, int(ramp_steps), int(k))
 
 
 def micromodulus(K: float, delta: float) -> float:
@@ -208,7 +219,8 @@ class Model:
 
     def __init__(self, coords, volumes, off, idx, *, c, sc=None, sc_hash=None,
                  c_bond=None, no_fail=None, bc_type=None, bc_disp=None, bc_force=None,
-                 disp_rate=0.0, load=0.0, dt=1e-7, damping=0.0, density=1.0, rows=None):
+                 disp_rate=0.0, load=0.0, dt=1e-7, damping=0.0, density=1.0, rows=None,
+                 ramp_steps=0):
         self.x = _c64(coords)
         n = self.x.shape[0]
         self.vol = _c64(volumes)
@@ -244,6 +256,7 @@ class Model:
         m.bc_force = _p(self.bc_force)
         m.disp_rate, m.load = float(disp_rate), float(load)
         m.dt, m.damping, m.density = float(dt), float(damping), float(density)
+        m.ramp_steps = int(ramp_steps)
         self.m = m
         self.nrows = m.nrows
         self.nbonds = int(self.off[-1])
@@ -255,7 +268,8 @@ class Model:
         return cls(w.coords, w.volumes, off, idx, c=c, sc=w.sc, sc_hash=w.sc_hash,
                    c_bond=c_bond, no_fail=w.no_fail, bc_type=w.bc_type, bc_disp=w.bc_disp,
                    bc_force=w.bc_force, disp_rate=w.disp_rate, load=w.load, dt=w.dt,
-                   damping=w.damping, density=w.density, rows=rows)
+                   damping=w.damping, density=w.density, rows=rows,
+                   ramp_steps=getattr(w, "ramp_steps", 0))
 
     def step(self, step_index, u, v, mu, margin=None, want_force=False):
         """One step; returns (u_out, v_out[, F]) per row.  mu/margin updated in place."""
@@ -275,6 +289,15 @@ class Model:
         assert v.dtype == np.float64 and v.flags.c_contiguous
         lib().or_run(ctypes.byref(self.m), int(first_step), int(nsteps), u.ctypes.data,
                      v.ctypes.data, mu.ctypes.data, _p(margin))
+
+    def run_vv(self, first_step, nsteps, u, v, a, mu, init=False):
+        """Damped velocity-Verlet steps over all nodes (see oracle.c); u, v, a
+        (acceleration) and mu updated in place.  init: form a^0 from (u, v) first."""
+        assert self.rows is None
+        for arr in (u, v, a):
+            assert arr.dtype == np.float64 and arr.flags.c_contiguous
+        lib().or_run_vv(ctypes.byref(self.m), int(first_step), int(nsteps), int(bool(init)),
+                        u.ctypes.data, v.ctypes.data, a.ctypes.data, mu.ctypes.data)
 
     def damage(self, mu):
         phi = np.empty(self.nrows)

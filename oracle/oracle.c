@@ -270,10 +270,28 @@ typedef struct {
     const uint8_t* bc_type;  /* 3n: 1 = displacement-controlled component */
     const double* bc_disp;   /* 3n: prescribed displacement per unit scale */
     const double* bc_force;  /* 3n body-force density per unit load, or NULL */
-    double disp_rate;        /* displacement scale after step k = disp_rate * k */
+    double disp_rate;        /* displacement scale rate (see or_scale below) */
     double load;             /* body-force scale */
     double dt, damping, density;
+    int64_t ramp_steps;      /* 0: scale(k) = disp_rate k; T > 0: smooth start over T steps */
 } or_model;
+
+/* Displacement scale after step k.  Linear, rate * k, or with a smooth start
+ * (Sections 5-6: a fifth-order polynomial displacement-time curve, so that the
+ * loaded nodes start with zero acceleration and reach the steady rate with zero
+ * acceleration): over the first T steps rate * T * P(k/T) with
+ *   P(tau) = tau^4 - (3/5) tau^5,
+ * whose value and first three derivatives vanish at 0, with P'(1) = 1,
+ * P''(1) = 0 and P(1) = 2/5; afterwards the line rate * (k - 3T/5) that
+ * continues it. */
+double or_scale(double rate, int64_t ramp_steps, int64_t k)
+{
+    if (ramp_steps <= 0) return rate * (double)k;
+    double T = (double)ramp_steps;
+    if (k >= ramp_steps) return rate * ((double)k - 0.6 * T);
+    double tau = (double)k / T;
+    return rate * T * (tau * tau * tau * tau - 0.6 * tau * tau * tau * tau * tau);
+}
 
 static double bond_sc(const or_model* m, int64_t i, int64_t j)
 {
@@ -329,8 +347,8 @@ void or_step(const or_model* m, int64_t step, const double* u, const double* v,
              uint8_t* mu, double* margin, double* u_out, double* v_out, double* F_out)
 {
     double a_damp = m->damping, rho = m->density, dt = m->dt;
-    double s_now = m->disp_rate * (double)step;
-    double s_next = m->disp_rate * (double)(step + 1);
+    double s_now = or_scale(m->disp_rate, m->ramp_steps, step);
+    double s_next = or_scale(m->disp_rate, m->ramp_steps, step + 1);
 #pragma omp parallel for schedule(dynamic, 256)
     for (int64_t r = 0; r < m->nrows; ++r) {
         int64_t i = m->rows ? m->rows[r] : r;
@@ -366,6 +384,67 @@ void or_run(const or_model* m, int64_t first_step, int64_t nsteps, double* u, do
     }
     free(u2);
     free(v2);
+}
+
+/* Damped velocity-Verlet (Section 3.6, "Time integration"; the velocity-
+ * dependent damping force after Groot & Warren 1997 with lambda = 1/2).  State
+ * (u^n, v^n, a^n) at step n; one step, for free components:
+ *   u^{n+1} = u^n + dt v^n + (dt^2/2) a^n
+ *   vt      = v^n + (dt/2) a^n                        (half-step velocity)
+ *   a^{n+1} = (F(u^{n+1}) - eta vt) / rho              (F at the new positions,
+ *                                                        bonds breaking there first)
+ *   v^{n+1} = v^n + (dt/2) (a^n + a^{n+1})
+ * Displacement-controlled components: u^{n+1} = g scale(n+1),
+ * v^{n+1} = g (scale(n+1) - scale(n)) / dt, a^{n+1} = 0.
+ * With init != 0 the acceleration of the initial state is formed first,
+ * a^0 = (F(u^0) - eta v^0) / rho (bonds past s_c at u^0 break).  All nodes are
+ * rows.  u, v, a, mu in/out. */
+static void vv_accel(const or_model* m, const double* u, const double* vt, uint8_t* mu,
+                     double* acc)
+{
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < m->n; ++i) {
+        double F[3];
+        row_force(m, i, u, mu, NULL, F);
+        for (int a = 0; a < 3; ++a)
+            acc[3 * i + a] = m->bc_type[3 * i + a] == 1
+                                 ? 0.0
+                                 : (F[a] - m->damping * vt[3 * i + a]) / m->density;
+    }
+}
+
+void or_run_vv(const or_model* m, int64_t first_step, int64_t nsteps, int init, double* u,
+               double* v, double* acc, uint8_t* mu)
+{
+    int64_t n3 = 3 * m->n;
+    double dt = m->dt;
+    double* vt = (double*)malloc((size_t)n3 * sizeof(double) + 8);
+    double* an = (double*)malloc((size_t)n3 * sizeof(double) + 8);
+    if (init) vv_accel(m, u, v, mu, acc);
+    for (int64_t k = 0; k < nsteps; ++k) {
+        int64_t step = first_step + k;
+        double s_now = or_scale(m->disp_rate, m->ramp_steps, step);
+        double s_next = or_scale(m->disp_rate, m->ramp_steps, step + 1);
+        for (int64_t e = 0; e < n3; ++e) {
+            if (m->bc_type[e] == 1) {
+                u[e] = m->bc_disp[e] * s_next;
+                vt[e] = 0.0;
+            } else {
+                u[e] = u[e] + dt * v[e] + 0.5 * dt * dt * acc[e];
+                vt[e] = v[e] + 0.5 * dt * acc[e];
+            }
+        }
+        vv_accel(m, u, vt, mu, an);
+        for (int64_t e = 0; e < n3; ++e) {
+            if (m->bc_type[e] == 1)
+                v[e] = m->bc_disp[e] * (s_next - s_now) / dt;
+            else
+                v[e] = v[e] + 0.5 * dt * (acc[e] + an[e]);
+            acc[e] = an[e];
+        }
+    }
+    free(vt);
+    free(an);
 }
 
 /* Eq. (8) with volume weights: phi_i = 1 - sum_j mu_ij V_j / sum_j V_j over the

@@ -55,6 +55,7 @@ class Workload:
     steps: int
     shape: Tuple[int, int, int]
     dx: float
+    ramp_steps: int = 0       # 0: displacement scale rate*k; T: smooth start over T steps
 
     @property
     def n(self) -> int:
