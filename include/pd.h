@@ -67,8 +67,29 @@ typedef struct {
     int32_t blocks_per_sm;/* resident blocks per SM for the step grid; 0 = default */
     int32_t reorder;      /* 0 = keep the caller's node order (best for lattices given
                              row-major); 1 = sort nodes by horizon-sized cells */
-    int32_t reserved0;
+    int32_t integrator;   /* PD_INTEGRATOR_EC (0) or PD_INTEGRATOR_VV (1), see below */
 } pd_config;
+
+/*
+ * Time integrators (Section 3.6, "Time integration"), with F(u) the force
+ * density of Eq. 10 plus the body force:
+ *  PD_INTEGRATOR_EC  damped Euler-Cromer (Eq. 11):
+ *                    v^{n+1} = v^n + dt (F(u^n) - eta v^n) / rho,
+ *                    u^{n+1} = u^n + dt v^{n+1}
+ *  PD_INTEGRATOR_VV  damped velocity-Verlet, the damping force taken at the
+ *                    half-step velocity (Groot & Warren 1997, lambda = 1/2):
+ *                    u^{n+1} = u^n + dt v^n + dt^2/2 a^n,
+ *                    vt = v^n + dt/2 a^n,
+ *                    a^{n+1} = (F(u^{n+1}) - eta vt) / rho,
+ *                    v^{n+1} = v^n + dt/2 (a^n + a^{n+1}),
+ *                    a^0 = (F(u^0) - eta v^0) / rho at the state last set (or 0).
+ *                    pd_get_state returns the full-step v^n (one extra force
+ *                    evaluation that changes nothing); pd_set_state starts a new
+ *                    history (a^n is formed again from the state given).
+ * One step costs the same in both (one force evaluation).
+ */
+#define PD_INTEGRATOR_EC 0
+#define PD_INTEGRATOR_VV 1
 
 typedef struct {
     double c;             /* micromodulus, Eq. 5 (see pd_micromodulus) */
@@ -85,8 +106,13 @@ typedef struct {
     const double* disp;    /* n*3: prescribed displacement per unit scale (NULL = 0) */
     const double* force;   /* n*3: body-force density per unit load, N m^-3 (NULL = 0) */
     const uint8_t* no_fail;/* n: bonds touching a flagged node never break (NULL = none) */
-    double disp_rate;      /* displacement scale after step k is disp_rate * k */
+    double disp_rate;      /* displacement scale rate, see ramp_steps */
     double load;           /* body-force scale */
+    int64_t ramp_steps;    /* 0: the displacement scale after step k is disp_rate * k;
+                              T > 0: smooth start (Sections 5-6, a fifth-order
+                              displacement-time curve with zero initial velocity and
+                              acceleration): disp_rate * T * P(k/T) for k < T with
+                              P(t) = t^4 - (3/5) t^5, then disp_rate * (k - 3T/5) */
 } pd_bc;
 
 typedef struct {

@@ -118,7 +118,7 @@ def lib():
         L.or_scale.argtypes = [ctypes.c_double, ctypes.c_int64, ctypes.c_int64]
         L.or_run_vv.restype = None
         L.or_run_vv.argtypes = [ctypes.POINTER(_Model), ctypes.c_int64, ctypes.c_int64,
-                                ctypes.c_int, P, P, P, P]
+                                ctypes.c_int, P, P, P, P, P]
         L.or_stiffness_factors.restype = None
         L.or_stiffness_factors.argtypes = [P, P, ctypes.c_int64, ctypes.c_double, P, P,
                                            ctypes.c_int, ctypes.c_double, P]
@@ -290,14 +290,14 @@ class Model:
         lib().or_run(ctypes.byref(self.m), int(first_step), int(nsteps), u.ctypes.data,
                      v.ctypes.data, mu.ctypes.data, _p(margin))
 
-    def run_vv(self, first_step, nsteps, u, v, a, mu, init=False):
+    def run_vv(self, first_step, nsteps, u, v, a, mu, init=False, margin=None):
         """Damped velocity-Verlet steps over all nodes (see oracle.c); u, v, a
         (acceleration) and mu updated in place.  init: form a^0 from (u, v) first."""
         assert self.rows is None
         for arr in (u, v, a):
             assert arr.dtype == np.float64 and arr.flags.c_contiguous
         lib().or_run_vv(ctypes.byref(self.m), int(first_step), int(nsteps), int(bool(init)),
-                        u.ctypes.data, v.ctypes.data, a.ctypes.data, mu.ctypes.data)
+                        u.ctypes.data, v.ctypes.data, a.ctypes.data, mu.ctypes.data, _p(margin))
 
     def damage(self, mu):
         phi = np.empty(self.nrows)

@@ -398,14 +398,14 @@ void or_run(const or_model* m, int64_t first_step, int64_t nsteps, double* u, do
  * v^{n+1} = g (scale(n+1) - scale(n)) / dt, a^{n+1} = 0.
  * With init != 0 the acceleration of the initial state is formed first,
  * a^0 = (F(u^0) - eta v^0) / rho (bonds past s_c at u^0 break).  All nodes are
- * rows.  u, v, a, mu in/out. */
+ * rows.  u, v, a, mu in/out; margin (or NULL) keeps min |s - s_c| per entry. */
 static void vv_accel(const or_model* m, const double* u, const double* vt, uint8_t* mu,
-                     double* acc)
+                     double* margin, double* acc)
 {
 #pragma omp parallel for schedule(dynamic, 256)
     for (int64_t i = 0; i < m->n; ++i) {
         double F[3];
-        row_force(m, i, u, mu, NULL, F);
+        row_force(m, i, u, mu, margin, F);
         for (int a = 0; a < 3; ++a)
             acc[3 * i + a] = m->bc_type[3 * i + a] == 1
                                  ? 0.0
@@ -414,13 +414,13 @@ static void vv_accel(const or_model* m, const double* u, const double* vt, uint8
 }
 
 void or_run_vv(const or_model* m, int64_t first_step, int64_t nsteps, int init, double* u,
-               double* v, double* acc, uint8_t* mu)
+               double* v, double* acc, uint8_t* mu, double* margin)
 {
     int64_t n3 = 3 * m->n;
     double dt = m->dt;
     double* vt = (double*)malloc((size_t)n3 * sizeof(double) + 8);
     double* an = (double*)malloc((size_t)n3 * sizeof(double) + 8);
-    if (init) vv_accel(m, u, v, mu, acc);
+    if (init) vv_accel(m, u, v, mu, margin, acc);
     for (int64_t k = 0; k < nsteps; ++k) {
         int64_t step = first_step + k;
         double s_now = or_scale(m->disp_rate, m->ramp_steps, step);
@@ -434,7 +434,7 @@ void or_run_vv(const or_model* m, int64_t first_step, int64_t nsteps, int init, 
                 vt[e] = v[e] + 0.5 * dt * acc[e];
             }
         }
-        vv_accel(m, u, vt, mu, an);
+        vv_accel(m, u, vt, mu, margin, an);
         for (int64_t e = 0; e < n3; ++e) {
             if (m->bc_type[e] == 1)
                 v[e] = m->bc_disp[e] * (s_next - s_now) / dt;

@@ -26,7 +26,7 @@ __all__ = [
     "pd_get_bonds", "pd_set_bonds", "pd_damage", "pd_set_params", "pd_batch_create",
     "pd_batch_offsets", "pd_autotune", "pd_adjoint_forward", "pd_adjoint_backward",
     "pd_adjoint_backward_static", "pd_stiffness_factors", "PD_STIFF_CONICAL",
-    "PD_STIFF_SURFACE",
+    "PD_STIFF_SURFACE", "PD_INTEGRATOR_EC", "PD_INTEGRATOR_VV",
     "instance_from_workload", "Model",
     "PD_PREC_F32", "PD_PREC_F64",
 ]
@@ -35,6 +35,8 @@ PD_PREC_F64 = 64
 PD_PREC_F32 = 32
 PD_STIFF_CONICAL = 1
 PD_STIFF_SURFACE = 2
+PD_INTEGRATOR_EC = 0
+PD_INTEGRATOR_VV = 1
 _STATUS = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_CUDA", 3: "PD_ERR_OOM",
            4: "PD_ERR_NONFINITE", 5: "PD_ERR_UNSTABLE_DT", 6: "PD_ERR_FAMILY_TOO_LARGE",
            7: "PD_ERR_TIMEOUT", 8: "PD_ERR_STATE"}
@@ -53,7 +55,7 @@ class _Config(ctypes.Structure):
                 ("density", ctypes.c_double), ("check_dt", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("reorder", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+                ("reorder", ctypes.c_int32), ("integrator", ctypes.c_int32)]
 
 
 class _Material(ctypes.Structure):
@@ -65,7 +67,8 @@ class _Material(ctypes.Structure):
 class _Bc(ctypes.Structure):
     _fields_ = [("type", ctypes.c_void_p), ("disp", ctypes.c_void_p),
                 ("force", ctypes.c_void_p), ("no_fail", ctypes.c_void_p),
-                ("disp_rate", ctypes.c_double), ("load", ctypes.c_double)]
+                ("disp_rate", ctypes.c_double), ("load", ctypes.c_double),
+                ("ramp_steps", ctypes.c_int64)]
 
 
 class _Instance(ctypes.Structure):
@@ -175,7 +178,8 @@ def pd_create(coords, volumes, horizon: float, *, c: float, sc: float = 0.0,
               bc_force=None, no_fail=None, disp_rate: float = 0.0, load: float = 0.0,
               dt: float, damping: float, density: float, precision: int = PD_PREC_F64,
               graph_steps: int = 0, check_dt: bool = False, device: int = 0, stream=None,
-              block_threads: int = 0, blocks_per_sm: int = 0, reorder: int = 0) -> int:
+              block_threads: int = 0, blocks_per_sm: int = 0, reorder: int = 0,
+              integrator: int = 0, ramp_steps: int = 0) -> int:
     """Create a model; returns an opaque handle (int).  See pd.h for the semantics."""
     x, kx = _ptr(coords, np.float64)
     n = (kx.numel() if hasattr(kx, "numel") else kx.size) // 3
@@ -199,11 +203,9 @@ def pd_create(coords, volumes, horizon: float, *, c: float, sc: float = 0.0,
         mat.sc_mode = 1
         mat.sc_seed, mat.sc_lo, mat.sc_hi = int(sc_hash[0]), float(sc_hash[1]), float(sc_hash[2])
     bc = _Bc(type=bt, disp=bd, force=bf, no_fail=nf, disp_rate=float(disp_rate),
-             load=float(load))
-    cfg = _Config(precision=int(precision), graph_steps=int(graph_steps), dt=float(dt),
-                  damping=float(damping), density=float(density), check_dt=int(bool(check_dt)),
-                  device=int(device), stream=stream, block_threads=int(block_threads),
-                  blocks_per_sm=int(blocks_per_sm), reorder=int(reorder))
+             load=float(load), ramp_steps=int(ramp_steps))
+    cfg = _config(precision, graph_steps, dt, damping, density, check_dt, device, stream,
+                  block_threads, blocks_per_sm, reorder, integrator)
     h = ctypes.c_void_p()
     _check(lib().pd_create(n, x, vol, float(horizon), fo, fi, cp, ncut, ctypes.byref(mat),
                            ctypes.byref(bc), ctypes.byref(cfg), ctypes.byref(h)))
@@ -287,17 +289,18 @@ def pd_set_params(h: int, c: float, sc: float, load: float, disp_rate: float,
 
 
 def _config(precision, graph_steps, dt, damping, density, check_dt, device, stream,
-            block_threads, blocks_per_sm, reorder):
+            block_threads, blocks_per_sm, reorder, integrator=0):
     return _Config(precision=int(precision), graph_steps=int(graph_steps), dt=float(dt),
                    damping=float(damping), density=float(density), check_dt=int(bool(check_dt)),
                    device=int(device), stream=stream, block_threads=int(block_threads),
-                   blocks_per_sm=int(blocks_per_sm), reorder=int(reorder))
+                   blocks_per_sm=int(blocks_per_sm), reorder=int(reorder),
+                   integrator=int(integrator))
 
 
 def pd_batch_create(instances, *, dt: float, damping: float, density: float,
                     precision: int = PD_PREC_F64, graph_steps: int = 0, check_dt: bool = False,
                     device: int = 0, stream=None, block_threads: int = 0,
-                    blocks_per_sm: int = 0, reorder: int = 0) -> int:
+                    blocks_per_sm: int = 0, reorder: int = 0, integrator: int = 0) -> int:
     """Create a batch handle from a list of dicts with the keys of ``pd_create``'s
     body arguments: coords, volumes, horizon, c, sc / sc_hash, cuts, bc_type,
     bc_disp, bc_force, no_fail, disp_rate, load."""
@@ -324,9 +327,10 @@ def pd_batch_create(instances, *, dt: float, damping: float, density: float,
                            n_cuts=0 if ca is None else ca.shape[0], mat=mat,
                            bc=_Bc(type=bt, disp=bd, force=bf, no_fail=nf,
                                   disp_rate=float(I.get("disp_rate", 0.0)),
-                                  load=float(I.get("load", 0.0))))
+                                  load=float(I.get("load", 0.0)),
+                                  ramp_steps=int(I.get("ramp_steps", 0))))
     cfg = _config(precision, graph_steps, dt, damping, density, check_dt, device, stream,
-                  block_threads, blocks_per_sm, reorder)
+                  block_threads, blocks_per_sm, reorder, integrator)
     h = ctypes.c_void_p()
     _check(lib().pd_batch_create(len(instances), arr, ctypes.byref(cfg), ctypes.byref(h)))
     return h.value
@@ -409,7 +413,8 @@ def instance_from_workload(w, c=None) -> dict:
         c = pd_micromodulus(w.bulk_modulus, w.horizon)
     return dict(coords=w.coords, volumes=w.volumes, horizon=w.horizon, c=c, sc=w.sc,
                 sc_hash=w.sc_hash, cuts=w.cuts_array(), bc_type=w.bc_type, bc_disp=w.bc_disp,
-                bc_force=w.bc_force, no_fail=w.no_fail, disp_rate=w.disp_rate, load=w.load)
+                bc_force=w.bc_force, no_fail=w.no_fail, disp_rate=w.disp_rate, load=w.load,
+                ramp_steps=getattr(w, "ramp_steps", 0))
 
 
 class Model:
@@ -440,7 +445,8 @@ class Model:
         return cls(coords=w.coords, volumes=w.volumes, horizon=w.horizon, c=c, sc=w.sc,
                    sc_hash=w.sc_hash, cuts=w.cuts_array(), bc_type=w.bc_type, bc_disp=w.bc_disp,
                    bc_force=w.bc_force, no_fail=w.no_fail, disp_rate=w.disp_rate, load=w.load,
-                   dt=w.dt, damping=w.damping, density=w.density, precision=precision, **kw)
+                   dt=w.dt, damping=w.damping, density=w.density, precision=precision,
+                   ramp_steps=getattr(w, "ramp_steps", 0), **kw)
 
     def close(self):
         if self.h:

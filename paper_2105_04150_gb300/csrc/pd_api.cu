@@ -115,6 +115,10 @@ struct pd_handle {
     double* x64 = nullptr;
     double* vol = nullptr;
     double* ilen = nullptr;  // FP64: per slot 1 / |xi|
+    int integrator = PD_INTEGRATOR_EC;
+    int64_t ramp_steps = 0;
+    void* vpeek = nullptr;  // velocity-Verlet: full-step velocity for pd_get_state
+    int64_t peek_step = -1; // step whose force pass filled vpeek (-1: none)
     void* wsum_inv = nullptr;
     void* damage = nullptr;
     int* err = nullptr;
@@ -219,6 +223,8 @@ StepArgsF32 args_f32(pd_handle* h, int k)
     a.rho = h->rho;
     a.disp_rate = h->disp_rate;
     a.load = h->load;
+    a.ramp_steps = h->ramp_steps;
+    a.vv = h->integrator == PD_INTEGRATOR_VV ? 1 : 0;
     a.delta = h->delta;
     a.inv_delta = 1.0 / h->delta;
     return a;
@@ -259,6 +265,8 @@ StepArgsF64 args_f64(pd_handle* h, int k)
     a.rho = h->rho;
     a.disp_rate = h->disp_rate;
     a.load = h->load;
+    a.ramp_steps = h->ramp_steps;
+    a.vv = h->integrator == PD_INTEGRATOR_VV ? 1 : 0;
     return a;
 }
 
@@ -307,6 +315,32 @@ pd_status check_dev_err(pd_handle* h)
     PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
     if (e & PD_DEVERR_NONFINITE)
         return fail(PD_ERR_NONFINITE, "a displacement became non-finite (check dt and loads)");
+    return PD_OK;
+}
+
+// Velocity-Verlet evaluates the force at u^n at the start of the next step;
+// what the method has at the end of step n (the breaks at u^n, the full-step
+// velocity v^n) comes from that pass run once ahead: it records the breaks
+// (the next step would make the same decisions on the same u^n) and writes
+// v^n into vpeek, nothing else.  Cached per step.
+pd_status vv_force_pass(pd_handle* h)
+{
+    if (h->integrator != PD_INTEGRATOR_VV || h->peek_step == h->step) return PD_OK;
+    cudaError_t e;
+    if (h->precision == 32) {
+        StepArgsF32 a = args_f32(h, 0);
+        a.peek = 1;
+        a.vout = (float*)h->vpeek;
+        e = launch_step_f32(a, h->sc_mode, h->grid, h->block, h->stream);
+    } else {
+        StepArgsF64 a = args_f64(h, 0);
+        a.peek = 1;
+        a.vout = (double*)h->vpeek;
+        e = launch_step_f64(a, h->sc_mode, h->grid, h->block, h->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "velocity-Verlet force pass");
+    h->peek_step = h->step;
+    h->damage_fresh = false;  // breaks may have been recorded: damage from the flags
     return PD_OK;
 }
 
@@ -371,6 +405,8 @@ pd_status check_cfg(const pd_config* cfg)
         (cfg->block_threads < 32 || cfg->block_threads > 256 || cfg->block_threads % 32))
         return fail(PD_ERR_ARG, "block_threads must be a multiple of 32 in [32, 256]");
     if (cfg->reorder != 0 && cfg->reorder != 1) return fail(PD_ERR_ARG, "reorder must be 0 or 1");
+    if (cfg->integrator != PD_INTEGRATOR_EC && cfg->integrator != PD_INTEGRATOR_VV)
+        return fail(PD_ERR_ARG, "integrator must be PD_INTEGRATOR_EC or PD_INTEGRATOR_VV");
     return PD_OK;
 }
 
@@ -398,6 +434,7 @@ pd_status check_body(int64_t n, const double* coords, const double* volumes, dou
     if (!(horizon > 0.0) || !std::isfinite(horizon)) return fail(PD_ERR_ARG, "horizon must be > 0");
     if (!std::isfinite(bc->disp_rate) || !std::isfinite(bc->load))
         return fail(PD_ERR_ARG, "disp_rate and load must be finite");
+    if (bc->ramp_steps < 0) return fail(PD_ERR_ARG, "ramp_steps must be >= 0");
     if (!finite_all(coords, 3 * n)) return fail(PD_ERR_ARG, "non-finite coordinates");
     for (int64_t i = 0; i < n; ++i)
         if (!(volumes[i] > 0.0) || !std::isfinite(volumes[i]))
@@ -442,6 +479,7 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
     h->eta = cfg->damping;
     h->rho = cfg->density;
     h->graph_steps = cfg->graph_steps;
+    h->integrator = cfg->integrator;
     h->block = cfg->block_threads ? cfg->block_threads : 256;
     h->device = cfg->device;
     h->vol0 = d.wvol[0];
@@ -507,7 +545,13 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
     ALLOC(h->x64, double, 3 * np);
     ALLOC(h->vol, double, np);
     ALLOC(h->err, int, 1);
-    ALLOC(h->step_ctr, int64_t, 1);
+    ALLOC(h->step_ctr, int64_t, 2);  // [0] step counter, [1] step of the last set state
+    if (h->integrator == PD_INTEGRATOR_VV) {
+        if (f32)
+            ALLOC(h->vpeek, float, 3 * np);
+        else
+            ALLOC(h->vpeek, double, 3 * np);
+    }
     ALLOC(h->staging, double, 3 * n);
     if (!d.inst.empty()) {
         ALLOC(h->inst, int32_t, np);
@@ -613,6 +657,7 @@ void set_material(pd_handle* h, const pd_material* mat, const pd_bc* bc)
     h->sc_hi = mat->sc_mode == 1 ? mat->sc_hi : mat->sc;
     h->disp_rate = bc->disp_rate;
     h->load = bc->load;
+    h->ramp_steps = bc->ramp_steps;
 }
 
 }  // namespace
@@ -689,8 +734,10 @@ pd_status pd_batch_create(int32_t n_inst, const pd_instance* inst, const pd_conf
         if ((st = check_body(I.n, I.coords, I.volumes, I.horizon, I.cuts, I.n_cuts, &I.bc)) != PD_OK ||
             (st = check_material(&I.mat)) != PD_OK)
             return fail(st, "instance %d: %s", b, g_err.c_str());
-        if (I.bc.disp_rate != inst[0].bc.disp_rate || I.bc.load != inst[0].bc.load)
-            return fail(PD_ERR_ARG, "instance %d: disp_rate and load must equal instance 0's", b);
+        if (I.bc.disp_rate != inst[0].bc.disp_rate || I.bc.load != inst[0].bc.load ||
+            I.bc.ramp_steps != inst[0].bc.ramp_steps)
+            return fail(PD_ERR_ARG,
+                        "instance %d: disp_rate, load and ramp_steps must equal instance 0's", b);
         n += I.n;
         unit = std::max(unit, I.horizon);
         any_nofail = any_nofail || I.bc.no_fail != nullptr;
@@ -873,6 +920,12 @@ pd_status pd_get_state(pd_handle* h, double* u, double* v, int64_t* step)
     if (!h) return fail(PD_ERR_ARG, "NULL handle");
     PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
     const int cur = (int)(h->step & 1);
+    const void* vsrc = h->v;
+    if (v && h->integrator == PD_INTEGRATOR_VV) {
+        pd_status st = vv_force_pass(h);
+        if (st != PD_OK) return st;
+        vsrc = h->vpeek;
+    }
     double* outs[2] = {u, v};
     for (int w = 0; w < 2; ++w) {
         double* o = outs[w];
@@ -882,11 +935,11 @@ pd_status pd_get_state(pd_handle* h, double* u, double* v, int64_t* step)
         double* uo = w == 0 ? dst : nullptr;
         double* vo = w == 1 ? dst : nullptr;
         if (h->precision == 32)
-            PD_CUDA(launch_get_state_f32(h->rec32[cur], h->lo32, (const float*)h->v, h->gid,
+            PD_CUDA(launch_get_state_f32(h->rec32[cur], h->lo32, (const float*)vsrc, h->gid,
                                          h->n, h->delta, uo, vo, h->stream),
                     "get state");
         else
-            PD_CUDA(launch_get_state_f64(h->rec[cur], (const double*)h->v, h->gid, h->n, uo, vo,
+            PD_CUDA(launch_get_state_f64(h->rec[cur], (const double*)vsrc, h->gid, h->n, uo, vo,
                                          h->stream),
                     "get state");
         if (!dev)
@@ -932,8 +985,14 @@ pd_status pd_set_state(pd_handle* h, const double* u, const double* v, int64_t s
                     "set state");
         if (src == h->staging) PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
     }
+    // the velocity-Verlet history starts again at this step (a^n formed afresh)
+    PD_CUDA(cudaMemcpyAsync(h->step_ctr + 1, &h->step, sizeof(int64_t), cudaMemcpyHostToDevice,
+                            h->stream),
+            "set history start");
+    PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
     PD_CUDA(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream), "clear error flag");
     h->damage_fresh = false;
+    h->peek_step = -1;
     return PD_OK;
 }
 
@@ -941,8 +1000,10 @@ pd_status pd_get_bonds(pd_handle* h, uint8_t* mu)
 {
     if (!h || !mu) return fail(PD_ERR_ARG, "NULL argument");
     PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    pd_status st = vv_force_pass(h);
+    if (st != PD_OK) return st;
     std::vector<int64_t> pos;
-    pd_status st = canonical_slots(h, pos);
+    st = canonical_slots(h, pos);
     if (st != PD_OK) return st;
     std::vector<uint32_t> bits((size_t)(h->n_slices * h->Q * 32));
     PD_CUDA(cudaMemcpy(bits.data(), h->bits, bits.size() * 4, cudaMemcpyDeviceToHost),
@@ -975,6 +1036,7 @@ pd_status pd_set_bonds(pd_handle* h, const uint8_t* mu)
     PD_CUDA(cudaMemcpy(h->bits, bits.data(), bits.size() * 4, cudaMemcpyHostToDevice),
             "upload bond flags");
     h->damage_fresh = false;
+    h->peek_step = -1;
     return PD_OK;
 }
 
@@ -982,6 +1044,8 @@ pd_status pd_damage(pd_handle* h, double* phi)
 {
     if (!h || !phi) return fail(PD_ERR_ARG, "NULL argument");
     PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    pd_status st = vv_force_pass(h);
+    if (st != PD_OK) return st;
     const bool dev = is_device_ptr(phi);
     double* dst = dev ? phi : h->staging;
     if (h->damage_fresh)  // written by the last step kernel (fused)
@@ -1000,8 +1064,9 @@ pd_status pd_damage(pd_handle* h, double* phi)
 pd_status pd_adjoint_forward(pd_handle* h, int64_t n_steps, int64_t checkpoint_every)
 {
     if (!h) return fail(PD_ERR_ARG, "NULL handle");
-    if (h->precision != 64 || h->batch)
-        return fail(PD_ERR_STATE, "the adjoint is available on FP64 single-model handles");
+    if (h->precision != 64 || h->batch || h->integrator != PD_INTEGRATOR_EC)
+        return fail(PD_ERR_STATE,
+                    "the adjoint is available on FP64 single-model Euler-Cromer handles");
     if (n_steps < 1 || checkpoint_every < 0)
         return fail(PD_ERR_ARG, "need n_steps >= 1 and checkpoint_every >= 0");
     PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
@@ -1181,6 +1246,7 @@ pd_status pd_adjoint_backward(pd_handle* h, const double* dLdu, const double* dL
     if (ke == cudaSuccess)
         ke = cudaMemcpyAsync(h->v, T.fin_v, 8 * np3, cudaMemcpyDeviceToDevice, h->stream);
     h->damage_fresh = false;
+    h->peek_step = -1;
     if (ke != cudaSuccess) return cuda_fail(ke, "adjoint sweep");
 
     // outputs
@@ -1245,7 +1311,7 @@ pd_status pd_autotune(pd_handle* h, int32_t trial_steps, int32_t* block_threads,
         bufs.push_back({h->damage, (size_t)(8 * np), {}});
     }
     bufs.push_back({h->bits, (size_t)(4 * h->n_slices * h->Q * 32), {}});
-    bufs.push_back({h->step_ctr, sizeof(int64_t), {}});
+    bufs.push_back({h->step_ctr, 2 * sizeof(int64_t), {}});
     bufs.push_back({h->err, sizeof(int), {}});
     for (Buf& b : bufs) {
         b.keep.resize(b.bytes);
@@ -1368,6 +1434,7 @@ pd_status pd_set_params(pd_handle* h, double c, double sc, double load, double d
     }
     PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
     h->damage_fresh = false;
+    h->peek_step = -1;
     return PD_OK;
 }
 
@@ -1548,6 +1615,7 @@ pd_status pd_adjoint_backward_static(pd_handle* h, const double* dLdu, const dou
     if (ke == cudaSuccess)
         ke = cudaMemcpyAsync(h->v, T.fin_v, 8 * np3, cudaMemcpyDeviceToDevice, h->stream);
     h->damage_fresh = false;
+    h->peek_step = -1;
     if (ke != cudaSuccess) return cuda_fail(ke, "adjoint sweep");
 
     if (dL_dload) {

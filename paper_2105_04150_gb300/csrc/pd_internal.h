@@ -89,6 +89,10 @@ struct StepArgsF32 {
     double sc, sc_lo, sc_hi;
     uint64_t sc_seed;
     double dt, eta, rho, disp_rate, load, delta, inv_delta;
+    int64_t ramp_steps;        // smooth loading start over this many steps (0 = linear)
+    int32_t vv;                // 1: damped velocity-Verlet, 0: damped Euler-Cromer
+    int32_t peek;              // 1: forces and full-step velocity into vout only
+    float* vout;               // peek: 3 floats per node (library order)
 };
 
 struct StepArgsF64 {
@@ -119,6 +123,10 @@ struct StepArgsF64 {
     double sc, sc_lo, sc_hi;
     uint64_t sc_seed;
     double dt, eta, rho, disp_rate, load;
+    int64_t ramp_steps;        // smooth loading start over this many steps (0 = linear)
+    int32_t vv;                // 1: damped velocity-Verlet, 0: damped Euler-Cromer
+    int32_t peek;              // 1: forces and full-step velocity into vout only
+    double* vout;              // peek: 3 doubles per node (library order)
 };
 
 // Arguments of one reverse step of the FP64 adjoint (pd_adjoint.cu); node arrays
@@ -201,6 +209,23 @@ cudaError_t launch_gather_damage(int precision, const void* dmg, const int32_t* 
 // per slot 1 / |x_j - x_i| from the FP64 reference positions (0 for unused slots)
 cudaError_t launch_inv_len(const double* x64, const int32_t* nbr, const int32_t* sw, int64_t n,
                            int Q, double* ilen, cudaStream_t s);
+// step_ctr[0] is the device step counter; step_ctr[1] the step at which the
+// state was last set (velocity-Verlet forms a^n afresh there)
+
+#ifdef __CUDACC__
+// Displacement scale after step k: rate * k, or with a smooth start over T
+// steps (a fifth-order displacement-time curve, zero initial velocity and
+// acceleration): rate * T * P(k/T), P(t) = t^4 - (3/5) t^5, then the line
+// rate * (k - 3T/5) that continues it.
+__device__ __forceinline__ double bc_scale(double rate, int64_t T, int64_t k)
+{
+    if (T <= 0) return rate * (double)k;
+    if (k >= T) return rate * ((double)k - 0.6 * (double)T);
+    const double t = (double)k / (double)T;
+    return rate * (double)T * (t * t * t * t - 0.6 * t * t * t * t * t);
+}
+#endif
+
 // 1/sqrt(x), x > 0, in FP64: the FP32 hardware estimate refined by two
 // Newton-Raphson steps for f(y) = 1/y^2 - x (quadratic convergence: relative
 // error ~2^-22 -> ~2^-43 -> rounding level); residual r = 1 - x y^2 taken with

@@ -316,7 +316,8 @@ __global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS)
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t step = *a.step_ctr + a.k;
+    const int64_t step = a.step_ctr[0] + a.k;
+    const bool first = a.vv && step == a.step_ctr[1];  // velocity-Verlet: a^n formed afresh
     const int cur = (int)(step & 1);
     const int Q = a.Q;
     const int64_t W = 32LL * Q;
@@ -415,7 +416,8 @@ __global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS)
         }
         if (UW) ws = wc * (float)alive_count;
 
-        // ---- integration of the lane's node (Eq. 11, damped Euler-Cromer)
+        // ---- integration of the lane's node (damped Euler-Cromer, Eq. 11, or
+        // damped velocity-Verlet)
         if (i < a.n) {
             const uint32_t cls = a.bcc[i];
             uint32_t mask = 0u;
@@ -435,18 +437,33 @@ __global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS)
             bool finite = true;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
+                // stored velocity: v^n (Euler-Cromer) or, for velocity-Verlet, the
+                // half-step velocity v^{n-1} + dt/2 a^{n-1} (v^n right after a set state)
                 const float vi = a.v[3 * i + c];
-                float vn = vi + dtf * (F[c] - etaf * vi) / rhof;
+                float vn, vfull;
+                if (a.vv) {
+                    const float acc = (F[c] - etaf * vi) / rhof;
+                    vfull = first ? vi : vi + 0.5f * dtf * acc;
+                    vn = vfull + 0.5f * dtf * acc;
+                } else {
+                    vn = vi + dtf * (F[c] - etaf * vi) / rhof;
+                    vfull = vn;
+                }
                 ff_add(H[c], L[c], vn * dtd);
                 if (mask & (1u << c)) {
-                    const double s_now = a.disp_rate * (double)step;
-                    const double s_next = a.disp_rate * (double)(step + 1);
+                    const double s_now = bc_scale(a.disp_rate, a.ramp_steps, step);
+                    const double s_next = bc_scale(a.disp_rate, a.ramp_steps, step + 1);
                     ff_set(bc->disp[c] * s_next * a.inv_delta, H[c], L[c]);
                     vn = (float)(bc->disp[c] * (s_next - s_now) / a.dt);
+                    vfull = vi;
                 }
                 finite = finite && isfinite(H[c]);
-                a.v[3 * i + c] = vn;
+                if (a.peek)
+                    a.vout[3 * i + c] = vfull;
+                else
+                    a.v[3 * i + c] = vn;
             }
+            if (a.peek) continue;
             st_rec(Rout + 2 * i, make_float4(ni.x, ni.y, ni.z, H[0]),
                    make_float4(H[1], H[2], bf_pack(L[1], L[0]), bf_pack(0.0f, L[2])));
             a.lo32[i] = make_float4(L[0], L[1], L[2], 0.0f);

@@ -51,7 +51,8 @@ __global__ void __launch_bounds__(256) k_step_f64(const StepArgsF64 a)
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t step = *a.step_ctr + a.k;
+    const int64_t step = a.step_ctr[0] + a.k;
+    const bool first = a.vv && step == a.step_ctr[1];  // velocity-Verlet: a^n formed afresh
     const int cur = (int)(step & 1);
     const int Q = a.Q;
     const int64_t W = 32LL * Q;
@@ -144,24 +145,39 @@ __global__ void __launch_bounds__(256) k_step_f64(const StepArgsF64 a)
                     F[c] += a.load * bc.force[c];
                 }
             }
-            const double s_now = a.disp_rate * (double)step;
-            const double s_next = a.disp_rate * (double)(step + 1);
+            const double s_now = bc_scale(a.disp_rate, a.ramp_steps, step);
+            const double s_next = bc_scale(a.disp_rate, a.ramp_steps, step + 1);
             const double uo[3] = {u01.x, u01.y, u23.x};
             double un[3];
             bool finite = true;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
+                // stored velocity: v^n (Euler-Cromer) or, for velocity-Verlet, the
+                // half-step velocity v^{n-1} + dt/2 a^{n-1} (v^n right after a set state)
                 const double vi = a.v[3 * i + c];
-                double vn = vi + a.dt * (F[c] - a.eta * vi) / a.rho;
+                double vn, vfull;
+                if (a.vv) {
+                    const double acc = (F[c] - a.eta * vi) / a.rho;
+                    vfull = first ? vi : vi + 0.5 * a.dt * acc;
+                    vn = vfull + 0.5 * a.dt * acc;
+                } else {
+                    vn = vi + a.dt * (F[c] - a.eta * vi) / a.rho;
+                    vfull = vn;
+                }
                 double u = uo[c] + a.dt * vn;
                 if (mask & (1u << c)) {
                     u = gdisp[c] * s_next;
                     vn = gdisp[c] * (s_next - s_now) / a.dt;
+                    vfull = vi;
                 }
                 finite = finite && isfinite(u);
                 un[c] = u;
-                a.v[3 * i + c] = vn;
+                if (a.peek)
+                    a.vout[3 * i + c] = vfull;
+                else
+                    a.v[3 * i + c] = vn;
             }
+            if (a.peek) continue;
             rout[4 * i] = x01;
             rout[4 * i + 1] = x23;
             rout[4 * i + 2] = make_double2(un[0], un[1]);

@@ -131,6 +131,6 @@ def test_batch_create_rejects_bad_instances(L):
     other = dict(inst, load=5.0)
     with pytest.raises(pdgb.PdError) as e:
         pdgb.pd_batch_create([inst, other], dt=1e-7, damping=0.0, density=2400.0)
-    assert "disp_rate and load" in str(e.value)
+    assert "disp_rate, load and ramp_steps" in str(e.value)
     with pytest.raises(pdgb.PdError):
         pdgb.pd_batch_create([inst], dt=0.0, damping=0.0, density=2400.0)
