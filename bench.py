@@ -62,6 +62,10 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="beam",
                    choices=["beam", "plate", "bar", "batch", "adjoint"])
+    p.add_argument("--integrator", default="ec", choices=["ec", "vv"],
+                   help="damped Euler-Cromer (default) or damped velocity-Verlet")
+    p.add_argument("--ramp-steps", type=int, default=0,
+                   help="smooth start of the displacement loading over this many steps")
     p.add_argument("--fd-directions", type=int, default=32)
     p.add_argument("--checkpoint-every", type=int, default=45)
     p.add_argument("--precision", type=int, default=32, choices=[32, 64])
@@ -79,8 +83,10 @@ def make_workload(name):
     return workloads.tensile_bar()
 
 
-def describe(w, n_bonds, precision):
+def describe(w, n_bonds, precision, integrator="ec"):
     return {
+        "integrator": {"ec": "damped Euler-Cromer", "vv": "damped velocity-Verlet"}[integrator],
+        "ramp_steps": int(getattr(w, "ramp_steps", 0)),
         "workload": f"{w.name}: {w.n:,} nodes, {n_bonds:,} directed bonds, "
                     f"delta = {w.horizon / w.dx:.4g} dx, "
                     + ("per-bond s_c ~ U[9e-5, 1.1e-4)" if w.sc_hash else f"s_c = {w.sc:g}"),
@@ -283,11 +289,13 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev_sync = torch.cuda.synchronize
     w = make_workload(args.workload)
+    w.ramp_steps = args.ramp_steps
     c = pdgb.pd_micromodulus(w.bulk_modulus, w.horizon)
     stream = torch.cuda.Stream(device=local)
     G = max(0, min(args.graph_steps, args.steps))
     m = pdgb.Model.from_workload(w, precision=args.precision, c=c, graph_steps=G,
-                                 stream=stream.cuda_stream, device=local)
+                                 stream=stream.cuda_stream, device=local,
+                                 integrator=1 if args.integrator == "vv" else 0)
     info = m.info()
     n_bonds = info["n_bonds"]
     # warm-up: W steps (also captures the graph)
@@ -373,7 +381,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "time_steps_per_s": 1e3 / ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.precision == 32 else "f64",
-        "data": "synthetic", "config": describe(w, n_bonds, args.precision),
+        "data": "synthetic", "config": describe(w, n_bonds, args.precision, args.integrator),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk.summary(t_on, t_off),
     }
