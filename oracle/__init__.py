@@ -31,6 +31,10 @@ What pins each function (tests in ``tests/test_oracle_pins.py``):
   volume correction is symmetric, 1 between bulk nodes when V0 is the bulk
   family volume, and equals 2 V0 / (V_i + V_j) with V_i counted directly from
   the stencil for nodes on a free face (``tests/test_oracle_stiffness.py``).
+* bilinear softening (``kr`` > 1): reduces to the PMB law bit for bit at
+  kr = 1; a two-node bond follows the closed-form bilinear envelope under
+  loading, unloads along the secant to the origin and reloads onto the
+  envelope; the remembered stretch never decreases (``tests/test_oracle_soft.py``).
 * ``adjoint``: central differences of the pinned forward run
   (``tests/test_oracle_adjoint.py``).
 """
@@ -80,6 +84,7 @@ class _Model(ctypes.Structure):
         ("disp_rate", ctypes.c_double), ("load", ctypes.c_double),
         ("dt", ctypes.c_double), ("damping", ctypes.c_double), ("density", ctypes.c_double),
         ("ramp_steps", ctypes.c_int64),
+        ("kr", ctypes.c_double), ("kappa", ctypes.c_void_p),
     ]
 
 
@@ -220,7 +225,7 @@ class Model:
     def __init__(self, coords, volumes, off, idx, *, c, sc=None, sc_hash=None,
                  c_bond=None, no_fail=None, bc_type=None, bc_disp=None, bc_force=None,
                  disp_rate=0.0, load=0.0, dt=1e-7, damping=0.0, density=1.0, rows=None,
-                 ramp_steps=0):
+                 ramp_steps=0, kr=0.0):
         self.x = _c64(coords)
         n = self.x.shape[0]
         self.vol = _c64(volumes)
@@ -257,6 +262,10 @@ class Model:
         m.disp_rate, m.load = float(disp_rate), float(load)
         m.dt, m.damping, m.density = float(dt), float(damping), float(density)
         m.ramp_steps = int(ramp_steps)
+        # bilinear softening (kr > 1): the largest stretch of each family entry
+        self.kappa = np.zeros(max(int(self.off[-1]), 1))
+        m.kr = float(kr)
+        m.kappa = self.kappa.ctypes.data
         self.m = m
         self.nrows = m.nrows
         self.nbonds = int(self.off[-1])
@@ -269,7 +278,7 @@ class Model:
                    c_bond=c_bond, no_fail=w.no_fail, bc_type=w.bc_type, bc_disp=w.bc_disp,
                    bc_force=w.bc_force, disp_rate=w.disp_rate, load=w.load, dt=w.dt,
                    damping=w.damping, density=w.density, rows=rows,
-                   ramp_steps=getattr(w, "ramp_steps", 0))
+                   ramp_steps=getattr(w, "ramp_steps", 0), kr=getattr(w, "kr", 0.0))
 
     def step(self, step_index, u, v, mu, margin=None, want_force=False):
         """One step; returns (u_out, v_out[, F]) per row.  mu/margin updated in place."""

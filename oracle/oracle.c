@@ -274,7 +274,26 @@ typedef struct {
     double load;             /* body-force scale */
     double dt, damping, density;
     int64_t ramp_steps;      /* 0: scale(k) = disp_rate k; T > 0: smooth start over T steps */
+    double kr;               /* >= 1: bilinear softening with s_0 = s_c / kr; 0: PMB */
+    double* kappa;           /* kr >= 1: largest stretch each family entry has reached */
 } or_model;
+
+/* Bilinear bond law (Section 6, Example 3: the damage model of Gerstle et al.,
+ * with s_0 the linear elastic limit and k_r = s_c / s_0): the force rises as
+ * c s up to s_0, then falls linearly to zero at s_c.  The bond remembers the
+ * largest stretch kappa it has reached, and below the envelope it unloads
+ * towards the origin; its integrity is
+ *   mu(kappa) = 1                                   kappa <= s_0
+ *             = s_0 (s_c - kappa) / (kappa (s_c - s_0))   s_0 < kappa < s_c
+ *             = 0 (broken, irreversibly)             kappa >= s_c
+ * and the force is c s mu(kappa) V_j y/|y|.  kr = 1 (s_0 = s_c) is the PMB law
+ * again, with the history kept. */
+static double soft_mu(double kappa, double s0, double sc)
+{
+    if (kappa <= s0) return 1.0;
+    if (kappa >= sc) return 0.0;
+    return s0 * (sc - kappa) / (kappa * (sc - s0));
+}
 
 /* Displacement scale after step k.  Linear, rate * k, or with a smooth start
  * (Sections 5-6: a fifth-order polynomial displacement-time curve, so that the
@@ -326,12 +345,18 @@ static void row_force(const or_model* m, int64_t r, const double* u, uint8_t* mu
             if (d < margin[k]) margin[k] = d;
         }
         int nofail = m->no_fail && (m->no_fail[i] || m->no_fail[j]);
-        if (s >= sc && !nofail) {
+        double kap = s;
+        if (m->kr >= 1.0) {
+            kap = m->kappa[k] > s ? m->kappa[k] : s;
+            m->kappa[k] = kap;
+        }
+        if (kap >= sc && !nofail) {
             mu[k] = 0;
             continue;
         }
         double cij = m->c_bond ? m->c_bond[k] : m->c;
         double f = cij * s * m->vol[j] / rr;
+        if (m->kr >= 1.0) f = cij * s * soft_mu(kap, sc / m->kr, sc) * m->vol[j] / rr;
         for (int a = 0; a < 3; ++a) F[a] += f * y[a];
     }
     if (m->bc_force)
@@ -454,10 +479,18 @@ void or_damage(const or_model* m, const uint8_t* mu, double* phi)
 #pragma omp parallel for schedule(static)
     for (int64_t r = 0; r < m->nrows; ++r) {
         double num = 0.0, den = 0.0;
+        int64_t i = m->rows ? m->rows[r] : r;
         for (int64_t k = m->off[r]; k < m->off[r + 1]; ++k) {
             double vj = m->vol[m->idx[k]];
             den += vj;
-            if (mu[k]) num += vj;
+            if (!mu[k]) continue;
+            if (m->kr >= 1.0) {
+                /* Eq. (8) with the bond's integrity mu(kappa) in [0, 1] */
+                double sc = bond_sc(m, i, m->idx[k]);
+                num += soft_mu(m->kappa[k], sc / m->kr, sc) * vj;
+            } else {
+                num += vj;
+            }
         }
         phi[r] = den > 0.0 ? 1.0 - num / den : 0.0;
     }

@@ -56,6 +56,7 @@ class Workload:
     shape: Tuple[int, int, int]
     dx: float
     ramp_steps: int = 0       # 0: displacement scale rate*k; T: smooth start over T steps
+    kr: float = 0.0           # > 1: bilinear softening with s_0 = s_c / kr
 
     @property
     def n(self) -> int:
