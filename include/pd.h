@@ -99,8 +99,21 @@ typedef struct {
     uint64_t sc_seed;     /* sc_mode 1: SplitMix64 seed; bond {i,j} uses output
                              min(i,j)*2^32 + max(i,j) + 1 of the stream (caller ids) */
     double sc_lo, sc_hi;
+    double kr;            /* 0 = PMB (Eq. 5-6); >= 1 = bilinear softening, see below */
 } pd_material;
 
+/*
+ * Bilinear softening (Section 6, Example 3: the damage model with linear
+ * elastic limit s_0 and k_r = s_c / s_0 = G_F / G_0, s_0 = sqrt(5 G_0 / (6 E delta))):
+ * with kr >= 1 every bond has s_0 = s_c / kr and an integrity
+ *   mu = 1                                    while its stretch never exceeded s_0,
+ *   mu = s_0 (s_c - k) / (k (s_c - s_0))      k = the largest stretch so far (< s_c),
+ *   mu = 0                                    once k >= s_c (broken, as in Eq. 6),
+ * and pulls with c s mu V_j (Eq. 5 times mu): the force rises to c s_0, falls
+ * linearly to zero at s_c, and unloads along the secant to the origin.  The
+ * damage (Eq. 8) weighs each bond by its integrity.  kr = 1 is the PMB law.
+ * Not available in batches or with the adjoint.
+ */
 typedef struct {
     const uint8_t* type;   /* n*3: 1 = displacement-controlled component, 0 = free */
     const double* disp;    /* n*3: prescribed displacement per unit scale (NULL = 0) */
@@ -225,6 +238,15 @@ pd_status pd_set_state(pd_handle* h, const double* u, const double* v, int64_t s
  * directed bond in canonical order (host).  pd_set_bonds rejects values other than 0/1.
  */
 pd_status pd_get_bonds(pd_handle* h, uint8_t* mu);
+
+/*
+ * pd_get_bond_integrity - each directed bond's integrity mu in [0, 1] (canonical
+ * order, host doubles): the bilinear-softening factor above, or 1 / 0 for an
+ * intact / broken bond of the PMB law.
+ */
+pd_status pd_get_bond_integrity(pd_handle* h, double* mu);
+/* (With bilinear softening, pd_set_bonds also restarts every bond's history:
+ * integrity 1 for the bonds it marks intact, 0 for the others.) */
 pd_status pd_set_bonds(pd_handle* h, const uint8_t* mu);
 
 /*

@@ -25,7 +25,7 @@ __all__ = [
     "pd_get_info", "pd_get_family", "pd_step", "pd_sync", "pd_get_state", "pd_set_state",
     "pd_get_bonds", "pd_set_bonds", "pd_damage", "pd_set_params", "pd_batch_create",
     "pd_batch_offsets", "pd_autotune", "pd_adjoint_forward", "pd_adjoint_backward",
-    "pd_adjoint_backward_static", "pd_stiffness_factors", "PD_STIFF_CONICAL",
+    "pd_adjoint_backward_static", "pd_stiffness_factors", "pd_get_bond_integrity", "PD_STIFF_CONICAL",
     "PD_STIFF_SURFACE", "PD_INTEGRATOR_EC", "PD_INTEGRATOR_VV",
     "instance_from_workload", "Model",
     "PD_PREC_F32", "PD_PREC_F64",
@@ -61,7 +61,8 @@ class _Config(ctypes.Structure):
 class _Material(ctypes.Structure):
     _fields_ = [("c", ctypes.c_double), ("sc", ctypes.c_double), ("sc_mode", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("sc_seed", ctypes.c_uint64),
-                ("sc_lo", ctypes.c_double), ("sc_hi", ctypes.c_double)]
+                ("sc_lo", ctypes.c_double), ("sc_hi", ctypes.c_double),
+                ("kr", ctypes.c_double)]
 
 
 class _Bc(ctypes.Structure):
@@ -120,6 +121,7 @@ def lib():
             "pd_adjoint_backward": [P, P, P, P, P, P, P],
             "pd_adjoint_backward_static": [P, P, P, P, P, P, P],
             "pd_stiffness_factors": [I64, P, P, D, P, P, I32, D, P],
+            "pd_get_bond_integrity": [P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -179,7 +181,7 @@ def pd_create(coords, volumes, horizon: float, *, c: float, sc: float = 0.0,
               dt: float, damping: float, density: float, precision: int = PD_PREC_F64,
               graph_steps: int = 0, check_dt: bool = False, device: int = 0, stream=None,
               block_threads: int = 0, blocks_per_sm: int = 0, reorder: int = 0,
-              integrator: int = 0, ramp_steps: int = 0) -> int:
+              integrator: int = 0, ramp_steps: int = 0, kr: float = 0.0) -> int:
     """Create a model; returns an opaque handle (int).  See pd.h for the semantics."""
     x, kx = _ptr(coords, np.float64)
     n = (kx.numel() if hasattr(kx, "numel") else kx.size) // 3
@@ -198,7 +200,7 @@ def pd_create(coords, volumes, horizon: float, *, c: float, sc: float = 0.0,
     bd, kbd = _ptr(bc_disp, np.float64, 3 * n if bc_disp is not None else None)
     bf, kbf = _ptr(bc_force, np.float64, 3 * n if bc_force is not None else None)
     nf, knf = _ptr(no_fail, np.uint8, n if no_fail is not None else None)
-    mat = _Material(c=float(c), sc=float(sc), sc_mode=0)
+    mat = _Material(c=float(c), sc=float(sc), sc_mode=0, kr=float(kr))
     if sc_hash is not None:
         mat.sc_mode = 1
         mat.sc_seed, mat.sc_lo, mat.sc_hi = int(sc_hash[0]), float(sc_hash[1]), float(sc_hash[2])
@@ -261,6 +263,13 @@ def pd_get_bonds(h: int) -> np.ndarray:
     mu = np.empty(max(nb, 1), np.uint8)
     _check(lib().pd_get_bonds(h, mu.ctypes.data))
     return mu[:nb]
+
+
+def pd_get_bond_integrity(h: int) -> np.ndarray:
+    """Integrity mu in [0, 1] of every directed bond, canonical order."""
+    out = np.zeros(max(pd_get_info(h)["n_bonds"], 1))
+    _check(lib().pd_get_bond_integrity(h, out.ctypes.data))
+    return out[: pd_get_info(h)["n_bonds"]]
 
 
 def pd_set_bonds(h: int, mu) -> None:
@@ -446,7 +455,7 @@ class Model:
                    sc_hash=w.sc_hash, cuts=w.cuts_array(), bc_type=w.bc_type, bc_disp=w.bc_disp,
                    bc_force=w.bc_force, no_fail=w.no_fail, disp_rate=w.disp_rate, load=w.load,
                    dt=w.dt, damping=w.damping, density=w.density, precision=precision,
-                   ramp_steps=getattr(w, "ramp_steps", 0), **kw)
+                   ramp_steps=getattr(w, "ramp_steps", 0), kr=getattr(w, "kr", 0.0), **kw)
 
     def close(self):
         if self.h:

@@ -119,6 +119,8 @@ struct pd_handle {
     int64_t ramp_steps = 0;
     void* vpeek = nullptr;  // velocity-Verlet: full-step velocity for pd_get_state
     int64_t peek_step = -1; // step whose force pass filled vpeek (-1: none)
+    double kr = 0.0;        // >= 1: bilinear softening, s_0 = s_c / kr
+    void* integ = nullptr;  // softening: per-slot integrity (float / double)
     void* wsum_inv = nullptr;
     void* damage = nullptr;
     int* err = nullptr;
@@ -214,6 +216,11 @@ StepArgsF32 args_f32(pd_handle* h, int k)
     a.sc_f = (float)h->sc;
     a.sc_lo_f = (float)h->sc_lo;
     a.fast_lo = (float)((1.0 - 2.0 * a.guard) * h->sc_lo);
+    if (h->integ != nullptr) {  // softening: the band below the smallest s_0 is resolved too
+        a.integ = (float*)h->integ;
+        a.kr = h->kr;
+        a.fast_lo = (float)((1.0 - 2.0 * a.guard) * h->sc_lo / h->kr);
+    }
     a.sc = h->sc;
     a.sc_lo = h->sc_lo;
     a.sc_hi = h->sc_hi;
@@ -244,6 +251,8 @@ StepArgsF64 args_f64(pd_handle* h, int k)
     a.sw = h->sw;
     a.cbond = h->per_bond_c ? (const double*)h->cbond : nullptr;
     a.ilen = h->ilen;
+    a.integ = (double*)h->integ;
+    a.kr = h->kr;
     a.bcc = h->bcc;
     a.bct = h->bct;
     a.gid = h->gid;
@@ -270,10 +279,23 @@ StepArgsF64 args_f64(pd_handle* h, int k)
     return a;
 }
 
+// the FP32 step kernel build for this handle (bilinear softening or not)
+cudaError_t launch_f32(pd_handle* h, const StepArgsF32& a)
+{
+    if (h->integ != nullptr) return launch_step_f32_soft(a, h->sc_mode, h->grid, h->block, h->stream);
+    return launch_step_f32(a, h->sc_mode, h->grid, h->block, h->stream);
+}
+
+const void* f32_kernel(pd_handle* h)
+{
+    return h->integ != nullptr ? step_f32_kernel_soft(h->sc_mode, h->uniform_vol, h->per_bond_c)
+                               : step_f32_kernel(h->sc_mode, h->uniform_vol, h->per_bond_c);
+}
+
 cudaError_t launch_one(pd_handle* h, int k)
 {
     if (h->precision == 32)
-        return launch_step_f32(args_f32(h, k), h->sc_mode, h->grid, h->block, h->stream);
+        return launch_f32(h, args_f32(h, k));
     return launch_step_f64(args_f64(h, k), h->sc_mode, h->grid, h->block, h->stream);
 }
 
@@ -281,7 +303,7 @@ pd_status choose_grid(pd_handle* h, int blocks_per_sm)
 {
     int sms = 0;
     PD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "sm count");
-    const void* fn = h->precision == 32 ? step_f32_kernel(h->sc_mode, h->uniform_vol, h->per_bond_c)
+    const void* fn = h->precision == 32 ? f32_kernel(h)
                                         : step_f64_kernel(h->sc_mode);
     // no shared memory is used: give the unified L1/shared array to L1
     PD_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 0),
@@ -331,7 +353,7 @@ pd_status vv_force_pass(pd_handle* h)
         StepArgsF32 a = args_f32(h, 0);
         a.peek = 1;
         a.vout = (float*)h->vpeek;
-        e = launch_step_f32(a, h->sc_mode, h->grid, h->block, h->stream);
+        e = launch_f32(h, a);
     } else {
         StepArgsF64 a = args_f64(h, 0);
         a.peek = 1;
@@ -421,6 +443,8 @@ pd_status check_material(const pd_material* mat)
     } else {
         return fail(PD_ERR_ARG, "sc_mode must be 0 or 1");
     }
+    if (mat->kr != 0.0 && !(mat->kr >= 1.0 && std::isfinite(mat->kr)))
+        return fail(PD_ERR_ARG, "kr must be 0 (PMB) or a finite value >= 1 (bilinear softening)");
     return PD_OK;
 }
 
@@ -534,6 +558,14 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
         ALLOC(h->wsum_inv, double, np);
         ALLOC(h->damage, double, np);
         ALLOC(h->ilen, double, nbr.size());
+    }
+    if (h->kr >= 1.0) {  // bilinear softening: every bond starts intact, mu = 1
+        if (f32)
+            ALLOC(h->integ, float, nbr.size());
+        else
+            ALLOC(h->integ, double, nbr.size());
+        e = launch_fill(h->precision, h->integ, (int64_t)nbr.size(), 1.0, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "initial bond integrity");
     }
     ALLOC(h->nbr, int32_t, nbr.size());
     ALLOC(h->bits, uint32_t, bits.size());
@@ -650,6 +682,7 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
 void set_material(pd_handle* h, const pd_material* mat, const pd_bc* bc)
 {
     h->c = mat->c;
+    h->kr = mat->kr;
     h->sc_mode = mat->sc_mode;
     h->sc = mat->sc_mode == 0 ? mat->sc : 0.5 * (mat->sc_lo + mat->sc_hi);
     h->sc_seed = mat->sc_seed;
@@ -738,6 +771,8 @@ pd_status pd_batch_create(int32_t n_inst, const pd_instance* inst, const pd_conf
             I.bc.ramp_steps != inst[0].bc.ramp_steps)
             return fail(PD_ERR_ARG,
                         "instance %d: disp_rate, load and ramp_steps must equal instance 0's", b);
+        if (I.mat.kr != 0.0)
+            return fail(PD_ERR_ARG, "instance %d: bilinear softening is not available in batches", b);
         n += I.n;
         unit = std::max(unit, I.horizon);
         any_nofail = any_nofail || I.bc.no_fail != nullptr;
@@ -1017,6 +1052,44 @@ pd_status pd_get_bonds(pd_handle* h, uint8_t* mu)
     return PD_OK;
 }
 
+pd_status pd_get_bond_integrity(pd_handle* h, double* mu)
+{
+    if (!h || !mu) return fail(PD_ERR_ARG, "NULL argument");
+    PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    pd_status st = vv_force_pass(h);
+    if (st != PD_OK) return st;
+    std::vector<int64_t> pos;
+    if ((st = canonical_slots(h, pos)) != PD_OK) return st;
+    const int64_t W = 32LL * h->Q;
+    std::vector<uint32_t> bits((size_t)(h->n_slices * h->Q * 32));
+    PD_CUDA(cudaMemcpy(bits.data(), h->bits, bits.size() * 4, cudaMemcpyDeviceToHost),
+            "copy bond flags");
+    const size_t ns = (size_t)(h->n_slices * 32 * W);
+    std::vector<double> m64;
+    std::vector<float> m32;
+    if (h->integ) {
+        if (h->precision == 32) {
+            m32.resize(ns);
+            PD_CUDA(cudaMemcpy(m32.data(), h->integ, ns * 4, cudaMemcpyDeviceToHost), "copy integrity");
+        } else {
+            m64.resize(ns);
+            PD_CUDA(cudaMemcpy(m64.data(), h->integ, ns * 8, cudaMemcpyDeviceToHost), "copy integrity");
+        }
+    }
+    for (int64_t p = 0; p < h->n; ++p) {
+        const int64_t g = p / 32, l = p % 32;
+        for (int64_t m = 0; m < h->cnt[p]; ++m) {
+            const int64_t slot = (g * W + m) * 32 + l;
+            const bool intact = (bits[(g * h->Q + (m >> 5)) * 32 + l] >> (m & 31)) & 1u;
+            double v = intact ? 1.0 : 0.0;
+            if (intact && h->integ)
+                v = h->precision == 32 ? (double)m32[(size_t)slot] : m64[(size_t)slot];
+            mu[pos[(size_t)slot]] = v;
+        }
+    }
+    return PD_OK;
+}
+
 pd_status pd_set_bonds(pd_handle* h, const uint8_t* mu)
 {
     if (!h || !mu) return fail(PD_ERR_ARG, "NULL argument");
@@ -1035,6 +1108,24 @@ pd_status pd_set_bonds(pd_handle* h, const uint8_t* mu)
     }
     PD_CUDA(cudaMemcpy(h->bits, bits.data(), bits.size() * 4, cudaMemcpyHostToDevice),
             "upload bond flags");
+    if (h->integ) {  // a fresh bond state: intact bonds unsoftened, broken ones 0
+        const size_t ns = (size_t)(h->n_slices * 32 * W);
+        std::vector<double> m64;
+        std::vector<float> m32;
+        if (h->precision == 32) m32.assign(ns, 0.0f); else m64.assign(ns, 0.0);
+        for (int64_t p = 0; p < h->n; ++p) {
+            const int64_t g = p / 32, l = p % 32;
+            for (int64_t m = 0; m < h->cnt[p]; ++m)
+                if ((bits[(g * h->Q + (m >> 5)) * 32 + l] >> (m & 31)) & 1u) {
+                    const size_t slot = (size_t)((g * W + m) * 32 + l);
+                    if (h->precision == 32) m32[slot] = 1.0f; else m64[slot] = 1.0;
+                }
+        }
+        if (h->precision == 32)
+            PD_CUDA(cudaMemcpy(h->integ, m32.data(), ns * 4, cudaMemcpyHostToDevice), "upload integrity");
+        else
+            PD_CUDA(cudaMemcpy(h->integ, m64.data(), ns * 8, cudaMemcpyHostToDevice), "upload integrity");
+    }
     h->damage_fresh = false;
     h->peek_step = -1;
     return PD_OK;
@@ -1053,7 +1144,7 @@ pd_status pd_damage(pd_handle* h, double* phi)
                 "damage");
     else
         PD_CUDA(launch_damage(h->precision, h->wrec(), h->nbr, h->bits, h->sw, h->wsum_inv,
-                              h->gid, h->n, h->Q, dst, h->stream),
+                              h->gid, h->n, h->Q, h->integ, dst, h->stream),
                 "damage");
     if (!dev)
         PD_CUDA(cudaMemcpyAsync(phi, h->staging, 8 * h->n, cudaMemcpyDeviceToHost, h->stream),
@@ -1064,9 +1155,9 @@ pd_status pd_damage(pd_handle* h, double* phi)
 pd_status pd_adjoint_forward(pd_handle* h, int64_t n_steps, int64_t checkpoint_every)
 {
     if (!h) return fail(PD_ERR_ARG, "NULL handle");
-    if (h->precision != 64 || h->batch || h->integrator != PD_INTEGRATOR_EC)
+    if (h->precision != 64 || h->batch || h->integrator != PD_INTEGRATOR_EC || h->integ)
         return fail(PD_ERR_STATE,
-                    "the adjoint is available on FP64 single-model Euler-Cromer handles");
+                    "the adjoint is available on FP64 single-model Euler-Cromer PMB handles");
     if (n_steps < 1 || checkpoint_every < 0)
         return fail(PD_ERR_ARG, "need n_steps >= 1 and checkpoint_every >= 0");
     PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
@@ -1311,6 +1402,8 @@ pd_status pd_autotune(pd_handle* h, int32_t trial_steps, int32_t* block_threads,
         bufs.push_back({h->damage, (size_t)(8 * np), {}});
     }
     bufs.push_back({h->bits, (size_t)(4 * h->n_slices * h->Q * 32), {}});
+    if (h->integ)
+        bufs.push_back({h->integ, (size_t)((h->precision == 32 ? 4 : 8) * h->n_slices * h->Q * 32 * 32), {}});
     bufs.push_back({h->step_ctr, 2 * sizeof(int64_t), {}});
     bufs.push_back({h->err, sizeof(int), {}});
     for (Buf& b : bufs) {
@@ -1355,9 +1448,7 @@ pd_status pd_autotune(pd_handle* h, int32_t trial_steps, int32_t* block_threads,
                 best_bps = bps;
             }
             int occ = 0;
-            const void* fn = h->precision == 32
-                                 ? step_f32_kernel(h->sc_mode, h->uniform_vol, h->per_bond_c)
-                                 : step_f64_kernel(h->sc_mode);
+            const void* fn = h->precision == 32 ? f32_kernel(h) : step_f64_kernel(h->sc_mode);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block, 0);
             if (bps >= occ) break;  // larger requests are capped to the same grid
         }

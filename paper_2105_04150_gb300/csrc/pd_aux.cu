@@ -118,7 +118,7 @@ __device__ __forceinline__ double node_w<double>(const void* wrec, int64_t p)
 template <typename T>
 __device__ __forceinline__ T masked_wsum(const void* wrec, const int32_t* __restrict__ nbr,
                                          const uint32_t* __restrict__ bits, int64_t g, int lane,
-                                         int Wg, int Q)
+                                         int Wg, int Q, const T* __restrict__ integ = nullptr)
 {
     const int64_t W = 32LL * Q;
     T acc = 0;
@@ -126,7 +126,11 @@ __device__ __forceinline__ T masked_wsum(const void* wrec, const int32_t* __rest
         const uint32_t word = bits[(g * Q + q) * 32 + lane];
         const int mend = min(32, Wg - q * 32);
         for (int b = 0; b < mend; ++b)
-            if ((word >> b) & 1u) acc += node_w<T>(wrec, nbr[(g * W + q * 32 + b) * 32 + lane]);
+            if ((word >> b) & 1u) {
+                const int64_t slot = (g * W + q * 32 + b) * 32 + lane;
+                const T w = node_w<T>(wrec, nbr[slot]);
+                acc += integ != nullptr ? w * integ[slot] : w;
+            }
     }
     return acc;
 }
@@ -135,13 +139,13 @@ template <typename T>
 __global__ void k_damage(const void* __restrict__ wrec, const int32_t* __restrict__ nbr,
                          const uint32_t* __restrict__ bits, const int32_t* __restrict__ sw,
                          const T* __restrict__ wsum_inv, const int32_t* __restrict__ gid,
-                         int64_t n, int Q, double* __restrict__ phi)
+                         int64_t n, int Q, const T* __restrict__ integ, double* __restrict__ phi)
 {
     GRID_STRIDE(p, ((n + 31) >> 5) << 5)
     {
         const int64_t g = p >> 5;
         const int lane = (int)(p & 31);
-        const T acc = masked_wsum<T>(wrec, nbr, bits, g, lane, sw[g], Q);
+        const T acc = masked_wsum<T>(wrec, nbr, bits, g, lane, sw[g], Q, integ);
         // a node without family has no damage (the integral ratio of Eq. 8 is 0/0)
         if (p < n)
             phi[gid[p]] = wsum_inv[p] > 0 ? (double)fmax((T)0, (T)1 - acc * wsum_inv[p]) : 0.0;
@@ -258,15 +262,16 @@ cudaError_t launch_set_state_f64(const double* u_in, const double* v_in, const i
 
 cudaError_t launch_damage(int precision, const void* wrec, const int32_t* nbr,
                           const uint32_t* bits, const int32_t* sw, const void* wsum_inv,
-                          const int32_t* gid, int64_t n, int Q, double* phi_out, cudaStream_t s)
+                          const int32_t* gid, int64_t n, int Q, const void* integ,
+                          double* phi_out, cudaStream_t s)
 {
     const int g = grid_for(n, 256);
     if (precision == 32)
         k_damage<float><<<g, 256, 0, s>>>(wrec, nbr, bits, sw, (const float*)wsum_inv, gid, n, Q,
-                                          phi_out);
+                                          (const float*)integ, phi_out);
     else
         k_damage<double><<<g, 256, 0, s>>>(wrec, nbr, bits, sw, (const double*)wsum_inv, gid, n,
-                                           Q, phi_out);
+                                           Q, (const double*)integ, phi_out);
     return cudaGetLastError();
 }
 
@@ -294,6 +299,22 @@ cudaError_t launch_set_weights(int precision, void* wrec0, void* wrec1, const do
         k_wsum<double><<<grid_for(n, 256), 256, 0, s>>>(wrec0, nbr, init_bits, sw, n, Q,
                                                         (double*)wsum_inv);
     }
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_fill(T* __restrict__ dst, int64_t n, T v)
+{
+    GRID_STRIDE(e, n) dst[e] = v;
+}
+
+cudaError_t launch_fill(int precision, void* dst, int64_t n, double v, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    if (precision == 32)
+        k_fill<float><<<grid_for(n, 256), 256, 0, s>>>((float*)dst, n, (float)v);
+    else
+        k_fill<double><<<grid_for(n, 256), 256, 0, s>>>((double*)dst, n, v);
     return cudaGetLastError();
 }
 

@@ -93,6 +93,8 @@ struct StepArgsF32 {
     int32_t vv;                // 1: damped velocity-Verlet, 0: damped Euler-Cromer
     int32_t peek;              // 1: forces and full-step velocity into vout only
     float* vout;               // peek: 3 floats per node (library order)
+    float* integ;              // bilinear softening: per-slot integrity mu, or nullptr
+    double kr;                 // s_0 = s_c / kr
 };
 
 struct StepArgsF64 {
@@ -127,6 +129,8 @@ struct StepArgsF64 {
     int32_t vv;                // 1: damped velocity-Verlet, 0: damped Euler-Cromer
     int32_t peek;              // 1: forces and full-step velocity into vout only
     double* vout;              // peek: 3 doubles per node (library order)
+    double* integ;             // bilinear softening: per-slot integrity mu, or nullptr
+    double kr;                 // s_0 = s_c / kr
 };
 
 // Arguments of one reverse step of the FP64 adjoint (pd_adjoint.cu); node arrays
@@ -182,6 +186,10 @@ cudaError_t launch_step_f32(const StepArgsF32& a, int sc_mode, int grid, int blo
 cudaError_t launch_step_f64(const StepArgsF64& a, int sc_mode, int grid, int block,
                             cudaStream_t s);
 const void* step_f32_kernel(int sc_mode, bool uniform_w, bool per_bond_c);
+// bilinear-softening build of the FP32 step kernel (pd_step_f32_soft.cu)
+cudaError_t launch_step_f32_soft(const StepArgsF32& a, int sc_mode, int grid, int block,
+                                 cudaStream_t s);
+const void* step_f32_kernel_soft(int sc_mode, bool uniform_w, bool per_bond_c);
 const void* step_f64_kernel(int sc_mode);
 
 // ---- helper kernels (pd_aux.cu) ---------------------------------------------
@@ -198,9 +206,13 @@ cudaError_t launch_get_state_f64(const double* rec64, const double* v64, const i
 cudaError_t launch_set_state_f64(const double* u_in, const double* v_in, const int32_t* gid,
                                  int64_t n, double* rec64, double* v64, cudaStream_t s);
 // damage from the bond flags (Eq. 8), written to caller order
+// (integ: per-slot integrity weighting each intact bond, or nullptr)
 cudaError_t launch_damage(int precision, const void* wrec, const int32_t* nbr,
                           const uint32_t* bits, const int32_t* sw, const void* wsum_inv,
-                          const int32_t* gid, int64_t n, int Q, double* phi_out, cudaStream_t s);
+                          const int32_t* gid, int64_t n, int Q, const void* integ,
+                          double* phi_out, cudaStream_t s);
+// fill n values of `precision` (32 or 64) with v
+cudaError_t launch_fill(int precision, void* dst, int64_t n, double v, cudaStream_t s);
 // damage written by the last step -> caller order
 cudaError_t launch_gather_damage(int precision, const void* dmg, const int32_t* gid, int64_t n,
                                  double* phi_out, cudaStream_t s);

@@ -57,6 +57,15 @@ namespace {
 #endif
 constexpr int kUnroll = PD_F32_UNROLL;  // family slots in flight per lane
 
+// Bilinear-softening build (compiled by pd_step_f32_soft.cu): every slot also
+// carries the bond's integrity mu; the fast path scales the force by it, and
+// bonds whose stretch reaches the band below s_0 = s_c / kr are resolved like
+// the near-s_c ones, where mu is lowered.
+#ifndef PD_F32_SOFT
+#define PD_F32_SOFT 0
+#endif
+constexpr bool kSoft = PD_F32_SOFT != 0;
+
 // SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output m of the stream seeded
 // with `seed`.  Used as a counter-based draw of the per-bond critical stretch.
 __device__ __forceinline__ uint64_t splitmix_out(uint64_t seed, uint64_t m)
@@ -301,12 +310,31 @@ __device__ __noinline__ float4 resolve_bond(const StepArgsF32& a, int cur, int64
     }
     if (brk && a.has_nofail) brk = ((a.bct[a.bcc[i]].mask | a.bct[a.bcc[j]].mask) & 8u) == 0u;
     *broken = brk;
-    if (brk) return make_float4(0.f, 0.f, 0.f, 0.f);
+    if (brk) {
+        if (kSoft) a.integ[slot] = 0.0f;
+        return make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     const float wv = node_w<UW>(a, j, UW ? lane_wconst(a, i) : 0.0f);
     float w = wv;
     if (a.cbond != nullptr) w *= a.cbond[slot];
+    float mu = 1.0f;
+    if (kSoft) {
+        // integrity only decreases, as the stretch passes s_0 (0 for a no-fail
+        // bond past s_c); the fast path applies the stored value
+        mu = a.integ[slot];
+        const double s = (double)(b.num / b.den), s0 = sc / a.kr;
+        if (s > s0) {
+            const float ms = s >= sc ? 0.0f : (float)(s0 * (sc - s) / (s * (sc - s0)));
+            if (ms < mu) {
+                mu = ms;
+                a.integ[slot] = ms;
+            }
+        }
+        w *= mu;
+    }
     const float coef = bond_coef(b, w);
-    return make_float4(coef * b.yx, coef * b.yy, coef * b.yz, wv);
+    // .w: the damage weight (w V; for uniform weights the integrity alone)
+    return make_float4(coef * b.yx, coef * b.yy, coef * b.yz, kSoft ? (UW ? mu : wv * mu) : wv);
 }
 
 template <int SCM, bool UW>
@@ -384,13 +412,21 @@ __global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS)
                 float wj = node_w<UW>(a, jj[u], wc);
                 const float wv = wj;
                 if (cb != nullptr) wj *= ld_f32(cb + (g * W + m0 + u) * 32 + lane);
+                float mj = 1.0f;
+                if (kSoft) {
+                    mj = ld_f32(a.integ + (g * W + m0 + u) * 32 + lane);
+                    wj *= mj;
+                }
                 float coef = bond_coef(bd, wj);
                 coef = cand ? 0.0f : coef;
                 coef = alive ? coef : 0.0f;
                 fx = fmaf(coef, bd.yx, fx);
                 fy = fmaf(coef, bd.yy, fy);
                 fz = fmaf(coef, bd.yz, fz);
-                if (!UW) ws += (alive && !cand) ? wv : 0.0f;
+                if (kSoft)
+                    ws += (alive && !cand) ? (UW ? mj : wv * mj) : 0.0f;
+                else if (!UW)
+                    ws += (alive && !cand) ? wv : 0.0f;
             }
             pend |= (pc & wb) << b0;
             if (b0 + kUnroll == 32 || c + 1 == nch) {  // end of bond-flag word q
@@ -407,14 +443,14 @@ __global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS)
                         fx += f.x;
                         fy += f.y;
                         fz += f.z;
-                        if (!UW) ws += f.w;
+                        if (kSoft || !UW) ws += f.w;
                     }
                 }
                 if (nword != word) bw[q * 32] = nword;
                 alive_count += __popc(nword);
             }
         }
-        if (UW) ws = wc * (float)alive_count;
+        if (UW) ws = kSoft ? wc * ws : wc * (float)alive_count;
 
         // ---- integration of the lane's node (damped Euler-Cromer, Eq. 11, or
         // damped velocity-Verlet)
@@ -484,15 +520,23 @@ cudaError_t launch_v(const StepArgsF32& a, int grid, int block, cudaStream_t s)
 
 }  // namespace
 
+#if PD_F32_SOFT
+#define PD_F32_KERNEL_OF step_f32_kernel_soft
+#define PD_F32_LAUNCH launch_step_f32_soft
+#else
+#define PD_F32_KERNEL_OF step_f32_kernel
+#define PD_F32_LAUNCH launch_step_f32
+#endif
+
 // per_bond_c selects no separate variant (it is a uniform run-time branch)
-const void* step_f32_kernel(int sc_mode, bool uniform_w, bool /*per_bond_c*/)
+const void* PD_F32_KERNEL_OF(int sc_mode, bool uniform_w, bool /*per_bond_c*/)
 {
     if (sc_mode == 0)
         return uniform_w ? (const void*)k_step_f32<0, true> : (const void*)k_step_f32<0, false>;
     return uniform_w ? (const void*)k_step_f32<1, true> : (const void*)k_step_f32<1, false>;
 }
 
-cudaError_t launch_step_f32(const StepArgsF32& a, int sc_mode, int grid, int block, cudaStream_t s)
+cudaError_t PD_F32_LAUNCH(const StepArgsF32& a, int sc_mode, int grid, int block, cudaStream_t s)
 {
     if (sc_mode == 0)
         return a.uniform_w ? launch_v<0, true>(a, grid, block, s) : launch_v<0, false>(a, grid, block, s);

@@ -117,14 +117,29 @@ __global__ void __launch_bounds__(256) k_step_f64(const StepArgsF64 a)
                     if (brk && a.has_nofail) brk = !pair_no_fail(a.bcc, a.bct, i, jj[u]);
                     if (brk) {
                         nword &= ~(1u << (b0 + u));
+                        if (a.integ != nullptr) a.integ[slot] = 0.0;
                     } else {
-                        double wj = ra[u][1].y;
+                        // bilinear softening: the integrity only decreases, as the
+                        // stretch passes s_0 = s_c / kr (a no-fail bond past s_c keeps 0)
+                        double mu = 1.0;
+                        if (a.integ != nullptr) {
+                            mu = a.integ[slot];
+                            const double s0 = sc / a.kr;
+                            if (s > s0) {
+                                const double ms = s >= sc ? 0.0 : s0 * (sc - s) / (s * (sc - s0));
+                                if (ms < mu) {
+                                    mu = ms;
+                                    a.integ[slot] = ms;
+                                }
+                            }
+                        }
+                        double wj = ra[u][1].y * mu;
                         if (cb != nullptr) wj *= __ldg(cb + slot);
                         const double f = wj * s * ir;
                         fx += f * yx;
                         fy += f * yy;
                         fz += f * yz;
-                        ws += ra[u][1].y;
+                        ws += ra[u][1].y * mu;
                     }
                 }
             }

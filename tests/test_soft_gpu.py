@@ -1,0 +1,130 @@
+"""Bilinear softening on the GPU, through the C ABI, against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2105_04150_gb300 as pdgb
+import workloads
+
+pytestmark = pytest.mark.gpu
+F64, F32 = pdgb.PD_PREC_F64, pdgb.PD_PREC_F32
+BAND = 1e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pdgb.build()
+    oracle.build()
+
+
+def _integrity(om, mu, w):
+    """mu(kappa) of every family entry of an oracle model (0 where broken)."""
+    rows = np.repeat(np.arange(w.n), np.diff(om.off))
+    if w.sc_hash is not None:
+        sc = np.array([oracle.sc_bond(*w.sc_hash, int(i), int(j)) for i, j in zip(rows, om.idx)])
+    else:
+        sc = np.full(len(om.idx), w.sc)
+    s0, k = sc / w.kr, om.kappa[: len(om.idx)]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        m = np.where(k <= s0, 1.0, np.where(k >= sc, 0.0, s0 * (sc - k) / (k * (sc - s0))))
+    return np.where(mu == 1, m, 0.0)
+
+
+def _run(w, precision, steps):
+    off, idx = oracle.cut_family(w.coords, w.horizon, w.cuts_array())
+    om = oracle.Model.from_workload(w, off, idx)
+    u, v, mu = np.zeros((w.n, 3)), np.zeros((w.n, 3)), om.fresh_bonds()
+    margin = np.full(len(mu), np.inf)
+    om.run(0, steps, u, v, mu, margin)
+    m = pdgb.Model.from_workload(w, precision=precision, graph_steps=20)
+    m.step(steps)
+    ug, vg = m.state()
+    out = dict(u=ug, v=vg, b=m.bonds(), integ=pdgb.pd_get_bond_integrity(m.h), phi=m.damage())
+    m.close()
+    return out, dict(u=u, v=v, mu=mu, margin=margin, integ=_integrity(om, mu, w),
+                     phi=om.damage(mu))
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def _bar(kr):
+    w = workloads.tensile_bar(steps=1000)
+    w.kr = kr
+    return w
+
+
+def test_softening_fp64_tensile_bar_matches_oracle():
+    w = _bar(3.0)
+    g, o = _run(w, F64, w.steps)
+    assert (o["mu"] == 0).sum() > 0 and ((o["integ"] > 0) & (o["integ"] < 1)).sum() > 100
+    assert rel(g["u"], o["u"]) <= 1e-10 and rel(g["v"], o["v"]) <= 1e-9
+    diff = g["b"] != o["mu"]
+    assert np.all(o["margin"][diff] < BAND)
+    ok = ~diff
+    assert np.abs(g["integ"][ok] - o["integ"][ok]).max() <= 1e-9
+    assert np.abs(g["phi"] - o["phi"]).max() <= 1e-9 + 2.0 * diff.sum() / len(diff)
+
+
+def test_softening_fp32_tensile_bar_matches_oracle():
+    # u is compared in the softening regime before bonds break (step 500: about
+    # 50k bonds have passed s_0 = s_c/3, the first breaks come near step 550); past
+    # the first breaks FP32 rounding moves break steps (the same as for the PMB
+    # law), so at the end only the broken set and the damage are compared
+    w = _bar(3.0)
+    g, o = _run(w, F32, 500)
+    assert ((o["integ"] > 0) & (o["integ"] < 1)).sum() > 100 and (o["mu"] == 0).sum() == 0
+    assert rel(g["u"], o["u"]) <= 1e-4
+    assert np.abs(g["integ"] - o["integ"]).max() <= 1e-3
+    g, o = _run(w, F32, w.steps)
+    diff = g["b"] != o["mu"]
+    assert (o["mu"] == 0).sum() > 0 and diff.sum() <= 1e-3 * len(diff)
+    assert np.abs(g["phi"] - o["phi"]).max() <= 2e-2
+
+
+def test_softening_fp64_notched_beam_per_bond_sc():
+    w = workloads.notched_beam(48, 10, 12, length=48 / 600, rate=1e-7, steps=300)
+    w.kr = 2.0
+    g, o = _run(w, F64, w.steps)
+    assert rel(g["u"], o["u"]) <= 1e-10
+    diff = g["b"] != o["mu"]
+    assert np.all(o["margin"][diff] < BAND)
+    assert np.abs(g["integ"][~diff] - o["integ"][~diff]).max() <= 1e-9
+
+
+@pytest.mark.parametrize("precision", [F64, F32])
+def test_kr_one_equals_pmb_bitwise(precision):
+    w = _bar(0.0)
+    a = pdgb.Model.from_workload(w, precision=precision)
+    w.kr = 1.0
+    b = pdgb.Model.from_workload(w, precision=precision)
+    for m in (a, b):
+        m.step(w.steps)
+    ua, va = a.state()
+    ub, vb = b.state()
+    assert np.array_equal(ua, ub) and np.array_equal(va, vb)
+    assert np.array_equal(a.bonds(), b.bonds())
+    assert np.array_equal(a.damage(), b.damage())
+    assert np.array_equal(pdgb.pd_get_bond_integrity(a.h), a.bonds().astype(float))
+    a.close()
+    b.close()
+
+
+def test_fused_and_recomputed_damage_agree_and_set_bonds_resets():
+    w = _bar(3.0)
+    m = pdgb.Model.from_workload(w, precision=F64)
+    m.step(900)
+    phi_fused = m.damage()
+    u, v = m.state()
+    m.set_state(u, v)            # forces the recomputation from flags and integrity
+    phi_re = m.damage()
+    assert np.abs(phi_fused - phi_re).max() <= 1e-12
+    bonds = m.bonds()
+    m.set_bonds(bonds)
+    integ = pdgb.pd_get_bond_integrity(m.h)
+    assert np.array_equal(integ, bonds.astype(float))
+    m.close()
