@@ -66,6 +66,8 @@ def parse():
                    help="damped Euler-Cromer (default) or damped velocity-Verlet")
     p.add_argument("--ramp-steps", type=int, default=0,
                    help="smooth start of the displacement loading over this many steps")
+    p.add_argument("--kr", type=float, default=0.0,
+                   help="bilinear softening with s_0 = s_c / kr (0: the PMB law)")
     p.add_argument("--fd-directions", type=int, default=32)
     p.add_argument("--checkpoint-every", type=int, default=45)
     p.add_argument("--precision", type=int, default=32, choices=[32, 64])
@@ -87,6 +89,8 @@ def describe(w, n_bonds, precision, integrator="ec"):
     return {
         "integrator": {"ec": "damped Euler-Cromer", "vv": "damped velocity-Verlet"}[integrator],
         "ramp_steps": int(getattr(w, "ramp_steps", 0)),
+        "bond_law": ("PMB" if not getattr(w, "kr", 0.0)
+                     else f"bilinear softening, s_0 = s_c / {w.kr:g}"),
         "workload": f"{w.name}: {w.n:,} nodes, {n_bonds:,} directed bonds, "
                     f"delta = {w.horizon / w.dx:.4g} dx, "
                     + ("per-bond s_c ~ U[9e-5, 1.1e-4)" if w.sc_hash else f"s_c = {w.sc:g}"),
@@ -290,6 +294,7 @@ def run_ours(args):
     dev_sync = torch.cuda.synchronize
     w = make_workload(args.workload)
     w.ramp_steps = args.ramp_steps
+    w.kr = args.kr
     c = pdgb.pd_micromodulus(w.bulk_modulus, w.horizon)
     stream = torch.cuda.Stream(device=local)
     G = max(0, min(args.graph_steps, args.steps))
