@@ -358,7 +358,9 @@ def run_ours(args):
         return
     ms_step = ms_max / args.steps
     value = whole_job(n_bonds * args.steps, ms_max, world)
-    alg_bytes = n_bonds * BYTES_PER_BOND + w.n * BYTES_PER_NODE[args.precision]
+    # softening adds the per-bond integrity read every step (FP32 4 B, FP64 8 B)
+    per_bond = BYTES_PER_BOND + ((4.0 if args.precision == 32 else 8.0) if args.kr else 0.0)
+    alg_bytes = n_bonds * per_bond + w.n * BYTES_PER_NODE[args.precision]
     peak, peak_kind = hbm_peak()
     achieved = alg_bytes / (ms_step * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
