@@ -364,7 +364,8 @@ def run_ours(args):
     peak, peak_kind = hbm_peak()
     achieved = alg_bytes / (ms_step * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": profiled_traffic(args.precision, args.workload),
+                "frac": achieved / peak,
+                "traffic": None if args.kr else profiled_traffic(args.precision, args.workload),
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s", "algorithmic_bytes_per_launch": alg_bytes,
                 "kernel": f"k_step_f{args.precision}"}
