@@ -283,6 +283,8 @@ StepArgsF64 args_f64(pd_handle* h, int k)
 cudaError_t launch_f32(pd_handle* h, const StepArgsF32& a)
 {
     if (h->integ != nullptr) return launch_step_f32_soft(a, h->sc_mode, h->grid, h->block, h->stream);
+    if (a.vv || a.ramp_steps > 0 || a.peek)
+        return launch_step_f32_ext(a, h->sc_mode, h->grid, h->block, h->stream);
     return launch_step_f32(a, h->sc_mode, h->grid, h->block, h->stream);
 }
 

@@ -186,6 +186,10 @@ cudaError_t launch_step_f32(const StepArgsF32& a, int sc_mode, int grid, int blo
 cudaError_t launch_step_f64(const StepArgsF64& a, int sc_mode, int grid, int block,
                             cudaStream_t s);
 const void* step_f32_kernel(int sc_mode, bool uniform_w, bool per_bond_c);
+// extended-epilogue build (velocity-Verlet, smooth loading start, force pass)
+cudaError_t launch_step_f32_ext(const StepArgsF32& a, int sc_mode, int grid, int block,
+                                cudaStream_t s);
+const void* step_f32_kernel_ext(int sc_mode, bool uniform_w, bool per_bond_c);
 // bilinear-softening build of the FP32 step kernel (pd_step_f32_soft.cu)
 cudaError_t launch_step_f32_soft(const StepArgsF32& a, int sc_mode, int grid, int block,
                                  cudaStream_t s);

@@ -66,6 +66,16 @@ constexpr int kUnroll = PD_F32_UNROLL;  // family slots in flight per lane
 #endif
 constexpr bool kSoft = PD_F32_SOFT != 0;
 
+// Extended-epilogue build (pd_step_f32_ext.cu, and the softening build): the
+// per-node update also handles velocity-Verlet, the smooth loading start and
+// the read-only force pass.  The plain build keeps the Euler-Cromer epilogue
+// with the linear loading ramp: the extra branches alone cost the slot loop
+// about 9 % in code generation.
+#ifndef PD_F32_EXT
+#define PD_F32_EXT PD_F32_SOFT
+#endif
+constexpr bool kExt = PD_F32_EXT != 0;
+
 // SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output m of the stream seeded
 // with `seed`.  Used as a counter-based draw of the per-bond critical stretch.
 __device__ __forceinline__ uint64_t splitmix_out(uint64_t seed, uint64_t m)
@@ -345,7 +355,6 @@ __global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS)
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t step = a.step_ctr[0] + a.k;
-    const bool first = a.vv && step == a.step_ctr[1];  // velocity-Verlet: a^n formed afresh
     const int cur = (int)(step & 1);
     const int Q = a.Q;
     const int64_t W = 32LL * Q;
@@ -466,6 +475,8 @@ __global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS)
                 for (int c = 0; c < 3; ++c) F[c] += (float)(a.load * bc->force[c]);
             }
             const float dtf = (float)a.dt, etaf = (float)a.eta, rhof = (float)a.rho;
+            // velocity-Verlet: a^n is formed afresh at the step the state was set
+            const bool first = kExt && a.vv && step == a.step_ctr[1];
             const float dtd = (float)(a.dt * a.inv_delta);
             const float4 lo = a.lo32[i];
             float H[3] = {ni.hx, ni.hy, ni.hz};
@@ -476,30 +487,43 @@ __global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS)
                 // stored velocity: v^n (Euler-Cromer) or, for velocity-Verlet, the
                 // half-step velocity v^{n-1} + dt/2 a^{n-1} (v^n right after a set state)
                 const float vi = a.v[3 * i + c];
-                float vn, vfull;
-                if (a.vv) {
-                    const float acc = (F[c] - etaf * vi) / rhof;
-                    vfull = first ? vi : vi + 0.5f * dtf * acc;
-                    vn = vfull + 0.5f * dtf * acc;
-                } else {
-                    vn = vi + dtf * (F[c] - etaf * vi) / rhof;
-                    vfull = vn;
-                }
-                ff_add(H[c], L[c], vn * dtd);
-                if (mask & (1u << c)) {
-                    const double s_now = bc_scale(a.disp_rate, a.ramp_steps, step);
-                    const double s_next = bc_scale(a.disp_rate, a.ramp_steps, step + 1);
-                    ff_set(bc->disp[c] * s_next * a.inv_delta, H[c], L[c]);
-                    vn = (float)(bc->disp[c] * (s_next - s_now) / a.dt);
-                    vfull = vi;
-                }
-                finite = finite && isfinite(H[c]);
-                if (a.peek)
-                    a.vout[3 * i + c] = vfull;
-                else
+                if constexpr (!kExt) {
+                    float vn = vi + dtf * (F[c] - etaf * vi) / rhof;
+                    ff_add(H[c], L[c], vn * dtd);
+                    if (mask & (1u << c)) {
+                        const double s_now = a.disp_rate * (double)step;
+                        const double s_next = a.disp_rate * (double)(step + 1);
+                        ff_set(bc->disp[c] * s_next * a.inv_delta, H[c], L[c]);
+                        vn = (float)(bc->disp[c] * (s_next - s_now) / a.dt);
+                    }
+                    finite = finite && isfinite(H[c]);
                     a.v[3 * i + c] = vn;
+                } else {
+                    float vn, vfull;
+                    if (a.vv) {
+                        const float acc = (F[c] - etaf * vi) / rhof;
+                        vfull = first ? vi : vi + 0.5f * dtf * acc;
+                        vn = vfull + 0.5f * dtf * acc;
+                    } else {
+                        vn = vi + dtf * (F[c] - etaf * vi) / rhof;
+                        vfull = vn;
+                    }
+                    ff_add(H[c], L[c], vn * dtd);
+                    if (mask & (1u << c)) {
+                        const double s_now = bc_scale(a.disp_rate, a.ramp_steps, step);
+                        const double s_next = bc_scale(a.disp_rate, a.ramp_steps, step + 1);
+                        ff_set(bc->disp[c] * s_next * a.inv_delta, H[c], L[c]);
+                        vn = (float)(bc->disp[c] * (s_next - s_now) / a.dt);
+                        vfull = vi;
+                    }
+                    finite = finite && isfinite(H[c]);
+                    if (a.peek)
+                        a.vout[3 * i + c] = vfull;
+                    else
+                        a.v[3 * i + c] = vn;
+                }
             }
-            if (a.peek) continue;
+            if (kExt && a.peek) continue;
             st_rec(Rout + 2 * i, make_float4(ni.x, ni.y, ni.z, H[0]),
                    make_float4(H[1], H[2], bf_pack(L[1], L[0]), bf_pack(0.0f, L[2])));
             a.lo32[i] = make_float4(L[0], L[1], L[2], 0.0f);
@@ -523,6 +547,9 @@ cudaError_t launch_v(const StepArgsF32& a, int grid, int block, cudaStream_t s)
 #if PD_F32_SOFT
 #define PD_F32_KERNEL_OF step_f32_kernel_soft
 #define PD_F32_LAUNCH launch_step_f32_soft
+#elif PD_F32_EXT
+#define PD_F32_KERNEL_OF step_f32_kernel_ext
+#define PD_F32_LAUNCH launch_step_f32_ext
 #else
 #define PD_F32_KERNEL_OF step_f32_kernel
 #define PD_F32_LAUNCH launch_step_f32
