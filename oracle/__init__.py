@@ -35,6 +35,11 @@ What pins each function (tests in ``tests/test_oracle_pins.py``):
   kr = 1; a two-node bond follows the closed-form bilinear envelope under
   loading, unloads along the secant to the origin and reloads onto the
   envelope; the remembered stretch never decreases (``tests/test_oracle_soft.py``).
+* ordinary state-based linear solid (``state_based=(K, G)``): uniform dilation
+  gives theta = 3 eps and W = (9/2) K eps^2 at every node; simple shear gives
+  G gamma^2 / 2 times the stencil quadrature ratio (-> 1 for large horizons);
+  force = minus the energy gradient; rigid motions are force free; momentum is
+  conserved (``tests/test_oracle_osb.py``).
 * ``adjoint``: central differences of the pinned forward run
   (``tests/test_oracle_adjoint.py``).
 """
@@ -85,6 +90,9 @@ class _Model(ctypes.Structure):
         ("dt", ctypes.c_double), ("damping", ctypes.c_double), ("density", ctypes.c_double),
         ("ramp_steps", ctypes.c_int64),
         ("kr", ctypes.c_double), ("kappa", ctypes.c_void_p),
+        ("model", ctypes.c_int32), ("pad1", ctypes.c_int32),
+        ("K", ctypes.c_double), ("G", ctypes.c_double),
+        ("wvol", ctypes.c_void_p), ("theta", ctypes.c_void_p),
     ]
 
 
@@ -119,6 +127,8 @@ def lib():
         L.or_damage.argtypes = [ctypes.POINTER(_Model), P, P]
         L.or_energy_density.restype = None
         L.or_energy_density.argtypes = [ctypes.POINTER(_Model), P, P, P]
+        L.or_osb_weighted_volume.restype = None
+        L.or_osb_weighted_volume.argtypes = [ctypes.POINTER(_Model), P]
         L.or_scale.restype = ctypes.c_double
         L.or_scale.argtypes = [ctypes.c_double, ctypes.c_int64, ctypes.c_int64]
         L.or_run_vv.restype = None
@@ -225,7 +235,7 @@ class Model:
     def __init__(self, coords, volumes, off, idx, *, c, sc=None, sc_hash=None,
                  c_bond=None, no_fail=None, bc_type=None, bc_disp=None, bc_force=None,
                  disp_rate=0.0, load=0.0, dt=1e-7, damping=0.0, density=1.0, rows=None,
-                 ramp_steps=0, kr=0.0):
+                 ramp_steps=0, kr=0.0, state_based=None):
         self.x = _c64(coords)
         n = self.x.shape[0]
         self.vol = _c64(volumes)
@@ -266,7 +276,18 @@ class Model:
         self.kappa = np.zeros(max(int(self.off[-1]), 1))
         m.kr = float(kr)
         m.kappa = self.kappa.ctypes.data
+        # ordinary state-based linear solid: state_based = (K, G); all nodes are rows
+        self.wvol = np.zeros(n)
+        self.theta = np.zeros(n)
+        m.wvol = self.wvol.ctypes.data
+        m.theta = self.theta.ctypes.data
+        if state_based is not None:
+            assert self.rows is None
+            m.model = 1
+            m.K, m.G = float(state_based[0]), float(state_based[1])
         self.m = m
+        if state_based is not None:
+            lib().or_osb_weighted_volume(ctypes.byref(m), self.wvol.ctypes.data)
         self.nrows = m.nrows
         self.nbonds = int(self.off[-1])
 
@@ -278,7 +299,8 @@ class Model:
                    c_bond=c_bond, no_fail=w.no_fail, bc_type=w.bc_type, bc_disp=w.bc_disp,
                    bc_force=w.bc_force, disp_rate=w.disp_rate, load=w.load, dt=w.dt,
                    damping=w.damping, density=w.density, rows=rows,
-                   ramp_steps=getattr(w, "ramp_steps", 0), kr=getattr(w, "kr", 0.0))
+                   ramp_steps=getattr(w, "ramp_steps", 0), kr=getattr(w, "kr", 0.0),
+                   state_based=getattr(w, "state_based", None))
 
     def step(self, step_index, u, v, mu, margin=None, want_force=False):
         """One step; returns (u_out, v_out[, F]) per row.  mu/margin updated in place."""
@@ -302,7 +324,7 @@ class Model:
     def run_vv(self, first_step, nsteps, u, v, a, mu, init=False, margin=None):
         """Damped velocity-Verlet steps over all nodes (see oracle.c); u, v, a
         (acceleration) and mu updated in place.  init: form a^0 from (u, v) first."""
-        assert self.rows is None
+        assert self.rows is None and self.m.model == 0
         for arr in (u, v, a):
             assert arr.dtype == np.float64 and arr.flags.c_contiguous
         lib().or_run_vv(ctypes.byref(self.m), int(first_step), int(nsteps), int(bool(init)),

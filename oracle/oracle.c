@@ -276,6 +276,11 @@ typedef struct {
     int64_t ramp_steps;      /* 0: scale(k) = disp_rate k; T > 0: smooth start over T steps */
     double kr;               /* >= 1: bilinear softening with s_0 = s_c / kr; 0: PMB */
     double* kappa;           /* kr >= 1: largest stretch each family entry has reached */
+    int32_t model;           /* 0 bond-based PMB; 1 ordinary state-based (linear solid) */
+    int32_t pad1;
+    double K, G;             /* model 1: bulk and shear modulus */
+    double* wvol;            /* model 1: weighted volume m_i per node (or_osb_weighted_volume) */
+    double* theta;           /* model 1: dilation per node, scratch of the step */
 } or_model;
 
 /* Bilinear bond law (Section 6, Example 3: the damage model of Gerstle et al.,
@@ -368,9 +373,117 @@ static void row_force(const or_model* m, int64_t r, const double* u, uint8_t* mu
  * margin (per family entry, or NULL) keeps min |s - s_c| over intact bonds.
  * Outputs are per row: u_out, v_out (3 per row) and, if F_out != NULL, the
  * force density F_i of Eq. (11) before integration. */
+/* ------------------------------------------------------------------ */
+/* Ordinary state-based peridynamics (Section "State-based Peridynamics": two
+ * loops per step, a nodal dilation and then the nodal force), with the linear
+ * peridynamic solid of Silling et al. (2007) as the material and a constant
+ * influence function omega = 1:
+ *   m_i     = sum_j |xi_ij|^2 V_j                      (weighted volume, reference)
+ *   e_ij    = |y_ij| - |xi_ij|                         (bond extension)
+ *   theta_i = (3 / m_i) sum_j mu_ij |xi_ij| e_ij V_j    (dilation)
+ *   t_ij    = (3 K theta_i / m_i) |xi_ij| + (15 G / m_i) (e_ij - theta_i |xi_ij| / 3)
+ *   F_i     = sum_j mu_ij (t_ij + t_ji) y_ij / |y_ij| V_j
+ * Bonds break in the dilation loop with the rule of Eq. (6) (s = e / |xi|), so
+ * a bond breaking in a step contributes to neither loop.  All nodes are rows. */
+void or_osb_weighted_volume(const or_model* m, double* out)
+{
+    for (int64_t i = 0; i < m->n; ++i) {
+        double acc = 0.0;
+        for (int64_t k = m->off[i]; k < m->off[i + 1]; ++k)
+            acc += dist2(m->x + 3 * i, m->x + 3 * m->idx[k]) * m->vol[m->idx[k]];
+        out[i] = acc;
+    }
+}
+
+static void bond_geom(const or_model* m, int64_t i, int64_t j, const double* u, double* L,
+                      double* rr, double y[3])
+{
+    double xi[3];
+    for (int a = 0; a < 3; ++a) {
+        xi[a] = m->x[3 * j + a] - m->x[3 * i + a];
+        y[a] = xi[a] + u[3 * j + a] - u[3 * i + a];
+    }
+    *L = sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
+    *rr = sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+}
+
+/* dilation of every node (first loop); breaks bonds if `breaking` */
+static void osb_dilation(const or_model* m, const double* u, uint8_t* mu, double* margin,
+                         int breaking)
+{
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < m->n; ++i) {
+        double acc = 0.0;
+        for (int64_t k = m->off[i]; k < m->off[i + 1]; ++k) {
+            if (!mu[k]) continue;
+            int64_t j = m->idx[k];
+            double L, rr, y[3];
+            bond_geom(m, i, j, u, &L, &rr, y);
+            if (breaking) {
+                double s = (rr - L) / L;
+                double sc = bond_sc(m, i, j);
+                if (margin) {
+                    double d = fabs(s - sc);
+                    if (d < margin[k]) margin[k] = d;
+                }
+                int nofail = m->no_fail && (m->no_fail[i] || m->no_fail[j]);
+                if (s >= sc && !nofail) {
+                    mu[k] = 0;
+                    continue;
+                }
+            }
+            acc += L * (rr - L) * m->vol[j];
+        }
+        m->theta[i] = m->wvol[i] > 0.0 ? 3.0 * acc / m->wvol[i] : 0.0;
+    }
+}
+
+/* force density of node i (second loop) from the dilations */
+static void osb_force(const or_model* m, int64_t i, const double* u, const uint8_t* mu,
+                      double F[3])
+{
+    F[0] = F[1] = F[2] = 0.0;
+    for (int64_t k = m->off[i]; k < m->off[i + 1]; ++k) {
+        if (!mu[k]) continue;
+        int64_t j = m->idx[k];
+        double L, rr, y[3];
+        bond_geom(m, i, j, u, &L, &rr, y);
+        double e = rr - L;
+        double ti = 3.0 * m->K * m->theta[i] / m->wvol[i] * L +
+                    15.0 * m->G / m->wvol[i] * (e - m->theta[i] * L / 3.0);
+        double tj = 3.0 * m->K * m->theta[j] / m->wvol[j] * L +
+                    15.0 * m->G / m->wvol[j] * (e - m->theta[j] * L / 3.0);
+        double f = (ti + tj) * m->vol[j] / rr;
+        for (int a = 0; a < 3; ++a) F[a] += f * y[a];
+    }
+    if (m->bc_force)
+        for (int a = 0; a < 3; ++a) F[a] += m->load * m->bc_force[3 * i + a];
+}
+
+/* strain energy density of the linear solid:
+ * W_i = K theta_i^2 / 2 + (15 G / (2 m_i)) sum_j mu_ij (e_ij - theta_i |xi_ij| / 3)^2 V_j */
+static void osb_energy(const or_model* m, const double* u, const uint8_t* mu, double* W)
+{
+    osb_dilation(m, u, (uint8_t*)mu, NULL, 0);
+    for (int64_t i = 0; i < m->n; ++i) {
+        double acc = 0.0;
+        for (int64_t k = m->off[i]; k < m->off[i + 1]; ++k) {
+            if (!mu[k]) continue;
+            int64_t j = m->idx[k];
+            double L, rr, y[3];
+            bond_geom(m, i, j, u, &L, &rr, y);
+            double ed = (rr - L) - m->theta[i] * L / 3.0;
+            acc += ed * ed * m->vol[j];
+        }
+        W[i] = 0.5 * m->K * m->theta[i] * m->theta[i] +
+               (m->wvol[i] > 0.0 ? 7.5 * m->G / m->wvol[i] * acc : 0.0);
+    }
+}
+
 void or_step(const or_model* m, int64_t step, const double* u, const double* v,
              uint8_t* mu, double* margin, double* u_out, double* v_out, double* F_out)
 {
+    if (m->model == 1) osb_dilation(m, u, mu, margin, 1);
     double a_damp = m->damping, rho = m->density, dt = m->dt;
     double s_now = or_scale(m->disp_rate, m->ramp_steps, step);
     double s_next = or_scale(m->disp_rate, m->ramp_steps, step + 1);
@@ -378,7 +491,10 @@ void or_step(const or_model* m, int64_t step, const double* u, const double* v,
     for (int64_t r = 0; r < m->nrows; ++r) {
         int64_t i = m->rows ? m->rows[r] : r;
         double F[3];
-        row_force(m, r, u, mu, margin, F);
+        if (m->model == 1)
+            osb_force(m, i, u, mu, F);
+        else
+            row_force(m, r, u, mu, margin, F);
         for (int a = 0; a < 3; ++a) {
             double vi = v[3 * i + a];
             double vn = vi + dt * (F[a] - a_damp * vi) / rho;
@@ -501,6 +617,10 @@ void or_damage(const or_model* m, const uint8_t* mu, double* phi)
  * shares each bond's energy between its two end nodes). */
 void or_energy_density(const or_model* m, const double* u, const uint8_t* mu, double* W)
 {
+    if (m->model == 1) {
+        osb_energy(m, u, mu, W);
+        return;
+    }
 #pragma omp parallel for schedule(static)
     for (int64_t r = 0; r < m->nrows; ++r) {
         int64_t i = m->rows ? m->rows[r] : r;
