@@ -68,6 +68,8 @@ def parse():
                    help="smooth start of the displacement loading over this many steps")
     p.add_argument("--kr", type=float, default=0.0,
                    help="bilinear softening with s_0 = s_c / kr (0: the PMB law)")
+    p.add_argument("--state-based", type=float, default=None, metavar="NU",
+                   help="ordinary state-based linear solid with Poisson's ratio NU (FP64)")
     p.add_argument("--fd-directions", type=int, default=32)
     p.add_argument("--checkpoint-every", type=int, default=45)
     p.add_argument("--precision", type=int, default=32, choices=[32, 64])
@@ -89,7 +91,9 @@ def describe(w, n_bonds, precision, integrator="ec"):
     return {
         "integrator": {"ec": "damped Euler-Cromer", "vv": "damped velocity-Verlet"}[integrator],
         "ramp_steps": int(getattr(w, "ramp_steps", 0)),
-        "bond_law": ("PMB" if not getattr(w, "kr", 0.0)
+        "bond_law": ("ordinary state-based linear solid, K = %.3g, G = %.3g" % w.state_based
+                     if getattr(w, "state_based", None) is not None
+                     else "PMB" if not getattr(w, "kr", 0.0)
                      else f"bilinear softening, s_0 = s_c / {w.kr:g}"),
         "workload": f"{w.name}: {w.n:,} nodes, {n_bonds:,} directed bonds, "
                     f"delta = {w.horizon / w.dx:.4g} dx, "
@@ -295,6 +299,9 @@ def run_ours(args):
     w = make_workload(args.workload)
     w.ramp_steps = args.ramp_steps
     w.kr = args.kr
+    if args.state_based is not None:
+        nu = args.state_based
+        w.state_based = (w.bulk_modulus, 3 * w.bulk_modulus * (1 - 2 * nu) / (2 * (1 + nu)))
     c = pdgb.pd_micromodulus(w.bulk_modulus, w.horizon)
     stream = torch.cuda.Stream(device=local)
     G = max(0, min(args.graph_steps, args.steps))

@@ -95,12 +95,27 @@ typedef struct {
     double c;             /* micromodulus, Eq. 5 (see pd_micromodulus) */
     double sc;            /* critical stretch, used when sc_mode == 0 */
     int32_t sc_mode;      /* 0 = constant sc; 1 = per-bond draw U[sc_lo, sc_hi) */
-    int32_t reserved;
+    int32_t model;        /* 0 = bond-based PMB (c); 1 = ordinary state-based linear
+                             solid (bulk_modulus, shear_modulus), see below */
     uint64_t sc_seed;     /* sc_mode 1: SplitMix64 seed; bond {i,j} uses output
                              min(i,j)*2^32 + max(i,j) + 1 of the stream (caller ids) */
     double sc_lo, sc_hi;
     double kr;            /* 0 = PMB (Eq. 5-6); >= 1 = bilinear softening, see below */
+    double bulk_modulus;  /* model 1: K (Pa) */
+    double shear_modulus; /* model 1: G (Pa) */
 } pd_material;
+
+/*
+ * Ordinary state-based model (model = 1; the paper's "State-based
+ * Peridynamics" section: a nodal dilation loop, then the force loop), with the
+ * linear peridynamic solid of Silling et al. (2007) and a constant influence
+ * function: m_i = sum_j |xi|^2 V_j, theta_i = (3/m_i) sum_j mu_ij |xi| e_ij V_j
+ * (e = |y| - |xi|), t_ij = (3 K theta_i / m_i)|xi| + (15 G / m_i)(e - theta_i |xi|/3),
+ * F_i = sum_j mu_ij (t_ij + t_ji) V_j y/|y|.  Bonds break as in Eq. 6.  Unlike
+ * the PMB law it is not limited to Poisson's ratio 1/4.  FP64 handles with the
+ * Euler-Cromer integrator only; c is not used (any value > 0); no softening,
+ * per-bond stiffness, batches or adjoint.  Two kernels per step.
+ */
 
 /*
  * Bilinear softening (Section 6, Example 3: the damage model with linear

@@ -60,9 +60,10 @@ class _Config(ctypes.Structure):
 
 class _Material(ctypes.Structure):
     _fields_ = [("c", ctypes.c_double), ("sc", ctypes.c_double), ("sc_mode", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("sc_seed", ctypes.c_uint64),
+                ("model", ctypes.c_int32), ("sc_seed", ctypes.c_uint64),
                 ("sc_lo", ctypes.c_double), ("sc_hi", ctypes.c_double),
-                ("kr", ctypes.c_double)]
+                ("kr", ctypes.c_double), ("bulk_modulus", ctypes.c_double),
+                ("shear_modulus", ctypes.c_double)]
 
 
 class _Bc(ctypes.Structure):
@@ -181,7 +182,8 @@ def pd_create(coords, volumes, horizon: float, *, c: float, sc: float = 0.0,
               dt: float, damping: float, density: float, precision: int = PD_PREC_F64,
               graph_steps: int = 0, check_dt: bool = False, device: int = 0, stream=None,
               block_threads: int = 0, blocks_per_sm: int = 0, reorder: int = 0,
-              integrator: int = 0, ramp_steps: int = 0, kr: float = 0.0) -> int:
+              integrator: int = 0, ramp_steps: int = 0, kr: float = 0.0,
+              state_based=None) -> int:
     """Create a model; returns an opaque handle (int).  See pd.h for the semantics."""
     x, kx = _ptr(coords, np.float64)
     n = (kx.numel() if hasattr(kx, "numel") else kx.size) // 3
@@ -201,6 +203,9 @@ def pd_create(coords, volumes, horizon: float, *, c: float, sc: float = 0.0,
     bf, kbf = _ptr(bc_force, np.float64, 3 * n if bc_force is not None else None)
     nf, knf = _ptr(no_fail, np.uint8, n if no_fail is not None else None)
     mat = _Material(c=float(c), sc=float(sc), sc_mode=0, kr=float(kr))
+    if state_based is not None:  # (K, G): ordinary state-based linear solid
+        mat.model = 1
+        mat.bulk_modulus, mat.shear_modulus = float(state_based[0]), float(state_based[1])
     if sc_hash is not None:
         mat.sc_mode = 1
         mat.sc_seed, mat.sc_lo, mat.sc_hi = int(sc_hash[0]), float(sc_hash[1]), float(sc_hash[2])
@@ -455,7 +460,8 @@ class Model:
                    sc_hash=w.sc_hash, cuts=w.cuts_array(), bc_type=w.bc_type, bc_disp=w.bc_disp,
                    bc_force=w.bc_force, no_fail=w.no_fail, disp_rate=w.disp_rate, load=w.load,
                    dt=w.dt, damping=w.damping, density=w.density, precision=precision,
-                   ramp_steps=getattr(w, "ramp_steps", 0), kr=getattr(w, "kr", 0.0), **kw)
+                   ramp_steps=getattr(w, "ramp_steps", 0), kr=getattr(w, "kr", 0.0),
+                   state_based=getattr(w, "state_based", None), **kw)
 
     def close(self):
         if self.h:

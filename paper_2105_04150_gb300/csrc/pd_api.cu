@@ -121,6 +121,11 @@ struct pd_handle {
     int64_t peek_step = -1; // step whose force pass filled vpeek (-1: none)
     double kr = 0.0;        // >= 1: bilinear softening, s_0 = s_c / kr
     void* integ = nullptr;  // softening: per-slot integrity (float / double)
+    int model = 0;          // 1: ordinary state-based linear solid (FP64)
+    double osb_K = 0.0, osb_G = 0.0;
+    double* osb_len = nullptr;    // per slot |xi|
+    double* osb_mvol = nullptr;   // per node weighted volume
+    double* osb_theta = nullptr;  // per node dilation
     void* wsum_inv = nullptr;
     void* damage = nullptr;
     int* err = nullptr;
@@ -294,8 +299,22 @@ const void* f32_kernel(pd_handle* h)
                                : step_f32_kernel(h->sc_mode, h->uniform_vol, h->per_bond_c);
 }
 
+OsbArgs osb_args(pd_handle* h)
+{
+    OsbArgs o{};
+    o.len = h->osb_len;
+    o.vol = h->vol;
+    o.mvol = h->osb_mvol;
+    o.theta = h->osb_theta;
+    o.K = h->osb_K;
+    o.G = h->osb_G;
+    return o;
+}
+
 cudaError_t launch_one(pd_handle* h, int k)
 {
+    if (h->model == 1)
+        return launch_osb_step(args_f64(h, k), osb_args(h), h->grid, h->block, h->stream);
     if (h->precision == 32)
         return launch_f32(h, args_f32(h, k));
     return launch_step_f64(args_f64(h, k), h->sc_mode, h->grid, h->block, h->stream);
@@ -447,6 +466,14 @@ pd_status check_material(const pd_material* mat)
     }
     if (mat->kr != 0.0 && !(mat->kr >= 1.0 && std::isfinite(mat->kr)))
         return fail(PD_ERR_ARG, "kr must be 0 (PMB) or a finite value >= 1 (bilinear softening)");
+    if (mat->model != 0 && mat->model != 1) return fail(PD_ERR_ARG, "model must be 0 or 1");
+    if (mat->model == 1) {
+        if (!(mat->bulk_modulus > 0.0) || !(mat->shear_modulus >= 0.0) ||
+            !std::isfinite(mat->bulk_modulus) || !std::isfinite(mat->shear_modulus))
+            return fail(PD_ERR_ARG, "the state-based model needs bulk_modulus > 0, shear_modulus >= 0");
+        if (mat->kr != 0.0)
+            return fail(PD_ERR_ARG, "softening is not available with the state-based model");
+    }
     return PD_OK;
 }
 
@@ -561,6 +588,14 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
         ALLOC(h->damage, double, np);
         ALLOC(h->ilen, double, nbr.size());
     }
+    if (h->model == 1) {
+        if (f32) return fail(PD_ERR_ARG, "the state-based model is FP64 only");
+        if (h->integrator != PD_INTEGRATOR_EC)
+            return fail(PD_ERR_ARG, "the state-based model uses the Euler-Cromer integrator");
+        ALLOC(h->osb_len, double, nbr.size());
+        ALLOC(h->osb_mvol, double, np);
+        ALLOC(h->osb_theta, double, np);
+    }
     if (h->kr >= 1.0) {  // bilinear softening: every bond starts intact, mu = 1
         if (f32)
             ALLOC(h->integ, float, nbr.size());
@@ -673,6 +708,10 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
         e = launch_inv_len(h->x64, h->nbr, h->sw, n, h->Q, h->ilen, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "bond lengths");
     }
+    if (h->model == 1) {
+        e = launch_osb_setup(args_f64(h, 0), osb_args(h), h->x64, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "state-based set-up");
+    }
     if ((st = upload_weights(h)) != PD_OK) return st;
     h->blocks_per_sm = cfg->blocks_per_sm;
     if ((st = choose_grid(h, h->blocks_per_sm)) != PD_OK) return st;
@@ -685,6 +724,9 @@ void set_material(pd_handle* h, const pd_material* mat, const pd_bc* bc)
 {
     h->c = mat->c;
     h->kr = mat->kr;
+    h->model = mat->model;
+    h->osb_K = mat->bulk_modulus;
+    h->osb_G = mat->shear_modulus;
     h->sc_mode = mat->sc_mode;
     h->sc = mat->sc_mode == 0 ? mat->sc : 0.5 * (mat->sc_lo + mat->sc_hi);
     h->sc_seed = mat->sc_seed;
@@ -773,8 +815,10 @@ pd_status pd_batch_create(int32_t n_inst, const pd_instance* inst, const pd_conf
             I.bc.ramp_steps != inst[0].bc.ramp_steps)
             return fail(PD_ERR_ARG,
                         "instance %d: disp_rate, load and ramp_steps must equal instance 0's", b);
-        if (I.mat.kr != 0.0)
-            return fail(PD_ERR_ARG, "instance %d: bilinear softening is not available in batches", b);
+        if (I.mat.kr != 0.0 || I.mat.model != 0)
+            return fail(PD_ERR_ARG,
+                        "instance %d: softening and the state-based model are not available "
+                        "in batches", b);
         n += I.n;
         unit = std::max(unit, I.horizon);
         any_nofail = any_nofail || I.bc.no_fail != nullptr;
@@ -1157,7 +1201,8 @@ pd_status pd_damage(pd_handle* h, double* phi)
 pd_status pd_adjoint_forward(pd_handle* h, int64_t n_steps, int64_t checkpoint_every)
 {
     if (!h) return fail(PD_ERR_ARG, "NULL handle");
-    if (h->precision != 64 || h->batch || h->integrator != PD_INTEGRATOR_EC || h->integ)
+    if (h->precision != 64 || h->batch || h->integrator != PD_INTEGRATOR_EC || h->integ ||
+        h->model != 0)
         return fail(PD_ERR_STATE,
                     "the adjoint is available on FP64 single-model Euler-Cromer PMB handles");
     if (n_steps < 1 || checkpoint_every < 0)
@@ -1475,6 +1520,8 @@ pd_status pd_set_params(pd_handle* h, double c, double sc, double load, double d
 {
     if (!h) return fail(PD_ERR_ARG, "NULL handle");
     if (h->batch) return fail(PD_ERR_STATE, "pd_set_params is not available on a batch handle");
+    if (h->model == 1 && c_bond)
+        return fail(PD_ERR_STATE, "per-bond stiffness is not available with the state-based model");
     if (!(c > 0.0) || !std::isfinite(c)) return fail(PD_ERR_ARG, "c must be > 0");
     if (!(sc > 0.0) || !std::isfinite(sc)) return fail(PD_ERR_ARG, "sc must be > 0");
     if (!std::isfinite(load) || !std::isfinite(disp_rate))

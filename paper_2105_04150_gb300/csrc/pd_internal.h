@@ -133,6 +133,15 @@ struct StepArgsF64 {
     double kr;                 // s_0 = s_c / kr
 };
 
+// Ordinary state-based (linear solid) arrays, FP64 handles with model 1
+struct OsbArgs {
+    double* len;               // per slot |xi|
+    const double* vol;         // per node V
+    double* mvol;              // per node weighted volume m_i
+    double* theta;             // per node dilation of the current step
+    double K, G;               // bulk and shear modulus
+};
+
 // Arguments of one reverse step of the FP64 adjoint (pd_adjoint.cu); node arrays
 // in library order, n_pad entries.
 struct AdjArgs {
@@ -222,6 +231,12 @@ cudaError_t launch_gather_damage(int precision, const void* dmg, const int32_t* 
                                  double* phi_out, cudaStream_t s);
 // node weights w = wscale * V (FP32: the w array, passed as wrec0; FP64: both
 // record buffers) and wsum_inv (a slot is a real member iff its init_bits bit is set)
+// state-based model: per-slot |xi| and weighted volumes (once), and one step
+// (dilation kernel, then force + integration kernel)
+cudaError_t launch_osb_setup(const StepArgsF64& a, const OsbArgs& o, const double* x64,
+                             cudaStream_t s);
+cudaError_t launch_osb_step(const StepArgsF64& a, const OsbArgs& o, int grid, int block,
+                            cudaStream_t s);
 // per slot 1 / |x_j - x_i| from the FP64 reference positions (0 for unused slots)
 cudaError_t launch_inv_len(const double* x64, const int32_t* nbr, const int32_t* sw, int64_t n,
                            int Q, double* ilen, cudaStream_t s);

@@ -1,0 +1,81 @@
+"""Ordinary state-based linear solid on the GPU (FP64), through the C ABI,
+against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2105_04150_gb300 as pdgb
+import workloads
+
+pytestmark = pytest.mark.gpu
+F64, F32 = pdgb.PD_PREC_F64, pdgb.PD_PREC_F32
+BAND = 1e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pdgb.build()
+    oracle.build()
+
+
+def _moduli(K, nu):
+    return K, 3 * K * (1 - 2 * nu) / (2 * (1 + nu))
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def _compare(w, steps):
+    off, idx = oracle.cut_family(w.coords, w.horizon, w.cuts_array())
+    om = oracle.Model.from_workload(w, off, idx)
+    u, v, mu = np.zeros((w.n, 3)), np.zeros((w.n, 3)), om.fresh_bonds()
+    margin = np.full(len(mu), np.inf)
+    om.run(0, steps, u, v, mu, margin)
+    m = pdgb.Model.from_workload(w, precision=F64, graph_steps=16)
+    m.step(steps)
+    ug, vg = m.state()
+    b, phi = m.bonds(), m.damage()
+    m.close()
+    assert rel(ug, u) <= 1e-10 and rel(vg, v) <= 1e-9
+    diff = b != mu
+    assert np.all(margin[diff] < BAND), int(diff.sum())
+    assert np.abs(phi - om.damage(mu)).max() <= 1e-12 + 2.0 * diff.sum() / len(diff)
+    return mu
+
+
+@pytest.mark.parametrize("nu", [0.25, 0.35])
+def test_state_based_tensile_bar_matches_oracle(nu):
+    w = workloads.tensile_bar(steps=1000)
+    w.state_based = _moduli(w.bulk_modulus, nu)
+    mu = _compare(w, w.steps)
+    assert (mu == 0).sum() > 0
+
+
+def test_state_based_notched_beam_per_bond_sc():
+    w = workloads.notched_beam(48, 10, 12, length=48 / 600, rate=1e-7, steps=300)
+    w.state_based = _moduli(w.bulk_modulus, 0.2)
+    _compare(w, w.steps)
+
+
+def test_state_based_restrictions():
+    w = workloads.tensile_bar(8, 4, 4, steps=5)
+    w.state_based = _moduli(w.bulk_modulus, 0.3)
+    with pytest.raises(pdgb.PdError) as e:
+        pdgb.Model.from_workload(w, precision=F32)
+    assert e.value.name == "PD_ERR_ARG"
+    with pytest.raises(pdgb.PdError) as e:
+        pdgb.Model.from_workload(w, precision=F64, integrator=pdgb.PD_INTEGRATOR_VV)
+    assert e.value.name == "PD_ERR_ARG"
+    m = pdgb.Model.from_workload(w, precision=F64)
+    off, idx = m.family()
+    with pytest.raises(pdgb.PdError) as e:
+        m.set_params(1.0, w.sc, 0.0, w.disp_rate, np.ones(len(idx)))
+    assert e.value.name == "PD_ERR_STATE"
+    with pytest.raises(pdgb.PdError) as e:
+        pdgb.pd_adjoint_forward(m.h, 3)
+    assert e.value.name == "PD_ERR_STATE"
+    m.close()
