@@ -51,6 +51,11 @@ BYTES_PER_NODE = {32: 93.0, 64: 136.0}
 # (nominal 1.25).
 FP64_FLOPS_PER_BOND = 31.0
 FP64_PEAK_TFLOPS = 1.20
+# Ordinary state-based step, both loops: the dilation loop (xi, eta, y 9; |y|^2
+# 5; root 1; e 1; |xi| e V and the sum 3 = 19) and the force loop (y 9; |y|^2
+# 5; root 1; e 1; t_ij 5; t_ji 8; the sum, V / |y| 3; accumulation 6 = 38):
+# 57 flops per bond.
+OSB_FLOPS_PER_BOND = 57.0
 STEP_SRC = {32: "pd_step_f32.cu", 64: "pd_step_f64.cu"}
 
 
@@ -377,12 +382,15 @@ def run_ours(args):
                 else "fallback 6.8 TB/s", "algorithmic_bytes_per_launch": alg_bytes,
                 "kernel": f"k_step_f{args.precision}"}
     if args.precision == 64:
-        tf = FP64_FLOPS_PER_BOND * n_bonds / (ms_step * 1e-3) / 1e12
+        fpb = OSB_FLOPS_PER_BOND if args.state_based is not None else FP64_FLOPS_PER_BOND
+        tf = fpb * n_bonds / (ms_step * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": tf / FP64_PEAK_TFLOPS, "traffic": profiled_traffic(64, args.workload),
+                    "frac": tf / FP64_PEAK_TFLOPS,
+                    "traffic": None if args.state_based is not None
+                    else profiled_traffic(64, args.workload),
                     "peak_source": "FP64 FMA throughput measured by a probe on this pool's GB300 "
                                    "(nominal 1.25 TFLOP/s)",
-                    "algorithmic_flops_per_bond": FP64_FLOPS_PER_BOND,
+                    "algorithmic_flops_per_bond": fpb,
                     "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
                             "frac": achieved / peak}, "kernel": "k_step_f64"}
     cpu = None
