@@ -392,7 +392,9 @@ def run_ours(args):
                                    "(nominal 1.25 TFLOP/s)",
                     "algorithmic_flops_per_bond": fpb,
                     "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
-                            "frac": achieved / peak}, "kernel": "k_step_f64"}
+                            "frac": achieved / peak},
+                    "kernel": "k_osb_dilation + k_osb_force" if args.state_based is not None
+                    else "k_step_f64"}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         import oracle
