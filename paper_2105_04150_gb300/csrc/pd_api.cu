@@ -126,6 +126,8 @@ struct pd_handle {
     double* osb_len = nullptr;    // per slot |xi|
     double* osb_mvol = nullptr;   // per node weighted volume
     double* osb_theta = nullptr;  // per node dilation
+    double* osb_alpha = nullptr;  // per node force-scalar coefficients (see pd_step_osb.cu)
+    double* osb_beta = nullptr;
     void* wsum_inv = nullptr;
     void* damage = nullptr;
     int* err = nullptr;
@@ -306,6 +308,8 @@ OsbArgs osb_args(pd_handle* h)
     o.vol = h->vol;
     o.mvol = h->osb_mvol;
     o.theta = h->osb_theta;
+    o.alpha = h->osb_alpha;
+    o.beta = h->osb_beta;
     o.K = h->osb_K;
     o.G = h->osb_G;
     return o;
@@ -595,6 +599,8 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
         ALLOC(h->osb_len, double, nbr.size());
         ALLOC(h->osb_mvol, double, np);
         ALLOC(h->osb_theta, double, np);
+        ALLOC(h->osb_alpha, double, np);
+        ALLOC(h->osb_beta, double, np);
     }
     if (h->kr >= 1.0) {  // bilinear softening: every bond starts intact, mu = 1
         if (f32)

@@ -139,6 +139,8 @@ struct OsbArgs {
     const double* vol;         // per node V
     double* mvol;              // per node weighted volume m_i
     double* theta;             // per node dilation of the current step
+    double* alpha;             // per node 3 K theta / m - beta theta / 3 (current step)
+    double* beta;              // per node 15 G / m
     double K, G;               // bulk and shear modulus
 };
 

@@ -6,12 +6,15 @@
 //   k_osb_dilation  per node: bonds past s_c break (Eq. 6, s = e / |xi|), then
 //                   theta_i = (3 / m_i) sum_j mu_ij |xi| e_ij V_j, e = |y| - |xi|
 //   k_osb_force     per node: F_i = sum_j mu_ij (t_ij + t_ji) V_j y / |y| with
-//                   t_ij = (3 K theta_i / m_i) |xi| + (15 G / m_i)(e - theta_i |xi| / 3),
-//                   the neighbour's theta_j and m_j gathered; then the damped
-//                   Euler-Cromer update, boundary conditions and damage of the
-//                   bond-based FP64 step
+//                   t_ij = (3 K theta_i / m_i) |xi| + (15 G / m_i)(e - theta_i |xi| / 3);
+//                   then the damped Euler-Cromer update, boundary conditions
+//                   and damage of the bond-based FP64 step
 //
 // m_i = sum_j |xi|^2 V_j over the family after the initial cuts, computed once.
+// t_ij is linear in the bond: t_ij = alpha_i |xi| + beta_i e with
+// beta_i = 15 G / m_i (once) and alpha_i = 3 K theta_i / m_i - beta_i theta_i / 3
+// (written by the dilation kernel), so the force loop gathers two coefficients
+// per neighbour and divides nothing (FP64 division is costly on GB300).
 // The record layout, double buffering and step counter are the FP64 step's.
 #include <cuda_runtime.h>
 
@@ -77,6 +80,7 @@ __global__ void __launch_bounds__(256) k_osb_weighted_volume(const StepArgsF64 a
             }
         }
         o.mvol[p] = acc;
+        o.beta[p] = acc > 0.0 ? 15.0 * o.G / acc : 0.0;
     }
 }
 
@@ -118,7 +122,9 @@ __global__ void __launch_bounds__(256) k_osb_dilation(const StepArgsF64 a, OsbAr
             if (nword != word) *bw = nword;
         }
         const double m = o.mvol[i];
-        o.theta[i] = m > 0.0 ? 3.0 * acc / m : 0.0;
+        const double th = m > 0.0 ? 3.0 * acc / m : 0.0;
+        o.theta[i] = th;
+        o.alpha[i] = m > 0.0 ? 3.0 * o.K * th / m - o.beta[i] * th / 3.0 : 0.0;
     }
 }
 
@@ -136,9 +142,7 @@ __global__ void __launch_bounds__(256) k_osb_force(const StepArgsF64 a, OsbArgs 
     for (int64_t g = wid; g < nslices; g += nwarps) {
         const int64_t i = (g << 5) + lane;
         const int Wg = a.sw[g];
-        const double mi = o.mvol[i], thi = o.theta[i];
-        const double ai = mi > 0.0 ? 3.0 * o.K * thi / mi : 0.0;
-        const double bi = mi > 0.0 ? 15.0 * o.G / mi : 0.0;
+        const double ai = o.alpha[i], bi = o.beta[i];
         double fx = 0.0, fy = 0.0, fz = 0.0, ws = 0.0;
         for (int q = 0; q * 32 < Wg; ++q) {
             const uint32_t word = a.bits[(g * a.Q + q) * 32 + lane];
@@ -150,10 +154,9 @@ __global__ void __launch_bounds__(256) k_osb_force(const StepArgsF64 a, OsbArgs 
                 const OsbBond bd = osb_bond(rin, i, j);
                 const double L = o.len[slot];
                 const double e = bd.r - L;
-                const double mj = o.mvol[j], thj = o.theta[j];
-                const double ti = ai * L + bi * (e - thi * L / 3.0);
-                const double tj = (3.0 * o.K * thj / mj) * L + (15.0 * o.G / mj) * (e - thj * L / 3.0);
-                const double f = (ti + tj) * o.vol[j] * bd.ir;
+                // t_ij + t_ji
+                const double t = (ai + o.alpha[j]) * L + (bi + o.beta[j]) * e;
+                const double f = t * o.vol[j] * bd.ir;
                 fx += f * bd.y0;
                 fy += f * bd.y1;
                 fz += f * bd.y2;
