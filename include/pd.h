@@ -103,6 +103,9 @@ typedef struct {
     double kr;            /* 0 = PMB (Eq. 5-6); >= 1 = bilinear softening, see below */
     double bulk_modulus;  /* model 1: K (Pa) */
     double shear_modulus; /* model 1: G (Pa) */
+    double kink_ratio;    /* kr >= 1: 0 = bilinear; > 1 = trilinear with the kink at
+                             s_1 = kink_ratio * s_0 (< s_c) */
+    double kink_force;    /* trilinear: force at the kink / peak force c s_0, in (0, 1] */
 } pd_material;
 
 /*
@@ -125,8 +128,11 @@ typedef struct {
  *   mu = s_0 (s_c - k) / (k (s_c - s_0))      k = the largest stretch so far (< s_c),
  *   mu = 0                                    once k >= s_c (broken, as in Eq. 6),
  * and pulls with c s mu V_j (Eq. 5 times mu): the force rises to c s_0, falls
- * linearly to zero at s_c, and unloads along the secant to the origin.  The
- * damage (Eq. 8) weighs each bond by its integrity.  kr = 1 is the PMB law.
+ * linearly to zero at s_c, and unloads along the secant to the origin.  With
+ * kink_ratio > 1 the law is trilinear (Section 6, Example 2): the force falls
+ * from c s_0 to kink_force * c s_0 at s_1 = kink_ratio * s_0, then to zero at
+ * s_c; mu = envelope(k) / (c k).  The damage (Eq. 8) weighs each bond by its
+ * integrity.  kr = 1 is the PMB law.
  * Not available in batches or with the adjoint.
  */
 typedef struct {

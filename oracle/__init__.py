@@ -93,6 +93,7 @@ class _Model(ctypes.Structure):
         ("model", ctypes.c_int32), ("pad1", ctypes.c_int32),
         ("K", ctypes.c_double), ("G", ctypes.c_double),
         ("wvol", ctypes.c_void_p), ("theta", ctypes.c_void_p),
+        ("k1", ctypes.c_double), ("beta", ctypes.c_double),
     ]
 
 
@@ -235,7 +236,7 @@ class Model:
     def __init__(self, coords, volumes, off, idx, *, c, sc=None, sc_hash=None,
                  c_bond=None, no_fail=None, bc_type=None, bc_disp=None, bc_force=None,
                  disp_rate=0.0, load=0.0, dt=1e-7, damping=0.0, density=1.0, rows=None,
-                 ramp_steps=0, kr=0.0, state_based=None):
+                 ramp_steps=0, kr=0.0, state_based=None, trilinear=None):
         self.x = _c64(coords)
         n = self.x.shape[0]
         self.vol = _c64(volumes)
@@ -276,6 +277,8 @@ class Model:
         self.kappa = np.zeros(max(int(self.off[-1]), 1))
         m.kr = float(kr)
         m.kappa = self.kappa.ctypes.data
+        if trilinear is not None:  # (k1 = s_1 / s_0, beta = kink force / peak force)
+            m.k1, m.beta = float(trilinear[0]), float(trilinear[1])
         # ordinary state-based linear solid: state_based = (K, G); all nodes are rows
         self.wvol = np.zeros(n)
         self.theta = np.zeros(n)
@@ -300,7 +303,8 @@ class Model:
                    bc_force=w.bc_force, disp_rate=w.disp_rate, load=w.load, dt=w.dt,
                    damping=w.damping, density=w.density, rows=rows,
                    ramp_steps=getattr(w, "ramp_steps", 0), kr=getattr(w, "kr", 0.0),
-                   state_based=getattr(w, "state_based", None))
+                   state_based=getattr(w, "state_based", None),
+                   trilinear=getattr(w, "trilinear", None))
 
     def step(self, step_index, u, v, mu, margin=None, want_force=False):
         """One step; returns (u_out, v_out[, F]) per row.  mu/margin updated in place."""

@@ -281,6 +281,8 @@ typedef struct {
     double K, G;             /* model 1: bulk and shear modulus */
     double* wvol;            /* model 1: weighted volume m_i per node (or_osb_weighted_volume) */
     double* theta;           /* model 1: dilation per node, scratch of the step */
+    double k1;               /* > 1: trilinear softening with the kink at s_1 = k1 s_0 */
+    double beta;             /* trilinear: force at the kink / force at s_0 */
 } or_model;
 
 /* Bilinear bond law (Section 6, Example 3: the damage model of Gerstle et al.,
@@ -293,10 +295,19 @@ typedef struct {
  *             = 0 (broken, irreversibly)             kappa >= s_c
  * and the force is c s mu(kappa) V_j y/|y|.  kr = 1 (s_0 = s_c) is the PMB law
  * again, with the history kept. */
-static double soft_mu(double kappa, double s0, double sc)
+static double soft_mu(const or_model* m, double kappa, double s0, double sc)
 {
     if (kappa <= s0) return 1.0;
     if (kappa >= sc) return 0.0;
+    if (m->k1 > 1.0) {
+        /* trilinear (Section 6, Example 2, after Yang et al.): the force falls
+         * linearly from c s_0 at s_0 to beta c s_0 at the kink s_1, then to 0 at
+         * s_c; mu = envelope / (c kappa) */
+        double s1 = m->k1 * s0;
+        if (kappa <= s1)
+            return s0 * ((1.0 - m->beta) * (s1 - kappa) / (s1 - s0) + m->beta) / kappa;
+        return s0 * m->beta * (sc - kappa) / ((sc - s1) * kappa);
+    }
     return s0 * (sc - kappa) / (kappa * (sc - s0));
 }
 
@@ -361,7 +372,7 @@ static void row_force(const or_model* m, int64_t r, const double* u, uint8_t* mu
         }
         double cij = m->c_bond ? m->c_bond[k] : m->c;
         double f = cij * s * m->vol[j] / rr;
-        if (m->kr >= 1.0) f = cij * s * soft_mu(kap, sc / m->kr, sc) * m->vol[j] / rr;
+        if (m->kr >= 1.0) f = cij * s * soft_mu(m, kap, sc / m->kr, sc) * m->vol[j] / rr;
         for (int a = 0; a < 3; ++a) F[a] += f * y[a];
     }
     if (m->bc_force)
@@ -603,7 +614,7 @@ void or_damage(const or_model* m, const uint8_t* mu, double* phi)
             if (m->kr >= 1.0) {
                 /* Eq. (8) with the bond's integrity mu(kappa) in [0, 1] */
                 double sc = bond_sc(m, i, m->idx[k]);
-                num += soft_mu(m->kappa[k], sc / m->kr, sc) * vj;
+                num += soft_mu(m, m->kappa[k], sc / m->kr, sc) * vj;
             } else {
                 num += vj;
             }

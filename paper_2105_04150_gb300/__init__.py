@@ -63,7 +63,8 @@ class _Material(ctypes.Structure):
                 ("model", ctypes.c_int32), ("sc_seed", ctypes.c_uint64),
                 ("sc_lo", ctypes.c_double), ("sc_hi", ctypes.c_double),
                 ("kr", ctypes.c_double), ("bulk_modulus", ctypes.c_double),
-                ("shear_modulus", ctypes.c_double)]
+                ("shear_modulus", ctypes.c_double), ("kink_ratio", ctypes.c_double),
+                ("kink_force", ctypes.c_double)]
 
 
 class _Bc(ctypes.Structure):
@@ -183,7 +184,7 @@ def pd_create(coords, volumes, horizon: float, *, c: float, sc: float = 0.0,
               graph_steps: int = 0, check_dt: bool = False, device: int = 0, stream=None,
               block_threads: int = 0, blocks_per_sm: int = 0, reorder: int = 0,
               integrator: int = 0, ramp_steps: int = 0, kr: float = 0.0,
-              state_based=None) -> int:
+              state_based=None, trilinear=None) -> int:
     """Create a model; returns an opaque handle (int).  See pd.h for the semantics."""
     x, kx = _ptr(coords, np.float64)
     n = (kx.numel() if hasattr(kx, "numel") else kx.size) // 3
@@ -203,6 +204,8 @@ def pd_create(coords, volumes, horizon: float, *, c: float, sc: float = 0.0,
     bf, kbf = _ptr(bc_force, np.float64, 3 * n if bc_force is not None else None)
     nf, knf = _ptr(no_fail, np.uint8, n if no_fail is not None else None)
     mat = _Material(c=float(c), sc=float(sc), sc_mode=0, kr=float(kr))
+    if trilinear is not None:  # (s_1 / s_0, kink force / peak force)
+        mat.kink_ratio, mat.kink_force = float(trilinear[0]), float(trilinear[1])
     if state_based is not None:  # (K, G): ordinary state-based linear solid
         mat.model = 1
         mat.bulk_modulus, mat.shear_modulus = float(state_based[0]), float(state_based[1])
@@ -461,7 +464,8 @@ class Model:
                    bc_force=w.bc_force, no_fail=w.no_fail, disp_rate=w.disp_rate, load=w.load,
                    dt=w.dt, damping=w.damping, density=w.density, precision=precision,
                    ramp_steps=getattr(w, "ramp_steps", 0), kr=getattr(w, "kr", 0.0),
-                   state_based=getattr(w, "state_based", None), **kw)
+                   state_based=getattr(w, "state_based", None),
+                   trilinear=getattr(w, "trilinear", None), **kw)
 
     def close(self):
         if self.h:

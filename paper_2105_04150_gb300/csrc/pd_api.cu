@@ -120,6 +120,7 @@ struct pd_handle {
     void* vpeek = nullptr;  // velocity-Verlet: full-step velocity for pd_get_state
     int64_t peek_step = -1; // step whose force pass filled vpeek (-1: none)
     double kr = 0.0;        // >= 1: bilinear softening, s_0 = s_c / kr
+    double k1 = 0.0, beta = 1.0;  // trilinear kink (k1 > 1)
     void* integ = nullptr;  // softening: per-slot integrity (float / double)
     int model = 0;          // 1: ordinary state-based linear solid (FP64)
     double osb_K = 0.0, osb_G = 0.0;
@@ -226,6 +227,8 @@ StepArgsF32 args_f32(pd_handle* h, int k)
     if (h->integ != nullptr) {  // softening: the band below the smallest s_0 is resolved too
         a.integ = (float*)h->integ;
         a.kr = h->kr;
+        a.k1 = h->k1;
+        a.beta = h->beta;
         a.fast_lo = (float)((1.0 - 2.0 * a.guard) * h->sc_lo / h->kr);
     }
     a.sc = h->sc;
@@ -260,6 +263,8 @@ StepArgsF64 args_f64(pd_handle* h, int k)
     a.ilen = h->ilen;
     a.integ = (double*)h->integ;
     a.kr = h->kr;
+    a.k1 = h->k1;
+    a.beta = h->beta;
     a.bcc = h->bcc;
     a.bct = h->bct;
     a.gid = h->gid;
@@ -470,6 +475,10 @@ pd_status check_material(const pd_material* mat)
     }
     if (mat->kr != 0.0 && !(mat->kr >= 1.0 && std::isfinite(mat->kr)))
         return fail(PD_ERR_ARG, "kr must be 0 (PMB) or a finite value >= 1 (bilinear softening)");
+    if (mat->kink_ratio != 0.0 &&
+        !(mat->kr > 1.0 && mat->kink_ratio > 1.0 && mat->kink_ratio < mat->kr &&
+          mat->kink_force > 0.0 && mat->kink_force <= 1.0))
+        return fail(PD_ERR_ARG, "trilinear softening needs kr > kink_ratio > 1 and kink_force in (0, 1]");
     if (mat->model != 0 && mat->model != 1) return fail(PD_ERR_ARG, "model must be 0 or 1");
     if (mat->model == 1) {
         if (!(mat->bulk_modulus > 0.0) || !(mat->shear_modulus >= 0.0) ||
@@ -730,6 +739,8 @@ void set_material(pd_handle* h, const pd_material* mat, const pd_bc* bc)
 {
     h->c = mat->c;
     h->kr = mat->kr;
+    h->k1 = mat->kink_ratio;
+    h->beta = mat->kink_ratio > 1.0 ? mat->kink_force : 1.0;
     h->model = mat->model;
     h->osb_K = mat->bulk_modulus;
     h->osb_G = mat->shear_modulus;

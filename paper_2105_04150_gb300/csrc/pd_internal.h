@@ -95,6 +95,7 @@ struct StepArgsF32 {
     float* vout;               // peek: 3 floats per node (library order)
     float* integ;              // bilinear softening: per-slot integrity mu, or nullptr
     double kr;                 // s_0 = s_c / kr
+    double k1, beta;           // trilinear: kink at s_1 = k1 s_0 with force beta c s_0 (k1 > 1)
 };
 
 struct StepArgsF64 {
@@ -131,6 +132,7 @@ struct StepArgsF64 {
     double* vout;              // peek: 3 doubles per node (library order)
     double* integ;             // bilinear softening: per-slot integrity mu, or nullptr
     double kr;                 // s_0 = s_c / kr
+    double k1, beta;           // trilinear: kink at s_1 = k1 s_0 with force beta c s_0 (k1 > 1)
 };
 
 // Ordinary state-based (linear solid) arrays, FP64 handles with model 1
@@ -256,6 +258,22 @@ __device__ __forceinline__ double bc_scale(double rate, int64_t T, int64_t k)
     if (k >= T) return rate * ((double)k - 0.6 * (double)T);
     const double t = (double)k / (double)T;
     return rate * (double)T * (t * t * t * t - 0.6 * t * t * t * t * t);
+}
+#endif
+
+#ifdef __CUDACC__
+// Softening integrity mu = envelope(s) / (c s) for s_0 < s < s_c: bilinear (the
+// force falls linearly from c s_0 to 0 at s_c) or, with k1 > 1, trilinear (from
+// c s_0 to beta c s_0 at the kink s_1 = k1 s_0, then to 0 at s_c)
+__device__ __forceinline__ double soft_mu_of(double s, double s0, double sc, double k1,
+                                             double beta)
+{
+    if (k1 > 1.0) {
+        const double s1 = k1 * s0;
+        if (s <= s1) return s0 * ((1.0 - beta) * (s1 - s) / (s1 - s0) + beta) / s;
+        return s0 * beta * (sc - s) / ((sc - s1) * s);
+    }
+    return s0 * (sc - s) / (s * (sc - s0));
 }
 #endif
 

@@ -334,7 +334,7 @@ __device__ __noinline__ float4 resolve_bond(const StepArgsF32& a, int cur, int64
         mu = a.integ[slot];
         const double s = (double)(b.num / b.den), s0 = sc / a.kr;
         if (s > s0) {
-            const float ms = s >= sc ? 0.0f : (float)(s0 * (sc - s) / (s * (sc - s0)));
+            const float ms = s >= sc ? 0.0f : (float)soft_mu_of(s, s0, sc, a.k1, a.beta);
             if (ms < mu) {
                 mu = ms;
                 a.integ[slot] = ms;

@@ -126,7 +126,8 @@ __global__ void __launch_bounds__(256) k_step_f64(const StepArgsF64 a)
                             mu = a.integ[slot];
                             const double s0 = sc / a.kr;
                             if (s > s0) {
-                                const double ms = s >= sc ? 0.0 : s0 * (sc - s) / (s * (sc - s0));
+                                const double ms =
+                                    s >= sc ? 0.0 : soft_mu_of(s, s0, sc, a.k1, a.beta);
                                 if (ms < mu) {
                                     mu = ms;
                                     a.integ[slot] = ms;

@@ -79,3 +79,43 @@ def test_history_and_damage_are_monotone():
         assert np.all(phi >= prev_phi - 1e-15) and np.all((phi >= 0) & (phi <= 1))
         prev_k, prev_phi = soft.kappa.copy(), phi
     assert prev_phi.max() > 0.0
+
+
+def test_trilinear_envelope_kink_and_bilinear_limit():
+    L, c, V, sc, kr, k1, beta = 1.0, 2.0, 3.0, 0.012, 6.0, 2.5, 0.25
+    s0 = sc / kr
+    s1 = k1 * s0
+    x = np.array([[0.0, 0.0, 0.0], [L, 0.0, 0.0]])
+    off, idx = np.array([0, 1, 2]), np.array([1, 0], dtype=np.int32)
+    bt = np.ones((2, 3), np.uint8)
+
+    def envelope(s):
+        if s <= s0:
+            return c * s
+        if s <= s1:
+            return c * s0 * ((1 - beta) * (s1 - s) / (s1 - s0) + beta)
+        return c * s0 * beta * (sc - s) / (sc - s1)
+
+    m = oracle.Model(x, np.array([V, V]), off, idx, c=c, sc=sc, bc_type=bt, dt=1.0,
+                     density=1.0, kr=kr, trilinear=(k1, beta))
+    mu = m.fresh_bonds()
+    v = np.zeros((2, 3))
+    kmax = 0.0
+    path = list(np.linspace(0, 0.0095, 40)) + [0.003, 0.0, 0.011]
+    for n, s in enumerate(path):
+        u = np.zeros((2, 3)); u[1, 0] = s * L
+        _, _, F = m.step(n, u, v, mu, want_force=True)
+        kmax = max(kmax, s)
+        expect = envelope(s) * V if s >= kmax else c * s * envelope(kmax) / (c * kmax) * V
+        assert F[0, 0] == pytest.approx(expect, rel=1e-10, abs=1e-14)
+    # continuity at the kink and the bilinear law at k1 = 1, beta = 1
+    assert envelope(s1 * (1 - 1e-12)) == pytest.approx(envelope(s1 * (1 + 1e-12)), rel=1e-9)
+    a = oracle.Model(x, np.array([V, V]), off, idx, c=c, sc=sc, bc_type=bt, dt=1.0,
+                     density=1.0, kr=kr, trilinear=(1.0, 1.0))
+    b = oracle.Model(x, np.array([V, V]), off, idx, c=c, sc=sc, bc_type=bt, dt=1.0,
+                     density=1.0, kr=kr)
+    for n, s in enumerate((0.001, 0.004, 0.008, 0.006)):
+        u = np.zeros((2, 3)); u[1, 0] = s * L
+        _, _, Fa = a.step(n, u, v, a.fresh_bonds(), want_force=True)
+        _, _, Fb = b.step(n, u, v, b.fresh_bonds(), want_force=True)
+        assert np.array_equal(Fa, Fb)

@@ -58,6 +58,7 @@ class Workload:
     ramp_steps: int = 0       # 0: displacement scale rate*k; T: smooth start over T steps
     kr: float = 0.0           # > 1: bilinear softening with s_0 = s_c / kr
     state_based: object = None  # (K, G): ordinary state-based linear solid instead of PMB
+    trilinear: object = None    # (s_1 / s_0, kink force / peak force) with kr: trilinear law
 
     @property
     def n(self) -> int:
