@@ -401,6 +401,13 @@ def run_ours(args):
         oracle.build()
         cb = oracle_sample(w, oracle.micromodulus(w.bulk_modulus, w.horizon), budget_s=15.0)
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        # the same oracle on one host thread (a smaller sample of the same workload)
+        oracle.set_threads(1)
+        c1 = oracle_sample(w, oracle.micromodulus(w.bulk_modulus, w.horizon), budget_s=5.0)
+        oracle.set_threads(os.cpu_count() or 1)
+        cpu["single_thread"] = {"value": c1["value"], "unit": c1["unit"], "cores": 1,
+                                "sample": c1["sample"].replace(f"on {c1['cores']} host threads",
+                                                               "on 1 host thread")}
     line = {
         "metric": "bond updates/s", "value": value, "unit": "bond updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,

@@ -130,6 +130,8 @@ def lib():
         L.or_energy_density.argtypes = [ctypes.POINTER(_Model), P, P, P]
         L.or_osb_weighted_volume.restype = None
         L.or_osb_weighted_volume.argtypes = [ctypes.POINTER(_Model), P]
+        L.or_set_threads.restype = None
+        L.or_set_threads.argtypes = [ctypes.c_int]
         L.or_scale.restype = ctypes.c_double
         L.or_scale.argtypes = [ctypes.c_double, ctypes.c_int64, ctypes.c_int64]
         L.or_run_vv.restype = None
@@ -153,6 +155,11 @@ def _c64(a):
 def scale(rate: float, ramp_steps: int, k: int) -> float:
     """Displacement scale after step k (linear, or the smooth start; see oracle.c)."""
     return lib().or_scale(rate, int(ramp_steps), int(k))
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads used by the oracle's loops (for CPU-baseline timing)."""
+    lib().or_set_threads(int(n))
 
 
 def micromodulus(K: float, delta: float) -> float:

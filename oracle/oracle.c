@@ -36,6 +36,19 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Number of OpenMP threads of the oracle's loops (CPU-baseline timing). */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+void or_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------ */
 /* Eq. (5): constant micromodulus of the PMB model, c = 18 K / (pi delta^4). */
 double or_micromodulus(double bulk_modulus, double delta)
