@@ -129,6 +129,8 @@ struct pd_handle {
     double* osb_theta = nullptr;  // per node dilation
     double* osb_alpha = nullptr;  // per node force-scalar coefficients (see pd_step_osb.cu)
     double* osb_beta = nullptr;
+    float *osb32_len = nullptr, *osb32_mvol = nullptr, *osb32_theta = nullptr,
+          *osb32_alpha = nullptr, *osb32_beta = nullptr;  // FP32 state-based arrays
     void* wsum_inv = nullptr;
     void* damage = nullptr;
     int* err = nullptr;
@@ -202,7 +204,7 @@ StepArgsF32 args_f32(pd_handle* h, int k)
     a.lo32 = h->lo32;
     a.w = h->w32;
     a.uniform_w = h->uniform_vol ? 1 : 0;
-    a.w_const = (float)((h->per_bond_c ? 1.0 : h->c) * h->vol0);
+    a.w_const = (float)(((h->per_bond_c || h->model == 1) ? 1.0 : h->c) * h->vol0);
     a.v = (float*)h->v;
     a.nbr = h->nbr;
     a.bits = h->bits;
@@ -320,8 +322,25 @@ OsbArgs osb_args(pd_handle* h)
     return o;
 }
 
+OsbArgs32 osb32_args(pd_handle* h)
+{
+    OsbArgs32 o{};
+    o.len = h->osb32_len;
+    o.mvol = h->osb32_mvol;
+    o.theta = h->osb32_theta;
+    o.alpha = h->osb32_alpha;
+    o.beta = h->osb32_beta;
+    o.K = h->osb_K;
+    o.G = h->osb_G;
+    o.delta = h->delta;
+    return o;
+}
+
 cudaError_t launch_one(pd_handle* h, int k)
 {
+    if (h->model == 1 && h->precision == 32)
+        return launch_osb32_step(args_f32(h, k), osb32_args(h), h->sc_mode, h->grid, h->block,
+                                 h->stream);
     if (h->model == 1)
         return launch_osb_step(args_f64(h, k), osb_args(h), h->grid, h->block, h->stream);
     if (h->precision == 32)
@@ -350,7 +369,8 @@ pd_status choose_grid(pd_handle* h, int blocks_per_sm)
 
 pd_status upload_weights(pd_handle* h)
 {
-    const double wscale = h->per_bond_c ? 1.0 : h->c;
+    // node weights: c V (bond-based), V (per-bond stiffness, state-based)
+    const double wscale = (h->per_bond_c || h->model == 1) ? 1.0 : h->c;
     void* w0 = h->precision == 32 ? (void*)h->w32 : (void*)h->rec[0];
     void* w1 = h->precision == 32 ? nullptr : (void*)h->rec[1];
     PD_CUDA(launch_set_weights(h->precision, w0, w1, h->vol, h->nbr, h->bits0, h->sw, h->n, h->Q,
@@ -602,14 +622,21 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
         ALLOC(h->ilen, double, nbr.size());
     }
     if (h->model == 1) {
-        if (f32) return fail(PD_ERR_ARG, "the state-based model is FP64 only");
         if (h->integrator != PD_INTEGRATOR_EC)
             return fail(PD_ERR_ARG, "the state-based model uses the Euler-Cromer integrator");
-        ALLOC(h->osb_len, double, nbr.size());
-        ALLOC(h->osb_mvol, double, np);
-        ALLOC(h->osb_theta, double, np);
-        ALLOC(h->osb_alpha, double, np);
-        ALLOC(h->osb_beta, double, np);
+        if (f32) {
+            ALLOC(h->osb32_len, float, nbr.size());
+            ALLOC(h->osb32_mvol, float, np);
+            ALLOC(h->osb32_theta, float, np);
+            ALLOC(h->osb32_alpha, float, np);
+            ALLOC(h->osb32_beta, float, np);
+        } else {
+            ALLOC(h->osb_len, double, nbr.size());
+            ALLOC(h->osb_mvol, double, np);
+            ALLOC(h->osb_theta, double, np);
+            ALLOC(h->osb_alpha, double, np);
+            ALLOC(h->osb_beta, double, np);
+        }
     }
     if (h->kr >= 1.0) {  // bilinear softening: every bond starts intact, mu = 1
         if (f32)
@@ -723,11 +750,15 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
         e = launch_inv_len(h->x64, h->nbr, h->sw, n, h->Q, h->ilen, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "bond lengths");
     }
-    if (h->model == 1) {
+    if (h->model == 1 && !f32) {
         e = launch_osb_setup(args_f64(h, 0), osb_args(h), h->x64, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "state-based set-up");
     }
     if ((st = upload_weights(h)) != PD_OK) return st;
+    if (h->model == 1 && f32) {  // needs the node weights (volumes)
+        e = launch_osb32_setup(args_f32(h, 0), osb32_args(h), h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "state-based set-up");
+    }
     h->blocks_per_sm = cfg->blocks_per_sm;
     if ((st = choose_grid(h, h->blocks_per_sm)) != PD_OK) return st;
     e = cudaStreamSynchronize(h->stream);

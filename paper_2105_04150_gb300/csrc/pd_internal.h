@@ -146,6 +146,17 @@ struct OsbArgs {
     double K, G;               // bulk and shear modulus
 };
 
+// Ordinary state-based arrays of FP32 handles (lengths in horizon units;
+// alpha, beta multiplied by delta, see pd_step_f32.cu)
+struct OsbArgs32 {
+    float* len;
+    float* mvol;
+    float* theta;
+    float* alpha;
+    float* beta;
+    double K, G, delta;
+};
+
 // Arguments of one reverse step of the FP64 adjoint (pd_adjoint.cu); node arrays
 // in library order, n_pad entries.
 struct AdjArgs {
@@ -241,6 +252,9 @@ cudaError_t launch_osb_setup(const StepArgsF64& a, const OsbArgs& o, const doubl
                              cudaStream_t s);
 cudaError_t launch_osb_step(const StepArgsF64& a, const OsbArgs& o, int grid, int block,
                             cudaStream_t s);
+cudaError_t launch_osb32_setup(const StepArgsF32& a, const OsbArgs32& o, cudaStream_t s);
+cudaError_t launch_osb32_step(const StepArgsF32& a, const OsbArgs32& o, int sc_mode, int grid,
+                              int block, cudaStream_t s);
 // per slot 1 / |x_j - x_i| from the FP64 reference positions (0 for unused slots)
 cudaError_t launch_inv_len(const double* x64, const int32_t* nbr, const int32_t* sw, int64_t n,
                            int Q, double* ilen, cudaStream_t s);
