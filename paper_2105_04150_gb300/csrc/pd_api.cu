@@ -655,7 +655,7 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
     ALLOC(h->gid, int32_t, np);
     ALLOC(h->x64, double, 3 * np);
     ALLOC(h->vol, double, np);
-    ALLOC(h->err, int, 1);
+    ALLOC(h->err, int, 2);  // [0] step kernels' flags, [1] input checks
     ALLOC(h->step_ctr, int64_t, 2);  // [0] step counter, [1] step of the last set state
     if (h->integrator == PD_INTEGRATOR_VV) {
         if (f32)
@@ -663,7 +663,7 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
         else
             ALLOC(h->vpeek, double, 3 * np);
     }
-    ALLOC(h->staging, double, 3 * n);
+    ALLOC(h->staging, double, 6 * n);  // u and v halves for host transfers
     if (!d.inst.empty()) {
         ALLOC(h->inst, int32_t, np);
         ALLOC(h->hid, int32_t, np);
@@ -1083,36 +1083,45 @@ pd_status pd_set_state(pd_handle* h, const double* u, const double* v, int64_t s
 {
     if (!h) return fail(PD_ERR_ARG, "NULL handle");
     PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    // stage host inputs (u and v halves of the staging area), check their values
+    // on the device (device inputs are the caller's responsibility, as before),
+    // and only then change the state
+    const double* ins[2] = {u, v};
+    const double* src[2] = {nullptr, nullptr};
+    int* chk = h->err + 1;
+    PD_CUDA(cudaMemsetAsync(chk, 0, sizeof(int), h->stream), "clear input flag");
+    for (int w = 0; w < 2; ++w) {
+        if (!ins[w]) continue;
+        src[w] = ins[w];
+        if (!is_device_ptr(ins[w])) {
+            double* dst = h->staging + 3 * h->n * w;
+            PD_CUDA(cudaMemcpyAsync(dst, ins[w], 24 * h->n, cudaMemcpyHostToDevice, h->stream),
+                    "copy state to device");
+            src[w] = dst;
+            PD_CUDA(launch_check_finite(src[w], 3 * h->n, chk, h->stream), "check state");
+        }
+    }
+    int bad = 0;
+    PD_CUDA(cudaMemcpyAsync(&bad, chk, sizeof(int), cudaMemcpyDeviceToHost, h->stream),
+            "read input flag");
+    PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
+    if (bad) return fail(PD_ERR_ARG, "non-finite state");
     if (step >= 0 && step != h->step) {
         h->step = step;
         PD_CUDA(cudaMemcpyAsync(h->step_ctr, &h->step, sizeof(int64_t), cudaMemcpyHostToDevice,
                                 h->stream),
                 "set step");
-        PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
     }
     const int cur = (int)(h->step & 1);
-    const double* ins[2] = {u, v};
-    for (int w = 0; w < 2; ++w) {
-        const double* in = ins[w];
-        if (!in) continue;
-        const double* src = in;
-        if (!is_device_ptr(in)) {
-            if (!finite_all(in, 3 * h->n)) return fail(PD_ERR_ARG, "non-finite state");
-            PD_CUDA(cudaMemcpyAsync(h->staging, in, 24 * h->n, cudaMemcpyHostToDevice, h->stream),
-                    "copy state to device");
-            src = h->staging;
-        }
-        const double* ui = w == 0 ? src : nullptr;
-        const double* vi = w == 1 ? src : nullptr;
+    if (src[0] || src[1]) {
         if (h->precision == 32)
-            PD_CUDA(launch_set_state_f32(ui, vi, h->gid, h->n, 1.0 / h->delta, h->rec32[cur],
-                                         h->lo32, (float*)h->v, h->stream),
+            PD_CUDA(launch_set_state_f32(src[0], src[1], h->gid, h->n, 1.0 / h->delta,
+                                         h->rec32[cur], h->lo32, (float*)h->v, h->stream),
                     "set state");
         else
-            PD_CUDA(launch_set_state_f64(ui, vi, h->gid, h->n, h->rec[cur], (double*)h->v,
-                                         h->stream),
+            PD_CUDA(launch_set_state_f64(src[0], src[1], h->gid, h->n, h->rec[cur],
+                                         (double*)h->v, h->stream),
                     "set state");
-        if (src == h->staging) PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
     }
     // the velocity-Verlet history starts again at this step (a^n formed afresh)
     PD_CUDA(cudaMemcpyAsync(h->step_ctr + 1, &h->step, sizeof(int64_t), cudaMemcpyHostToDevice,

@@ -302,10 +302,24 @@ cudaError_t launch_set_weights(int precision, void* wrec0, void* wrec1, const do
     return cudaGetLastError();
 }
 
+__global__ void k_check_finite(const double* __restrict__ x, int64_t m, int* __restrict__ flag)
+{
+    bool bad = false;
+    GRID_STRIDE(e, m) bad = bad || !isfinite(x[e]);
+    if (bad) atomicOr(flag, 1);
+}
+
 template <typename T>
 __global__ void k_fill(T* __restrict__ dst, int64_t n, T v)
 {
     GRID_STRIDE(e, n) dst[e] = v;
+}
+
+cudaError_t launch_check_finite(const double* x, int64_t m, int* flag, cudaStream_t s)
+{
+    if (m <= 0) return cudaSuccess;
+    k_check_finite<<<grid_for(m, 256), 256, 0, s>>>(x, m, flag);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fill(int precision, void* dst, int64_t n, double v, cudaStream_t s)

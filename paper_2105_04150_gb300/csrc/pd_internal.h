@@ -239,6 +239,8 @@ cudaError_t launch_damage(int precision, const void* wrec, const int32_t* nbr,
                           const uint32_t* bits, const int32_t* sw, const void* wsum_inv,
                           const int32_t* gid, int64_t n, int Q, const void* integ,
                           double* phi_out, cudaStream_t s);
+// flag |= 1 if any of x[0..m) is not finite
+cudaError_t launch_check_finite(const double* x, int64_t m, int* flag, cudaStream_t s);
 // fill n values of `precision` (32 or 64) with v
 cudaError_t launch_fill(int precision, void* dst, int64_t n, double v, cudaStream_t s);
 // damage written by the last step -> caller order
