@@ -1123,11 +1123,12 @@ pd_status pd_set_state(pd_handle* h, const double* u, const double* v, int64_t s
                                          (double*)h->v, h->stream),
                     "set state");
     }
-    // the velocity-Verlet history starts again at this step (a^n formed afresh)
+    // the velocity-Verlet history starts again at this step (a^n formed afresh);
+    // the host inputs were consumed before the check above, so nothing more
+    // needs to finish before returning
     PD_CUDA(cudaMemcpyAsync(h->step_ctr + 1, &h->step, sizeof(int64_t), cudaMemcpyHostToDevice,
                             h->stream),
             "set history start");
-    PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
     PD_CUDA(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream), "clear error flag");
     h->damage_fresh = false;
     h->peek_step = -1;
