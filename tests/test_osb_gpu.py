@@ -97,3 +97,10 @@ def test_state_based_fp32_matches_oracle():
     b = m.bonds()
     m.close()
     assert (mu == 0).sum() > 0 and (b != mu).sum() <= 1e-3 * len(mu)
+
+
+def test_state_based_with_smooth_ramp_matches_oracle():
+    w = workloads.tensile_bar(steps=600)
+    w.state_based = _moduli(w.bulk_modulus, 0.3)
+    w.ramp_steps = 300
+    _compare(w, w.steps)

@@ -146,3 +146,24 @@ def test_adjoint_rejects_velocity_verlet():
         pdgb.pd_adjoint_forward(m.h, 5)
     assert e.value.name == "PD_ERR_STATE"
     m.close()
+
+
+def test_velocity_verlet_with_softening_matches_oracle():
+    # the read-only force pass also lowers integrities at u^n (idempotently)
+    w = _bar(steps=700)
+    w.kr = 3.0
+    off, idx = oracle.cut_family(w.coords, w.horizon, w.cuts_array())
+    om = oracle.Model.from_workload(w, off, idx)
+    u, v, a = np.zeros((w.n, 3)), np.zeros((w.n, 3)), np.zeros((w.n, 3))
+    mu = om.fresh_bonds()
+    margin = np.full(len(mu), np.inf)
+    om.run_vv(0, w.steps, u, v, a, mu, init=True, margin=margin)
+    m = pdgb.Model.from_workload(w, precision=F64, integrator=VV, graph_steps=10)
+    for _ in range(7):
+        m.step(100)
+        m.state()
+    ug, vg = m.state()
+    b = m.bonds()
+    m.close()
+    assert rel(ug, u) <= 1e-10 and rel(vg, v) <= 1e-9
+    assert np.all(margin[b != mu] < BAND)
