@@ -64,6 +64,17 @@ def _args(w, **over):
     (dict(graph_steps=-2), "PD_ERR_ARG"),
     (dict(block_threads=48), "PD_ERR_ARG"),
     (dict(sc_hash=(1, 2e-4, 1e-4)), "PD_ERR_ARG"),
+    # integrators, loading ramp, softening laws, state-based model
+    (dict(integrator=2), "PD_ERR_ARG"),
+    (dict(ramp_steps=-1), "PD_ERR_ARG"),
+    (dict(kr=0.5), "PD_ERR_ARG"),
+    (dict(kr=float("inf")), "PD_ERR_ARG"),
+    (dict(kr=4.0, trilinear=(5.0, 0.25)), "PD_ERR_ARG"),      # kink past s_c
+    (dict(kr=4.0, trilinear=(2.0, 1.5)), "PD_ERR_ARG"),       # kink force above the peak
+    (dict(trilinear=(2.0, 0.25)), "PD_ERR_ARG"),              # kink without softening
+    (dict(state_based=(0.0, 1e9)), "PD_ERR_ARG"),
+    (dict(state_based=(1e9, -1.0)), "PD_ERR_ARG"),
+    (dict(state_based=(1e9, 1e9), kr=2.0), "PD_ERR_ARG"),
 ])
 def test_create_rejects_bad_arguments(L, over, status):
     w = workloads.tensile_bar(6, 4, 4)
