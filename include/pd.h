@@ -179,15 +179,22 @@ pd_status pd_micromodulus(double K, double delta, double* c_out);
  *                     of node i of V_j, and v0 > 0 the family volume of a node in
  *                     the bulk (on a cubic lattice with delta = 3.01 dx that is
  *                     122 dx^3)
+ *   PD_STIFF_PARTIAL  partial volume beta_ij of the discrete equation of motion
+ *                     (Section 2.3): the fraction of node j's cell inside the
+ *                     horizon, by the linear rule (horizon + dx/2 - |xi|) / dx
+ *                     clipped to [0, 1], dx > 0 the lattice spacing; build the
+ *                     family with horizon + dx/2 to include the cells that
+ *                     straddle the horizon from outside
  * The flags combine (the factors multiply).  coords n*3, volumes n (host);
  * factor: host, one double per family entry.  Host-only work.  PD_ERR_ARG on
- * bad flags, horizon, v0 or family.
+ * bad flags, horizon, v0, dx or family.
  */
 #define PD_STIFF_CONICAL 1
 #define PD_STIFF_SURFACE 2
+#define PD_STIFF_PARTIAL 4
 pd_status pd_stiffness_factors(int64_t n, const double* coords, const double* volumes,
                                double horizon, const int64_t* fam_off, const int32_t* fam_idx,
-                               int32_t flags, double v0, double* factor);
+                               int32_t flags, double v0, double dx, double* factor);
 
 /*
  * pd_create - build a model and upload it to the GPU.

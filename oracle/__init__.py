@@ -140,6 +140,9 @@ def lib():
         L.or_stiffness_factors.restype = None
         L.or_stiffness_factors.argtypes = [P, P, ctypes.c_int64, ctypes.c_double, P, P,
                                            ctypes.c_int, ctypes.c_double, P]
+        L.or_stiffness_factors2.restype = None
+        L.or_stiffness_factors2.argtypes = [P, P, ctypes.c_int64, ctypes.c_double, P, P,
+                                            ctypes.c_int, ctypes.c_double, ctypes.c_double, P]
         _lib = L
     return _lib
 
@@ -217,12 +220,13 @@ def cut_family(coords, delta, cuts, rows=None, method="cells"):
     return cum[off], idx[keep.astype(bool)]
 
 
-CONICAL, SURFACE = 1, 2
+CONICAL, SURFACE, PARTIAL = 1, 2, 4
 
 
-def stiffness_factors(coords, volumes, delta, off, idx, flags, v0=0.0):
-    """Per family entry factors multiplying c: conical micromodulus (bit 1) and the
-    volume surface correction 2 V0 / (V_i + V_j) (bit 2); see oracle.c."""
+def stiffness_factors(coords, volumes, delta, off, idx, flags, v0=0.0, dx=0.0):
+    """Per family entry factors multiplying c: conical micromodulus (bit 1), the
+    volume surface correction 2 V0 / (V_i + V_j) (bit 2) and the linear partial
+    volume with lattice spacing dx (bit 4); see oracle.c."""
     x = _c64(coords)
     vol = _c64(volumes)
     off = np.ascontiguousarray(off, dtype=np.int64)
@@ -231,9 +235,9 @@ def stiffness_factors(coords, volumes, delta, off, idx, flags, v0=0.0):
     # rows are nodes 0..nrows-1; the volume correction needs every node as a row
     assert nrows <= x.shape[0] and (not flags & SURFACE or nrows == x.shape[0])
     out = np.zeros(max(idx.shape[0], 1))
-    lib().or_stiffness_factors(x.ctypes.data, vol.ctypes.data, nrows, delta,
-                               off.ctypes.data, idx.ctypes.data, int(flags), float(v0),
-                               out.ctypes.data)
+    lib().or_stiffness_factors2(x.ctypes.data, vol.ctypes.data, nrows, delta,
+                                off.ctypes.data, idx.ctypes.data, int(flags), float(v0),
+                                float(dx), out.ctypes.data)
     return out[: idx.shape[0]]
 
 

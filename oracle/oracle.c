@@ -680,10 +680,32 @@ void or_energy_density(const or_model* m, const double* u, const uint8_t* mu, do
  *     the family volume sum_{j in H_i} V_j of node i (family as given, i.e.
  *     after the initial notch removal) and V0 the family volume of a node in
  *     the bulk (an input).
- * With both bits the factors multiply.  All nodes are rows. */
+ *   bit 2, partial volume (Section 2.3, beta_ij of the discrete equation of
+ *     motion): the fraction of node j's cell inside the horizon, taken as the
+ *     linear rule beta = (delta + dx/2 - |xi|) / dx clipped to [0, 1], dx = dx_pv
+ *     the lattice spacing (a family built with horizon delta + dx/2 gives the
+ *     cells straddling the horizon their outer part too);
+ * With several bits the factors multiply.  All nodes are rows. */
+static double partial_volume(double L, double delta, double dx)
+{
+    double b = (delta + 0.5 * dx - L) / dx;
+    return b < 0.0 ? 0.0 : (b > 1.0 ? 1.0 : b);
+}
+
+void or_stiffness_factors2(const double* x, const double* vol, int64_t n, double delta,
+                           const int64_t* off, const int32_t* idx, int flags, double v0,
+                           double dx_pv, double* out);
+
 void or_stiffness_factors(const double* x, const double* vol, int64_t n, double delta,
                           const int64_t* off, const int32_t* idx, int flags, double v0,
                           double* out)
+{
+    or_stiffness_factors2(x, vol, n, delta, off, idx, flags, v0, 0.0, out);
+}
+
+void or_stiffness_factors2(const double* x, const double* vol, int64_t n, double delta,
+                           const int64_t* off, const int32_t* idx, int flags, double v0,
+                           double dx_pv, double* out)
 {
     double* fv = NULL;
     if (flags & 2) {
@@ -703,6 +725,7 @@ void or_stiffness_factors(const double* x, const double* vol, int64_t n, double 
                 f *= 5.0 * (1.0 - L / delta);
             }
             if (flags & 2) f *= 2.0 * v0 / (fv[i] + fv[j]);
+            if (flags & 4) f *= partial_volume(sqrt(dist2(x + 3 * i, x + 3 * j)), delta, dx_pv);
             out[k] = f;
         }
     free(fv);

@@ -26,7 +26,7 @@ __all__ = [
     "pd_get_bonds", "pd_set_bonds", "pd_damage", "pd_set_params", "pd_batch_create",
     "pd_batch_offsets", "pd_autotune", "pd_adjoint_forward", "pd_adjoint_backward",
     "pd_adjoint_backward_static", "pd_stiffness_factors", "pd_get_bond_integrity", "PD_STIFF_CONICAL",
-    "PD_STIFF_SURFACE", "PD_INTEGRATOR_EC", "PD_INTEGRATOR_VV",
+    "PD_STIFF_SURFACE", "PD_STIFF_PARTIAL", "PD_INTEGRATOR_EC", "PD_INTEGRATOR_VV",
     "instance_from_workload", "Model",
     "PD_PREC_F32", "PD_PREC_F64",
 ]
@@ -35,6 +35,7 @@ PD_PREC_F64 = 64
 PD_PREC_F32 = 32
 PD_STIFF_CONICAL = 1
 PD_STIFF_SURFACE = 2
+PD_STIFF_PARTIAL = 4
 PD_INTEGRATOR_EC = 0
 PD_INTEGRATOR_VV = 1
 _STATUS = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_CUDA", 3: "PD_ERR_OOM",
@@ -122,7 +123,7 @@ def lib():
             "pd_adjoint_forward": [P, I64, I64],
             "pd_adjoint_backward": [P, P, P, P, P, P, P],
             "pd_adjoint_backward_static": [P, P, P, P, P, P, P],
-            "pd_stiffness_factors": [I64, P, P, D, P, P, I32, D, P],
+            "pd_stiffness_factors": [I64, P, P, D, P, P, I32, D, D, P],
             "pd_get_bond_integrity": [P, P],
         }
         for name, args in sig.items():
@@ -409,9 +410,10 @@ def pd_adjoint_backward_static(h: int, dLdu, dLdv=None, want_c: bool = True):
     return (None if gc is None else gc[:nb]), gl.value, gu, gv
 
 
-def pd_stiffness_factors(coords, volumes, horizon, off, idx, flags, v0=0.0):
+def pd_stiffness_factors(coords, volumes, horizon, off, idx, flags, v0=0.0, dx=0.0):
     """Per directed bond stiffness factors (canonical order) for the conical
-    micromodulus and/or the volume surface correction; c_bond = c * factor."""
+    micromodulus, the volume surface correction and/or the partial volume;
+    c_bond = c * factor."""
     x = np.ascontiguousarray(coords, dtype=np.float64)
     vol = np.ascontiguousarray(volumes, dtype=np.float64)
     off = np.ascontiguousarray(off, dtype=np.int64)
@@ -420,7 +422,7 @@ def pd_stiffness_factors(coords, volumes, horizon, off, idx, flags, v0=0.0):
     out = np.zeros(max(idx.shape[0], 1))
     _check(lib().pd_stiffness_factors(n, x.ctypes.data, vol.ctypes.data, float(horizon),
                                       off.ctypes.data, idx.ctypes.data, int(flags), float(v0),
-                                      out.ctypes.data))
+                                      float(dx), out.ctypes.data))
     return out[: idx.shape[0]]
 
 

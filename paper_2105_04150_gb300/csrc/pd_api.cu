@@ -444,19 +444,22 @@ pd_status pd_micromodulus(double K, double delta, double* c_out)
 
 pd_status pd_stiffness_factors(int64_t n, const double* coords, const double* volumes,
                                double horizon, const int64_t* fam_off, const int32_t* fam_idx,
-                               int32_t flags, double v0, double* factor)
+                               int32_t flags, double v0, double dx, double* factor)
 {
     if (n < 1 || !coords || !volumes || !fam_off || !fam_idx || !factor)
         return fail(PD_ERR_ARG, "need n >= 1 and non-NULL coords, volumes, family and factor");
-    if (flags < 1 || flags > (PD_STIFF_CONICAL | PD_STIFF_SURFACE))
-        return fail(PD_ERR_ARG, "flags must combine PD_STIFF_CONICAL and PD_STIFF_SURFACE");
+    if (flags < 1 || flags > (PD_STIFF_CONICAL | PD_STIFF_SURFACE | PD_STIFF_PARTIAL))
+        return fail(PD_ERR_ARG,
+                    "flags must combine PD_STIFF_CONICAL, PD_STIFF_SURFACE and PD_STIFF_PARTIAL");
+    if ((flags & PD_STIFF_PARTIAL) && !(dx > 0.0 && std::isfinite(dx)))
+        return fail(PD_ERR_ARG, "the partial volume needs a finite lattice spacing dx > 0");
     if (!(horizon > 0.0) || !std::isfinite(horizon))
         return fail(PD_ERR_ARG, "horizon must be finite and > 0");
     if ((flags & PD_STIFF_SURFACE) && !(v0 > 0.0 && std::isfinite(v0)))
         return fail(PD_ERR_ARG, "the surface correction needs a finite v0 > 0");
     const std::string msg = check_family(n, fam_off, fam_idx);
     if (!msg.empty()) return fail(PD_ERR_ARG, "%s", msg.c_str());
-    stiffness_factors(n, coords, volumes, horizon, fam_off, fam_idx, flags, v0, factor);
+    stiffness_factors(n, coords, volumes, horizon, fam_off, fam_idx, flags, v0, dx, factor);
     return PD_OK;
 }
 

@@ -305,7 +305,7 @@ std::string bc_classes(int64_t n, const uint8_t* type, const double* disp, const
 }
 
 void stiffness_factors(int64_t n, const double* x, const double* vol, double delta,
-                       const int64_t* off, const int32_t* idx, int flags, double v0,
+                       const int64_t* off, const int32_t* idx, int flags, double v0, double dx,
                        double* factor)
 {
     // family volumes first (the correction needs both ends'), then one pass
@@ -326,12 +326,12 @@ void stiffness_factors(int64_t n, const double* x, const double* vol, double del
         for (int64_t k = off[i]; k < off[i + 1]; ++k) {
             const int64_t j = idx[k];
             double f = 1.0;
-            if (flags & 1) {
-                const double d0 = x[3 * j] - x[3 * i], d1 = x[3 * j + 1] - x[3 * i + 1],
-                             d2 = x[3 * j + 2] - x[3 * i + 2];
-                f = 5.0 * (1.0 - std::sqrt(d0 * d0 + d1 * d1 + d2 * d2) * inv_delta);
-            }
+            const double d0 = x[3 * j] - x[3 * i], d1 = x[3 * j + 1] - x[3 * i + 1],
+                         d2 = x[3 * j + 2] - x[3 * i + 2];
+            const double len = std::sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+            if (flags & 1) f = 5.0 * (1.0 - len * inv_delta);
             if (flags & 2) f *= (2.0 * v0) / (fam[(size_t)i] + fam[(size_t)j]);
+            if (flags & 4) f *= std::min(1.0, std::max(0.0, (delta + 0.5 * dx - len) / dx));
             factor[k] = f;
         }
     }

@@ -39,8 +39,9 @@ std::string bc_classes(int64_t n, const uint8_t* type, const double* disp, const
 // Per directed bond (canonical order) factors multiplying the constant c:
 // flags bit 0 conical micromodulus, factor 5 (1 - |xi|/delta); bit 1 volume
 // surface correction 2 v0 / (V_i + V_j) with V_i the family volume of node i.
+// bit 2: partial volume, the linear rule (delta + dx/2 - |xi|) / dx in [0, 1]
 void stiffness_factors(int64_t n, const double* x, const double* vol, double delta,
-                       const int64_t* off, const int32_t* idx, int flags, double v0,
+                       const int64_t* off, const int32_t* idx, int flags, double v0, double dx,
                        double* factor);
 double stable_dt(int64_t n, const double* x, const double* vol, const std::vector<int64_t>& off,
                  const std::vector<int32_t>& idx, double c, double rho);

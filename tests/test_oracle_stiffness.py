@@ -122,3 +122,25 @@ def test_factors_multiply():
     both = oracle.stiffness_factors(x, np.ones(n), 3.01, off, idx, oracle.CONICAL | oracle.SURFACE,
                                     v0=122.0)
     assert np.allclose(both, a * b, rtol=1e-15, atol=0)
+
+
+def test_partial_volume_rule_values_and_quadrature():
+    # a bond of length L gets (delta + dx/2 - L) / dx clipped to [0, 1]
+    x = np.array([[0.0, 0.0, 0.0], [2.5, 0.0, 0.0], [0.0, 3.1, 0.0], [0.0, 0.0, 3.4]])
+    off = np.array([0, 3, 4, 5, 6])
+    idx = np.array([1, 2, 3, 0, 0, 0], dtype=np.int32)
+    f = oracle.stiffness_factors(x, np.ones(4), 3.01, off, idx, oracle.PARTIAL, dx=1.0)
+    assert np.allclose(f, [1.0, 0.41, 0.11, 1.0, 0.41, 0.11], atol=1e-12)
+    # on a lattice, the partial volumes of the horizon (family built with
+    # delta + dx/2) approximate the sphere volume 4/3 pi delta^3 better than counts
+    r = 3.01
+    m = 11
+    xl = workloads.lattice(m, m, m, 1.0)
+    c = (m // 2 * m + m // 2) * m + m // 2
+    off2, idx2 = oracle.family(xl, r + 0.5, rows=np.array([c]))
+    x1 = np.vstack([xl[c:c + 1], xl])
+    pv = oracle.stiffness_factors(x1, np.ones(x1.shape[0]), r, np.array([0, len(idx2)]),
+                                  idx2 + 1, oracle.PARTIAL, dx=1.0)
+    sphere = 4.0 / 3.0 * np.pi * r ** 3
+    full = len(_offsets(r))
+    assert abs(pv.sum() - sphere) < abs(full - sphere)

@@ -8,7 +8,7 @@ import oracle
 import paper_2105_04150_gb300 as pdgb
 import workloads
 
-CON, SUR = pdgb.PD_STIFF_CONICAL, pdgb.PD_STIFF_SURFACE
+CON, SUR, PAR = pdgb.PD_STIFF_CONICAL, pdgb.PD_STIFF_SURFACE, pdgb.PD_STIFF_PARTIAL
 
 
 @pytest.fixture(scope="module")
@@ -30,19 +30,19 @@ def _jittered():
     return x, vol, off, idx
 
 
-@pytest.mark.parametrize("flags", [CON, SUR, CON | SUR])
+@pytest.mark.parametrize("flags", [CON, SUR, CON | SUR, PAR, CON | SUR | PAR])
 def test_library_factors_equal_oracle(libs, flags):
     x, vol, off, idx = _jittered()
     v0 = 122 * 1e-9
-    got = pdgb.pd_stiffness_factors(x, vol, 3.01e-3, off, idx, flags, v0)
-    ref = oracle.stiffness_factors(x, vol, 3.01e-3, off, idx, flags, v0)
+    got = pdgb.pd_stiffness_factors(x, vol, 3.01e-3, off, idx, flags, v0, dx=1e-3)
+    ref = oracle.stiffness_factors(x, vol, 3.01e-3, off, idx, flags, v0, dx=1e-3)
     assert got.shape == ref.shape
     assert np.abs(got - ref).max() <= 1e-14 * np.abs(ref).max()
 
 
 def test_library_factors_reject_bad_arguments(libs):
     x, vol, off, idx = _jittered()
-    for flags, v0 in ((0, 1.0), (4, 1.0), (SUR, 0.0), (SUR, float("nan"))):
+    for flags, v0 in ((0, 1.0), (8, 1.0), (SUR, 0.0), (SUR, float("nan")), (PAR, 1.0)):
         with pytest.raises(pdgb.PdError) as e:
             pdgb.pd_stiffness_factors(x, vol, 3.01e-3, off, idx, flags, v0)
         assert e.value.name == "PD_ERR_ARG"
@@ -61,8 +61,8 @@ def test_corrected_stiffness_step_matches_oracle(libs, precision):
     w = workloads.tensile_bar(24, 8, 8, steps=1000)
     c = oracle.micromodulus(w.bulk_modulus, w.horizon)
     off, idx = oracle.cut_family(w.coords, w.horizon, w.cuts_array())
-    fac = pdgb.pd_stiffness_factors(w.coords, w.volumes, w.horizon, off, idx, CON | SUR,
-                                    122 * w.dx ** 3)
+    fac = pdgb.pd_stiffness_factors(w.coords, w.volumes, w.horizon, off, idx, CON | SUR | PAR,
+                                    122 * w.dx ** 3, dx=w.dx)
     m = pdgb.Model.from_workload(w, precision=precision, c=c)
     m.set_params(c, w.sc, w.load, w.disp_rate, c * fac)
     m.step(w.steps)
