@@ -396,3 +396,62 @@ def test_full_size_notched_beam_sampled_one_step(prec):
         assert rel(u_g[rows], uo) <= 1e-6
         assert rel(du_g, du_o) <= 1e-3
         assert diff.mean() < 1e-3
+
+
+def test_full_size_plate_sampled_one_step():
+    """16,000,000-node plate (1.89e9 directed bonds) in the benchmark's launch
+    configuration, FP32: one step from a common state in which part of the
+    bonds reach s_c, compared on 2000 sampled nodes computed one by one by the
+    oracle (the step's break decisions are part of what is compared)."""
+    w = workloads.plate()
+    c = oracle.micromodulus(w.bulk_modulus, w.horizon)
+    m = pdgb.Model.from_workload(w, precision=F32, c=c, graph_steps=20)
+    assert m.info()["n"] == 16_000_000
+    rng = np.random.default_rng(11)
+    u0 = 2.0e-4 * (w.coords - w.coords.mean(axis=0)) * np.array([0.2, 1.0, 0.3])
+    u0 += rng.normal(0.0, 2e-8, size=u0.shape)
+    v0 = rng.normal(0.0, 1e-3, size=u0.shape)
+    m.set_state(u0, v0, step=40)
+    m.step(1)
+    u_g, _ = m.state()
+    m.close()
+    rows = np.sort(rng.choice(w.n, 2000, replace=False))
+    off_r, idx_r = oracle.cut_family(w.coords, w.horizon, w.cuts_array(), rows=rows)
+    om = oracle.Model.from_workload(w, off_r, idx_r, c=c, rows=rows)
+    mu = om.fresh_bonds()
+    uo, _ = om.step(40, u0, v0, mu)
+    assert (mu == 0).any() and mu.any()
+    assert rel(u_g[rows], uo) <= 1e-6
+    assert rel(u_g[rows] - u0[rows], uo - u0[rows]) <= 1e-3
+
+
+def test_full_size_batch_sampled_one_step():
+    """The 256-instance batch (4.5M nodes) with its autotuned launch shape, FP32:
+    one step from a common state, sampled nodes of eight instances compared with
+    each instance's own oracle model."""
+    ws = workloads.batch_instances()
+    bm = pdgb.Model.batch(ws, precision=F32, graph_steps=20)
+    bm.autotune(5)
+    offs = bm.offsets()
+    rng = np.random.default_rng(12)
+    n = int(offs[-1])
+    u0 = np.concatenate([1.5e-4 * (w.coords - w.coords.mean(axis=0)) for w in ws])
+    u0 += rng.normal(0.0, 1e-9, size=u0.shape)
+    v0 = rng.normal(0.0, 1e-4, size=(n, 3))
+    bm.set_state(u0, v0, step=10)
+    bm.step(1)
+    u_g, _ = bm.state()
+    bm.close()
+    broke = 0
+    for k in rng.choice(len(ws), 8, replace=False):
+        w = ws[k]
+        a = int(offs[k])
+        rows = np.sort(rng.choice(w.n, min(w.n, 300), replace=False))
+        off_r, idx_r = oracle.cut_family(w.coords, w.horizon, w.cuts_array(), rows=rows)
+        om = oracle.Model.from_workload(w, off_r, idx_r, rows=rows)
+        mu = om.fresh_bonds()
+        uo, _ = om.step(10, u0[a:a + w.n], v0[a:a + w.n], mu)
+        broke += int((mu == 0).sum())
+        assert rel(u_g[a + rows], uo) <= 1e-6
+        assert rel(u_g[a + rows] - u0[a + rows], uo - u0[a + rows]) <= 1e-3
+    assert broke > 0
