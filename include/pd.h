@@ -51,11 +51,22 @@ typedef enum {
 #define PD_PREC_F64 64   /* FP64 throughout */
 #define PD_PREC_F32 32   /* FP32 bond arithmetic; FP64 displacement accumulation and
                             an FP64 re-test of bonds whose stretch is near s_c */
+#define PD_PREC_DW 48    /* FP64-grade step from FP32 double-word arithmetic: node
+                            state (u, v) and integration in FP64 exactly as with
+                            PD_PREC_F64; every bond quantity (xi, eta, y, the
+                            stretch of Eq. 4, |y|, the force of Eq. 5) carried as an
+                            unevaluated sum of two FP32 numbers (~48-bit significand,
+                            bond-force relative error ~1e-13), and the break test
+                            decided against the FP64 s_c.  Single models with the
+                            Euler-Cromer integrator and the PMB law only: no batches,
+                            per-bond stiffness, softening, state-based model or
+                            adjoint (those calls return PD_ERR_ARG / PD_ERR_STATE).
+                            pd_get_info reports 48. */
 #define PD_MAX_FAMILY 1024
 #define PD_MAX_BC_CLASSES 256
 
 typedef struct {
-    int32_t precision;    /* PD_PREC_F64 or PD_PREC_F32 */
+    int32_t precision;    /* PD_PREC_F64, PD_PREC_F32 or PD_PREC_DW */
     int32_t graph_steps;  /* steps per captured CUDA graph; 0 = direct launches */
     double dt;            /* time step, s */
     double damping;       /* eta of Eq. 11, kg m^-3 s^-1 */

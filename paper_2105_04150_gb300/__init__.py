@@ -28,11 +28,12 @@ __all__ = [
     "pd_adjoint_backward_static", "pd_stiffness_factors", "pd_get_bond_integrity", "PD_STIFF_CONICAL",
     "PD_STIFF_SURFACE", "PD_STIFF_PARTIAL", "PD_INTEGRATOR_EC", "PD_INTEGRATOR_VV",
     "instance_from_workload", "Model",
-    "PD_PREC_F32", "PD_PREC_F64",
+    "PD_PREC_F32", "PD_PREC_F64", "PD_PREC_DW",
 ]
 
 PD_PREC_F64 = 64
 PD_PREC_F32 = 32
+PD_PREC_DW = 48  # FP64-grade bonds in double-word FP32 arithmetic, FP64 node state
 PD_STIFF_CONICAL = 1
 PD_STIFF_SURFACE = 2
 PD_STIFF_PARTIAL = 4

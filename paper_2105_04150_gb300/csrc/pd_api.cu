@@ -115,6 +115,11 @@ struct pd_handle {
     double* x64 = nullptr;
     double* vol = nullptr;
     double* ilen = nullptr;  // FP64: per slot 1 / |xi|
+    // PD_PREC_DW: FP64 layout and integration, bonds in double-word FP32 arithmetic
+    bool dw = false;
+    float4* recdw[2] = {nullptr, nullptr};  // double-word copies of the records
+    float2* lendw = nullptr;                // per slot |xi| / delta
+    double dw_origin[3] = {0.0, 0.0, 0.0};  // origin of the double-word positions
     int integrator = PD_INTEGRATOR_EC;
     int64_t ramp_steps = 0;
     void* vpeek = nullptr;  // velocity-Verlet: full-step velocity for pd_get_state
@@ -336,8 +341,45 @@ OsbArgs32 osb32_args(pd_handle* h)
     return o;
 }
 
+DwArgs dw_args(pd_handle* h)
+{
+    DwArgs d{};
+    d.rec[0] = h->recdw[0];
+    d.rec[1] = h->recdw[1];
+    d.len = h->lendw;
+    d.inv_delta = 1.0 / h->delta;
+    d.w_const = h->c * h->vol0;
+    d.dt_rho = h->dt / h->rho;
+    // the leading word of a double-word stretch is within 2^-23 of it: below
+    // this band the break test cannot be near any s_c of the model
+    d.fast_lo = (float)((1.0 - 0x1.0p-20) * (h->sc_mode == 0 ? h->sc : h->sc_lo));
+    d.uniform_w = h->uniform_vol ? 1 : 0;
+    return d;
+}
+
+// double-word records of both buffers from the FP64 records
+pd_status dw_publish(pd_handle* h)
+{
+    if (!h->dw) return PD_OK;
+    for (int b = 0; b < 2; ++b)
+        PD_CUDA(launch_dw_publish(h->rec[b], h->recdw[b], h->n_pad, h->dw_origin, 1.0 / h->delta,
+                                  h->stream),
+                "double-word records");
+    return PD_OK;
+}
+
+const void* step_kernel_fn(pd_handle* h)
+{
+    if (h->precision == 32) return f32_kernel(h);
+    if (h->dw) return step_dw_kernel(h->sc_mode, h->uniform_vol);
+    return step_f64_kernel(h->sc_mode);
+}
+
 cudaError_t launch_one(pd_handle* h, int k)
 {
+    if (h->dw)
+        return launch_step_dw(args_f64(h, k), dw_args(h), h->sc_mode, h->grid, h->block,
+                              h->stream);
     if (h->model == 1 && h->precision == 32)
         return launch_osb32_step(args_f32(h, k), osb32_args(h), h->sc_mode, h->grid, h->block,
                                  h->stream);
@@ -352,8 +394,7 @@ pd_status choose_grid(pd_handle* h, int blocks_per_sm)
 {
     int sms = 0;
     PD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "sm count");
-    const void* fn = h->precision == 32 ? f32_kernel(h)
-                                        : step_f64_kernel(h->sc_mode);
+    const void* fn = step_kernel_fn(h);
     // no shared memory is used: give the unified L1/shared array to L1
     PD_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 0),
             "carveout");
@@ -376,7 +417,7 @@ pd_status upload_weights(pd_handle* h)
     PD_CUDA(launch_set_weights(h->precision, w0, w1, h->vol, h->nbr, h->bits0, h->sw, h->n, h->Q,
                                wscale, h->wsum_inv, h->stream),
             "set weights");
-    return PD_OK;
+    return dw_publish(h);
 }
 
 pd_status check_dev_err(pd_handle* h)
@@ -469,8 +510,11 @@ namespace {
 
 pd_status check_cfg(const pd_config* cfg)
 {
-    if (cfg->precision != PD_PREC_F32 && cfg->precision != PD_PREC_F64)
-        return fail(PD_ERR_ARG, "precision must be 32 or 64");
+    if (cfg->precision != PD_PREC_F32 && cfg->precision != PD_PREC_F64 &&
+        cfg->precision != PD_PREC_DW)
+        return fail(PD_ERR_ARG, "precision must be PD_PREC_F32, PD_PREC_F64 or PD_PREC_DW");
+    if (cfg->precision == PD_PREC_DW && cfg->integrator != PD_INTEGRATOR_EC)
+        return fail(PD_ERR_ARG, "PD_PREC_DW uses the Euler-Cromer integrator");
     if (!(cfg->dt > 0.0) || !(cfg->density > 0.0) || !(cfg->damping >= 0.0) ||
         !std::isfinite(cfg->dt) || !std::isfinite(cfg->density) || !std::isfinite(cfg->damping))
         return fail(PD_ERR_ARG, "dt and density must be > 0, damping >= 0");
@@ -562,7 +606,8 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
     h->n_slices = (n + 31) / 32;
     h->n_pad = 32 * h->n_slices;
     h->n_bonds = h->off[n];
-    h->precision = cfg->precision;
+    h->dw = cfg->precision == PD_PREC_DW;
+    h->precision = h->dw ? PD_PREC_F64 : cfg->precision;
     h->delta = d.unit;
     h->dt = cfg->dt;
     h->eta = cfg->damping;
@@ -622,7 +667,13 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
         ALLOC(h->v, double, 3 * np);
         ALLOC(h->wsum_inv, double, np);
         ALLOC(h->damage, double, np);
-        ALLOC(h->ilen, double, nbr.size());
+        if (h->dw) {
+            ALLOC(h->recdw[0], float4, 4 * np);
+            ALLOC(h->recdw[1], float4, 4 * np);
+            ALLOC(h->lendw, float2, nbr.size());
+        } else {
+            ALLOC(h->ilen, double, nbr.size());
+        }
     }
     if (h->model == 1) {
         if (h->integrator != PD_INTEGRATOR_EC)
@@ -685,6 +736,7 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
                 hi[a] = std::max(hi[a], d.coords[3 * i + a]);
             }
         for (int a = 0; a < 3; ++a) gctr[a] = 0.5 * (lo[a] + hi[a]);
+        for (int a = 0; a < 3; ++a) h->dw_origin[a] = gctr[a];
     }
     std::vector<double> xs(3 * np, 0.0), vs(np, 0.0), cs(3 * np, 0.0);
     std::vector<uint8_t> clsp(np, 0);
@@ -749,8 +801,14 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
                      "upload instance table")))
             return st;
     }
-    if (!f32) {
+    if (!f32 && !h->dw) {
         e = launch_inv_len(h->x64, h->nbr, h->sw, n, h->Q, h->ilen, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "bond lengths");
+    }
+    if (h->dw) {
+        if (h->model != 0 || h->kr != 0.0)
+            return fail(PD_ERR_ARG, "PD_PREC_DW supports the PMB model without softening");
+        e = launch_dw_len(h->x64, h->nbr, h->sw, n, h->Q, 1.0 / h->delta, h->lendw, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "bond lengths");
     }
     if (h->model == 1 && !f32) {
@@ -854,6 +912,8 @@ pd_status pd_batch_create(int32_t n_inst, const pd_instance* inst, const pd_conf
     if (n_inst < 1 || !inst || !cfg) return fail(PD_ERR_ARG, "need n_inst >= 1, inst and cfg");
     pd_status st;
     if ((st = check_cfg(cfg)) != PD_OK) return st;
+    if (cfg->precision == PD_PREC_DW)
+        return fail(PD_ERR_ARG, "batches take PD_PREC_F32 or PD_PREC_F64");
     int64_t n = 0;
     double unit = 0.0;
     bool any_nofail = false;
@@ -983,7 +1043,7 @@ pd_status pd_get_info(pd_handle* h, pd_info_t* out)
     out->n = h->n;
     out->n_bonds = h->n_bonds;
     out->step = h->step;
-    out->precision = h->precision;
+    out->precision = h->dw ? PD_PREC_DW : h->precision;
     out->ell_width = 32 * h->Q;
     out->device_bytes = h->device_bytes;
     return PD_OK;
@@ -1125,6 +1185,10 @@ pd_status pd_set_state(pd_handle* h, const double* u, const double* v, int64_t s
             PD_CUDA(launch_set_state_f64(src[0], src[1], h->gid, h->n, h->rec[cur],
                                          (double*)h->v, h->stream),
                     "set state");
+        if (h->dw)
+            PD_CUDA(launch_dw_publish(h->rec[cur], h->recdw[cur], h->n_pad, h->dw_origin,
+                                      1.0 / h->delta, h->stream),
+                    "double-word records");
     }
     // the velocity-Verlet history starts again at this step (a^n formed afresh);
     // the host inputs were consumed before the check above, so nothing more
@@ -1262,8 +1326,8 @@ pd_status pd_damage(pd_handle* h, double* phi)
 pd_status pd_adjoint_forward(pd_handle* h, int64_t n_steps, int64_t checkpoint_every)
 {
     if (!h) return fail(PD_ERR_ARG, "NULL handle");
-    if (h->precision != 64 || h->batch || h->integrator != PD_INTEGRATOR_EC || h->integ ||
-        h->model != 0)
+    if (h->precision != 64 || h->dw || h->batch || h->integrator != PD_INTEGRATOR_EC ||
+        h->integ || h->model != 0)
         return fail(PD_ERR_STATE,
                     "the adjoint is available on FP64 single-model Euler-Cromer PMB handles");
     if (n_steps < 1 || checkpoint_every < 0)
@@ -1506,6 +1570,10 @@ pd_status pd_autotune(pd_handle* h, int32_t trial_steps, int32_t* block_threads,
     } else {
         bufs.push_back({h->rec[0], (size_t)(64 * np), {}});
         bufs.push_back({h->rec[1], (size_t)(64 * np), {}});
+        if (h->dw) {
+            bufs.push_back({h->recdw[0], (size_t)(64 * np), {}});
+            bufs.push_back({h->recdw[1], (size_t)(64 * np), {}});
+        }
         bufs.push_back({h->v, (size_t)(24 * np), {}});
         bufs.push_back({h->damage, (size_t)(8 * np), {}});
     }
@@ -1556,7 +1624,7 @@ pd_status pd_autotune(pd_handle* h, int32_t trial_steps, int32_t* block_threads,
                 best_bps = bps;
             }
             int occ = 0;
-            const void* fn = h->precision == 32 ? f32_kernel(h) : step_f64_kernel(h->sc_mode);
+            const void* fn = step_kernel_fn(h);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block, 0);
             if (bps >= occ) break;  // larger requests are capped to the same grid
         }
@@ -1583,6 +1651,8 @@ pd_status pd_set_params(pd_handle* h, double c, double sc, double load, double d
     if (h->batch) return fail(PD_ERR_STATE, "pd_set_params is not available on a batch handle");
     if (h->model == 1 && c_bond)
         return fail(PD_ERR_STATE, "per-bond stiffness is not available with the state-based model");
+    if (h->dw && c_bond)
+        return fail(PD_ERR_STATE, "per-bond stiffness is not available with PD_PREC_DW");
     if (!(c > 0.0) || !std::isfinite(c)) return fail(PD_ERR_ARG, "c must be > 0");
     if (!(sc > 0.0) || !std::isfinite(sc)) return fail(PD_ERR_ARG, "sc must be > 0");
     if (!std::isfinite(load) || !std::isfinite(disp_rate))

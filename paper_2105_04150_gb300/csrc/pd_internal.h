@@ -29,6 +29,8 @@
 // FP64 path:
 //   rec[2] 8 doubles per node {x, y, z, w, ux, uy, uz, 0}, double buffered
 //   v      double velocity, 3 per node
+//   (PD_PREC_DW handles add 64-byte double-word copies of the records for the
+//   neighbours and a double-word reference length per slot, see DwArgs)
 #pragma once
 
 #include <cstdint>
@@ -135,6 +137,18 @@ struct StepArgsF64 {
     double k1, beta;           // trilinear: kink at s_1 = k1 s_0 with force beta c s_0 (k1 > 1)
 };
 
+// Double-word (FP64-grade) step of FP64 handles created with PD_PREC_DW
+// (pd_step_dw.cu): neighbour records and per-slot reference lengths
+struct DwArgs {
+    const float4* rec[2];      // 4 float4 per node, double buffered like the FP64 records
+    const float2* len;         // per slot |xi| / delta as a double-word (hi, lo)
+    double inv_delta;          // 1 / delta
+    double w_const;            // c V when the node weights are uniform
+    double dt_rho;             // dt / rho
+    float fast_lo;             // leading stretch words below this are decided without s_c
+    int32_t uniform_w;         // 1: every node has weight w_const
+};
+
 // Ordinary state-based (linear solid) arrays, FP64 handles with model 1
 struct OsbArgs {
     double* len;               // per slot |xi|
@@ -219,6 +233,14 @@ cudaError_t launch_step_f32_soft(const StepArgsF32& a, int sc_mode, int grid, in
                                  cudaStream_t s);
 const void* step_f32_kernel_soft(int sc_mode, bool uniform_w, bool per_bond_c);
 const void* step_f64_kernel(int sc_mode);
+cudaError_t launch_step_dw(const StepArgsF64& a, const DwArgs& d, int sc_mode, int grid, int block,
+                           cudaStream_t s);
+const void* step_dw_kernel(int sc_mode, bool uniform_w);
+// double-word records from the FP64 records (positions relative to origin[3])
+cudaError_t launch_dw_publish(const double* rec64, float4* rec, int64_t n_pad, const double* origin,
+                              double inv_delta, cudaStream_t s);
+cudaError_t launch_dw_len(const double* x64, const int32_t* nbr, const int32_t* sw, int64_t n, int Q,
+                          double inv_delta, float2* len, cudaStream_t s);
 
 // ---- helper kernels (pd_aux.cu) ---------------------------------------------
 cudaError_t launch_advance(int64_t* step_ctr, int64_t k, cudaStream_t s);

@@ -1,0 +1,507 @@
+// FP64-grade peridynamic step from double-word FP32 arithmetic (sm_103a).
+//
+// GB300 issues FP32 operations at about 58 times its FP64 rate, and the FP64
+// step kernel is bound by the FP64 pipe.  This kernel computes the same step
+// (Eq. 4 stretch, Eq. 6 breaking, Eq. 5/10 force, Eq. 11 update, Eq. 8
+// damage) with every bond quantity carried as an unevaluated sum of two FP32
+// numbers, h + l with |l| <= ulp(h)/2 (double-word arithmetic: Dekker 1971;
+// Knuth's two-sum; the products and error bounds of Joldes, Muller & Popescu,
+// ACM TOMS 2017), which carries about 48 significant bits: the relative
+// accuracy of a bond force is ~1e-13, far inside the FP64 parity bar, for a
+// few hundred FP32 operations instead of ~30 FP64 ones.
+//
+// Work decomposition, bond flags, node order and the double-buffered records
+// are those of the FP32 kernel (lane per node over the sliced family).
+// Node state stays FP64: each node's owner keeps u and v in the FP64 records
+// and integrates in FP64; what neighbours read is a 64-byte double-word copy
+//   {xh.x, xh.y, xh.z, uh.x} {uh.y, uh.z, wh, wl} {xl.x, xl.y, xl.z, ul.x} {ul.y, ul.z, 0, 0}
+// with positions x~ = (x - origin) / delta and u~ = u / delta in units of the
+// horizon and w = c V, read as two 256-bit loads.  The reference length
+// |xi| / delta of each slot is a double-word computed once in FP64.
+//
+// Per bond, with xi and eta the double-word differences (exact leading
+// parts): y = xi + eta, num = eta . (2 xi + eta) = |y|^2 - |xi|^2 without
+// cancellation, |y|^2 = L^2 + num, s = num / (L (L + |y|)), and the force
+// c V s y / |y|.  |y|, 1/|y| and the quotient come from FP32 seeds
+// (approximate rsqrt / rcp, one Newton step) with a double-word correction.
+// Both directions of a bond produce the same s bit for bit (every operation
+// is odd or even under exchanging i and j), so they break together.  A bond
+// whose leading stretch word reaches a band just below the smallest s_c is
+// decided at the end of its flag word against the FP64 s_c, as in the FP32
+// kernel; the rest of the break test needs no FP64 operation.
+#include <cuda_runtime.h>
+
+#include "pd_internal.h"
+
+namespace pd {
+namespace {
+
+constexpr int kUnroll = 2;  // family slots in flight per lane
+
+__device__ __forceinline__ uint64_t splitmix_out(uint64_t seed, uint64_t m)
+{
+    uint64_t z = seed + m * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double sc_draw(uint64_t seed, double lo, double hi, int32_t gi,
+                                          int32_t gj)
+{
+    const uint64_t a = (uint64_t)(uint32_t)min(gi, gj);
+    const uint64_t b = (uint64_t)(uint32_t)max(gi, gj);
+    const uint64_t h = splitmix_out(seed, ((a << 32) | b) + 1ull);
+    return lo + (hi - lo) * ((double)(h >> 11) * 0x1.0p-53);
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void ld_rec(const float4* p, float4& a, float4& b)
+{
+    asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z),
+                   "=f"(b.w)
+                 : "l"(p));
+}
+
+__device__ __forceinline__ void st_rec(float4* p, const float4& a, const float4& b)
+{
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(a.x),
+                 "f"(a.y), "f"(a.z), "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
+                 : "memory");
+}
+
+// hardware approximations, used only as seeds that are refined below
+__device__ __forceinline__ float rsqrt_seed(float x)
+{
+    float r;
+    asm("rsqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_seed(float x)
+{
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// ---- double-word arithmetic
+struct Dw {
+    float h, l;
+};
+
+// exact sum (Knuth)
+__device__ __forceinline__ Dw two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+
+// exact sum when |a| >= |b| (Dekker)
+__device__ __forceinline__ Dw fast_two_sum(float a, float b)
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+
+// a - b, the leading difference exact, not renormalised
+__device__ __forceinline__ Dw dw_sub(float ah, float al, float bh, float bl)
+{
+    Dw t = two_sum(ah, -bh);
+    t.l += al - bl;
+    return t;
+}
+
+// sum of terms that do not cancel to below ~2^-20 of themselves
+__device__ __forceinline__ Dw dw_add(Dw a, Dw b)
+{
+    const Dw t = two_sum(a.h, b.h);
+    return fast_two_sum(t.h, t.l + (a.l + b.l));
+}
+
+// sum of any two double-words (cancellation included): absolute error
+// ~2^-48 (|a| + |b|)
+__device__ __forceinline__ Dw dw_add_any(Dw a, Dw b)
+{
+    const Dw t = two_sum(a.h, b.h);
+    return two_sum(t.h, t.l + (a.l + b.l));
+}
+
+// product (the exact product of the leading words plus the cross terms)
+__device__ __forceinline__ Dw dw_mul(Dw a, Dw b)
+{
+    const float p = a.h * b.h;
+    const float e = fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)));
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ Dw dw_mul_f(Dw a, float b)
+{
+    const float p = a.h * b;
+    const float e = fmaf(a.l, b, fmaf(a.h, b, -p));
+    return fast_two_sum(p, e);
+}
+
+// The lane's own record (double-word position and displacement).
+struct OwnDw {
+    float xh[3], xl[3], uh[3], ul[3];
+};
+
+__device__ __forceinline__ OwnDw own_of(const float4 a0, const float4 a1, const float4 b0,
+                                        const float4 b1)
+{
+    OwnDw o;
+    o.xh[0] = a0.x; o.xh[1] = a0.y; o.xh[2] = a0.z;
+    o.uh[0] = a0.w; o.uh[1] = a1.x; o.uh[2] = a1.y;
+    o.xl[0] = b0.x; o.xl[1] = b0.y; o.xl[2] = b0.z;
+    o.ul[0] = b0.w; o.ul[1] = b1.x; o.ul[2] = b1.y;
+    return o;
+}
+
+struct BondDw {
+    Dw s;     // stretch
+    Dw f[3];  // s y / |y| (times w_j unless the weights are uniform)
+};
+
+template <bool UW>
+__device__ __forceinline__ BondDw bond_dw(const OwnDw& o, const float4 a0, const float4 a1,
+                                          const float4 b0, const float4 b1, const float2 len)
+{
+    const float jxh[3] = {a0.x, a0.y, a0.z}, juh[3] = {a0.w, a1.x, a1.y};
+    const float jxl[3] = {b0.x, b0.y, b0.z}, jul[3] = {b0.w, b1.x, b1.y};
+    Dw y[3], nm[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const Dw xi = dw_sub(jxh[c], jxl[c], o.xh[c], o.xl[c]);
+        const Dw et = dw_sub(juh[c], jul[c], o.uh[c], o.ul[c]);
+        y[c] = dw_add(xi, et);
+        const Dw t = dw_add(Dw{2.0f * xi.h, 2.0f * xi.l}, et);
+        nm[c] = dw_mul(et, t);
+    }
+    const Dw num = dw_add_any(dw_add_any(nm[0], nm[1]), nm[2]);
+    const Dw L{len.x, len.y};
+    const Dw y2 = dw_add_any(dw_mul(L, L), num);
+    // 1/|y| seed refined once in FP32 (Newton), then |y| and 1/|y| corrected
+    // to double-word accuracy from the residuals
+    float r0 = rsqrt_seed(y2.h);
+    r0 = r0 * fmaf(-0.5f * y2.h * r0, r0, 1.5f);
+    const float rh = y2.h * r0;
+    const Dw r = fast_two_sum(rh, 0.5f * (fmaf(-rh, rh, y2.h) + y2.l) * r0);
+    const float dd = fmaf(-r.h, r0, 1.0f) - r.l * r0;
+    const Dw ir = fast_two_sum(r0, r0 * dd);
+    // s = num / den, den = L (L + |y|): FP32 quotient plus the remainder's
+    const Dw den = dw_mul(L, dw_add(L, r));
+    float q = rcp_seed(den.h);
+    q = fmaf(q, fmaf(-den.h, q, 1.0f), q);
+    const float q0 = num.h * q;
+    const Dw p = dw_mul_f(den, q0);
+    const float rem = ((num.h - p.h) - p.l) + num.l;
+    BondDw out;
+    out.s = fast_two_sum(q0, rem * q);
+    Dw coef = dw_mul(out.s, ir);
+    if (!UW) coef = dw_mul(coef, Dw{a1.z, a1.w});
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out.f[c] = dw_mul(coef, y[c]);
+    return out;
+}
+
+// A bond whose leading stretch word reached the band below the smallest s_c:
+// recomputed and decided in FP64 against its s_c, then the no-fail rule.
+// Returns its contribution (zero when it breaks).
+template <int SCM, bool UW>
+__device__ __noinline__ BondDw resolve_dw(const StepArgsF64& a, const DwArgs& d, int cur,
+                                          int64_t i, int64_t j, int64_t slot, bool* broken)
+{
+    const float4* __restrict__ R = d.rec[cur];
+    float4 a0, a1, b0, b1, c0, c1, e0, e1;
+    ld_rec(R + 4 * i, a0, a1);
+    ld_rec(R + 4 * i + 2, b0, b1);
+    ld_rec(R + 4 * j, c0, c1);
+    ld_rec(R + 4 * j + 2, e0, e1);
+    BondDw bd = bond_dw<UW>(own_of(a0, a1, b0, b1), c0, c1, e0, e1, d.len[slot]);
+    const double sc = SCM == 0 ? a.sc : sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i], a.gid[j]);
+    bool brk = (double)bd.s.h + (double)bd.s.l >= sc;
+    if (brk && a.has_nofail) brk = ((a.bct[a.bcc[i]].mask | a.bct[a.bcc[j]].mask) & 8u) == 0u;
+    *broken = brk;
+    if (brk) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) bd.f[c] = Dw{0.0f, 0.0f};
+    }
+    return bd;
+}
+
+template <int SCM, bool UW>
+__global__ void __launch_bounds__(256, 2)
+    k_step_dw(const __grid_constant__ StepArgsF64 a, const __grid_constant__ DwArgs d)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t step = a.step_ctr[0] + a.k;
+    const int cur = (int)(step & 1);
+    const int Q = a.Q;
+    const int64_t W = 32LL * Q;
+    const int64_t nslices = (a.n + 31) >> 5;
+    const float4* __restrict__ R = d.rec[cur];
+    float4* __restrict__ Rout = const_cast<float4*>(d.rec[cur ^ 1]);
+    const double2* __restrict__ rin = reinterpret_cast<const double2*>(a.rec[cur]);
+    double2* __restrict__ rout = reinterpret_cast<double2*>(const_cast<double*>(a.rec[cur ^ 1]));
+
+    for (int64_t g = wid; g < nslices; g += nwarps) {
+        const int Wg = a.sw[g];
+        const int32_t* __restrict__ col = a.nbr + g * W * 32 + lane;
+        if (lane == 0) prefetch_l2(col, (uint32_t)(((Wg + 3) & ~3) * 128));
+        const int64_t i = (g << 5) + lane;
+        float4 oa0, oa1, ob0, ob1;
+        ld_rec(R + 4 * i, oa0, oa1);
+        ld_rec(R + 4 * i + 2, ob0, ob1);
+        const OwnDw own = own_of(oa0, oa1, ob0, ob1);
+        uint32_t* bw = a.bits + g * Q * 32 + lane;
+        float Fh[3] = {0.f, 0.f, 0.f}, Fl[3] = {0.f, 0.f, 0.f};
+        float wsh = 0.f, wsl = 0.f;  // non-uniform weights: sum of w_j over intact bonds
+        int alive_count = 0;
+
+        const int nch = (Wg + kUnroll - 1) / kUnroll;
+        int32_t jn[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) jn[u] = __ldg(col + u * 32);
+        uint32_t word = 0u, nword = 0u, pend = 0u;
+        for (int c = 0; c < nch; ++c) {
+            const int m0 = c * kUnroll;
+            const int q = m0 >> 5, b0 = m0 & 31;
+            if (b0 == 0) {
+                word = bw[q * 32];
+                nword = word;
+                pend = 0u;
+            }
+            int32_t jj[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) jj[u] = jn[u];
+            if (c + 1 < nch) {
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) jn[u] = __ldg(col + (m0 + kUnroll + u) * 32);
+            }
+            float4 ra0[kUnroll], ra1[kUnroll], rb0[kUnroll], rb1[kUnroll];
+            float2 ln[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                ld_rec(R + 4 * (int64_t)jj[u], ra0[u], ra1[u]);
+                ld_rec(R + 4 * (int64_t)jj[u] + 2, rb0[u], rb1[u]);
+                ln[u] = __ldg(d.len + (g * W + m0 + u) * 32 + lane);
+            }
+            const uint32_t wb = word >> b0;
+            uint32_t pc = 0u;
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const bool alive = (wb >> u) & 1u;
+                const BondDw bd = bond_dw<UW>(own, ra0[u], ra1[u], rb0[u], rb1[u], ln[u]);
+                const bool cand = bd.s.h >= d.fast_lo;
+                pc |= cand ? (1u << u) : 0u;
+                const bool ok = alive && !cand;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const Dw t = two_sum(Fh[k], ok ? bd.f[k].h : 0.0f);
+                    Fh[k] = t.h;
+                    Fl[k] += t.l + (ok ? bd.f[k].l : 0.0f);
+                }
+                if (UW) {
+                    alive_count += ok ? 1 : 0;
+                } else {
+                    const Dw t = two_sum(wsh, ok ? ra1[u].z : 0.0f);
+                    wsh = t.h;
+                    wsl += t.l + (ok ? ra1[u].w : 0.0f);
+                }
+            }
+            pend |= (pc & wb) << b0;
+            if (b0 + kUnroll == 32 || c + 1 == nch) {  // end of bond-flag word q
+                while (pend) {
+                    const int b = __ffs(pend) - 1;
+                    pend &= pend - 1u;
+                    const int64_t slot = (g * W + q * 32 + b) * 32 + lane;
+                    const int64_t j = col[(int64_t)(q * 32 + b) * 32];
+                    bool broken;
+                    const BondDw f = resolve_dw<SCM, UW>(a, d, cur, i, j, slot, &broken);
+                    if (broken) {
+                        nword &= ~(1u << b);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            const Dw t = two_sum(Fh[k], f.f[k].h);
+                            Fh[k] = t.h;
+                            Fl[k] += t.l + f.f[k].l;
+                        }
+                        if (UW) {
+                            ++alive_count;
+                        } else {
+                            float4 c0, c1;
+                            ld_rec(R + 4 * j, c0, c1);
+                            const Dw t = two_sum(wsh, c1.z);
+                            wsh = t.h;
+                            wsl += t.l + c1.w;
+                        }
+                    }
+                }
+                if (nword != word) bw[q * 32] = nword;
+            }
+        }
+
+        // ---- integration of the lane's node in FP64 (damped Euler-Cromer, Eq. 11)
+        if (i < a.n) {
+            const uint32_t cls = a.bcc[i];
+            uint32_t mask = 0u;
+            double gdisp[3] = {0.0, 0.0, 0.0};
+            const double wscale = UW ? d.w_const : 1.0;
+            double F[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) F[k] = ((double)Fh[k] + (double)Fl[k]) * wscale;
+            if (cls != 0u) {
+                const BcClass& bc = a.bct[cls];
+                mask = bc.mask;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    gdisp[k] = bc.disp[k];
+                    F[k] += a.load * bc.force[k];
+                }
+            }
+            const double s_now = bc_scale(a.disp_rate, a.ramp_steps, step);
+            const double s_next = bc_scale(a.disp_rate, a.ramp_steps, step + 1);
+            const double2 u01 = rin[4 * i + 2], u23 = rin[4 * i + 3];
+            const double uo[3] = {u01.x, u01.y, u23.x};
+            double un[3];
+            float uh[3], ul[3];
+            bool finite = true;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const double vi = a.v[3 * i + k];
+                double vn = vi + (F[k] - a.eta * vi) * d.dt_rho;
+                double u = uo[k] + a.dt * vn;
+                if (mask & (1u << k)) {
+                    u = gdisp[k] * s_next;
+                    vn = gdisp[k] * (s_next - s_now) / a.dt;
+                }
+                finite = finite && isfinite(u);
+                un[k] = u;
+                a.v[3 * i + k] = vn;
+                const double ut = u * d.inv_delta;
+                uh[k] = (float)ut;
+                ul[k] = (float)(ut - (double)uh[k]);
+            }
+            rout[4 * i] = rin[4 * i];
+            rout[4 * i + 1] = rin[4 * i + 1];
+            rout[4 * i + 2] = make_double2(un[0], un[1]);
+            rout[4 * i + 3] = make_double2(un[2], 0.0);
+            st_rec(Rout + 4 * i, make_float4(own.xh[0], own.xh[1], own.xh[2], uh[0]),
+                   make_float4(uh[1], uh[2], oa1.z, oa1.w));
+            st_rec(Rout + 4 * i + 2, make_float4(own.xl[0], own.xl[1], own.xl[2], ul[0]),
+                   make_float4(ul[1], ul[2], 0.0f, 0.0f));
+            const double ws = UW ? d.w_const * (double)alive_count : (double)wsh + (double)wsl;
+            const double wi = a.wsum_inv[i];
+            a.damage[i] = wi > 0.0 ? fmax(0.0, 1.0 - ws * wi) : 0.0;
+            if (!finite) atomicOr(a.err, PD_DEVERR_NONFINITE);
+        }
+    }
+}
+
+// Double-word records of every node from the FP64 records (after a state or
+// the weights were set), and the double-word reference length of every slot.
+__global__ void k_dw_publish(const double* __restrict__ rec64, float4* __restrict__ rec,
+                             int64_t n_pad, double ox, double oy, double oz, double inv_delta)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pad;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const double* r = rec64 + 8 * p;
+        const double xt[3] = {(r[0] - ox) * inv_delta, (r[1] - oy) * inv_delta,
+                              (r[2] - oz) * inv_delta};
+        const double ut[3] = {r[4] * inv_delta, r[5] * inv_delta, r[6] * inv_delta};
+        float xh[3], xl[3], uh[3], ul[3];
+        for (int k = 0; k < 3; ++k) {
+            xh[k] = (float)xt[k];
+            xl[k] = (float)(xt[k] - (double)xh[k]);
+            uh[k] = (float)ut[k];
+            ul[k] = (float)(ut[k] - (double)uh[k]);
+        }
+        const float wh = (float)r[3];
+        const float wl = (float)(r[3] - (double)wh);
+        rec[4 * p] = make_float4(xh[0], xh[1], xh[2], uh[0]);
+        rec[4 * p + 1] = make_float4(uh[1], uh[2], wh, wl);
+        rec[4 * p + 2] = make_float4(xl[0], xl[1], xl[2], ul[0]);
+        rec[4 * p + 3] = make_float4(ul[1], ul[2], 0.0f, 0.0f);
+    }
+}
+
+__global__ void k_dw_len(const double* __restrict__ x64, const int32_t* __restrict__ nbr,
+                         const int32_t* __restrict__ sw, int64_t n, int Q, double inv_delta,
+                         float2* __restrict__ len)
+{
+    const int64_t W = 32LL * Q;
+    const int64_t total = ((n + 31) >> 5) << 5;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = p >> 5;
+        const int lane = (int)(p & 31);
+        const int Wg = sw[g];
+        for (int m = 0; m < Wg; ++m) {
+            const int64_t slot = (g * W + m) * 32 + lane;
+            const int64_t j = nbr[slot];
+            float2 v = make_float2(0.0f, 0.0f);
+            if (j != p) {
+                const double ex = x64[3 * j] - x64[3 * p], ey = x64[3 * j + 1] - x64[3 * p + 1],
+                             ez = x64[3 * j + 2] - x64[3 * p + 2];
+                const double L = sqrt(ex * ex + ey * ey + ez * ez) * inv_delta;
+                v.x = (float)L;
+                v.y = (float)(L - (double)v.x);
+            }
+            len[slot] = v;
+        }
+    }
+}
+
+int grid_of(int64_t work)
+{
+    const int64_t b = (work + 255) / 256;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
+}
+
+}  // namespace
+
+cudaError_t launch_step_dw(const StepArgsF64& a, const DwArgs& d, int sc_mode, int grid, int block,
+                           cudaStream_t s)
+{
+    if (sc_mode == 0) {
+        if (d.uniform_w) k_step_dw<0, true><<<grid, block, 0, s>>>(a, d);
+        else k_step_dw<0, false><<<grid, block, 0, s>>>(a, d);
+    } else {
+        if (d.uniform_w) k_step_dw<1, true><<<grid, block, 0, s>>>(a, d);
+        else k_step_dw<1, false><<<grid, block, 0, s>>>(a, d);
+    }
+    return cudaGetLastError();
+}
+
+const void* step_dw_kernel(int sc_mode, bool uniform_w)
+{
+    if (sc_mode == 0)
+        return uniform_w ? (const void*)k_step_dw<0, true> : (const void*)k_step_dw<0, false>;
+    return uniform_w ? (const void*)k_step_dw<1, true> : (const void*)k_step_dw<1, false>;
+}
+
+cudaError_t launch_dw_publish(const double* rec64, float4* rec, int64_t n_pad, const double* origin,
+                              double inv_delta, cudaStream_t s)
+{
+    k_dw_publish<<<grid_of(n_pad), 256, 0, s>>>(rec64, rec, n_pad, origin[0], origin[1], origin[2],
+                                                inv_delta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dw_len(const double* x64, const int32_t* nbr, const int32_t* sw, int64_t n, int Q,
+                          double inv_delta, float2* len, cudaStream_t s)
+{
+    k_dw_len<<<grid_of(((n + 31) >> 5) << 5), 256, 0, s>>>(x64, nbr, sw, n, Q, inv_delta, len);
+    return cudaGetLastError();
+}
+
+}  // namespace pd
