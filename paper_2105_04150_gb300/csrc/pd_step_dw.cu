@@ -36,7 +36,9 @@
 namespace pd {
 namespace {
 
-constexpr int kUnroll = 2;  // family slots in flight per lane
+#ifndef PD_DW_MIN_BLOCKS
+#define PD_DW_MIN_BLOCKS 2
+#endif
 
 __device__ __forceinline__ uint64_t splitmix_out(uint64_t seed, uint64_t m)
 {
@@ -89,7 +91,11 @@ __device__ __forceinline__ float rcp_seed(float x)
     return r;
 }
 
-// ---- double-word arithmetic
+// ---- double-word arithmetic.  Values are unevaluated sums h + l; the
+// operations below leave their result unnormalised (|l| up to a few ulp(h))
+// wherever the next operation takes that, which keeps ~46-bit accuracy for
+// far fewer FP32 operations than renormalising after each step.  The FP32
+// pipe is the limit here, so the code is scalar: negated operands cost nothing.
 struct Dw {
     float h, l;
 };
@@ -102,49 +108,20 @@ __device__ __forceinline__ Dw two_sum(float a, float b)
     return {s, (a - (s - bb)) + (b - bb)};
 }
 
-// exact sum when |a| >= |b| (Dekker)
-__device__ __forceinline__ Dw fast_two_sum(float a, float b)
+// a + b: the leading words summed exactly, everything else in FP32
+__device__ __forceinline__ Dw dw_add(Dw a, Dw b)
 {
-    const float s = a + b;
-    return {s, b - (s - a)};
-}
-
-// a - b, the leading difference exact, not renormalised
-__device__ __forceinline__ Dw dw_sub(float ah, float al, float bh, float bl)
-{
-    Dw t = two_sum(ah, -bh);
-    t.l += al - bl;
+    Dw t = two_sum(a.h, b.h);
+    t.l += a.l + b.l;
     return t;
 }
 
-// sum of terms that do not cancel to below ~2^-20 of themselves
-__device__ __forceinline__ Dw dw_add(Dw a, Dw b)
-{
-    const Dw t = two_sum(a.h, b.h);
-    return fast_two_sum(t.h, t.l + (a.l + b.l));
-}
-
-// sum of any two double-words (cancellation included): absolute error
-// ~2^-48 (|a| + |b|)
-__device__ __forceinline__ Dw dw_add_any(Dw a, Dw b)
-{
-    const Dw t = two_sum(a.h, b.h);
-    return two_sum(t.h, t.l + (a.l + b.l));
-}
-
-// product (the exact product of the leading words plus the cross terms)
+// a * b: the exact product of the leading words plus the cross terms
+// (Joldes, Muller & Popescu's DWTimesDW without the final renormalisation)
 __device__ __forceinline__ Dw dw_mul(Dw a, Dw b)
 {
     const float p = a.h * b.h;
-    const float e = fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)));
-    return fast_two_sum(p, e);
-}
-
-__device__ __forceinline__ Dw dw_mul_f(Dw a, float b)
-{
-    const float p = a.h * b;
-    const float e = fmaf(a.l, b, fmaf(a.h, b, -p));
-    return fast_two_sum(p, e);
+    return {p, fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)))};
 }
 
 // The lane's own record (double-word position and displacement).
@@ -152,91 +129,109 @@ struct OwnDw {
     float xh[3], xl[3], uh[3], ul[3];
 };
 
-__device__ __forceinline__ OwnDw own_of(const float4 a0, const float4 a1, const float4 b0,
-                                        const float4 b1)
+// One neighbour's record as the two 256-bit loads deliver it.
+struct Rec {
+    float4 a0, a1, b0, b1;
+};
+
+__device__ __forceinline__ OwnDw own_of(const Rec& r)
 {
     OwnDw o;
-    o.xh[0] = a0.x; o.xh[1] = a0.y; o.xh[2] = a0.z;
-    o.uh[0] = a0.w; o.uh[1] = a1.x; o.uh[2] = a1.y;
-    o.xl[0] = b0.x; o.xl[1] = b0.y; o.xl[2] = b0.z;
-    o.ul[0] = b0.w; o.ul[1] = b1.x; o.ul[2] = b1.y;
+    o.xh[0] = r.a0.x; o.xh[1] = r.a0.y; o.xh[2] = r.a0.z;
+    o.uh[0] = r.a0.w; o.uh[1] = r.a1.x; o.uh[2] = r.a1.y;
+    o.xl[0] = r.b0.x; o.xl[1] = r.b0.y; o.xl[2] = r.b0.z;
+    o.ul[0] = r.b0.w; o.ul[1] = r.b1.x; o.ul[2] = r.b1.y;
     return o;
 }
 
 struct BondDw {
     Dw s;     // stretch
-    Dw f[3];  // s y / |y| (times w_j unless the weights are uniform)
+    Dw coef;  // s / |y| (times w_j unless the weights are uniform)
+    Dw y[3];  // deformed bond vector / delta
 };
 
+// One bond of the lane's node.  `len` is the slot's |xi| / delta (slots
+// without a bond hold 1 and their neighbour is the node itself).
 template <bool UW>
-__device__ __forceinline__ BondDw bond_dw(const OwnDw& o, const float4 a0, const float4 a1,
-                                          const float4 b0, const float4 b1, const float2 len)
+__device__ __forceinline__ BondDw bond_dw(const OwnDw& o, const Rec& j, const float2 len)
 {
-    const float jxh[3] = {a0.x, a0.y, a0.z}, juh[3] = {a0.w, a1.x, a1.y};
-    const float jxl[3] = {b0.x, b0.y, b0.z}, jul[3] = {b0.w, b1.x, b1.y};
-    Dw y[3], nm[3];
+    const float jxh[3] = {j.a0.x, j.a0.y, j.a0.z}, juh[3] = {j.a0.w, j.a1.x, j.a1.y};
+    const float jxl[3] = {j.b0.x, j.b0.y, j.b0.z}, jul[3] = {j.b0.w, j.b1.x, j.b1.y};
+    BondDw out;
+    Dw nm[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const Dw xi = dw_sub(jxh[c], jxl[c], o.xh[c], o.xl[c]);
-        const Dw et = dw_sub(juh[c], jul[c], o.uh[c], o.ul[c]);
-        y[c] = dw_add(xi, et);
-        const Dw t = dw_add(Dw{2.0f * xi.h, 2.0f * xi.l}, et);
-        nm[c] = dw_mul(et, t);
+        // xi = x_j - x_i and eta = u_j - u_i, the leading differences exact
+        Dw xi = two_sum(jxh[c], -o.xh[c]);
+        xi.l += jxl[c] - o.xl[c];
+        Dw et = two_sum(juh[c], -o.uh[c]);
+        et.l += jul[c] - o.ul[c];
+        out.y[c] = dw_add(xi, et);
+        nm[c] = dw_mul(et, dw_add(xi, out.y[c]));  // eta_c (2 xi_c + eta_c)
     }
-    const Dw num = dw_add_any(dw_add_any(nm[0], nm[1]), nm[2]);
+    // num = eta . (2 xi + eta) = |y|^2 - |xi|^2
+    Dw num = two_sum(nm[0].h, nm[1].h);
+    num.l += nm[0].l + nm[1].l;
+    num = dw_add(num, nm[2]);
     const Dw L{len.x, len.y};
-    const Dw y2 = dw_add_any(dw_mul(L, L), num);
-    // 1/|y| seed refined once in FP32 (Newton), then |y| and 1/|y| corrected
-    // to double-word accuracy from the residuals
+    const Dw y2 = dw_add(dw_mul(L, L), num);
+    // 1/|y| seed refined once in FP32 (Newton), then |y| and 1/|y| corrected to
+    // double-word accuracy from the residuals
     float r0 = rsqrt_seed(y2.h);
-    r0 = r0 * fmaf(-0.5f * y2.h * r0, r0, 1.5f);
+    r0 = r0 * fmaf(-(0.5f * y2.h) * r0, r0, 1.5f);
     const float rh = y2.h * r0;
-    const Dw r = fast_two_sum(rh, 0.5f * (fmaf(-rh, rh, y2.h) + y2.l) * r0);
-    const float dd = fmaf(-r.h, r0, 1.0f) - r.l * r0;
-    const Dw ir = fast_two_sum(r0, r0 * dd);
+    const Dw r{rh, (fmaf(-rh, rh, y2.h) + y2.l) * r0 * 0.5f};
+    const Dw ir{r0, r0 * fmaf(-r.l, r0, fmaf(-r.h, r0, 1.0f))};
     // s = num / den, den = L (L + |y|): FP32 quotient plus the remainder's
     const Dw den = dw_mul(L, dw_add(L, r));
     float q = rcp_seed(den.h);
     q = fmaf(q, fmaf(-den.h, q, 1.0f), q);
     const float q0 = num.h * q;
-    const Dw p = dw_mul_f(den, q0);
-    const float rem = ((num.h - p.h) - p.l) + num.l;
-    BondDw out;
-    out.s = fast_two_sum(q0, rem * q);
-    Dw coef = dw_mul(out.s, ir);
-    if (!UW) coef = dw_mul(coef, Dw{a1.z, a1.w});
-#pragma unroll
-    for (int c = 0; c < 3; ++c) out.f[c] = dw_mul(coef, y[c]);
+    const float ph = den.h * q0;
+    const float pl = fmaf(den.l, q0, fmaf(den.h, q0, -ph));
+    out.s = Dw{q0, (((num.h - ph) - pl) + num.l) * q};
+    out.coef = dw_mul(out.s, ir);
+    if (!UW) out.coef = dw_mul(out.coef, Dw{j.a1.z, j.a1.w});
     return out;
 }
 
+// F += coef y when `ok` (a select: whatever a masked slot computed, including
+// a non-finite value, is dropped)
+__device__ __forceinline__ void add_force(Dw (&F)[3], const BondDw& b, bool ok)
+{
+    const Dw cf{ok ? b.coef.h : 0.0f, ok ? b.coef.l : 0.0f};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const Dw f = dw_mul(cf, b.y[k]);
+        const Dw t = two_sum(F[k].h, f.h);
+        F[k].h = t.h;
+        F[k].l += t.l + f.l;
+    }
+}
+
 // A bond whose leading stretch word reached the band below the smallest s_c:
-// recomputed and decided in FP64 against its s_c, then the no-fail rule.
-// Returns its contribution (zero when it breaks).
+// recomputed with the same arithmetic and decided in FP64 against its s_c,
+// then the no-fail rule.
 template <int SCM, bool UW>
 __device__ __noinline__ BondDw resolve_dw(const StepArgsF64& a, const DwArgs& d, int cur,
                                           int64_t i, int64_t j, int64_t slot, bool* broken)
 {
     const float4* __restrict__ R = d.rec[cur];
-    float4 a0, a1, b0, b1, c0, c1, e0, e1;
-    ld_rec(R + 4 * i, a0, a1);
-    ld_rec(R + 4 * i + 2, b0, b1);
-    ld_rec(R + 4 * j, c0, c1);
-    ld_rec(R + 4 * j + 2, e0, e1);
-    BondDw bd = bond_dw<UW>(own_of(a0, a1, b0, b1), c0, c1, e0, e1, d.len[slot]);
+    Rec own, nb;
+    ld_rec(R + 4 * i, own.a0, own.a1);
+    ld_rec(R + 4 * i + 2, own.b0, own.b1);
+    ld_rec(R + 4 * j, nb.a0, nb.a1);
+    ld_rec(R + 4 * j + 2, nb.b0, nb.b1);
+    const BondDw bd = bond_dw<UW>(own_of(own), nb, d.len[slot]);
     const double sc = SCM == 0 ? a.sc : sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i], a.gid[j]);
     bool brk = (double)bd.s.h + (double)bd.s.l >= sc;
     if (brk && a.has_nofail) brk = ((a.bct[a.bcc[i]].mask | a.bct[a.bcc[j]].mask) & 8u) == 0u;
     *broken = brk;
-    if (brk) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) bd.f[c] = Dw{0.0f, 0.0f};
-    }
     return bd;
 }
 
 template <int SCM, bool UW>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, PD_DW_MIN_BLOCKS)
     k_step_dw(const __grid_constant__ StepArgsF64 a, const __grid_constant__ DwArgs d)
 {
     const int lane = threadIdx.x & 31;
@@ -257,68 +252,58 @@ __global__ void __launch_bounds__(256, 2)
         const int32_t* __restrict__ col = a.nbr + g * W * 32 + lane;
         if (lane == 0) prefetch_l2(col, (uint32_t)(((Wg + 3) & ~3) * 128));
         const int64_t i = (g << 5) + lane;
-        float4 oa0, oa1, ob0, ob1;
-        ld_rec(R + 4 * i, oa0, oa1);
-        ld_rec(R + 4 * i + 2, ob0, ob1);
-        const OwnDw own = own_of(oa0, oa1, ob0, ob1);
+        Rec me;
+        ld_rec(R + 4 * i, me.a0, me.a1);
+        ld_rec(R + 4 * i + 2, me.b0, me.b1);
+        const OwnDw own = own_of(me);
         uint32_t* bw = a.bits + g * Q * 32 + lane;
-        float Fh[3] = {0.f, 0.f, 0.f}, Fl[3] = {0.f, 0.f, 0.f};
-        float wsh = 0.f, wsl = 0.f;  // non-uniform weights: sum of w_j over intact bonds
+        // force sums of the A and B halves, and (non-uniform weights) the sum of
+        // w_j over intact bonds
+        Dw F[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        Dw ws{0.f, 0.f};
         int alive_count = 0;
 
-        const int nch = (Wg + kUnroll - 1) / kUnroll;
-        int32_t jn[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) jn[u] = __ldg(col + u * 32);
+        // chunks of two slots (bonds A and B); ids one chunk ahead
+        const int nch = (Wg + 1) >> 1;
+        int32_t jn0 = __ldg(col), jn1 = __ldg(col + 32);
         uint32_t word = 0u, nword = 0u, pend = 0u;
         for (int c = 0; c < nch; ++c) {
-            const int m0 = c * kUnroll;
+            const int m0 = 2 * c;
             const int q = m0 >> 5, b0 = m0 & 31;
             if (b0 == 0) {
                 word = bw[q * 32];
                 nword = word;
                 pend = 0u;
             }
-            int32_t jj[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) jj[u] = jn[u];
+            const int32_t j0 = jn0, j1 = jn1;
             if (c + 1 < nch) {
-#pragma unroll
-                for (int u = 0; u < kUnroll; ++u) jn[u] = __ldg(col + (m0 + kUnroll + u) * 32);
+                jn0 = __ldg(col + (m0 + 2) * 32);
+                jn1 = __ldg(col + (m0 + 3) * 32);
             }
-            float4 ra0[kUnroll], ra1[kUnroll], rb0[kUnroll], rb1[kUnroll];
-            float2 ln[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                ld_rec(R + 4 * (int64_t)jj[u], ra0[u], ra1[u]);
-                ld_rec(R + 4 * (int64_t)jj[u] + 2, rb0[u], rb1[u]);
-                ln[u] = __ldg(d.len + (g * W + m0 + u) * 32 + lane);
-            }
+            Rec A, B;
+            ld_rec(R + 4 * (int64_t)j0, A.a0, A.a1);
+            ld_rec(R + 4 * (int64_t)j0 + 2, A.b0, A.b1);
+            ld_rec(R + 4 * (int64_t)j1, B.a0, B.a1);
+            ld_rec(R + 4 * (int64_t)j1 + 2, B.b0, B.b1);
+            const float2 lA = __ldg(d.len + (g * W + m0) * 32 + lane);
+            const float2 lB = __ldg(d.len + (g * W + m0 + 1) * 32 + lane);
             const uint32_t wb = word >> b0;
-            uint32_t pc = 0u;
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const bool alive = (wb >> u) & 1u;
-                const BondDw bd = bond_dw<UW>(own, ra0[u], ra1[u], rb0[u], rb1[u], ln[u]);
-                const bool cand = bd.s.h >= d.fast_lo;
-                pc |= cand ? (1u << u) : 0u;
-                const bool ok = alive && !cand;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const Dw t = two_sum(Fh[k], ok ? bd.f[k].h : 0.0f);
-                    Fh[k] = t.h;
-                    Fl[k] += t.l + (ok ? bd.f[k].l : 0.0f);
-                }
-                if (UW) {
-                    alive_count += ok ? 1 : 0;
-                } else {
-                    const Dw t = two_sum(wsh, ok ? ra1[u].z : 0.0f);
-                    wsh = t.h;
-                    wsl += t.l + (ok ? ra1[u].w : 0.0f);
-                }
+            const BondDw bA = bond_dw<UW>(own, A, lA);
+            const BondDw bB = bond_dw<UW>(own, B, lB);
+            const bool candA = bA.s.h >= d.fast_lo, candB = bB.s.h >= d.fast_lo;
+            const bool okA = (wb & 1u) && !candA, okB = ((wb >> 1) & 1u) && !candB;
+            pend |= (((candA ? 1u : 0u) | (candB ? 2u : 0u)) & wb) << b0;
+            add_force(F, bA, okA);
+            add_force(F, bB, okB);
+            if (!UW) {
+                Dw t = two_sum(ws.h, okA ? A.a1.z : 0.0f);
+                ws.h = t.h;
+                ws.l += t.l + (okA ? A.a1.w : 0.0f);
+                t = two_sum(ws.h, okB ? B.a1.z : 0.0f);
+                ws.h = t.h;
+                ws.l += t.l + (okB ? B.a1.w : 0.0f);
             }
-            pend |= (pc & wb) << b0;
-            if (b0 + kUnroll == 32 || c + 1 == nch) {  // end of bond-flag word q
+            if (b0 + 2 == 32 || c + 1 == nch) {  // end of bond-flag word q
                 while (pend) {
                     const int b = __ffs(pend) - 1;
                     pend &= pend - 1u;
@@ -329,24 +314,18 @@ __global__ void __launch_bounds__(256, 2)
                     if (broken) {
                         nword &= ~(1u << b);
                     } else {
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            const Dw t = two_sum(Fh[k], f.f[k].h);
-                            Fh[k] = t.h;
-                            Fl[k] += t.l + f.f[k].l;
-                        }
-                        if (UW) {
-                            ++alive_count;
-                        } else {
+                        add_force(F, f, true);
+                        if (!UW) {
                             float4 c0, c1;
                             ld_rec(R + 4 * j, c0, c1);
-                            const Dw t = two_sum(wsh, c1.z);
-                            wsh = t.h;
-                            wsl += t.l + c1.w;
+                            const Dw t = two_sum(ws.h, c1.z);
+                            ws.h = t.h;
+                            ws.l += t.l + c1.w;
                         }
                     }
                 }
                 if (nword != word) bw[q * 32] = nword;
+                alive_count += __popc(nword);
             }
         }
 
@@ -356,16 +335,16 @@ __global__ void __launch_bounds__(256, 2)
             uint32_t mask = 0u;
             double gdisp[3] = {0.0, 0.0, 0.0};
             const double wscale = UW ? d.w_const : 1.0;
-            double F[3];
+            double Fn[3];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) F[k] = ((double)Fh[k] + (double)Fl[k]) * wscale;
+            for (int k = 0; k < 3; ++k) Fn[k] = ((double)F[k].h + (double)F[k].l) * wscale;
             if (cls != 0u) {
                 const BcClass& bc = a.bct[cls];
                 mask = bc.mask;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     gdisp[k] = bc.disp[k];
-                    F[k] += a.load * bc.force[k];
+                    Fn[k] += a.load * bc.force[k];
                 }
             }
             const double s_now = bc_scale(a.disp_rate, a.ramp_steps, step);
@@ -378,7 +357,7 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const double vi = a.v[3 * i + k];
-                double vn = vi + (F[k] - a.eta * vi) * d.dt_rho;
+                double vn = vi + (Fn[k] - a.eta * vi) * d.dt_rho;
                 double u = uo[k] + a.dt * vn;
                 if (mask & (1u << k)) {
                     u = gdisp[k] * s_next;
@@ -395,13 +374,14 @@ __global__ void __launch_bounds__(256, 2)
             rout[4 * i + 1] = rin[4 * i + 1];
             rout[4 * i + 2] = make_double2(un[0], un[1]);
             rout[4 * i + 3] = make_double2(un[2], 0.0);
-            st_rec(Rout + 4 * i, make_float4(own.xh[0], own.xh[1], own.xh[2], uh[0]),
-                   make_float4(uh[1], uh[2], oa1.z, oa1.w));
-            st_rec(Rout + 4 * i + 2, make_float4(own.xl[0], own.xl[1], own.xl[2], ul[0]),
+            st_rec(Rout + 4 * i, make_float4(me.a0.x, me.a0.y, me.a0.z, uh[0]),
+                   make_float4(uh[1], uh[2], me.a1.z, me.a1.w));
+            st_rec(Rout + 4 * i + 2, make_float4(me.b0.x, me.b0.y, me.b0.z, ul[0]),
                    make_float4(ul[1], ul[2], 0.0f, 0.0f));
-            const double ws = UW ? d.w_const * (double)alive_count : (double)wsh + (double)wsl;
+            const double wsum = UW ? d.w_const * (double)alive_count
+                                   : (double)ws.h + (double)ws.l;
             const double wi = a.wsum_inv[i];
-            a.damage[i] = wi > 0.0 ? fmax(0.0, 1.0 - ws * wi) : 0.0;
+            a.damage[i] = wi > 0.0 ? fmax(0.0, 1.0 - wsum * wi) : 0.0;
             if (!finite) atomicOr(a.err, PD_DEVERR_NONFINITE);
         }
     }
@@ -444,11 +424,10 @@ __global__ void k_dw_len(const double* __restrict__ x64, const int32_t* __restri
          p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t g = p >> 5;
         const int lane = (int)(p & 31);
-        const int Wg = sw[g];
-        for (int m = 0; m < Wg; ++m) {
+        for (int m = 0; m < W; ++m) {
             const int64_t slot = (g * W + m) * 32 + lane;
             const int64_t j = nbr[slot];
-            float2 v = make_float2(0.0f, 0.0f);
+            float2 v = make_float2(1.0f, 0.0f);  // no bond: a finite placeholder
             if (j != p) {
                 const double ex = x64[3 * j] - x64[3 * p], ey = x64[3 * j + 1] - x64[3 * p + 1],
                              ez = x64[3 * j + 2] - x64[3 * p + 2];
