@@ -736,7 +736,23 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
                 hi[a] = std::max(hi[a], d.coords[3 * i + a]);
             }
         for (int a = 0; a < 3; ++a) gctr[a] = 0.5 * (lo[a] + hi[a]);
-        for (int a = 0; a < 3; ++a) h->dw_origin[a] = gctr[a];
+        if (h->dw) {
+            // double-word positions start B horizons above zero, B above the
+            // largest coordinate difference of any bond: then for every bond
+            // x_j / x_i is in [1/2, 2] per component, and the difference of the
+            // leading words is exact (Sterbenz)
+            double maxd = 0.0;
+            const int64_t* off = h->off.data();
+            const int32_t* idx = h->idx.data();
+#pragma omp parallel for reduction(max : maxd) schedule(static)
+            for (int64_t i = 0; i < n; ++i)
+                for (int64_t k = off[i]; k < off[i + 1]; ++k)
+                    for (int a = 0; a < 3; ++a)
+                        maxd = std::max(maxd, std::fabs(d.coords[3 * (int64_t)idx[k] + a] -
+                                                        d.coords[3 * i + a]));
+            const double B = std::ceil(maxd / d.unit) + 1.0;
+            for (int a = 0; a < 3; ++a) h->dw_origin[a] = lo[a] - B * d.unit;
+        }
     }
     std::vector<double> xs(3 * np, 0.0), vs(np, 0.0), cs(3 * np, 0.0);
     std::vector<uint8_t> clsp(np, 0);

@@ -16,8 +16,12 @@
 // and integrates in FP64; what neighbours read is a 64-byte double-word copy
 //   {xh.x, xh.y, xh.z, uh.x} {uh.y, uh.z, wh, wl} {xl.x, xl.y, xl.z, ul.x} {ul.y, ul.z, 0, 0}
 // with positions x~ = (x - origin) / delta and u~ = u / delta in units of the
-// horizon and w = c V, read as two 256-bit loads.  The reference length
-// |xi| / delta of each slot is a double-word computed once in FP64.
+// horizon and w = c V, read as two 256-bit loads.  The origin puts every
+// position component at least B horizons above zero, B above the largest
+// component of any bond, so the leading words of two bonded positions are
+// within a factor 2 and their difference is exact (Sterbenz's lemma).  The
+// reference length |xi| / delta of each slot is a double-word computed once
+// in FP64.
 //
 // Per bond, with xi and eta the double-word differences (exact leading
 // parts): y = xi + eta, num = eta . (2 xi + eta) = |y|^2 - |xi|^2 without
@@ -161,9 +165,10 @@ __device__ __forceinline__ BondDw bond_dw(const OwnDw& o, const Rec& j, const fl
     Dw nm[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        // xi = x_j - x_i and eta = u_j - u_i, the leading differences exact
-        Dw xi = two_sum(jxh[c], -o.xh[c]);
-        xi.l += jxl[c] - o.xl[c];
+        // xi = x_j - x_i and eta = u_j - u_i, the leading differences exact: for
+        // positions by construction of their origin (Sterbenz), for
+        // displacements by a two-sum
+        const Dw xi{jxh[c] - o.xh[c], jxl[c] - o.xl[c]};
         Dw et = two_sum(juh[c], -o.uh[c]);
         et.l += jul[c] - o.ul[c];
         out.y[c] = dw_add(xi, et);
