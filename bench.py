@@ -56,7 +56,24 @@ FP64_PEAK_TFLOPS = 1.20
 # 5; root 1; e 1; t_ij 5; t_ji 8; the sum, V / |y| 3; accumulation 6 = 38):
 # 57 flops per bond.
 OSB_FLOPS_PER_BOND = 57.0
-STEP_SRC = {32: "pd_step_f32.cu", 64: "pd_step_f64.cu"}
+# The double-word step (precision 48) is bound by the FP32 pipe.  FP32
+# operations per bond of its arithmetic (pd_step_dw.cu, uniform weights; an add,
+# multiply or fused multiply-add each counted once): xi 2, eta 8, y 8 and
+# 2 xi + eta 8 and their product 4 per component (90); the sum num 16; L^2 and
+# |y|^2 12; the refined 1/|y| seed 4, |y| 5, 1/|y| 3; den 12; the quotient 10;
+# s / |y| 4; the force term and its double-word accumulation 12 per component
+# (36) = 192, plus two hardware reciprocal(-square-root) seeds.  Peak: FP32 FMA
+# lane rate measured by a probe on this machine's GB300, 35.1 T/s (70.2 TFLOP/s
+# counting an FMA as two).
+DW_FP32_OPS_PER_BOND = 192.0
+FP32_PEAK_TOPS = 35.1
+# per node: the double-word record 64 B read + 64 B written, the FP64 record
+# (x, w copied, u) 56 B read + 56 B written, FP64 velocity 24 + 24 B, damage
+# 8 B, wsum_inv 8 B, BC class 1 B; per bond 8 B of double-word |xi| on top
+BYTES_PER_NODE[48] = 305.0
+DW_BYTES_PER_BOND = BYTES_PER_BOND + 8.0
+STEP_SRC = {32: "pd_step_f32.cu", 64: "pd_step_f64.cu", 48: "pd_step_dw.cu"}
+STEP_TAG = {32: "f32", 64: "f64", 48: "dw"}
 
 
 def parse():
@@ -77,7 +94,8 @@ def parse():
                    help="ordinary state-based linear solid with Poisson's ratio NU (FP64)")
     p.add_argument("--fd-directions", type=int, default=32)
     p.add_argument("--checkpoint-every", type=int, default=45)
-    p.add_argument("--precision", type=int, default=32, choices=[32, 64])
+    p.add_argument("--precision", type=int, default=32, choices=[32, 64, 48],
+                   help="32: FP32 bonds; 64: FP64; 48: FP64-grade double-word FP32 bonds")
     p.add_argument("--graph-steps", type=int, default=50)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -103,7 +121,8 @@ def describe(w, n_bonds, precision, integrator="ec"):
         "workload": f"{w.name}: {w.n:,} nodes, {n_bonds:,} directed bonds, "
                     f"delta = {w.horizon / w.dx:.4g} dx, "
                     + ("per-bond s_c ~ U[9e-5, 1.1e-4)" if w.sc_hash else f"s_c = {w.sc:g}"),
-        "precision": "fp32 bonds, fp64 displacement" if precision == 32 else "fp64",
+        "precision": {32: "fp32 bonds, fp64 displacement", 64: "fp64",
+                      48: "fp64-grade: double-word fp32 bonds, fp64 node state"}[precision],
         "n_nodes": w.n,
         "n_bonds": int(n_bonds),
         "l2_policy": "inputs larger than L2 (padded family index > 129 MB streamed per step)",
@@ -222,7 +241,7 @@ def profiled_traffic(precision, workload):
     current kernel source (matched by hash); else None."""
     src = os.path.join(ROOT, "paper_2105_04150_gb300", "csrc", STEP_SRC[precision])
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    path = os.path.join(ROOT, "profiles", f"step_f{precision}_{workload}_traffic.txt")
+    path = os.path.join(ROOT, "profiles", f"step_{STEP_TAG[precision]}_{workload}_traffic.txt")
     try:
         kv = dict(l.split(None, 1) for l in open(path) if l.strip() and not l.startswith("#"))
         if kv.get("kernel_source_sha256_16", "").strip() == sha:
@@ -372,6 +391,8 @@ def run_ours(args):
     value = whole_job(n_bonds * args.steps, ms_max, world)
     # softening adds the per-bond integrity read every step (FP32 4 B, FP64 8 B)
     per_bond = BYTES_PER_BOND + ((4.0 if args.precision == 32 else 8.0) if args.kr else 0.0)
+    if args.precision == 48:
+        per_bond = DW_BYTES_PER_BOND
     alg_bytes = n_bonds * per_bond + w.n * BYTES_PER_NODE[args.precision]
     peak, peak_kind = hbm_peak()
     achieved = alg_bytes / (ms_step * 1e-3) / 1e9
@@ -395,6 +416,22 @@ def run_ours(args):
                             "frac": achieved / peak},
                     "kernel": "k_osb_dilation + k_osb_force" if args.state_based is not None
                     else "k_step_f64"}
+    if args.precision == 48:
+        tops = DW_FP32_OPS_PER_BOND * n_bonds / (ms_step * 1e-3) / 1e12
+        tf64 = FP64_FLOPS_PER_BOND * n_bonds / (ms_step * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": tops, "peak": FP32_PEAK_TOPS, "unit": "TFLOP/s",
+                    "frac": tops / FP32_PEAK_TOPS,
+                    "traffic": profiled_traffic(48, args.workload),
+                    "peak_source": "FP32 operations (add, multiply or fma each counted once) "
+                                   "against the FP32 FMA lane rate measured by a probe on this "
+                                   "pool's GB300 (70.2 TFLOP/s counting an FMA as two)",
+                    "algorithmic_flops_per_bond": DW_FP32_OPS_PER_BOND,
+                    "fp64_equivalent": {"achieved": tf64, "peak": FP64_PEAK_TFLOPS,
+                                        "unit": "TFLOP/s", "frac": tf64 / FP64_PEAK_TFLOPS,
+                                        "flops_per_bond": FP64_FLOPS_PER_BOND},
+                    "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak},
+                    "kernel": "k_step_dw"}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -412,7 +449,8 @@ def run_ours(args):
         "metric": "bond updates/s", "value": value, "unit": "bond updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "time_steps_per_s": 1e3 / ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if args.precision == 32 else "f64",
+        "vs_baseline": None,
+        "dtype": {32: "f32", 64: "f64", 48: "f32 double-word"}[args.precision],
         "data": "synthetic", "config": describe(w, n_bonds, args.precision, args.integrator),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk.summary(t_on, t_off),
@@ -624,6 +662,9 @@ def run_adjoint(args):
 
 def main():
     args = parse()
+    if args.precision == 48 and (args.workload in ("batch", "adjoint") or args.kr
+                                 or args.state_based is not None or args.integrator != "ec"):
+        raise SystemExit("--precision 48 runs single PMB models with the Euler-Cromer integrator")
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":

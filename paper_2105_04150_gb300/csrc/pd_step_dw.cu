@@ -43,6 +43,9 @@ namespace {
 #ifndef PD_DW_MIN_BLOCKS
 #define PD_DW_MIN_BLOCKS 2
 #endif
+#ifndef PD_DW_PREFETCH
+#define PD_DW_PREFETCH 1
+#endif
 
 __device__ __forceinline__ uint64_t splitmix_out(uint64_t seed, uint64_t m)
 {
@@ -285,6 +288,7 @@ __global__ void __launch_bounds__(256, PD_DW_MIN_BLOCKS)
                 jn0 = __ldg(col + (m0 + 2) * 32);
                 jn1 = __ldg(col + (m0 + 3) * 32);
             }
+
             Rec A, B;
             ld_rec(R + 4 * (int64_t)j0, A.a0, A.a1);
             ld_rec(R + 4 * (int64_t)j0 + 2, A.b0, A.b1);
@@ -298,6 +302,11 @@ __global__ void __launch_bounds__(256, PD_DW_MIN_BLOCKS)
             const bool candA = bA.s.h >= d.fast_lo, candB = bB.s.h >= d.fast_lo;
             const bool okA = (wb & 1u) && !candA, okB = ((wb >> 1) & 1u) && !candB;
             pend |= (((candA ? 1u : 0u) | (candB ? 2u : 0u)) & wb) << b0;
+#if PD_DW_PREFETCH
+            // the next chunk's records start toward L1 (their ids have arrived by now)
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(R + 4 * (int64_t)jn0));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(R + 4 * (int64_t)jn1));
+#endif
             add_force(F, bA, okA);
             add_force(F, bB, okB);
             if (!UW) {
