@@ -58,9 +58,10 @@ typedef enum {
                             unevaluated sum of two FP32 numbers (~48-bit significand,
                             bond-force relative error ~1e-13), and the break test
                             decided against the FP64 s_c.  Single models with the
-                            Euler-Cromer integrator and the PMB law only: no batches,
-                            per-bond stiffness, softening, state-based model or
-                            adjoint (those calls return PD_ERR_ARG / PD_ERR_STATE).
+                            Euler-Cromer integrator and the PMB law (per-bond
+                            stiffness included): no batches, softening or
+                            state-based model (PD_ERR_ARG).  The adjoint records
+                            and recomputes its forward runs with this step.
                             pd_get_info reports 48. */
 #define PD_MAX_FAMILY 1024
 #define PD_MAX_BC_CLASSES 256

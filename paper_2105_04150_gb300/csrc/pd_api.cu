@@ -119,6 +119,7 @@ struct pd_handle {
     bool dw = false;
     float4* recdw[2] = {nullptr, nullptr};  // double-word copies of the records
     float2* lendw = nullptr;                // per slot |xi| / delta
+    float2* cbdw = nullptr;                 // per slot c_ij (per-bond stiffness)
     double dw_origin[3] = {0.0, 0.0, 0.0};  // origin of the double-word positions
     int integrator = PD_INTEGRATOR_EC;
     int64_t ramp_steps = 0;
@@ -347,12 +348,14 @@ DwArgs dw_args(pd_handle* h)
     d.rec[0] = h->recdw[0];
     d.rec[1] = h->recdw[1];
     d.len = h->lendw;
+    d.cb = h->per_bond_c ? h->cbdw : nullptr;
     d.inv_delta = 1.0 / h->delta;
-    d.w_const = h->c * h->vol0;
+    d.w_const = (h->per_bond_c ? 1.0 : h->c) * h->vol0;
     d.dt_rho = h->dt / h->rho;
     // the leading word of a double-word stretch is within 2^-23 of it: below
     // this band the break test cannot be near any s_c of the model
-    d.fast_lo = (float)((1.0 - 0x1.0p-20) * (h->sc_mode == 0 ? h->sc : h->sc_lo));
+    d.fast_lo = h->frozen ? INFINITY
+                          : (float)((1.0 - 0x1.0p-20) * (h->sc_mode == 0 ? h->sc : h->sc_lo));
     d.uniform_w = h->uniform_vol ? 1 : 0;
     return d;
 }
@@ -671,9 +674,8 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
             ALLOC(h->recdw[0], float4, 4 * np);
             ALLOC(h->recdw[1], float4, 4 * np);
             ALLOC(h->lendw, float2, nbr.size());
-        } else {
-            ALLOC(h->ilen, double, nbr.size());
         }
+        ALLOC(h->ilen, double, nbr.size());  // also the adjoint's
     }
     if (h->model == 1) {
         if (h->integrator != PD_INTEGRATOR_EC)
@@ -817,7 +819,7 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
                      "upload instance table")))
             return st;
     }
-    if (!f32 && !h->dw) {
+    if (!f32) {
         e = launch_inv_len(h->x64, h->nbr, h->sw, n, h->Q, h->ilen, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "bond lengths");
     }
@@ -1342,8 +1344,8 @@ pd_status pd_damage(pd_handle* h, double* phi)
 pd_status pd_adjoint_forward(pd_handle* h, int64_t n_steps, int64_t checkpoint_every)
 {
     if (!h) return fail(PD_ERR_ARG, "NULL handle");
-    if (h->precision != 64 || h->dw || h->batch || h->integrator != PD_INTEGRATOR_EC ||
-        h->integ || h->model != 0)
+    if (h->precision != 64 || h->batch || h->integrator != PD_INTEGRATOR_EC || h->integ ||
+        h->model != 0)
         return fail(PD_ERR_STATE,
                     "the adjoint is available on FP64 single-model Euler-Cromer PMB handles");
     if (n_steps < 1 || checkpoint_every < 0)
@@ -1489,6 +1491,9 @@ pd_status pd_adjoint_backward(pd_handle* h, const double* dLdu, const double* dL
         if (ke == cudaSuccess) ke = cudaStreamSynchronize(h->stream);
         const int cur = (int)(h->step & 1);
         if (ke == cudaSuccess) ke = launch_insert_u(T.ck_u + k * np3, h->n_pad, h->rec[cur], h->stream);
+        if (ke == cudaSuccess && h->dw)
+            ke = launch_dw_publish(h->rec[cur], h->recdw[cur], h->n_pad, h->dw_origin,
+                                   1.0 / h->delta, h->stream);
         if (ke == cudaSuccess)
             ke = cudaMemcpyAsync(h->v, T.ck_v + k * np3, 8 * np3, cudaMemcpyDeviceToDevice, h->stream);
         if (ke == cudaSuccess)
@@ -1522,6 +1527,9 @@ pd_status pd_adjoint_backward(pd_handle* h, const double* dLdu, const double* dL
                              h->stream);
     if (ke == cudaSuccess) ke = cudaStreamSynchronize(h->stream);
     if (ke == cudaSuccess) ke = launch_insert_u(T.fin_u, h->n_pad, h->rec[h->step & 1], h->stream);
+    if (ke == cudaSuccess && h->dw)
+        ke = launch_dw_publish(h->rec[h->step & 1], h->recdw[h->step & 1], h->n_pad, h->dw_origin,
+                               1.0 / h->delta, h->stream);
     if (ke == cudaSuccess)
         ke = cudaMemcpyAsync(h->v, T.fin_v, 8 * np3, cudaMemcpyDeviceToDevice, h->stream);
     h->damage_fresh = false;
@@ -1667,8 +1675,6 @@ pd_status pd_set_params(pd_handle* h, double c, double sc, double load, double d
     if (h->batch) return fail(PD_ERR_STATE, "pd_set_params is not available on a batch handle");
     if (h->model == 1 && c_bond)
         return fail(PD_ERR_STATE, "per-bond stiffness is not available with the state-based model");
-    if (h->dw && c_bond)
-        return fail(PD_ERR_STATE, "per-bond stiffness is not available with PD_PREC_DW");
     if (!(c > 0.0) || !std::isfinite(c)) return fail(PD_ERR_ARG, "c must be > 0");
     if (!(sc > 0.0) || !std::isfinite(sc)) return fail(PD_ERR_ARG, "sc must be > 0");
     if (!std::isfinite(load) || !std::isfinite(disp_rate))
@@ -1698,6 +1704,14 @@ pd_status pd_set_params(pd_handle* h, double c, double sc, double load, double d
                 if (pos[s] >= 0) cb[s] = c_bond[pos[s]];
             PD_CUDA(cudaMemcpy(h->cbond, cb.data(), slots * 8, cudaMemcpyHostToDevice),
                     "upload c_bond");
+            if (h->dw) {
+                if (!h->cbdw) {
+                    cudaError_t e = h->alloc(&h->cbdw, slots);
+                    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc c_bond");
+                }
+                PD_CUDA(launch_dw_split((const double*)h->cbond, (int64_t)slots, h->cbdw, h->stream),
+                        "double-word c_bond");
+            }
         }
     }
     const bool pbc = c_bond != nullptr;
@@ -1869,6 +1883,9 @@ pd_status pd_adjoint_backward_static(pd_handle* h, const double* dLdu, const dou
         if (ke == cudaSuccess) ke = cudaStreamSynchronize(h->stream);
         const int cur = (int)(h->step & 1);
         if (ke == cudaSuccess) ke = launch_insert_u(T.ck_u + k * np3, h->n_pad, h->rec[cur], h->stream);
+        if (ke == cudaSuccess && h->dw)
+            ke = launch_dw_publish(h->rec[cur], h->recdw[cur], h->n_pad, h->dw_origin,
+                                   1.0 / h->delta, h->stream);
         if (ke == cudaSuccess)
             ke = cudaMemcpyAsync(h->v, T.ck_v + k * np3, 8 * np3, cudaMemcpyDeviceToDevice, h->stream);
         if (ke == cudaSuccess)
@@ -1899,6 +1916,9 @@ pd_status pd_adjoint_backward_static(pd_handle* h, const double* dLdu, const dou
                              h->stream);
     if (ke == cudaSuccess) ke = cudaStreamSynchronize(h->stream);
     if (ke == cudaSuccess) ke = launch_insert_u(T.fin_u, h->n_pad, h->rec[h->step & 1], h->stream);
+    if (ke == cudaSuccess && h->dw)
+        ke = launch_dw_publish(h->rec[h->step & 1], h->recdw[h->step & 1], h->n_pad, h->dw_origin,
+                               1.0 / h->delta, h->stream);
     if (ke == cudaSuccess)
         ke = cudaMemcpyAsync(h->v, T.fin_v, 8 * np3, cudaMemcpyDeviceToDevice, h->stream);
     h->damage_fresh = false;

@@ -142,10 +142,12 @@ struct StepArgsF64 {
 struct DwArgs {
     const float4* rec[2];      // 4 float4 per node, double buffered like the FP64 records
     const float2* len;         // per slot |xi| / delta as a double-word (hi, lo)
+    const float2* cb;          // per slot stiffness c_ij as a double-word, or nullptr
     double inv_delta;          // 1 / delta
     double w_const;            // c V when the node weights are uniform
     double dt_rho;             // dt / rho
     float fast_lo;             // leading stretch words below this are decided without s_c
+                               // (+inf while the bond flags are frozen)
     int32_t uniform_w;         // 1: every node has weight w_const
 };
 
@@ -241,6 +243,8 @@ cudaError_t launch_dw_publish(const double* rec64, float4* rec, int64_t n_pad, c
                               double inv_delta, cudaStream_t s);
 cudaError_t launch_dw_len(const double* x64, const int32_t* nbr, const int32_t* sw, int64_t n, int Q,
                           double inv_delta, float2* len, cudaStream_t s);
+// double-word copy of an FP64 per-slot array
+cudaError_t launch_dw_split(const double* in, int64_t count, float2* out, cudaStream_t s);
 
 // ---- helper kernels (pd_aux.cu) ---------------------------------------------
 cudaError_t launch_advance(int64_t* step_ctr, int64_t k, cudaStream_t s);

@@ -203,6 +203,12 @@ __device__ __forceinline__ BondDw bond_dw(const OwnDw& o, const Rec& j, const fl
     return out;
 }
 
+// per-bond stiffness c_ij (a double-word per slot) on the coefficient
+__device__ __forceinline__ void scale_coef(BondDw& b, const float2 c)
+{
+    b.coef = dw_mul(b.coef, Dw{c.x, c.y});
+}
+
 // F += coef y when `ok` (a select: whatever a masked slot computed, including
 // a non-finite value, is dropped)
 __device__ __forceinline__ void add_force(Dw (&F)[3], const BondDw& b, bool ok)
@@ -230,7 +236,8 @@ __device__ __noinline__ BondDw resolve_dw(const StepArgsF64& a, const DwArgs& d,
     ld_rec(R + 4 * i + 2, own.b0, own.b1);
     ld_rec(R + 4 * j, nb.a0, nb.a1);
     ld_rec(R + 4 * j + 2, nb.b0, nb.b1);
-    const BondDw bd = bond_dw<UW>(own_of(own), nb, d.len[slot]);
+    BondDw bd = bond_dw<UW>(own_of(own), nb, d.len[slot]);
+    if (d.cb != nullptr) scale_coef(bd, d.cb[slot]);
     const double sc = SCM == 0 ? a.sc : sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i], a.gid[j]);
     bool brk = (double)bd.s.h + (double)bd.s.l >= sc;
     if (brk && a.has_nofail) brk = ((a.bct[a.bcc[i]].mask | a.bct[a.bcc[j]].mask) & 8u) == 0u;
@@ -297,8 +304,12 @@ __global__ void __launch_bounds__(256, PD_DW_MIN_BLOCKS)
             const float2 lA = __ldg(d.len + (g * W + m0) * 32 + lane);
             const float2 lB = __ldg(d.len + (g * W + m0 + 1) * 32 + lane);
             const uint32_t wb = word >> b0;
-            const BondDw bA = bond_dw<UW>(own, A, lA);
-            const BondDw bB = bond_dw<UW>(own, B, lB);
+            BondDw bA = bond_dw<UW>(own, A, lA);
+            BondDw bB = bond_dw<UW>(own, B, lB);
+            if (d.cb != nullptr) {  // per-bond stiffness (a uniform branch)
+                scale_coef(bA, __ldg(d.cb + (g * W + m0) * 32 + lane));
+                scale_coef(bB, __ldg(d.cb + (g * W + m0 + 1) * 32 + lane));
+            }
             const bool candA = bA.s.h >= d.fast_lo, candB = bB.s.h >= d.fast_lo;
             const bool okA = (wb & 1u) && !candA, okB = ((wb >> 1) & 1u) && !candB;
             pend |= (((candA ? 1u : 0u) | (candB ? 2u : 0u)) & wb) << b0;
@@ -454,6 +465,15 @@ __global__ void k_dw_len(const double* __restrict__ x64, const int32_t* __restri
     }
 }
 
+__global__ void k_dw_split(const double* __restrict__ in, int64_t count, float2* __restrict__ out)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const float h = (float)in[k];
+        out[k] = make_float2(h, (float)(in[k] - (double)h));
+    }
+}
+
 int grid_of(int64_t work)
 {
     const int64_t b = (work + 255) / 256;
@@ -494,6 +514,12 @@ cudaError_t launch_dw_len(const double* x64, const int32_t* nbr, const int32_t* 
                           double inv_delta, float2* len, cudaStream_t s)
 {
     k_dw_len<<<grid_of(((n + 31) >> 5) << 5), 256, 0, s>>>(x64, nbr, sw, n, Q, inv_delta, len);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dw_split(const double* in, int64_t count, float2* out, cudaStream_t s)
+{
+    k_dw_split<<<grid_of(count), 256, 0, s>>>(in, count, out);
     return cudaGetLastError();
 }
 

@@ -186,15 +186,60 @@ def test_unsupported_combinations_are_refused():
             pdgb.Model.from_workload(w2, precision=DW, c=c)
     with pytest.raises(pdgb.PdError):
         pdgb.Model.batch([w, w], precision=DW)
-    m = pdgb.Model.from_workload(w, precision=DW, c=c)
-    off, _ = m.family()
-    with pytest.raises(pdgb.PdError) as e:
-        m.set_params(c, w.sc, w.load, w.disp_rate, np.full(off[-1], c))
-    assert e.value.name == "PD_ERR_STATE"
-    with pytest.raises(pdgb.PdError) as e:
-        pdgb.pd_adjoint_forward(m.h, 5)
-    assert e.value.name == "PD_ERR_STATE"
+
+
+def _grf_stiffness(w, off, idx, c0, seed=2105041505):
+    om, ph = workloads.grf_params(seed, 5 * w.dx)
+    rows = np.repeat(np.arange(w.n), np.diff(off))
+    return c0 * (1.0 + 0.1 * workloads.grf_eval(0.5 * (w.coords[rows] + w.coords[idx]), om, ph))
+
+
+def test_per_bond_stiffness_matches_oracle():
+    w = workloads.cracked_plate_force(30, 16, 4, load=2e11, steps=120)
+    off, idx = oracle.cut_family(w.coords, w.horizon, w.cuts_array())
+    c0 = oracle.micromodulus(w.bulk_modulus, w.horizon)
+    cb = _grf_stiffness(w, off, idx, c0)
+    om = oracle.Model.from_workload(w, off, idx, c=c0, c_bond=cb)
+    u = np.zeros((w.n, 3)); v = np.zeros((w.n, 3)); mu = om.fresh_bonds()
+    om.run(0, w.steps, u, v, mu)
+    m = pdgb.Model.from_workload(w, precision=DW, c=c0, graph_steps=10)
+    m.set_params(c0, w.sc, w.load, w.disp_rate, cb)
+    m.step(w.steps)
+    ug, vg = m.state()
     m.close()
+    assert np.abs(u).max() > 0
+    assert rel(ug, u) <= 1e-10 and rel(vg, v) <= 1e-9
+
+
+def test_adjoint_on_a_double_word_handle_matches_oracle_reverse_mode():
+    # the adjoint's recorded and recomputed forward runs use the double-word
+    # step; the reverse sweep is the FP64 one
+    w = workloads.cracked_plate_force(16, 10, 3, load=3e11, steps=60)
+    w.sc = 1.0
+    off, idx = oracle.cut_family(w.coords, w.horizon, w.cuts_array())
+    c0 = oracle.micromodulus(w.bulk_modulus, w.horizon)
+    cb = _grf_stiffness(w, off, idx, c0, seed=2105041506)
+    rows = np.repeat(np.arange(w.n), np.diff(off))
+    key = {(int(i), int(j)): q for q, (i, j) in enumerate(zip(rows, idx))}
+    cb = 0.5 * (cb + cb[[key[(int(j), int(i))] for i, j in zip(rows, idx)]])
+    u0, v0 = workloads.random_state(w.n, 3, 1e-7, 1e-3)
+    rng = np.random.default_rng(1)
+    gu = rng.standard_normal((w.n, 3))
+    gv = rng.standard_normal((w.n, 3)) * 1e-7
+    om = oracle.Model.from_workload(w, off, idx, c=c0, c_bond=cb)
+    gc_o, gl_o, gu_o, gv_o = oracle.adjoint(om, 0, w.steps, u0, v0, om.fresh_bonds(), gu, gv)
+    m = pdgb.Model.from_workload(w, precision=DW, c=c0)
+    m.set_params(c0, w.sc, w.load, w.disp_rate, cb)
+    m.set_state(u0, v0, step=0)
+    pdgb.pd_adjoint_forward(m.h, w.steps, 7)
+    uN, vN = m.state()
+    gc, gl, gu0, gv0 = pdgb.pd_adjoint_backward(m.h, gu, gv)
+    uA, vA = m.state()
+    m.close()
+    assert np.array_equal(uN, uA) and np.array_equal(vN, vA)
+    assert rel(gc, gc_o) <= 1e-9
+    assert abs(gl - gl_o) <= 1e-9 * abs(gl_o)
+    assert rel(gu0, gu_o) <= 1e-9 and rel(gv0, gv_o) <= 1e-9
 
 
 def test_full_size_notched_beam_sampled_one_step():
