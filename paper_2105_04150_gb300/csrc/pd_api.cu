@@ -153,6 +153,10 @@ struct pd_handle {
         double *ub[2] = {nullptr, nullptr}, *vb[2] = {nullptr, nullptr}, *ubm = nullptr,
                *w = nullptr, *gc = nullptr, *gl = nullptr, *partial = nullptr, *out = nullptr;
         int n_partial = 0;
+        // double-word reverse sweep (PD_PREC_DW): records of u^n and w, and the
+        // per-slot gradient accumulator
+        float4 *rrec = nullptr, *wrec = nullptr;
+        float2* gcdw = nullptr;
     } tape;
     // batches: instance of each node, instance-local ids, per-instance s_c table
     bool batch = false;
@@ -1432,6 +1436,12 @@ pd_status pd_adjoint_backward(pd_handle* h, const double* dLdu, const double* dL
         if ((e = h->alloc(&T.partial, (size_t)T.n_partial)) != cudaSuccess)
             return cuda_fail(e, "cudaMalloc reduction scratch");
     }
+    if (h->dw && !T.gcdw) {
+        if ((e = h->alloc(&T.rrec, (size_t)(4 * h->n_pad))) != cudaSuccess ||
+            (e = h->alloc(&T.wrec, (size_t)(2 * h->n_pad))) != cudaSuccess ||
+            (e = h->alloc(&T.gcdw, (size_t)slots)) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc double-word adjoint buffers");
+    }
     // seed: dL/du^N, dL/dv^N in library order
     auto to_lib = [&](const double* src, double* dst) -> pd_status {
         if (!src) {
@@ -1454,6 +1464,7 @@ pd_status pd_adjoint_backward(pd_handle* h, const double* dLdu, const double* dL
     if ((st = to_lib(dLdu, T.ub[0])) != PD_OK || (st = to_lib(dLdv, T.vb[0])) != PD_OK) return st;
     PD_CUDA(cudaMemsetAsync(T.gc, 0, 8 * slots, h->stream), "memset");
     PD_CUDA(cudaMemsetAsync(T.gl, 0, 8 * h->n_pad, h->stream), "memset");
+    if (h->dw) PD_CUDA(cudaMemsetAsync(T.gcdw, 0, 8 * slots, h->stream), "memset");
 
     int sms = 0;
     PD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "sm count");
@@ -1476,6 +1487,31 @@ pd_status pd_adjoint_backward(pd_handle* h, const double* dLdu, const double* dL
     A.dt_rho = h->dt / h->rho;
     A.damp = 1.0 - h->dt * h->eta / h->rho;
     A.n = h->n;
+    AdjDwArgs D{};
+    if (h->dw) {
+        D.rec = T.rrec;
+        D.wrec = T.wrec;
+        D.len = h->lendw;
+        D.cb = h->per_bond_c ? h->cbdw : nullptr;
+        const float ch = (float)h->c;
+        D.c = make_float2(ch, (float)(h->c - (double)ch));
+        D.gc = T.gcdw;
+        D.w = T.w;
+        D.ubm = T.ubm;
+        D.gl = T.gl;
+        D.nbr = h->nbr;
+        D.bits = h->bits;
+        D.sw = h->sw;
+        D.Q = h->Q;
+        D.uniform_w = h->uniform_vol ? 1 : 0;
+        D.n = h->n;
+        D.bcc = h->bcc;
+        D.bct = h->bct;
+        D.dt_rho = A.dt_rho;
+        D.damp = A.damp;
+        D.inv_delta = 1.0 / h->delta;
+        D.vol0 = h->vol0;
+    }
 
     h->frozen = true;
     h->drop_graph();
@@ -1507,17 +1543,29 @@ pd_status pd_adjoint_backward(pd_handle* h, const double* dLdu, const double* dL
         }
         // reverse through the segment
         for (int64_t t = len - 1; t >= 0 && ke == cudaSuccess; --t) {
-            ke = launch_adj_mask(T.ub[cb], T.vb[cb], h->bcc, h->bct, h->n_pad, h->dt, T.ubm, T.w,
-                                 h->stream);
             A.un = T.seg + t * np3;
             A.w = T.w;
             A.ubm = T.ubm;
             A.ub_out = T.ub[cb ^ 1];
             A.vb_out = T.vb[cb ^ 1];
-            if (ke == cudaSuccess) ke = launch_adj_step(A, agrid, 256, h->stream);
+            if (h->dw) {
+                ke = launch_adj_mask_publish_dw(T.ub[cb], T.vb[cb], h->bcc, h->bct, h->dt,
+                                                h->recdw[0], A.un, h->vol, h->n_pad,
+                                                1.0 / h->delta, T.ubm, T.w, T.rrec, T.wrec,
+                                                h->stream);
+                D.ub_out = A.ub_out;
+                D.vb_out = A.vb_out;
+                if (ke == cudaSuccess) ke = launch_adj_step_dw(D, agrid, 256, h->stream);
+            } else {
+                ke = launch_adj_mask(T.ub[cb], T.vb[cb], h->bcc, h->bct, h->n_pad, h->dt, T.ubm,
+                                     T.w, h->stream);
+                if (ke == cudaSuccess) ke = launch_adj_step(A, agrid, 256, h->stream);
+            }
             cb ^= 1;
         }
     }
+    if (h->dw && ke == cudaSuccess)
+        ke = launch_adj_merge_dw(T.gcdw, slots, A.dt_rho, T.gc, h->stream);
     h->frozen = false;
     h->drop_graph();
     // restore the final state u^N, v^N

@@ -200,6 +200,40 @@ struct AdjArgs {
     int64_t n;
 };
 
+// Reverse step of PD_PREC_DW handles (pd_adjoint_dw.cu): double-word records
+// of u^n and w for the neighbours, FP64 node outputs
+struct AdjDwArgs {
+    const float4* rec;         // 4 float4 per node: positions, u^n / delta, V
+    const float4* wrec;        // 2 float4 per node: w
+    const float2* len;         // per slot |xi| / delta
+    const float2* cb;          // per slot c_ij, or nullptr for the constant c
+    float2 c;                  // the constant c as a double-word
+    float2* gc;                // per slot dL/dc accumulator, without dt/rho
+    const double* w;           // w (FP64)
+    const double* ubm;         // ubar of step n+1, controlled components zeroed
+    double* ub_out;            // ubar^n
+    double* vb_out;            // vbar^n
+    double* gl;                // per-node accumulator of force . w
+    const int32_t* nbr;
+    const uint32_t* bits;      // frozen bond flags
+    const int32_t* sw;
+    int32_t Q;
+    int32_t uniform_w;         // 1: every node has volume vol0
+    int64_t n;
+    const uint8_t* bcc;
+    const BcClass* bct;
+    double dt_rho, damp, inv_delta, vol0;
+};
+
+cudaError_t launch_adj_mask_publish_dw(const double* ub, const double* vb, const uint8_t* bcc,
+                                       const BcClass* bct, double dt, const float4* fwd,
+                                       const double* un, const double* vol, int64_t n_pad,
+                                       double inv_delta, double* ubm, double* w, float4* rec,
+                                       float4* wrec, cudaStream_t s);
+cudaError_t launch_adj_step_dw(const AdjDwArgs& a, int grid, int block, cudaStream_t s);
+cudaError_t launch_adj_merge_dw(const float2* acc, int64_t count, double scale, double* gc,
+                                cudaStream_t s);
+
 cudaError_t launch_adj_mask(const double* ub, const double* vb, const uint8_t* bcc,
                             const BcClass* bct, int64_t n, double dt, double* ubm, double* w,
                             cudaStream_t s);

@@ -35,6 +35,7 @@
 // kernel; the rest of the break test needs no FP64 operation.
 #include <cuda_runtime.h>
 
+#include "pd_dw.h"
 #include "pd_internal.h"
 
 namespace pd {
@@ -69,87 +70,7 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ void ld_rec(const float4* p, float4& a, float4& b)
-{
-    asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z),
-                   "=f"(b.w)
-                 : "l"(p));
-}
-
-__device__ __forceinline__ void st_rec(float4* p, const float4& a, const float4& b)
-{
-    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(a.x),
-                 "f"(a.y), "f"(a.z), "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
-                 : "memory");
-}
-
-// hardware approximations, used only as seeds that are refined below
-__device__ __forceinline__ float rsqrt_seed(float x)
-{
-    float r;
-    asm("rsqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ float rcp_seed(float x)
-{
-    float r;
-    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-// ---- double-word arithmetic.  Values are unevaluated sums h + l; the
-// operations below leave their result unnormalised (|l| up to a few ulp(h))
-// wherever the next operation takes that, which keeps ~46-bit accuracy for
-// far fewer FP32 operations than renormalising after each step.  The FP32
-// pipe is the limit here, so the code is scalar: negated operands cost nothing.
-struct Dw {
-    float h, l;
-};
-
-// exact sum (Knuth)
-__device__ __forceinline__ Dw two_sum(float a, float b)
-{
-    const float s = a + b;
-    const float bb = s - a;
-    return {s, (a - (s - bb)) + (b - bb)};
-}
-
-// a + b: the leading words summed exactly, everything else in FP32
-__device__ __forceinline__ Dw dw_add(Dw a, Dw b)
-{
-    Dw t = two_sum(a.h, b.h);
-    t.l += a.l + b.l;
-    return t;
-}
-
-// a * b: the exact product of the leading words plus the cross terms
-// (Joldes, Muller & Popescu's DWTimesDW without the final renormalisation)
-__device__ __forceinline__ Dw dw_mul(Dw a, Dw b)
-{
-    const float p = a.h * b.h;
-    return {p, fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)))};
-}
-
-// The lane's own record (double-word position and displacement).
-struct OwnDw {
-    float xh[3], xl[3], uh[3], ul[3];
-};
-
-// One neighbour's record as the two 256-bit loads deliver it.
-struct Rec {
-    float4 a0, a1, b0, b1;
-};
-
-__device__ __forceinline__ OwnDw own_of(const Rec& r)
-{
-    OwnDw o;
-    o.xh[0] = r.a0.x; o.xh[1] = r.a0.y; o.xh[2] = r.a0.z;
-    o.uh[0] = r.a0.w; o.uh[1] = r.a1.x; o.uh[2] = r.a1.y;
-    o.xl[0] = r.b0.x; o.xl[1] = r.b0.y; o.xl[2] = r.b0.z;
-    o.ul[0] = r.b0.w; o.ul[1] = r.b1.x; o.ul[2] = r.b1.y;
-    return o;
-}
+using namespace dwa;
 
 struct BondDw {
     Dw s;     // stretch
@@ -183,21 +104,10 @@ __device__ __forceinline__ BondDw bond_dw(const OwnDw& o, const Rec& j, const fl
     num = dw_add(num, nm[2]);
     const Dw L{len.x, len.y};
     const Dw y2 = dw_add(dw_mul(L, L), num);
-    // 1/|y| seed refined once in FP32 (Newton), then |y| and 1/|y| corrected to
-    // double-word accuracy from the residuals
-    float r0 = rsqrt_seed(y2.h);
-    r0 = r0 * fmaf(-(0.5f * y2.h) * r0, r0, 1.5f);
-    const float rh = y2.h * r0;
-    const Dw r{rh, (fmaf(-rh, rh, y2.h) + y2.l) * r0 * 0.5f};
-    const Dw ir{r0, r0 * fmaf(-r.l, r0, fmaf(-r.h, r0, 1.0f))};
+    Dw r, ir;
+    dw_norm(y2, r, ir);
     // s = num / den, den = L (L + |y|): FP32 quotient plus the remainder's
-    const Dw den = dw_mul(L, dw_add(L, r));
-    float q = rcp_seed(den.h);
-    q = fmaf(q, fmaf(-den.h, q, 1.0f), q);
-    const float q0 = num.h * q;
-    const float ph = den.h * q0;
-    const float pl = fmaf(den.l, q0, fmaf(den.h, q0, -ph));
-    out.s = Dw{q0, (((num.h - ph) - pl) + num.l) * q};
+    out.s = dw_div(num, dw_mul(L, dw_add(L, r)));
     out.coef = dw_mul(out.s, ir);
     if (!UW) out.coef = dw_mul(out.coef, Dw{j.a1.z, j.a1.w});
     return out;

@@ -242,6 +242,34 @@ def test_adjoint_on_a_double_word_handle_matches_oracle_reverse_mode():
     assert rel(gu0, gu_o) <= 1e-9 and rel(gv0, gv_o) <= 1e-9
 
 
+def test_adjoint_gradient_of_small_stretches_equals_fp64_handle():
+    # from rest under a force load the stretches stay small for many steps: the
+    # double-word reverse step must keep s accurate in absolute terms (a form
+    # like |y| / L - 1 loses it to the positions' rounding)
+    w = workloads.cracked_plate_force(40, 16, 4, load=8e6, steps=300)
+    c0 = oracle.micromodulus(w.bulk_modulus, w.horizon)
+    off, idx = oracle.cut_family(w.coords, w.horizon, w.cuts_array())
+    cb = workloads.bond_stiffness_grf(w, off, idx, c0)
+    above, below = workloads.mouth_nodes(w)
+    out = {}
+    for prec in (F64, DW):
+        m = pdgb.Model.from_workload(w, precision=prec, c=c0)
+        m.set_params(c0, w.sc, w.load, w.disp_rate, cb)
+        pdgb.pd_adjoint_forward(m.h, w.steps, 17)
+        u, _ = m.state()
+        gu = np.zeros((w.n, 3))
+        cmod = u[above, 1].mean() - u[below, 1].mean()
+        gu[above, 1] = 2 * cmod / len(above)
+        gu[below, 1] = -2 * cmod / len(below)
+        out[prec] = pdgb.pd_adjoint_backward(m.h, gu)
+        m.close()
+    (gc64, gl64, gu64, _), (gcdw, gldw, gudw, _) = out[F64], out[DW]
+    assert np.abs(gc64).max() > 0
+    assert rel(gcdw, gc64) <= 1e-8, rel(gcdw, gc64)
+    assert abs(gldw - gl64) <= 1e-8 * abs(gl64)
+    assert rel(gudw, gu64) <= 1e-8
+
+
 def test_full_size_notched_beam_sampled_one_step():
     """1,009,200-node beam in the benchmark's launch configuration: one step from
     a common state with broken bonds against the oracle's step of 2000 sampled
