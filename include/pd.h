@@ -60,8 +60,8 @@ typedef enum {
                             decided against the FP64 s_c.  Single models with the
                             Euler-Cromer integrator and the PMB law (per-bond
                             stiffness included): no batches, softening or
-                            state-based model (PD_ERR_ARG).  The adjoint records
-                            and recomputes its forward runs with this step.
+                            state-based model (PD_ERR_ARG).  The adjoint runs in
+                            double-word arithmetic as well (see pd_adjoint_forward).
                             pd_get_info reports 48. */
 #define PD_MAX_FAMILY 1024
 #define PD_MAX_BC_CLASSES 256
@@ -310,8 +310,11 @@ pd_status pd_set_params(pd_handle* h, double c, double sc, double load, double d
  * Sensitivities (outer-loop use, Section 3.6): the gradient of a loss of the
  * final state with respect to every directed bond's stiffness, the body-force
  * load and the initial state, by a hand-written reverse sweep of the damped
- * Euler-Cromer recurrence.  FP64 handles only (PD_ERR_STATE otherwise), not
- * batch handles.
+ * Euler-Cromer recurrence.  FP64 and PD_PREC_DW handles (PD_ERR_STATE
+ * otherwise), not batch handles.  On PD_PREC_DW handles the recorded and
+ * recomputed forward runs use the double-word step and pd_adjoint_backward's
+ * reverse sweep is in double-word arithmetic too (FP64-grade; the same outputs
+ * to ~1e-10); pd_adjoint_backward_static keeps the FP64 reverse sweep.
  *
  * pd_adjoint_forward - advance n_steps (>= 1) from the current state with the
  *   bond flags frozen (no bond breaks, so the run is a smooth function of the
