@@ -487,6 +487,30 @@ def run_batch(args):
         t_off = time.time()
     bm.sync()
     ms_b = e0.elapsed_time(e1) / args.steps
+    n_nodes = sum(w.n for w in ws)
+    # end to end through the public API: pinned host u and v of all instances in
+    # and out every step
+    e2e = None
+    if not args.no_e2e:
+        uh = torch.empty((n_nodes, 3), dtype=torch.float64).pin_memory()
+        vh = torch.empty((n_nodes, 3), dtype=torch.float64).pin_memory()
+        pdgb.pd_get_state(bm.h, uh, vh)
+        k_e2e = max(3, min(args.steps, 50))
+        for _ in range(2):
+            pdgb.pd_set_state(bm.h, uh, vh)
+            bm.step(1)
+            pdgb.pd_get_state(bm.h, uh, vh)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(k_e2e):
+            pdgb.pd_set_state(bm.h, uh, vh)
+            bm.step(1)
+            pdgb.pd_get_state(bm.h, uh, vh)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t
+        e2e = {"value": n_bonds * k_e2e / el, "unit": "bond updates/s",
+               "h2d_bytes_per_step": 2 * uh.numel() * 8, "d2h_bytes_per_step": 2 * uh.numel() * 8,
+               "steps": k_e2e}
     bm.close()
     # per-instance loop: one handle per instance, each step launches every instance
     hs = [pdgb.Model.from_workload(w, precision=args.precision, graph_steps=0,
@@ -505,6 +529,40 @@ def run_batch(args):
     for m in hs:
         m.close()
     n_inst = len(ws)
+    # roofline: the FP32 step's algorithmic bytes over all instances
+    alg_bytes = n_bonds * BYTES_PER_BOND + n_nodes * BYTES_PER_NODE[args.precision]
+    peak, peak_kind = hbm_peak()
+    achieved = alg_bytes / (ms_b * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "kernel": f"k_step_f{args.precision} (batch)"}
+    # the oracle over whole instances, in order, for about 10 s of host time
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        done_bonds, el, used = 0, 0.0, 0
+        for w in ws:
+            off, idx = oracle.cut_family(w.coords, w.horizon, w.cuts_array())
+            om = oracle.Model.from_workload(w, off, idx,
+                                            c=oracle.micromodulus(w.bulk_modulus, w.horizon))
+            u, v = np.zeros((w.n, 3)), np.zeros((w.n, 3))
+            mu = om.fresh_bonds()
+            t = time.perf_counter()
+            for k in range(5):
+                om.step(k, u, v, mu)
+            el += time.perf_counter() - t
+            done_bonds += 5 * om.nbonds
+            used += 1
+            if el > 10.0:
+                break
+        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        cpu = {"value": done_bonds / el, "unit": "bond updates/s", "cores": cores,
+               "kind": "oracle",
+               "sample": f"5 oracle FP64 steps of each of the first {used} instances "
+                         f"(the per-instance loop), OpenMP on {cores} host threads"}
     line = {
         "metric": "bond updates/s", "value": n_bonds / (ms_b * 1e-3), "unit": "bond updates/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
@@ -517,6 +575,7 @@ def run_batch(args):
         "loop": {"ms_per_step": ms_l, "instance_steps_per_s": n_inst / (ms_l * 1e-3),
                  "launches_per_step": n_inst, "steps": k_loop},
         "batched_over_loop": ms_l / ms_b,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": args.steps + args.steps // G + (1 if args.steps % G else 0),
         "clocks": clk.summary(t_on, t_off),
     }
