@@ -726,8 +726,8 @@ def run_adjoint(args):
 def main():
     args = parse()
     if args.precision == 48 and (args.workload == "batch" or args.kr
-                                 or args.state_based is not None or args.integrator != "ec"):
-        raise SystemExit("--precision 48 runs single PMB models with the Euler-Cromer integrator")
+                                 or args.state_based is not None):
+        raise SystemExit("--precision 48 runs single PMB models")
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":

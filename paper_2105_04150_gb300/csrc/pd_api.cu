@@ -456,7 +456,8 @@ pd_status vv_force_pass(pd_handle* h)
         StepArgsF64 a = args_f64(h, 0);
         a.peek = 1;
         a.vout = (double*)h->vpeek;
-        e = launch_step_f64(a, h->sc_mode, h->grid, h->block, h->stream);
+        e = h->dw ? launch_step_dw(a, dw_args(h), h->sc_mode, h->grid, h->block, h->stream)
+                  : launch_step_f64(a, h->sc_mode, h->grid, h->block, h->stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "velocity-Verlet force pass");
     h->peek_step = h->step;
@@ -520,8 +521,6 @@ pd_status check_cfg(const pd_config* cfg)
     if (cfg->precision != PD_PREC_F32 && cfg->precision != PD_PREC_F64 &&
         cfg->precision != PD_PREC_DW)
         return fail(PD_ERR_ARG, "precision must be PD_PREC_F32, PD_PREC_F64 or PD_PREC_DW");
-    if (cfg->precision == PD_PREC_DW && cfg->integrator != PD_INTEGRATOR_EC)
-        return fail(PD_ERR_ARG, "PD_PREC_DW uses the Euler-Cromer integrator");
     if (!(cfg->dt > 0.0) || !(cfg->density > 0.0) || !(cfg->damping >= 0.0) ||
         !std::isfinite(cfg->dt) || !std::isfinite(cfg->density) || !std::isfinite(cfg->damping))
         return fail(PD_ERR_ARG, "dt and density must be > 0, damping >= 0");

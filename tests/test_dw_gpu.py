@@ -177,8 +177,6 @@ def test_agrees_with_the_fp64_path():
 def test_unsupported_combinations_are_refused():
     w = workloads.tensile_bar(8, 4, 4, steps=5)
     c = oracle.micromodulus(w.bulk_modulus, w.horizon)
-    with pytest.raises(pdgb.PdError):
-        pdgb.Model.from_workload(w, precision=DW, c=c, integrator=pdgb.PD_INTEGRATOR_VV)
     for attr, value in (("kr", 2.0), ("state_based", (w.bulk_modulus, 0.6 * w.bulk_modulus))):
         w2 = workloads.tensile_bar(8, 4, 4, steps=5)
         setattr(w2, attr, value)
@@ -186,6 +184,40 @@ def test_unsupported_combinations_are_refused():
             pdgb.Model.from_workload(w2, precision=DW, c=c)
     with pytest.raises(pdgb.PdError):
         pdgb.Model.batch([w, w], precision=DW)
+
+
+@pytest.mark.parametrize("ramp", [0, 300])
+def test_velocity_verlet_matches_oracle(ramp):
+    w = workloads.tensile_bar()
+    w.ramp_steps = ramp
+    off, idx = oracle.cut_family(w.coords, w.horizon, w.cuts_array())
+    om = oracle.Model.from_workload(w, off, idx)
+    u, v, acc = np.zeros((w.n, 3)), np.zeros((w.n, 3)), np.zeros((w.n, 3))
+    mu = om.fresh_bonds()
+    margin = np.full(len(mu), np.inf)
+    om.run_vv(0, w.steps, u, v, acc, mu, init=True, margin=margin)
+    assert (mu == 0).sum() > 0
+    g = gpu_run(w, w.steps, graph_steps=16, integrator=pdgb.PD_INTEGRATOR_VV)
+    assert rel(g["u"], u) <= 1e-10 and rel(g["v"], v) <= 1e-9
+    diff = g["mu"] != mu
+    assert np.all(margin[diff] < BAND), int(diff.sum())
+
+
+def test_velocity_verlet_full_step_velocity_read_changes_nothing():
+    w = workloads.tensile_bar(steps=300)
+    ref = gpu_run(w, 300, integrator=pdgb.PD_INTEGRATOR_VV)
+    c = oracle.micromodulus(w.bulk_modulus, w.horizon)
+    m = pdgb.Model.from_workload(w, precision=DW, c=c, graph_steps=25,
+                                 integrator=pdgb.PD_INTEGRATOR_VV)
+    for _ in range(6):
+        m.step(50)
+        m.state()
+        m.bonds()
+    u, v = m.state()
+    b = m.bonds()
+    m.close()
+    assert np.array_equal(u, ref["u"]) and np.array_equal(v, ref["v"])
+    assert np.array_equal(b, ref["mu"])
 
 
 def _grf_stiffness(w, off, idx, c0, seed=2105041505):
