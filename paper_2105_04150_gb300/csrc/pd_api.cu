@@ -358,8 +358,10 @@ DwArgs dw_args(pd_handle* h)
     d.dt_rho = h->dt / h->rho;
     // the leading word of a double-word stretch is within 2^-23 of it: below
     // this band the break test cannot be near any s_c of the model
+    // (with softening: below the smallest s_0 = s_c / kr)
     d.fast_lo = h->frozen ? INFINITY
-                          : (float)((1.0 - 0x1.0p-20) * (h->sc_mode == 0 ? h->sc : h->sc_lo));
+                          : (float)((1.0 - 0x1.0p-20) * (h->sc_mode == 0 ? h->sc : h->sc_lo) /
+                                    (h->integ != nullptr ? h->kr : 1.0));
     d.uniform_w = h->uniform_vol ? 1 : 0;
     return d;
 }
@@ -378,7 +380,9 @@ pd_status dw_publish(pd_handle* h)
 const void* step_kernel_fn(pd_handle* h)
 {
     if (h->precision == 32) return f32_kernel(h);
-    if (h->dw) return step_dw_kernel(h->sc_mode, h->uniform_vol);
+    if (h->dw)
+        return step_dw_kernel(h->sc_mode, h->uniform_vol, h->integ != nullptr,
+                              h->integrator == PD_INTEGRATOR_VV);
     return step_f64_kernel(h->sc_mode);
 }
 
@@ -827,8 +831,8 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
         if (e != cudaSuccess) return cuda_fail(e, "bond lengths");
     }
     if (h->dw) {
-        if (h->model != 0 || h->kr != 0.0)
-            return fail(PD_ERR_ARG, "PD_PREC_DW supports the PMB model without softening");
+        if (h->model != 0)
+            return fail(PD_ERR_ARG, "PD_PREC_DW supports the bond-based model");
         e = launch_dw_len(h->x64, h->nbr, h->sw, n, h->Q, 1.0 / h->delta, h->lendw, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "bond lengths");
     }

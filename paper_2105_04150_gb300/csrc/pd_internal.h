@@ -271,7 +271,7 @@ const void* step_f32_kernel_soft(int sc_mode, bool uniform_w, bool per_bond_c);
 const void* step_f64_kernel(int sc_mode);
 cudaError_t launch_step_dw(const StepArgsF64& a, const DwArgs& d, int sc_mode, int grid, int block,
                            cudaStream_t s);
-const void* step_dw_kernel(int sc_mode, bool uniform_w);
+const void* step_dw_kernel(int sc_mode, bool uniform_w, bool soft, bool vv);
 // double-word records from the FP64 records (positions relative to origin[3])
 cudaError_t launch_dw_publish(const double* rec64, float4* rec, int64_t n_pad, const double* origin,
                               double inv_delta, cudaStream_t s);

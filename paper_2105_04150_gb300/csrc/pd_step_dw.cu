@@ -47,6 +47,15 @@ namespace {
 #ifndef PD_DW_PREFETCH
 #define PD_DW_PREFETCH 1
 #endif
+// Velocity-Verlet build (pd_step_dw_vv.cu includes this file with PD_DW_VV 1):
+// the velocity-Verlet epilogue and the read-only force pass, compiled apart from
+// the Euler-Cromer one so that the latter's bond loop keeps its code.  A
+// separate translation unit, not a template parameter: ptxas 13.0.88 fails on
+// this kernel with a fourth one.
+#ifndef PD_DW_VV
+#define PD_DW_VV 0
+#endif
+constexpr bool VV = PD_DW_VV != 0;
 
 __device__ __forceinline__ uint64_t splitmix_out(uint64_t seed, uint64_t m)
 {
@@ -136,9 +145,10 @@ __device__ __forceinline__ void add_force(Dw (&F)[3], const BondDw& b, bool ok)
 // A bond whose leading stretch word reached the band below the smallest s_c:
 // recomputed with the same arithmetic and decided in FP64 against its s_c,
 // then the no-fail rule.
-template <int SCM, bool UW>
+template <int SCM, bool UW, bool SOFT>
 __device__ __noinline__ BondDw resolve_dw(const StepArgsF64& a, const DwArgs& d, int cur,
-                                          int64_t i, int64_t j, int64_t slot, bool* broken)
+                                          int64_t i, int64_t j, int64_t slot, bool* broken,
+                                          double* mu_out)
 {
     const float4* __restrict__ R = d.rec[cur];
     Rec own, nb;
@@ -149,13 +159,48 @@ __device__ __noinline__ BondDw resolve_dw(const StepArgsF64& a, const DwArgs& d,
     BondDw bd = bond_dw<UW>(own_of(own), nb, d.len[slot]);
     if (d.cb != nullptr) scale_coef(bd, d.cb[slot]);
     const double sc = SCM == 0 ? a.sc : sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i], a.gid[j]);
-    bool brk = (double)bd.s.h + (double)bd.s.l >= sc;
+    const double s64 = (double)bd.s.h + (double)bd.s.l;
+    bool brk = s64 >= sc;
     if (brk && a.has_nofail) brk = ((a.bct[a.bcc[i]].mask | a.bct[a.bcc[j]].mask) & 8u) == 0u;
     *broken = brk;
+    double mu = 1.0;
+    if (SOFT) {
+        // the integrity only decreases, as the stretch passes s_0 = s_c / kr (a
+        // no-fail bond past s_c keeps 0); the force is scaled by it
+        if (brk) {
+            a.integ[slot] = 0.0;
+        } else {
+            mu = a.integ[slot];
+            const double s0 = sc / a.kr;
+            if (s64 > s0) {
+                const double ms = s64 >= sc ? 0.0 : soft_mu_of(s64, s0, sc, a.k1, a.beta);
+                if (ms < mu) {
+                    mu = ms;
+                    a.integ[slot] = ms;
+                }
+            }
+            const float mh = (float)mu;
+            bd.coef = dw_mul(bd.coef, Dw{mh, (float)(mu - (double)mh)});
+        }
+    }
+    *mu_out = mu;
     return bd;
 }
 
-template <int SCM, bool UW>
+// softening: a bond's stored integrity scales its force (the fast path needs no
+// FP64 operation for the unsoftened ones, recognised by their bit pattern);
+// returns mu - 1 for the damage weight
+__device__ __forceinline__ double soften(BondDw& b, const double* integ, int64_t slot)
+{
+    const unsigned long long bits = __ldg(reinterpret_cast<const unsigned long long*>(integ) + slot);
+    if (bits == 0x3FF0000000000000ull) return 0.0;  // mu = 1
+    const double mu = __longlong_as_double(bits);
+    const float mh = (float)mu;
+    b.coef = dw_mul(b.coef, Dw{mh, (float)(mu - (double)mh)});
+    return mu - 1.0;
+}
+
+template <int SCM, bool UW, bool SOFT>
 __global__ void __launch_bounds__(256, PD_DW_MIN_BLOCKS)
     k_step_dw(const __grid_constant__ StepArgsF64 a, const __grid_constant__ DwArgs d)
 {
@@ -187,6 +232,7 @@ __global__ void __launch_bounds__(256, PD_DW_MIN_BLOCKS)
         Dw F[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         Dw ws{0.f, 0.f};
         int alive_count = 0;
+        double wsoft = 0.0;  // softening: sum of (mu - 1) w~_j over intact softened bonds
 
         // chunks of two slots (bonds A and B); ids one chunk ahead
         const int nch = (Wg + 1) >> 1;
@@ -222,6 +268,14 @@ __global__ void __launch_bounds__(256, PD_DW_MIN_BLOCKS)
             }
             const bool candA = bA.s.h >= d.fast_lo, candB = bB.s.h >= d.fast_lo;
             const bool okA = (wb & 1u) && !candA, okB = ((wb >> 1) & 1u) && !candB;
+            if (SOFT) {
+                const double dA = soften(bA, a.integ, (g * W + m0) * 32 + lane);
+                const double dB = soften(bB, a.integ, (g * W + m0 + 1) * 32 + lane);
+                if (okA && dA != 0.0)
+                    wsoft += dA * (UW ? 1.0 : (double)A.a1.z + (double)A.a1.w);
+                if (okB && dB != 0.0)
+                    wsoft += dB * (UW ? 1.0 : (double)B.a1.z + (double)B.a1.w);
+            }
             pend |= (((candA ? 1u : 0u) | (candB ? 2u : 0u)) & wb) << b0;
 #if PD_DW_PREFETCH
             // the next chunk's records start toward L1 (their ids have arrived by now)
@@ -245,18 +299,21 @@ __global__ void __launch_bounds__(256, PD_DW_MIN_BLOCKS)
                     const int64_t slot = (g * W + q * 32 + b) * 32 + lane;
                     const int64_t j = col[(int64_t)(q * 32 + b) * 32];
                     bool broken;
-                    const BondDw f = resolve_dw<SCM, UW>(a, d, cur, i, j, slot, &broken);
+                    double mu;
+                    const BondDw f = resolve_dw<SCM, UW, SOFT>(a, d, cur, i, j, slot, &broken, &mu);
                     if (broken) {
                         nword &= ~(1u << b);
                     } else {
                         add_force(F, f, true);
+                        float4 c0, c1;
+                        if (!UW || (SOFT && mu != 1.0)) ld_rec(R + 4 * j, c0, c1);
                         if (!UW) {
-                            float4 c0, c1;
-                            ld_rec(R + 4 * j, c0, c1);
                             const Dw t = two_sum(ws.h, c1.z);
                             ws.h = t.h;
                             ws.l += t.l + c1.w;
                         }
+                        if (SOFT && mu != 1.0)
+                            wsoft += (mu - 1.0) * (UW ? 1.0 : (double)c1.z + (double)c1.w);
                     }
                 }
                 if (nword != word) bw[q * 32] = nword;
@@ -287,7 +344,7 @@ __global__ void __launch_bounds__(256, PD_DW_MIN_BLOCKS)
             const double2 u01 = rin[4 * i + 2], u23 = rin[4 * i + 3];
             const double uo[3] = {u01.x, u01.y, u23.x};
             // velocity-Verlet: a^n is formed afresh at the step the state was set
-            const bool first = a.vv && step == a.step_ctr[1];
+            const bool first = VV && a.vv && step == a.step_ctr[1];
             double un[3];
             float uh[3], ul[3];
             bool finite = true;
@@ -298,7 +355,7 @@ __global__ void __launch_bounds__(256, PD_DW_MIN_BLOCKS)
                 const double vi = a.v[3 * i + k];
                 const double adt = (Fn[k] - a.eta * vi) * d.dt_rho;  // dt a
                 double vn, vfull;
-                if (a.vv) {
+                if (VV && a.vv) {
                     vfull = first ? vi : vi + 0.5 * adt;
                     vn = vfull + 0.5 * adt;
                 } else {
@@ -313,7 +370,7 @@ __global__ void __launch_bounds__(256, PD_DW_MIN_BLOCKS)
                 }
                 finite = finite && isfinite(u);
                 un[k] = u;
-                if (a.peek)
+                if (VV && a.peek)
                     a.vout[3 * i + k] = vfull;
                 else
                     a.v[3 * i + k] = vn;
@@ -321,7 +378,7 @@ __global__ void __launch_bounds__(256, PD_DW_MIN_BLOCKS)
                 uh[k] = (float)ut;
                 ul[k] = (float)(ut - (double)uh[k]);
             }
-            if (a.peek) continue;  // the read-only force pass of velocity-Verlet
+            if (VV && a.peek) continue;  // the read-only force pass of velocity-Verlet
             rout[4 * i] = rin[4 * i];
             rout[4 * i + 1] = rin[4 * i + 1];
             rout[4 * i + 2] = make_double2(un[0], un[1]);
@@ -330,8 +387,8 @@ __global__ void __launch_bounds__(256, PD_DW_MIN_BLOCKS)
                    make_float4(uh[1], uh[2], me.a1.z, me.a1.w));
             st_rec(Rout + 4 * i + 2, make_float4(me.b0.x, me.b0.y, me.b0.z, ul[0]),
                    make_float4(ul[1], ul[2], 0.0f, 0.0f));
-            const double wsum = UW ? d.w_const * (double)alive_count
-                                   : (double)ws.h + (double)ws.l;
+            const double wsum = UW ? d.w_const * ((double)alive_count + wsoft)
+                                   : ((double)ws.h + (double)ws.l) + wsoft;
             const double wi = a.wsum_inv[i];
             a.damage[i] = wi > 0.0 ? fmax(0.0, 1.0 - wsum * wi) : 0.0;
             if (!finite) atomicOr(a.err, PD_DEVERR_NONFINITE);
@@ -409,24 +466,39 @@ int grid_of(int64_t work)
 
 }  // namespace
 
+#if PD_DW_VV
+#define PD_DW_KERNELS step_dw_kernels_vv
+#else
+#define PD_DW_KERNELS step_dw_kernels_ec
+#endif
+// the kernel variants of this build: [sc_mode][uniform weights][softening]
+const void* PD_DW_KERNELS(int sc_mode, bool uniform_w, bool soft)
+{
+    static const void* const k[8] = {
+        (const void*)k_step_dw<0, false, false>, (const void*)k_step_dw<0, false, true>,
+        (const void*)k_step_dw<0, true, false>,  (const void*)k_step_dw<0, true, true>,
+        (const void*)k_step_dw<1, false, false>, (const void*)k_step_dw<1, false, true>,
+        (const void*)k_step_dw<1, true, false>,  (const void*)k_step_dw<1, true, true>};
+    return k[(sc_mode ? 4 : 0) + (uniform_w ? 2 : 0) + (soft ? 1 : 0)];
+}
+#undef PD_DW_KERNELS
+
+#if !PD_DW_VV
+const void* step_dw_kernels_vv(int sc_mode, bool uniform_w, bool soft);
+
+const void* step_dw_kernel(int sc_mode, bool uniform_w, bool soft, bool vv)
+{
+    return vv ? step_dw_kernels_vv(sc_mode, uniform_w, soft)
+              : step_dw_kernels_ec(sc_mode, uniform_w, soft);
+}
+
 cudaError_t launch_step_dw(const StepArgsF64& a, const DwArgs& d, int sc_mode, int grid, int block,
                            cudaStream_t s)
 {
-    if (sc_mode == 0) {
-        if (d.uniform_w) k_step_dw<0, true><<<grid, block, 0, s>>>(a, d);
-        else k_step_dw<0, false><<<grid, block, 0, s>>>(a, d);
-    } else {
-        if (d.uniform_w) k_step_dw<1, true><<<grid, block, 0, s>>>(a, d);
-        else k_step_dw<1, false><<<grid, block, 0, s>>>(a, d);
-    }
-    return cudaGetLastError();
-}
-
-const void* step_dw_kernel(int sc_mode, bool uniform_w)
-{
-    if (sc_mode == 0)
-        return uniform_w ? (const void*)k_step_dw<0, true> : (const void*)k_step_dw<0, false>;
-    return uniform_w ? (const void*)k_step_dw<1, true> : (const void*)k_step_dw<1, false>;
+    const void* fn = step_dw_kernel(sc_mode, d.uniform_w != 0, a.integ != nullptr,
+                                    a.vv != 0 || a.peek != 0);
+    void* args[] = {const_cast<StepArgsF64*>(&a), const_cast<DwArgs*>(&d)};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, s);
 }
 
 cudaError_t launch_dw_publish(const double* rec64, float4* rec, int64_t n_pad, const double* origin,
@@ -449,5 +521,7 @@ cudaError_t launch_dw_split(const double* in, int64_t count, float2* out, cudaSt
     k_dw_split<<<grid_of(count), 256, 0, s>>>(in, count, out);
     return cudaGetLastError();
 }
+
+#endif  // !PD_DW_VV
 
 }  // namespace pd

@@ -7,7 +7,7 @@ import paper_2105_04150_gb300 as pdgb
 import workloads
 
 pytestmark = pytest.mark.gpu
-F64, F32 = pdgb.PD_PREC_F64, pdgb.PD_PREC_F32
+F64, F32, DW = pdgb.PD_PREC_F64, pdgb.PD_PREC_F32, pdgb.PD_PREC_DW
 BAND = 1e-9
 # integrity: u agrees to 1e-10 of max|u| (~1e-4 m), so stretches to ~1e-14 m /
 # |xi| (1e-3 m) = 1e-11, and |d mu / ds| <= 1 / s_0 ~ 1e3 near s_0: ~1e-8
@@ -68,9 +68,25 @@ def _bar(kr):
     return w
 
 
-def test_softening_fp64_tensile_bar_matches_oracle():
+# Softening makes the bar's response unstable once fracture starts: rounding
+# differences grow about 5000-fold between steps 550 and 1000 (measured against
+# the oracle: FP64 4e-14 -> 9.5e-11, double-word 2.7e-12 -> 1.4e-8, with 39k bonds
+# broken at the end).  The double-word step (48-bit significand, ~30x the FP64
+# rounding) is held to the FP64 bar up to the onset of fracture (600 steps, 40
+# bonds broken); after it, u within 1e-7 and broken sets within 1e-4 of the bonds.
+def _dw_after_fracture(w):
+    g, o = _run(w, DW, w.steps)
+    assert rel(g["u"], o["u"]) <= 1e-7
+    assert (g["b"] != o["mu"]).mean() <= 1e-4
+
+
+@pytest.mark.parametrize("precision", [F64, DW])
+def test_softening_fp64_tensile_bar_matches_oracle(precision):
     w = _bar(3.0)
-    g, o = _run(w, F64, w.steps)
+    if precision == DW:
+        _dw_after_fracture(w)
+        w.steps = 600
+    g, o = _run(w, precision, w.steps)
     assert (o["mu"] == 0).sum() > 0 and ((o["integ"] > 0) & (o["integ"] < 1)).sum() > 100
     assert rel(g["u"], o["u"]) <= 1e-10 and rel(g["v"], o["v"]) <= 1e-9
     diff = g["b"] != o["mu"]
@@ -96,17 +112,18 @@ def test_softening_fp32_tensile_bar_matches_oracle():
     assert np.abs(g["phi"] - o["phi"]).max() <= 2e-2
 
 
-def test_softening_fp64_notched_beam_per_bond_sc():
+@pytest.mark.parametrize("precision", [F64, DW])
+def test_softening_fp64_notched_beam_per_bond_sc(precision):
     w = workloads.notched_beam(48, 10, 12, length=48 / 600, rate=1e-7, steps=300)
     w.kr = 2.0
-    g, o = _run(w, F64, w.steps)
+    g, o = _run(w, precision, w.steps)
     assert rel(g["u"], o["u"]) <= 1e-10
     diff = g["b"] != o["mu"]
     assert np.all(o["margin"][diff] < BAND)
     assert np.abs(g["integ"][~diff] - o["integ"][~diff]).max() <= INTEG_TOL
 
 
-@pytest.mark.parametrize("precision", [F64, F32])
+@pytest.mark.parametrize("precision", [F64, F32, DW])
 def test_kr_one_equals_pmb_bitwise(precision):
     w = _bar(0.0)
     a = pdgb.Model.from_workload(w, precision=precision)
@@ -124,9 +141,10 @@ def test_kr_one_equals_pmb_bitwise(precision):
     b.close()
 
 
-def test_fused_and_recomputed_damage_agree_and_set_bonds_resets():
+@pytest.mark.parametrize("precision", [F64, DW])
+def test_fused_and_recomputed_damage_agree_and_set_bonds_resets(precision):
     w = _bar(3.0)
-    m = pdgb.Model.from_workload(w, precision=F64)
+    m = pdgb.Model.from_workload(w, precision=precision)
     m.step(900)
     phi_fused = m.damage()
     u, v = m.state()
@@ -140,14 +158,17 @@ def test_fused_and_recomputed_damage_agree_and_set_bonds_resets():
     m.close()
 
 
-@pytest.mark.parametrize("precision", [F64, F32])
+@pytest.mark.parametrize("precision", [F64, F32, DW])
 def test_trilinear_softening_matches_oracle(precision):
     w = _bar(4.0)
     w.trilinear = (2.0, 0.25)
-    steps = w.steps if precision == F64 else 500
+    if precision == DW:  # trilinear: compared before bonds break, as FP32 below
+        _dw_after_fracture(w)
+        w.steps = 500
+    steps = w.steps if precision != F32 else 500
     g, o = _run(w, precision, steps)
     assert ((o["integ"] > 0) & (o["integ"] < 1)).sum() > 100
-    if precision == F64:
+    if precision != F32:
         assert rel(g["u"], o["u"]) <= 1e-10
         diff = g["b"] != o["mu"]
         assert np.all(o["margin"][diff] < BAND)
