@@ -66,6 +66,8 @@ OSB_FLOPS_PER_BOND = 57.0
 # lane rate measured by a probe on this machine's GB300, 35.1 T/s (70.2 TFLOP/s
 # counting an FMA as two).
 DW_FP32_OPS_PER_BOND = 192.0
+# per-node weights (batches): the coefficient times w_j (4) and the weight sum (8)
+DW_FP32_OPS_PER_BOND_NODE_W = DW_FP32_OPS_PER_BOND + 12.0
 FP32_PEAK_TOPS = 35.1
 # per node: the double-word record 64 B read + 64 B written, the FP64 record
 # (x, w copied, u) 56 B read + 56 B written, FP64 velocity 24 + 24 B, damage
@@ -529,15 +531,26 @@ def run_batch(args):
     for m in hs:
         m.close()
     n_inst = len(ws)
-    # roofline: the FP32 step's algorithmic bytes over all instances
-    alg_bytes = n_bonds * BYTES_PER_BOND + n_nodes * BYTES_PER_NODE[args.precision]
+    # roofline: the step's algorithmic bytes over all instances (FP32, FP64), or
+    # the double-word step's FP32 operations
+    per_bond = DW_BYTES_PER_BOND if args.precision == 48 else BYTES_PER_BOND
+    alg_bytes = n_bonds * per_bond + n_nodes * BYTES_PER_NODE[args.precision]
     peak, peak_kind = hbm_peak()
     achieved = alg_bytes / (ms_b * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                 "algorithmic_bytes_per_launch": alg_bytes,
-                "kernel": f"k_step_f{args.precision} (batch)"}
+                "kernel": f"k_step_{STEP_TAG[args.precision]} (batch)"}
+    if args.precision == 48:
+        tops = DW_FP32_OPS_PER_BOND_NODE_W * n_bonds / (ms_b * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": tops, "peak": FP32_PEAK_TOPS,
+                    "unit": "TFLOP/s", "frac": tops / FP32_PEAK_TOPS, "traffic": None,
+                    "peak_source": "FP32 operations against the measured FP32 FMA lane rate",
+                    "algorithmic_flops_per_bond": DW_FP32_OPS_PER_BOND_NODE_W,
+                    "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak},
+                    "kernel": "k_step_dw (batch, per-node weights)"}
     # the oracle over whole instances, in order, for about 10 s of host time
     cpu = None
     if not args.no_cpu_baseline:
@@ -567,7 +580,8 @@ def run_batch(args):
         "metric": "bond updates/s", "value": n_bonds / (ms_b * 1e-3), "unit": "bond updates/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
+        "dtype": {32: "f32", 64: "f64", 48: "f32 double-word"}[args.precision],
+        "data": "synthetic",
         "config": {"workload": f"batch of {n_inst} bars and notched beams, "
                                f"{sum(w.n for w in ws):,} nodes, {n_bonds:,} directed bonds",
                    "autotuned_launch": {"block_threads": block, "blocks_per_sm": bps}},
@@ -725,8 +739,8 @@ def run_adjoint(args):
 
 def main():
     args = parse()
-    if args.precision == 48 and (args.workload == "batch" or args.state_based is not None):
-        raise SystemExit("--precision 48 runs single bond-based models")
+    if args.precision == 48 and args.state_based is not None:
+        raise SystemExit("--precision 48 runs bond-based models")
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":

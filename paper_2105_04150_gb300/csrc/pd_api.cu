@@ -362,7 +362,8 @@ DwArgs dw_args(pd_handle* h)
     d.fast_lo = h->frozen ? INFINITY
                           : (float)((1.0 - 0x1.0p-20) * (h->sc_mode == 0 ? h->sc : h->sc_lo) /
                                     (h->integ != nullptr ? h->kr : 1.0));
-    d.uniform_w = h->uniform_vol ? 1 : 0;
+    // batches: the per-node weights (each instance's c folded in)
+    d.uniform_w = h->uniform_vol && !h->batch ? 1 : 0;
     return d;
 }
 
@@ -381,7 +382,7 @@ const void* step_kernel_fn(pd_handle* h)
 {
     if (h->precision == 32) return f32_kernel(h);
     if (h->dw)
-        return step_dw_kernel(h->sc_mode, h->uniform_vol, h->integ != nullptr,
+        return step_dw_kernel(h->sc_mode, h->uniform_vol && !h->batch, h->integ != nullptr,
                               h->integrator == PD_INTEGRATOR_VV);
     return step_f64_kernel(h->sc_mode);
 }
@@ -937,8 +938,6 @@ pd_status pd_batch_create(int32_t n_inst, const pd_instance* inst, const pd_conf
     if (n_inst < 1 || !inst || !cfg) return fail(PD_ERR_ARG, "need n_inst >= 1, inst and cfg");
     pd_status st;
     if ((st = check_cfg(cfg)) != PD_OK) return st;
-    if (cfg->precision == PD_PREC_DW)
-        return fail(PD_ERR_ARG, "batches take PD_PREC_F32 or PD_PREC_F64");
     int64_t n = 0;
     double unit = 0.0;
     bool any_nofail = false;

@@ -158,7 +158,13 @@ __device__ __noinline__ BondDw resolve_dw(const StepArgsF64& a, const DwArgs& d,
     ld_rec(R + 4 * j + 2, nb.b0, nb.b1);
     BondDw bd = bond_dw<UW>(own_of(own), nb, d.len[slot]);
     if (d.cb != nullptr) scale_coef(bd, d.cb[slot]);
-    const double sc = SCM == 0 ? a.sc : sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i], a.gid[j]);
+    double sc = a.sc;
+    if (a.inst != nullptr) {  // batch: the instance's own parameters, local ids as keys
+        const InstParams& ip = a.itab[a.inst[i]];
+        sc = ip.sc_mode == 1 ? sc_draw(ip.sc_seed, ip.sc_lo, ip.sc_hi, a.hid[i], a.hid[j]) : ip.sc;
+    } else if (SCM == 1) {
+        sc = sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i], a.gid[j]);
+    }
     const double s64 = (double)bd.s.h + (double)bd.s.l;
     bool brk = s64 >= sc;
     if (brk && a.has_nofail) brk = ((a.bct[a.bcc[i]].mask | a.bct[a.bcc[j]].mask) & 8u) == 0u;
@@ -227,6 +233,11 @@ __global__ void __launch_bounds__(256, PD_DW_MIN_BLOCKS)
         ld_rec(R + 4 * i + 2, me.b0, me.b1);
         const OwnDw own = own_of(me);
         uint32_t* bw = a.bits + g * Q * 32 + lane;
+        // band below the smallest s_c the node's bonds can have (per instance in a
+        // batch: both ends of a bond belong to the same instance)
+        const float fast_lo = a.inst != nullptr
+                                  ? (float)((1.0 - 0x1.0p-20) * a.itab[a.inst[i]].sc_lo)
+                                  : d.fast_lo;
         // force sums of the A and B halves, and (non-uniform weights) the sum of
         // w_j over intact bonds
         Dw F[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
@@ -266,7 +277,7 @@ __global__ void __launch_bounds__(256, PD_DW_MIN_BLOCKS)
                 scale_coef(bA, __ldg(d.cb + (g * W + m0) * 32 + lane));
                 scale_coef(bB, __ldg(d.cb + (g * W + m0 + 1) * 32 + lane));
             }
-            const bool candA = bA.s.h >= d.fast_lo, candB = bB.s.h >= d.fast_lo;
+            const bool candA = bA.s.h >= fast_lo, candB = bB.s.h >= fast_lo;
             const bool okA = (wb & 1u) && !candA, okB = ((wb >> 1) & 1u) && !candB;
             if (SOFT) {
                 const double dA = soften(bA, a.integ, (g * W + m0) * 32 + lane);

@@ -15,7 +15,7 @@ import paper_2105_04150_gb300 as pdgb
 import workloads
 
 pytestmark = pytest.mark.gpu
-F64, F32 = pdgb.PD_PREC_F64, pdgb.PD_PREC_F32
+F64, F32, DW = pdgb.PD_PREC_F64, pdgb.PD_PREC_F32, pdgb.PD_PREC_DW
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -50,7 +50,7 @@ def _alone(w, prec, steps):
     return out
 
 
-@pytest.mark.parametrize("prec", [F64, F32])
+@pytest.mark.parametrize("prec", [F64, F32, DW])
 def test_batch_instances_equal_models_alone(prec):
     ws = _instances()
     # all instances share dt, damping, density; loads/rates must agree across the batch
@@ -82,6 +82,13 @@ def test_batch_instances_equal_models_alone(prec):
             assert np.array_equal(mk, a["mu"])
             assert np.array_equal(u[s], a["u"]) and np.array_equal(v[s], a["v"])
             assert np.array_equal(phi[s], a["phi"])
+        elif prec == DW:
+            # a batch takes the per-node-weight variant of the double-word step
+            # (alone: one weight per model), which rounds differently
+            den = max(np.abs(a["u"]).max(), 1e-300)
+            assert np.abs(u[s] - a["u"]).max() <= 1e-12 * den
+            assert np.array_equal(mk, a["mu"])
+            assert np.abs(phi[s] - a["phi"]).max() <= 1e-12
         else:
             assert (mk != a["mu"]).mean() < 1e-3 if len(mk) else True
             den = max(np.abs(a["u"]).max(), 1e-300)
@@ -90,11 +97,12 @@ def test_batch_instances_equal_models_alone(prec):
     assert broke > 0
 
 
-def test_batch_instance_matches_oracle():
+@pytest.mark.parametrize("prec", [F64, DW])
+def test_batch_instance_matches_oracle(prec):
     ws = _instances()[:3]
     for w in ws:
         w.dt, w.damping, w.density = 1e-7, 2.5e6, 2400.0
-    bm = pdgb.Model.batch(ws, precision=F64)
+    bm = pdgb.Model.batch(ws, precision=prec)
     bm.step(80)
     u, _ = bm.state()
     off = bm.offsets()

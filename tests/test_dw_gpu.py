@@ -182,8 +182,6 @@ def test_unsupported_combinations_are_refused():
         setattr(w2, attr, value)
         with pytest.raises(pdgb.PdError):
             pdgb.Model.from_workload(w2, precision=DW, c=c)
-    with pytest.raises(pdgb.PdError):
-        pdgb.Model.batch([w, w], precision=DW)
 
 
 @pytest.mark.parametrize("ramp", [0, 300])
