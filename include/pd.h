@@ -146,7 +146,8 @@ typedef struct {
  * from c s_0 to kink_force * c s_0 at s_1 = kink_ratio * s_0, then to zero at
  * s_c; mu = envelope(k) / (c k).  The damage (Eq. 8) weighs each bond by its
  * integrity.  kr = 1 is the PMB law.
- * Not available in batches or with the adjoint.
+ * Not available with the adjoint; in a batch, kr, kink_ratio and kink_force
+ * must be the same for every instance.
  */
 typedef struct {
     const uint8_t* type;   /* n*3: 1 = displacement-controlled component, 0 = free */
@@ -379,7 +380,8 @@ typedef struct {
     const double* cuts;      /* host, n_cuts*6 (see pd_create), or NULL */
     int32_t n_cuts;
     int32_t reserved;
-    pd_material mat;         /* c and critical stretch of this instance */
+    pd_material mat;         /* c and critical stretch of this instance (the softening
+                                parameters and model must equal instance 0's) */
     pd_bc bc;                /* BCs of this instance; disp_rate and load must be equal
                                 across the batch (they are handle-wide) */
 } pd_instance;

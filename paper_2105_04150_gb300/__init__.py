@@ -322,7 +322,7 @@ def pd_batch_create(instances, *, dt: float, damping: float, density: float,
                     blocks_per_sm: int = 0, reorder: int = 0, integrator: int = 0) -> int:
     """Create a batch handle from a list of dicts with the keys of ``pd_create``'s
     body arguments: coords, volumes, horizon, c, sc / sc_hash, cuts, bc_type,
-    bc_disp, bc_force, no_fail, disp_rate, load."""
+    bc_disp, bc_force, no_fail, disp_rate, load, ramp_steps, kr, trilinear."""
     keep = []
     arr = (_Instance * len(instances))()
     for k, I in enumerate(instances):
@@ -338,7 +338,10 @@ def pd_batch_create(instances, *, dt: float, damping: float, density: float,
         bf, kbf = _ptr(I.get("bc_force"), np.float64, 3 * n if I.get("bc_force") is not None else None)
         nf, knf = _ptr(I.get("no_fail"), np.uint8, n if I.get("no_fail") is not None else None)
         keep += [kx, kv, kc, kbt, kbd, kbf, knf]
-        mat = _Material(c=float(I["c"]), sc=float(I.get("sc", 0.0)), sc_mode=0)
+        mat = _Material(c=float(I["c"]), sc=float(I.get("sc", 0.0)), sc_mode=0,
+                        kr=float(I.get("kr", 0.0)))
+        if I.get("trilinear") is not None:  # (s_1 / s_0, kink force / peak force)
+            mat.kink_ratio, mat.kink_force = float(I["trilinear"][0]), float(I["trilinear"][1])
         if I.get("sc_hash") is not None:
             s = I["sc_hash"]
             mat.sc_mode, mat.sc_seed, mat.sc_lo, mat.sc_hi = 1, int(s[0]), float(s[1]), float(s[2])
@@ -434,7 +437,8 @@ def instance_from_workload(w, c=None) -> dict:
     return dict(coords=w.coords, volumes=w.volumes, horizon=w.horizon, c=c, sc=w.sc,
                 sc_hash=w.sc_hash, cuts=w.cuts_array(), bc_type=w.bc_type, bc_disp=w.bc_disp,
                 bc_force=w.bc_force, no_fail=w.no_fail, disp_rate=w.disp_rate, load=w.load,
-                ramp_steps=getattr(w, "ramp_steps", 0))
+                ramp_steps=getattr(w, "ramp_steps", 0), kr=getattr(w, "kr", 0.0),
+                trilinear=getattr(w, "trilinear", None))
 
 
 class Model:

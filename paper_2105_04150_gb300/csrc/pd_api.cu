@@ -950,10 +950,13 @@ pd_status pd_batch_create(int32_t n_inst, const pd_instance* inst, const pd_conf
             I.bc.ramp_steps != inst[0].bc.ramp_steps)
             return fail(PD_ERR_ARG,
                         "instance %d: disp_rate, load and ramp_steps must equal instance 0's", b);
-        if (I.mat.kr != 0.0 || I.mat.model != 0)
+        if (I.mat.model != 0)
             return fail(PD_ERR_ARG,
-                        "instance %d: softening and the state-based model are not available "
-                        "in batches", b);
+                        "instance %d: the state-based model is not available in batches", b);
+        if (I.mat.kr != inst[0].mat.kr || I.mat.kink_ratio != inst[0].mat.kink_ratio ||
+            I.mat.kink_force != inst[0].mat.kink_force)
+            return fail(PD_ERR_ARG,
+                        "instance %d: kr, kink_ratio and kink_force must equal instance 0's", b);
         n += I.n;
         unit = std::max(unit, I.horizon);
         any_nofail = any_nofail || I.bc.no_fail != nullptr;
@@ -1011,7 +1014,9 @@ pd_status pd_batch_create(int32_t n_inst, const pd_instance* inst, const pd_conf
         ip.sc_lo = I.mat.sc_mode == 1 ? I.mat.sc_lo : I.mat.sc;
         ip.sc_hi = I.mat.sc_mode == 1 ? I.mat.sc_hi : I.mat.sc;
         ip.sc_seed = I.mat.sc_seed;
-        ip.fast_lo = (float)((1.0 - 2.0 * kGuard) * ip.sc_lo);
+        // softening: the band below the smallest s_0 = s_c / kr is resolved too
+        ip.fast_lo = (float)((1.0 - 2.0 * kGuard) * ip.sc_lo /
+                             (inst[0].mat.kr >= 1.0 ? inst[0].mat.kr : 1.0));
         ip.w_const = (float)(I.mat.c * I.volumes[0]);
         for (int64_t i = 1; i < I.n && uniform_all; ++i) uniform_all = I.volumes[i] == I.volumes[0];
         h->inst_off.push_back(o + I.n);

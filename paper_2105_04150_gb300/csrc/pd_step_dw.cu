@@ -236,7 +236,8 @@ __global__ void __launch_bounds__(256, PD_DW_MIN_BLOCKS)
         // band below the smallest s_c the node's bonds can have (per instance in a
         // batch: both ends of a bond belong to the same instance)
         const float fast_lo = a.inst != nullptr
-                                  ? (float)((1.0 - 0x1.0p-20) * a.itab[a.inst[i]].sc_lo)
+                                  ? (float)((1.0 - 0x1.0p-20) * a.itab[a.inst[i]].sc_lo /
+                                            (SOFT ? a.kr : 1.0))
                                   : d.fast_lo;
         // force sums of the A and B halves, and (non-uniform weights) the sum of
         // w_j over intact bonds
