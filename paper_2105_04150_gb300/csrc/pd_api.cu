@@ -834,7 +834,7 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
     if (h->dw) {
         if (h->model != 0)
             return fail(PD_ERR_ARG, "PD_PREC_DW supports the bond-based model");
-        e = launch_dw_len(h->x64, h->nbr, h->sw, n, h->Q, 1.0 / h->delta, h->lendw, h->stream);
+        e = launch_dw_len(h->x64, h->nbr, n, h->Q, 1.0 / h->delta, h->lendw, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "bond lengths");
     }
     if (h->model == 1 && !f32) {

@@ -275,7 +275,8 @@ const void* step_dw_kernel(int sc_mode, bool uniform_w, bool soft, bool vv);
 // double-word records from the FP64 records (positions relative to origin[3])
 cudaError_t launch_dw_publish(const double* rec64, float4* rec, int64_t n_pad, const double* origin,
                               double inv_delta, cudaStream_t s);
-cudaError_t launch_dw_len(const double* x64, const int32_t* nbr, const int32_t* sw, int64_t n, int Q,
+// every slot's |xi| / delta (1 where there is no bond)
+cudaError_t launch_dw_len(const double* x64, const int32_t* nbr, int64_t n, int Q,
                           double inv_delta, float2* len, cudaStream_t s);
 // double-word copy of an FP64 per-slot array
 cudaError_t launch_dw_split(const double* in, int64_t count, float2* out, cudaStream_t s);

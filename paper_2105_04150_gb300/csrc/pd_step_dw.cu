@@ -4,11 +4,13 @@
 // step kernel is bound by the FP64 pipe.  This kernel computes the same step
 // (Eq. 4 stretch, Eq. 6 breaking, Eq. 5/10 force, Eq. 11 update, Eq. 8
 // damage) with every bond quantity carried as an unevaluated sum of two FP32
-// numbers, h + l with |l| <= ulp(h)/2 (double-word arithmetic: Dekker 1971;
-// Knuth's two-sum; the products and error bounds of Joldes, Muller & Popescu,
-// ACM TOMS 2017), which carries about 48 significant bits: the relative
-// accuracy of a bond force is ~1e-13, far inside the FP64 parity bar, for a
-// few hundred FP32 operations instead of ~30 FP64 ones.
+// numbers (double-word arithmetic, pd_dw.h), about 48 significant bits: the
+// relative accuracy of a bond force is ~1e-13, far inside the FP64 parity bar,
+// for about two hundred FP32 operations instead of ~30 FP64 ones.  Variants:
+// sc_mode, uniform or per-node weights (batches take the latter), softening
+// (the stored FP64 integrity scales the force; bonds near s_0 are resolved in
+// FP64), per-bond stiffness (a run-time branch), velocity-Verlet (its own
+// translation unit, below).
 //
 // Work decomposition, bond flags, node order and the double-buffered records
 // are those of the FP32 kernel (lane per node over the sliced family).
@@ -436,8 +438,7 @@ __global__ void k_dw_publish(const double* __restrict__ rec64, float4* __restric
 }
 
 __global__ void k_dw_len(const double* __restrict__ x64, const int32_t* __restrict__ nbr,
-                         const int32_t* __restrict__ sw, int64_t n, int Q, double inv_delta,
-                         float2* __restrict__ len)
+                         int64_t n, int Q, double inv_delta, float2* __restrict__ len)
 {
     const int64_t W = 32LL * Q;
     const int64_t total = ((n + 31) >> 5) << 5;
@@ -521,10 +522,10 @@ cudaError_t launch_dw_publish(const double* rec64, float4* rec, int64_t n_pad, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_dw_len(const double* x64, const int32_t* nbr, const int32_t* sw, int64_t n, int Q,
+cudaError_t launch_dw_len(const double* x64, const int32_t* nbr, int64_t n, int Q,
                           double inv_delta, float2* len, cudaStream_t s)
 {
-    k_dw_len<<<grid_of(((n + 31) >> 5) << 5), 256, 0, s>>>(x64, nbr, sw, n, Q, inv_delta, len);
+    k_dw_len<<<grid_of(((n + 31) >> 5) << 5), 256, 0, s>>>(x64, nbr, n, Q, inv_delta, len);
     return cudaGetLastError();
 }
 
