@@ -57,11 +57,11 @@ typedef enum {
                             stretch of Eq. 4, |y|, the force of Eq. 5) carried as an
                             unevaluated sum of two FP32 numbers (~48-bit significand,
                             bond-force relative error ~1e-13), and the break test
-                            decided against the FP64 s_c.  Bond-based models with
-                            either integrator, per-bond stiffness, bilinear or
-                            trilinear softening, and batches; not the state-based
-                            model (PD_ERR_ARG).  The adjoint runs in double-word
-                            arithmetic as well (see pd_adjoint_forward).
+                            decided against the FP64 s_c.  Everything PD_PREC_F64
+                            offers: both integrators, per-bond stiffness,
+                            softening, batches, the state-based model (Euler-Cromer)
+                            and the adjoint, which runs in double-word arithmetic
+                            as well (see pd_adjoint_forward).
                             pd_get_info reports 48. */
 #define PD_MAX_FAMILY 1024
 #define PD_MAX_BC_CLASSES 256

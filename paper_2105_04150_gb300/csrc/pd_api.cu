@@ -135,6 +135,7 @@ struct pd_handle {
     double* osb_theta = nullptr;  // per node dilation
     double* osb_alpha = nullptr;  // per node force-scalar coefficients (see pd_step_osb.cu)
     double* osb_beta = nullptr;
+    float4* osbdw_ab = nullptr;   // double-word state-based: per node alpha~, beta~
     float *osb32_len = nullptr, *osb32_mvol = nullptr, *osb32_theta = nullptr,
           *osb32_alpha = nullptr, *osb32_beta = nullptr;  // FP32 state-based arrays
     void* wsum_inv = nullptr;
@@ -332,6 +333,19 @@ OsbArgs osb_args(pd_handle* h)
     return o;
 }
 
+OsbDwArgs osbdw_args(pd_handle* h)
+{
+    OsbDwArgs o{};
+    o.len = h->lendw;
+    o.vol = h->vol;
+    o.mvol = h->osb_mvol;
+    o.theta = h->osb_theta;
+    o.ab = h->osbdw_ab;
+    o.K = h->osb_K;
+    o.G = h->osb_G;
+    return o;
+}
+
 OsbArgs32 osb32_args(pd_handle* h)
 {
     OsbArgs32 o{};
@@ -354,7 +368,7 @@ DwArgs dw_args(pd_handle* h)
     d.len = h->lendw;
     d.cb = h->per_bond_c ? h->cbdw : nullptr;
     d.inv_delta = 1.0 / h->delta;
-    d.w_const = (h->per_bond_c ? 1.0 : h->c) * h->vol0;
+    d.w_const = ((h->per_bond_c || h->model == 1) ? 1.0 : h->c) * h->vol0;
     d.dt_rho = h->dt / h->rho;
     // the leading word of a double-word stretch is within 2^-23 of it: below
     // this band the break test cannot be near any s_c of the model
@@ -389,6 +403,9 @@ const void* step_kernel_fn(pd_handle* h)
 
 cudaError_t launch_one(pd_handle* h, int k)
 {
+    if (h->dw && h->model == 1)
+        return launch_osb_dw_step(args_f64(h, k), dw_args(h), osbdw_args(h), h->grid, h->block,
+                                  h->stream);
     if (h->dw)
         return launch_step_dw(args_f64(h, k), dw_args(h), h->sc_mode, h->grid, h->block,
                               h->stream);
@@ -694,6 +711,10 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
             ALLOC(h->osb32_theta, float, np);
             ALLOC(h->osb32_alpha, float, np);
             ALLOC(h->osb32_beta, float, np);
+        } else if (h->dw) {
+            ALLOC(h->osb_mvol, double, np);
+            ALLOC(h->osb_theta, double, np);
+            ALLOC(h->osbdw_ab, float4, np);
         } else {
             ALLOC(h->osb_len, double, nbr.size());
             ALLOC(h->osb_mvol, double, np);
@@ -832,13 +853,12 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
         if (e != cudaSuccess) return cuda_fail(e, "bond lengths");
     }
     if (h->dw) {
-        if (h->model != 0)
-            return fail(PD_ERR_ARG, "PD_PREC_DW supports the bond-based model");
         e = launch_dw_len(h->x64, h->nbr, n, h->Q, 1.0 / h->delta, h->lendw, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "bond lengths");
     }
     if (h->model == 1 && !f32) {
-        e = launch_osb_setup(args_f64(h, 0), osb_args(h), h->x64, h->stream);
+        e = h->dw ? launch_osb_dw_setup(args_f64(h, 0), osbdw_args(h), h->stream)
+                  : launch_osb_setup(args_f64(h, 0), osb_args(h), h->x64, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "state-based set-up");
     }
     if ((st = upload_weights(h)) != PD_OK) return st;

@@ -162,6 +162,21 @@ struct OsbArgs {
     double K, G;               // bulk and shear modulus
 };
 
+// Ordinary state-based arrays of PD_PREC_DW handles (pd_step_osb_dw.cu; lengths
+// in horizon units)
+struct OsbDwArgs {
+    const float2* len;         // per slot |xi| / delta (the double-word step's)
+    const double* vol;         // per node V
+    double* mvol;              // per node m~ = sum |xi~|^2 V_j
+    double* theta;             // per node dilation of the current step
+    float4* ab;                // per node {alpha~ h, l, beta~ h, l} (double-words)
+    double K, G;
+};
+
+cudaError_t launch_osb_dw_setup(const StepArgsF64& a, const OsbDwArgs& o, cudaStream_t s);
+cudaError_t launch_osb_dw_step(const StepArgsF64& a, const DwArgs& d, const OsbDwArgs& o, int grid,
+                               int block, cudaStream_t s);
+
 // Ordinary state-based arrays of FP32 handles (lengths in horizon units;
 // alpha, beta multiplied by delta, see pd_step_f32.cu)
 struct OsbArgs32 {

@@ -174,16 +174,6 @@ def test_agrees_with_the_fp64_path():
     assert (g["mu"] == 0).sum() > 0
 
 
-def test_unsupported_combinations_are_refused():
-    w = workloads.tensile_bar(8, 4, 4, steps=5)
-    c = oracle.micromodulus(w.bulk_modulus, w.horizon)
-    for attr, value in (("state_based", (w.bulk_modulus, 0.6 * w.bulk_modulus)),):
-        w2 = workloads.tensile_bar(8, 4, 4, steps=5)
-        setattr(w2, attr, value)
-        with pytest.raises(pdgb.PdError):
-            pdgb.Model.from_workload(w2, precision=DW, c=c)
-
-
 @pytest.mark.parametrize("ramp", [0, 300])
 def test_velocity_verlet_matches_oracle(ramp):
     w = workloads.tensile_bar()

@@ -8,7 +8,7 @@ import paper_2105_04150_gb300 as pdgb
 import workloads
 
 pytestmark = pytest.mark.gpu
-F64, F32 = pdgb.PD_PREC_F64, pdgb.PD_PREC_F32
+F64, F32, DW = pdgb.PD_PREC_F64, pdgb.PD_PREC_F32, pdgb.PD_PREC_DW
 BAND = 1e-9
 
 
@@ -29,45 +29,49 @@ def rel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-def _compare(w, steps):
+def _compare(w, steps, precision=F64):
     off, idx = oracle.cut_family(w.coords, w.horizon, w.cuts_array())
     om = oracle.Model.from_workload(w, off, idx)
     u, v, mu = np.zeros((w.n, 3)), np.zeros((w.n, 3)), om.fresh_bonds()
     margin = np.full(len(mu), np.inf)
     om.run(0, steps, u, v, mu, margin)
-    m = pdgb.Model.from_workload(w, precision=F64, graph_steps=16)
+    m = pdgb.Model.from_workload(w, precision=precision, graph_steps=16)
     m.step(steps)
     ug, vg = m.state()
     b, phi = m.bonds(), m.damage()
     m.close()
-    assert rel(ug, u) <= 1e-10 and rel(vg, v) <= 1e-9
+    assert rel(ug, u) <= 1e-10 and rel(vg, v) <= 1e-9, (rel(ug, u), rel(vg, v))
     diff = b != mu
     assert np.all(margin[diff] < BAND), int(diff.sum())
     assert np.abs(phi - om.damage(mu)).max() <= 1e-12 + 2.0 * diff.sum() / len(diff)
     return mu
 
 
+@pytest.mark.parametrize("precision", [F64, DW])
 @pytest.mark.parametrize("nu", [0.25, 0.35])
-def test_state_based_tensile_bar_matches_oracle(nu):
+def test_state_based_tensile_bar_matches_oracle(nu, precision):
+    # FP64 and the FP64-grade double-word step are held to the same bar
     w = workloads.tensile_bar(steps=1000)
     w.state_based = _moduli(w.bulk_modulus, nu)
-    mu = _compare(w, w.steps)
+    mu = _compare(w, w.steps, precision)
     assert (mu == 0).sum() > 0
 
 
-def test_state_based_notched_beam_per_bond_sc():
+@pytest.mark.parametrize("precision", [F64, DW])
+def test_state_based_notched_beam_per_bond_sc(precision):
     w = workloads.notched_beam(48, 10, 12, length=48 / 600, rate=1e-7, steps=300)
     w.state_based = _moduli(w.bulk_modulus, 0.2)
-    _compare(w, w.steps)
+    _compare(w, w.steps, precision)
 
 
-def test_state_based_restrictions():
+@pytest.mark.parametrize("precision", [F64, DW])
+def test_state_based_restrictions(precision):
     w = workloads.tensile_bar(8, 4, 4, steps=5)
     w.state_based = _moduli(w.bulk_modulus, 0.3)
     with pytest.raises(pdgb.PdError) as e:
-        pdgb.Model.from_workload(w, precision=F64, integrator=pdgb.PD_INTEGRATOR_VV)
+        pdgb.Model.from_workload(w, precision=precision, integrator=pdgb.PD_INTEGRATOR_VV)
     assert e.value.name == "PD_ERR_ARG"
-    m = pdgb.Model.from_workload(w, precision=F64)
+    m = pdgb.Model.from_workload(w, precision=precision)
     off, idx = m.family()
     with pytest.raises(pdgb.PdError) as e:
         m.set_params(1.0, w.sc, 0.0, w.disp_rate, np.ones(len(idx)))
@@ -99,8 +103,9 @@ def test_state_based_fp32_matches_oracle():
     assert (mu == 0).sum() > 0 and (b != mu).sum() <= 1e-3 * len(mu)
 
 
-def test_state_based_with_smooth_ramp_matches_oracle():
+@pytest.mark.parametrize("precision", [F64, DW])
+def test_state_based_with_smooth_ramp_matches_oracle(precision):
     w = workloads.tensile_bar(steps=600)
     w.state_based = _moduli(w.bulk_modulus, 0.3)
     w.ramp_steps = 300
-    _compare(w, w.steps)
+    _compare(w, w.steps, precision)
