@@ -127,9 +127,10 @@ typedef struct {
  * function: m_i = sum_j |xi|^2 V_j, theta_i = (3/m_i) sum_j mu_ij |xi| e_ij V_j
  * (e = |y| - |xi|), t_ij = (3 K theta_i / m_i)|xi| + (15 G / m_i)(e - theta_i |xi|/3),
  * F_i = sum_j mu_ij (t_ij + t_ji) V_j y/|y|.  Bonds break as in Eq. 6.  Unlike
- * the PMB law it is not limited to Poisson's ratio 1/4.  FP64 and FP32 handles
- * (FP32: the bond-based path's records, horizon units and near-s_c FP64
- * decision) with the Euler-Cromer integrator; c is not used (any value > 0);
+ * the PMB law it is not limited to Poisson's ratio 1/4.  FP64, FP32 and
+ * PD_PREC_DW handles (FP32 and PD_PREC_DW: the bond-based path's records,
+ * horizon units and near-s_c FP64 decision) with the Euler-Cromer integrator;
+ * c is not used (any value > 0);
  * no softening, per-bond stiffness, batches or adjoint.  Two kernels per step.
  */
 
