@@ -339,7 +339,7 @@ class Model:
     def run_vv(self, first_step, nsteps, u, v, a, mu, init=False, margin=None):
         """Damped velocity-Verlet steps over all nodes (see oracle.c); u, v, a
         (acceleration) and mu updated in place.  init: form a^0 from (u, v) first."""
-        assert self.rows is None and self.m.model == 0
+        assert self.rows is None
         for arr in (u, v, a):
             assert arr.dtype == np.float64 and arr.flags.c_contiguous
         lib().or_run_vv(ctypes.byref(self.m), int(first_step), int(nsteps), int(bool(init)),

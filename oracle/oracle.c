@@ -567,10 +567,16 @@ void or_run(const or_model* m, int64_t first_step, int64_t nsteps, double* u, do
 static void vv_accel(const or_model* m, const double* u, const double* vt, uint8_t* mu,
                      double* margin, double* acc)
 {
+    /* the state-based model: its first loop (dilations, bonds past s_c break)
+     * before the forces, as in or_step */
+    if (m->model == 1) osb_dilation(m, u, mu, margin, 1);
 #pragma omp parallel for schedule(dynamic, 256)
     for (int64_t i = 0; i < m->n; ++i) {
         double F[3];
-        row_force(m, i, u, mu, margin, F);
+        if (m->model == 1)
+            osb_force(m, i, u, mu, F);
+        else
+            row_force(m, i, u, mu, margin, F);
         for (int a = 0; a < 3; ++a)
             acc[3 * i + a] = m->bc_type[3 * i + a] == 1
                                  ? 0.0

@@ -95,3 +95,50 @@ def test_rigid_motion_is_force_free_and_momentum_is_conserved():
     u = rng.uniform(-2e-6, 2e-6, x.shape)
     _, _, F = m.step(0, u, np.zeros_like(u), mu, want_force=True)
     assert np.abs((vol[:, None] * F).sum(0)).max() <= 1e-12 * np.abs(vol[:, None] * F).sum()
+
+
+def test_velocity_verlet_conserves_the_state_based_energy():
+    # undamped, unloaded, nothing breaks: the velocity-Verlet run of the linear
+    # solid keeps kinetic + strain energy to O(dt^2) (it is symplectic), which it
+    # does only if the integrator applies this model's forces (minus the gradient
+    # of the same energy); the Euler-Cromer run of the same state agrees to O(dt)
+    x = workloads.lattice(8, 6, 6, 1e-3, jitter=0.15, seed=4)
+    vol = np.full(x.shape[0], 1e-9)
+    off, idx = oracle.family(x, 3.01e-3)
+    K, G, rho = 3e9, 1.4e9, 2400.0
+    mk = lambda dt: oracle.Model(x, vol, off, idx, c=1.0, sc=1.0, state_based=(K, G),
+                                 dt=dt, damping=0.0, density=rho)
+    rng = np.random.default_rng(9)
+    u0 = rng.normal(0.0, 2e-8, x.shape)
+    v0 = rng.normal(0.0, 1e-3, x.shape)
+
+    def energy(m, u, v, mu):
+        return float((vol * (0.5 * rho * (v * v).sum(axis=1) + m.energy_density(u, mu))).sum())
+
+    dt, n = 2e-8, 400
+    m = mk(dt)
+    u, v, a, mu = u0.copy(), v0.copy(), np.zeros_like(x), m.fresh_bonds()
+    E0 = energy(m, u, v, mu)
+    m.run_vv(0, 1, u, v, a, mu, init=True)
+    drift = 0.0
+    for k in range(1, n):
+        m.run_vv(k, 1, u, v, a, mu)
+        drift = max(drift, abs(energy(m, u, v, mu) - E0) / E0)
+    assert mu.all() and drift < 2e-4, drift
+    # a wrong force (here: half of it) is not conservative with this energy
+    m2 = oracle.Model(x, vol, off, idx, c=1.0, sc=1.0, state_based=(K, G), dt=dt, damping=0.0,
+                      density=2.0 * rho)
+    u2, v2, a2, mu2 = u0.copy(), v0.copy(), np.zeros_like(x), m2.fresh_bonds()
+    m2.run_vv(0, n, u2, v2, a2, mu2, init=True)
+    assert abs(energy(m, u2, v2, mu2) - E0) / E0 > 20 * drift
+    # Euler-Cromer agrees to first order in dt
+    errs = []
+    for h in (dt, dt / 2):
+        steps = int(round(n * dt / h))
+        mv, me = mk(h), mk(h)
+        uv, vv_, av, bv = u0.copy(), v0.copy(), np.zeros_like(x), mv.fresh_bonds()
+        mv.run_vv(0, steps, uv, vv_, av, bv, init=True)
+        ue, ve, be = u0.copy(), v0.copy(), me.fresh_bonds()
+        me.run(0, steps, ue, ve, be)
+        errs.append(np.abs(ue - uv).max())
+    assert 1.6 < errs[0] / errs[1] < 2.5, errs
