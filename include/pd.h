@@ -59,8 +59,8 @@ typedef enum {
                             bond-force relative error ~1e-13), and the break test
                             decided against the FP64 s_c.  Everything PD_PREC_F64
                             offers: both integrators, per-bond stiffness,
-                            softening, batches, the state-based model (Euler-Cromer)
-                            and the adjoint, which runs in double-word arithmetic
+                            softening, batches, the state-based model and the
+                            adjoint, which runs in double-word arithmetic
                             as well (see pd_adjoint_forward).
                             pd_get_info reports 48. */
 #define PD_MAX_FAMILY 1024
@@ -129,7 +129,7 @@ typedef struct {
  * F_i = sum_j mu_ij (t_ij + t_ji) V_j y/|y|.  Bonds break as in Eq. 6.  Unlike
  * the PMB law it is not limited to Poisson's ratio 1/4.  FP64, FP32 and
  * PD_PREC_DW handles (FP32 and PD_PREC_DW: the bond-based path's records,
- * horizon units and near-s_c FP64 decision) with the Euler-Cromer integrator;
+ * horizon units and near-s_c FP64 decision) with either integrator;
  * c is not used (any value > 0);
  * no softening, per-bond stiffness, batches or adjoint.  Two kernels per step.
  */

@@ -473,13 +473,20 @@ pd_status vv_force_pass(pd_handle* h)
         StepArgsF32 a = args_f32(h, 0);
         a.peek = 1;
         a.vout = (float*)h->vpeek;
-        e = launch_f32(h, a);
+        e = h->model == 1 ? launch_osb32_step(a, osb32_args(h), h->sc_mode, h->grid, h->block,
+                                              h->stream)
+                          : launch_f32(h, a);
     } else {
         StepArgsF64 a = args_f64(h, 0);
         a.peek = 1;
         a.vout = (double*)h->vpeek;
-        e = h->dw ? launch_step_dw(a, dw_args(h), h->sc_mode, h->grid, h->block, h->stream)
-                  : launch_step_f64(a, h->sc_mode, h->grid, h->block, h->stream);
+        if (h->model == 1)
+            e = h->dw ? launch_osb_dw_step(a, dw_args(h), osbdw_args(h), h->grid, h->block,
+                                           h->stream)
+                      : launch_osb_step(a, osb_args(h), h->grid, h->block, h->stream);
+        else
+            e = h->dw ? launch_step_dw(a, dw_args(h), h->sc_mode, h->grid, h->block, h->stream)
+                      : launch_step_f64(a, h->sc_mode, h->grid, h->block, h->stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "velocity-Verlet force pass");
     h->peek_step = h->step;
@@ -703,8 +710,6 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
         ALLOC(h->ilen, double, nbr.size());  // also the adjoint's
     }
     if (h->model == 1) {
-        if (h->integrator != PD_INTEGRATOR_EC)
-            return fail(PD_ERR_ARG, "the state-based model uses the Euler-Cromer integrator");
         if (f32) {
             ALLOC(h->osb32_len, float, nbr.size());
             ALLOC(h->osb32_mvol, float, np);

@@ -35,21 +35,38 @@ __device__ __forceinline__ void integrate_osb_f32(const StepArgsF32& a, int64_t 
     const float4 lo = a.lo32[i];
     float H[3] = {ni.hx, ni.hy, ni.hz};
     float L[3] = {lo.x, lo.y, lo.z};
+    // velocity-Verlet: a^n is formed afresh at the step the state was set
+    const bool first = a.vv && step == a.step_ctr[1];
     bool finite = true;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
+        // stored velocity: v^n (Euler-Cromer) or the half-step velocity
+        // (velocity-Verlet), as in the bond-based FP32 step
         const float vi = a.v[3 * i + c];
-        float vn = vi + dtf * (F[c] - etaf * vi) / rhof;
+        float vn, vfull;
+        if (a.vv) {
+            const float acc = (F[c] - etaf * vi) / rhof;
+            vfull = first ? vi : vi + 0.5f * dtf * acc;
+            vn = vfull + 0.5f * dtf * acc;
+        } else {
+            vn = vi + dtf * (F[c] - etaf * vi) / rhof;
+            vfull = vn;
+        }
         ff_add(H[c], L[c], vn * dtd);
         if (mask & (1u << c)) {
             const double s_now = bc_scale(a.disp_rate, a.ramp_steps, step);
             const double s_next = bc_scale(a.disp_rate, a.ramp_steps, step + 1);
             ff_set(bc->disp[c] * s_next * a.inv_delta, H[c], L[c]);
             vn = (float)(bc->disp[c] * (s_next - s_now) / a.dt);
+            vfull = vi;
         }
         finite = finite && isfinite(H[c]);
-        a.v[3 * i + c] = vn;
+        if (a.peek)
+            a.vout[3 * i + c] = vfull;
+        else
+            a.v[3 * i + c] = vn;
     }
+    if (a.peek) return;  // the read-only force pass of velocity-Verlet
     st_rec(Rout + 2 * i, make_float4(ni.x, ni.y, ni.z, H[0]),
            make_float4(H[1], H[2], bf_pack(L[1], L[0]), bf_pack(0.0f, L[2])));
     a.lo32[i] = make_float4(L[0], L[1], L[2], 0.0f);

@@ -7,8 +7,8 @@
 //                   theta_i = (3 / m_i) sum_j mu_ij |xi| e_ij V_j, e = |y| - |xi|
 //   k_osb_force     per node: F_i = sum_j mu_ij (t_ij + t_ji) V_j y / |y| with
 //                   t_ij = (3 K theta_i / m_i) |xi| + (15 G / m_i)(e - theta_i |xi| / 3);
-//                   then the damped Euler-Cromer update, boundary conditions
-//                   and damage of the bond-based FP64 step
+//                   then the damped Euler-Cromer or velocity-Verlet update,
+//                   boundary conditions and damage of the bond-based FP64 step
 //
 // m_i = sum_j |xi|^2 V_j over the family after the initial cuts, computed once.
 // t_ij is linear in the bond: t_ij = alpha_i |xi| + beta_i e with
@@ -184,21 +184,38 @@ __global__ void __launch_bounds__(256) k_osb_force(const StepArgsF64 a, OsbArgs 
         const double s_now = bc_scale(a.disp_rate, a.ramp_steps, step);
         const double s_next = bc_scale(a.disp_rate, a.ramp_steps, step + 1);
         const double uo[3] = {u01.x, u01.y, u23.x};
+        // velocity-Verlet: a^n is formed afresh at the step the state was set
+        const bool first = a.vv && step == a.step_ctr[1];
         double un[3];
         bool finite = true;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
+            // stored velocity: v^n (Euler-Cromer) or the half-step velocity
+            // (velocity-Verlet), as in the bond-based FP64 step
             const double vi = a.v[3 * i + c];
-            double vn = vi + a.dt * (F[c] - a.eta * vi) / a.rho;
+            double vn, vfull;
+            if (a.vv) {
+                const double acc = (F[c] - a.eta * vi) / a.rho;
+                vfull = first ? vi : vi + 0.5 * a.dt * acc;
+                vn = vfull + 0.5 * a.dt * acc;
+            } else {
+                vn = vi + a.dt * (F[c] - a.eta * vi) / a.rho;
+                vfull = vn;
+            }
             double u = uo[c] + a.dt * vn;
             if (mask & (1u << c)) {
                 u = gdisp[c] * s_next;
                 vn = gdisp[c] * (s_next - s_now) / a.dt;
+                vfull = vi;
             }
             finite = finite && isfinite(u);
             un[c] = u;
-            a.v[3 * i + c] = vn;
+            if (a.peek)
+                a.vout[3 * i + c] = vfull;
+            else
+                a.v[3 * i + c] = vn;
         }
+        if (a.peek) continue;  // the read-only force pass of velocity-Verlet
         rout[4 * i] = x01;
         rout[4 * i + 1] = x23;
         rout[4 * i + 2] = make_double2(un[0], un[1]);

@@ -16,8 +16,8 @@
 // the band below the smallest s_c; the force loop reads the flags it left.
 // Per node the coefficients alpha~, beta~ are published as double-words
 // ({alpha_h, alpha_l, beta_h, beta_l}, one 128-bit load per neighbour); the
-// integration, boundary conditions and damage are the bond-based double-word
-// step's, in FP64.
+// integration (Euler-Cromer or velocity-Verlet), boundary conditions and
+// damage are the bond-based double-word step's, in FP64.
 #include <cuda_runtime.h>
 
 #include "pd_dw.h"
@@ -315,23 +315,37 @@ __global__ void __launch_bounds__(256, 2)
         const double s_next = bc_scale(a.disp_rate, a.ramp_steps, step + 1);
         const double2 u01 = rin[4 * i + 2], u23 = rin[4 * i + 3];
         const double uo[3] = {u01.x, u01.y, u23.x};
+        const bool first = a.vv && step == a.step_ctr[1];
         double un[3];
         float uh[3], ul[3];
         bool finite = true;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const double vi = a.v[3 * i + k];
-            double vn = vi + (Fn[k] - a.eta * vi) * d.dt_rho;
+            const double adt = (Fn[k] - a.eta * vi) * d.dt_rho;  // dt a
+            double vn, vfull;
+            if (a.vv) {
+                vfull = first ? vi : vi + 0.5 * adt;
+                vn = vfull + 0.5 * adt;
+            } else {
+                vn = vi + adt;
+                vfull = vn;
+            }
             double u = uo[k] + a.dt * vn;
             if (mask & (1u << k)) {
                 u = gdisp[k] * s_next;
                 vn = gdisp[k] * (s_next - s_now) / a.dt;
+                vfull = vi;
             }
             finite = finite && isfinite(u);
             un[k] = u;
-            a.v[3 * i + k] = vn;
+            if (a.peek)
+                a.vout[3 * i + k] = vfull;
+            else
+                a.v[3 * i + k] = vn;
             split(u * d.inv_delta, uh[k], ul[k]);
         }
+        if (a.peek) continue;  // the read-only force pass of velocity-Verlet
         rout[4 * i] = rin[4 * i];
         rout[4 * i + 1] = rin[4 * i + 1];
         rout[4 * i + 2] = make_double2(un[0], un[1]);

@@ -68,9 +68,6 @@ def test_state_based_notched_beam_per_bond_sc(precision):
 def test_state_based_restrictions(precision):
     w = workloads.tensile_bar(8, 4, 4, steps=5)
     w.state_based = _moduli(w.bulk_modulus, 0.3)
-    with pytest.raises(pdgb.PdError) as e:
-        pdgb.Model.from_workload(w, precision=precision, integrator=pdgb.PD_INTEGRATOR_VV)
-    assert e.value.name == "PD_ERR_ARG"
     m = pdgb.Model.from_workload(w, precision=precision)
     off, idx = m.family()
     with pytest.raises(pdgb.PdError) as e:
@@ -109,3 +106,50 @@ def test_state_based_with_smooth_ramp_matches_oracle(precision):
     w.state_based = _moduli(w.bulk_modulus, 0.3)
     w.ramp_steps = 300
     _compare(w, w.steps, precision)
+
+
+@pytest.mark.parametrize("precision", [F64, DW, F32])
+def test_state_based_velocity_verlet_matches_oracle(precision):
+    w = workloads.tensile_bar(steps=700)
+    w.state_based = _moduli(w.bulk_modulus, 0.3)
+    off, idx = oracle.cut_family(w.coords, w.horizon, w.cuts_array())
+    om = oracle.Model.from_workload(w, off, idx)
+    steps = w.steps if precision != F32 else 400  # FP32: before the first breaks (R13)
+    u, v, acc = np.zeros((w.n, 3)), np.zeros((w.n, 3)), np.zeros((w.n, 3))
+    mu = om.fresh_bonds()
+    margin = np.full(len(mu), np.inf)
+    om.run_vv(0, steps, u, v, acc, mu, init=True, margin=margin)
+    m = pdgb.Model.from_workload(w, precision=precision, graph_steps=16,
+                                 integrator=pdgb.PD_INTEGRATOR_VV)
+    m.step(steps)
+    ug, vg = m.state()
+    b = m.bonds()
+    m.close()
+    if precision == F32:
+        assert (mu == 0).sum() == 0 and rel(ug, u) <= 1e-4
+        return
+    assert (mu == 0).sum() > 0
+    assert rel(ug, u) <= 1e-10 and rel(vg, v) <= 1e-9, (rel(ug, u), rel(vg, v))
+    diff = b != mu
+    assert np.all(margin[diff] < BAND), int(diff.sum())
+
+
+@pytest.mark.parametrize("precision", [F64, DW, F32])
+def test_state_based_full_step_velocity_read_changes_nothing(precision):
+    w = workloads.tensile_bar(steps=300)
+    w.state_based = _moduli(w.bulk_modulus, 0.3)
+    vv = pdgb.PD_INTEGRATOR_VV
+    ref = pdgb.Model.from_workload(w, precision=precision, integrator=vv)
+    ref.step(300)
+    ur, vr = ref.state()
+    br = ref.bonds()
+    ref.close()
+    m = pdgb.Model.from_workload(w, precision=precision, integrator=vv, graph_steps=25)
+    for _ in range(6):
+        m.step(50)
+        m.state()
+        m.bonds()
+    u, v = m.state()
+    b = m.bonds()
+    m.close()
+    assert np.array_equal(u, ur) and np.array_equal(v, vr) and np.array_equal(b, br)
