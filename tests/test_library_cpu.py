@@ -83,6 +83,18 @@ def test_create_rejects_bad_arguments(L, over, status):
     assert e.value.name == status
 
 
+def test_batch_rejects_differing_softening_laws(L):
+    # the softening law is handle-wide: every instance must agree with instance 0
+    # (checked before any device work)
+    ws = [workloads.tensile_bar(6, 4, 4), workloads.tensile_bar(7, 4, 4)]
+    for (kr0, t0), (kr1, t1) in (((2.0, None), (3.0, None)), ((0.0, None), (2.0, None)),
+                                 ((4.0, (2.0, 0.25)), (4.0, (2.0, 0.5)))):
+        ws[0].kr, ws[0].trilinear, ws[1].kr, ws[1].trilinear = kr0, t0, kr1, t1
+        with pytest.raises(pdgb.PdError) as e:
+            pdgb.Model.batch(ws, precision=pdgb.PD_PREC_DW)
+        assert e.value.name == "PD_ERR_ARG" and "instance 1" in str(e.value)
+
+
 def test_create_rejects_bad_geometry_and_family(L):
     w = workloads.tensile_bar(6, 4, 4)
     x = w.coords.copy()
