@@ -1,7 +1,7 @@
 """torch.autograd.Function around the hand-written adjoint (pd_adjoint_*).
 
 ``PeridynamicRun.apply(c_bond, load, u0, v0, model, n_steps, checkpoint_every)``
-runs ``n_steps`` damped Euler-Cromer steps of ``model`` (an FP64
+runs ``n_steps`` damped Euler-Cromer steps of ``model`` (an FP64 or PD_PREC_DW
 ``paper_2105_04150_gb300.Model``) from (u0, v0) with the bond flags frozen, with
 the per-directed-bond stiffness ``c_bond`` and body-force scale ``load``, and
 returns the final displacement u^N (n x 3).  Its backward runs the library's

@@ -1383,7 +1383,8 @@ pd_status pd_adjoint_forward(pd_handle* h, int64_t n_steps, int64_t checkpoint_e
     if (h->precision != 64 || h->batch || h->integrator != PD_INTEGRATOR_EC || h->integ ||
         h->model != 0)
         return fail(PD_ERR_STATE,
-                    "the adjoint is available on FP64 single-model Euler-Cromer PMB handles");
+                    "the adjoint is available on FP64 and PD_PREC_DW single-model "
+                    "Euler-Cromer PMB handles");
     if (n_steps < 1 || checkpoint_every < 0)
         return fail(PD_ERR_ARG, "need n_steps >= 1 and checkpoint_every >= 0");
     PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
