@@ -131,7 +131,9 @@ def describe(w, n_bonds, precision, integrator="ec"):
                       48: "fp64-grade: double-word fp32 bonds, fp64 node state"}[precision],
         "n_nodes": w.n,
         "n_bonds": int(n_bonds),
-        "l2_policy": "inputs larger than L2 (padded family index > 129 MB streamed per step)",
+        "l2_policy": ("inputs larger than L2 (family index > 129 MB streamed per step)"
+                      if 4 * n_bonds > 129e6 else
+                      "inputs smaller than L2, no flush between steps (a parity-size case)"),
     }
 
 
@@ -289,6 +291,7 @@ def oracle_sample(w, c, budget_s, steps=None, warmup=0):
     return {
         "value": m.nbonds * n_steps / el, "unit": "bond updates/s", "cores": cores,
         "kind": "oracle", "seconds": el, "steps": n_steps,
+        "n_bonds_total": m.nbonds if rows is None else None,
         "sample": f"{n_steps} oracle FP64 steps over {m.nrows:,} of {w.n:,} rows "
                   f"({m.nbonds:,} bonds each) of the same workload, OpenMP on {cores} host threads",
     }
@@ -301,16 +304,29 @@ def run_reference(args):
     import oracle
     oracle.build()
     w = make_workload(args.workload)
+    w.ramp_steps = args.ramp_steps
+    w.kr = args.kr
+    if args.state_based is not None:
+        nu = args.state_based
+        w.state_based = (w.bulk_modulus, 3 * w.bulk_modulus * (1 - 2 * nu) / (2 * (1 + nu)))
     c = oracle.micromodulus(w.bulk_modulus, w.horizon)
     # each timed step is a row sample sized so the whole run takes about a minute
     budget = float(os.environ.get("BENCH_REFERENCE_BUDGET_S", "60"))
     res = oracle_sample(w, c, budget_s=budget, steps=args.steps, warmup=args.warmup)
+    # the workload's directed bonds, for the same config object as our arm's
+    n_bonds = res["n_bonds_total"]
+    if n_bonds is None:
+        n_bonds = 0
+        for lo in range(0, w.n, 1 << 20):
+            rows = np.arange(lo, min(w.n, lo + (1 << 20)))
+            off, _ = oracle.cut_family(w.coords, w.horizon, w.cuts_array(), rows=rows)
+            n_bonds += int(off[-1])
     line = {
         "impl": "reference", "metric": "bond updates/s", "value": res["value"],
         "unit": "bond updates/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["seconds"] * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": w.name, "sample": res["sample"]},
+        "data": "synthetic", "config": describe(w, n_bonds, args.precision, args.integrator),
         "cpu_baseline": {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")},
         "e2e": {"value": res["value"], "unit": "bond updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
