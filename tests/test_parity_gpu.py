@@ -322,7 +322,7 @@ def test_nonfinite_state_is_reported():
     import torch
     w = workloads.tensile_bar(10, 4, 4, steps=3)
     c = oracle.micromodulus(w.bulk_modulus, w.horizon)
-    for prec in (F64, F32):
+    for prec in (F64, F32, pdgb.PD_PREC_DW):
         m = pdgb.Model.from_workload(w, precision=prec, c=c)
         bad = np.zeros((w.n, 3))
         bad[7, 1] = np.nan
