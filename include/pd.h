@@ -293,6 +293,21 @@ pd_status pd_get_bond_integrity(pd_handle* h, double* mu);
 pd_status pd_set_bonds(pd_handle* h, const uint8_t* mu);
 
 /*
+ * pd_remove_bonds - break m bonds after creation, e.g. to cut a notch or a
+ * pre-crack into a model built without one: the notched beams of Section 6
+ * break every bond crossing the notch's void as an initial condition, and a
+ * broken bond carries no force for the rest of the run (Eq. 6).  pairs: host,
+ * 2*m int64 node ids (i, j) in the caller's order (the concatenated ids of a
+ * batch); both directions i->j and j->i are broken.  Every pair must be a bond
+ * of the family after the initial cuts; nothing changes if one is not
+ * (PD_ERR_ARG names it).  Unlike an initial cut, a removed bond stays in the
+ * family, so it counts as broken in pd_damage (Eq. 8).  With bilinear
+ * softening the integrity of the removed bonds becomes 0.  Synchronises the
+ * handle's stream; m = 0 does nothing.
+ */
+pd_status pd_remove_bonds(pd_handle* h, const int64_t* pairs, int64_t m);
+
+/*
  * pd_damage - phi_i = 1 - sum_j mu_ij V_j / sum_j V_j over the family after the
  * initial cuts (Eq. 8), for the current state.  phi: n doubles, host or device.
  */

@@ -23,7 +23,7 @@ from . import _build
 __all__ = [
     "PdError", "build", "lib", "pd_micromodulus", "pd_create", "pd_destroy", "pd_last_error",
     "pd_get_info", "pd_get_family", "pd_step", "pd_sync", "pd_get_state", "pd_set_state",
-    "pd_get_bonds", "pd_set_bonds", "pd_damage", "pd_set_params", "pd_batch_create",
+    "pd_get_bonds", "pd_set_bonds", "pd_remove_bonds", "pd_damage", "pd_set_params", "pd_batch_create",
     "pd_batch_offsets", "pd_autotune", "pd_adjoint_forward", "pd_adjoint_backward",
     "pd_adjoint_backward_static", "pd_stiffness_factors", "pd_get_bond_integrity", "PD_STIFF_CONICAL",
     "PD_STIFF_SURFACE", "PD_STIFF_PARTIAL", "PD_INTEGRATOR_EC", "PD_INTEGRATOR_VV",
@@ -116,6 +116,7 @@ def lib():
             "pd_set_state": [P, P, P, I64],
             "pd_get_bonds": [P, P],
             "pd_set_bonds": [P, P],
+            "pd_remove_bonds": [P, P, I64],
             "pd_damage": [P, P],
             "pd_set_params": [P, D, D, D, D, P],
             "pd_batch_create": [I32, P, P, P],
@@ -288,6 +289,12 @@ def pd_set_bonds(h: int, mu) -> None:
     if nb == 0:
         return
     _check(lib().pd_set_bonds(h, p))
+
+
+def pd_remove_bonds(h: int, pairs) -> None:
+    """Break the bonds (i, j) and (j, i) of every row of pairs (m x 2 node ids)."""
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int64).reshape(-1, 2))
+    _check(lib().pd_remove_bonds(h, pr.ctypes.data if pr.size else None, pr.shape[0]))
 
 
 def pd_damage(h: int, phi=None):
@@ -509,6 +516,9 @@ class Model:
 
     def set_bonds(self, mu):
         pd_set_bonds(self.h, mu)
+
+    def remove_bonds(self, pairs):
+        pd_remove_bonds(self.h, pairs)
 
     def damage(self, phi=None):
         return pd_damage(self.h, phi)

@@ -1356,6 +1356,72 @@ pd_status pd_set_bonds(pd_handle* h, const uint8_t* mu)
     return PD_OK;
 }
 
+pd_status pd_remove_bonds(pd_handle* h, const int64_t* pairs, int64_t m)
+{
+    if (!h || (m > 0 && !pairs) || m < 0) return fail(PD_ERR_ARG, "need a handle, m >= 0 and pairs");
+    if (m == 0) return PD_OK;
+    // canonical index of both directions of every pair, checked before anything changes
+    std::vector<int64_t> kset;
+    kset.reserve((size_t)(2 * m));
+    for (int64_t e = 0; e < m; ++e) {
+        const int64_t i = pairs[2 * e], j = pairs[2 * e + 1];
+        if (i < 0 || j < 0 || i >= h->n || j >= h->n || i == j)
+            return fail(PD_ERR_ARG, "pair %lld: (%lld, %lld) is not a pair of distinct nodes",
+                        (long long)e, (long long)i, (long long)j);
+        for (int dir = 0; dir < 2; ++dir) {
+            const int64_t a = dir ? j : i, b = dir ? i : j;
+            const int32_t* lo = h->idx.data() + h->off[a];
+            const int32_t* hi = h->idx.data() + h->off[a + 1];
+            const int32_t* it = std::lower_bound(lo, hi, (int32_t)b);  // rows are sorted
+            const int64_t k = (it != hi && *it == b) ? (int64_t)(it - h->idx.data()) : -1;
+            if (k < 0)
+                return fail(PD_ERR_ARG, "pair %lld: %lld -> %lld is not a bond of the family",
+                            (long long)e, (long long)a, (long long)b);
+            kset.push_back(k);
+        }
+    }
+    PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    pd_status st = vv_force_pass(h);  // a pending Velocity-Verlet force pass sees the old bonds
+    if (st != PD_OK) return st;
+    std::vector<int64_t> pos;
+    if ((st = canonical_slots(h, pos)) != PD_OK) return st;
+    std::vector<int64_t> slot_of((size_t)h->n_bonds, -1);
+    for (size_t q = 0; q < pos.size(); ++q)
+        if (pos[q] >= 0) slot_of[(size_t)pos[q]] = (int64_t)q;
+    const int64_t W = 32LL * h->Q;
+    const size_t nk = kset.size();
+    std::vector<int64_t> word(nk), slot(nk);
+    std::vector<uint32_t> mask(nk);
+    for (size_t e = 0; e < nk; ++e) {
+        const int64_t q = slot_of[(size_t)kset[e]];
+        if (q < 0) return fail(PD_ERR_STATE, "bond without a slot");
+        const int64_t g = q / (32 * W), r = q % (32 * W), mm = r / 32, l = r % 32;
+        word[e] = (g * h->Q + (mm >> 5)) * 32 + l;
+        mask[e] = 1u << (mm & 31);
+        slot[e] = q;
+    }
+    int64_t* d_word = nullptr;
+    int64_t* d_slot = nullptr;
+    uint32_t* d_mask = nullptr;
+    cudaError_t e = cudaMalloc(&d_word, nk * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&d_slot, nk * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&d_mask, nk * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(d_word, word.data(), nk * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_slot, slot.data(), nk * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_mask, mask.data(), nk * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = launch_clear_slots(h->bits, d_word, d_mask, d_slot, (int64_t)nk, h->precision,
+                               h->integ, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(d_word);
+    cudaFree(d_slot);
+    cudaFree(d_mask);
+    PD_CUDA(e, "remove bonds");
+    h->damage_fresh = false;
+    h->peek_step = -1;
+    return PD_OK;
+}
+
 pd_status pd_damage(pd_handle* h, double* phi)
 {
     if (!h || !phi) return fail(PD_ERR_ARG, "NULL argument");

@@ -315,6 +315,33 @@ __global__ void k_fill(T* __restrict__ dst, int64_t n, T v)
     GRID_STRIDE(e, n) dst[e] = v;
 }
 
+// clear bond-flag bits (word index, mask of bits to clear) and zero the
+// integrity of the same slots (softening handles)
+__global__ void k_clear_slots(uint32_t* __restrict__ bits, const int64_t* __restrict__ word,
+                              const uint32_t* __restrict__ mask, const int64_t* __restrict__ slot,
+                              int64_t m, int precision, void* integ)
+{
+    GRID_STRIDE(e, m)
+    {
+        atomicAnd(bits + word[e], ~mask[e]);
+        if (integ != nullptr) {
+            if (precision == 32)
+                static_cast<float*>(integ)[slot[e]] = 0.0f;
+            else
+                static_cast<double*>(integ)[slot[e]] = 0.0;
+        }
+    }
+}
+
+cudaError_t launch_clear_slots(uint32_t* bits, const int64_t* word, const uint32_t* mask,
+                               const int64_t* slot, int64_t m, int precision, void* integ,
+                               cudaStream_t s)
+{
+    if (m <= 0) return cudaSuccess;
+    k_clear_slots<<<grid_for(m, 256), 256, 0, s>>>(bits, word, mask, slot, m, precision, integ);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_check_finite(const double* x, int64_t m, int* flag, cudaStream_t s)
 {
     if (m <= 0) return cudaSuccess;

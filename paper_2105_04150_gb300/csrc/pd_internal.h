@@ -317,6 +317,11 @@ cudaError_t launch_damage(int precision, const void* wrec, const int32_t* nbr,
                           double* phi_out, cudaStream_t s);
 // flag |= 1 if any of x[0..m) is not finite
 cudaError_t launch_check_finite(const double* x, int64_t m, int* flag, cudaStream_t s);
+// clear the bond flags of m slots (bits[word[e]] &= ~mask[e]) and zero their
+// integrity when integ is not null (float for precision 32, else double)
+cudaError_t launch_clear_slots(uint32_t* bits, const int64_t* word, const uint32_t* mask,
+                               const int64_t* slot, int64_t m, int precision, void* integ,
+                               cudaStream_t s);
 // fill n values of `precision` (32 or 64) with v
 cudaError_t launch_fill(int precision, void* dst, int64_t n, double v, cudaStream_t s);
 // damage written by the last step -> caller order
