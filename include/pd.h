@@ -180,6 +180,22 @@ typedef struct {
 pd_status pd_micromodulus(double K, double delta, double* c_out);
 
 /*
+ * pd_critical_stretch - the critical stretch of Eq. 7 from the fracture energy
+ * release rate G_F (J/m^2), Young's modulus E (Pa; E = 3 K (1 - 2 nu)) and the
+ * horizon delta (m), for a three-dimensional body or a plane-stress or
+ * plane-strain two-dimensional one:
+ *   PD_DIM_3D        s_c = sqrt(5 G_F / (6 E delta))
+ *   PD_PLANE_STRESS  s_c = sqrt(4 pi G_F / (9 E delta))
+ *   PD_PLANE_STRAIN  s_c = sqrt(5 pi G_F / (12 E delta))
+ * Host-only.  PD_ERR_ARG unless G_F, E and delta are finite and > 0 and dim is
+ * one of the three.
+ */
+#define PD_PLANE_STRESS 1
+#define PD_PLANE_STRAIN 2
+#define PD_DIM_3D 3
+pd_status pd_critical_stretch(double G_F, double E, double delta, int32_t dim, double* s_c_out);
+
+/*
  * pd_stiffness_factors - stiffness corrections as per-bond factors, one per
  * directed bond of the family (fam_off[n+1], fam_idx: canonical order, e.g.
  * from pd_get_family), to pass as c_bond = c * factor to pd_set_params:

@@ -107,6 +107,10 @@ def lib():
         L.or_micromodulus.argtypes = [ctypes.c_double, ctypes.c_double]
         L.or_critical_stretch_3d.restype = ctypes.c_double
         L.or_critical_stretch_3d.argtypes = [ctypes.c_double] * 3
+        L.or_critical_stretch_2d.restype = ctypes.c_double
+        L.or_critical_stretch_2d.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int]
+        L.or_youngs_modulus.restype = ctypes.c_double
+        L.or_youngs_modulus.argtypes = [ctypes.c_double] * 2
         L.or_splitmix64.restype = ctypes.c_uint64
         L.or_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
         L.or_sc_bond.restype = ctypes.c_double
@@ -171,6 +175,19 @@ def micromodulus(K: float, delta: float) -> float:
 
 def critical_stretch_3d(G_F: float, E: float, delta: float) -> float:
     return lib().or_critical_stretch_3d(G_F, E, delta)
+
+
+def critical_stretch(G_F: float, E: float, delta: float, kind: str = "3d") -> float:
+    """Eq. 7 for kind "3d", "plane_stress" or "plane_strain"."""
+    if kind == "3d":
+        return lib().or_critical_stretch_3d(G_F, E, delta)
+    if kind not in ("plane_stress", "plane_strain"):
+        raise ValueError(kind)
+    return lib().or_critical_stretch_2d(G_F, E, delta, int(kind == "plane_strain"))
+
+
+def youngs_modulus(K: float, nu: float) -> float:
+    return lib().or_youngs_modulus(K, nu)
 
 
 def splitmix64(seed: int, m: int) -> int:

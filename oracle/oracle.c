@@ -63,6 +63,21 @@ double or_critical_stretch_3d(double G_F, double E, double delta)
     return sqrt(5.0 * G_F / (6.0 * E * delta));
 }
 
+/* Eq. (7), the two-dimensional cases: plane stress s_c = sqrt(4 pi G_F / (9 E delta)),
+ * plane strain s_c = sqrt(5 pi G_F / (12 E delta)). */
+double or_critical_stretch_2d(double G_F, double E, double delta, int plane_strain)
+{
+    if (plane_strain) return sqrt(5.0 * M_PI * G_F / (12.0 * E * delta));
+    return sqrt(4.0 * M_PI * G_F / (9.0 * E * delta));
+}
+
+/* Young's modulus from the bulk modulus and Poisson's ratio, E = 3 K (1 - 2 nu)
+ * (the relation quoted with Eq. 7). */
+double or_youngs_modulus(double K, double nu)
+{
+    return 3.0 * K * (1.0 - 2.0 * nu);
+}
+
 /* SplitMix64: the m-th output (m >= 1) of the generator seeded with `seed`. */
 uint64_t or_splitmix64(uint64_t seed, uint64_t m)
 {

@@ -21,14 +21,14 @@ import numpy as np
 from . import _build
 
 __all__ = [
-    "PdError", "build", "lib", "pd_micromodulus", "pd_create", "pd_destroy", "pd_last_error",
+    "PdError", "build", "lib", "pd_micromodulus", "pd_critical_stretch", "pd_create", "pd_destroy", "pd_last_error",
     "pd_get_info", "pd_get_family", "pd_step", "pd_sync", "pd_get_state", "pd_set_state",
     "pd_get_bonds", "pd_set_bonds", "pd_remove_bonds", "pd_damage", "pd_set_params", "pd_batch_create",
     "pd_batch_offsets", "pd_autotune", "pd_adjoint_forward", "pd_adjoint_backward",
     "pd_adjoint_backward_static", "pd_stiffness_factors", "pd_get_bond_integrity", "PD_STIFF_CONICAL",
     "PD_STIFF_SURFACE", "PD_STIFF_PARTIAL", "PD_INTEGRATOR_EC", "PD_INTEGRATOR_VV",
     "instance_from_workload", "Model",
-    "PD_PREC_F32", "PD_PREC_F64", "PD_PREC_DW",
+    "PD_PREC_F32", "PD_PREC_F64", "PD_PREC_DW", "PD_DIM_3D", "PD_PLANE_STRESS", "PD_PLANE_STRAIN",
 ]
 
 PD_PREC_F64 = 64
@@ -37,6 +37,9 @@ PD_PREC_DW = 48  # FP64-grade bonds in double-word FP32 arithmetic, FP64 node st
 PD_STIFF_CONICAL = 1
 PD_STIFF_SURFACE = 2
 PD_STIFF_PARTIAL = 4
+PD_PLANE_STRESS = 1  # pd_critical_stretch body kinds (Eq. 7)
+PD_PLANE_STRAIN = 2
+PD_DIM_3D = 3
 PD_INTEGRATOR_EC = 0
 PD_INTEGRATOR_VV = 1
 _STATUS = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_CUDA", 3: "PD_ERR_OOM",
@@ -107,6 +110,7 @@ def lib():
         P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
         sig = {
             "pd_micromodulus": [D, D, P],
+            "pd_critical_stretch": [D, D, D, I32, P],
             "pd_create": [I64, P, P, D, P, P, P, I32, P, P, P, P],
             "pd_get_info": [P, P],
             "pd_get_family": [P, P, P],
@@ -178,6 +182,13 @@ def pd_micromodulus(K: float, delta: float) -> float:
     c = ctypes.c_double()
     _check(lib().pd_micromodulus(float(K), float(delta), ctypes.byref(c)))
     return c.value
+
+
+def pd_critical_stretch(G_F: float, E: float, delta: float, dim: int = PD_DIM_3D) -> float:
+    """s_c of Eq. 7 from the fracture energy G_F, Young's modulus E and the horizon."""
+    s = ctypes.c_double()
+    _check(lib().pd_critical_stretch(float(G_F), float(E), float(delta), int(dim), ctypes.byref(s)))
+    return s.value
 
 
 def pd_create(coords, volumes, horizon: float, *, c: float, sc: float = 0.0,

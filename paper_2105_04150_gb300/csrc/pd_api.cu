@@ -520,6 +520,21 @@ pd_status pd_micromodulus(double K, double delta, double* c_out)
     return PD_OK;
 }
 
+pd_status pd_critical_stretch(double G_F, double E, double delta, int32_t dim, double* s_c_out)
+{
+    if (!s_c_out) return fail(PD_ERR_ARG, "s_c_out is NULL");
+    if (!(G_F > 0.0) || !(E > 0.0) || !(delta > 0.0) || !std::isfinite(G_F) ||
+        !std::isfinite(E) || !std::isfinite(delta))
+        return fail(PD_ERR_ARG, "G_F, E and delta must be finite and > 0");
+    switch (dim) {
+    case PD_DIM_3D: *s_c_out = std::sqrt(5.0 * G_F / (6.0 * E * delta)); break;
+    case PD_PLANE_STRESS: *s_c_out = std::sqrt(4.0 * M_PI * G_F / (9.0 * E * delta)); break;
+    case PD_PLANE_STRAIN: *s_c_out = std::sqrt(5.0 * M_PI * G_F / (12.0 * E * delta)); break;
+    default: return fail(PD_ERR_ARG, "dim must be PD_DIM_3D, PD_PLANE_STRESS or PD_PLANE_STRAIN");
+    }
+    return PD_OK;
+}
+
 pd_status pd_stiffness_factors(int64_t n, const double* coords, const double* volumes,
                                double horizon, const int64_t* fam_off, const int32_t* fam_idx,
                                int32_t flags, double v0, double dx, double* factor)

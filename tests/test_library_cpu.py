@@ -47,6 +47,20 @@ def test_micromodulus_matches_oracle(L):
     assert e.value.name == "PD_ERR_ARG"
 
 
+
+def test_critical_stretch_matches_oracle(L):
+    kinds = {pdgb.PD_DIM_3D: "3d", pdgb.PD_PLANE_STRESS: "plane_stress",
+             pdgb.PD_PLANE_STRAIN: "plane_strain"}
+    for G_F, E, d in [(120.0, 37e9, 0.0157), (6.9e4, 190e9, 4.7e-3), (1.0, 1.0, 1.0)]:
+        for dim, kind in kinds.items():
+            got = pdgb.pd_critical_stretch(G_F, E, d, dim)
+            want = oracle.critical_stretch(G_F, E, d, kind)
+            assert abs(got - want) <= 1e-15 * want
+    for bad in [(-1.0, 1.0, 1.0, 3), (1.0, 0.0, 1.0, 3), (1.0, 1.0, float("inf"), 3),
+                (1.0, 1.0, 1.0, 0), (1.0, 1.0, 1.0, 4)]:
+        with pytest.raises(pdgb.PdError):
+            pdgb.pd_critical_stretch(*bad)
+
 def _args(w, **over):
     kw = dict(coords=w.coords, volumes=w.volumes, horizon=w.horizon, c=1e20, sc=1e-3,
               bc_type=w.bc_type, bc_disp=w.bc_disp, dt=1e-7, damping=0.0, density=2400.0)

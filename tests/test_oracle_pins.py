@@ -321,6 +321,51 @@ def test_cut_crossing_predicate():
 
 
 # ---------------------------------------------------------------- SplitMix64 draw
+@pytest.mark.parametrize("kind,nu", [("3d", 0.25), ("plane_stress", 1.0 / 3.0),
+                                     ("plane_strain", 0.25)])
+def test_critical_stretch_equals_fracture_energy_integral(kind, nu):
+    # Eq. 7 against its derivation (Silling & Askari 2005), both integrals by
+    # quadrature: the micromodulus is fixed by equating the peridynamic energy
+    # density under a uniform isotropic strain with the classical one (the
+    # bond-based Poisson ratio: 1/4 in 3D and plane strain, 1/3 in plane
+    # stress), and G_F is the energy of every bond crossing a unit fracture area
+    # when each bond is stretched to s_c (micropotential c s^2 xi / 2).
+    from scipy import integrate
+    delta, E, G = 0.0157, 37e9, 120.0
+    if kind == "3d":
+        W = E / (2.0 * (1.0 - 2.0 * nu)) * 3.0           # (9/2) K with K = E / (3 (1 - 2 nu))
+        shell = integrate.quad(lambda x: 0.5 * (x / 2.0) * 4.0 * math.pi * x * x, 0, delta,
+                               epsabs=0, epsrel=1e-13)[0]
+        c = W / shell
+        I = integrate.tplquad(lambda ph, x, z: (x / 2.0) * 2.0 * math.pi * x * x * math.sin(ph),
+                              0, delta, lambda z: z, lambda z: delta,
+                              lambda z, x: 0.0, lambda z, x: math.acos(min(1.0, z / x)),
+                              epsabs=0, epsrel=1e-11)[0]
+    else:
+        # thickness t enters c as 1/t and the crack area as t: work with c t
+        W = E / (1.0 - nu) if kind == "plane_stress" else E / ((1.0 + nu) * (1.0 - 2.0 * nu))
+        ring = integrate.quad(lambda x: 0.5 * (x / 2.0) * 2.0 * math.pi * x, 0, delta,
+                              epsabs=0, epsrel=1e-13)[0]
+        c = W / ring
+        I = integrate.tplquad(lambda ph, x, z: (x / 2.0) * x,
+                              0, delta, lambda z: z, lambda z: delta,
+                              lambda z, x: -math.acos(min(1.0, z / x)),
+                              lambda z, x: math.acos(min(1.0, z / x)),
+                              epsabs=0, epsrel=1e-11)[0]
+    expect = math.sqrt(G / (c * I))
+    got = oracle.critical_stretch(G, E, delta, kind)
+    assert abs(got - expect) <= 1e-8 * expect, (got, expect)
+
+
+def test_youngs_modulus_from_lame_parameters():
+    # E = 3 K (1 - 2 nu) against E, K and nu written from the Lame parameters
+    for lam, mu in [(1.0e9, 2.0e9), (3.0e10, 1.2e10), (5.0, 5.0)]:
+        K = lam + 2.0 * mu / 3.0
+        nu = lam / (2.0 * (lam + mu))
+        E = mu * (3.0 * lam + 2.0 * mu) / (lam + mu)
+        assert abs(oracle.youngs_modulus(K, nu) - E) <= 1e-12 * E
+
+
 def test_splitmix64_reference_outputs():
     lines = [l.split() for l in open(os.path.join(GOLD, "splitmix64_seed1234567.txt"))
              if l.strip() and not l.startswith("#")]
