@@ -1346,7 +1346,7 @@ pd_status pd_set_bonds(pd_handle* h, const uint8_t* mu)
         for (int64_t m = 0; m < h->cnt[p]; ++m)
             if (mu[pos[(g * W + m) * 32 + l]]) bits[(g * h->Q + (m >> 5)) * 32 + l] |= 1u << (m & 31);
     }
-    PD_CUDA(cudaMemcpy(h->bits, bits.data(), bits.size() * 4, cudaMemcpyHostToDevice),
+    PD_CUDA(cudaMemcpyAsync(h->bits, bits.data(), bits.size() * 4, cudaMemcpyHostToDevice, h->stream),
             "upload bond flags");
     if (h->integ) {  // a fresh bond state: intact bonds unsoftened, broken ones 0
         const size_t ns = (size_t)(h->n_slices * 32 * W);
@@ -1362,9 +1362,9 @@ pd_status pd_set_bonds(pd_handle* h, const uint8_t* mu)
                 }
         }
         if (h->precision == 32)
-            PD_CUDA(cudaMemcpy(h->integ, m32.data(), ns * 4, cudaMemcpyHostToDevice), "upload integrity");
+            PD_CUDA(cudaMemcpyAsync(h->integ, m32.data(), ns * 4, cudaMemcpyHostToDevice, h->stream), "upload integrity");
         else
-            PD_CUDA(cudaMemcpy(h->integ, m64.data(), ns * 8, cudaMemcpyHostToDevice), "upload integrity");
+            PD_CUDA(cudaMemcpyAsync(h->integ, m64.data(), ns * 8, cudaMemcpyHostToDevice, h->stream), "upload integrity");
     }
     h->damage_fresh = false;
     h->peek_step = -1;
@@ -1375,9 +1375,15 @@ pd_status pd_remove_bonds(pd_handle* h, const int64_t* pairs, int64_t m)
 {
     if (!h || (m > 0 && !pairs) || m < 0) return fail(PD_ERR_ARG, "need a handle, m >= 0 and pairs");
     if (m == 0) return PD_OK;
-    // canonical index of both directions of every pair, checked before anything changes
-    std::vector<int64_t> kset;
-    kset.reserve((size_t)(2 * m));
+    // every pair is checked before anything changes.  The slot of a directed
+    // bond a -> b: the layout lists node a's family in ascending device
+    // position, so it is the rank of inv[b] in that row.
+    const int64_t W = 32LL * h->Q;
+    std::vector<int64_t> word, slot;
+    std::vector<uint32_t> mask;
+    word.reserve((size_t)(2 * m));
+    slot.reserve((size_t)(2 * m));
+    mask.reserve((size_t)(2 * m));
     for (int64_t e = 0; e < m; ++e) {
         const int64_t i = pairs[2 * e], j = pairs[2 * e + 1];
         if (i < 0 || j < 0 || i >= h->n || j >= h->n || i == j)
@@ -1388,42 +1394,31 @@ pd_status pd_remove_bonds(pd_handle* h, const int64_t* pairs, int64_t m)
             const int32_t* lo = h->idx.data() + h->off[a];
             const int32_t* hi = h->idx.data() + h->off[a + 1];
             const int32_t* it = std::lower_bound(lo, hi, (int32_t)b);  // rows are sorted
-            const int64_t k = (it != hi && *it == b) ? (int64_t)(it - h->idx.data()) : -1;
-            if (k < 0)
+            if (it == hi || *it != b)
                 return fail(PD_ERR_ARG, "pair %lld: %lld -> %lld is not a bond of the family",
                             (long long)e, (long long)a, (long long)b);
-            kset.push_back(k);
+            const int32_t pb = h->inv[(size_t)b];
+            int64_t mm = 0;
+            for (const int32_t* q = lo; q < hi; ++q) mm += h->inv[(size_t)*q] < pb ? 1 : 0;
+            const int64_t p = h->inv[(size_t)a], g = p / 32, l = p % 32;
+            word.push_back((g * h->Q + (mm >> 5)) * 32 + l);
+            mask.push_back(1u << (mm & 31));
+            slot.push_back((g * W + mm) * 32 + l);
         }
     }
     PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
     pd_status st = vv_force_pass(h);  // a pending Velocity-Verlet force pass sees the old bonds
     if (st != PD_OK) return st;
-    std::vector<int64_t> pos;
-    if ((st = canonical_slots(h, pos)) != PD_OK) return st;
-    std::vector<int64_t> slot_of((size_t)h->n_bonds, -1);
-    for (size_t q = 0; q < pos.size(); ++q)
-        if (pos[q] >= 0) slot_of[(size_t)pos[q]] = (int64_t)q;
-    const int64_t W = 32LL * h->Q;
-    const size_t nk = kset.size();
-    std::vector<int64_t> word(nk), slot(nk);
-    std::vector<uint32_t> mask(nk);
-    for (size_t e = 0; e < nk; ++e) {
-        const int64_t q = slot_of[(size_t)kset[e]];
-        if (q < 0) return fail(PD_ERR_STATE, "bond without a slot");
-        const int64_t g = q / (32 * W), r = q % (32 * W), mm = r / 32, l = r % 32;
-        word[e] = (g * h->Q + (mm >> 5)) * 32 + l;
-        mask[e] = 1u << (mm & 31);
-        slot[e] = q;
-    }
+    const size_t nk = word.size();
     int64_t* d_word = nullptr;
     int64_t* d_slot = nullptr;
     uint32_t* d_mask = nullptr;
     cudaError_t e = cudaMalloc(&d_word, nk * 8);
     if (e == cudaSuccess) e = cudaMalloc(&d_slot, nk * 8);
     if (e == cudaSuccess) e = cudaMalloc(&d_mask, nk * 4);
-    if (e == cudaSuccess) e = cudaMemcpy(d_word, word.data(), nk * 8, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(d_slot, slot.data(), nk * 8, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(d_mask, mask.data(), nk * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_word, word.data(), nk * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_slot, slot.data(), nk * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_mask, mask.data(), nk * 4, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
         e = launch_clear_slots(h->bits, d_word, d_mask, d_slot, (int64_t)nk, h->precision,
                                h->integ, h->stream);
@@ -1774,7 +1769,7 @@ pd_status pd_autotune(pd_handle* h, int32_t trial_steps, int32_t* block_threads,
     }
     auto restore = [&]() -> pd_status {
         for (Buf& b : bufs)
-            PD_CUDA(cudaMemcpy(b.dev, b.keep.data(), b.bytes, cudaMemcpyHostToDevice),
+            PD_CUDA(cudaMemcpyAsync(b.dev, b.keep.data(), b.bytes, cudaMemcpyHostToDevice, h->stream),
                     "restore state");
         return PD_OK;
     };
@@ -1858,13 +1853,13 @@ pd_status pd_set_params(pd_handle* h, double c, double sc, double load, double d
             std::vector<float> cb(slots, 0.0f);
             for (size_t s = 0; s < slots; ++s)
                 if (pos[s] >= 0) cb[s] = (float)c_bond[pos[s]];
-            PD_CUDA(cudaMemcpy(h->cbond, cb.data(), slots * 4, cudaMemcpyHostToDevice),
+            PD_CUDA(cudaMemcpyAsync(h->cbond, cb.data(), slots * 4, cudaMemcpyHostToDevice, h->stream),
                     "upload c_bond");
         } else {
             std::vector<double> cb(slots, 0.0);
             for (size_t s = 0; s < slots; ++s)
                 if (pos[s] >= 0) cb[s] = c_bond[pos[s]];
-            PD_CUDA(cudaMemcpy(h->cbond, cb.data(), slots * 8, cudaMemcpyHostToDevice),
+            PD_CUDA(cudaMemcpyAsync(h->cbond, cb.data(), slots * 8, cudaMemcpyHostToDevice, h->stream),
                     "upload c_bond");
             if (h->dw) {
                 if (!h->cbdw) {

@@ -97,6 +97,14 @@ def test_create_rejects_bad_arguments(L, over, status):
     assert e.value.name == status
 
 
+def test_create_rejects_an_empty_body(L):
+    w = workloads.tensile_bar(6, 4, 4)
+    with pytest.raises(pdgb.PdError) as e:
+        pdgb.pd_create(**_args(w, coords=np.zeros((0, 3)), volumes=np.zeros(0),
+                               bc_type=np.zeros((0, 3), np.uint8), bc_disp=np.zeros((0, 3))))
+    assert e.value.name == "PD_ERR_ARG" and "n must be" in str(e.value)
+
+
 def test_batch_rejects_differing_softening_laws(L):
     # the softening law is handle-wide: every instance must agree with instance 0
     # (checked before any device work)
