@@ -385,23 +385,31 @@ def _adjoint_sig():
         L.or_adjoint.restype = None
         L.or_adjoint.argtypes = [ctypes.POINTER(_Model), ctypes.c_int64, ctypes.c_int64,
                                  P, P, P, P, P, P, P, P, P]
+        L.or_adjoint_vv.restype = None
+        L.or_adjoint_vv.argtypes = L.or_adjoint.argtypes
         L._adj_ready = True
     return L
 
 
-def adjoint(model: "Model", first_step, nsteps, u0, v0, mu, dLdu, dLdv=None):
-    """Reverse-mode gradient of L(u^N, v^N) with frozen bond flags mu (see oracle.c).
+def adjoint(model: "Model", first_step, nsteps, u0, v0, mu, dLdu, dLdv=None,
+            integrator="ec"):
+    """Reverse-mode gradient of L(u^N, v^N) with frozen bond flags mu (see oracle.c):
+    of the damped Euler-Cromer run (integrator "ec") or of the damped
+    velocity-Verlet run started from (u0, v0) with its acceleration formed
+    afresh (integrator "vv", or_run_vv with init).
 
     Returns (dL/dc per family entry, dL/dload, dL/du0, dL/dv0)."""
     assert model.rows is None
+    assert integrator in ("ec", "vv")
     L = _adjoint_sig()
+    fn = L.or_adjoint if integrator == "ec" else L.or_adjoint_vv
     u0 = _c64(u0); v0 = _c64(v0); dLdu = _c64(dLdu)
     dLdv = None if dLdv is None else _c64(dLdv)
     mu = np.ascontiguousarray(mu, np.uint8)
     gc = np.zeros(max(model.nbonds, 1))
     gl = ctypes.c_double()
     gu = np.empty_like(u0); gv = np.empty_like(v0)
-    L.or_adjoint(ctypes.byref(model.m), int(first_step), int(nsteps), u0.ctypes.data,
-                 v0.ctypes.data, mu.ctypes.data, dLdu.ctypes.data, _p(dLdv), gc.ctypes.data,
-                 ctypes.byref(gl), gu.ctypes.data, gv.ctypes.data)
+    fn(ctypes.byref(model.m), int(first_step), int(nsteps), u0.ctypes.data,
+       v0.ctypes.data, mu.ctypes.data, dLdu.ctypes.data, _p(dLdv), gc.ctypes.data,
+       ctypes.byref(gl), gu.ctypes.data, gv.ctypes.data)
     return gc[: model.nbonds], gl.value, gu, gv

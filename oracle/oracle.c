@@ -840,3 +840,111 @@ void or_adjoint(const or_model* m, int64_t first_step, int64_t nsteps, const dou
     if (dLdv0) memcpy(dLdv0, vb, (size_t)n3 * sizeof(double));
     free(U); free(v); free(u2); free(v2); free(muc); free(ub); free(vb); free(w);
 }
+
+/* out += scale (J^T w) at u, with J = dF/du of the pairwise force density
+ * (frozen flags mu), and the matching stiffness and load sensitivities:
+ *   dLdc[m->j] += scale mu s V_j (y/r).w_m,   *gload += scale sum_m force_m . w_m
+ * (the terms of or_adjoint's reverse step, with w given). */
+static void jt_accumulate(const or_model* m, const double* u, const double* w,
+                          const uint8_t* mu, double scale, double* out, double* dLdc,
+                          double* gload)
+{
+    const int64_t n = m->n;
+    if (m->bc_force)
+        for (int64_t e = 0; e < 3 * n; ++e) *gload += scale * m->bc_force[e] * w[e];
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int64_t q = m->off[i]; q < m->off[i + 1]; ++q) {
+            if (!mu[q]) continue;
+            const int64_t j = m->idx[q];
+            double xi[3], y[3], d[3];
+            for (int c = 0; c < 3; ++c) {
+                xi[c] = m->x[3 * j + c] - m->x[3 * i + c];
+                y[c] = xi[c] + u[3 * j + c] - u[3 * i + c];
+                d[c] = m->vol[i] * w[3 * j + c] - m->vol[j] * w[3 * i + c];
+            }
+            const double L = sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
+            const double r = sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+            const double s = (r - L) / L;
+            const double yd = y[0] * d[0] + y[1] * d[1] + y[2] * d[2];
+            const double cij = m->c_bond ? m->c_bond[q] : m->c;
+            for (int c = 0; c < 3; ++c)
+                acc[c] += cij * ((1.0 / L - 1.0 / r) * d[c] + y[c] * yd / (r * r * r));
+            const double yw = y[0] * w[3 * i] + y[1] * w[3 * i + 1] + y[2] * w[3 * i + 2];
+            dLdc[q] += scale * s * m->vol[j] * yw / r;
+        }
+        for (int c = 0; c < 3; ++c) out[3 * i + c] += scale * acc[c];
+    }
+}
+
+/* Reverse mode of the damped velocity-Verlet run of or_run_vv started with
+ * init = 1 (a^0 formed from the initial state), bond flags frozen (mu), for a
+ * loss L(u^N, v^N).  Each assignment of the forward step, in its order
+ *   a^0     = P (F(u^0) - eta v^0) / rho
+ *   u^{n+1} = u^n + dt v^n + dt^2/2 a^n          (free components)
+ *   vt      = v^n + dt/2 a^n                      (free components, else 0)
+ *   a^{n+1} = P (F(u^{n+1}) - eta vt) / rho
+ *   v^{n+1} = v^n + dt/2 (a^n + a^{n+1})          (free components)
+ * (P keeps the free components; controlled ones follow the prescribed ramp and
+ * do not depend on the state), is reversed in the opposite order with the
+ * adjoints ubar, vbar, abar of u, v, a.  F = F_int + load b, and
+ * d(J^T)/dc, db as in or_adjoint.  Stores every u^n (small cases). */
+void or_adjoint_vv(const or_model* m, int64_t first_step, int64_t nsteps, const double* u0,
+                   const double* v0, const uint8_t* mu, const double* dLdu, const double* dLdv,
+                   double* dLdc, double* dLdload, double* dLdu0, double* dLdv0)
+{
+    const int64_t n = m->n, n3 = 3 * n;
+    const double dt = m->dt, rho = m->density, eta = m->damping;
+    double* U = (double*)malloc((size_t)(nsteps + 1) * n3 * sizeof(double) + 8);
+    double* v = (double*)malloc((size_t)n3 * sizeof(double) + 8);
+    double* a = (double*)malloc((size_t)n3 * sizeof(double) + 8);
+    uint8_t* muc = (uint8_t*)malloc((size_t)(m->off[n] > 0 ? m->off[n] : 1));
+    memcpy(U, u0, (size_t)n3 * sizeof(double));
+    memcpy(v, v0, (size_t)n3 * sizeof(double));
+    memcpy(muc, mu, (size_t)(m->off[n] > 0 ? m->off[n] : 1));
+    /* forward, keeping u^n; frozen flags: the run must not break a bond */
+    or_run_vv(m, first_step, 0, 1, U, v, a, muc, NULL);
+    for (int64_t k = 0; k < nsteps; ++k) {
+        memcpy(U + (k + 1) * n3, U + k * n3, (size_t)n3 * sizeof(double));
+        or_run_vv(m, first_step + k, 1, 0, U + (k + 1) * n3, v, a, muc, NULL);
+    }
+    double* ub = (double*)malloc((size_t)n3 * sizeof(double) + 8);
+    double* vb = (double*)malloc((size_t)n3 * sizeof(double) + 8);
+    double* ab = (double*)malloc((size_t)n3 * sizeof(double) + 8);
+    double* t = (double*)malloc((size_t)n3 * sizeof(double) + 8);
+    memcpy(ub, dLdu, (size_t)n3 * sizeof(double));
+    for (int64_t e = 0; e < n3; ++e) {
+        vb[e] = dLdv ? dLdv[e] : 0.0;
+        ab[e] = 0.0;
+    }
+    for (int64_t k = 0; k < m->off[n]; ++k) dLdc[k] = 0.0;
+    double gload = 0.0;
+    for (int64_t k = nsteps - 1; k >= 0; --k) {
+        /* v^{k+1} = v^k + dt/2 (a^k + a^{k+1}) */
+        for (int64_t e = 0; e < n3; ++e) {
+            if (m->bc_type[e] == 1) vb[e] = 0.0;
+            ab[e] += 0.5 * dt * vb[e];
+        }
+        /* a^{k+1} = P (F(u^{k+1}) - eta vt) / rho */
+        for (int64_t e = 0; e < n3; ++e) t[e] = m->bc_type[e] == 1 ? 0.0 : ab[e];
+        jt_accumulate(m, U + (k + 1) * n3, t, mu, 1.0 / rho, ub, dLdc, &gload);
+        /* vt = v^k + dt/2 a^k, u^{k+1} = u^k + dt v^k + dt^2/2 a^k (free components) */
+        for (int64_t e = 0; e < n3; ++e) {
+            const double vtb = -eta / rho * t[e];
+            const double up = m->bc_type[e] == 1 ? 0.0 : ub[e];
+            const double vbk = vb[e] + vtb + dt * up;
+            ab[e] = 0.5 * dt * vb[e] + 0.5 * dt * vtb + 0.5 * dt * dt * up;
+            vb[e] = vbk;
+            ub[e] = up;
+        }
+    }
+    /* a^0 = P (F(u^0) - eta v^0) / rho */
+    for (int64_t e = 0; e < n3; ++e) t[e] = m->bc_type[e] == 1 ? 0.0 : ab[e];
+    jt_accumulate(m, U, t, mu, 1.0 / rho, ub, dLdc, &gload);
+    for (int64_t e = 0; e < n3; ++e) vb[e] += -eta / rho * t[e];
+    if (dLdload) *dLdload = gload;
+    if (dLdu0) memcpy(dLdu0, ub, (size_t)n3 * sizeof(double));
+    if (dLdv0) memcpy(dLdv0, vb, (size_t)n3 * sizeof(double));
+    free(U); free(v); free(a); free(muc); free(ub); free(vb); free(ab); free(t);
+}

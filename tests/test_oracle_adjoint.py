@@ -101,3 +101,54 @@ def test_oracle_adjoint_zero_steps_is_identity():
     gc, gl, gu0, gv0 = oracle.adjoint(m, 0, 0, u0, v0, m.fresh_bonds(), gu, gv)
     assert np.all(gc == 0.0) and gl == 0.0
     assert np.array_equal(gu0, gu) and np.array_equal(gv0, gv)
+
+
+# ---------------------------------------------------------------- velocity-Verlet
+def _loss_vv(w, off, idx, c0, cb, u0, v0, gu, gv, load=None):
+    m = oracle.Model.from_workload(w, off, idx, c=c0, c_bond=cb)
+    if load is not None:
+        m.m.load = load
+    u = u0.copy(); v = v0.copy(); a = np.zeros_like(u0); mu = m.fresh_bonds()
+    m.run_vv(0, w.steps, u, v, a, mu, init=True)
+    assert mu.all()
+    return float((gu * u).sum() + (gv * v).sum())
+
+
+def test_oracle_vv_adjoint_matches_central_differences():
+    # the reverse sweep of the damped velocity-Verlet run (acceleration formed
+    # from the initial state) against central differences of that run
+    w, off, idx, c0, cb, u0, v0, gu, gv, rng = _case(7)
+    m = oracle.Model.from_workload(w, off, idx, c=c0, c_bond=cb)
+    gc, gl, gu0, gv0 = oracle.adjoint(m, 0, w.steps, u0, v0, m.fresh_bonds(), gu, gv,
+                                      integrator="vv")
+
+    def fd(f, h):
+        return (f(h) - f(-h)) / (2 * h)
+
+    for k in range(2):
+        dc = rng.standard_normal(len(idx)) * c0
+        num = fd(lambda t: _loss_vv(w, off, idx, c0, cb + t * dc, u0, v0, gu, gv), 1e-6)
+        ana = float(gc @ dc)
+        assert abs(num - ana) <= 1e-6 * abs(ana), (num, ana)
+    h = 1e-6 * w.load
+    num = fd(lambda t: _loss_vv(w, off, idx, c0, cb, u0, v0, gu, gv, load=w.load + t), h)
+    assert abs(num - gl) <= 1e-6 * abs(gl), (num, gl)
+    du = rng.standard_normal(u0.shape) * 1e-7
+    num = fd(lambda t: _loss_vv(w, off, idx, c0, cb, u0 + t * du, v0, gu, gv), 1e-3)
+    ana = float((gu0 * du).sum())
+    assert abs(num - ana) <= 1e-6 * abs(ana), (num, ana)
+    dv = rng.standard_normal(v0.shape) * 1e-3
+    num = fd(lambda t: _loss_vv(w, off, idx, c0, cb, u0, v0 + t * dv, gu, gv), 1e-3)
+    ana = float((gv0 * dv).sum())
+    assert abs(num - ana) <= 1e-6 * abs(ana), (num, ana)
+    ctl = w.bc_type == 1
+    assert np.all(gv0[ctl] == 0.0) and np.any(gu0[ctl] != 0.0)
+
+
+def test_oracle_vv_adjoint_zero_steps_is_identity():
+    w, off, idx, c0, cb, u0, v0, gu, gv, rng = _case(9)
+    m = oracle.Model.from_workload(w, off, idx, c=c0, c_bond=cb)
+    gc, gl, gu0, gv0 = oracle.adjoint(m, 0, 0, u0, v0, m.fresh_bonds(), gu, gv,
+                                      integrator="vv")
+    assert np.all(gc == 0.0) and gl == 0.0
+    assert np.array_equal(gu0, gu) and np.array_equal(gv0, gv)
