@@ -343,8 +343,13 @@ pd_status pd_set_params(pd_handle* h, double c, double sc, double load, double d
  * Sensitivities (outer-loop use, Section 3.6): the gradient of a loss of the
  * final state with respect to every directed bond's stiffness, the body-force
  * load and the initial state, by a hand-written reverse sweep of the damped
- * Euler-Cromer recurrence.  FP64 and PD_PREC_DW handles (PD_ERR_STATE
- * otherwise), not batch handles.  On PD_PREC_DW handles the recorded and
+ * Euler-Cromer recurrence or of the damped velocity-Verlet run (the handle's
+ * integrator; the time-integration equations of Section 2.4).  FP64 and
+ * PD_PREC_DW PMB handles without softening (PD_ERR_STATE otherwise), not batch
+ * handles.  A velocity-Verlet run must start where the state was set
+ * (pd_set_state, or creation), so that its acceleration is formed afresh from
+ * (u^0, v^0); then dL_dv0 is the derivative with respect to that velocity and
+ * dLdv refers to the full-step velocity v^N that pd_get_state reports.  On PD_PREC_DW handles the recorded and
  * recomputed forward runs use the double-word step and pd_adjoint_backward's
  * reverse sweep is in double-word arithmetic too (FP64-grade; the same outputs
  * to ~1e-10); pd_adjoint_backward_static keeps the FP64 reverse sweep.

@@ -1,10 +1,10 @@
 """torch.autograd.Function around the hand-written adjoint (pd_adjoint_*).
 
 ``PeridynamicRun.apply(c_bond, load, u0, v0, model, n_steps, checkpoint_every)``
-runs ``n_steps`` damped Euler-Cromer steps of ``model`` (an FP64 or PD_PREC_DW
-``paper_2105_04150_gb300.Model``) from (u0, v0) with the bond flags frozen, with
-the per-directed-bond stiffness ``c_bond`` and body-force scale ``load``, and
-returns the final displacement u^N (n x 3).  Its backward runs the library's
+runs ``n_steps`` steps of ``model`` (an FP64 or PD_PREC_DW
+``paper_2105_04150_gb300.Model``, with either integrator) from (u0, v0) with the
+bond flags frozen, with the per-directed-bond stiffness ``c_bond`` and
+body-force scale ``load``, and returns the final displacement u^N (n x 3).  Its backward runs the library's
 reverse sweep and returns dL/dc_bond, dL/dload, dL/du0 and dL/dv0.
 
 All arithmetic happens in the CUDA library; this module only moves tensors

@@ -1,8 +1,9 @@
 // Hand-written adjoint of the damped Euler-Cromer run with frozen bond flags
 // (FP64).  One reverse step n+1 -> n is two launches:
-//   k_adj_mask  w = vbar + dt ubar with the controlled components of ubar and
-//               vbar zeroed (a prescribed component does not depend on the
-//               previous state)
+//   k_adj_mask  w = ws (vbar + dt ubar) with the controlled components of ubar
+//               and vbar zeroed (a prescribed component does not depend on the
+//               previous state); ws = 1 for an Euler-Cromer step, 1/2 for the
+//               half kicks that open and close a velocity-Verlet run
 //   k_adj_step  per node m over its family (the same sliced layout and lane-per-
 //               node walk as the forward step):
 //                 ubar^n_m = ubar_m + (dt/rho) sum_j c_mj K_mj (V_m w_j - V_j w_m)
@@ -36,7 +37,8 @@ int grid_for(int64_t work, int block)
 
 __global__ void k_adj_mask(const double* __restrict__ ub, const double* __restrict__ vb,
                            const uint8_t* __restrict__ bcc, const BcClass* __restrict__ bct,
-                           int64_t n, double dt, double* __restrict__ ubm, double* __restrict__ w)
+                           int64_t n, double dt, double ws, double* __restrict__ ubm,
+                           double* __restrict__ w)
 {
     GRID_STRIDE(p, n)
     {
@@ -47,7 +49,7 @@ __global__ void k_adj_mask(const double* __restrict__ ub, const double* __restri
             const double u = ctl ? 0.0 : ub[3 * p + c];
             const double v = ctl ? 0.0 : vb[3 * p + c];
             ubm[3 * p + c] = u;
-            w[3 * p + c] = v + dt * u;
+            w[3 * p + c] = ws * (v + dt * u);
         }
     }
 }
@@ -223,10 +225,10 @@ __global__ void k_slots_to_canonical(const double* __restrict__ val, const int32
 }  // namespace
 
 cudaError_t launch_adj_mask(const double* ub, const double* vb, const uint8_t* bcc,
-                            const BcClass* bct, int64_t n, double dt, double* ubm, double* w,
-                            cudaStream_t s)
+                            const BcClass* bct, int64_t n, double dt, double ws, double* ubm,
+                            double* w, cudaStream_t s)
 {
-    k_adj_mask<<<grid_for(n, 256), 256, 0, s>>>(ub, vb, bcc, bct, n, dt, ubm, w);
+    k_adj_mask<<<grid_for(n, 256), 256, 0, s>>>(ub, vb, bcc, bct, n, dt, ws, ubm, w);
     return cudaGetLastError();
 }
 

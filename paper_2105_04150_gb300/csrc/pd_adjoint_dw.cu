@@ -37,15 +37,15 @@ __device__ __forceinline__ void split(double x, float& h, float& l)
     l = (float)(x - (double)h);
 }
 
-// Start of a reverse step for node p: w = vbar + dt ubar with the controlled
-// components of ubar and vbar zeroed (as k_adj_mask), and the double-word
+// Start of a reverse step for node p: w = ws (vbar + dt ubar) with the
+// controlled components of ubar and vbar zeroed (as k_adj_mask), and the double-word
 // records the bond loop reads: positions copied from the forward double-word
 // records, u^n / delta and V as the forward kernel has them ({xh, uh.x}
 // {uh.y, uh.z, Vh, Vl} {xl, ul.x} {ul.y, ul.z, 0, 0}), and w ({wh, wl.x}
 // {wl.y, wl.z, 0, 0}).
 __global__ void k_adj_mask_publish_dw(const double* __restrict__ ub, const double* __restrict__ vb,
                                       const uint8_t* __restrict__ bcc,
-                                      const BcClass* __restrict__ bct, double dt,
+                                      const BcClass* __restrict__ bct, double dt, double ws,
                                       const float4* __restrict__ fwd,
                                       const double* __restrict__ un,
                                       const double* __restrict__ vol, int64_t n_pad,
@@ -63,7 +63,7 @@ __global__ void k_adj_mask_publish_dw(const double* __restrict__ ub, const doubl
             const bool ctl = (mask >> k) & 1u;
             const double u = ctl ? 0.0 : ub[3 * p + k];
             const double v = ctl ? 0.0 : vb[3 * p + k];
-            const double wk = v + dt * u;
+            const double wk = ws * (v + dt * u);
             ubm[3 * p + k] = u;
             w[3 * p + k] = wk;
             split(un[3 * p + k] * inv_delta, uh[k], ul[k]);
@@ -236,12 +236,12 @@ __global__ void k_adj_merge_dw(const float2* __restrict__ acc, int64_t count, do
 }  // namespace
 
 cudaError_t launch_adj_mask_publish_dw(const double* ub, const double* vb, const uint8_t* bcc,
-                                       const BcClass* bct, double dt, const float4* fwd,
-                                       const double* un, const double* vol, int64_t n_pad,
-                                       double inv_delta, double* ubm, double* w, float4* rec,
-                                       float4* wrec, cudaStream_t s)
+                                       const BcClass* bct, double dt, double ws,
+                                       const float4* fwd, const double* un, const double* vol,
+                                       int64_t n_pad, double inv_delta, double* ubm, double* w,
+                                       float4* rec, float4* wrec, cudaStream_t s)
 {
-    k_adj_mask_publish_dw<<<grid_of(n_pad), 256, 0, s>>>(ub, vb, bcc, bct, dt, fwd, un, vol, n_pad,
+    k_adj_mask_publish_dw<<<grid_of(n_pad), 256, 0, s>>>(ub, vb, bcc, bct, dt, ws, fwd, un, vol, n_pad,
                                                          inv_delta, ubm, w, rec, wrec);
     return cudaGetLastError();
 }

@@ -125,6 +125,7 @@ struct pd_handle {
     int64_t ramp_steps = 0;
     void* vpeek = nullptr;  // velocity-Verlet: full-step velocity for pd_get_state
     int64_t peek_step = -1; // step whose force pass filled vpeek (-1: none)
+    int64_t vv_start = 0;   // step of the last set state (velocity-Verlet: a^n formed afresh)
     double kr = 0.0;        // >= 1: bilinear softening, s_0 = s_c / kr
     double k1 = 0.0, beta = 1.0;  // trilinear kink (k1 > 1)
     void* integ = nullptr;  // softening: per-slot integrity (float / double)
@@ -147,6 +148,7 @@ struct pd_handle {
     bool frozen = false;
     struct Tape {
         bool valid = false;
+        bool vv = false;  // velocity-Verlet run (opens with a half kick, ends with one)
         int64_t N = 0, C = 0, nck = 0, step0 = 0;
         double *ck_u = nullptr, *ck_v = nullptr, *seg = nullptr, *fin_u = nullptr,
                *fin_v = nullptr;
@@ -1265,6 +1267,7 @@ pd_status pd_set_state(pd_handle* h, const double* u, const double* v, int64_t s
     PD_CUDA(cudaMemcpyAsync(h->step_ctr + 1, &h->step, sizeof(int64_t), cudaMemcpyHostToDevice,
                             h->stream),
             "set history start");
+    h->vv_start = h->step;
     PD_CUDA(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream), "clear error flag");
     h->damage_fresh = false;
     h->peek_step = -1;
@@ -1456,13 +1459,16 @@ pd_status pd_damage(pd_handle* h, double* phi)
 pd_status pd_adjoint_forward(pd_handle* h, int64_t n_steps, int64_t checkpoint_every)
 {
     if (!h) return fail(PD_ERR_ARG, "NULL handle");
-    if (h->precision != 64 || h->batch || h->integrator != PD_INTEGRATOR_EC || h->integ ||
-        h->model != 0)
+    if (h->precision != 64 || h->batch || h->integ || h->model != 0)
         return fail(PD_ERR_STATE,
-                    "the adjoint is available on FP64 and PD_PREC_DW single-model "
-                    "Euler-Cromer PMB handles");
+                    "the adjoint is available on FP64 and PD_PREC_DW single-model PMB handles");
     if (n_steps < 1 || checkpoint_every < 0)
         return fail(PD_ERR_ARG, "need n_steps >= 1 and checkpoint_every >= 0");
+    const bool vv = h->integrator == PD_INTEGRATOR_VV;
+    if (vv && h->vv_start != h->step)
+        return fail(PD_ERR_STATE,
+                    "a velocity-Verlet adjoint run starts from a state set by pd_set_state "
+                    "(or at creation), where the acceleration is formed afresh");
     PD_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
     auto& T = h->tape;
     int64_t C = checkpoint_every > 0 ? std::min(checkpoint_every, n_steps)
@@ -1515,6 +1521,7 @@ pd_status pd_adjoint_forward(pd_handle* h, int64_t n_steps, int64_t checkpoint_e
     T.C = C;
     T.nck = nck;
     T.step0 = step0;
+    T.vv = vv;
     T.valid = true;
     return check_dev_err(h);
 }
@@ -1625,7 +1632,38 @@ pd_status pd_adjoint_backward(pd_handle* h, const double* dLdu, const double* dL
     h->frozen = true;
     h->drop_graph();
     int cb = 0;
+    // one reverse step at u^n (w = ws (vbar + dtw ubar), vbar^n = damp w); a
+    // velocity-Verlet run is the Euler-Cromer recurrence in (u, half-step
+    // velocity) between a half kick at its first step and a half kick that
+    // forms the full-step velocity it ends with: ws = 1/2 there, and
+    // damp = 1 + (1 - dt eta / rho) so that damp ws = 1 - dt eta / (2 rho)
+    const double damp_full = A.damp;
+    auto reverse_step = [&](const double* un, double dtw, double ws, double damp) {
+        A.un = un;
+        A.w = T.w;
+        A.ubm = T.ubm;
+        A.ub_out = T.ub[cb ^ 1];
+        A.vb_out = T.vb[cb ^ 1];
+        A.damp = damp;
+        cudaError_t r;
+        if (h->dw) {
+            r = launch_adj_mask_publish_dw(T.ub[cb], T.vb[cb], h->bcc, h->bct, dtw, ws,
+                                           h->recdw[0], un, h->vol, h->n_pad, 1.0 / h->delta,
+                                           T.ubm, T.w, T.rrec, T.wrec, h->stream);
+            D.ub_out = A.ub_out;
+            D.vb_out = A.vb_out;
+            D.damp = damp;
+            if (r == cudaSuccess) r = launch_adj_step_dw(D, agrid, 256, h->stream);
+        } else {
+            r = launch_adj_mask(T.ub[cb], T.vb[cb], h->bcc, h->bct, h->n_pad, dtw, ws, T.ubm, T.w,
+                                h->stream);
+            if (r == cudaSuccess) r = launch_adj_step(A, agrid, 256, h->stream);
+        }
+        cb ^= 1;
+        return r;
+    };
     cudaError_t ke = cudaSuccess;
+    if (T.vv && dLdv) ke = reverse_step(T.fin_u, 0.0, 0.5, 1.0 + damp_full);
     for (int64_t k = T.nck - 1; k >= 0 && ke == cudaSuccess; --k) {
         const int64_t start = k * T.C;
         const int64_t len = std::min(T.C, T.N - start);
@@ -1652,25 +1690,9 @@ pd_status pd_adjoint_backward(pd_handle* h, const double* dLdu, const double* dL
         }
         // reverse through the segment
         for (int64_t t = len - 1; t >= 0 && ke == cudaSuccess; --t) {
-            A.un = T.seg + t * np3;
-            A.w = T.w;
-            A.ubm = T.ubm;
-            A.ub_out = T.ub[cb ^ 1];
-            A.vb_out = T.vb[cb ^ 1];
-            if (h->dw) {
-                ke = launch_adj_mask_publish_dw(T.ub[cb], T.vb[cb], h->bcc, h->bct, h->dt,
-                                                h->recdw[0], A.un, h->vol, h->n_pad,
-                                                1.0 / h->delta, T.ubm, T.w, T.rrec, T.wrec,
-                                                h->stream);
-                D.ub_out = A.ub_out;
-                D.vb_out = A.vb_out;
-                if (ke == cudaSuccess) ke = launch_adj_step_dw(D, agrid, 256, h->stream);
-            } else {
-                ke = launch_adj_mask(T.ub[cb], T.vb[cb], h->bcc, h->bct, h->n_pad, h->dt, T.ubm,
-                                     T.w, h->stream);
-                if (ke == cudaSuccess) ke = launch_adj_step(A, agrid, 256, h->stream);
-            }
-            cb ^= 1;
+            const bool half = T.vv && start + t == 0;
+            ke = reverse_step(T.seg + t * np3, h->dt, half ? 0.5 : 1.0,
+                              half ? 1.0 + damp_full : damp_full);
         }
     }
     if (h->dw && ke == cudaSuccess)
@@ -2030,7 +2052,24 @@ pd_status pd_adjoint_backward_static(pd_handle* h, const double* dLdu, const dou
     // segments are recomputed with direct launches (no graph is built or used)
     h->frozen = true;
     int cb = 0;
+    // one reverse step at u^n, with the half kicks of a velocity-Verlet run as
+    // in pd_adjoint_backward
+    const double damp_full = A.damp;
+    auto reverse_step = [&](const double* un, double dtw, double ws, double damp) {
+        cudaError_t r = launch_adj_mask(b.ub[cb], b.vb[cb], h->bcc, h->bct, h->n_pad, dtw, ws,
+                                        b.ubm, b.w, h->stream);
+        A.un = un;
+        A.w = b.w;
+        A.ubm = b.ubm;
+        A.ub_out = b.ub[cb ^ 1];
+        A.vb_out = b.vb[cb ^ 1];
+        A.damp = damp;
+        if (r == cudaSuccess) r = launch_adj_step(A, agrid, 256, h->stream);
+        cb ^= 1;
+        return r;
+    };
     cudaError_t ke = cudaSuccess;
+    if (T.vv && dLdv) ke = reverse_step(T.fin_u, 0.0, 0.5, 1.0 + damp_full);
     for (int64_t k = T.nck - 1; k >= 0 && ke == cudaSuccess; --k) {
         const int64_t start = k * T.C;
         const int64_t len = std::min(T.C, T.N - start);
@@ -2055,15 +2094,9 @@ pd_status pd_adjoint_backward_static(pd_handle* h, const double* dLdu, const dou
                 ke = launch_extract_u(h->rec[h->step & 1], h->n_pad, T.seg + t * np3, h->stream);
         }
         for (int64_t t = len - 1; t >= 0 && ke == cudaSuccess; --t) {
-            ke = launch_adj_mask(b.ub[cb], b.vb[cb], h->bcc, h->bct, h->n_pad, h->dt, b.ubm, b.w,
-                                 h->stream);
-            A.un = T.seg + t * np3;
-            A.w = b.w;
-            A.ubm = b.ubm;
-            A.ub_out = b.ub[cb ^ 1];
-            A.vb_out = b.vb[cb ^ 1];
-            if (ke == cudaSuccess) ke = launch_adj_step(A, agrid, 256, h->stream);
-            cb ^= 1;
+            const bool half = T.vv && start + t == 0;
+            ke = reverse_step(T.seg + t * np3, h->dt, half ? 0.5 : 1.0,
+                              half ? 1.0 + damp_full : damp_full);
         }
     }
     h->frozen = false;

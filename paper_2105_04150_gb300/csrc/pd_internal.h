@@ -241,17 +241,17 @@ struct AdjDwArgs {
 };
 
 cudaError_t launch_adj_mask_publish_dw(const double* ub, const double* vb, const uint8_t* bcc,
-                                       const BcClass* bct, double dt, const float4* fwd,
-                                       const double* un, const double* vol, int64_t n_pad,
-                                       double inv_delta, double* ubm, double* w, float4* rec,
-                                       float4* wrec, cudaStream_t s);
+                                       const BcClass* bct, double dt, double ws,
+                                       const float4* fwd, const double* un, const double* vol,
+                                       int64_t n_pad, double inv_delta, double* ubm, double* w,
+                                       float4* rec, float4* wrec, cudaStream_t s);
 cudaError_t launch_adj_step_dw(const AdjDwArgs& a, int grid, int block, cudaStream_t s);
 cudaError_t launch_adj_merge_dw(const float2* acc, int64_t count, double scale, double* gc,
                                 cudaStream_t s);
 
 cudaError_t launch_adj_mask(const double* ub, const double* vb, const uint8_t* bcc,
-                            const BcClass* bct, int64_t n, double dt, double* ubm, double* w,
-                            cudaStream_t s);
+                            const BcClass* bct, int64_t n, double dt, double ws, double* ubm,
+                            double* w, cudaStream_t s);
 cudaError_t launch_adj_step(const AdjArgs& a, int grid, int block, cudaStream_t s);
 cudaError_t launch_extract_u(const double* rec, int64_t n, double* u, cudaStream_t s);
 cudaError_t launch_insert_u(const double* u, int64_t n, double* rec, cudaStream_t s);

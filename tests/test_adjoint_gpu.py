@@ -215,3 +215,52 @@ def test_sensitivity_plate_full_size():
         ana = float(gc @ dc) + gl * dl
         assert abs(fd - ana) <= 1e-6 * abs(ana), (fd, ana)
     m.close()
+
+
+# ---------------------------------------------------------------- velocity-Verlet
+VV = pdgb.PD_INTEGRATOR_VV
+
+
+@pytest.mark.parametrize("prec", [F64, pdgb.PD_PREC_DW])
+def test_velocity_verlet_adjoint_matches_oracle_reverse_mode(prec):
+    # the damped velocity-Verlet run from a set state (acceleration formed
+    # afresh), loss on u^N and the full-step v^N, checkpoints every 7 steps;
+    # both reverse sweeps (pd_adjoint_backward, and the FP64 one of
+    # pd_adjoint_backward_static) against the oracle's
+    w, off, idx, c0, cb, u0, v0, gu, gv, rng = _case(11, steps=60)
+    om = oracle.Model.from_workload(w, off, idx, c=c0, c_bond=cb)
+    gc_o, gl_o, gu_o, gv_o = oracle.adjoint(om, 0, w.steps, u0, v0, om.fresh_bonds(), gu, gv,
+                                            integrator="vv")
+    uo, vo, ao, mu = u0.copy(), v0.copy(), np.zeros_like(u0), om.fresh_bonds()
+    om.run_vv(0, w.steps, uo, vo, ao, mu, init=True)
+    m = pdgb.Model.from_workload(w, precision=prec, c=c0, integrator=VV)
+    m.set_params(c0, w.sc, w.load, w.disp_rate, cb)
+    m.set_state(u0, v0, step=0)
+    pdgb.pd_adjoint_forward(m.h, w.steps, 7)
+    uN, vN = m.state()
+    assert rel(uN, uo) <= 1e-10 and rel(vN, vo) <= 1e-9
+    for backward in (pdgb.pd_adjoint_backward, pdgb.pd_adjoint_backward_static):
+        gc, gl, gu0, gv0 = backward(m.h, gu, gv)
+        uA, vA = m.state()
+        assert np.array_equal(uN, uA) and np.array_equal(vN, vA)
+        assert rel(gc, gc_o) <= 1e-9, rel(gc, gc_o)
+        assert abs(gl - gl_o) <= 1e-9 * abs(gl_o)
+        assert rel(gu0, gu_o) <= 1e-9 and rel(gv0, gv_o) <= 1e-9
+    # without dL/dv^N the closing half kick drops out
+    gc_o, gl_o, gu_o, gv_o = oracle.adjoint(om, 0, w.steps, u0, v0, om.fresh_bonds(), gu, None,
+                                            integrator="vv")
+    gc, gl, gu0, gv0 = pdgb.pd_adjoint_backward(m.h, gu)
+    assert rel(gc, gc_o) <= 1e-9 and rel(gu0, gu_o) <= 1e-9 and rel(gv0, gv_o) <= 1e-9
+    m.close()
+
+
+def test_velocity_verlet_adjoint_starts_from_a_set_state():
+    w, off, idx, c0, cb, u0, v0, gu, gv, rng = _case(12, steps=10)
+    m = pdgb.Model.from_workload(w, precision=F64, c=c0, integrator=VV)
+    pdgb.pd_adjoint_forward(m.h, 5)          # from creation: allowed
+    with pytest.raises(pdgb.PdError) as e:   # mid-run: the history is not fresh
+        pdgb.pd_adjoint_forward(m.h, 5)
+    assert e.value.name == "PD_ERR_STATE"
+    m.set_state(u0, v0)
+    pdgb.pd_adjoint_forward(m.h, 5)
+    m.close()

@@ -140,12 +140,20 @@ def test_velocity_verlet_batch_instance_equals_alone():
         assert np.array_equal(vb[offs[k]:offs[k + 1]], v)
 
 
-def test_adjoint_rejects_velocity_verlet():
-    m = pdgb.Model.from_workload(_bar(steps=5), precision=F64, integrator=VV)
-    with pytest.raises(pdgb.PdError) as e:
-        pdgb.pd_adjoint_forward(m.h, 5)
-    assert e.value.name == "PD_ERR_STATE"
-    m.close()
+def test_adjoint_rejects_velocity_verlet_with_softening_or_fp32():
+    # the velocity-Verlet adjoint (tests/test_adjoint_gpu.py) covers FP64-grade
+    # PMB handles without softening, as for Euler-Cromer
+    w = _bar(steps=5)
+    for kw in (dict(precision=F32), dict(precision=F64, kr=3.0)):
+        ws = w
+        if "kr" in kw:
+            ws = _bar(steps=5)
+            ws.kr = kw.pop("kr")
+        m = pdgb.Model.from_workload(ws, integrator=VV, **kw)
+        with pytest.raises(pdgb.PdError) as e:
+            pdgb.pd_adjoint_forward(m.h, 5)
+        assert e.value.name == "PD_ERR_STATE"
+        m.close()
 
 
 def test_velocity_verlet_with_softening_matches_oracle():
