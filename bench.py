@@ -644,7 +644,9 @@ def run_adjoint(args):
     stream = torch.cuda.Stream()
     G = max(1, min(args.graph_steps, N))
     prec = 48 if args.precision == 48 else 64  # the adjoint is FP64 or FP64-grade double-word
-    m = pdgb.Model.from_workload(w, precision=prec, c=c0, graph_steps=G, stream=stream.cuda_stream)
+    vv = args.integrator == "vv"
+    m = pdgb.Model.from_workload(w, precision=prec, c=c0, graph_steps=G, stream=stream.cuda_stream,
+                                 integrator=pdgb.PD_INTEGRATOR_VV if vv else pdgb.PD_INTEGRATOR_EC)
     off, idx = m.family()
     n_bonds = len(idx)
     cb = workloads.bond_stiffness_grf(w, off, idx, c0)
@@ -720,15 +722,20 @@ def run_adjoint(args):
         S = int(max(2, min(N, 15.0 / (3.0 * per_step))))
         _, gS, _ = gradient(cb, w.load, steps=S, ck=min(C, S))
         uS, vS = zero.copy(), zero.copy()
-        om.run(0, S, uS, vS, om.fresh_bonds())
+        if vv:
+            om.run_vv(0, S, uS, vS, zero.copy(), om.fresh_bonds(), init=True)
+        else:
+            om.run(0, S, uS, vS, om.fresh_bonds())
         _, g_u = cmod_loss(uS, above, below)
         t = time.perf_counter()
-        gc_o, gl_o, _, _ = oracle.adjoint(om, 0, S, zero, zero, om.fresh_bonds(), g_u, None)
+        gc_o, gl_o, _, _ = oracle.adjoint(om, 0, S, zero, zero, om.fresh_bonds(), g_u, None,
+                                          integrator="vv" if vv else "ec")
         el = time.perf_counter() - t
         cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
         cpu = {"value": n_bonds * S / el, "unit": "bond updates/s", "cores": cores,
                "kind": "oracle",
-               "sample": f"oracle FP64 reverse mode (all states stored) over {S} steps of the "
+               "sample": f"oracle FP64 reverse mode (all states stored, "
+                         f"{'velocity-Verlet' if vv else 'Euler-Cromer'}) over {S} steps of the "
                          f"full plate, {n_bonds:,} bonds, OpenMP on {cores} host threads"}
         oracle_check = {"steps": S, "checkpoint_every": min(C, S),
                         "dL_dc_max_rel_err": float(np.abs(gS - gc_o).max() / np.abs(gc_o).max())}
@@ -737,6 +744,8 @@ def run_adjoint(args):
     launches = (N + 2 * nck + 1) + (5 * N - 2 * nck + 9)
     if prec == 48:  # double-word records again per recomputed segment and at the end,
         launches += nck + 2  # and the gradient merge
+    if vv:  # the force pass that forms the full-step velocity the loss reads with u^N
+        launches += 1
     line = {
         "metric": "bond updates/s", "value": n_bonds * N / (ms_grad * 1e-3),
         "unit": "bond updates/s", "n_gpus": 1, "steps": N, "warmup": args.warmup,
@@ -746,6 +755,7 @@ def run_adjoint(args):
         "config": {"workload": f"{w.name}: {w.n:,} nodes, {n_bonds:,} directed bonds, "
                                f"gradient of CMOD^2 after {N} steps w.r.t. per-bond stiffness "
                                f"and edge load, checkpoint every {C} steps",
+                   "integrator": "damped velocity-Verlet" if vv else "damped Euler-Cromer",
                    "load": w.load},
         "gradient_ms": ms_grad, "gradient_parts_ms": parts, "forward_ms": ms_fwd,
         "adjoint_over_forward": ms_grad / ms_fwd, "bonds_broken": broken,
