@@ -265,6 +265,27 @@ def oracle_sample(w, c, budget_s, steps=None, warmup=0):
     import oracle
     off_all = None
     rng = np.random.default_rng(0)
+    if getattr(w, "state_based", None) is not None:
+        # the state-based step reads every node's dilation: whole steps only
+        off, idx = oracle.cut_family(w.coords, w.horizon, w.cuts_array())
+        m = oracle.Model.from_workload(w, off, idx, c=c)
+        u, v = workloads.random_state(w.n, 1, 1e-9, 1e-4)
+        mu = m.fresh_bonds()
+        t = time.perf_counter()
+        m.step(0, u, v, mu)
+        t1 = time.perf_counter() - t
+        n_steps = int(max(1, min(steps if steps is not None else 5, budget_s / max(t1, 1e-9))))
+        t = time.perf_counter()
+        for k in range(n_steps):
+            m.step(1 + k, u, v, mu)
+        el = time.perf_counter() - t
+        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        return {
+            "value": m.nbonds * n_steps / el, "unit": "bond updates/s", "cores": cores,
+            "kind": "oracle", "seconds": el, "steps": n_steps, "n_bonds_total": m.nbonds,
+            "sample": f"{n_steps} oracle FP64 state-based steps over all {w.n:,} rows "
+                      f"({m.nbonds:,} bonds) of the same workload, OpenMP on {cores} host threads",
+        }
     # estimate the full-step cost from a 2% row sample
     probe_rows = np.sort(rng.choice(w.n, max(1, w.n // 50), replace=False))
     off, idx = oracle.cut_family(w.coords, w.horizon, w.cuts_array(), rows=probe_rows)
@@ -415,15 +436,22 @@ def run_ours(args):
     per_bond = BYTES_PER_BOND + ((4.0 if args.precision == 32 else 8.0) if args.kr else 0.0)
     if args.precision == 48:
         per_bond = DW_BYTES_PER_BOND + (8.0 if args.kr else 0.0)
+    osb = args.state_based is not None
     alg_bytes = n_bonds * per_bond + w.n * BYTES_PER_NODE[args.precision]
+    if osb and args.precision == 32:
+        # two passes over the family (ids and flags twice), and per node the
+        # weighted volume, dilation and (alpha', beta') besides the step's node data
+        alg_bytes = n_bonds * 2 * BYTES_PER_BOND + w.n * (BYTES_PER_NODE[32] + 16)
     peak, peak_kind = hbm_peak()
     achieved = alg_bytes / (ms_step * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak,
-                "traffic": None if args.kr else profiled_traffic(args.precision, args.workload),
+                "traffic": None if (args.kr or osb)
+                else profiled_traffic(args.precision, args.workload),
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s", "algorithmic_bytes_per_launch": alg_bytes,
-                "kernel": f"k_step_f{args.precision}"}
+                "kernel": "k_osb32_dilation + k_osb32_force" if osb
+                else f"k_step_f{args.precision}"}
     if args.precision == 64:
         fpb = OSB_FLOPS_PER_BOND if args.state_based is not None else FP64_FLOPS_PER_BOND
         tf = fpb * n_bonds / (ms_step * 1e-3) / 1e12
@@ -439,14 +467,13 @@ def run_ours(args):
                     "kernel": "k_osb_dilation + k_osb_force" if args.state_based is not None
                     else "k_step_f64"}
     if args.precision == 48:
-        osb = args.state_based is not None
         ops = DW_OSB_FP32_OPS_PER_BOND if osb else DW_FP32_OPS_PER_BOND
         f64 = OSB_FLOPS_PER_BOND if osb else FP64_FLOPS_PER_BOND
         tops = ops * n_bonds / (ms_step * 1e-3) / 1e12
         tf64 = f64 * n_bonds / (ms_step * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": tops, "peak": FP32_PEAK_TOPS, "unit": "TFLOP/s",
                     "frac": tops / FP32_PEAK_TOPS,
-                    "traffic": profiled_traffic(48, args.workload),
+                    "traffic": None if osb else profiled_traffic(48, args.workload),
                     "peak_source": "FP32 operations (add, multiply or fma each counted once) "
                                    "against the FP32 FMA lane rate measured by a probe on this "
                                    "pool's GB300 (70.2 TFLOP/s counting an FMA as two)",

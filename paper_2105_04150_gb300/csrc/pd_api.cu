@@ -126,6 +126,7 @@ struct pd_handle {
     void* vpeek = nullptr;  // velocity-Verlet: full-step velocity for pd_get_state
     int64_t peek_step = -1; // step whose force pass filled vpeek (-1: none)
     int64_t vv_start = 0;   // step of the last set state (velocity-Verlet: a^n formed afresh)
+    int grid_dil = 0;       // grid of the FP32 state-based dilation kernel
     double kr = 0.0;        // >= 1: bilinear softening, s_0 = s_c / kr
     double k1 = 0.0, beta = 1.0;  // trilinear kink (k1 > 1)
     void* integ = nullptr;  // softening: per-slot integrity (float / double)
@@ -137,8 +138,8 @@ struct pd_handle {
     double* osb_alpha = nullptr;  // per node force-scalar coefficients (see pd_step_osb.cu)
     double* osb_beta = nullptr;
     float4* osbdw_ab = nullptr;   // double-word state-based: per node alpha~, beta~
-    float *osb32_len = nullptr, *osb32_mvol = nullptr, *osb32_theta = nullptr,
-          *osb32_alpha = nullptr, *osb32_beta = nullptr;  // FP32 state-based arrays
+    float *osb32_mvol = nullptr, *osb32_theta = nullptr;  // FP32 state-based arrays
+    float2* osb32_ab = nullptr;
     void* wsum_inv = nullptr;
     void* damage = nullptr;
     int* err = nullptr;
@@ -351,11 +352,9 @@ OsbDwArgs osbdw_args(pd_handle* h)
 OsbArgs32 osb32_args(pd_handle* h)
 {
     OsbArgs32 o{};
-    o.len = h->osb32_len;
     o.mvol = h->osb32_mvol;
     o.theta = h->osb32_theta;
-    o.alpha = h->osb32_alpha;
-    o.beta = h->osb32_beta;
+    o.ab = h->osb32_ab;
     o.K = h->osb_K;
     o.G = h->osb_G;
     o.delta = h->delta;
@@ -412,7 +411,7 @@ cudaError_t launch_one(pd_handle* h, int k)
         return launch_step_dw(args_f64(h, k), dw_args(h), h->sc_mode, h->grid, h->block,
                               h->stream);
     if (h->model == 1 && h->precision == 32)
-        return launch_osb32_step(args_f32(h, k), osb32_args(h), h->sc_mode, h->grid, h->block,
+        return launch_osb32_step(args_f32(h, k), osb32_args(h), h->sc_mode, h->grid, h->grid_dil, h->block,
                                  h->stream);
     if (h->model == 1)
         return launch_osb_step(args_f64(h, k), osb_args(h), h->grid, h->block, h->stream);
@@ -436,6 +435,17 @@ pd_status choose_grid(pd_handle* h, int blocks_per_sm)
     const int64_t warps_per_block = h->block / 32;
     const int64_t need = (h->n_slices + warps_per_block - 1) / warps_per_block;
     h->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * occ, need));
+    h->grid_dil = h->grid;
+    if (h->model == 1 && h->precision == 32) {  // the state-based dilation kernel's own grid
+        const void* fd = osb32_dilation_kernel(h->sc_mode, h->uniform_vol);
+        PD_CUDA(cudaFuncSetAttribute(fd, cudaFuncAttributePreferredSharedMemoryCarveout, 0),
+                "carveout");
+        int od = 0;
+        PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&od, fd, h->block, 0), "occupancy");
+        if (blocks_per_sm > 0) od = std::min(od, blocks_per_sm);
+        h->grid_dil = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(od, 1),
+                                                                  need));
+    }
     return PD_OK;
 }
 
@@ -475,7 +485,7 @@ pd_status vv_force_pass(pd_handle* h)
         StepArgsF32 a = args_f32(h, 0);
         a.peek = 1;
         a.vout = (float*)h->vpeek;
-        e = h->model == 1 ? launch_osb32_step(a, osb32_args(h), h->sc_mode, h->grid, h->block,
+        e = h->model == 1 ? launch_osb32_step(a, osb32_args(h), h->sc_mode, h->grid, h->grid_dil, h->block,
                                               h->stream)
                           : launch_f32(h, a);
     } else {
@@ -728,11 +738,9 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
     }
     if (h->model == 1) {
         if (f32) {
-            ALLOC(h->osb32_len, float, nbr.size());
             ALLOC(h->osb32_mvol, float, np);
             ALLOC(h->osb32_theta, float, np);
-            ALLOC(h->osb32_alpha, float, np);
-            ALLOC(h->osb32_beta, float, np);
+            ALLOC(h->osb32_ab, float2, np);
         } else if (h->dw) {
             ALLOC(h->osb_mvol, double, np);
             ALLOC(h->osb_theta, double, np);

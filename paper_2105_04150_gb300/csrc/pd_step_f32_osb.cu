@@ -9,9 +9,12 @@ namespace {
 // ---------------------------------------------------------------------------
 // Ordinary state-based model in FP32 (the FP64 form and the formulas are in
 // pd_step_osb.cu).  Lengths in horizon units: e = |y| - |xi| comes out of the
-// cancellation-free bond terms as num |xi| / den; theta is unit free; the
-// per-node coefficients are stored multiplied by delta (alpha' = delta alpha,
-// beta' = delta beta with m in horizon units), so that
+// cancellation-free bond terms as num |xi| / den (den = |xi| (|xi| + |y|)), so
+// the dilation's |xi| e = num |xi|^2 / den needs no length at all and the force
+// forms |xi| from |xi|^2 with one reciprocal square root: no per-slot length
+// is stored or read.  theta is unit free; the per-node coefficients are stored
+// multiplied by delta (alpha' = delta alpha, beta' = delta beta with m in
+// horizon units) as one (alpha', beta') pair per node, so that
 // t'_ij + t'_ji = (alpha'_i + alpha'_j) |xi| + (beta'_i + beta'_j) e is a force
 // density per unit volume.  Bonds break in the dilation kernel, with the
 // near-s_c decision of the bond-based kernel; node weights are the volumes.
@@ -131,8 +134,9 @@ __global__ void __launch_bounds__(256) k_osb32_dilation(const __grid_constant__ 
                 const BondF32 bd = bond_f32_pk(pi, ra[u], rb[u]);
                 const bool cand = bd.num >= a.fast_lo * bd.den;
                 pc |= cand ? (1u << u) : 0u;
-                const float L = o.len[(g * W + m0 + u) * 32 + lane];
-                const float contrib = L * (bd.num * L / bd.den) * node_w<UW>(a, jj[u], wc);
+                // |xi| e V_j = num |xi|^2 V_j / den, |xi|^2 = |y|^2 - num
+                const float contrib =
+                    __fdividef(bd.num * (bd.y2 - bd.num), bd.den) * node_w<UW>(a, jj[u], wc);
                 acc += (alive && !cand) ? contrib : 0.0f;
             }
             pend |= (pc & wb) << b0;
@@ -150,8 +154,7 @@ __global__ void __launch_bounds__(256) k_osb32_dilation(const __grid_constant__ 
                         float4 ra1, rb1;
                         ld_rec(R + 2 * (int64_t)j, ra1, rb1);
                         const BondF32 bd = bond_f32_pk(pi, ra1, rb1);
-                        const float L = o.len[slot];
-                        acc += L * (bd.num * L / bd.den) * node_w<UW>(a, j, wc);
+                        acc += __fdividef(bd.num * (bd.y2 - bd.num), bd.den) * node_w<UW>(a, j, wc);
                     }
                 }
                 if (nword != word) bw[q * 32] = nword;
@@ -160,8 +163,8 @@ __global__ void __launch_bounds__(256) k_osb32_dilation(const __grid_constant__ 
         const float m = o.mvol[i];
         const float th = m > 0.0f ? 3.0f * acc / m : 0.0f;
         o.theta[i] = th;
-        o.alpha[i] = m > 0.0f ? (float)(3.0 * o.K * th / (o.delta * m)) - o.beta[i] * th / 3.0f
-                              : 0.0f;
+        const float be = o.ab[i].y;  // static: set up once from m
+        o.ab[i].x = m > 0.0f ? (float)(3.0 * o.K * th / (o.delta * m)) - be * th / 3.0f : 0.0f;
     }
 }
 
@@ -187,7 +190,8 @@ __global__ void __launch_bounds__(256) k_osb32_force(const __grid_constant__ Ste
         const NodeF32 ni = unpack(ai, bi);
         const LanePairs pi = lane_pairs(ai, bi);
         const float wc = UW ? lane_wconst(a, i) : 0.0f;
-        const float al = o.alpha[i], be = o.beta[i];
+        const float2 abi = o.ab[i];
+        const float al = abi.x, be = abi.y;
         const uint32_t* bw = a.bits + g * a.Q * 32 + lane;
         float fx = 0.f, fy = 0.f, fz = 0.f, ws = 0.f;
         uint32_t word = 0u;
@@ -214,9 +218,11 @@ __global__ void __launch_bounds__(256) k_osb32_force(const __grid_constant__ Ste
             for (int u = 0; u < kUnroll; ++u) {
                 const bool alive = (wb >> u) & 1u;
                 const BondF32 bd = bond_f32_pk(pi, ra[u], rb[u]);
-                const float L = o.len[(g * W + m0 + u) * 32 + lane];
-                const float e = bd.num * L / bd.den;
-                const float t = (al + o.alpha[jj[u]]) * L + (be + o.beta[jj[u]]) * e;  // t'_ij + t'_ji
+                const float2 abj = __ldg(o.ab + jj[u]);  // written by the dilation launch
+                const float xx = bd.y2 - bd.num;        // |xi|^2
+                const float L = xx * rsqrtf(xx);
+                const float e = __fdividef(bd.num * L, bd.den);
+                const float t = (al + abj.x) * L + (be + abj.y) * e;  // t'_ij + t'_ji
                 const float vj = node_w<UW>(a, jj[u], wc);
                 float f = t * vj * rsqrtf(bd.y2);
                 f = alive ? f : 0.0f;
@@ -230,7 +236,7 @@ __global__ void __launch_bounds__(256) k_osb32_force(const __grid_constant__ Ste
     }
 }
 
-// per-slot |xi| (horizon units), weighted volume m (horizon units) and beta'
+// weighted volume m (horizon units) and beta' of every node
 __global__ void k_osb32_setup(const StepArgsF32 a, const OsbArgs32 o)
 {
     const int64_t W = 32LL * a.Q;
@@ -248,12 +254,11 @@ __global__ void k_osb32_setup(const StepArgsF32 a, const OsbArgs32 o)
                              e2 = a.x64[3 * j + 2] - a.x64[3 * p + 2];
                 L = sqrt(e0 * e0 + e1 * e1 + e2 * e2) * a.inv_delta;
             }
-            o.len[slot] = (float)L;
             if ((a.bits[(g * a.Q + (k >> 5)) * 32 + lane] >> (k & 31)) & 1u)
                 m += L * L * (double)node_w<false>(a, j, 0.0f);
         }
         o.mvol[p] = (float)m;
-        o.beta[p] = m > 0.0 ? (float)(15.0 * o.G / (o.delta * m)) : 0.0f;
+        o.ab[p] = make_float2(0.0f, m > 0.0 ? (float)(15.0 * o.G / (o.delta * m)) : 0.0f);
     }
 }
 
@@ -266,22 +271,31 @@ cudaError_t launch_osb32_setup(const StepArgsF32& a, const OsbArgs32& o, cudaStr
     return cudaGetLastError();
 }
 
-cudaError_t launch_osb32_step(const StepArgsF32& a, const OsbArgs32& o, int sc_mode, int grid,
-                              int block, cudaStream_t s)
+namespace {
+template <int SCM, bool UW>
+cudaError_t osb32_step(const StepArgsF32& a, const OsbArgs32& o, int grid, int grid_dil,
+                       int block, cudaStream_t s)
 {
-    if (sc_mode == 0 && a.uniform_w) {
-        k_osb32_dilation<0, true><<<grid, block, 0, s>>>(a, o);
-        if (cudaPeekAtLastError() == cudaSuccess) k_osb32_force<0, true><<<grid, block, 0, s>>>(a, o);
-    } else if (sc_mode == 0) {
-        k_osb32_dilation<0, false><<<grid, block, 0, s>>>(a, o);
-        if (cudaPeekAtLastError() == cudaSuccess) k_osb32_force<0, false><<<grid, block, 0, s>>>(a, o);
-    } else if (a.uniform_w) {
-        k_osb32_dilation<1, true><<<grid, block, 0, s>>>(a, o);
-        if (cudaPeekAtLastError() == cudaSuccess) k_osb32_force<1, true><<<grid, block, 0, s>>>(a, o);
-    } else {
-        k_osb32_dilation<1, false><<<grid, block, 0, s>>>(a, o);
-        if (cudaPeekAtLastError() == cudaSuccess) k_osb32_force<1, false><<<grid, block, 0, s>>>(a, o);
-    }
+    k_osb32_dilation<SCM, UW><<<grid_dil, block, 0, s>>>(a, o);
+    if (cudaPeekAtLastError() == cudaSuccess) k_osb32_force<SCM, UW><<<grid, block, 0, s>>>(a, o);
     return cudaGetLastError();
+}
+}  // namespace
+
+const void* osb32_dilation_kernel(int sc_mode, bool uniform_w)
+{
+    if (sc_mode == 0)
+        return uniform_w ? (const void*)k_osb32_dilation<0, true> : (const void*)k_osb32_dilation<0, false>;
+    return uniform_w ? (const void*)k_osb32_dilation<1, true> : (const void*)k_osb32_dilation<1, false>;
+}
+
+cudaError_t launch_osb32_step(const StepArgsF32& a, const OsbArgs32& o, int sc_mode, int grid,
+                              int grid_dil, int block, cudaStream_t s)
+{
+    if (sc_mode == 0)
+        return a.uniform_w ? osb32_step<0, true>(a, o, grid, grid_dil, block, s)
+                           : osb32_step<0, false>(a, o, grid, grid_dil, block, s);
+    return a.uniform_w ? osb32_step<1, true>(a, o, grid, grid_dil, block, s)
+                       : osb32_step<1, false>(a, o, grid, grid_dil, block, s);
 }
 }  // namespace pd
