@@ -130,8 +130,9 @@ typedef struct {
  * the PMB law it is not limited to Poisson's ratio 1/4.  FP64, FP32 and
  * PD_PREC_DW handles (FP32 and PD_PREC_DW: the bond-based path's records,
  * horizon units and near-s_c FP64 decision) with either integrator;
- * c is not used (any value > 0);
- * no softening, per-bond stiffness, batches or adjoint.  Two kernels per step.
+ * c is not used (any value > 0) except by the dt stability check;
+ * in batches with one (K, G) for every instance; no softening, per-bond
+ * stiffness or adjoint.  Two kernels per step.
  */
 
 /*
@@ -418,7 +419,8 @@ typedef struct {
     int32_t n_cuts;
     int32_t reserved;
     pd_material mat;         /* c and critical stretch of this instance (the softening
-                                parameters and model must equal instance 0's) */
+                                parameters, the model and, for the state-based model,
+                                bulk_modulus and shear_modulus must equal instance 0's) */
     pd_bc bc;                /* BCs of this instance; disp_rate and load must be equal
                                 across the batch (they are handle-wide) */
 } pd_instance;

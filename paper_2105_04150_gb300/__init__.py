@@ -340,7 +340,8 @@ def pd_batch_create(instances, *, dt: float, damping: float, density: float,
                     blocks_per_sm: int = 0, reorder: int = 0, integrator: int = 0) -> int:
     """Create a batch handle from a list of dicts with the keys of ``pd_create``'s
     body arguments: coords, volumes, horizon, c, sc / sc_hash, cuts, bc_type,
-    bc_disp, bc_force, no_fail, disp_rate, load, ramp_steps, kr, trilinear."""
+    bc_disp, bc_force, no_fail, disp_rate, load, ramp_steps, kr, trilinear,
+    state_based."""
     keep = []
     arr = (_Instance * len(instances))()
     for k, I in enumerate(instances):
@@ -360,6 +361,10 @@ def pd_batch_create(instances, *, dt: float, damping: float, density: float,
                         kr=float(I.get("kr", 0.0)))
         if I.get("trilinear") is not None:  # (s_1 / s_0, kink force / peak force)
             mat.kink_ratio, mat.kink_force = float(I["trilinear"][0]), float(I["trilinear"][1])
+        if I.get("state_based") is not None:  # (K, G): ordinary state-based linear solid
+            mat.model = 1
+            mat.bulk_modulus = float(I["state_based"][0])
+            mat.shear_modulus = float(I["state_based"][1])
         if I.get("sc_hash") is not None:
             s = I["sc_hash"]
             mat.sc_mode, mat.sc_seed, mat.sc_lo, mat.sc_hi = 1, int(s[0]), float(s[1]), float(s[2])
@@ -456,7 +461,8 @@ def instance_from_workload(w, c=None) -> dict:
                 sc_hash=w.sc_hash, cuts=w.cuts_array(), bc_type=w.bc_type, bc_disp=w.bc_disp,
                 bc_force=w.bc_force, no_fail=w.no_fail, disp_rate=w.disp_rate, load=w.load,
                 ramp_steps=getattr(w, "ramp_steps", 0), kr=getattr(w, "kr", 0.0),
-                trilinear=getattr(w, "trilinear", None))
+                trilinear=getattr(w, "trilinear", None),
+                state_based=getattr(w, "state_based", None))
 
 
 class Model:

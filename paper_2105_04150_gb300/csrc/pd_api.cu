@@ -1014,9 +1014,12 @@ pd_status pd_batch_create(int32_t n_inst, const pd_instance* inst, const pd_conf
             I.bc.ramp_steps != inst[0].bc.ramp_steps)
             return fail(PD_ERR_ARG,
                         "instance %d: disp_rate, load and ramp_steps must equal instance 0's", b);
-        if (I.mat.model != 0)
+        if (I.mat.model != inst[0].mat.model ||
+            (I.mat.model == 1 && (I.mat.bulk_modulus != inst[0].mat.bulk_modulus ||
+                                  I.mat.shear_modulus != inst[0].mat.shear_modulus)))
             return fail(PD_ERR_ARG,
-                        "instance %d: the state-based model is not available in batches", b);
+                        "instance %d: model, bulk_modulus and shear_modulus must equal instance 0's",
+                        b);
         if (I.mat.kr != inst[0].mat.kr || I.mat.kink_ratio != inst[0].mat.kink_ratio ||
             I.mat.kink_force != inst[0].mat.kink_force)
             return fail(PD_ERR_ARG,
@@ -1049,6 +1052,16 @@ pd_status pd_batch_create(int32_t n_inst, const pd_instance* inst, const pd_conf
             return fail(PD_ERR_ARG, "instance %d: %s", b, msg.c_str());
         }
         apply_cuts(I.n, I.coords, I.cuts, I.n_cuts, off, idx);
+        if (cfg->check_dt && I.mat.model == 1) {
+            // the state-based weights are plain volumes: bound each instance with
+            // its own PMB-equivalent micromodulus, as for a single model
+            const double dtc = stable_dt(I.n, I.coords, I.volumes, off, idx, I.mat.c, cfg->density);
+            if (cfg->dt > dtc) {
+                delete h;
+                return fail(PD_ERR_UNSTABLE_DT, "instance %d: dt = %g exceeds the stable bound %g",
+                            b, cfg->dt, dtc);
+            }
+        }
         for (int64_t i = 0; i < I.n; ++i) h->off.push_back(h->off.back() + (off[i + 1] - off[i]));
         for (int32_t j : idx) h->idx.push_back((int32_t)(j + o));
         double lo[3], hi[3];
@@ -1067,7 +1080,9 @@ pd_status pd_batch_create(int32_t n_inst, const pd_instance* inst, const pd_conf
                 if (I.bc.disp) disp[3 * k + a] = I.bc.disp[3 * i + a];
                 if (I.bc.force) force[3 * k + a] = I.bc.force[3 * i + a];
             }
-            wv[k] = I.mat.c * I.volumes[i];
+            // bond-based weights carry the instance's micromodulus; the state-based
+            // model's are the volumes
+            wv[k] = (I.mat.model == 1 ? 1.0 : I.mat.c) * I.volumes[i];
             if (I.bc.no_fail) nofail[k] = I.bc.no_fail[i];
             d.inst[k] = b;
             d.hid[k] = (int32_t)i;
@@ -1081,7 +1096,7 @@ pd_status pd_batch_create(int32_t n_inst, const pd_instance* inst, const pd_conf
         // softening: the band below the smallest s_0 = s_c / kr is resolved too
         ip.fast_lo = (float)((1.0 - 2.0 * kGuard) * ip.sc_lo /
                              (inst[0].mat.kr >= 1.0 ? inst[0].mat.kr : 1.0));
-        ip.w_const = (float)(I.mat.c * I.volumes[0]);
+        ip.w_const = (float)((I.mat.model == 1 ? 1.0 : I.mat.c) * I.volumes[0]);
         for (int64_t i = 1; i < I.n && uniform_all; ++i) uniform_all = I.volumes[i] == I.volumes[0];
         h->inst_off.push_back(o + I.n);
     }

@@ -101,6 +101,8 @@ __global__ void __launch_bounds__(256) k_osb32_dilation(const __grid_constant__ 
         ld_rec(R + 2 * i, ai, bi);
         const LanePairs pi = lane_pairs(ai, bi);
         const float wc = UW ? lane_wconst(a, i) : 0.0f;
+        // per instance in a batch, as in the bond-based step
+        const float fast_lo = a.inst != nullptr ? a.itab[a.inst[i]].fast_lo : a.fast_lo;
         uint32_t* bw = a.bits + g * a.Q * 32 + lane;
         float acc = 0.0f;
         uint32_t word = 0u, nword = 0u, pend = 0u;
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(256) k_osb32_dilation(const __grid_constant__ 
             for (int u = 0; u < kUnroll; ++u) {
                 const bool alive = (wb >> u) & 1u;
                 const BondF32 bd = bond_f32_pk(pi, ra[u], rb[u]);
-                const bool cand = bd.num >= a.fast_lo * bd.den;
+                const bool cand = bd.num >= fast_lo * bd.den;
                 pc |= cand ? (1u << u) : 0u;
                 // |xi| e V_j = num |xi|^2 V_j / den, |xi|^2 = |y|^2 - num
                 const float contrib =

@@ -33,11 +33,24 @@ __device__ __forceinline__ uint64_t splitmix_out(uint64_t seed, uint64_t m)
 
 __device__ __forceinline__ double bond_sc(const StepArgsF64& a, int64_t i, int64_t j)
 {
-    if (a.sc_lo == a.sc_hi) return a.sc;
-    const uint64_t gi = (uint32_t)a.gid[i], gj = (uint32_t)a.gid[j];
+    double lo_sc = a.sc_lo, hi_sc = a.sc_hi, sc = a.sc;
+    uint64_t seed = a.sc_seed, gi, gj;
+    if (a.inst != nullptr) {  // batch: the instance's parameters, instance-local ids as keys
+        const InstParams& ip = a.itab[a.inst[i]];
+        if (ip.sc_mode == 0) return ip.sc;
+        lo_sc = ip.sc_lo;
+        hi_sc = ip.sc_hi;
+        seed = ip.sc_seed;
+        gi = (uint32_t)a.hid[i];
+        gj = (uint32_t)a.hid[j];
+    } else {
+        if (lo_sc == hi_sc) return sc;
+        gi = (uint32_t)a.gid[i];
+        gj = (uint32_t)a.gid[j];
+    }
     const uint64_t lo = gi < gj ? gi : gj, hi = gi < gj ? gj : gi;
-    const uint64_t h = splitmix_out(a.sc_seed, ((lo << 32) | hi) + 1ull);
-    return a.sc_lo + (a.sc_hi - a.sc_lo) * ((double)(h >> 11) * 0x1.0p-53);
+    const uint64_t h = splitmix_out(seed, ((lo << 32) | hi) + 1ull);
+    return lo_sc + (hi_sc - lo_sc) * ((double)(h >> 11) * 0x1.0p-53);
 }
 
 // deformed bond vector and its length from the records of i and j

@@ -38,11 +38,24 @@ __device__ __forceinline__ uint64_t splitmix_out(uint64_t seed, uint64_t m)
 
 __device__ __forceinline__ double bond_sc(const StepArgsF64& a, int64_t i, int64_t j)
 {
-    if (a.sc_lo == a.sc_hi) return a.sc;
-    const uint64_t gi = (uint32_t)a.gid[i], gj = (uint32_t)a.gid[j];
+    double lo_sc = a.sc_lo, hi_sc = a.sc_hi, sc = a.sc;
+    uint64_t seed = a.sc_seed, gi, gj;
+    if (a.inst != nullptr) {  // batch: the instance's parameters, instance-local ids as keys
+        const InstParams& ip = a.itab[a.inst[i]];
+        if (ip.sc_mode == 0) return ip.sc;
+        lo_sc = ip.sc_lo;
+        hi_sc = ip.sc_hi;
+        seed = ip.sc_seed;
+        gi = (uint32_t)a.hid[i];
+        gj = (uint32_t)a.hid[j];
+    } else {
+        if (lo_sc == hi_sc) return sc;
+        gi = (uint32_t)a.gid[i];
+        gj = (uint32_t)a.gid[j];
+    }
     const uint64_t lo = gi < gj ? gi : gj, hi = gi < gj ? gj : gi;
-    const uint64_t h = splitmix_out(a.sc_seed, ((lo << 32) | hi) + 1ull);
-    return a.sc_lo + (a.sc_hi - a.sc_lo) * ((double)(h >> 11) * 0x1.0p-53);
+    const uint64_t h = splitmix_out(seed, ((lo << 32) | hi) + 1ull);
+    return lo_sc + (hi_sc - lo_sc) * ((double)(h >> 11) * 0x1.0p-53);
 }
 
 __device__ __forceinline__ void split(double x, float& h, float& l)
@@ -145,6 +158,11 @@ __global__ void __launch_bounds__(256, 2)
         ld_rec(R + 4 * i + 2, me.b0, me.b1);
         const OwnDw own = own_of(me);
         uint32_t* bw = a.bits + g * Q * 32 + lane;
+        // band below the smallest s_c the node's bonds can have (per instance in
+        // a batch: both ends of a bond belong to the same instance)
+        const float fast_lo = a.inst != nullptr
+                                  ? (float)((1.0 - 0x1.0p-20) * a.itab[a.inst[i]].sc_lo)
+                                  : d.fast_lo;
         Dw acc{0.f, 0.f};  // sum of L~ e~ V_j over intact bonds
         const int nch = (Wg + 1) >> 1;
         int32_t jn0 = __ldg(col), jn1 = __ldg(col + 32);
@@ -170,7 +188,7 @@ __global__ void __launch_bounds__(256, 2)
                 ld_rec(R + 4 * (int64_t)jj[u] + 2, nb.b0, nb.b1);
                 const float2 len = __ldg(d.len + (g * W + m0 + u) * 32 + lane);
                 const OsbBondDw bd = osb_bond_dw(own, nb, len);
-                const bool cand = bd.s.h >= d.fast_lo;
+                const bool cand = bd.s.h >= fast_lo;
                 const bool ok = ((wb >> u) & 1u) && !cand;
                 pend |= (cand && ((wb >> u) & 1u) ? 1u : 0u) << (b0 + u);
                 const Dw L{len.x, len.y};

@@ -141,6 +141,57 @@ def test_batch_with_softening_equals_models_alone(prec):
     assert softened > 0
 
 
+@pytest.mark.parametrize("prec", [F64, F32, DW])
+def test_batch_of_state_based_models_equals_models_alone(prec):
+    # the ordinary state-based solid in a batch: one (K, G) for the batch, each
+    # instance its own size and s_c (one a per-bond draw keyed by local ids)
+    K = 5e9
+    ws = [workloads.tensile_bar(16, 5, 5, rate=4e-6, steps=100, K=K, sc=3e-3),
+          workloads.tensile_bar(11, 4, 3, rate=5e-6, slab=2, steps=100, K=K, sc=2e-3),
+          workloads.tensile_bar(20, 3, 3, rate=4e-6, steps=100, K=K, sc=2.5e-3)]
+    ws[2].sc_hash = (2105041507, 2e-3, 3e-3)
+    for w in ws:
+        w.state_based = (K, 0.6 * K)  # nu = 1/4
+    steps = 100
+    bm = pdgb.Model.batch(ws, precision=prec, graph_steps=20)
+    off = bm.offsets()
+    bm.step(steps)
+    u, v = bm.state()
+    mu = bm.bonds()
+    phi = bm.damage()
+    boff, _ = bm.family()
+    bm.close()
+    broke = 0
+    for k, w in enumerate(ws):
+        a = _alone(w, prec, steps)
+        s = slice(off[k], off[k + 1])
+        mk = mu[boff[off[k]]:boff[off[k + 1]]]
+        broke += int((a["mu"] == 0).sum())
+        den = np.abs(a["u"]).max()
+        if prec == F64:
+            assert np.array_equal(u[s], a["u"]) and np.array_equal(v[s], a["v"])
+            assert np.array_equal(mk, a["mu"]) and np.array_equal(phi[s], a["phi"])
+        elif prec == DW:
+            # per-node weights in the batch, one weight alone: rounding only
+            assert np.abs(u[s] - a["u"]).max() <= 1e-10 * den
+            assert (mk != a["mu"]).mean() <= 1e-3
+        else:
+            assert np.abs(u[s] - a["u"]).max() <= 1e-4 * den
+            assert (mk != a["mu"]).mean() < 1e-3
+    assert broke > 0
+
+
+def test_batch_rejects_mixed_state_based_parameters():
+    ws = [workloads.tensile_bar(6, 3, 3, steps=5), workloads.tensile_bar(5, 3, 3, steps=5)]
+    ws[0].state_based = (5e9, 3e9)
+    with pytest.raises(pdgb.PdError) as e:  # one bond-based, one state-based
+        pdgb.Model.batch(ws, precision=F64)
+    assert e.value.name == "PD_ERR_ARG"
+    ws[1].state_based = (5e9, 2e9)
+    with pytest.raises(pdgb.PdError):        # different shear moduli
+        pdgb.Model.batch(ws, precision=F64)
+
+
 @pytest.mark.parametrize("prec", [F64, DW])
 def test_batch_instance_matches_oracle(prec):
     ws = _instances()[:3]
