@@ -138,7 +138,8 @@ struct pd_handle {
     void* vpeek = nullptr;  // velocity-Verlet: full-step velocity for pd_get_state
     int64_t peek_step = -1; // step whose force pass filled vpeek (-1: none)
     int64_t vv_start = 0;   // step of the last set state (velocity-Verlet: a^n formed afresh)
-    int grid_dil = 0;       // grid of the FP32 state-based dilation kernel
+    int grid_dil = 0;       // grids of the FP32 state-based dilation and force kernels
+    int grid_osbf = 0;
     double kr = 0.0;        // >= 1: bilinear softening, s_0 = s_c / kr
     double k1 = 0.0, beta = 1.0;  // trilinear kink (k1 > 1)
     void* integ = nullptr;  // softening: per-slot integrity (float / double)
@@ -423,7 +424,7 @@ cudaError_t launch_one(pd_handle* h, int k)
         return launch_step_dw(args_f64(h, k), dw_args(h), h->sc_mode, h->grid, h->block,
                               h->stream);
     if (h->model == 1 && h->precision == 32)
-        return launch_osb32_step(args_f32(h, k), osb32_args(h), h->sc_mode, h->grid, h->grid_dil, h->block,
+        return launch_osb32_step(args_f32(h, k), osb32_args(h), h->sc_mode, h->grid_osbf, h->grid_dil, h->block,
                                  h->stream);
     if (h->model == 1)
         return launch_osb_step(args_f64(h, k), osb_args(h), h->grid, h->block, h->stream);
@@ -448,15 +449,21 @@ pd_status choose_grid(pd_handle* h, int blocks_per_sm)
     const int64_t need = (h->n_slices + warps_per_block - 1) / warps_per_block;
     h->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * occ, need));
     h->grid_dil = h->grid;
-    if (h->model == 1 && h->precision == 32) {  // the state-based dilation kernel's own grid
-        const void* fd = osb32_dilation_kernel(h->sc_mode, h->uniform_vol);
-        PD_CUDA(cudaFuncSetAttribute(fd, cudaFuncAttributePreferredSharedMemoryCarveout, 0),
-                "carveout");
-        int od = 0;
-        PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&od, fd, h->block, 0), "occupancy");
-        if (blocks_per_sm > 0) od = std::min(od, blocks_per_sm);
-        h->grid_dil = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(od, 1),
-                                                                  need));
+    h->grid_osbf = h->grid;
+    if (h->model == 1 && h->precision == 32) {  // the state-based kernels' own grids
+        auto grid_of_kernel = [&](const void* fn, int& out) -> pd_status {
+            PD_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 0),
+                    "carveout");
+            int o = 0;
+            PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, h->block, 0), "occupancy");
+            if (blocks_per_sm > 0) o = std::min(o, blocks_per_sm);
+            out = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(o, 1), need));
+            return PD_OK;
+        };
+        pd_status st = grid_of_kernel(osb32_dilation_kernel(h->sc_mode, h->uniform_vol), h->grid_dil);
+        if (st == PD_OK)
+            st = grid_of_kernel(osb32_force_kernel(h->sc_mode, h->uniform_vol), h->grid_osbf);
+        if (st != PD_OK) return st;
     }
     return PD_OK;
 }
@@ -497,7 +504,7 @@ pd_status vv_force_pass(pd_handle* h)
         StepArgsF32 a = args_f32(h, 0);
         a.peek = 1;
         a.vout = (float*)h->vpeek;
-        e = h->model == 1 ? launch_osb32_step(a, osb32_args(h), h->sc_mode, h->grid, h->grid_dil, h->block,
+        e = h->model == 1 ? launch_osb32_step(a, osb32_args(h), h->sc_mode, h->grid_osbf, h->grid_dil, h->block,
                                               h->stream)
                           : launch_f32(h, a);
     } else {

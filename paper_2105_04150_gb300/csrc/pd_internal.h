@@ -334,10 +334,11 @@ cudaError_t launch_osb_setup(const StepArgsF64& a, const OsbArgs& o, const doubl
 cudaError_t launch_osb_step(const StepArgsF64& a, const OsbArgs& o, int grid, int block,
                             cudaStream_t s);
 cudaError_t launch_osb32_setup(const StepArgsF32& a, const OsbArgs32& o, cudaStream_t s);
-// dilation launch on its own grid (it fits more resident blocks than the force kernel)
+// the two state-based launches, each on a grid sized by its own occupancy
 cudaError_t launch_osb32_step(const StepArgsF32& a, const OsbArgs32& o, int sc_mode, int grid,
                               int grid_dil, int block, cudaStream_t s);
 const void* osb32_dilation_kernel(int sc_mode, bool uniform_w);
+const void* osb32_force_kernel(int sc_mode, bool uniform_w);
 // per slot 1 / |x_j - x_i| from the FP64 reference positions (0 for unused slots)
 cudaError_t launch_inv_len(const double* x64, const int32_t* nbr, const int32_t* sw, int64_t n,
                            int Q, double* ilen, cudaStream_t s);

@@ -291,6 +291,13 @@ const void* osb32_dilation_kernel(int sc_mode, bool uniform_w)
     return uniform_w ? (const void*)k_osb32_dilation<1, true> : (const void*)k_osb32_dilation<1, false>;
 }
 
+const void* osb32_force_kernel(int sc_mode, bool uniform_w)
+{
+    if (sc_mode == 0)
+        return uniform_w ? (const void*)k_osb32_force<0, true> : (const void*)k_osb32_force<0, false>;
+    return uniform_w ? (const void*)k_osb32_force<1, true> : (const void*)k_osb32_force<1, false>;
+}
+
 cudaError_t launch_osb32_step(const StepArgsF32& a, const OsbArgs32& o, int sc_mode, int grid,
                               int grid_dil, int block, cudaStream_t s)
 {
