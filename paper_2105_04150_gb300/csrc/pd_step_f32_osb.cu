@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256) k_osb32_dilation(const __grid_constant__ 
 }
 
 template <int SCM, bool UW>
-__global__ void __launch_bounds__(256) k_osb32_force(const __grid_constant__ StepArgsF32 a,
+__global__ void __launch_bounds__(256, 3) k_osb32_force(const __grid_constant__ StepArgsF32 a,
                                                      const OsbArgs32 o)
 {
     const int lane = threadIdx.x & 31;
