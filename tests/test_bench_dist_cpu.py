@@ -79,3 +79,20 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank_zero():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_state_based_oracle_timing_runs_whole_steps():
+    # the state-based oracle reads every node's dilation, so the CPU baseline
+    # of a state-based line times whole steps over all rows
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    import workloads
+    oracle.build()
+    w = workloads.tensile_bar(8, 4, 4, steps=3)
+    w.state_based = (w.bulk_modulus, 0.6 * w.bulk_modulus)
+    r = bench.oracle_sample(w, oracle.micromodulus(w.bulk_modulus, w.horizon), budget_s=0.5,
+                            steps=2)
+    off, idx = oracle.cut_family(w.coords, w.horizon, w.cuts_array())
+    assert r["kind"] == "oracle" and r["value"] > 0 and r["n_bonds_total"] == len(idx)
+    assert 1 <= r["steps"] <= 2 and "state-based" in r["sample"]
