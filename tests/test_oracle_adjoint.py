@@ -152,3 +152,31 @@ def test_oracle_vv_adjoint_zero_steps_is_identity():
                                       integrator="vv")
     assert np.all(gc == 0.0) and gl == 0.0
     assert np.array_equal(gu0, gu) and np.array_equal(gv0, gv)
+
+
+def test_bond_jacobian_dot_product():
+    # <J v, w> = <v, J^T w> for J = dF/du of the pairwise force density: J v by
+    # central differences of the oracle's force, J^T w from one reverse step
+    # (L = <w, v^1> with v^1 = v^0 + dt (F(u^0) - eta v^0) / rho, so
+    # dL/du^0 = (dt / rho) J^T w); no controlled components
+    w = workloads.cracked_plate_force(9, 7, 3, load=3e11, steps=1)
+    w.bc_type[:] = 0
+    w.sc = 1.0
+    off, idx = oracle.cut_family(w.coords, w.horizon, w.cuts_array())
+    c0 = oracle.micromodulus(w.bulk_modulus, w.horizon)
+    m = oracle.Model.from_workload(w, off, idx, c=c0)
+    rng = np.random.default_rng(21)
+    u0, v0 = workloads.random_state(w.n, 22, 1e-7, 1e-3)
+    vdir = rng.standard_normal((w.n, 3)) * 1e-7
+    wvec = rng.standard_normal((w.n, 3))
+
+    def force(u):
+        _, _, F = m.step(0, u.copy(), v0.copy(), m.fresh_bonds(), want_force=True)
+        return F
+
+    h = 1e-3
+    Jv = (force(u0 + h * vdir) - force(u0 - h * vdir)) / (2 * h)
+    _, _, gu0, _ = oracle.adjoint(m, 0, 1, u0, v0, m.fresh_bonds(), np.zeros_like(u0), wvec)
+    JTw = gu0 * w.density / w.dt
+    lhs, rhs = float((Jv * wvec).sum()), float((vdir * JTw).sum())
+    assert abs(lhs - rhs) <= 1e-7 * abs(rhs), (lhs, rhs)
