@@ -40,8 +40,13 @@ What pins each function (tests in ``tests/test_oracle_pins.py``):
   G gamma^2 / 2 times the stencil quadrature ratio (-> 1 for large horizons);
   force = minus the energy gradient; rigid motions are force free; momentum is
   conserved (``tests/test_oracle_osb.py``).
-* ``adjoint``: central differences of the pinned forward run
-  (``tests/test_oracle_adjoint.py``).
+* ``critical_stretch`` (Eq. 7) in 3D, plane stress and plane strain: the
+  fracture-energy derivation by quadrature (micromodulus from the
+  strain-energy match, energy of the bonds crossing a unit area);
+  ``youngs_modulus``: the Lame-parameter forms.
+* ``adjoint`` (Euler-Cromer and velocity-Verlet reverse modes): central
+  differences of the pinned forward runs; the dot-product test of the bond
+  Jacobian (``tests/test_oracle_adjoint.py``).
 """
 from __future__ import annotations
 

@@ -21,6 +21,11 @@
  *       v^{n+1} = v^n + dt (F(u^n) - eta v^n) / rho,  u^{n+1} = u^n + dt v^{n+1}
  *   - displacement BC:  u = g * rate * (n+1) after the update, and the velocity
  *       of that component is the prescribed rate g * rate / dt.
+ *   - critical stretch  Eq. (7), Section 2.2 (3D, plane stress, plane strain)
+ *   - reverse mode      of the damped Euler-Cromer run (or_adjoint) and of the
+ *       damped velocity-Verlet run (or_adjoint_vv), bond flags frozen: the
+ *       forward assignments reversed in turn (the paper's outer loops,
+ *       Section 3.6; it prints no adjoint)
  * Per node the bonds are visited in ascending neighbour id; each node owns its
  * row of bond flags, so the node loop may run in parallel without races.
  *
