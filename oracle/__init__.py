@@ -23,7 +23,14 @@ What pins each function (tests in ``tests/test_oracle_pins.py``):
   bond reproduces the closed-form linear recurrence and breaks at the
   analytic step; displacement BCs follow the prescribed ramp.
 * ``damage`` (Eq. 8): zero at the start, in [0, 1], monotone, and equal to the
-  fraction of crossing offsets for a node next to a full planar cut.
+  fraction of crossing offsets for a node next to a full planar cut; with
+  unequal volumes, phi_i of a star-shaped family computed by hand in exact
+  fractions (each bond weighted by the neighbour's volume V_j).
+* no-fail nodes (Section 6): a two-node bond pulled past s_c with the flag on
+  either end alone stays intact in both directions and keeps its force.
+* body force (Eqs. 10-11): a node without bonds under load * b follows the
+  damped Euler-Cromer recurrence in exact rationals (bond-based and
+  state-based steps).
 * ``splitmix64``: the published reference outputs of the generator.
 * ``stiffness_factors`` (micromodulus functions, surface correction): the
   conical function reproduces the lattice quadrature ratio computed directly

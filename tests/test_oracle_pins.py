@@ -413,3 +413,104 @@ def test_family_boundary_is_inclusive():
     for method in ("brute", "cells"):
         off, idx = oracle.family(x, 2.0, rows=center, method=method)
         assert len(idx) == len(_offsets(2.0)) == 32
+
+
+# ------------------------------------------- Eq. (8) with unequal volumes
+def test_damage_weights_neighbours_by_their_volume():
+    # A star: node 0 bonded to nodes 1..4 (and each of them to node 0 only),
+    # with unequal volumes.  Eq. (8) weights each bond of the family by the
+    # neighbour's volume V_j, so with bonds 0-2 and 0-4 broken
+    #   phi_0 = 1 - (V_1 + V_3) / (V_1 + V_2 + V_3 + V_4),
+    # while node 2 (its only bond broken) has phi = 1 and node 1 has phi = 0.
+    # An unweighted count (1 - 2/4) or the owner's volume in place of V_j
+    # gives 0.5 for node 0 instead.
+    V = [Fraction(5, 4), Fraction(1, 2), Fraction(2), Fraction(3), Fraction(7)]
+    x = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0],
+                  [0.0, 0.0, 1.0], [-1.0, 0.0, 0.0]])
+    off = np.array([0, 4, 5, 6, 7, 8], dtype=np.int64)
+    idx = np.array([1, 2, 3, 4, 0, 0, 0, 0], dtype=np.int32)
+    mdl = oracle.Model(x, np.array([float(a) for a in V]), off, idx, c=1.0, sc=1.0)
+    mu = np.array([1, 0, 1, 0, 1, 0, 1, 0], dtype=np.uint8)  # both directions of 0-2, 0-4
+    phi = mdl.damage(mu)
+    expect0 = 1 - (V[1] + V[3]) / (V[1] + V[2] + V[3] + V[4])
+    assert expect0 == Fraction(18, 25)
+    assert phi[0] == pytest.approx(float(expect0), abs=1e-15)
+    assert phi[1] == 0.0 and phi[3] == 0.0
+    assert phi[2] == 1.0 and phi[4] == 1.0
+    # a partly broken family of a node whose neighbours differ only in volume:
+    # node 0 keeps the bond to the heaviest neighbour only
+    mu2 = np.array([0, 0, 0, 1, 1, 1, 1, 1], dtype=np.uint8)
+    phi2 = mdl.damage(mu2)
+    assert phi2[0] == pytest.approx(float(1 - V[4] / (V[1] + V[2] + V[3] + V[4])), abs=1e-15)
+
+
+# ------------------------------------------------- no-fail nodes (Section 6)
+@pytest.mark.parametrize("flagged", [0, 1])
+def test_no_fail_flag_on_either_end_keeps_bond(flagged):
+    # A bond with one end in a no-fail zone never breaks, whichever end carries
+    # the flag: both directions of the pair stay intact past s_c, and the bond
+    # keeps pulling the ends together with c s V_j (as in the two-node
+    # recurrence).  Without the flag the same motion breaks it at
+    # n* = ceil(s_c L / (2 r)).
+    L, r, sc = 1.0, 1e-3, 0.0105
+    x, off, idx = _two_nodes(L)
+    bt = np.ones((2, 3), np.uint8)
+    g = np.zeros((2, 3)); g[0, 0] = -r; g[1, 0] = r
+    nf = np.zeros(2, np.uint8); nf[flagged] = 1
+    nstar = math.ceil(sc * L / (2 * r))
+    for flags in (nf, None):
+        mdl = oracle.Model(x, np.array([2.0, 3.0]), off, idx, c=1.5, sc=sc, bc_type=bt,
+                           bc_disp=g, disp_rate=1.0, dt=1.0, damping=0.0, density=1.0,
+                           no_fail=flags)
+        u = np.zeros((2, 3)); v = np.zeros((2, 3)); mu = mdl.fresh_bonds()
+        for n in range(nstar + 5):
+            _, _, F = mdl.step(n, u, v, mu, want_force=True)
+            u = np.array([[-r * n, 0, 0], [r * n, 0, 0]], dtype=float)
+            s = 2 * r * n / L
+            if flags is not None or n < nstar:
+                assert mu[0] == 1 and mu[1] == 1
+                # force density on node 0 (+x toward node 1) and node 1 (-x)
+                assert F[0, 0] == pytest.approx(1.5 * s * 3.0, rel=1e-12, abs=1e-300)
+                assert F[1, 0] == pytest.approx(-1.5 * s * 2.0, rel=1e-12, abs=1e-300)
+            else:
+                assert mu[0] == 0 and mu[1] == 0
+                assert np.all(F == 0.0)
+            u, v = mdl.step(n, u, v, mu.copy())
+
+
+# ------------------------------------- body force in Eqs. (10)-(11)
+@pytest.mark.parametrize("state_based", [None, (2.0, 1.0)])
+def test_body_force_drives_free_node_by_exact_recurrence(state_based):
+    # A node with no bonds feels only the body force load * b_i (Eq. 11: the
+    # force density it adds to the internal force of Eq. 10).  Under the damped
+    # Euler-Cromer reading its velocity and displacement follow
+    #   v <- v + dt (load b - eta v) / rho,   u <- u + dt v,
+    # iterated here in exact rationals per component.  A flipped sign, a
+    # missing load factor or a force divided by the volume fails this.
+    b = [Fraction(3, 2), Fraction(-5, 4), Fraction(1, 8)]
+    load, rho, eta, dt, V = Fraction(7, 2), Fraction(5), Fraction(3, 4), Fraction(1, 16), 2.5
+    x = np.array([[0.0, 0.0, 0.0], [10.0, 0.0, 0.0]])
+    off = np.array([0, 0, 0], dtype=np.int64)
+    idx = np.zeros(0, dtype=np.int32)
+    bf = np.zeros((2, 3)); bf[0] = [float(t) for t in b]
+    mdl = oracle.Model(x, np.array([V, V]), off, idx, c=1.0, sc=1.0, bc_force=bf,
+                       load=float(load), dt=float(dt), damping=float(eta),
+                       density=float(rho), state_based=state_based)
+    u = np.zeros((2, 3)); v = np.zeros((2, 3)); mu = np.ones(1, np.uint8)
+    uq = [Fraction(0)] * 3
+    vq = [Fraction(0)] * 3
+    for n in range(240):
+        _, _, F = mdl.step(n, u, v, mu, want_force=True)
+        for a in range(3):
+            assert F[0, a] == float(load * b[a])
+        u, v = mdl.step(n, u, v, mu)
+        for a in range(3):
+            vq[a] = vq[a] + dt * (load * b[a] - eta * vq[a]) / rho
+            uq[a] = uq[a] + dt * vq[a]
+            assert u[0, a] == pytest.approx(float(uq[a]), rel=1e-13, abs=1e-300)
+            assert v[0, a] == pytest.approx(float(vq[a]), rel=1e-13, abs=1e-300)
+        assert np.all(u[1] == 0.0) and np.all(v[1] == 0.0)
+    # approaching the steady velocity the damping admits, load b / eta
+    # (15 time units = 2.25 relaxation times rho / eta)
+    for a in range(3):
+        assert float(vq[a]) == pytest.approx(float(load * b[a] / eta), rel=0.2)
