@@ -127,7 +127,7 @@ def describe(w, n_bonds, precision, integrator="ec"):
         "workload": f"{w.name}: {w.n:,} nodes, {n_bonds:,} directed bonds, "
                     f"delta = {w.horizon / w.dx:.4g} dx, "
                     + ("per-bond s_c ~ U[9e-5, 1.1e-4)" if w.sc_hash else f"s_c = {w.sc:g}"),
-        "precision": {32: "fp32 bonds, fp64 displacement", 64: "fp64",
+        "precision": {32: "fp32 bonds, float-float (48-bit) displacement", 64: "fp64",
                       48: "fp64-grade: double-word fp32 bonds, fp64 node state"}[precision],
         "n_nodes": w.n,
         "n_bonds": int(n_bonds),

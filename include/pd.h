@@ -49,8 +49,11 @@ typedef enum {
 } pd_status;
 
 #define PD_PREC_F64 64   /* FP64 throughout */
-#define PD_PREC_F32 32   /* FP32 bond arithmetic; FP64 displacement accumulation and
-                            an FP64 re-test of bonds whose stretch is near s_c */
+#define PD_PREC_F32 32   /* FP32 bond arithmetic; each node's displacement accumulated
+                            as a float-float pair (48-bit significand, exact
+                            two-sum updates; neighbours read the high word and a
+                            bf16 rounding of the low word); an FP64 re-test of
+                            bonds whose stretch is near s_c */
 #define PD_PREC_DW 48    /* FP64-grade step from FP32 double-word arithmetic: node
                             state (u, v) and integration in FP64 exactly as with
                             PD_PREC_F64; every bond quantity (xi, eta, y, the
