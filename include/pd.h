@@ -392,9 +392,11 @@ pd_status pd_adjoint_backward(pd_handle* h, const double* dLdu, const double* dL
  * array of PD_STATIC_SCRATCH_BYTES (64 MiB) per device, instead of the buffers
  * pd_adjoint_backward allocates on its first call and keeps in the handle.  The
  * array occupies that much device memory wherever the library's device code is
- * loaded.  A model needing more (about 152 B per node + 8 B per SELL slot + 12 B
- * per directed bond, + 8 B per bond when dL_dc is host memory) gets PD_ERR_ARG
- * with the required size in pd_last_error().  The recorded forward run
+ * loaded.  A model needing more gets PD_ERR_ARG with the required size in
+ * pd_last_error().  The need is 152 B per node (node count padded to a
+ * multiple of 32) + 8 B per SELL slot; with dL_dc, 8 B per node + 4 B per
+ * directed bond more (the family in canonical order), and a further 8 B per
+ * directed bond when dL_dc is host memory (each part rounded up to 256 B).  The recorded forward run
  * (pd_adjoint_forward, which does allocate) must exist: PD_ERR_STATE otherwise.
  *
  * The first call on a device looks up the array's device address

@@ -23,14 +23,14 @@ def _gpu():
     pdgb.build()
 
 
-def _model(nx, ny, nz, steps, seed):
+def _model(nx, ny, nz, steps, seed, precision=F64, integrator=pdgb.PD_INTEGRATOR_EC):
     w = workloads.cracked_plate_force(nx, ny, nz, load=3e11, steps=steps)
     w.bc_type[:4, 0] = 1
     w.bc_disp[:4, 0] = 1e-9
     w.disp_rate = 1.0
     w.sc = 1.0
     c0 = pdgb.pd_micromodulus(w.bulk_modulus, w.horizon)
-    m = pdgb.Model.from_workload(w, precision=F64, c=c0)
+    m = pdgb.Model.from_workload(w, precision=precision, c=c0, integrator=integrator)
     off, idx = m.family()
     rows = np.repeat(np.arange(w.n), np.diff(off))
     om, ph = workloads.grf_params(2105041507 + seed, 5 * w.dx)
@@ -64,6 +64,52 @@ def test_static_backward_matches_allocating_backward_twice():
         _same(got, ref)
         u, v = m.state()
         assert np.array_equal(u, uN) and np.array_equal(v, vN) and m.info()["step"] == w.steps
+    m.close()
+
+
+@pytest.mark.parametrize("precision", [F64, pdgb.PD_PREC_DW])
+@pytest.mark.parametrize("integrator", [pdgb.PD_INTEGRATOR_EC, pdgb.PD_INTEGRATOR_VV])
+def test_static_backward_on_every_accepted_handle(precision, integrator):
+    # double-word handles (the static sweep is the FP64 one; the allocating
+    # sweep is in double-word arithmetic, equal to ~1e-10) and velocity-Verlet
+    # handles (half kicks at both ends of the run), each called twice in a row
+    w, m, gu, gv = _model(14, 9, 3, 30, 21 + precision + integrator, precision, integrator)
+    pdgb.pd_adjoint_forward(m.h, w.steps, 6)
+    uN, vN = m.state()
+    for dv in (gv, None):
+        ref = pdgb.pd_adjoint_backward(m.h, gu, dv)
+        for _ in range(2):
+            _same(pdgb.pd_adjoint_backward_static(m.h, gu, dv), ref)
+            u, v = m.state()
+            assert np.array_equal(u, uN) and np.array_equal(v, vN)
+    m.close()
+
+
+def test_static_backward_writes_device_outputs():
+    # every input and output a device pointer: dL/dc is then written in place by
+    # the scatter to canonical order, without the host staging copy
+    import ctypes
+    import torch
+    w, m, gu, gv = _model(15, 9, 3, 25, 31)
+    pdgb.pd_adjoint_forward(m.h, w.steps, 5)
+    ref = pdgb.pd_adjoint_backward(m.h, gu, gv)
+    info = m.info()
+    n, nb = info["n"], info["n_bonds"]
+    dev = torch.device("cuda", 0)
+    du = torch.from_numpy(np.ascontiguousarray(gu)).to(dev)
+    dv = torch.from_numpy(np.ascontiguousarray(gv)).to(dev)
+    for _ in range(2):
+        gc = torch.full((nb,), float("nan"), dtype=torch.float64, device=dev)
+        g0 = torch.full((n, 3), float("nan"), dtype=torch.float64, device=dev)
+        g1 = torch.full((n, 3), float("nan"), dtype=torch.float64, device=dev)
+        gl = ctypes.c_double()
+        torch.cuda.synchronize()
+        st = pdgb.lib().pd_adjoint_backward_static(m.h, du.data_ptr(), dv.data_ptr(),
+                                                   gc.data_ptr(), ctypes.byref(gl),
+                                                   g0.data_ptr(), g1.data_ptr())
+        assert st == 0, pdgb.lib().pd_last_error()
+        torch.cuda.synchronize()
+        _same((gc.cpu().numpy(), gl.value, g0.cpu().numpy(), g1.cpu().numpy()), ref)
     m.close()
 
 
