@@ -175,7 +175,16 @@ typedef struct {
     int32_t precision;
     int32_t ell_width;    /* padded family width used on the device (multiple of 32) */
     int64_t device_bytes; /* device memory held by the handle */
+    int32_t layout;       /* PD_LAYOUT_SELL, or PD_LAYOUT_LATTICE: an FP32 Euler-Cromer
+                             PMB model with uniform volumes whose nodes fill a cubic
+                             lattice box and whose family is the 122-offset stencil
+                             (3 dx <= delta < sqrt(10) dx) minus cuts; its steps run
+                             the lattice stencil kernel (no neighbour ids read)
+                             unless per-bond stiffness is set */
+    int32_t pad0;
 } pd_info_t;
+#define PD_LAYOUT_SELL 0
+#define PD_LAYOUT_LATTICE 1
 
 /*
  * pd_micromodulus - c = 18 K / (pi delta^4) (Eq. 5, Section 2.2).

@@ -27,6 +27,7 @@ __all__ = [
     "pd_batch_offsets", "pd_autotune", "pd_adjoint_forward", "pd_adjoint_backward",
     "pd_adjoint_backward_static", "pd_stiffness_factors", "pd_get_bond_integrity", "PD_STIFF_CONICAL",
     "PD_STIFF_SURFACE", "PD_STIFF_PARTIAL", "PD_INTEGRATOR_EC", "PD_INTEGRATOR_VV",
+    "PD_LAYOUT_SELL", "PD_LAYOUT_LATTICE",
     "instance_from_workload", "Model",
     "PD_PREC_F32", "PD_PREC_F64", "PD_PREC_DW", "PD_DIM_3D", "PD_PLANE_STRESS", "PD_PLANE_STRAIN",
 ]
@@ -40,6 +41,8 @@ PD_STIFF_PARTIAL = 4
 PD_PLANE_STRESS = 1  # pd_critical_stretch body kinds (Eq. 7)
 PD_PLANE_STRAIN = 2
 PD_DIM_3D = 3
+PD_LAYOUT_SELL = 0      # pd_get_info()["layout"]: sliced ELL, the general step kernel
+PD_LAYOUT_LATTICE = 1   # regular lattice: the stencil kernel (no neighbour ids read)
 PD_INTEGRATOR_EC = 0
 PD_INTEGRATOR_VV = 1
 _STATUS = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_CUDA", 3: "PD_ERR_OOM",
@@ -88,7 +91,8 @@ class _Instance(ctypes.Structure):
 class _Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("n_bonds", ctypes.c_int64), ("step", ctypes.c_int64),
                 ("precision", ctypes.c_int32), ("ell_width", ctypes.c_int32),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("layout", ctypes.c_int32),
+                ("pad0", ctypes.c_int32)]
 
 
 _lib = None

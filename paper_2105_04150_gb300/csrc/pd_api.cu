@@ -175,6 +175,11 @@ struct pd_handle {
         float4 *rrec = nullptr, *wrec = nullptr;
         float2* gcdw = nullptr;
     } tape;
+    // regular lattice (FP32 Euler-Cromer PMB models): stencil-ordered layout,
+    // node records with a halo of lat_halo records on both sides
+    bool lattice = false;
+    Lattice lat;
+    int64_t lat_halo = 0;
     // batches: instance of each node, instance-local ids, per-instance s_c table
     bool batch = false;
     std::vector<int64_t> inst_off;
@@ -273,6 +278,21 @@ StepArgsF32 args_f32(pd_handle* h, int k)
     a.vv = h->integrator == PD_INTEGRATOR_VV ? 1 : 0;
     a.delta = h->delta;
     a.inv_delta = 1.0 / h->delta;
+    if (h->lattice) {
+        a.lat_sy = (int32_t)h->lat.N[2];
+        a.lat_sx = (int32_t)(h->lat.N[1] * h->lat.N[2]);
+        const double kap = h->lat.dx / h->delta;
+        const double f = (1.0 - 2.0 * kGuard) * h->sc_lo;
+        for (int c = -3; c <= 3; ++c) {
+            a.lat_xi[c + 3] = (float)(kap * c);
+            a.lat_xi2[c + 3] = 2.0f * a.lat_xi[c + 3];
+        }
+        for (int q = 0; q <= kStencilR2; ++q) {
+            a.lat_q[q] = (float)(kap * kap * q);
+            a.lat_l[q] = (float)(kap * std::sqrt((double)q));
+            a.lat_thr[q] = (float)(f * (2.0 + f) * kap * kap * q);
+        }
+    }
     return a;
 }
 
@@ -320,9 +340,19 @@ StepArgsF64 args_f64(pd_handle* h, int k)
     return a;
 }
 
+// the regular-lattice stencil kernel serves Euler-Cromer PMB steps with a linear
+// loading ramp and uniform weights (the general kernel everything else, on the
+// same stencil-ordered layout)
+bool use_lat(const pd_handle* h, const StepArgsF32& a)
+{
+    return h->lattice && !h->per_bond_c && h->integ == nullptr && !a.vv && a.ramp_steps == 0 &&
+           !a.peek && h->uniform_vol;
+}
+
 // the FP32 step kernel build for this handle (bilinear softening or not)
 cudaError_t launch_f32(pd_handle* h, const StepArgsF32& a)
 {
+    if (use_lat(h, a)) return launch_step_f32_lat(a, h->sc_mode, h->grid, h->block, h->stream);
     if (h->integ != nullptr) return launch_step_f32_soft(a, h->sc_mode, h->grid, h->block, h->stream);
     if (a.vv || a.ramp_steps > 0 || a.peek)
         return launch_step_f32_ext(a, h->sc_mode, h->grid, h->block, h->stream);
@@ -331,6 +361,9 @@ cudaError_t launch_f32(pd_handle* h, const StepArgsF32& a)
 
 const void* f32_kernel(pd_handle* h)
 {
+    if (h->lattice && !h->per_bond_c && h->integ == nullptr &&
+        h->integrator == PD_INTEGRATOR_EC && h->ramp_steps == 0 && h->uniform_vol)
+        return step_f32_kernel_lat(h->sc_mode);
     return h->integ != nullptr ? step_f32_kernel_soft(h->sc_mode, h->uniform_vol, h->per_bond_c)
                                : step_f32_kernel(h->sc_mode, h->uniform_vol, h->per_bond_c);
 }
@@ -712,10 +745,23 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
     std::string msg = bc_classes(n, d.type, d.disp, d.force, d.no_fail, table, cls, h->has_nofail);
     if (!msg.empty()) return fail(PD_ERR_ARG, "%s", msg.c_str());
 
-    spatial_order(n, d.coords, d.horizon, cfg->reorder, h->perm, h->inv);
+    // FP32 Euler-Cromer PMB models on a regular lattice (the stencil kernel's
+    // case): lattice node order and the stencil-ordered layout
+    h->lattice = cfg->precision == PD_PREC_F32 && h->model == 0 && h->kr < 1.0 &&
+                 h->integrator == PD_INTEGRATOR_EC && h->ramp_steps == 0 && d.inst.empty() &&
+                 cfg->reorder == 0 && h->uniform_vol &&
+                 detect_lattice(n, d.coords, h->off, h->idx, h->lat, h->perm, h->inv);
     std::vector<int32_t> nbr, sw;
     std::vector<uint32_t> bits;
-    build_layout(n, h->off, h->idx, h->perm, h->inv, h->Q, nbr, bits, sw, h->cnt);
+    if (h->lattice) {
+        h->Q = (kStencil + 31) / 32;
+        build_layout_stencil(n, h->off, h->idx, h->perm, h->inv, h->lat, nbr, bits, sw, h->cnt);
+        const int64_t sy = h->lat.N[2], sx = h->lat.N[1] * h->lat.N[2];
+        h->lat_halo = 3 * sx + 3 * sy + 3;
+    } else {
+        spatial_order(n, d.coords, d.horizon, cfg->reorder, h->perm, h->inv);
+        build_layout(n, h->off, h->idx, h->perm, h->inv, h->Q, nbr, bits, sw, h->cnt);
+    }
 
     // ---- device
     cudaError_t e = cudaSetDevice(h->device);
@@ -735,8 +781,12 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc " #ptr); \
     } while (0)
     if (f32) {
-        ALLOC(h->rec32[0], float4, 2 * np);
-        ALLOC(h->rec32[1], float4, 2 * np);
+        // records with a zero halo (lattice: the stencil's wrapped reads stay in bounds)
+        const int64_t H = h->lat_halo;
+        for (int k = 0; k < 2; ++k) {
+            ALLOC(h->rec32[k], float4, 2 * (np + 2 * H));
+            h->rec32[k] += 2 * H;
+        }
         ALLOC(h->lo32, float4, np);
         ALLOC(h->w32, float, np);
         ALLOC(h->v, float, 3 * np);
@@ -1161,6 +1211,8 @@ pd_status pd_get_info(pd_handle* h, pd_info_t* out)
     out->precision = h->dw ? PD_PREC_DW : h->precision;
     out->ell_width = 32 * h->Q;
     out->device_bytes = h->device_bytes;
+    out->layout = h->lattice ? PD_LAYOUT_LATTICE : PD_LAYOUT_SELL;
+    out->pad0 = 0;
     return PD_OK;
 }
 
@@ -1337,8 +1389,10 @@ pd_status pd_get_bonds(pd_handle* h, uint8_t* mu)
     const int64_t W = 32LL * h->Q;
     for (int64_t p = 0; p < h->n; ++p) {
         const int64_t g = p / 32, l = p % 32;
-        for (int64_t m = 0; m < h->cnt[p]; ++m)
-            mu[pos[(g * W + m) * 32 + l]] = (bits[(g * h->Q + (m >> 5)) * 32 + l] >> (m & 31)) & 1u;
+        for (int64_t m = 0; m < W; ++m) {
+            const int64_t k = pos[(g * W + m) * 32 + l];
+            if (k >= 0) mu[k] = (bits[(g * h->Q + (m >> 5)) * 32 + l] >> (m & 31)) & 1u;
+        }
     }
     return PD_OK;
 }
@@ -1369,8 +1423,9 @@ pd_status pd_get_bond_integrity(pd_handle* h, double* mu)
     }
     for (int64_t p = 0; p < h->n; ++p) {
         const int64_t g = p / 32, l = p % 32;
-        for (int64_t m = 0; m < h->cnt[p]; ++m) {
+        for (int64_t m = 0; m < W; ++m) {
             const int64_t slot = (g * W + m) * 32 + l;
+            if (pos[(size_t)slot] < 0) continue;
             const bool intact = (bits[(g * h->Q + (m >> 5)) * 32 + l] >> (m & 31)) & 1u;
             double v = intact ? 1.0 : 0.0;
             if (intact && h->integ)
@@ -1395,8 +1450,10 @@ pd_status pd_set_bonds(pd_handle* h, const uint8_t* mu)
     std::vector<uint32_t> bits((size_t)(h->n_slices * h->Q * 32), 0u);
     for (int64_t p = 0; p < h->n; ++p) {
         const int64_t g = p / 32, l = p % 32;
-        for (int64_t m = 0; m < h->cnt[p]; ++m)
-            if (mu[pos[(g * W + m) * 32 + l]]) bits[(g * h->Q + (m >> 5)) * 32 + l] |= 1u << (m & 31);
+        for (int64_t m = 0; m < W; ++m) {
+            const int64_t k = pos[(g * W + m) * 32 + l];
+            if (k >= 0 && mu[k]) bits[(g * h->Q + (m >> 5)) * 32 + l] |= 1u << (m & 31);
+        }
     }
     PD_CUDA(cudaMemcpyAsync(h->bits, bits.data(), bits.size() * 4, cudaMemcpyHostToDevice, h->stream),
             "upload bond flags");
@@ -1407,7 +1464,7 @@ pd_status pd_set_bonds(pd_handle* h, const uint8_t* mu)
         if (h->precision == 32) m32.assign(ns, 0.0f); else m64.assign(ns, 0.0);
         for (int64_t p = 0; p < h->n; ++p) {
             const int64_t g = p / 32, l = p % 32;
-            for (int64_t m = 0; m < h->cnt[p]; ++m)
+            for (int64_t m = 0; m < W; ++m)
                 if ((bits[(g * h->Q + (m >> 5)) * 32 + l] >> (m & 31)) & 1u) {
                     const size_t slot = (size_t)((g * W + m) * 32 + l);
                     if (h->precision == 32) m32[slot] = 1.0f; else m64[slot] = 1.0;
@@ -1452,7 +1509,11 @@ pd_status pd_remove_bonds(pd_handle* h, const int64_t* pairs, int64_t m)
                             (long long)e, (long long)a, (long long)b);
             const int32_t pb = h->inv[(size_t)b];
             int64_t mm = 0;
-            for (const int32_t* q = lo; q < hi; ++q) mm += h->inv[(size_t)*q] < pb ? 1 : 0;
+            if (h->lattice) {  // stencil-ordered layout: the slot of the lattice offset
+                mm = stencil_slot(h->lat, h->inv[(size_t)a], pb);
+            } else {
+                for (const int32_t* q = lo; q < hi; ++q) mm += h->inv[(size_t)*q] < pb ? 1 : 0;
+            }
             const int64_t p = h->inv[(size_t)a], g = p / 32, l = p % 32;
             word.push_back((g * h->Q + (mm >> 5)) * 32 + l);
             mask.push_back(1u << (mm & 31));

@@ -57,6 +57,32 @@ struct InstParams {
     uint64_t sc_seed;
 };
 
+// Regular-lattice stencil.  On a cubic lattice of spacing dx with
+// 3 dx <= delta < sqrt(10) dx, the family of Eq. 9 of an interior node is the
+// set of the 122 integer offsets o with 0 < |o|^2 <= 9 (in units of dx); a
+// node near a face or a cut has a subset of them.  Slot m of such a model's
+// layout holds offset m of this list, ordered lexicographically by
+// (o_x, o_y, o_z), so offsets with the same (o_x, o_y) (a "row") are
+// consecutive and differ by one node along z.
+constexpr int kStencil = 122;
+constexpr int kStencilR2 = 9;
+struct Off3 {
+    int x, y, z, q;  // q = |o|^2
+};
+__host__ __device__ constexpr Off3 stencil_offset(int m)
+{
+    int k = 0;
+    for (int a = -3; a <= 3; ++a)
+        for (int b = -3; b <= 3; ++b)
+            for (int c = -3; c <= 3; ++c) {
+                const int q = a * a + b * b + c * c;
+                if (q == 0 || q > kStencilR2) continue;
+                if (k == m) return Off3{a, b, c, q};
+                ++k;
+            }
+    return Off3{0, 0, 0, 0};
+}
+
 struct StepArgsF32 {
     const int32_t* inst;       // batch: instance of each node, or nullptr
     const InstParams* itab;    // batch: per-instance s_c parameters
@@ -98,6 +124,14 @@ struct StepArgsF32 {
     float* integ;              // bilinear softening: per-slot integrity mu, or nullptr
     double kr;                 // s_0 = s_c / kr
     double k1, beta;           // trilinear: kink at s_1 = k1 s_0 with force beta c s_0 (k1 > 1)
+    // regular-lattice stencil kernel (pd_step_f32_lat.cu); node p = (ix Ny + iy) Nz + iz
+    int32_t lat_sx, lat_sy;    // node-order strides of x and y (z: 1)
+    float lat_xi[7];           // kappa c for c = -3..3 (kappa = dx / delta: xi in horizon units)
+    float lat_xi2[7];          // 2 kappa c
+    float lat_q[kStencilR2 + 1];    // |xi|^2 = kappa^2 q for q = |o|^2
+    float lat_l[kStencilR2 + 1];    // |xi| = kappa sqrt(q)
+    float lat_thr[kStencilR2 + 1];  // num threshold of the near-s_c band: s >= fast_lo
+                                    // <=> num >= fast_lo (2 + fast_lo) |xi|^2
 };
 
 struct StepArgsF64 {
@@ -277,6 +311,11 @@ const void* step_f32_kernel(int sc_mode, bool uniform_w, bool per_bond_c);
 cudaError_t launch_step_f32_ext(const StepArgsF32& a, int sc_mode, int grid, int block,
                                 cudaStream_t s);
 const void* step_f32_kernel_ext(int sc_mode, bool uniform_w, bool per_bond_c);
+// regular-lattice stencil build of the FP32 Euler-Cromer step (pd_step_f32_lat.cu):
+// node records with a halo of lat_halo records on both sides
+cudaError_t launch_step_f32_lat(const StepArgsF32& a, int sc_mode, int grid, int block,
+                                cudaStream_t s);
+const void* step_f32_kernel_lat(int sc_mode);
 // bilinear-softening build of the FP32 step kernel (pd_step_f32_soft.cu)
 cudaError_t launch_step_f32_soft(const StepArgsF32& a, int sc_mode, int grid, int block,
                                  cudaStream_t s);

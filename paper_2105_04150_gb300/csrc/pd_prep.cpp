@@ -227,6 +227,136 @@ void build_layout(int64_t n, const std::vector<int64_t>& off, const std::vector<
     }
 }
 
+bool detect_lattice(int64_t n, const double* x, const std::vector<int64_t>& off,
+                    const std::vector<int32_t>& idx, Lattice& L, std::vector<int32_t>& perm,
+                    std::vector<int32_t>& inv)
+{
+    if (n < 2 || idx.empty()) return false;
+    // spacing: the shortest bond
+    double d2min = HUGE_VAL;
+#pragma omp parallel for reduction(min : d2min) schedule(static)
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = off[i]; k < off[i + 1]; ++k) {
+            const double* a = x + 3 * i;
+            const double* b = x + 3 * (int64_t)idx[k];
+            const double d2 = (b[0] - a[0]) * (b[0] - a[0]) + (b[1] - a[1]) * (b[1] - a[1]) +
+                              (b[2] - a[2]) * (b[2] - a[2]);
+            d2min = std::min(d2min, d2);
+        }
+    if (!(d2min > 0.0) || !std::isfinite(d2min)) return false;
+    const double dx = std::sqrt(d2min);
+    double lo[3];
+    for (int a = 0; a < 3; ++a) lo[a] = x[a];
+    for (int64_t i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) lo[a] = std::min(lo[a], x[3 * i + a]);
+    // integer lattice coordinates, exact to 1e-9 dx
+    std::vector<int64_t> ic(3 * n);
+    int64_t N[3] = {0, 0, 0};
+    const double tol = 1e-9 * dx;
+    int bad = 0;
+#pragma omp parallel for reduction(max : bad) schedule(static)
+    for (int64_t i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            const double t = (x[3 * i + a] - lo[a]) / dx;
+            const double r = std::nearbyint(t);
+            const bool off_site = !(std::fabs(x[3 * i + a] - (lo[a] + r * dx)) <= tol) || r > 2.0e9;
+            if (off_site) bad = 1;
+            ic[3 * i + a] = off_site ? 0 : (int64_t)r;
+        }
+    if (bad) return false;
+    for (int64_t i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) N[a] = std::max(N[a], ic[3 * i + a] + 1);
+    if (N[0] * N[1] * N[2] != n) return false;
+    perm.assign(n, -1);
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t p = (ic[3 * i] * N[1] + ic[3 * i + 1]) * N[2] + ic[3 * i + 2];
+        if (perm[p] != -1) return false;  // two nodes on one lattice site
+        perm[p] = (int32_t)i;
+    }
+    // every bond a stencil offset, the largest |o|^2 = 9
+    int qmax = 0;
+#pragma omp parallel for reduction(max : qmax) schedule(static)
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = off[i]; k < off[i + 1]; ++k) {
+            const int64_t j = idx[k];
+            int q = 0;
+            for (int a = 0; a < 3; ++a) {
+                const int64_t d = ic[3 * j + a] - ic[3 * i + a];
+                q += (d < -3 || d > 3) ? 100 : (int)(d * d);
+            }
+            qmax = std::max(qmax, q);
+        }
+    if (qmax != kStencilR2) return false;
+    inv.assign(n, 0);
+    for (int64_t p = 0; p < n; ++p) inv[perm[p]] = (int32_t)p;
+    for (int a = 0; a < 3; ++a) L.N[a] = N[a];
+    L.dx = dx;
+    return true;
+}
+
+namespace {
+// slot of each offset (o + 3 in [0, 7)^3), -1 outside the stencil
+struct StencilLut {
+    int s[343];
+    StencilLut()
+    {
+        for (int& v : s) v = -1;
+        for (int m = 0; m < kStencil; ++m) {
+            const Off3 o = stencil_offset(m);
+            s[((o.x + 3) * 7 + (o.y + 3)) * 7 + (o.z + 3)] = m;
+        }
+    }
+};
+const StencilLut& stencil_lut()
+{
+    static const StencilLut lut;
+    return lut;
+}
+}  // namespace
+
+int stencil_slot(const Lattice& L, int64_t p, int64_t q)
+{
+    const int64_t pz = p % L.N[2], py = (p / L.N[2]) % L.N[1], px = p / (L.N[2] * L.N[1]);
+    const int64_t qz = q % L.N[2], qy = (q / L.N[2]) % L.N[1], qx = q / (L.N[2] * L.N[1]);
+    const int64_t ox = qx - px, oy = qy - py, oz = qz - pz;
+    if (ox < -3 || ox > 3 || oy < -3 || oy > 3 || oz < -3 || oz > 3) return -1;
+    return stencil_lut().s[((ox + 3) * 7 + (oy + 3)) * 7 + (oz + 3)];
+}
+
+void build_layout_stencil(int64_t n, const std::vector<int64_t>& off,
+                          const std::vector<int32_t>& idx, const std::vector<int32_t>& perm,
+                          const std::vector<int32_t>& inv, const Lattice& L,
+                          std::vector<int32_t>& nbr, std::vector<uint32_t>& bits,
+                          std::vector<int32_t>& sw, std::vector<int32_t>& cnt)
+{
+    const int Q = (kStencil + 31) / 32;
+    const int64_t W = 32LL * Q;
+    const int64_t ns = (n + 31) / 32;
+    nbr.resize((size_t)(ns * W * 32));
+    bits.assign((size_t)(ns * Q * 32), 0u);
+    sw.assign((size_t)ns, 0);
+    cnt.assign((size_t)(ns * 32), 0);
+#pragma omp parallel for schedule(static)
+    for (int64_t g = 0; g < ns; ++g) {
+        int32_t width = 0;
+        for (int l = 0; l < 32; ++l) {
+            const int64_t p = g * 32 + l;
+            for (int64_t k = 0; k < W; ++k) nbr[(g * W + k) * 32 + l] = (int32_t)p;
+            if (p >= n) continue;
+            const int64_t i = perm[p];
+            for (int64_t k = off[i]; k < off[i + 1]; ++k) {
+                const int32_t q = inv[idx[k]];
+                const int m = stencil_slot(L, p, q);  // detect_lattice checked m >= 0
+                nbr[(g * W + m) * 32 + l] = q;
+                bits[(g * Q + (m >> 5)) * 32 + l] |= 1u << (m & 31);
+                width = std::max(width, m + 1);
+            }
+            cnt[p] = (int32_t)(off[i + 1] - off[i]);
+        }
+        sw[g] = width;
+    }
+}
+
 void slot_to_canonical(int64_t n, const std::vector<int64_t>& off, const std::vector<int32_t>& idx,
                        const std::vector<int32_t>& perm, const std::vector<int32_t>& nbr,
                        const std::vector<int32_t>& cnt, int Q, std::vector<int64_t>& pos)
@@ -241,8 +371,10 @@ void slot_to_canonical(int64_t n, const std::vector<int64_t>& off, const std::ve
         const int64_t i = perm[p];
         const int32_t* b = idx.data() + off[i];
         const int32_t* e = idx.data() + off[i + 1];
-        for (int64_t m = 0; m < cnt[p]; ++m) {
+        if (cnt[p] == 0) continue;
+        for (int64_t m = 0; m < W; ++m) {
             const int64_t slot = (g * W + m) * 32 + l;
+            if (nbr[slot] == (int32_t)p) continue;  // unused
             const int32_t j = perm[nbr[slot]];
             pos[slot] = off[i] + (std::lower_bound(b, e, j) - b);
         }

@@ -27,7 +27,29 @@ void build_layout(int64_t n, const std::vector<int64_t>& off, const std::vector<
                   const std::vector<int32_t>& perm, const std::vector<int32_t>& inv, int Q,
                   std::vector<int32_t>& nbr, std::vector<uint32_t>& bits,
                   std::vector<int32_t>& sw, std::vector<int32_t>& cnt);
-// Canonical CSR position of every device slot (-1 for unused slots).
+// Regular cubic lattice: every node at lo + dx (ix, iy, iz), the n nodes filling
+// an Nx x Ny x Nz box, and every bond of the family one of the stencil offsets
+// (0 < |o|^2 <= 9, some bond with |o|^2 = 9).  On success perm / inv put the
+// nodes in lattice order p = (ix Ny + iy) Nz + iz and true is returned.
+struct Lattice {
+    int64_t N[3] = {0, 0, 0};
+    double dx = 0.0;
+};
+bool detect_lattice(int64_t n, const double* x, const std::vector<int64_t>& off,
+                    const std::vector<int32_t>& idx, Lattice& L, std::vector<int32_t>& perm,
+                    std::vector<int32_t>& inv);
+// Stencil-ordered layout of a lattice model (W = 128 slots, slot m = stencil
+// offset m, kStencil used): absent members hold the node itself with flag 0.
+void build_layout_stencil(int64_t n, const std::vector<int64_t>& off,
+                          const std::vector<int32_t>& idx, const std::vector<int32_t>& perm,
+                          const std::vector<int32_t>& inv, const Lattice& L,
+                          std::vector<int32_t>& nbr, std::vector<uint32_t>& bits,
+                          std::vector<int32_t>& sw, std::vector<int32_t>& cnt);
+// Stencil slot of the bond from lattice node p to q (library positions), -1 if
+// the offset is not a stencil offset.
+int stencil_slot(const Lattice& L, int64_t p, int64_t q);
+// Canonical CSR position of every device slot (-1 for unused slots).  A slot
+// is used when its neighbour differs from the node itself.
 void slot_to_canonical(int64_t n, const std::vector<int64_t>& off, const std::vector<int32_t>& idx,
                        const std::vector<int32_t>& perm, const std::vector<int32_t>& nbr,
                        const std::vector<int32_t>& cnt, int Q, std::vector<int64_t>& pos);

@@ -82,6 +82,10 @@ constexpr bool kExt = PD_F32_EXT != 0;
 #ifndef PD_F32_OSB
 #define PD_F32_OSB 0
 #endif
+// Lattice build (pd_step_f32_lat.cu): the same, for the regular-lattice stencil kernel.
+#ifndef PD_F32_LAT
+#define PD_F32_LAT 0
+#endif
 
 // SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output m of the stream seeded
 // with `seed`.  Used as a counter-based draw of the per-bond critical stretch.
@@ -551,7 +555,7 @@ cudaError_t launch_v(const StepArgsF32& a, int grid, int block, cudaStream_t s)
 
 }  // namespace
 
-#if !PD_F32_OSB
+#if !PD_F32_OSB && !PD_F32_LAT
 #if PD_F32_SOFT
 #define PD_F32_KERNEL_OF step_f32_kernel_soft
 #define PD_F32_LAUNCH launch_step_f32_soft
@@ -577,6 +581,6 @@ cudaError_t PD_F32_LAUNCH(const StepArgsF32& a, int sc_mode, int grid, int block
         return a.uniform_w ? launch_v<0, true>(a, grid, block, s) : launch_v<0, false>(a, grid, block, s);
     return a.uniform_w ? launch_v<1, true>(a, grid, block, s) : launch_v<1, false>(a, grid, block, s);
 }
-#endif  // PD_F32_OSB
+#endif  // !PD_F32_OSB && !PD_F32_LAT
 
 }  // namespace pd

@@ -1,0 +1,162 @@
+"""The regular-lattice stencil kernel (FP32 Euler-Cromer PMB models whose nodes
+fill a cubic lattice box with delta in [3 dx, sqrt(10) dx)) through the C ABI.
+
+Which models take it, and that it matches the FP64 oracle (at the FP32 bar of
+the parity tests: u within 1e-4 relative, v within 1e-3, broken sets within
+0.1 %, damage equal to Eq. 8 of the GPU's own flags) and the general sliced-ELL
+kernel on the same model: short lattice axes where a warp's offsets wrap
+around lattice lines, ragged last slices, a notch, per-bond critical stretch
+and no-fail nodes; per-bond stiffness on a lattice handle (general kernel on
+the stencil-ordered layout); bond flags read, written and cut in stencil order.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2105_04150_gb300 as pdgb
+import workloads
+
+from test_parity_gpu import check_f32, gpu_run, oracle_run, rel
+
+pytestmark = pytest.mark.gpu
+
+F32, F64 = pdgb.PD_PREC_F32, pdgb.PD_PREC_F64
+LAT, SELL = pdgb.PD_LAYOUT_LATTICE, pdgb.PD_LAYOUT_SELL
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pdgb.build()
+    oracle.build()
+
+
+def _layout(w, precision=F32, **kw):
+    m = pdgb.Model.from_workload(w, precision=precision, **kw)
+    lay = m.info()["layout"]
+    m.close()
+    return lay
+
+
+def test_which_models_take_the_lattice_kernel():
+    w = workloads.tensile_bar(20, 7, 6, rate=1e-6, steps=10)
+    assert _layout(w) == LAT
+    assert _layout(w, precision=F64) == SELL
+    assert _layout(w, precision=pdgb.PD_PREC_DW) == SELL
+    assert _layout(w, reorder=1) == SELL
+    assert _layout(w, integrator=pdgb.PD_INTEGRATOR_VV) == SELL
+    b = workloads.notched_beam(30, 8, 9, length=0.05, rate=1e-7, steps=10)
+    assert _layout(b) == LAT                       # a notch removes bonds: still a lattice
+    j = workloads.tensile_bar(12, 6, 6, rate=1e-6, steps=10)
+    j.coords = workloads.lattice(12, 6, 6, j.dx, jitter=0.2, seed=3)
+    assert _layout(j) == SELL                      # not on a lattice
+    s = workloads.tensile_bar(12, 6, 6, rate=1e-6, steps=10)
+    s.horizon = 2.01 * s.dx
+    assert _layout(s) == SELL                      # a smaller stencil
+    s.horizon = 3.3 * s.dx
+    assert _layout(s) == SELL                      # a larger one
+    v = workloads.tensile_bar(12, 6, 6, rate=1e-6, steps=10)
+    v.volumes = v.volumes * np.linspace(0.9, 1.1, v.n)
+    assert _layout(v) == SELL                      # non-uniform volumes
+    p = workloads.tensile_bar(12, 6, 6, rate=1e-6, steps=10)
+    perm = np.random.default_rng(1).permutation(p.n)
+    p.coords = p.coords[perm]                      # any node order: the lattice order is internal
+    assert _layout(p) == LAT
+
+
+@pytest.mark.parametrize("shape", [(13, 5, 6), (9, 4, 3), (25, 11, 2), (17, 9, 8)])
+def test_short_axes_and_ragged_slices_match_oracle(shape):
+    # Nz < 7: offsets of a warp wrap across several lattice lines; n not a
+    # multiple of 32; a random start state so that every component moves
+    w = workloads.tensile_bar(*shape, rate=3e-7, slab=1, steps=80)
+    u0, v0 = workloads.random_state(w.n, 7, 1e-7, 1e-2)
+    o = oracle_run(w, w.steps, u0=u0, v0=v0)
+    g = gpu_run(w, w.steps, F32, u0=u0, v0=v0, graph_steps=8)
+    assert g["info"]["layout"] == LAT
+    check_f32(g, o)
+
+
+def test_node_order_of_the_caller_is_kept():
+    # nodes handed over in a shuffled order: results come back in that order
+    w = workloads.tensile_bar(18, 7, 6, rate=4e-7, slab=2, steps=120)
+    perm = np.random.default_rng(5).permutation(w.n)
+    for name in ("coords", "volumes", "bc_type", "bc_disp"):
+        setattr(w, name, np.ascontiguousarray(getattr(w, name)[perm]))
+    o = oracle_run(w, w.steps)
+    g = gpu_run(w, w.steps, F32)
+    assert g["info"]["layout"] == LAT
+    check_f32(g, o)
+
+
+def test_notched_beam_hashed_sc_no_fail_matches_oracle():
+    # per-bond s_c drawn from the pair of caller ids, a notch, and a no-fail strip
+    # under the load: the near-s_c decisions run through the stencil's resolver
+    w = workloads.notched_beam(40, 9, 10, length=0.07, rate=2e-7, steps=220)
+    nf = np.zeros(w.n, np.uint8)
+    top = w.coords[:, 2] > w.coords[:, 2].max() - 1.5 * w.dx
+    nf[top] = 1
+    w.no_fail = nf
+    o = oracle_run(w, w.steps)
+    assert (o["mu"] == 0).sum() > 100                   # the run breaks bonds
+    g = gpu_run(w, w.steps, F32, graph_steps=20)
+    assert g["info"]["layout"] == LAT
+    check_f32(g, o)
+
+
+def test_lattice_kernel_equals_general_kernel():
+    # the same model through both FP32 kernels (reorder = 1 takes the general
+    # one): different summation orders, the same arithmetic bar
+    w = workloads.notched_beam(36, 8, 9, length=0.06, rate=2e-7, steps=150)
+    a = gpu_run(w, w.steps, F32)
+    b = gpu_run(w, w.steps, F32, reorder=1)
+    assert a["info"]["layout"] == LAT and b["info"]["layout"] == SELL
+    assert rel(a["u"], b["u"]) <= 1e-5, rel(a["u"], b["u"])
+    assert (a["mu"] != b["mu"]).mean() < 1e-3
+
+
+def test_per_bond_stiffness_on_a_lattice_handle():
+    # per-bond c: the general kernel runs on the stencil-ordered layout
+    w = workloads.tensile_bar(16, 6, 7, rate=5e-7, steps=100)
+    c = oracle.micromodulus(w.bulk_modulus, w.horizon)
+    off, idx = oracle.cut_family(w.coords, w.horizon, w.cuts_array())
+    rows = np.repeat(np.arange(w.n), np.diff(off))
+    mid = 0.5 * (w.coords[rows] + w.coords[idx])
+    cb = c * (1.0 + 0.1 * np.sin(mid[:, 0] / w.dx) * np.cos(mid[:, 1] / w.dx))
+    o = oracle_run(w, w.steps, c=c, c_bond=cb, off_idx=(off, idx))
+    g = gpu_run(w, w.steps, F32, c=c, c_bond=cb)
+    assert g["info"]["layout"] == LAT
+    check_f32(g, o)
+
+
+def test_bond_flags_round_trip_and_cut_in_stencil_order():
+    w = workloads.tensile_bar(14, 6, 6, rate=2e-6, steps=60)
+    c = oracle.micromodulus(w.bulk_modulus, w.horizon)
+    m = pdgb.Model.from_workload(w, precision=F32, c=c)
+    assert m.info()["layout"] == LAT
+    off, idx = m.family()
+    rng = np.random.default_rng(9)
+    mu = (rng.random(len(idx)) > 0.2).astype(np.uint8)
+    rows = np.repeat(np.arange(w.n), np.diff(off))
+    key = np.minimum(rows, idx) * w.n + np.maximum(rows, idx)
+    _, inv = np.unique(key, return_inverse=True)
+    mu = mu[np.unique(key, return_index=True)[1]][inv]   # symmetric flags
+    m.set_bonds(mu)
+    assert np.array_equal(m.bonds(), mu)
+    # cut a few intact pairs: exactly those directions become 0
+    pairs = np.stack([rows, idx], 1)[(mu == 1) & (rows < idx)][:25]
+    m.remove_bonds(pairs)
+    expect = mu.copy()
+    for i, j in pairs:
+        expect[(rows == i) & (idx == j)] = 0
+        expect[(rows == j) & (idx == i)] = 0
+    assert np.array_equal(m.bonds(), expect)
+    # and a run from those flags equals the oracle's from the same flags
+    om = oracle.Model.from_workload(w, off, idx, c=c)
+    u = np.zeros((w.n, 3)); v = np.zeros((w.n, 3)); omu = expect.copy()
+    om.run(0, w.steps, u, v, omu)
+    m.step(w.steps)
+    ug, vg = m.state()
+    assert rel(ug, u) <= 1e-4 and (m.bonds() != omu).mean() < 1e-3
+    m.close()

@@ -4,7 +4,10 @@ Tolerances (written here, derived from the arithmetic):
   FP64 path   u and v within 1e-10 relative (max node error / max node value);
               broken-bond set identical except bonds the oracle saw within
               1e-9 (absolute stretch) of s_c at some step.
-  FP32 path   u within 1e-4 relative; broken-bond sets differ in < 0.1 % of bonds.
+  FP32 path   u within 1e-4 relative, v within 1e-3 (the FP64 bar's v/u ratio);
+              broken-bond sets differ in < 0.1 % of bonds; the damage equals
+              Eq. 8 of the GPU's own bond flags to 1e-5 (FP32 rounding of the
+              family weight sum, up to ~128 terms of relative error 6e-8).
 Relative error = max_i |a_i - b_i| / max_i |b_i| over all node components.
 """
 import numpy as np
@@ -43,7 +46,7 @@ def oracle_run(w, steps, c=None, c_bond=None, u0=None, v0=None, off_idx=None):
     mu = m.fresh_bonds()
     margin = np.full(m.nbonds, np.inf)
     m.run(0, steps, u, v, mu, margin)
-    return dict(u=u, v=v, mu=mu, margin=margin, phi=m.damage(mu), off=off, idx=idx)
+    return dict(u=u, v=v, mu=mu, margin=margin, phi=m.damage(mu), off=off, idx=idx, model=m)
 
 
 def gpu_run(w, steps, precision, c=None, c_bond=None, u0=None, v0=None, **kw):
@@ -71,11 +74,15 @@ def check_f64(g, o, tol=1e-10):
     assert np.abs(g["phi"] - o["phi"]).max() <= 1e-12 + 2.0 * diff.sum() / max(len(diff), 1)
 
 
-def check_f32(g, o, tol=1e-4):
+def check_f32(g, o, tol=1e-4, vtol=1e-3):
     assert np.array_equal(g["fam"][0], o["off"]) and np.array_equal(g["fam"][1], o["idx"])
     assert rel(g["u"], o["u"]) <= tol, rel(g["u"], o["u"])
+    assert rel(g["v"], o["v"]) <= vtol, rel(g["v"], o["v"])
     frac = (g["mu"] != o["mu"]).mean() if len(o["mu"]) else 0.0
     assert frac < 1e-3, frac
+    # damage: Eq. 8 of the GPU's own flags (the flags themselves are checked above)
+    phi_own = o["model"].damage(np.ascontiguousarray(g["mu"], dtype=np.uint8))
+    assert np.abs(g["phi"] - phi_own).max() <= 1e-5, np.abs(g["phi"] - phi_own).max()
 
 
 # ------------------------------------------------------------------ tensile bar

@@ -125,10 +125,12 @@ def test_softening_fp64_notched_beam_per_bond_sc(precision):
 
 @pytest.mark.parametrize("precision", [F64, F32, DW])
 def test_kr_one_equals_pmb_bitwise(precision):
+    # reorder = 1 keeps the FP32 PMB model on the general step kernel (the one
+    # the softening build extends) instead of the regular-lattice stencil kernel
     w = _bar(0.0)
-    a = pdgb.Model.from_workload(w, precision=precision)
+    a = pdgb.Model.from_workload(w, precision=precision, reorder=1)
     w.kr = 1.0
-    b = pdgb.Model.from_workload(w, precision=precision)
+    b = pdgb.Model.from_workload(w, precision=precision, reorder=1)
     for m in (a, b):
         m.step(w.steps)
     ua, va = a.state()
