@@ -49,11 +49,13 @@ typedef enum {
 } pd_status;
 
 #define PD_PREC_F64 64   /* FP64 throughout */
-#define PD_PREC_F32 32   /* FP32 bond arithmetic; each node's displacement accumulated
-                            as a float-float pair (48-bit significand, exact
-                            two-sum updates; neighbours read the high word and a
-                            bf16 rounding of the low word); an FP64 re-test of
-                            bonds whose stretch is near s_c */
+#define PD_PREC_F32 32   /* FP32 bond arithmetic; an FP64 re-test of bonds whose
+                            stretch is near s_c.  Each node's displacement is
+                            accumulated in FP64 on lattice models (layout
+                            PD_LAYOUT_LATTICE; the bond arithmetic reads it rounded
+                            to FP32), else as a float-float pair (48-bit
+                            significand, exact two-sum updates; neighbours read the
+                            high word and a bf16 rounding of the low word) */
 #define PD_PREC_DW 48    /* FP64-grade step from FP32 double-word arithmetic: node
                             state (u, v) and integration in FP64 exactly as with
                             PD_PREC_F64; every bond quantity (xi, eta, y, the
@@ -176,11 +178,13 @@ typedef struct {
     int32_t ell_width;    /* padded family width used on the device (multiple of 32) */
     int64_t device_bytes; /* device memory held by the handle */
     int32_t layout;       /* PD_LAYOUT_SELL, or PD_LAYOUT_LATTICE: an FP32 Euler-Cromer
-                             PMB model with uniform volumes whose nodes fill a cubic
-                             lattice box and whose family is the 122-offset stencil
-                             (3 dx <= delta < sqrt(10) dx) minus cuts; its steps run
-                             the lattice stencil kernel (no neighbour ids read)
-                             unless per-bond stiffness is set */
+                             PMB model with uniform volumes, a linear loading ramp and
+                             the caller's node order allowed (reorder 0), whose nodes
+                             fill a cubic lattice box and whose family is the
+                             122-offset stencil (3 dx <= delta < sqrt(10) dx) minus
+                             cuts; its steps run the lattice stencil kernel (no
+                             neighbour ids read; u accumulated in FP64, published to
+                             the bond arithmetic rounded to FP32) */
     int32_t pad0;
 } pd_info_t;
 #define PD_LAYOUT_SELL 0

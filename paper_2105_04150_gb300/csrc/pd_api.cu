@@ -176,10 +176,13 @@ struct pd_handle {
         float2* gcdw = nullptr;
     } tape;
     // regular lattice (FP32 Euler-Cromer PMB models): stencil-ordered layout,
-    // node records with a halo of lat_halo records on both sides
+    // FP64 displacement and FP32 published records with a halo of lat_halo
+    // records on both sides (no rec32 / lo32)
     bool lattice = false;
     Lattice lat;
     int64_t lat_halo = 0;
+    double* lat_u[2] = {nullptr, nullptr};   // u / delta, FP64, 3 per node
+    float4* lat_pub[2] = {nullptr, nullptr}; // FP32 copies the neighbours read
     // batches: instance of each node, instance-local ids, per-instance s_c table
     bool batch = false;
     std::vector<int64_t> inst_off;
@@ -278,7 +281,15 @@ StepArgsF32 args_f32(pd_handle* h, int k)
     a.vv = h->integrator == PD_INTEGRATOR_VV ? 1 : 0;
     a.delta = h->delta;
     a.inv_delta = 1.0 / h->delta;
+    a.dt_f = (float)h->dt;
+    a.eta_f = (float)h->eta;
+    a.rho_f = (float)h->rho;
+    a.dtd_f = (float)(a.dt * a.inv_delta);
     if (h->lattice) {
+        a.lat_u[0] = h->lat_u[0];
+        a.lat_u[1] = h->lat_u[1];
+        a.lat_pub[0] = h->lat_pub[0];
+        a.lat_pub[1] = h->lat_pub[1];
         a.lat_sy = (int32_t)h->lat.N[2];
         a.lat_sx = (int32_t)(h->lat.N[1] * h->lat.N[2]);
         const double kap = h->lat.dx / h->delta;
@@ -340,19 +351,12 @@ StepArgsF64 args_f64(pd_handle* h, int k)
     return a;
 }
 
-// the regular-lattice stencil kernel serves Euler-Cromer PMB steps with a linear
-// loading ramp and uniform weights (the general kernel everything else, on the
-// same stencil-ordered layout)
-bool use_lat(const pd_handle* h, const StepArgsF32& a)
-{
-    return h->lattice && !h->per_bond_c && h->integ == nullptr && !a.vv && a.ramp_steps == 0 &&
-           !a.peek && h->uniform_vol;
-}
-
 // the FP32 step kernel build for this handle (bilinear softening or not)
 cudaError_t launch_f32(pd_handle* h, const StepArgsF32& a)
 {
-    if (use_lat(h, a)) return launch_step_f32_lat(a, h->sc_mode, h->grid, h->block, h->stream);
+    // a regular-lattice model (created only for the Euler-Cromer PMB step with a
+    // linear loading ramp and uniform volumes) has the stencil kernel's state
+    if (h->lattice) return launch_step_f32_lat(a, h->sc_mode, h->grid, h->block, h->stream);
     if (h->integ != nullptr) return launch_step_f32_soft(a, h->sc_mode, h->grid, h->block, h->stream);
     if (a.vv || a.ramp_steps > 0 || a.peek)
         return launch_step_f32_ext(a, h->sc_mode, h->grid, h->block, h->stream);
@@ -361,9 +365,7 @@ cudaError_t launch_f32(pd_handle* h, const StepArgsF32& a)
 
 const void* f32_kernel(pd_handle* h)
 {
-    if (h->lattice && !h->per_bond_c && h->integ == nullptr &&
-        h->integrator == PD_INTEGRATOR_EC && h->ramp_steps == 0 && h->uniform_vol)
-        return step_f32_kernel_lat(h->sc_mode);
+    if (h->lattice) return step_f32_kernel_lat(h->sc_mode, h->per_bond_c);
     return h->integ != nullptr ? step_f32_kernel_soft(h->sc_mode, h->uniform_vol, h->per_bond_c)
                                : step_f32_kernel(h->sc_mode, h->uniform_vol, h->per_bond_c);
 }
@@ -757,7 +759,8 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
         h->Q = (kStencil + 31) / 32;
         build_layout_stencil(n, h->off, h->idx, h->perm, h->inv, h->lat, nbr, bits, sw, h->cnt);
         const int64_t sy = h->lat.N[2], sx = h->lat.N[1] * h->lat.N[2];
-        h->lat_halo = 3 * sx + 3 * sy + 3;
+        // the stencil's reach, and one slice more: a warp walks two slices
+        h->lat_halo = 3 * sx + 3 * sy + 3 + 32;
     } else {
         spatial_order(n, d.coords, d.horizon, cfg->reorder, h->perm, h->inv);
         build_layout(n, h->off, h->idx, h->perm, h->inv, h->Q, nbr, bits, sw, h->cnt);
@@ -780,14 +783,21 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
         e = h->alloc((type**)&(ptr), (size_t)(count));               \
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc " #ptr); \
     } while (0)
-    if (f32) {
-        // records with a zero halo (lattice: the stencil's wrapped reads stay in bounds)
+    if (f32 && h->lattice) {
+        // published records with a zero halo: the stencil's wrapped reads stay in bounds
         const int64_t H = h->lat_halo;
         for (int k = 0; k < 2; ++k) {
-            ALLOC(h->rec32[k], float4, 2 * (np + 2 * H));
-            h->rec32[k] += 2 * H;
+            ALLOC(h->lat_pub[k], float4, np + 2 * H);
+            h->lat_pub[k] += H;
+            ALLOC(h->lat_u[k], double, 3 * np);
         }
-        ALLOC(h->lo32, float4, np);
+    }
+    if (f32) {
+        if (!h->lattice) {
+            ALLOC(h->rec32[0], float4, 2 * np);
+            ALLOC(h->rec32[1], float4, 2 * np);
+            ALLOC(h->lo32, float4, np);
+        }
         ALLOC(h->w32, float, np);
         ALLOC(h->v, float, 3 * np);
         ALLOC(h->wsum_inv, float, np);
@@ -913,7 +923,7 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
     pd_status st;
     std::vector<float4> r32;
     std::vector<double> r64;
-    if (f32) {
+    if (f32 && !h->lattice) {  // (lattice: the state starts at zero, as allocated)
         r32.assign(2 * np, make_float4(0.f, 0.f, 0.f, 0.f));
         for (int64_t p = 0; p < n; ++p)
             r32[2 * p] = make_float4((float)((xs[3 * p] - cs[3 * p]) / d.unit),
@@ -922,7 +932,7 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
         if ((st = up(h->rec32[0], r32.data(), 32 * np, "upload records")) ||
             (st = up(h->rec32[1], r32.data(), 32 * np, "upload records")))
             return st;
-    } else {
+    } else if (!f32) {
         r64.assign(8 * np, 0.0);
         for (int64_t p = 0; p < n; ++p)
             for (int a = 0; a < 3; ++a) r64[8 * p + a] = xs[3 * p + a];
@@ -1295,7 +1305,11 @@ pd_status pd_get_state(pd_handle* h, double* u, double* v, int64_t* step)
         double* dst = dev ? o : h->staging;
         double* uo = w == 0 ? dst : nullptr;
         double* vo = w == 1 ? dst : nullptr;
-        if (h->precision == 32)
+        if (h->lattice)
+            PD_CUDA(launch_get_state_lat(h->lat_u[cur], (const float*)vsrc, h->gid, h->n,
+                                         h->delta, uo, vo, h->stream),
+                    "get state");
+        else if (h->precision == 32)
             PD_CUDA(launch_get_state_f32(h->rec32[cur], h->lo32, (const float*)vsrc, h->gid,
                                          h->n, h->delta, uo, vo, h->stream),
                     "get state");
@@ -1347,7 +1361,11 @@ pd_status pd_set_state(pd_handle* h, const double* u, const double* v, int64_t s
     }
     const int cur = (int)(h->step & 1);
     if (src[0] || src[1]) {
-        if (h->precision == 32)
+        if (h->lattice)
+            PD_CUDA(launch_set_state_lat(src[0], src[1], h->gid, h->n, 1.0 / h->delta,
+                                         h->lat_u[cur], h->lat_pub[cur], (float*)h->v, h->stream),
+                    "set state");
+        else if (h->precision == 32)
             PD_CUDA(launch_set_state_f32(src[0], src[1], h->gid, h->n, 1.0 / h->delta,
                                          h->rec32[cur], h->lo32, (float*)h->v, h->stream),
                     "set state");
@@ -1879,7 +1897,14 @@ pd_status pd_autotune(pd_handle* h, int32_t trial_steps, int32_t* block_threads,
     };
     const int64_t np = h->n_pad;
     std::vector<Buf> bufs;
-    if (h->precision == 32) {
+    if (h->lattice) {
+        for (int k = 0; k < 2; ++k) {
+            bufs.push_back({h->lat_u[k], (size_t)(24 * np), {}});
+            bufs.push_back({h->lat_pub[k], (size_t)(16 * np), {}});
+        }
+        bufs.push_back({h->v, (size_t)(12 * np), {}});
+        bufs.push_back({h->damage, (size_t)(4 * np), {}});
+    } else if (h->precision == 32) {
         bufs.push_back({h->rec32[0], (size_t)(32 * np), {}});
         bufs.push_back({h->rec32[1], (size_t)(32 * np), {}});
         bufs.push_back({h->lo32, (size_t)(16 * np), {}});

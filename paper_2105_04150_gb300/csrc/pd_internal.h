@@ -132,6 +132,12 @@ struct StepArgsF32 {
     float lat_l[kStencilR2 + 1];    // |xi| = kappa sqrt(q)
     float lat_thr[kStencilR2 + 1];  // num threshold of the near-s_c band: s >= fast_lo
                                     // <=> num >= fast_lo (2 + fast_lo) |xi|^2
+    float dt_f, eta_f, rho_f;  // dt, eta, rho rounded to FP32 once, on the host
+    float dtd_f;               // dt / delta (velocity to displacement in horizon units)
+    // regular-lattice models keep their state differently (no rec / lo32):
+    double* lat_u[2];          // u / delta in FP64, 3 per node, double buffered
+    const float4* lat_pub[2];  // {u_x, u_y, u_z} / delta rounded to FP32, what the
+                               // neighbours read (16 B per node, zero halo), double buffered
 };
 
 struct StepArgsF64 {
@@ -312,10 +318,10 @@ cudaError_t launch_step_f32_ext(const StepArgsF32& a, int sc_mode, int grid, int
                                 cudaStream_t s);
 const void* step_f32_kernel_ext(int sc_mode, bool uniform_w, bool per_bond_c);
 // regular-lattice stencil build of the FP32 Euler-Cromer step (pd_step_f32_lat.cu):
-// node records with a halo of lat_halo records on both sides
+// published records with a zero halo on both sides
 cudaError_t launch_step_f32_lat(const StepArgsF32& a, int sc_mode, int grid, int block,
                                 cudaStream_t s);
-const void* step_f32_kernel_lat(int sc_mode);
+const void* step_f32_kernel_lat(int sc_mode, bool per_bond_c);
 // bilinear-softening build of the FP32 step kernel (pd_step_f32_soft.cu)
 cudaError_t launch_step_f32_soft(const StepArgsF32& a, int sc_mode, int grid, int block,
                                  cudaStream_t s);
@@ -341,6 +347,13 @@ cudaError_t launch_get_state_f32(const float4* rec, const float4* lo32, const fl
                                  double* v_out, cudaStream_t s);
 cudaError_t launch_set_state_f32(const double* u_in, const double* v_in, const int32_t* gid,
                                  int64_t n, double inv_delta, float4* rec, float4* lo32,
+                                 float* v32, cudaStream_t s);
+// regular-lattice FP32 models: FP64 displacement (horizon units) and FP32 velocity
+cudaError_t launch_get_state_lat(const double* u_lat, const float* v32, const int32_t* gid,
+                                 int64_t n, double delta, double* u_out, double* v_out,
+                                 cudaStream_t s);
+cudaError_t launch_set_state_lat(const double* u_in, const double* v_in, const int32_t* gid,
+                                 int64_t n, double inv_delta, double* u_lat, float4* pub,
                                  float* v32, cudaStream_t s);
 cudaError_t launch_get_state_f64(const double* rec64, const double* v64, const int32_t* gid,
                                  int64_t n, double* u_out, double* v_out, cudaStream_t s);

@@ -1,6 +1,6 @@
 // FP32-bulk step of a model on a regular cubic lattice: the stencil kernel.
 //
-// The same fused step as k_step_f32 (Eqs. 4-6, 10-11, damped Euler-Cromer,
+// The fused step of k_step_f32 (Eqs. 4-6, 10-11, damped Euler-Cromer,
 // displacement BCs, damage of Eq. 8) for the common case of the paper's
 // benchmark bodies: nodes on a cubic lattice of spacing dx with
 // 3 dx <= delta < sqrt(10) dx, so that every family is a subset of the 122
@@ -8,7 +8,7 @@
 // order p = (ix Ny + iy) Nz + iz with slot m of every node's flags holding
 // stencil offset m.  The neighbour across offset o is then node p + o_x Sx +
 // o_y Sy + o_z, and the reference bond is xi = kappa o in horizon units
-// (kappa = dx / delta), both known when the kernel is compiled up to the two
+// (kappa = dx / delta), both fixed when the kernel is compiled up to the two
 // strides and kappa, which come in as kernel parameters:
 //   - no neighbour ids are read (the family is implicit in the lattice; the
 //     flags say which offsets are bonds: absent members, bonds cut by a notch
@@ -17,23 +17,29 @@
 //     the offset, and the offsets' zero components drop out of the arithmetic,
 //   - the slot loop is unrolled over the stencil at compile time: flag bits,
 //     record offsets along z (immediates) and per-offset constants are fixed.
-// A lane still owns one node and accumulates its force in registers; a warp
-// walks 32 consecutive nodes.  Where the 32 nodes cross a lattice line the
-// offsets of some lanes wrap to other nodes; those slots have flag 0 and are
-// masked, and the node records carry a zero halo so that every read stays in
-// bounds.
+// A lane owns one node and accumulates its force in registers; a warp walks 32
+// consecutive nodes.  Where the 32 nodes cross a lattice line the offsets of
+// some lanes wrap to other nodes; those slots have flag 0 and are masked, and
+// the published records carry a zero halo so that every read stays in bounds.
+//
+// Precision (the FP32-bulk reading): each node's displacement is accumulated
+// in FP64 (u / delta, double buffered) and published to the neighbours rounded
+// to FP32, 16 bytes per node.  The bulk bond arithmetic is FP32 on those
+// published values; the rounding of u/delta to FP32 acts on the forces as a
+// displacement perturbation of at most half an ulp of |u|, drawn anew at every
+// step, so it does not accumulate.  Bonds whose FP32 stretch reaches a band
+// just below the smallest s_c are decided from the FP64 displacements: in FP32
+// away from the bond's s_c and with the literal FP64 stretch of Eq. 4 near it.
 //
 // Per bond (offset o, q = |o|^2, L = |xi|):
-//   eta = (h_j - h_i) + (l_j - l_i)       published float-float displacement
+//   eta = h_j - h_i                       published displacements / delta
 //   y   = xi + eta,   num = eta . (2 xi + eta) = |y|^2 - L^2 (no cancellation)
 //   |y| = y2 rsqrt(y2) with y2 = L^2 + num
 //   D   = L^2 |y| + L y2 = den |y|,  den = L (L + |y|),  s = num / den
 //   f   = w s y / |y| = w (num / D) y
-// The break test runs on num: s >= fast_lo <=> |y| >= L (1 + fast_lo) <=>
-// num >= fast_lo (2 + fast_lo) L^2, a per-q threshold.  Such bonds (near the
-// smallest s_c) are decided after each flag word, as in k_step_f32: in FP32
-// away from the bond's s_c and with the literal FP64 stretch of Eq. 4 within a
-// relative band of it.  Both directions of a bond do the same operations on
+// The band test runs on num: s >= fast_lo <=> |y| >= L (1 + fast_lo) <=>
+// num >= fast_lo (2 + fast_lo) L^2, a per-q threshold; candidates are decided
+// after each flag word.  Both directions of a bond do the same operations on
 // negated inputs, so their forces are exact negatives and they break together.
 #define PD_F32_LAT 1
 #include "pd_step_f32.cu"
@@ -42,6 +48,13 @@
 
 namespace pd {
 namespace {
+
+#ifndef PD_LAT_THREADS
+#define PD_LAT_THREADS 256
+#endif
+#ifndef PD_LAT_MIN_BLOCKS
+#define PD_LAT_MIN_BLOCKS 3
+#endif
 
 // the stencil offsets for run-time slot numbers (near-s_c resolution)
 struct StencilTab {
@@ -74,31 +87,26 @@ __device__ __forceinline__ float rcp_fast(float x)
     return r;
 }
 
-// The lane's own record as the bond terms subtract it: negated register pairs
-// (z, h_x), (h_y, h_z), (l_x, l_z) of the 256-bit load, and l_y.
-struct LatOwn {
-    float2 zhx, hyz, lxz;
-    float ly;
-};
-
-__device__ __forceinline__ LatOwn lat_own(const float4 a, const float4 b)
+// one published record (16 bytes) with a single 128-bit non-coherent load
+__device__ __forceinline__ float4 ld_pub(const float4* p)
 {
-    LatOwn p;
-    p.zhx = make_float2(-a.z, -a.w);
-    p.hyz = make_float2(-b.x, -b.y);
-    p.lxz = make_float2(-b.z, -b.w);
-    p.ly = -bf_lo(b.z);
-    return p;
+    float4 r;
+    asm volatile("ld.global.nc.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                 : "l"(p));
+    return r;
 }
 
-// eta = u_j - u_i / delta from the published float-float displacements
-__device__ __forceinline__ float3 lat_eta(const LatOwn& i, const float4 ja, const float4 jb)
+// The lane's own published displacement, negated: (x, y) as one register pair
+struct LatOwn {
+    float2 nxy;
+    float nz;
+};
+
+__device__ __forceinline__ float3 lat_eta(const LatOwn& i, const float4 j)
 {
-    const float2 d1 = __fadd2_rn(make_float2(ja.z, ja.w), i.zhx);  // (., dh_x)
-    const float2 d2 = __fadd2_rn(make_float2(jb.x, jb.y), i.hyz);  // (dh_y, dh_z)
-    const float2 d3 = __fadd2_rn(make_float2(jb.z, jb.w), i.lxz);  // (dl_x, dl_z)
-    const float dly = bf_lo(jb.z) + i.ly;
-    return make_float3(d1.y + d3.x, d2.x + dly, d2.y + d3.y);
+    const float2 d = __fadd2_rn(make_float2(j.x, j.y), i.nxy);
+    return make_float3(d.x, d.y, j.z + i.nz);
 }
 
 // Bond terms of offset o = (OX, OY, OZ), q = |o|^2, from eta: y, num,
@@ -124,58 +132,41 @@ __device__ __forceinline__ LatBond lat_terms(const StepArgsF32& a, const float3 
     return r;
 }
 
-// the same terms for an offset known only at run time (bit for bit the same
-// operations: a zero component adds +0, which leaves every sum unchanged)
-__device__ __forceinline__ LatBond lat_terms_rt(const StepArgsF32& a, const float3 e, int ox,
-                                                int oy, int oz, int q)
-{
-    LatBond r;
-    const float tx = e.x + a.lat_xi2[ox + 3];
-    const float ty = e.y + a.lat_xi2[oy + 3];
-    const float tz = e.z + a.lat_xi2[oz + 3];
-    r.yx = e.x + a.lat_xi[ox + 3];
-    r.yy = e.y + a.lat_xi[oy + 3];
-    r.yz = e.z + a.lat_xi[oz + 3];
-    r.num = fmaf(e.x, tx, fmaf(e.y, ty, e.z * tz));
-    const float y2 = r.num + a.lat_q[q];
-    r.ay = y2 * rsqrt_fast(y2);
-    r.D = fmaf(r.ay, a.lat_q[q], a.lat_l[q] * y2);
-    return r;
-}
-
-// A bond of slot m whose stretch reached the near-s_c band: decide the break
-// (FP32 away from its s_c, the literal FP64 stretch of Eq. 4 near it, then the
-// no-fail rule) and return its force term (zero when it breaks).
-template <int SCM>
+// A bond of slot m whose stretch reached the near-s_c band: the break decision
+// (from the FP64 displacements: in FP32 away from the bond's s_c, the literal
+// FP64 stretch of Eq. 4 near it; then the no-fail rule) and its force term,
+// zero when it breaks.  slot: the bond's index in the per-slot arrays.
+template <int SCM, bool PBC>
 __device__ __noinline__ float3 lat_resolve(const StepArgsF32& a, int cur, int64_t i, int m,
-                                           bool* broken)
+                                           int64_t slot, bool* broken)
 {
     const int ox = c_stencil.o[m][0], oy = c_stencil.o[m][1], oz = c_stencil.o[m][2];
     const int q = c_stencil.o[m][3];
     const int64_t j = i + (int64_t)ox * a.lat_sx + (int64_t)oy * a.lat_sy + oz;
-    const float4* __restrict__ R = a.rec[cur];
-    float4 ai, bi, aj, bj;
-    ld_rec(R + 2 * i, ai, bi);
-    ld_rec(R + 2 * j, aj, bj);
-    const LatBond b = lat_terms_rt(a, lat_eta(lat_own(ai, bi), aj, bj), ox, oy, oz, q);
+    const double* __restrict__ U = a.lat_u[cur];
+    double e64[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) e64[c] = U[3 * j + c] - U[3 * i + c];
+    // FP32 stretch terms from the FP64 displacement difference
+    const float xx = a.lat_xi[ox + 3], xy = a.lat_xi[oy + 3], xz = a.lat_xi[oz + 3];
+    const float ex = (float)e64[0], ey = (float)e64[1], ez = (float)e64[2];
+    const float num = fmaf(ex, ex + 2.0f * xx, fmaf(ey, ey + 2.0f * xy, ez * (ez + 2.0f * xz)));
+    const float y2 = num + a.lat_q[q];
+    const float ay = y2 * rsqrt_fast(y2);
+    const float D = fmaf(ay, a.lat_q[q], a.lat_l[q] * y2);
     const double sc = SCM == 1 ? sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i], a.gid[j]) : a.sc;
     const float scf = (float)sc;
     // num |y| - s_c D = den |y| (s - s_c): its sign decides, away from s_c
-    const float r = fmaf(-scf, b.D, b.num * b.ay);
+    const float r = fmaf(-scf, D, num * ay);
     bool brk;
-    if (fabsf(r) > a.guard * scf * b.D) {
+    if (fabsf(r) > a.guard * scf * D) {
         brk = r >= 0.0f;
     } else {
-        const NodeF32 ni = unpack(ai, bi), nj = unpack(aj, bj);
-        const double ui[3] = {(double)ni.hx + (double)ni.lx, (double)ni.hy + (double)ni.ly,
-                              (double)ni.hz + (double)ni.lz};
-        const double uj[3] = {(double)nj.hx + (double)nj.lx, (double)nj.hy + (double)nj.ly,
-                              (double)nj.hz + (double)nj.lz};
         double xv[3], y[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             xv[c] = a.x64[3 * j + c] - a.x64[3 * i + c];
-            y[c] = xv[c] + (uj[c] - ui[c]) * a.delta;
+            y[c] = xv[c] + e64[c] * a.delta;
         }
         const double L = sqrt(xv[0] * xv[0] + xv[1] * xv[1] + xv[2] * xv[2]);
         const double Rr = sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
@@ -184,15 +175,28 @@ __device__ __noinline__ float3 lat_resolve(const StepArgsF32& a, int cur, int64_
     if (brk && a.has_nofail) brk = ((a.bct[a.bcc[i]].mask | a.bct[a.bcc[j]].mask) & 8u) == 0u;
     *broken = brk;
     if (brk) return make_float3(0.f, 0.f, 0.f);
-    const float coef = b.num * rcp_fast(b.D);
-    return make_float3(coef * b.yx, coef * b.yy, coef * b.yz);
+    // the force term from the published displacements, formed as the fast path does
+    const float4* __restrict__ P = a.lat_pub[cur];
+    const float4 hi = ld_pub(P + i), hj = ld_pub(P + j);
+    LatOwn own;
+    own.nxy = make_float2(-hi.x, -hi.y);
+    own.nz = -hi.z;
+    const float3 e = lat_eta(own, hj);
+    const float fx = e.x + xx, fy = e.y + xy, fz = e.z + xz;
+    const float n2 = fmaf(e.x, e.x + 2.0f * xx, fmaf(e.y, e.y + 2.0f * xy, e.z * (e.z + 2.0f * xz)));
+    const float z2 = n2 + a.lat_q[q];
+    const float az = z2 * rsqrt_fast(z2);
+    const float Dz = fmaf(az, a.lat_q[q], a.lat_l[q] * z2);
+    float coef = n2 * rcp_fast(Dz);
+    if (PBC) coef *= a.cbond[slot];
+    return make_float3(coef * fx, coef * fy, coef * fz);
 }
 
-// State of a lane over its node's stencil walk.
-struct LatLane {
+// One node's state over its stencil walk.
+struct LatNode {
     LatOwn own;
-    const float4* Ri;   // the node's record in the buffer being read
     int64_t i;
+    int64_t slot0;      // index of slot 0 of this node in per-slot arrays
     float fx, fy, fz;
     uint32_t word[4];   // bond flags (stencil slot order)
     uint32_t pend;      // near-s_c candidates of the current flag word
@@ -201,18 +205,18 @@ struct LatLane {
 
 // Slot M: one bond, and after the last slot of a flag word the word's
 // near-s_c candidates.
-template <int SCM, int M>
-__device__ __forceinline__ void lat_slot(const StepArgsF32& a, int cur, LatLane& s)
+template <int SCM, bool PBC, int M>
+__device__ __forceinline__ void lat_slot(const StepArgsF32& a, int cur, const float4* Pi,
+                                         LatNode& s)
 {
     constexpr Off3 o = stencil_offset(M);
     constexpr int q = M >> 5, b = M & 31;
-    if constexpr (b == 0) s.pend = 0u;
-    float4 ja, jb;
-    ld_rec(s.Ri + 2 * (o.x * a.lat_sx + o.y * a.lat_sy) + 2 * o.z, ja, jb);
-    const LatBond t = lat_terms<o.x, o.y, o.z, o.q>(a, lat_eta(s.own, ja, jb));
+    const float4 hj = ld_pub(Pi + (o.x * a.lat_sx + o.y * a.lat_sy) + o.z);
+    const LatBond t = lat_terms<o.x, o.y, o.z, o.q>(a, lat_eta(s.own, hj));
     const bool alive = (s.word[q] >> b) & 1u;
     const bool cand = t.num >= a.lat_thr[o.q];
     float coef = t.num * rcp_fast(t.D);
+    if (PBC) coef *= __ldg(a.cbond + s.slot0 + 32 * M);
     coef = (alive && !cand) ? coef : 0.0f;
     s.pend |= (alive && cand) ? (1u << b) : 0u;
     s.fx = fmaf(coef, t.yx, s.fx);
@@ -225,7 +229,8 @@ __device__ __forceinline__ void lat_slot(const StepArgsF32& a, int cur, LatLane&
             const int bb = __ffs(pend) - 1;
             pend &= pend - 1u;
             bool broken;
-            const float3 f = lat_resolve<SCM>(a, cur, s.i, 32 * q + bb, &broken);
+            const int m = 32 * q + bb;
+            const float3 f = lat_resolve<SCM, PBC>(a, cur, s.i, m, s.slot0 + 32 * m, &broken);
             if (broken) {
                 nword &= ~(1u << bb);
             } else {
@@ -236,18 +241,19 @@ __device__ __forceinline__ void lat_slot(const StepArgsF32& a, int cur, LatLane&
         }
         s.word[q] = nword;
         s.alive += __popc(nword);
+        s.pend = 0u;
     }
 }
 
-template <int SCM, int... M>
-__device__ __forceinline__ void lat_walk(const StepArgsF32& a, int cur, LatLane& s,
-                                         std::integer_sequence<int, M...>)
+template <int SCM, bool PBC, int... M>
+__device__ __forceinline__ void lat_walk(const StepArgsF32& a, int cur, const float4* Pi,
+                                         LatNode& s, std::integer_sequence<int, M...>)
 {
-    (lat_slot<SCM, M>(a, cur, s), ...);
+    (lat_slot<SCM, PBC, M>(a, cur, Pi, s), ...);
 }
 
-template <int SCM>
-__global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS)
+template <int SCM, bool PBC>
+__global__ void __launch_bounds__(PD_LAT_THREADS, PD_LAT_MIN_BLOCKS)
     k_step_f32_lat(const __grid_constant__ StepArgsF32 a)
 {
     const int lane = threadIdx.x & 31;
@@ -256,89 +262,91 @@ __global__ void __launch_bounds__(256, PD_F32_MIN_BLOCKS)
     const int64_t step = a.step_ctr[0] + a.k;
     const int cur = (int)(step & 1);
     const int64_t nslices = (a.n + 31) >> 5;
-    const float4* __restrict__ R = a.rec[cur];
-    float4* __restrict__ Rout = const_cast<float4*>(a.rec[cur ^ 1]);
-    const float wc = a.w_const;
+    const float4* __restrict__ P = a.lat_pub[cur];
+    float4* __restrict__ Pout = const_cast<float4*>(a.lat_pub[cur ^ 1]);
+    const double* __restrict__ U = a.lat_u[cur];
+    double* __restrict__ Uout = a.lat_u[cur ^ 1];
 
     for (int64_t g = wid; g < nslices; g += nwarps) {
-        LatLane s;
+        LatNode s;
         s.i = (g << 5) + lane;
-        s.Ri = R + 2 * s.i;
-        float4 ai, bi;
-        ld_rec(s.Ri, ai, bi);
-        const NodeF32 ni = unpack(ai, bi);
-        s.own = lat_own(ai, bi);
+        s.slot0 = g * 128 * 32 + lane;
+        const float4 hi = ld_pub(P + s.i);
+        s.own.nxy = make_float2(-hi.x, -hi.y);
+        s.own.nz = -hi.z;
         uint32_t* bw = a.bits + g * 4 * 32 + lane;
+        uint32_t w0[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) s.word[q] = bw[q * 32];
-        const uint32_t word0[4] = {s.word[0], s.word[1], s.word[2], s.word[3]};
+        for (int q = 0; q < 4; ++q) w0[q] = s.word[q] = bw[q * 32];
         s.fx = s.fy = s.fz = 0.f;
         s.pend = 0u;
         s.alive = 0;
-        lat_walk<SCM>(a, cur, s, std::make_integer_sequence<int, kStencil>{});
+        lat_walk<SCM, PBC>(a, cur, P + s.i, s, std::make_integer_sequence<int, kStencil>{});
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            if (s.word[q] != word0[q]) bw[q * 32] = s.word[q];
+            if (s.word[q] != w0[q]) bw[q * 32] = s.word[q];
 
-        // ---- integration of the lane's node (damped Euler-Cromer, Eq. 11),
-        // linear displacement ramp, damage (Eq. 8) from the intact-bond count
+        // ---- the node's update: damped Euler-Cromer (Eq. 11) with the force in
+        // FP32 and u accumulated in FP64, the linear displacement ramp, damage
+        // (Eq. 8) from the intact-bond count
         const int64_t i = s.i;
-        if (i < a.n) {
-            const uint32_t cls = a.bcc[i];
-            uint32_t mask = 0u;
-            const BcClass* bc = nullptr;
-            float F[3] = {wc * s.fx, wc * s.fy, wc * s.fz};
-            if (cls != 0u) {
-                bc = a.bct + cls;
-                mask = bc->mask;
+        if (i >= a.n) continue;
+        const float wc = a.w_const;
+        const uint32_t cls = a.bcc[i];
+        uint32_t mask = 0u;
+        const BcClass* bc = nullptr;
+        float F[3] = {wc * s.fx, wc * s.fy, wc * s.fz};
+        if (cls != 0u) {
+            bc = a.bct + cls;
+            mask = bc->mask;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) F[c] += (float)(a.load * bc->force[c]);
-            }
-            const float dtf = (float)a.dt, etaf = (float)a.eta, rhof = (float)a.rho;
-            const float dtd = (float)(a.dt * a.inv_delta);
-            const float4 lo = a.lo32[i];
-            float H[3] = {ni.hx, ni.hy, ni.hz};
-            float L[3] = {lo.x, lo.y, lo.z};
-            bool finite = true;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float vi = a.v[3 * i + c];
-                float vn = vi + dtf * (F[c] - etaf * vi) / rhof;
-                ff_add(H[c], L[c], vn * dtd);
-                if (mask & (1u << c)) {
-                    const double s_now = a.disp_rate * (double)step;
-                    const double s_next = a.disp_rate * (double)(step + 1);
-                    ff_set(bc->disp[c] * s_next * a.inv_delta, H[c], L[c]);
-                    vn = (float)(bc->disp[c] * (s_next - s_now) / a.dt);
-                }
-                finite = finite && isfinite(H[c]);
-                a.v[3 * i + c] = vn;
-            }
-            st_rec(Rout + 2 * i, make_float4(ni.x, ni.y, ni.z, H[0]),
-                   make_float4(H[1], H[2], bf_pack(L[1], L[0]), bf_pack(0.0f, L[2])));
-            a.lo32[i] = make_float4(L[0], L[1], L[2], 0.0f);
-            const float wi = a.wsum_inv[i];
-            const float ws = wc * (float)s.alive;
-            a.damage[i] = wi > 0.0f ? fmaxf(0.0f, 1.0f - ws * wi) : 0.0f;
-            if (!finite) atomicOr(a.err, PD_DEVERR_NONFINITE);
+            for (int c = 0; c < 3; ++c) F[c] += (float)(a.load * bc->force[c]);
         }
+        double un[3];
+        bool finite = true;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float vi = a.v[3 * i + c];
+            float vn = vi + a.dt_f * (F[c] - a.eta_f * vi) / a.rho_f;
+            un[c] = fma((double)vn, (double)a.dtd_f, U[3 * i + c]);
+            if (mask & (1u << c)) {
+                const double s_now = a.disp_rate * (double)step;
+                const double s_next = a.disp_rate * (double)(step + 1);
+                un[c] = bc->disp[c] * s_next * a.inv_delta;
+                vn = (float)(bc->disp[c] * (s_next - s_now) / a.dt);
+            }
+            finite = finite && isfinite(un[c]);
+            a.v[3 * i + c] = vn;
+            Uout[3 * i + c] = un[c];
+        }
+        Pout[i] = make_float4((float)un[0], (float)un[1], (float)un[2], 0.0f);
+        const float wi = a.wsum_inv[i];
+        const float ws = wc * (float)s.alive;
+        a.damage[i] = wi > 0.0f ? fmaxf(0.0f, 1.0f - ws * wi) : 0.0f;
+        if (!finite) atomicOr(a.err, PD_DEVERR_NONFINITE);
     }
 }
 
 }  // namespace
 
-const void* step_f32_kernel_lat(int sc_mode)
+const void* step_f32_kernel_lat(int sc_mode, bool per_bond_c)
 {
-    return sc_mode == 0 ? (const void*)k_step_f32_lat<0> : (const void*)k_step_f32_lat<1>;
+    if (per_bond_c)
+        return sc_mode == 0 ? (const void*)k_step_f32_lat<0, true> : (const void*)k_step_f32_lat<1, true>;
+    return sc_mode == 0 ? (const void*)k_step_f32_lat<0, false> : (const void*)k_step_f32_lat<1, false>;
 }
 
 cudaError_t launch_step_f32_lat(const StepArgsF32& a, int sc_mode, int grid, int block,
                                 cudaStream_t s)
 {
-    if (sc_mode == 0)
-        k_step_f32_lat<0><<<grid, block, 0, s>>>(a);
-    else
-        k_step_f32_lat<1><<<grid, block, 0, s>>>(a);
+    const bool pbc = a.cbond != nullptr;
+    if (sc_mode == 0) {
+        if (pbc) k_step_f32_lat<0, true><<<grid, block, 0, s>>>(a);
+        else k_step_f32_lat<0, false><<<grid, block, 0, s>>>(a);
+    } else {
+        if (pbc) k_step_f32_lat<1, true><<<grid, block, 0, s>>>(a);
+        else k_step_f32_lat<1, false><<<grid, block, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -6,8 +6,9 @@ the parity tests: u within 1e-4 relative, v within 1e-3, broken sets within
 0.1 %, damage equal to Eq. 8 of the GPU's own flags) and the general sliced-ELL
 kernel on the same model: short lattice axes where a warp's offsets wrap
 around lattice lines, ragged last slices, a notch, per-bond critical stretch
-and no-fail nodes; per-bond stiffness on a lattice handle (general kernel on
-the stencil-ordered layout); bond flags read, written and cut in stencil order.
+and no-fail nodes, per-bond stiffness; bond flags read, written and cut in
+stencil order.  Lattice models keep u in FP64 and publish it rounded to FP32
+for the bulk bond arithmetic (the FP32-bulk reading).
 """
 import numpy as np
 import pytest
@@ -105,19 +106,22 @@ def test_notched_beam_hashed_sc_no_fail_matches_oracle():
     check_f32(g, o)
 
 
-def test_lattice_kernel_equals_general_kernel():
+def test_lattice_kernel_agrees_with_general_kernel():
     # the same model through both FP32 kernels (reorder = 1 takes the general
-    # one): different summation orders, the same arithmetic bar
+    # one): both within the FP32 bar of the oracle, and of each other
     w = workloads.notched_beam(36, 8, 9, length=0.06, rate=2e-7, steps=150)
+    o = oracle_run(w, w.steps)
     a = gpu_run(w, w.steps, F32)
     b = gpu_run(w, w.steps, F32, reorder=1)
     assert a["info"]["layout"] == LAT and b["info"]["layout"] == SELL
-    assert rel(a["u"], b["u"]) <= 1e-5, rel(a["u"], b["u"])
+    check_f32(a, o)
+    check_f32(b, o)
+    assert rel(a["u"], b["u"]) <= 1e-4, rel(a["u"], b["u"])
     assert (a["mu"] != b["mu"]).mean() < 1e-3
 
 
 def test_per_bond_stiffness_on_a_lattice_handle():
-    # per-bond c: the general kernel runs on the stencil-ordered layout
+    # per-bond c read per stencil slot by the lattice kernel
     w = workloads.tensile_bar(16, 6, 7, rate=5e-7, steps=100)
     c = oracle.micromodulus(w.bulk_modulus, w.horizon)
     off, idx = oracle.cut_family(w.coords, w.horizon, w.cuts_array())
