@@ -298,6 +298,12 @@ StepArgsF32 args_f32(pd_handle* h, int k)
             a.lat_xi[c + 3] = (float)(kap * c);
             a.lat_xi2[c + 3] = 2.0f * a.lat_xi[c + 3];
         }
+        for (int j = 0; j < kStencilRows; ++j) {
+            const Off3 r = stencil_row(j);
+            a.lat_rxi[j] = make_float4(a.lat_xi[r.x + 3], a.lat_xi[r.y + 3], a.lat_xi2[r.x + 3],
+                                       a.lat_xi2[r.y + 3]);
+            a.lat_roff[j] = r.x * a.lat_sx + r.y * a.lat_sy;
+        }
         for (int q = 0; q <= kStencilR2; ++q) {
             a.lat_q[q] = (float)(kap * kap * q);
             a.lat_l[q] = (float)(kap * std::sqrt((double)q));
@@ -756,7 +762,7 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
     std::vector<int32_t> nbr, sw;
     std::vector<uint32_t> bits;
     if (h->lattice) {
-        h->Q = (kStencil + 31) / 32;
+        h->Q = kStencilSlots / 32;
         build_layout_stencil(n, h->off, h->idx, h->perm, h->inv, h->lat, nbr, bits, sw, h->cnt);
         const int64_t sy = h->lat.N[2], sx = h->lat.N[1] * h->lat.N[2];
         // the stencil's reach, and one slice more: a warp walks two slices

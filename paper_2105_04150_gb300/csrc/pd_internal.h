@@ -60,26 +60,101 @@ struct InstParams {
 // Regular-lattice stencil.  On a cubic lattice of spacing dx with
 // 3 dx <= delta < sqrt(10) dx, the family of Eq. 9 of an interior node is the
 // set of the 122 integer offsets o with 0 < |o|^2 <= 9 (in units of dx); a
-// node near a face or a cut has a subset of them.  Slot m of such a model's
-// layout holds offset m of this list, ordered lexicographically by
-// (o_x, o_y, o_z), so offsets with the same (o_x, o_y) (a "row") are
-// consecutive and differ by one node along z.
+// node near a face or a cut has a subset of them.  A lattice model's layout
+// gives each offset a fixed slot (of 128: 4 flag words of 32 bits).  The
+// offsets are grouped in "rows" (o_x, o_y fixed, o_z running), rows of equal
+// q_xy = o_x^2 + o_y^2 in segments, and the segments laid out so that no row
+// crosses a flag word:
+//   word 0: q_xy = 1 (4 rows, o_z = -2..2), q_xy = 8 (4 rows, o_z = -1..1)
+//   word 1: q_xy = 2 (4 rows, -2..2), q_xy = 0 (o_z = +-1..3), q_xy = 9 (4 rows, o_z = 0)
+//   word 2: q_xy = 4 (4 rows, -2..2), q_xy = 5 (rows 0-1, -2..2)
+//   word 3: q_xy = 5 (rows 2-7, -2..2)
+// Within a q_xy the rows with o_y = 0 come first, then those with o_x = 0, then
+// the rest, each group in lexicographic (o_x, o_y) order; a segment holds rows
+// of one such group, so that its zero components are known.  Slots 62, 63, 94,
+// 95, 126 and 127 are unused.  The stencil kernel walks a segment of 5-offset
+// rows as a loop over its rows with the o_z offsets unrolled, and the short
+// rows (q_xy = 0, 8, 9) unrolled.
 constexpr int kStencil = 122;
+constexpr int kStencilSlots = 128;
 constexpr int kStencilR2 = 9;
+constexpr int kStencilSegs = 10;
+constexpr int kStencilRows = 29;
 struct Off3 {
-    int x, y, z, q;  // q = |o|^2
+    int x, y, z, q;  // q = |o|^2; q = 0 marks an unused slot
 };
-__host__ __device__ constexpr Off3 stencil_offset(int m)
+struct StencilSeg {
+    int qxy;      // o_x^2 + o_y^2 of its rows
+    int row0;     // first row (of the rows with this q_xy, in the order above)
+    int nrows;
+    int word;     // flag word
+    int bit0;     // first bit in the word
+    int first;    // index of its first row among all kStencilRows rows
+    int zx, zy;   // 1: o_x (o_y) is 0 in every row of the segment
+    int unroll;   // 1: rows unrolled in the kernel, 0: a loop over the rows
+};
+__host__ __device__ constexpr int stencil_row_len(int qxy)
+{
+    return qxy == 0 ? 6 : qxy == 8 ? 3 : qxy == 9 ? 1 : 5;
+}
+// o_z of position k in a row
+__host__ __device__ constexpr int stencil_row_oz(int qxy, int k)
+{
+    return qxy == 0 ? (k < 3 ? k - 3 : k - 2) : k - (stencil_row_len(qxy) - 1) / 2;
+}
+// (o_x, o_y) of row r among the rows with o_x^2 + o_y^2 = qxy: o_y = 0 first,
+// then o_x = 0, then the others, each lexicographic
+__host__ __device__ constexpr Off3 stencil_row_xy(int qxy, int r)
 {
     int k = 0;
-    for (int a = -3; a <= 3; ++a)
-        for (int b = -3; b <= 3; ++b)
-            for (int c = -3; c <= 3; ++c) {
-                const int q = a * a + b * b + c * c;
-                if (q == 0 || q > kStencilR2) continue;
-                if (k == m) return Off3{a, b, c, q};
+    for (int grp = 0; grp < 3; ++grp)
+        for (int a = -3; a <= 3; ++a)
+            for (int b = -3; b <= 3; ++b) {
+                if (a * a + b * b != qxy) continue;
+                const int g = b == 0 ? 0 : a == 0 ? 1 : 2;
+                if (g != grp) continue;
+                if (k == r) return Off3{a, b, 0, qxy};
                 ++k;
             }
+    return Off3{0, 0, 0, 0};
+}
+__host__ __device__ constexpr StencilSeg stencil_seg(int sg)
+{
+    constexpr int q[kStencilSegs] = {1, 1, 8, 2, 0, 9, 4, 4, 5, 5};
+    constexpr int r0[kStencilSegs] = {0, 2, 0, 0, 0, 0, 0, 2, 0, 2};
+    constexpr int nr[kStencilSegs] = {2, 2, 4, 4, 1, 4, 2, 2, 2, 6};
+    constexpr int w[kStencilSegs] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3};
+    constexpr int b[kStencilSegs] = {0, 10, 20, 0, 20, 26, 0, 10, 20, 0};
+    constexpr int zx[kStencilSegs] = {0, 1, 0, 0, 1, 0, 0, 1, 0, 0};
+    constexpr int zy[kStencilSegs] = {1, 0, 0, 0, 1, 0, 1, 0, 0, 0};
+    constexpr int un[kStencilSegs] = {0, 0, 1, 0, 1, 1, 0, 0, 0, 0};
+    int first = 0;
+    for (int k = 0; k < sg; ++k) first += nr[k];
+    return StencilSeg{q[sg], r0[sg], nr[sg], w[sg], b[sg], first, zx[sg], zy[sg], un[sg]};
+}
+// the offset of slot m (q = 0: unused slot)
+__host__ __device__ constexpr Off3 stencil_offset(int m)
+{
+    for (int sg = 0; sg < kStencilSegs; ++sg) {
+        const StencilSeg s = stencil_seg(sg);
+        const int len = stencil_row_len(s.qxy);
+        const int start = 32 * s.word + s.bit0;
+        if (m >= start && m < start + len * s.nrows) {
+            const int r = (m - start) / len, k = (m - start) % len;
+            const Off3 xy = stencil_row_xy(s.qxy, s.row0 + r);
+            const int oz = stencil_row_oz(s.qxy, k);
+            return Off3{xy.x, xy.y, oz, s.qxy + oz * oz};
+        }
+    }
+    return Off3{0, 0, 0, 0};
+}
+// (o_x, o_y) of row j of all kStencilRows rows, in segment order
+__host__ __device__ constexpr Off3 stencil_row(int j)
+{
+    for (int sg = 0; sg < kStencilSegs; ++sg) {
+        const StencilSeg s = stencil_seg(sg);
+        if (j >= s.first && j < s.first + s.nrows) return stencil_row_xy(s.qxy, s.row0 + j - s.first);
+    }
     return Off3{0, 0, 0, 0};
 }
 
@@ -126,6 +201,8 @@ struct StepArgsF32 {
     double k1, beta;           // trilinear: kink at s_1 = k1 s_0 with force beta c s_0 (k1 > 1)
     // regular-lattice stencil kernel (pd_step_f32_lat.cu); node p = (ix Ny + iy) Nz + iz
     int32_t lat_sx, lat_sy;    // node-order strides of x and y (z: 1)
+    float4 lat_rxi[kStencilRows];   // per row (segment order): kappa (o_x, o_y, 2 o_x, 2 o_y)
+    int32_t lat_roff[kStencilRows]; // per row: node offset o_x Sx + o_y Sy
     float lat_xi[7];           // kappa c for c = -3..3 (kappa = dx / delta: xi in horizon units)
     float lat_xi2[7];          // 2 kappa c
     float lat_q[kStencilR2 + 1];    // |xi|^2 = kappa^2 q for q = |o|^2

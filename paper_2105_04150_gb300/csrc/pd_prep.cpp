@@ -301,8 +301,9 @@ struct StencilLut {
     StencilLut()
     {
         for (int& v : s) v = -1;
-        for (int m = 0; m < kStencil; ++m) {
+        for (int m = 0; m < kStencilSlots; ++m) {
             const Off3 o = stencil_offset(m);
+            if (o.q == 0) continue;  // unused slot
             s[((o.x + 3) * 7 + (o.y + 3)) * 7 + (o.z + 3)] = m;
         }
     }
@@ -329,7 +330,7 @@ void build_layout_stencil(int64_t n, const std::vector<int64_t>& off,
                           std::vector<int32_t>& nbr, std::vector<uint32_t>& bits,
                           std::vector<int32_t>& sw, std::vector<int32_t>& cnt)
 {
-    const int Q = (kStencil + 31) / 32;
+    const int Q = kStencilSlots / 32;
     const int64_t W = 32LL * Q;
     const int64_t ns = (n + 31) / 32;
     nbr.resize((size_t)(ns * W * 32));

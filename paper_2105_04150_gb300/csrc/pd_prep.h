@@ -38,8 +38,9 @@ struct Lattice {
 bool detect_lattice(int64_t n, const double* x, const std::vector<int64_t>& off,
                     const std::vector<int32_t>& idx, Lattice& L, std::vector<int32_t>& perm,
                     std::vector<int32_t>& inv);
-// Stencil-ordered layout of a lattice model (W = 128 slots, slot m = stencil
-// offset m, kStencil used): absent members hold the node itself with flag 0.
+// Stencil-ordered layout of a lattice model (W = 128 slots, slot m holds
+// stencil_offset(m)): absent members and unused slots hold the node itself
+// with flag 0.
 void build_layout_stencil(int64_t n, const std::vector<int64_t>& off,
                           const std::vector<int32_t>& idx, const std::vector<int32_t>& perm,
                           const std::vector<int32_t>& inv, const Lattice& L,

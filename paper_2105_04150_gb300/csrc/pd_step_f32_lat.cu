@@ -53,17 +53,17 @@ namespace {
 #define PD_LAT_THREADS 256
 #endif
 #ifndef PD_LAT_MIN_BLOCKS
-#define PD_LAT_MIN_BLOCKS 3
+#define PD_LAT_MIN_BLOCKS 4
 #endif
 
 // the stencil offsets for run-time slot numbers (near-s_c resolution)
 struct StencilTab {
-    signed char o[kStencil][4];
+    signed char o[kStencilSlots][4];
 };
 constexpr StencilTab make_stencil_tab()
 {
     StencilTab t{};
-    for (int m = 0; m < kStencil; ++m) {
+    for (int m = 0; m < kStencilSlots; ++m) {
         const Off3 o = stencil_offset(m);
         t.o[m][0] = (signed char)o.x;
         t.o[m][1] = (signed char)o.y;
@@ -107,29 +107,6 @@ __device__ __forceinline__ float3 lat_eta(const LatOwn& i, const float4 j)
 {
     const float2 d = __fadd2_rn(make_float2(j.x, j.y), i.nxy);
     return make_float3(d.x, d.y, j.z + i.nz);
-}
-
-// Bond terms of offset o = (OX, OY, OZ), q = |o|^2, from eta: y, num,
-// D = den |y| and |y|; the offset's zero components drop out at compile time.
-struct LatBond {
-    float yx, yy, yz, num, D, ay;
-};
-
-template <int OX, int OY, int OZ, int Q>
-__device__ __forceinline__ LatBond lat_terms(const StepArgsF32& a, const float3 e)
-{
-    LatBond r;
-    const float tx = OX ? e.x + a.lat_xi2[OX + 3] : e.x;
-    const float ty = OY ? e.y + a.lat_xi2[OY + 3] : e.y;
-    const float tz = OZ ? e.z + a.lat_xi2[OZ + 3] : e.z;
-    r.yx = OX ? e.x + a.lat_xi[OX + 3] : e.x;
-    r.yy = OY ? e.y + a.lat_xi[OY + 3] : e.y;
-    r.yz = OZ ? e.z + a.lat_xi[OZ + 3] : e.z;
-    r.num = fmaf(e.x, tx, fmaf(e.y, ty, e.z * tz));
-    const float y2 = r.num + a.lat_q[Q];
-    r.ay = y2 * rsqrt_fast(y2);
-    r.D = fmaf(r.ay, a.lat_q[Q], a.lat_l[Q] * y2);
-    return r;
 }
 
 // A bond of slot m whose stretch reached the near-s_c band: the break decision
@@ -203,54 +180,145 @@ struct LatNode {
     int alive;          // intact bonds after this step's decisions
 };
 
-// Slot M: one bond, and after the last slot of a flag word the word's
-// near-s_c candidates.
-template <int SCM, bool PBC, int M>
-__device__ __forceinline__ void lat_slot(const StepArgsF32& a, int cur, const float4* Pi,
-                                         LatNode& s)
+// Bond K of a row with q_xy = QXY: o_z = stencil_row_oz(QXY, K); xx, xy and
+// xx2, xy2: xi and 2 xi of the row's o_x, o_y (ZX / ZY: that component is 0);
+// rb: the row's flags from bit 0, rp: the row's near-s_c candidates.
+template <int QXY, int K, int ZX, int ZY, bool PBC>
+__device__ __forceinline__ void lat_row_bond(const StepArgsF32& a, float xx, float xy, float xx2,
+                                             float xy2, const float4* Prow, const float* cbrow,
+                                             uint32_t rb, uint32_t& rp, LatNode& s)
 {
-    constexpr Off3 o = stencil_offset(M);
-    constexpr int q = M >> 5, b = M & 31;
-    const float4 hj = ld_pub(Pi + (o.x * a.lat_sx + o.y * a.lat_sy) + o.z);
-    const LatBond t = lat_terms<o.x, o.y, o.z, o.q>(a, lat_eta(s.own, hj));
-    const bool alive = (s.word[q] >> b) & 1u;
-    const bool cand = t.num >= a.lat_thr[o.q];
-    float coef = t.num * rcp_fast(t.D);
-    if (PBC) coef *= __ldg(a.cbond + s.slot0 + 32 * M);
+    constexpr int OZ = stencil_row_oz(QXY, K);
+    constexpr int Q = QXY + OZ * OZ;
+    const float3 e = lat_eta(s.own, ld_pub(Prow + OZ));
+    const float yx = ZX ? e.x : e.x + xx, tx = ZX ? e.x : e.x + xx2;
+    const float yy = ZY ? e.y : e.y + xy, ty = ZY ? e.y : e.y + xy2;
+    const float yz = OZ ? e.z + a.lat_xi[OZ + 3] : e.z;
+    const float tz = OZ ? e.z + a.lat_xi2[OZ + 3] : e.z;
+    const float num = fmaf(e.x, tx, fmaf(e.y, ty, e.z * tz));
+    const float y2 = num + a.lat_q[Q];
+    const float ay = y2 * rsqrt_fast(y2);
+    const float D = fmaf(ay, a.lat_q[Q], a.lat_l[Q] * y2);
+    const bool alive = (rb >> K) & 1u;
+    const bool cand = num >= a.lat_thr[Q];
+    float coef = num * rcp_fast(D);
+    if (PBC) coef *= __ldg(cbrow + 32 * K);
     coef = (alive && !cand) ? coef : 0.0f;
-    s.pend |= (alive && cand) ? (1u << b) : 0u;
-    s.fx = fmaf(coef, t.yx, s.fx);
-    s.fy = fmaf(coef, t.yy, s.fy);
-    s.fz = fmaf(coef, t.yz, s.fz);
-    if constexpr (b == 31 || M == kStencil - 1) {
-        uint32_t nword = s.word[q];
-        uint32_t pend = s.pend;
-        while (pend) {
-            const int bb = __ffs(pend) - 1;
-            pend &= pend - 1u;
-            bool broken;
-            const int m = 32 * q + bb;
-            const float3 f = lat_resolve<SCM, PBC>(a, cur, s.i, m, s.slot0 + 32 * m, &broken);
-            if (broken) {
-                nword &= ~(1u << bb);
-            } else {
-                s.fx += f.x;
-                s.fy += f.y;
-                s.fz += f.z;
-            }
-        }
-        s.word[q] = nword;
-        s.alive += __popc(nword);
-        s.pend = 0u;
+    rp |= (alive && cand) ? (1u << K) : 0u;
+    s.fx = fmaf(coef, yx, s.fx);
+    s.fy = fmaf(coef, yy, s.fy);
+    s.fz = fmaf(coef, yz, s.fz);
+}
+
+// Row R (compile-time) of segment SG, unrolled, its offsets fixed
+template <bool PBC, int SG, int R, int... K>
+__device__ __forceinline__ void lat_row_fixed(const StepArgsF32& a, const float4* Pi, LatNode& s,
+                                              std::integer_sequence<int, K...>)
+{
+    constexpr StencilSeg sg = stencil_seg(SG);
+    constexpr Off3 o = stencil_row_xy(sg.qxy, sg.row0 + R);
+    constexpr int b0 = sg.bit0 + stencil_row_len(sg.qxy) * R;
+    const float4* Prow = Pi + (o.x * a.lat_sx + o.y * a.lat_sy);
+    const uint32_t rb = s.word[sg.word] >> b0;
+    const float* cbrow = PBC ? a.cbond + s.slot0 + 32 * (32 * sg.word + b0) : nullptr;
+    uint32_t rp = 0u;
+    (lat_row_bond<sg.qxy, K, o.x == 0, o.y == 0, PBC>(a, a.lat_xi[o.x + 3], a.lat_xi[o.y + 3],
+                                                      a.lat_xi2[o.x + 3], a.lat_xi2[o.y + 3],
+                                                      Prow, cbrow, rb, rp, s),
+     ...);
+    s.pend |= rp << b0;
+}
+
+template <bool PBC, int SG, int... R>
+__device__ __forceinline__ void lat_rows_fixed(const StepArgsF32& a, const float4* Pi, LatNode& s,
+                                               std::integer_sequence<int, R...>)
+{
+    (lat_row_fixed<PBC, SG, R>(a, Pi, s,
+                               std::make_integer_sequence<int, stencil_row_len(stencil_seg(SG).qxy)>{}),
+     ...);
+}
+
+// Segment SG as a loop over its rows (offsets of a row unrolled)
+template <bool PBC, int SG, int... K>
+__device__ __forceinline__ void lat_rows_loop(const StepArgsF32& a, const float4* Pi, LatNode& s,
+                                              std::integer_sequence<int, K...>)
+{
+    constexpr StencilSeg sg = stencil_seg(SG);
+    constexpr int len = stencil_row_len(sg.qxy);
+#pragma unroll 1
+    for (int r = 0; r < sg.nrows; ++r) {
+        const float4 xr = a.lat_rxi[sg.first + r];
+        const float4* Prow = Pi + a.lat_roff[sg.first + r];
+        const int b0 = sg.bit0 + len * r;
+        const uint32_t rb = s.word[sg.word] >> b0;
+        const float* cbrow = PBC ? a.cbond + s.slot0 + 32 * (32 * sg.word + b0) : nullptr;
+        uint32_t rp = 0u;
+        (lat_row_bond<sg.qxy, K, sg.zx, sg.zy, PBC>(a, xr.x, xr.y, xr.z, xr.w, Prow, cbrow, rb,
+                                                    rp, s),
+         ...);
+        s.pend |= rp << b0;
     }
 }
 
-template <int SCM, bool PBC, int... M>
-__device__ __forceinline__ void lat_walk(const StepArgsF32& a, int cur, const float4* Pi,
-                                         LatNode& s, std::integer_sequence<int, M...>)
+template <bool PBC, int SG>
+__device__ __forceinline__ void lat_seg(const StepArgsF32& a, const float4* Pi, LatNode& s)
 {
-    (lat_slot<SCM, PBC, M>(a, cur, Pi, s), ...);
+    constexpr StencilSeg sg = stencil_seg(SG);
+    if constexpr (sg.unroll)
+        lat_rows_fixed<PBC, SG>(a, Pi, s, std::make_integer_sequence<int, sg.nrows>{});
+    else
+        lat_rows_loop<PBC, SG>(a, Pi, s, std::make_integer_sequence<int, stencil_row_len(sg.qxy)>{});
 }
+
+// After the last segment of flag word W: decide the word's near-s_c candidates.
+template <int SCM, bool PBC, int W>
+__device__ __forceinline__ void lat_word_end(const StepArgsF32& a, int cur, LatNode& s)
+{
+    uint32_t nword = s.word[W];
+    uint32_t pend = s.pend;
+    while (pend) {
+        const int bb = __ffs(pend) - 1;
+        pend &= pend - 1u;
+        bool broken;
+        const int m = 32 * W + bb;
+        const float3 f = lat_resolve<SCM, PBC>(a, cur, s.i, m, s.slot0 + 32 * m, &broken);
+        if (broken) {
+            nword &= ~(1u << bb);
+        } else {
+            s.fx += f.x;
+            s.fy += f.y;
+            s.fz += f.z;
+        }
+    }
+    s.word[W] = nword;
+    s.alive += __popc(nword);
+    s.pend = 0u;
+}
+
+// the walk over the stencil: the segments of each flag word, then the word's
+// near-s_c candidates (the segment and word layout of stencil_seg)
+template <int SCM, bool PBC>
+__device__ __forceinline__ void lat_walk(const StepArgsF32& a, int cur, const float4* Pi,
+                                         LatNode& s)
+{
+    lat_seg<PBC, 0>(a, Pi, s);
+    lat_seg<PBC, 1>(a, Pi, s);
+    lat_seg<PBC, 2>(a, Pi, s);
+    lat_word_end<SCM, PBC, 0>(a, cur, s);
+    lat_seg<PBC, 3>(a, Pi, s);
+    lat_seg<PBC, 4>(a, Pi, s);
+    lat_seg<PBC, 5>(a, Pi, s);
+    lat_word_end<SCM, PBC, 1>(a, cur, s);
+    lat_seg<PBC, 6>(a, Pi, s);
+    lat_seg<PBC, 7>(a, Pi, s);
+    lat_seg<PBC, 8>(a, Pi, s);
+    lat_word_end<SCM, PBC, 2>(a, cur, s);
+    lat_seg<PBC, 9>(a, Pi, s);
+    lat_word_end<SCM, PBC, 3>(a, cur, s);
+}
+static_assert(stencil_seg(2).word == 0 && stencil_seg(3).word == 1 && stencil_seg(5).word == 1 &&
+                  stencil_seg(6).word == 2 && stencil_seg(8).word == 2 && stencil_seg(9).word == 3,
+              "lat_walk follows the segment layout");
 
 template <int SCM, bool PBC>
 __global__ void __launch_bounds__(PD_LAT_THREADS, PD_LAT_MIN_BLOCKS)
@@ -281,7 +349,7 @@ __global__ void __launch_bounds__(PD_LAT_THREADS, PD_LAT_MIN_BLOCKS)
         s.fx = s.fy = s.fz = 0.f;
         s.pend = 0u;
         s.alive = 0;
-        lat_walk<SCM, PBC>(a, cur, P + s.i, s, std::make_integer_sequence<int, kStencil>{});
+        lat_walk<SCM, PBC>(a, cur, P + s.i, s);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
             if (s.word[q] != w0[q]) bw[q * 32] = s.word[q];
