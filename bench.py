@@ -103,18 +103,24 @@ def parse():
     p.add_argument("--checkpoint-every", type=int, default=45)
     p.add_argument("--precision", type=int, default=32, choices=[32, 64, 48],
                    help="32: FP32 bonds; 64: FP64; 48: FP64-grade double-word FP32 bonds")
+    p.add_argument("--shape", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"),
+                   help="lattice dimensions of the beam, plate or bar (default: the workload's)")
     p.add_argument("--graph-steps", type=int, default=50)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-outer", action="store_true",
+                   help="leave out the batch and adjoint sub-objects of the default line")
     return p.parse_args()
 
 
-def make_workload(name):
+def make_workload(name, shape=None):
     if name == "beam":
-        return workloads.notched_beam()
+        if shape is None:
+            return workloads.notched_beam()
+        return workloads.notched_beam(*shape, length=shape[0] / 600.0)  # the beam's spacing
     if name == "plate":
-        return workloads.plate()
-    return workloads.tensile_bar()
+        return workloads.plate() if shape is None else workloads.plate(*shape)
+    return workloads.tensile_bar() if shape is None else workloads.tensile_bar(*shape)
 
 
 def describe(w, n_bonds, precision, integrator="ec", lattice=None):
@@ -327,7 +333,7 @@ def run_reference(args):
         return
     import oracle
     oracle.build()
-    w = make_workload(args.workload)
+    w = make_workload(args.workload, args.shape)
     w.ramp_steps = args.ramp_steps
     w.kr = args.kr
     if args.state_based is not None:
@@ -370,7 +376,7 @@ def run_ours(args):
     pdgb.lib()
     torch.cuda.set_device(local)
     dev_sync = torch.cuda.synchronize
-    w = make_workload(args.workload)
+    w = make_workload(args.workload, args.shape)
     w.ramp_steps = args.ramp_steps
     w.kr = args.kr
     if args.state_based is not None:
@@ -520,6 +526,21 @@ def run_ours(args):
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk.summary(t_on, t_off),
     }
+    if world == 1 and not args.no_outer and args.workload == "beam":
+        # the outer-loop forms, measured in the same process: the batched UQ sweep
+        # (256 instances) and the sensitivity plate's adjoint (2000 steps,
+        # checkpoints every 45; central differences on a few directions and the
+        # oracle's reverse mode over a bounded number of steps)
+        b = measure_batch(args, max(10, min(args.steps, 200)), 5, False, False)
+        line["batch"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "instance_steps_per_s",
+                                           "loop", "batched_over_loop",
+                                           "loop_single_model_kernels", "roofline", "config",
+                                           "gpu_launches", "clocks")}
+        a = measure_adjoint(args, 2000, 45, 4, 1, not args.no_cpu_baseline)
+        line["adjoint"] = {k: a[k] for k in ("value", "unit", "dtype", "config", "gradient_ms",
+                                             "gradient_parts_ms", "forward_ms",
+                                             "adjoint_over_forward", "bonds_broken", "fd",
+                                             "oracle_check", "gpu_launches", "clocks")}
     print(json.dumps(line), flush=True)
     if group is not None:
         group.barrier()
@@ -528,17 +549,53 @@ def run_ours(args):
 def run_batch(args):
     """256 independent bars and notched beams (2k-60k nodes, per-instance K and s_c):
     one batch handle (one fused launch per step, graph-captured, autotuned launch
-    shape) against a loop that launches every instance's own step kernel."""
+    shape) against per-instance loops captured in one CUDA graph."""
+    print(json.dumps(measure_batch(args, args.steps, args.warmup, not args.no_cpu_baseline,
+                                   not args.no_e2e)), flush=True)
+
+
+def loop_graph_ms(pdgb, torch, ws, precision, general, stream, G, reps):
+    """The per-instance loop: one handle per instance, every instance stepped G
+    times per replay (G step launches and one counter advance each), all of them
+    captured in one CUDA graph; ms per step of all instances."""
+    hs = [pdgb.Model.from_workload(w, precision=precision, graph_steps=0,
+                                   stream=stream.cuda_stream, general=general) for w in ws]
+    layouts = sorted({m.info()["layout"] for m in hs})
+    for m in hs:
+        m.step(2)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        for m in hs:
+            pdgb.pd_step(m.h, G)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):  # replays go to the current stream
+        g.replay()  # warm-up replay
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            g.replay()
+        e1.record(stream)
+        e1.synchronize()
+    ms = e0.elapsed_time(e1) / (reps * G)
+    del g
+    for m in hs:
+        m.close()
+    return ms, layouts
+
+
+def measure_batch(args, steps, warmup, with_cpu, with_e2e):
     import torch
     import paper_2105_04150_gb300 as pdgb
     torch.cuda.set_device(0)
     ws = workloads.batch_instances()
     stream = torch.cuda.Stream()
-    G = max(1, min(args.graph_steps, args.steps))
+    G = max(1, min(args.graph_steps, steps))
     bm = pdgb.Model.batch(ws, precision=args.precision, graph_steps=G, stream=stream.cuda_stream)
     n_bonds = bm.info()["n_bonds"]
     block, bps = bm.autotune(10)
-    bm.step(args.warmup)
+    bm.step(warmup)
     bm.sync()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -546,21 +603,21 @@ def run_batch(args):
         time.sleep(0.5)
         t_on = time.time()
         e0.record(stream)
-        bm.step(args.steps)
+        bm.step(steps)
         e1.record(stream)
         e1.synchronize()
         t_off = time.time()
     bm.sync()
-    ms_b = e0.elapsed_time(e1) / args.steps
+    ms_b = e0.elapsed_time(e1) / steps
     n_nodes = sum(w.n for w in ws)
     # end to end through the public API: pinned host u and v of all instances in
     # and out every step
     e2e = None
-    if not args.no_e2e:
+    if with_e2e:
         uh = torch.empty((n_nodes, 3), dtype=torch.float64).pin_memory()
         vh = torch.empty((n_nodes, 3), dtype=torch.float64).pin_memory()
         pdgb.pd_get_state(bm.h, uh, vh)
-        k_e2e = max(3, min(args.steps, 50))
+        k_e2e = max(3, min(steps, 50))
         for _ in range(2):
             pdgb.pd_set_state(bm.h, uh, vh)
             bm.step(1)
@@ -577,23 +634,14 @@ def run_batch(args):
                "h2d_bytes_per_step": 2 * uh.numel() * 8, "d2h_bytes_per_step": 2 * uh.numel() * 8,
                "steps": k_e2e}
     bm.close()
-    # per-instance loop: one handle per instance, each step launches every instance
-    hs = [pdgb.Model.from_workload(w, precision=args.precision, graph_steps=0,
-                                   stream=stream.cuda_stream) for w in ws]
-    k_loop = max(3, min(args.steps, 20))
-    for m in hs:
-        m.step(2)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(k_loop):
-        for m in hs:
-            pdgb.pd_step(m.h, 1)
-    e1.record(stream)
-    e1.synchronize()
-    ms_l = e0.elapsed_time(e1) / k_loop
-    for m in hs:
-        m.close()
     n_inst = len(ws)
+    # the per-instance loops, each captured in one CUDA graph of GL steps: the
+    # batch's own (general) step kernel, and each instance's best single-model step
+    # (FP32 bars and beams alone are lattice models: the stencil kernel)
+    GL = 10
+    reps = max(1, min(steps, 20) // GL)
+    ms_l, lay_l = loop_graph_ms(pdgb, torch, ws, args.precision, True, stream, GL, reps)
+    ms_ll, lay_ll = loop_graph_ms(pdgb, torch, ws, args.precision, False, stream, GL, reps)
     # roofline: the step's algorithmic bytes over all instances (FP32, FP64), or
     # the double-word step's FP32 operations
     per_bond = DW_BYTES_PER_BOND if args.precision == 48 else BYTES_PER_BOND
@@ -616,7 +664,7 @@ def run_batch(args):
                     "kernel": "k_step_dw (batch, per-node weights)"}
     # the oracle over whole instances, in order, for about 10 s of host time
     cpu = None
-    if not args.no_cpu_baseline:
+    if with_cpu:
         import oracle
         oracle.build()
         done_bonds, el, used = 0, 0.0, 0
@@ -639,24 +687,31 @@ def run_batch(args):
                "kind": "oracle",
                "sample": f"5 oracle FP64 steps of each of the first {used} instances "
                          f"(the per-instance loop), OpenMP on {cores} host threads"}
-    line = {
+    loop_launches = n_inst + n_inst / GL  # per step: a step kernel per instance, an advance per graph
+    return {
         "metric": "bond updates/s", "value": n_bonds / (ms_b * 1e-3), "unit": "bond updates/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
+        "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": ms_b,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {32: "f32", 64: "f64", 48: "f32 double-word"}[args.precision],
         "data": "synthetic",
         "config": {"workload": f"batch of {n_inst} bars and notched beams, "
-                               f"{sum(w.n for w in ws):,} nodes, {n_bonds:,} directed bonds",
+                               f"{n_nodes:,} nodes, {n_bonds:,} directed bonds",
                    "autotuned_launch": {"block_threads": block, "blocks_per_sm": bps}},
         "instance_steps_per_s": n_inst / (ms_b * 1e-3),
         "loop": {"ms_per_step": ms_l, "instance_steps_per_s": n_inst / (ms_l * 1e-3),
-                 "launches_per_step": n_inst, "steps": k_loop},
+                 "launches_per_step": loop_launches, "graph_steps": GL, "steps": reps * GL,
+                 "kernel": "the batch's general step kernel, one handle per instance",
+                 "layouts": lay_l},
         "batched_over_loop": ms_l / ms_b,
+        "loop_single_model_kernels": {
+            "ms_per_step": ms_ll, "instance_steps_per_s": n_inst / (ms_ll * 1e-3),
+            "launches_per_step": loop_launches, "graph_steps": GL, "steps": reps * GL,
+            "kernel": "each instance's own best step (regular-lattice stencil kernel)",
+            "layouts": lay_ll, "batched_over_loop": ms_ll / ms_b},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": args.steps + args.steps // G + (1 if args.steps % G else 0),
+        "gpu_launches": steps + steps // G + (1 if steps % G else 0),
         "clocks": clk.summary(t_on, t_off),
     }
-    print(json.dumps(line), flush=True)
 
 
 def cmod_loss(u, above, below):
@@ -675,10 +730,14 @@ def run_adjoint(args):
     random field) and the edge load: checkpointed forward + reverse sweep (FP64),
     against the plain forward run, central differences on random directions and
     the oracle's reverse mode on a bounded number of steps."""
+    print(json.dumps(measure_adjoint(args, args.steps, args.checkpoint_every, args.fd_directions,
+                                     args.warmup, not args.no_cpu_baseline)), flush=True)
+
+
+def measure_adjoint(args, N, C, fd_directions, warmup, with_cpu):
     import torch
     import paper_2105_04150_gb300 as pdgb
     torch.cuda.set_device(0)
-    N, C = args.steps, args.checkpoint_every
     w = workloads.sensitivity_plate(steps=N)
     c0 = pdgb.pd_micromodulus(w.bulk_modulus, w.horizon)
     stream = torch.cuda.Stream()
@@ -715,7 +774,7 @@ def run_adjoint(args):
             times.update(forward_ms=(t1 - t0) * 1e3, backward_ms=(t2 - t1) * 1e3)
         return L, gc, gl
 
-    for _ in range(max(1, min(args.warmup, 3))):
+    for _ in range(max(1, min(warmup, 3))):
         forward_loss(cb, w.load)
         gradient(cb, w.load)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -741,7 +800,7 @@ def run_adjoint(args):
     rng = np.random.default_rng(2105041506)
     h = 1e-3  # of a direction whose per-bond entries are 0.1 c0: relative changes ~1e-4
     worst = 0.0
-    for _ in range(args.fd_directions):
+    for _ in range(fd_directions):
         r = rng.standard_normal(n_bonds)
         dc = 0.5 * (r + r[rev]) * 0.1 * c0
         dl = rng.standard_normal() * 0.1 * w.load
@@ -751,7 +810,7 @@ def run_adjoint(args):
         worst = max(worst, abs(fd - ana) / abs(ana))
 
     cpu, oracle_check = None, None
-    if not args.no_cpu_baseline:
+    if with_cpu:
         import oracle
         oracle.build()
         om = oracle.Model.from_workload(w, off, idx, c=c0, c_bond=cb)
@@ -786,9 +845,9 @@ def run_adjoint(args):
         launches += nck + 2  # and the gradient merge
     if vv:  # the force pass that forms the full-step velocity the loss reads with u^N
         launches += 1
-    line = {
+    return {
         "metric": "bond updates/s", "value": n_bonds * N / (ms_grad * 1e-3),
-        "unit": "bond updates/s", "n_gpus": 1, "steps": N, "warmup": args.warmup,
+        "unit": "bond updates/s", "n_gpus": 1, "steps": N, "warmup": warmup,
         "ms_per_step": ms_grad / N, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == 64 else "f32 double-word",
         "data": "synthetic",
@@ -800,14 +859,13 @@ def run_adjoint(args):
         "gradient_ms": ms_grad, "gradient_parts_ms": parts, "forward_ms": ms_fwd,
         "adjoint_over_forward": ms_grad / ms_fwd, "bonds_broken": broken,
         "loss": L0, "dL_dload": gl,
-        "fd": {"directions": args.fd_directions, "h_rel": h, "max_rel_err": worst},
+        "fd": {"directions": fd_directions, "h_rel": h, "max_rel_err": worst},
         "oracle_check": oracle_check, "cpu_baseline": cpu,
         "e2e": {"value": n_bonds * N / (ms_grad * 1e-3), "unit": "bond updates/s",
                 "h2d_bytes_per_step": 2 * 24 * w.n / N, "d2h_bytes_per_step": (24 * w.n * 3 +
                                                                              8 * n_bonds) / N},
         "gpu_launches": launches, "clocks": clk.summary(t_on, t_off),
     }
-    print(json.dumps(line), flush=True)
 
 
 def main():

@@ -85,6 +85,8 @@ typedef struct {
     int32_t reorder;      /* 0 = keep the caller's node order (best for lattices given
                              row-major); 1 = sort nodes by horizon-sized cells */
     int32_t integrator;   /* PD_INTEGRATOR_EC (0) or PD_INTEGRATOR_VV (1), see below */
+    int32_t general;      /* 0 = the regular-lattice stencil step where it applies (see
+                             pd_info_t.layout); 1 = always the general sliced-ELL step */
 } pd_config;
 
 /*

@@ -63,7 +63,8 @@ class _Config(ctypes.Structure):
                 ("density", ctypes.c_double), ("check_dt", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("reorder", ctypes.c_int32), ("integrator", ctypes.c_int32)]
+                ("reorder", ctypes.c_int32), ("integrator", ctypes.c_int32),
+                ("general", ctypes.c_int32)]
 
 
 class _Material(ctypes.Structure):
@@ -202,7 +203,7 @@ def pd_create(coords, volumes, horizon: float, *, c: float, sc: float = 0.0,
               graph_steps: int = 0, check_dt: bool = False, device: int = 0, stream=None,
               block_threads: int = 0, blocks_per_sm: int = 0, reorder: int = 0,
               integrator: int = 0, ramp_steps: int = 0, kr: float = 0.0,
-              state_based=None, trilinear=None) -> int:
+              state_based=None, trilinear=None, general: bool = False) -> int:
     """Create a model; returns an opaque handle (int).  See pd.h for the semantics."""
     x, kx = _ptr(coords, np.float64)
     n = (kx.numel() if hasattr(kx, "numel") else kx.size) // 3
@@ -233,7 +234,7 @@ def pd_create(coords, volumes, horizon: float, *, c: float, sc: float = 0.0,
     bc = _Bc(type=bt, disp=bd, force=bf, no_fail=nf, disp_rate=float(disp_rate),
              load=float(load), ramp_steps=int(ramp_steps))
     cfg = _config(precision, graph_steps, dt, damping, density, check_dt, device, stream,
-                  block_threads, blocks_per_sm, reorder, integrator)
+                  block_threads, blocks_per_sm, reorder, integrator, general)
     h = ctypes.c_void_p()
     _check(lib().pd_create(n, x, vol, float(horizon), fo, fi, cp, ncut, ctypes.byref(mat),
                            ctypes.byref(bc), ctypes.byref(cfg), ctypes.byref(h)))
@@ -330,12 +331,12 @@ def pd_set_params(h: int, c: float, sc: float, load: float, disp_rate: float,
 
 
 def _config(precision, graph_steps, dt, damping, density, check_dt, device, stream,
-            block_threads, blocks_per_sm, reorder, integrator=0):
+            block_threads, blocks_per_sm, reorder, integrator=0, general=0):
     return _Config(precision=int(precision), graph_steps=int(graph_steps), dt=float(dt),
                    damping=float(damping), density=float(density), check_dt=int(bool(check_dt)),
                    device=int(device), stream=stream, block_threads=int(block_threads),
                    blocks_per_sm=int(blocks_per_sm), reorder=int(reorder),
-                   integrator=int(integrator))
+                   integrator=int(integrator), general=int(bool(general)))
 
 
 def pd_batch_create(instances, *, dt: float, damping: float, density: float,

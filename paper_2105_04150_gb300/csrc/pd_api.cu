@@ -648,6 +648,7 @@ pd_status check_cfg(const pd_config* cfg)
     if (cfg->reorder != 0 && cfg->reorder != 1) return fail(PD_ERR_ARG, "reorder must be 0 or 1");
     if (cfg->integrator != PD_INTEGRATOR_EC && cfg->integrator != PD_INTEGRATOR_VV)
         return fail(PD_ERR_ARG, "integrator must be PD_INTEGRATOR_EC or PD_INTEGRATOR_VV");
+    if (cfg->general != 0 && cfg->general != 1) return fail(PD_ERR_ARG, "general must be 0 or 1");
     return PD_OK;
 }
 
@@ -757,7 +758,7 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
     // case): lattice node order and the stencil-ordered layout
     h->lattice = cfg->precision == PD_PREC_F32 && h->model == 0 && h->kr < 1.0 &&
                  h->integrator == PD_INTEGRATOR_EC && h->ramp_steps == 0 && d.inst.empty() &&
-                 cfg->reorder == 0 && h->uniform_vol &&
+                 cfg->reorder == 0 && cfg->general == 0 && h->uniform_vol &&
                  detect_lattice(n, d.coords, h->off, h->idx, h->lat, h->perm, h->inv);
     std::vector<int32_t> nbr, sw;
     std::vector<uint32_t> bits;

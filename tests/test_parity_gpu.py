@@ -352,6 +352,31 @@ def test_deterministic_repeat():
         assert np.array_equal(a["u"], b["u"]) and np.array_equal(a["mu"], b["mu"])
 
 
+# ------------------------------------------------------------------ full size, whole runs
+@pytest.fixture(scope="module")
+def beam_full_run():
+    """The 1,009,200-node notched beam (per-bond s_c, 117,707,156 directed bonds)
+    run whole by the oracle for 200 steps from rest: the top-centre strip moves
+    2e-6 m and the first bonds next to it reach s_c and break (40 of them)."""
+    w = workloads.notched_beam()
+    return w, oracle_run(w, 200)
+
+
+@pytest.mark.parametrize("prec", [F64, pdgb.PD_PREC_DW, F32])
+def test_full_size_notched_beam_200_steps(beam_full_run, prec):
+    # the benchmark's workload and launch configuration (graphs of 50 steps);
+    # every node and every bond compared at the bars of the module docstring
+    w, o = beam_full_run
+    assert (o["mu"] == 0).sum() > 10
+    g = gpu_run(w, 200, prec, graph_steps=50)
+    assert g["info"]["n"] == 1009200 and g["info"]["step"] == 200
+    if prec == F32:
+        assert g["info"]["layout"] == pdgb.PD_LAYOUT_LATTICE
+        check_f32(g, o)
+    else:
+        check_f64(g, o)
+
+
 # ------------------------------------------------------------------ full size, sampled
 @pytest.mark.parametrize("prec", [F32, F64])
 def test_full_size_notched_beam_sampled_one_step(prec):
