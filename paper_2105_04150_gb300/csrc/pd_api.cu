@@ -766,8 +766,8 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
         h->Q = kStencilSlots / 32;
         build_layout_stencil(n, h->off, h->idx, h->perm, h->inv, h->lat, nbr, bits, sw, h->cnt);
         const int64_t sy = h->lat.N[2], sx = h->lat.N[1] * h->lat.N[2];
-        // the stencil's reach, and one slice more: a warp walks two slices
-        h->lat_halo = 3 * sx + 3 * sy + 3 + 32;
+        // the stencil's reach: |o_x Sx + o_y Sy + o_z| <= 3 Sx + 3 Sy + 3
+        h->lat_halo = 3 * sx + 3 * sy + 3;
     } else {
         spatial_order(n, d.coords, d.horizon, cfg->reorder, h->perm, h->inv);
         build_layout(n, h->off, h->idx, h->perm, h->inv, h->Q, nbr, bits, sw, h->cnt);
