@@ -594,6 +594,8 @@ def measure_batch(args, steps, warmup, with_cpu, with_e2e):
     G = max(1, min(args.graph_steps, steps))
     bm = pdgb.Model.batch(ws, precision=args.precision, graph_steps=G, stream=stream.cuda_stream)
     n_bonds = bm.info()["n_bonds"]
+    # FP32 batches of lattice models (these bars and beams) run the stencil kernel
+    lat = bm.info()["layout"] == pdgb.PD_LAYOUT_LATTICE
     block, bps = bm.autotune(10)
     bm.step(warmup)
     bm.sync()
@@ -652,7 +654,11 @@ def measure_batch(args, steps, warmup, with_cpu, with_e2e):
                 "frac": achieved / peak, "traffic": None,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                 "algorithmic_bytes_per_launch": alg_bytes,
-                "kernel": f"k_step_{STEP_TAG[args.precision]} (batch)"}
+                "kernel": "k_step_f32_lat (batch)" if lat
+                else f"k_step_{STEP_TAG[args.precision]} (batch)"}
+    if lat:
+        roofline["note"] = ("algorithmic bytes of the stored-family step; the lattice stencil "
+                            "kernel reads no neighbour ids")
     if args.precision == 48:
         tops = DW_FP32_OPS_PER_BOND_NODE_W * n_bonds / (ms_b * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": tops, "peak": FP32_PEAK_TOPS,
@@ -696,6 +702,7 @@ def measure_batch(args, steps, warmup, with_cpu, with_e2e):
         "data": "synthetic",
         "config": {"workload": f"batch of {n_inst} bars and notched beams, "
                                f"{n_nodes:,} nodes, {n_bonds:,} directed bonds",
+                   "layout": "lattice stencil kernel" if lat else "sliced ELL",
                    "autotuned_launch": {"block_threads": block, "blocks_per_sm": bps}},
         "instance_steps_per_s": n_inst / (ms_b * 1e-3),
         "loop": {"ms_per_step": ms_l, "instance_steps_per_s": n_inst / (ms_l * 1e-3),

@@ -179,7 +179,8 @@ struct pd_handle {
     // FP64 displacement and FP32 published records with a halo of lat_halo
     // records on both sides (no rec32 / lo32)
     bool lattice = false;
-    Lattice lat;
+    std::vector<Lattice> lats;      // one per instance (a single model: one)
+    std::vector<int32_t> lat_of;    // batches: the lattice of each library position
     int64_t lat_halo = 0;
     double* lat_u[2] = {nullptr, nullptr};   // u / delta, FP64, 3 per node
     float4* lat_pub[2] = {nullptr, nullptr}; // FP32 copies the neighbours read
@@ -290,9 +291,11 @@ StepArgsF32 args_f32(pd_handle* h, int k)
         a.lat_u[1] = h->lat_u[1];
         a.lat_pub[0] = h->lat_pub[0];
         a.lat_pub[1] = h->lat_pub[1];
-        a.lat_sy = (int32_t)h->lat.N[2];
-        a.lat_sx = (int32_t)(h->lat.N[1] * h->lat.N[2]);
-        const double kap = h->lat.dx / h->delta;
+        // a single model in horizon units; a batch in each instance's lattice
+        // units (kappa = 1; strides and thresholds per instance in itab)
+        a.lat_sy = h->batch ? 0 : (int32_t)h->lats[0].N[2];
+        a.lat_sx = h->batch ? 0 : (int32_t)(h->lats[0].N[1] * h->lats[0].N[2]);
+        const double kap = h->batch ? 1.0 : h->lats[0].dx / h->delta;
         const double f = (1.0 - 2.0 * kGuard) * h->sc_lo;
         for (int c = -3; c <= 3; ++c) {
             a.lat_xi[c + 3] = (float)(kap * c);
@@ -303,6 +306,8 @@ StepArgsF32 args_f32(pd_handle* h, int k)
             a.lat_rxi[j] = make_float4(a.lat_xi[r.x + 3], a.lat_xi[r.y + 3], a.lat_xi2[r.x + 3],
                                        a.lat_xi2[r.y + 3]);
             a.lat_roff[j] = r.x * a.lat_sx + r.y * a.lat_sy;
+            a.lat_rox[j] = r.x;
+            a.lat_roy[j] = r.y;
         }
         for (int q = 0; q <= kStencilR2; ++q) {
             a.lat_q[q] = (float)(kap * kap * q);
@@ -362,6 +367,8 @@ cudaError_t launch_f32(pd_handle* h, const StepArgsF32& a)
 {
     // a regular-lattice model (created only for the Euler-Cromer PMB step with a
     // linear loading ramp and uniform volumes) has the stencil kernel's state
+    if (h->lattice && h->batch)
+        return launch_step_f32_lat_batch(a, h->sc_mode, h->grid, h->block, h->stream);
     if (h->lattice) return launch_step_f32_lat(a, h->sc_mode, h->grid, h->block, h->stream);
     if (h->integ != nullptr) return launch_step_f32_soft(a, h->sc_mode, h->grid, h->block, h->stream);
     if (a.vv || a.ramp_steps > 0 || a.peek)
@@ -371,6 +378,7 @@ cudaError_t launch_f32(pd_handle* h, const StepArgsF32& a)
 
 const void* f32_kernel(pd_handle* h)
 {
+    if (h->lattice && h->batch) return step_f32_kernel_lat_batch(h->sc_mode, h->per_bond_c);
     if (h->lattice) return step_f32_kernel_lat(h->sc_mode, h->per_bond_c);
     return h->integ != nullptr ? step_f32_kernel_soft(h->sc_mode, h->uniform_vol, h->per_bond_c)
                                : step_f32_kernel(h->sc_mode, h->uniform_vol, h->per_bond_c);
@@ -714,6 +722,10 @@ struct ModelDesc {
     int uniform_w = -1;               // batches: 1 if every instance has uniform weights
     std::vector<int32_t> inst, hid;   // batches only
     std::vector<InstParams> itab;
+    // batches whose instances are all regular-lattice models: their lattices
+    // (first = offset in the concatenation) and the lattice order of each
+    std::vector<Lattice> lats;
+    std::vector<int32_t> lat_perm;
 };
 
 pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
@@ -756,18 +768,32 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
 
     // FP32 Euler-Cromer PMB models on a regular lattice (the stencil kernel's
     // case): lattice node order and the stencil-ordered layout
-    h->lattice = cfg->precision == PD_PREC_F32 && h->model == 0 && h->kr < 1.0 &&
-                 h->integrator == PD_INTEGRATOR_EC && h->ramp_steps == 0 && d.inst.empty() &&
-                 cfg->reorder == 0 && cfg->general == 0 && h->uniform_vol &&
-                 detect_lattice(n, d.coords, h->off, h->idx, h->lat, h->perm, h->inv);
+    // (a batch whose instances all are: pd_batch_create found their lattices)
+    if (!d.lats.empty()) {
+        h->lattice = true;
+        h->lats = d.lats;
+        h->perm = d.lat_perm;
+        h->inv.assign(n, 0);
+        for (int64_t p = 0; p < n; ++p) h->inv[h->perm[p]] = (int32_t)p;
+        h->lat_of.resize(n);
+        for (int64_t p = 0; p < n; ++p) h->lat_of[p] = d.inst[h->perm[p]];
+    } else {
+        h->lats.assign(1, Lattice{});
+        h->lattice = cfg->precision == PD_PREC_F32 && h->model == 0 && h->kr < 1.0 &&
+                     h->integrator == PD_INTEGRATOR_EC && h->ramp_steps == 0 && d.inst.empty() &&
+                     cfg->reorder == 0 && cfg->general == 0 && h->uniform_vol &&
+                     detect_lattice(n, d.coords, h->off, h->idx, h->lats[0], h->perm, h->inv);
+    }
     std::vector<int32_t> nbr, sw;
     std::vector<uint32_t> bits;
     if (h->lattice) {
         h->Q = kStencilSlots / 32;
-        build_layout_stencil(n, h->off, h->idx, h->perm, h->inv, h->lat, nbr, bits, sw, h->cnt);
-        const int64_t sy = h->lat.N[2], sx = h->lat.N[1] * h->lat.N[2];
+        build_layout_stencil(n, h->off, h->idx, h->perm, h->inv, h->lats,
+                             h->lat_of.empty() ? nullptr : &h->lat_of, nbr, bits, sw, h->cnt);
         // the stencil's reach: |o_x Sx + o_y Sy + o_z| <= 3 Sx + 3 Sy + 3
-        h->lat_halo = 3 * sx + 3 * sy + 3;
+        h->lat_halo = 0;
+        for (const Lattice& L : h->lats)
+            h->lat_halo = std::max<int64_t>(h->lat_halo, 3 * L.N[1] * L.N[2] + 3 * L.N[2] + 3);
     } else {
         spatial_order(n, d.coords, d.horizon, cfg->reorder, h->perm, h->inv);
         build_layout(n, h->off, h->idx, h->perm, h->inv, h->Q, nbr, bits, sw, h->cnt);
@@ -1115,6 +1141,13 @@ pd_status pd_batch_create(int32_t n_inst, const pd_instance* inst, const pd_conf
     h->off.assign(1, 0);
     h->inst_off.assign(1, 0);
     bool uniform_all = true;  // every instance has uniform volumes
+    // FP32 Euler-Cromer PMB batches whose instances all are regular lattices run
+    // the stencil kernel, each instance in its own lattice units
+    bool all_lattice = cfg->precision == PD_PREC_F32 && inst[0].mat.model == 0 &&
+                       inst[0].mat.kr < 1.0 && cfg->integrator == PD_INTEGRATOR_EC &&
+                       inst[0].bc.ramp_steps == 0 && cfg->reorder == 0 && cfg->general == 0;
+    std::vector<Lattice> lats;
+    std::vector<int32_t> lat_perm;
     for (int32_t b = 0; b < n_inst; ++b) {
         const pd_instance& I = inst[b];
         const int64_t o = h->inst_off.back();
@@ -1126,6 +1159,16 @@ pd_status pd_batch_create(int32_t n_inst, const pd_instance* inst, const pd_conf
             return fail(PD_ERR_ARG, "instance %d: %s", b, msg.c_str());
         }
         apply_cuts(I.n, I.coords, I.cuts, I.n_cuts, off, idx);
+        if (all_lattice) {
+            Lattice L;
+            std::vector<int32_t> pb, ib;
+            all_lattice = detect_lattice(I.n, I.coords, off, idx, L, pb, ib);
+            if (all_lattice) {
+                L.first = o;
+                lats.push_back(L);
+                for (int32_t q : pb) lat_perm.push_back((int32_t)(q + o));
+            }
+        }
         if (cfg->check_dt && I.mat.model == 1) {
             // the state-based weights are plain volumes: bound each instance with
             // its own PMB-equivalent micromodulus, as for a single model
@@ -1171,6 +1214,16 @@ pd_status pd_batch_create(int32_t n_inst, const pd_instance* inst, const pd_conf
         ip.fast_lo = (float)((1.0 - 2.0 * kGuard) * ip.sc_lo /
                              (inst[0].mat.kr >= 1.0 ? inst[0].mat.kr : 1.0));
         ip.w_const = (float)((I.mat.model == 1 ? 1.0 : I.mat.c) * I.volumes[0]);
+        if (all_lattice) {
+            const Lattice& L = lats.back();
+            const double f = (1.0 - 2.0 * kGuard) * ip.sc_lo;
+            ip.lat_sx = (int32_t)(L.N[1] * L.N[2]);
+            ip.lat_sy = (int32_t)L.N[2];
+            ip.lat_thr_t = (float)(f * (2.0 + f));
+            ip.dtd = (float)(cfg->dt / L.dx);
+            ip.unit = L.dx;
+            ip.inv_unit = 1.0 / L.dx;
+        }
         for (int64_t i = 1; i < I.n && uniform_all; ++i) uniform_all = I.volumes[i] == I.volumes[0];
         h->inst_off.push_back(o + I.n);
     }
@@ -1190,6 +1243,10 @@ pd_status pd_batch_create(int32_t n_inst, const pd_instance* inst, const pd_conf
     d.unit = unit;
     d.horizon = unit;
     d.uniform_w = uniform_all ? 1 : 0;
+    if (all_lattice && uniform_all) {
+        d.lats = lats;
+        d.lat_perm = lat_perm;
+    }
     if ((st = build_device(h, d, cfg)) != PD_OK) {
         h->release();
         delete h;
@@ -1314,7 +1371,8 @@ pd_status pd_get_state(pd_handle* h, double* u, double* v, int64_t* step)
         double* vo = w == 1 ? dst : nullptr;
         if (h->lattice)
             PD_CUDA(launch_get_state_lat(h->lat_u[cur], (const float*)vsrc, h->gid, h->n,
-                                         h->delta, uo, vo, h->stream),
+                                         h->delta, h->batch ? h->inst : nullptr, h->itab, uo,
+                                         vo, h->stream),
                     "get state");
         else if (h->precision == 32)
             PD_CUDA(launch_get_state_f32(h->rec32[cur], h->lo32, (const float*)vsrc, h->gid,
@@ -1370,7 +1428,8 @@ pd_status pd_set_state(pd_handle* h, const double* u, const double* v, int64_t s
     if (src[0] || src[1]) {
         if (h->lattice)
             PD_CUDA(launch_set_state_lat(src[0], src[1], h->gid, h->n, 1.0 / h->delta,
-                                         h->lat_u[cur], h->lat_pub[cur], (float*)h->v, h->stream),
+                                         h->batch ? h->inst : nullptr, h->itab, h->lat_u[cur],
+                                         h->lat_pub[cur], (float*)h->v, h->stream),
                     "set state");
         else if (h->precision == 32)
             PD_CUDA(launch_set_state_f32(src[0], src[1], h->gid, h->n, 1.0 / h->delta,
@@ -1535,7 +1594,8 @@ pd_status pd_remove_bonds(pd_handle* h, const int64_t* pairs, int64_t m)
             const int32_t pb = h->inv[(size_t)b];
             int64_t mm = 0;
             if (h->lattice) {  // stencil-ordered layout: the slot of the lattice offset
-                mm = stencil_slot(h->lat, h->inv[(size_t)a], pb);
+                const int64_t pa = h->inv[(size_t)a];
+                mm = stencil_slot(h->lats[h->lat_of.empty() ? 0 : h->lat_of[(size_t)pa]], pa, pb);
             } else {
                 for (const int32_t* q = lo; q < hi; ++q) mm += h->inv[(size_t)*q] < pb ? 1 : 0;
             }

@@ -74,30 +74,35 @@ __global__ void k_set_state_f32(const double* __restrict__ u_in, const double* _
 
 __global__ void k_get_state_lat(const double* __restrict__ ul, const float* __restrict__ v32,
                                 const int32_t* __restrict__ gid, int64_t n, double delta,
-                                double* __restrict__ u_out, double* __restrict__ v_out)
+                                const int32_t* __restrict__ inst,
+                                const InstParams* __restrict__ itab, double* __restrict__ u_out,
+                                double* __restrict__ v_out)
 {
     GRID_STRIDE(e, 3 * n)
     {
         const int64_t p = e / 3;
         const int c = (int)(e - 3 * p);
         const int64_t g = gid[p];
-        if (u_out) u_out[3 * g + c] = ul[e] * delta;
+        const double unit = inst ? itab[inst[p]].unit : delta;
+        if (u_out) u_out[3 * g + c] = ul[e] * unit;
         if (v_out) v_out[3 * g + c] = (double)v32[e];
     }
 }
 
 __global__ void k_set_state_lat(const double* __restrict__ u_in, const double* __restrict__ v_in,
                                 const int32_t* __restrict__ gid, int64_t n, double inv_delta,
-                                double* __restrict__ ul, float4* __restrict__ pub,
-                                float* __restrict__ v32)
+                                const int32_t* __restrict__ inst,
+                                const InstParams* __restrict__ itab, double* __restrict__ ul,
+                                float4* __restrict__ pub, float* __restrict__ v32)
 {
     GRID_STRIDE(p, n)
     {
         const int64_t g = gid[p];
         if (u_in) {
+            const double inv_unit = inst ? itab[inst[p]].inv_unit : inv_delta;
             double u[3];
             for (int c = 0; c < 3; ++c) {
-                u[c] = u_in[3 * g + c] * inv_delta;
+                u[c] = u_in[3 * g + c] * inv_unit;
                 ul[3 * p + c] = u[c];
             }
             pub[p] = make_float4((float)u[0], (float)u[1], (float)u[2], 0.0f);
@@ -282,19 +287,22 @@ cudaError_t launch_set_state_f32(const double* u_in, const double* v_in, const i
 }
 
 cudaError_t launch_get_state_lat(const double* u_lat, const float* v32, const int32_t* gid,
-                                 int64_t n, double delta, double* u_out, double* v_out,
+                                 int64_t n, double delta, const int32_t* inst,
+                                 const InstParams* itab, double* u_out, double* v_out,
                                  cudaStream_t s)
 {
-    k_get_state_lat<<<grid_for(3 * n, 256), 256, 0, s>>>(u_lat, v32, gid, n, delta, u_out, v_out);
+    k_get_state_lat<<<grid_for(3 * n, 256), 256, 0, s>>>(u_lat, v32, gid, n, delta, inst, itab,
+                                                         u_out, v_out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_set_state_lat(const double* u_in, const double* v_in, const int32_t* gid,
-                                 int64_t n, double inv_delta, double* u_lat, float4* pub,
-                                 float* v32, cudaStream_t s)
+                                 int64_t n, double inv_delta, const int32_t* inst,
+                                 const InstParams* itab, double* u_lat, float4* pub, float* v32,
+                                 cudaStream_t s)
 {
-    k_set_state_lat<<<grid_for(n, 256), 256, 0, s>>>(u_in, v_in, gid, n, inv_delta, u_lat, pub,
-                                                     v32);
+    k_set_state_lat<<<grid_for(n, 256), 256, 0, s>>>(u_in, v_in, gid, n, inv_delta, inst, itab,
+                                                     u_lat, pub, v32);
     return cudaGetLastError();
 }
 

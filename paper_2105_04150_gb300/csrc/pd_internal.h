@@ -55,6 +55,12 @@ struct InstParams {
     float pad;
     double sc, sc_lo, sc_hi;
     uint64_t sc_seed;
+    // a batch of regular-lattice models (the stencil kernel): each instance's
+    // state in units of its own spacing dx, its node-order strides
+    int32_t lat_sx, lat_sy;
+    float lat_thr_t;           // fast_lo (2 + fast_lo): s >= fast_lo <=> num >= q lat_thr_t
+    float dtd;                 // dt / dx
+    double unit, inv_unit;     // dx, 1 / dx
 };
 
 // Regular-lattice stencil.  On a cubic lattice of spacing dx with
@@ -203,6 +209,7 @@ struct StepArgsF32 {
     int32_t lat_sx, lat_sy;    // node-order strides of x and y (z: 1)
     float4 lat_rxi[kStencilRows];   // per row (segment order): kappa (o_x, o_y, 2 o_x, 2 o_y)
     int32_t lat_roff[kStencilRows]; // per row: node offset o_x Sx + o_y Sy
+    int32_t lat_rox[kStencilRows], lat_roy[kStencilRows];  // per row: o_x, o_y (batches)
     float lat_xi[7];           // kappa c for c = -3..3 (kappa = dx / delta: xi in horizon units)
     float lat_xi2[7];          // 2 kappa c
     float lat_q[kStencilR2 + 1];    // |xi|^2 = kappa^2 q for q = |o|^2
@@ -399,6 +406,10 @@ const void* step_f32_kernel_ext(int sc_mode, bool uniform_w, bool per_bond_c);
 cudaError_t launch_step_f32_lat(const StepArgsF32& a, int sc_mode, int grid, int block,
                                 cudaStream_t s);
 const void* step_f32_kernel_lat(int sc_mode, bool per_bond_c);
+// the same for a batch of lattice models (pd_step_f32_lat_batch.cu)
+cudaError_t launch_step_f32_lat_batch(const StepArgsF32& a, int sc_mode, int grid, int block,
+                                      cudaStream_t s);
+const void* step_f32_kernel_lat_batch(int sc_mode, bool per_bond_c);
 // bilinear-softening build of the FP32 step kernel (pd_step_f32_soft.cu)
 cudaError_t launch_step_f32_soft(const StepArgsF32& a, int sc_mode, int grid, int block,
                                  cudaStream_t s);
@@ -425,13 +436,16 @@ cudaError_t launch_get_state_f32(const float4* rec, const float4* lo32, const fl
 cudaError_t launch_set_state_f32(const double* u_in, const double* v_in, const int32_t* gid,
                                  int64_t n, double inv_delta, float4* rec, float4* lo32,
                                  float* v32, cudaStream_t s);
-// regular-lattice FP32 models: FP64 displacement (horizon units) and FP32 velocity
+// regular-lattice FP32 models: FP64 displacement (in units of delta, or of each
+// instance's spacing in a batch: inst / itab non-null) and FP32 velocity
 cudaError_t launch_get_state_lat(const double* u_lat, const float* v32, const int32_t* gid,
-                                 int64_t n, double delta, double* u_out, double* v_out,
+                                 int64_t n, double delta, const int32_t* inst,
+                                 const InstParams* itab, double* u_out, double* v_out,
                                  cudaStream_t s);
 cudaError_t launch_set_state_lat(const double* u_in, const double* v_in, const int32_t* gid,
-                                 int64_t n, double inv_delta, double* u_lat, float4* pub,
-                                 float* v32, cudaStream_t s);
+                                 int64_t n, double inv_delta, const int32_t* inst,
+                                 const InstParams* itab, double* u_lat, float4* pub, float* v32,
+                                 cudaStream_t s);
 cudaError_t launch_get_state_f64(const double* rec64, const double* v64, const int32_t* gid,
                                  int64_t n, double* u_out, double* v_out, cudaStream_t s);
 cudaError_t launch_set_state_f64(const double* u_in, const double* v_in, const int32_t* gid,

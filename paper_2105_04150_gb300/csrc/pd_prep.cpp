@@ -317,6 +317,8 @@ const StencilLut& stencil_lut()
 
 int stencil_slot(const Lattice& L, int64_t p, int64_t q)
 {
+    p -= L.first;
+    q -= L.first;
     const int64_t pz = p % L.N[2], py = (p / L.N[2]) % L.N[1], px = p / (L.N[2] * L.N[1]);
     const int64_t qz = q % L.N[2], qy = (q / L.N[2]) % L.N[1], qx = q / (L.N[2] * L.N[1]);
     const int64_t ox = qx - px, oy = qy - py, oz = qz - pz;
@@ -326,9 +328,10 @@ int stencil_slot(const Lattice& L, int64_t p, int64_t q)
 
 void build_layout_stencil(int64_t n, const std::vector<int64_t>& off,
                           const std::vector<int32_t>& idx, const std::vector<int32_t>& perm,
-                          const std::vector<int32_t>& inv, const Lattice& L,
-                          std::vector<int32_t>& nbr, std::vector<uint32_t>& bits,
-                          std::vector<int32_t>& sw, std::vector<int32_t>& cnt)
+                          const std::vector<int32_t>& inv, const std::vector<Lattice>& lats,
+                          const std::vector<int32_t>* lat_of, std::vector<int32_t>& nbr,
+                          std::vector<uint32_t>& bits, std::vector<int32_t>& sw,
+                          std::vector<int32_t>& cnt)
 {
     const int Q = kStencilSlots / 32;
     const int64_t W = 32LL * Q;
@@ -345,6 +348,7 @@ void build_layout_stencil(int64_t n, const std::vector<int64_t>& off,
             for (int64_t k = 0; k < W; ++k) nbr[(g * W + k) * 32 + l] = (int32_t)p;
             if (p >= n) continue;
             const int64_t i = perm[p];
+            const Lattice& L = lats[lat_of ? (*lat_of)[p] : 0];
             for (int64_t k = off[i]; k < off[i + 1]; ++k) {
                 const int32_t q = inv[idx[k]];
                 const int m = stencil_slot(L, p, q);  // detect_lattice checked m >= 0

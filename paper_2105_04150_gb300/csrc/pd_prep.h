@@ -34,20 +34,23 @@ void build_layout(int64_t n, const std::vector<int64_t>& off, const std::vector<
 struct Lattice {
     int64_t N[3] = {0, 0, 0};
     double dx = 0.0;
+    int64_t first = 0;  // position of its first node in the library order (batches)
 };
 bool detect_lattice(int64_t n, const double* x, const std::vector<int64_t>& off,
                     const std::vector<int32_t>& idx, Lattice& L, std::vector<int32_t>& perm,
                     std::vector<int32_t>& inv);
-// Stencil-ordered layout of a lattice model (W = 128 slots, slot m holds
+// Stencil-ordered layout of lattice models (W = 128 slots, slot m holds
 // stencil_offset(m)): absent members and unused slots hold the node itself
-// with flag 0.
+// with flag 0.  lats: one lattice per instance, in library order (a single
+// model: one); lat_of[p]: the lattice of library position p (nullptr: lats[0]).
 void build_layout_stencil(int64_t n, const std::vector<int64_t>& off,
                           const std::vector<int32_t>& idx, const std::vector<int32_t>& perm,
-                          const std::vector<int32_t>& inv, const Lattice& L,
-                          std::vector<int32_t>& nbr, std::vector<uint32_t>& bits,
-                          std::vector<int32_t>& sw, std::vector<int32_t>& cnt);
-// Stencil slot of the bond from lattice node p to q (library positions), -1 if
-// the offset is not a stencil offset.
+                          const std::vector<int32_t>& inv, const std::vector<Lattice>& lats,
+                          const std::vector<int32_t>* lat_of, std::vector<int32_t>& nbr,
+                          std::vector<uint32_t>& bits, std::vector<int32_t>& sw,
+                          std::vector<int32_t>& cnt);
+// Stencil slot of the bond from lattice node p to q (library positions, both in
+// lattice L), -1 if the offset is not a stencil offset.
 int stencil_slot(const Lattice& L, int64_t p, int64_t q);
 // Canonical CSR position of every device slot (-1 for unused slots).  A slot
 // is used when its neighbour differs from the node itself.

@@ -41,13 +41,24 @@
 // num >= fast_lo (2 + fast_lo) L^2, a per-q threshold; candidates are decided
 // after each flag word.  Both directions of a bond do the same operations on
 // negated inputs, so their forces are exact negatives and they break together.
+//
+// Batch build (pd_step_f32_lat_batch.cu, PD_LAT_BATCH): many lattice models in
+// one launch, each instance's state in units of its own spacing (kappa = 1, so
+// the stencil's constants are the same for all), its strides, near-s_c
+// threshold and material taken per node from the instance table.
 #define PD_F32_LAT 1
 #include "pd_step_f32.cu"
 
 #include <utility>
 
+#ifndef PD_LAT_BATCH
+#define PD_LAT_BATCH 0
+#endif
+
 namespace pd {
 namespace {
+
+constexpr bool kLatBatch = PD_LAT_BATCH != 0;
 
 #ifndef PD_LAT_THREADS
 #define PD_LAT_THREADS 256
@@ -115,11 +126,15 @@ __device__ __forceinline__ float3 lat_eta(const LatOwn& i, const float4 j)
 // zero when it breaks.  slot: the bond's index in the per-slot arrays.
 template <int SCM, bool PBC>
 __device__ __noinline__ float3 lat_resolve(const StepArgsF32& a, int cur, int64_t i, int m,
-                                           int64_t slot, bool* broken)
+                                           int64_t slot, int sx, int sy, bool* broken)
 {
     const int ox = c_stencil.o[m][0], oy = c_stencil.o[m][1], oz = c_stencil.o[m][2];
     const int q = c_stencil.o[m][3];
-    const int64_t j = i + (int64_t)ox * a.lat_sx + (int64_t)oy * a.lat_sy + oz;
+    if (!kLatBatch) {  // a single model: its strides are kernel parameters
+        sx = a.lat_sx;
+        sy = a.lat_sy;
+    }
+    const int64_t j = i + (int64_t)ox * sx + (int64_t)oy * sy + oz;
     const double* __restrict__ U = a.lat_u[cur];
     double e64[3];
 #pragma unroll
@@ -131,7 +146,13 @@ __device__ __noinline__ float3 lat_resolve(const StepArgsF32& a, int cur, int64_
     const float y2 = num + a.lat_q[q];
     const float ay = y2 * rsqrt_fast(y2);
     const float D = fmaf(ay, a.lat_q[q], a.lat_l[q] * y2);
-    const double sc = SCM == 1 ? sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i], a.gid[j]) : a.sc;
+    double sc = SCM == 1 ? sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i], a.gid[j]) : a.sc;
+    double unit = a.delta;
+    if (kLatBatch) {  // the instance's own s_c (local ids as keys) and length unit
+        const InstParams& ip = a.itab[a.inst[i]];
+        sc = ip.sc_mode == 1 ? sc_draw(ip.sc_seed, ip.sc_lo, ip.sc_hi, a.hid[i], a.hid[j]) : ip.sc;
+        unit = ip.unit;
+    }
     const float scf = (float)sc;
     // num |y| - s_c D = den |y| (s - s_c): its sign decides, away from s_c
     const float r = fmaf(-scf, D, num * ay);
@@ -143,7 +164,7 @@ __device__ __noinline__ float3 lat_resolve(const StepArgsF32& a, int cur, int64_
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             xv[c] = a.x64[3 * j + c] - a.x64[3 * i + c];
-            y[c] = xv[c] + e64[c] * a.delta;
+            y[c] = xv[c] + e64[c] * unit;
         }
         const double L = sqrt(xv[0] * xv[0] + xv[1] * xv[1] + xv[2] * xv[2]);
         const double Rr = sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
@@ -172,6 +193,8 @@ __device__ __noinline__ float3 lat_resolve(const StepArgsF32& a, int cur, int64_
 // One node's state over its stencil walk.
 struct LatNode {
     LatOwn own;
+    int sx, sy;         // batch: the instance's node-order strides
+    float thr_t;        // batch: its near-s_c threshold per unit q
     int64_t i;
     int64_t slot0;      // index of slot 0 of this node in per-slot arrays
     float fx, fy, fz;
@@ -200,7 +223,7 @@ __device__ __forceinline__ void lat_row_bond(const StepArgsF32& a, float xx, flo
     const float ay = y2 * rsqrt_fast(y2);
     const float D = fmaf(ay, a.lat_q[Q], a.lat_l[Q] * y2);
     const bool alive = (rb >> K) & 1u;
-    const bool cand = num >= a.lat_thr[Q];
+    const bool cand = num >= (kLatBatch ? (float)Q * s.thr_t : a.lat_thr[Q]);
     float coef = num * rcp_fast(D);
     if (PBC) coef *= __ldg(cbrow + 32 * K);
     coef = (alive && !cand) ? coef : 0.0f;
@@ -218,7 +241,8 @@ __device__ __forceinline__ void lat_row_fixed(const StepArgsF32& a, const float4
     constexpr StencilSeg sg = stencil_seg(SG);
     constexpr Off3 o = stencil_row_xy(sg.qxy, sg.row0 + R);
     constexpr int b0 = sg.bit0 + stencil_row_len(sg.qxy) * R;
-    const float4* Prow = Pi + (o.x * a.lat_sx + o.y * a.lat_sy);
+    const float4* Prow = Pi + (kLatBatch ? o.x * s.sx + o.y * s.sy
+                                         : o.x * a.lat_sx + o.y * a.lat_sy);
     const uint32_t rb = s.word[sg.word] >> b0;
     const float* cbrow = PBC ? a.cbond + s.slot0 + 32 * (32 * sg.word + b0) : nullptr;
     uint32_t rp = 0u;
@@ -248,7 +272,9 @@ __device__ __forceinline__ void lat_rows_loop(const StepArgsF32& a, const float4
 #pragma unroll 1
     for (int r = 0; r < sg.nrows; ++r) {
         const float4 xr = a.lat_rxi[sg.first + r];
-        const float4* Prow = Pi + a.lat_roff[sg.first + r];
+        const float4* Prow =
+            Pi + (kLatBatch ? a.lat_rox[sg.first + r] * s.sx + a.lat_roy[sg.first + r] * s.sy
+                            : a.lat_roff[sg.first + r]);
         const int b0 = sg.bit0 + len * r;
         const uint32_t rb = s.word[sg.word] >> b0;
         const float* cbrow = PBC ? a.cbond + s.slot0 + 32 * (32 * sg.word + b0) : nullptr;
@@ -281,7 +307,9 @@ __device__ __forceinline__ void lat_word_end(const StepArgsF32& a, int cur, LatN
         pend &= pend - 1u;
         bool broken;
         const int m = 32 * W + bb;
-        const float3 f = lat_resolve<SCM, PBC>(a, cur, s.i, m, s.slot0 + 32 * m, &broken);
+        const float3 f = lat_resolve<SCM, PBC>(a, cur, s.i, m, s.slot0 + 32 * m,
+                                               kLatBatch ? s.sx : 0, kLatBatch ? s.sy : 0,
+                                               &broken);
         if (broken) {
             nword &= ~(1u << bb);
         } else {
@@ -339,6 +367,12 @@ __global__ void __launch_bounds__(PD_LAT_THREADS, PD_LAT_MIN_BLOCKS)
         LatNode s;
         s.i = (g << 5) + lane;
         s.slot0 = g * 128 * 32 + lane;
+        if (kLatBatch) {
+            const InstParams& ip = a.itab[a.inst[s.i]];
+            s.sx = ip.lat_sx;
+            s.sy = ip.lat_sy;
+            s.thr_t = ip.lat_thr_t;
+        }
         const float4 hi = ld_pub(P + s.i);
         s.own.nxy = make_float2(-hi.x, -hi.y);
         s.own.nz = -hi.z;
@@ -359,7 +393,14 @@ __global__ void __launch_bounds__(PD_LAT_THREADS, PD_LAT_MIN_BLOCKS)
         // (Eq. 8) from the intact-bond count
         const int64_t i = s.i;
         if (i >= a.n) continue;
-        const float wc = a.w_const;
+        float wc = a.w_const, dtd = a.dtd_f;
+        double inv_unit = a.inv_delta;
+        if (kLatBatch) {
+            const InstParams& ip = a.itab[a.inst[i]];
+            wc = ip.w_const;
+            dtd = ip.dtd;
+            inv_unit = ip.inv_unit;
+        }
         const uint32_t cls = a.bcc[i];
         uint32_t mask = 0u;
         const BcClass* bc = nullptr;
@@ -376,11 +417,11 @@ __global__ void __launch_bounds__(PD_LAT_THREADS, PD_LAT_MIN_BLOCKS)
         for (int c = 0; c < 3; ++c) {
             const float vi = a.v[3 * i + c];
             float vn = vi + a.dt_f * (F[c] - a.eta_f * vi) / a.rho_f;
-            un[c] = fma((double)vn, (double)a.dtd_f, U[3 * i + c]);
+            un[c] = fma((double)vn, (double)dtd, U[3 * i + c]);
             if (mask & (1u << c)) {
                 const double s_now = a.disp_rate * (double)step;
                 const double s_next = a.disp_rate * (double)(step + 1);
-                un[c] = bc->disp[c] * s_next * a.inv_delta;
+                un[c] = bc->disp[c] * s_next * inv_unit;
                 vn = (float)(bc->disp[c] * (s_next - s_now) / a.dt);
             }
             finite = finite && isfinite(un[c]);
@@ -397,15 +438,22 @@ __global__ void __launch_bounds__(PD_LAT_THREADS, PD_LAT_MIN_BLOCKS)
 
 }  // namespace
 
-const void* step_f32_kernel_lat(int sc_mode, bool per_bond_c)
+#if PD_LAT_BATCH
+#define PD_LAT_KERNEL_OF step_f32_kernel_lat_batch
+#define PD_LAT_LAUNCH launch_step_f32_lat_batch
+#else
+#define PD_LAT_KERNEL_OF step_f32_kernel_lat
+#define PD_LAT_LAUNCH launch_step_f32_lat
+#endif
+
+const void* PD_LAT_KERNEL_OF(int sc_mode, bool per_bond_c)
 {
     if (per_bond_c)
         return sc_mode == 0 ? (const void*)k_step_f32_lat<0, true> : (const void*)k_step_f32_lat<1, true>;
     return sc_mode == 0 ? (const void*)k_step_f32_lat<0, false> : (const void*)k_step_f32_lat<1, false>;
 }
 
-cudaError_t launch_step_f32_lat(const StepArgsF32& a, int sc_mode, int grid, int block,
-                                cudaStream_t s)
+cudaError_t PD_LAT_LAUNCH(const StepArgsF32& a, int sc_mode, int grid, int block, cudaStream_t s)
 {
     const bool pbc = a.cbond != nullptr;
     if (sc_mode == 0) {

@@ -164,3 +164,81 @@ def test_bond_flags_round_trip_and_cut_in_stencil_order():
     ug, vg = m.state()
     assert rel(ug, u) <= 1e-4 and (m.bonds() != omu).mean() < 1e-3
     m.close()
+
+
+# ------------------------------------------------------------------ batches of lattices
+def _lattice_instances():
+    ws = [workloads.tensile_bar(16, 5, 5, rate=2e-6, steps=80, K=5e9, sc=3e-3),
+          workloads.notched_beam(30, 6, 8, length=0.05, rate=3e-7, steps=80),   # delta = pi dx
+          workloads.tensile_bar(11, 4, 3, rate=3e-6, slab=2, steps=80, K=2e10, sc=2e-3),
+          workloads.cracked_plate_force(14, 10, 3, load=4e11, steps=80),       # body force
+          workloads.tensile_bar(20, 3, 3, rate=4e-6, steps=80, K=8e9, sc=1.5e-3)]
+    for w in ws:
+        w.dt, w.damping, w.density = 1e-7, 2.5e6, 2400.0
+        w.disp_rate, w.load = 1.0, 4e11
+    return ws
+
+
+def test_lattice_batch_matches_oracle_per_instance():
+    # instances of different shapes, spacings and horizons (3.01 dx and pi dx),
+    # per-bond s_c in one of them, a body force in another, concatenated so that
+    # 32-node slices straddle instances: each instance against its own oracle run
+    ws = _lattice_instances()
+    bm = pdgb.Model.batch(ws, precision=F32, graph_steps=16)
+    assert bm.info()["layout"] == LAT
+    off = bm.offsets()
+    bm.step(80)
+    u, v = bm.state()
+    mu = bm.bonds()
+    phi = bm.damage()
+    boff, _ = bm.family()
+    bm.close()
+    broke = 0
+    for k, w in enumerate(ws):
+        o = oracle_run(w, 80)
+        s = slice(off[k], off[k + 1])
+        mk = mu[boff[off[k]]:boff[off[k + 1]]]
+        broke += int((o["mu"] == 0).sum())
+        assert rel(u[s], o["u"]) <= 1e-4, (k, rel(u[s], o["u"]))
+        assert rel(v[s], o["v"]) <= 1e-3, (k, rel(v[s], o["v"]))
+        assert (mk != o["mu"]).mean() < 1e-3
+        phi_own = o["model"].damage(np.ascontiguousarray(mk, dtype=np.uint8))
+        assert np.abs(phi[s] - phi_own).max() <= 1e-5
+    assert broke > 0
+
+
+def test_lattice_batch_only_when_every_instance_is_a_lattice():
+    ws = _lattice_instances()
+    bm = pdgb.Model.batch(ws, precision=F32)
+    assert bm.info()["layout"] == LAT
+    bm.close()
+    j = workloads.tensile_bar(10, 5, 5, rate=1e-6, steps=10)
+    j.coords = workloads.lattice(10, 5, 5, j.dx, jitter=0.2, seed=1)
+    j.dt, j.damping, j.density, j.disp_rate, j.load = 1e-7, 2.5e6, 2400.0, 1.0, 4e11
+    bm = pdgb.Model.batch(ws + [j], precision=F32)
+    assert bm.info()["layout"] == SELL
+    bm.close()
+    bm = pdgb.Model.batch(ws, precision=F64)
+    assert bm.info()["layout"] == SELL
+    bm.close()
+
+
+def test_lattice_batch_bond_flags_and_cuts():
+    # flags read and written in canonical order, and a cut into one instance
+    ws = _lattice_instances()[:3]
+    bm = pdgb.Model.batch(ws, precision=F32)
+    off = bm.offsets()
+    boff, bidx = bm.family()
+    rows = np.repeat(np.arange(int(off[-1])), np.diff(boff))
+    mu = bm.bonds()
+    assert mu.all()
+    k = 1  # the beam: cut the first 20 pairs of its row of node off[1] + 500
+    i = int(off[k]) + 500
+    js = bidx[boff[i]:boff[i + 1]][:20]
+    bm.remove_bonds(np.stack([np.full(len(js), i), js], 1))
+    mu2 = bm.bonds()
+    gone = ((rows == i) & np.isin(bidx, js)) | (np.isin(rows, js) & (bidx == i))
+    assert np.array_equal(mu2 == 0, gone)
+    bm.set_bonds(mu)
+    assert np.array_equal(bm.bonds(), mu)
+    bm.close()
