@@ -187,7 +187,8 @@ typedef struct {
                              cuts; its steps run the lattice stencil kernel (no
                              neighbour ids read; u accumulated in FP64, published to
                              the bond arithmetic rounded to FP32) */
-    int32_t pad0;
+    int32_t step_registers; /* registers per thread of the step kernel the handle
+                               launches (after pd_autotune: the variant it chose) */
 } pd_info_t;
 #define PD_LAYOUT_SELL 0
 #define PD_LAYOUT_LATTICE 1
@@ -465,9 +466,13 @@ pd_status pd_batch_offsets(pd_handle* h, int32_t* n_inst, int64_t* node_offset);
 
 /*
  * pd_autotune - time `trial_steps` steps for each candidate launch shape
- * (threads per block, resident blocks per SM) and keep the fastest.  The model
- * state (u, v, bond flags, step counter) is saved before and restored after,
- * so the simulation is unchanged.  trial_steps in [1, 1000].
+ * (threads per block 128 or 256, resident blocks per SM up to the kernel's
+ * occupancy) and, on lattice models (PD_LAYOUT_LATTICE), for each compiled
+ * register budget of the stencil kernel (64 registers for 4 blocks of 256
+ * threads, 80 for 3), and keep the fastest.  The model state (u, v, bond
+ * flags, step counter) is saved before and restored after, so the simulation
+ * is unchanged.  trial_steps in [1, 1000].  pd_info_t.step_registers tells
+ * the variant kept.
  */
 pd_status pd_autotune(pd_handle* h, int32_t trial_steps, int32_t* block_threads,
                       int32_t* blocks_per_sm);

@@ -93,7 +93,7 @@ class _Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("n_bonds", ctypes.c_int64), ("step", ctypes.c_int64),
                 ("precision", ctypes.c_int32), ("ell_width", ctypes.c_int32),
                 ("device_bytes", ctypes.c_int64), ("layout", ctypes.c_int32),
-                ("pad0", ctypes.c_int32)]
+                ("step_registers", ctypes.c_int32)]
 
 
 _lib = None

@@ -182,6 +182,7 @@ struct pd_handle {
     std::vector<Lattice> lats;      // one per instance (a single model: one)
     std::vector<int32_t> lat_of;    // batches: the lattice of each library position
     int64_t lat_halo = 0;
+    int lat_r80 = 0;                // 1: the stencil kernel built for 80 registers (autotune)
     double* lat_u[2] = {nullptr, nullptr};   // u / delta, FP64, 3 per node
     float4* lat_pub[2] = {nullptr, nullptr}; // FP32 copies the neighbours read
     // batches: instance of each node, instance-local ids, per-instance s_c table
@@ -368,8 +369,12 @@ cudaError_t launch_f32(pd_handle* h, const StepArgsF32& a)
     // a regular-lattice model (created only for the Euler-Cromer PMB step with a
     // linear loading ramp and uniform volumes) has the stencil kernel's state
     if (h->lattice && h->batch)
-        return launch_step_f32_lat_batch(a, h->sc_mode, h->grid, h->block, h->stream);
-    if (h->lattice) return launch_step_f32_lat(a, h->sc_mode, h->grid, h->block, h->stream);
+        return h->lat_r80
+                   ? launch_step_f32_lat_batch_r80(a, h->sc_mode, h->grid, h->block, h->stream)
+                   : launch_step_f32_lat_batch(a, h->sc_mode, h->grid, h->block, h->stream);
+    if (h->lattice)
+        return h->lat_r80 ? launch_step_f32_lat_r80(a, h->sc_mode, h->grid, h->block, h->stream)
+                          : launch_step_f32_lat(a, h->sc_mode, h->grid, h->block, h->stream);
     if (h->integ != nullptr) return launch_step_f32_soft(a, h->sc_mode, h->grid, h->block, h->stream);
     if (a.vv || a.ramp_steps > 0 || a.peek)
         return launch_step_f32_ext(a, h->sc_mode, h->grid, h->block, h->stream);
@@ -378,8 +383,12 @@ cudaError_t launch_f32(pd_handle* h, const StepArgsF32& a)
 
 const void* f32_kernel(pd_handle* h)
 {
-    if (h->lattice && h->batch) return step_f32_kernel_lat_batch(h->sc_mode, h->per_bond_c);
-    if (h->lattice) return step_f32_kernel_lat(h->sc_mode, h->per_bond_c);
+    if (h->lattice && h->batch)
+        return h->lat_r80 ? step_f32_kernel_lat_batch_r80(h->sc_mode, h->per_bond_c)
+                          : step_f32_kernel_lat_batch(h->sc_mode, h->per_bond_c);
+    if (h->lattice)
+        return h->lat_r80 ? step_f32_kernel_lat_r80(h->sc_mode, h->per_bond_c)
+                          : step_f32_kernel_lat(h->sc_mode, h->per_bond_c);
     return h->integ != nullptr ? step_f32_kernel_soft(h->sc_mode, h->uniform_vol, h->per_bond_c)
                                : step_f32_kernel(h->sc_mode, h->uniform_vol, h->per_bond_c);
 }
@@ -1286,7 +1295,13 @@ pd_status pd_get_info(pd_handle* h, pd_info_t* out)
     out->ell_width = 32 * h->Q;
     out->device_bytes = h->device_bytes;
     out->layout = h->lattice ? PD_LAYOUT_LATTICE : PD_LAYOUT_SELL;
-    out->pad0 = 0;
+    out->step_registers = 0;
+    cudaFuncAttributes fa;
+    if (cudaSetDevice(h->device) == cudaSuccess &&
+        cudaFuncGetAttributes(&fa, step_kernel_fn(h)) == cudaSuccess)
+        out->step_registers = fa.numRegs;
+    else
+        cudaGetLastError();
     return PD_OK;
 }
 
@@ -2002,17 +2017,20 @@ pd_status pd_autotune(pd_handle* h, int32_t trial_steps, int32_t* block_threads,
                     "restore state");
         return PD_OK;
     };
-    const int old_block = h->block, old_bps = h->blocks_per_sm;
+    const int old_block = h->block, old_bps = h->blocks_per_sm, old_r80 = h->lat_r80;
     const int64_t step0 = h->step;
     cudaEvent_t e0, e1;
     PD_CUDA(cudaEventCreate(&e0), "event");
     PD_CUDA(cudaEventCreate(&e1), "event");
     float best = 1e30f;
-    int best_block = old_block, best_bps = old_bps;
+    int best_block = old_block, best_bps = old_bps, best_r80 = old_r80;
     pd_status st = PD_OK;
     h->drop_graph();
+    // lattice models: both compiled register budgets of the stencil kernel too
+    for (int r80 = 0; r80 <= (h->lattice ? 1 : 0); ++r80)
     for (int block : {128, 256}) {
         for (int bps = 1; bps <= 16 && st == PD_OK; ++bps) {
+            h->lat_r80 = r80;
             h->block = block;
             if ((st = choose_grid(h, bps)) != PD_OK) break;
             if ((st = restore()) != PD_OK) break;
@@ -2032,6 +2050,7 @@ pd_status pd_autotune(pd_handle* h, int32_t trial_steps, int32_t* block_threads,
                 best = ms;
                 best_block = block;
                 best_bps = bps;
+                best_r80 = r80;
             }
             int occ = 0;
             const void* fn = step_kernel_fn(h);
@@ -2043,6 +2062,7 @@ pd_status pd_autotune(pd_handle* h, int32_t trial_steps, int32_t* block_threads,
     cudaEventDestroy(e1);
     h->block = st == PD_OK ? best_block : old_block;
     h->blocks_per_sm = st == PD_OK ? best_bps : old_bps;
+    h->lat_r80 = st == PD_OK ? best_r80 : old_r80;
     pd_status st2 = choose_grid(h, h->blocks_per_sm);
     pd_status st3 = restore();
     h->step = step0;

@@ -410,6 +410,14 @@ const void* step_f32_kernel_lat(int sc_mode, bool per_bond_c);
 cudaError_t launch_step_f32_lat_batch(const StepArgsF32& a, int sc_mode, int grid, int block,
                                       cudaStream_t s);
 const void* step_f32_kernel_lat_batch(int sc_mode, bool per_bond_c);
+// both allocated for 3 resident blocks (80 registers; pd_step_f32_lat_r80.cu,
+// pd_step_f32_lat_batch_r80.cu), the autotuner's compiled alternative
+cudaError_t launch_step_f32_lat_r80(const StepArgsF32& a, int sc_mode, int grid, int block,
+                                    cudaStream_t s);
+const void* step_f32_kernel_lat_r80(int sc_mode, bool per_bond_c);
+cudaError_t launch_step_f32_lat_batch_r80(const StepArgsF32& a, int sc_mode, int grid, int block,
+                                          cudaStream_t s);
+const void* step_f32_kernel_lat_batch_r80(int sc_mode, bool per_bond_c);
 // bilinear-softening build of the FP32 step kernel (pd_step_f32_soft.cu)
 cudaError_t launch_step_f32_soft(const StepArgsF32& a, int sc_mode, int grid, int block,
                                  cudaStream_t s);

@@ -63,6 +63,9 @@ constexpr bool kLatBatch = PD_LAT_BATCH != 0;
 #ifndef PD_LAT_THREADS
 #define PD_LAT_THREADS 256
 #endif
+// resident blocks of 256 threads per SM the register allocation is made for:
+// 4 (64 registers, the default) or 3 (80 registers, pd_step_f32_lat_r80.cu);
+// pd_autotune times both
 #ifndef PD_LAT_MIN_BLOCKS
 #define PD_LAT_MIN_BLOCKS 4
 #endif
@@ -438,9 +441,16 @@ __global__ void __launch_bounds__(PD_LAT_THREADS, PD_LAT_MIN_BLOCKS)
 
 }  // namespace
 
-#if PD_LAT_BATCH
+// entry points of this build: single model or batch, register budget
+#if PD_LAT_BATCH && PD_LAT_MIN_BLOCKS == 3
+#define PD_LAT_KERNEL_OF step_f32_kernel_lat_batch_r80
+#define PD_LAT_LAUNCH launch_step_f32_lat_batch_r80
+#elif PD_LAT_BATCH
 #define PD_LAT_KERNEL_OF step_f32_kernel_lat_batch
 #define PD_LAT_LAUNCH launch_step_f32_lat_batch
+#elif PD_LAT_MIN_BLOCKS == 3
+#define PD_LAT_KERNEL_OF step_f32_kernel_lat_r80
+#define PD_LAT_LAUNCH launch_step_f32_lat_r80
 #else
 #define PD_LAT_KERNEL_OF step_f32_kernel_lat
 #define PD_LAT_LAUNCH launch_step_f32_lat
