@@ -465,7 +465,8 @@ def run_ours(args):
                 else profiled_traffic("lat" if lat else args.precision, args.workload),
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s", "algorithmic_bytes_per_launch": alg_bytes,
-                "kernel": "k_osb32_dilation + k_osb32_force" if osb
+                "kernel": ("k_osb_lat_dilation + k_osb_lat_force" if lat
+                           else "k_osb32_dilation + k_osb32_force") if osb
                 else "k_step_f32_lat" if lat else f"k_step_f{args.precision}"}
     if lat:
         roofline["note"] = ("algorithmic bytes of the stored-family step (4.125 B per directed "

@@ -153,6 +153,8 @@ struct pd_handle {
     float4* osbdw_ab = nullptr;   // double-word state-based: per node alpha~, beta~
     float *osb32_mvol = nullptr, *osb32_theta = nullptr;  // FP32 state-based arrays
     float2* osb32_ab = nullptr;
+    float4* osblat_coef = nullptr;  // FP32 state-based lattice models (pd_step_f32_lat_osb.cu)
+    float4* osblat_rec = nullptr;
     void* wsum_inv = nullptr;
     void* damage = nullptr;
     int* err = nullptr;
@@ -420,6 +422,15 @@ OsbDwArgs osbdw_args(pd_handle* h)
     return o;
 }
 
+OsbLatArgs osblat_args(pd_handle* h)
+{
+    OsbLatArgs o{};
+    o.coef = h->osblat_coef;
+    o.rec = h->osblat_rec;
+    o.theta = h->osb32_theta;
+    return o;
+}
+
 OsbArgs32 osb32_args(pd_handle* h)
 {
     OsbArgs32 o{};
@@ -482,7 +493,10 @@ cudaError_t launch_one(pd_handle* h, int k)
         return launch_step_dw(args_f64(h, k), dw_args(h), h->sc_mode, h->grid, h->block,
                               h->stream);
     if (h->model == 1 && h->precision == 32)
-        return launch_osb32_step(args_f32(h, k), osb32_args(h), h->sc_mode, h->grid_osbf, h->grid_dil, h->block,
+        return h->lattice
+                   ? launch_osb_lat_step(args_f32(h, k), osblat_args(h), h->sc_mode, h->grid,
+                                         h->block, h->stream)
+                   : launch_osb32_step(args_f32(h, k), osb32_args(h), h->sc_mode, h->grid_osbf, h->grid_dil, h->block,
                                  h->stream);
     if (h->model == 1)
         return launch_osb_step(args_f64(h, k), osb_args(h), h->grid, h->block, h->stream);
@@ -508,7 +522,7 @@ pd_status choose_grid(pd_handle* h, int blocks_per_sm)
     h->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * occ, need));
     h->grid_dil = h->grid;
     h->grid_osbf = h->grid;
-    if (h->model == 1 && h->precision == 32) {  // the state-based kernels' own grids
+    if (h->model == 1 && h->precision == 32 && !h->lattice) {  // the state-based kernels' own grids
         auto grid_of_kernel = [&](const void* fn, int& out) -> pd_status {
             PD_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 0),
                     "carveout");
@@ -788,7 +802,8 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
         for (int64_t p = 0; p < n; ++p) h->lat_of[p] = d.inst[h->perm[p]];
     } else {
         h->lats.assign(1, Lattice{});
-        h->lattice = cfg->precision == PD_PREC_F32 && h->model == 0 && h->kr < 1.0 &&
+        h->lattice = cfg->precision == PD_PREC_F32 && (h->model == 0 || h->model == 1) &&
+                     h->kr < 1.0 &&
                      h->integrator == PD_INTEGRATOR_EC && h->ramp_steps == 0 && d.inst.empty() &&
                      cfg->reorder == 0 && cfg->general == 0 && h->uniform_vol &&
                      detect_lattice(n, d.coords, h->off, h->idx, h->lats[0], h->perm, h->inv);
@@ -859,9 +874,15 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
     }
     if (h->model == 1) {
         if (f32) {
-            ALLOC(h->osb32_mvol, float, np);
             ALLOC(h->osb32_theta, float, np);
-            ALLOC(h->osb32_ab, float2, np);
+            if (h->lattice) {
+                ALLOC(h->osblat_coef, float4, np);
+                ALLOC(h->osblat_rec, float4, 2 * (np + 2 * h->lat_halo));
+                h->osblat_rec += 2 * h->lat_halo;
+            } else {
+                ALLOC(h->osb32_mvol, float, np);
+                ALLOC(h->osb32_ab, float2, np);
+            }
         } else if (h->dw) {
             ALLOC(h->osb_mvol, double, np);
             ALLOC(h->osb_theta, double, np);
@@ -1014,7 +1035,29 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
     }
     if ((st = upload_weights(h)) != PD_OK) return st;
     if (h->model == 1 && f32) {  // needs the node weights (volumes)
-        e = launch_osb32_setup(args_f32(h, 0), osb32_args(h), h->stream);
+        if (h->lattice) {
+            // weighted volume m~_i = sum_j |xi~|^2 V_j over the family (lattice: the
+            // offsets' q; uniform volumes) and the per-node coefficients
+            const double kap = h->lats[0].dx / h->delta;
+            std::vector<float4> coef((size_t)np, make_float4(0.f, 0.f, 0.f, 0.f));
+            for (int64_t p = 0; p < n; ++p) {
+                const int64_t i = h->perm[p];
+                double m = 0.0;
+                for (int64_t k = h->off[i]; k < h->off[i + 1]; ++k) {
+                    const int sl = stencil_slot(h->lats[0], p, h->inv[h->idx[k]]);
+                    m += kap * kap * stencil_offset(sl).q * h->vol0;
+                }
+                if (m > 0.0)
+                    coef[p] = make_float4((float)(3.0 / m),
+                                          (float)((3.0 * h->osb_K - 5.0 * h->osb_G) / (h->delta * m)),
+                                          (float)(15.0 * h->osb_G / (h->delta * m)), 0.f);
+            }
+            e = cudaMemcpyAsync(h->osblat_coef, coef.data(), 16 * (size_t)np,
+                                cudaMemcpyHostToDevice, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        } else {
+            e = launch_osb32_setup(args_f32(h, 0), osb32_args(h), h->stream);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "state-based set-up");
     }
     h->blocks_per_sm = cfg->blocks_per_sm;

@@ -301,6 +301,17 @@ cudaError_t launch_osb_dw_setup(const StepArgsF64& a, const OsbDwArgs& o, cudaSt
 cudaError_t launch_osb_dw_step(const StepArgsF64& a, const DwArgs& d, const OsbDwArgs& o, int grid,
                                int block, cudaStream_t s);
 
+// Ordinary state-based arrays of FP32 lattice models (pd_step_f32_lat_osb.cu)
+struct OsbLatArgs {
+    const float4* coef;  // per node {3 / m~, (3K - 5G) / (delta m~), 15 G / (delta m~), 0}
+    float4* rec;         // per node the force loop's record {h, A | B, 0, 0, 0} (zero halo)
+    float* theta;        // per node dilation of the current step
+};
+cudaError_t launch_osb_lat_step(const StepArgsF32& a, const OsbLatArgs& o, int sc_mode, int grid,
+                                int block, cudaStream_t s);
+const void* osb_lat_force_kernel();
+const void* osb_lat_dilation_kernel(int sc_mode);
+
 // Ordinary state-based arrays of FP32 handles (lengths in horizon units;
 // alpha, beta multiplied by delta, see pd_step_f32.cu)
 struct OsbArgs32 {

@@ -54,6 +54,11 @@
 #ifndef PD_LAT_BATCH
 #define PD_LAT_BATCH 0
 #endif
+// State-based build (pd_step_f32_lat_osb.cu): this file's helpers without the
+// bond-based step's entry points.
+#ifndef PD_LAT_OSB
+#define PD_LAT_OSB 0
+#endif
 
 namespace pd {
 namespace {
@@ -123,21 +128,13 @@ __device__ __forceinline__ float3 lat_eta(const LatOwn& i, const float4 j)
     return make_float3(d.x, d.y, j.z + i.nz);
 }
 
-// A bond of slot m whose stretch reached the near-s_c band: the break decision
-// (from the FP64 displacements: in FP32 away from the bond's s_c, the literal
-// FP64 stretch of Eq. 4 near it; then the no-fail rule) and its force term,
-// zero when it breaks.  slot: the bond's index in the per-slot arrays.
-template <int SCM, bool PBC>
-__device__ __noinline__ float3 lat_resolve(const StepArgsF32& a, int cur, int64_t i, int m,
-                                           int64_t slot, int sx, int sy, bool* broken)
+// The break decision of the bond i -> j (offset (ox, oy, oz), q = |o|^2) whose
+// FP32 stretch reached the near-s_c band, from the FP64 displacements: in FP32
+// away from the bond's s_c, with the literal FP64 stretch of Eq. 4 near it; then
+// the no-fail rule.
+__device__ __forceinline__ bool lat_breaks(const StepArgsF32& a, int cur, int64_t i, int64_t j,
+                                           int ox, int oy, int oz, int q, double sc_single)
 {
-    const int ox = c_stencil.o[m][0], oy = c_stencil.o[m][1], oz = c_stencil.o[m][2];
-    const int q = c_stencil.o[m][3];
-    if (!kLatBatch) {  // a single model: its strides are kernel parameters
-        sx = a.lat_sx;
-        sy = a.lat_sy;
-    }
-    const int64_t j = i + (int64_t)ox * sx + (int64_t)oy * sy + oz;
     const double* __restrict__ U = a.lat_u[cur];
     double e64[3];
 #pragma unroll
@@ -149,7 +146,7 @@ __device__ __noinline__ float3 lat_resolve(const StepArgsF32& a, int cur, int64_
     const float y2 = num + a.lat_q[q];
     const float ay = y2 * rsqrt_fast(y2);
     const float D = fmaf(ay, a.lat_q[q], a.lat_l[q] * y2);
-    double sc = SCM == 1 ? sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i], a.gid[j]) : a.sc;
+    double sc = sc_single;
     double unit = a.delta;
     if (kLatBatch) {  // the instance's own s_c (local ids as keys) and length unit
         const InstParams& ip = a.itab[a.inst[i]];
@@ -174,9 +171,29 @@ __device__ __noinline__ float3 lat_resolve(const StepArgsF32& a, int cur, int64_
         brk = (Rr - L) / L >= sc;
     }
     if (brk && a.has_nofail) brk = ((a.bct[a.bcc[i]].mask | a.bct[a.bcc[j]].mask) & 8u) == 0u;
+    return brk;
+}
+
+// A bond of slot m whose stretch reached the near-s_c band: the break decision
+// (lat_breaks) and its force term, zero when it breaks.  slot: the bond's index
+// in the per-slot arrays; sx, sy: a batch instance's strides.
+template <int SCM, bool PBC>
+__device__ __noinline__ float3 lat_resolve(const StepArgsF32& a, int cur, int64_t i, int m,
+                                           int64_t slot, int sx, int sy, bool* broken)
+{
+    const int ox = c_stencil.o[m][0], oy = c_stencil.o[m][1], oz = c_stencil.o[m][2];
+    const int q = c_stencil.o[m][3];
+    if (!kLatBatch) {  // a single model: its strides are kernel parameters
+        sx = a.lat_sx;
+        sy = a.lat_sy;
+    }
+    const int64_t j = i + (int64_t)ox * sx + (int64_t)oy * sy + oz;
+    const double sc = SCM == 1 ? sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i], a.gid[j]) : a.sc;
+    const bool brk = lat_breaks(a, cur, i, j, ox, oy, oz, q, sc);
     *broken = brk;
     if (brk) return make_float3(0.f, 0.f, 0.f);
     // the force term from the published displacements, formed as the fast path does
+    const float xx = a.lat_xi[ox + 3], xy = a.lat_xi[oy + 3], xz = a.lat_xi[oz + 3];
     const float4* __restrict__ P = a.lat_pub[cur];
     const float4 hi = ld_pub(P + i), hj = ld_pub(P + j);
     LatOwn own;
@@ -441,6 +458,7 @@ __global__ void __launch_bounds__(PD_LAT_THREADS, PD_LAT_MIN_BLOCKS)
 
 }  // namespace
 
+#if !PD_LAT_OSB
 // entry points of this build: single model or batch, register budget
 #if PD_LAT_BATCH && PD_LAT_MIN_BLOCKS == 3
 #define PD_LAT_KERNEL_OF step_f32_kernel_lat_batch_r80
@@ -475,5 +493,6 @@ cudaError_t PD_LAT_LAUNCH(const StepArgsF32& a, int sc_mode, int grid, int block
     }
     return cudaGetLastError();
 }
+#endif  // !PD_LAT_OSB
 
 }  // namespace pd

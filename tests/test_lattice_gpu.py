@@ -242,3 +242,59 @@ def test_lattice_batch_bond_flags_and_cuts():
     bm.set_bonds(mu)
     assert np.array_equal(bm.bonds(), mu)
     bm.close()
+
+
+# ------------------------------------------------------------------ state-based on a lattice
+def _moduli(K, nu):
+    return (K, 3.0 * K * (1.0 - 2.0 * nu) / (2.0 * (1.0 + nu)))
+
+
+@pytest.mark.parametrize("nu", [0.25, 0.33])
+def test_state_based_lattice_matches_oracle_and_general_kernel(nu):
+    # the two stencil loops (dilation, force) against the oracle's two loops, and
+    # the general state-based kernels (general = 1) on the same model.  As for
+    # every FP32 fracture run (R13), u is compared early in the fracture (50
+    # steps: 11k-15k bonds broken) and the broken set later: on this beam with
+    # nu = 0.33 both FP32 kernels separate from the oracle once fracture runs
+    # (lattice from about step 100, general from 125), through breaks that move
+    # by a step; nu = 0.25 (no dilation term: 3K = 5G) stays at ~1e-7 to step 150.
+    w = workloads.notched_beam(36, 8, 9, length=0.06, rate=2e-7, steps=50)
+    w.state_based = _moduli(w.bulk_modulus, nu)
+    o = oracle_run(w, w.steps)
+    assert (o["mu"] == 0).sum() > 5000
+    g = gpu_run(w, w.steps, F32, graph_steps=10)
+    assert g["info"]["layout"] == LAT
+    check_f32(g, o)
+    b = gpu_run(w, w.steps, F32, general=True)
+    assert b["info"]["layout"] == SELL
+    check_f32(b, o)
+    o = oracle_run(w, 150)
+    for kw in ({}, {"general": True}):
+        g = gpu_run(w, 150, F32, **kw)
+        assert (g["mu"] != o["mu"]).mean() < 1e-3
+        if nu == 0.25:
+            check_f32(g, o)
+
+
+def test_state_based_lattice_tensile_bar():
+    # u before the first breaks (400 steps), the broken set after 1000 (R13)
+    w = workloads.tensile_bar(steps=1000)
+    w.state_based = _moduli(w.bulk_modulus, 0.3)
+    o = oracle_run(w, 400)
+    assert (o["mu"] == 0).sum() == 0
+    g = gpu_run(w, 400, F32, graph_steps=16)
+    assert g["info"]["layout"] == LAT
+    check_f32(g, o)
+    o = oracle_run(w, 1000)
+    g = gpu_run(w, 1000, F32, graph_steps=16)
+    assert (o["mu"] == 0).sum() > 0 and (g["mu"] != o["mu"]).mean() < 1e-3
+
+
+def test_state_based_lattice_short_axes_random_state():
+    w = workloads.tensile_bar(13, 5, 4, rate=3e-7, slab=1, steps=60)
+    w.state_based = _moduli(w.bulk_modulus, 0.3)
+    u0, v0 = workloads.random_state(w.n, 3, 1e-7, 1e-2)
+    o = oracle_run(w, w.steps, u0=u0, v0=v0)
+    g = gpu_run(w, w.steps, F32, u0=u0, v0=v0)
+    assert g["info"]["layout"] == LAT
+    check_f32(g, o)
