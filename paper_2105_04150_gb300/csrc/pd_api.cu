@@ -155,6 +155,7 @@ struct pd_handle {
     float2* osb32_ab = nullptr;
     float4* osblat_coef = nullptr;  // FP32 state-based lattice models (pd_step_f32_lat_osb.cu)
     float4* osblat_rec = nullptr;
+    float* osblat_b = nullptr;
     void* wsum_inv = nullptr;
     void* damage = nullptr;
     int* err = nullptr;
@@ -427,6 +428,7 @@ OsbLatArgs osblat_args(pd_handle* h)
     OsbLatArgs o{};
     o.coef = h->osblat_coef;
     o.rec = h->osblat_rec;
+    o.bco = h->osblat_b;
     o.theta = h->osb32_theta;
     return o;
 }
@@ -877,8 +879,10 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
             ALLOC(h->osb32_theta, float, np);
             if (h->lattice) {
                 ALLOC(h->osblat_coef, float4, np);
-                ALLOC(h->osblat_rec, float4, 2 * (np + 2 * h->lat_halo));
-                h->osblat_rec += 2 * h->lat_halo;
+                ALLOC(h->osblat_rec, float4, np + 2 * h->lat_halo);
+                h->osblat_rec += h->lat_halo;
+                ALLOC(h->osblat_b, float, np + 2 * h->lat_halo);
+                h->osblat_b += h->lat_halo;
             } else {
                 ALLOC(h->osb32_mvol, float, np);
                 ALLOC(h->osb32_ab, float2, np);
@@ -1052,8 +1056,13 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
                                           (float)((3.0 * h->osb_K - 5.0 * h->osb_G) / (h->delta * m)),
                                           (float)(15.0 * h->osb_G / (h->delta * m)), 0.f);
             }
+            std::vector<float> bco((size_t)np);
+            for (int64_t p = 0; p < np; ++p) bco[(size_t)p] = coef[(size_t)p].z;
             e = cudaMemcpyAsync(h->osblat_coef, coef.data(), 16 * (size_t)np,
                                 cudaMemcpyHostToDevice, h->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h->osblat_b, bco.data(), 4 * (size_t)np, cudaMemcpyHostToDevice,
+                                    h->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         } else {
             e = launch_osb32_setup(args_f32(h, 0), osb32_args(h), h->stream);

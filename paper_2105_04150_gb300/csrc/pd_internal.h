@@ -304,7 +304,8 @@ cudaError_t launch_osb_dw_step(const StepArgsF64& a, const DwArgs& d, const OsbD
 // Ordinary state-based arrays of FP32 lattice models (pd_step_f32_lat_osb.cu)
 struct OsbLatArgs {
     const float4* coef;  // per node {3 / m~, (3K - 5G) / (delta m~), 15 G / (delta m~), 0}
-    float4* rec;         // per node the force loop's record {h, A | B, 0, 0, 0} (zero halo)
+    float4* rec;         // per node the force loop's record {h, A} (zero halo)
+    const float* bco;    // per node B = 15 G / (delta m~) (zero halo)
     float* theta;        // per node dilation of the current step
 };
 cudaError_t launch_osb_lat_step(const StepArgsF32& a, const OsbLatArgs& o, int sc_mode, int grid,

@@ -14,7 +14,8 @@
 // Bonds break in the dilation loop (Eq. 6 with s = e / |xi|), with the bond
 // step's near-s_c decision, so a bond that breaks in a step enters neither
 // loop; the dilation kernel also writes the damage (Eq. 8) and, for the
-// force loop, one 32-byte record per node {h, A | B}: one load per neighbour.
+// force loop, a 16-byte record per node {h, A}; B, fixed, is read from a
+// per-node array beside it (16 + 4 bytes per neighbour).
 #define PD_LAT_OSB 1
 #include "pd_step_f32_lat.cu"
 
@@ -67,17 +68,12 @@ __device__ __noinline__ float osb_resolve(const StepArgsF32& a, int cur, int64_t
 // (Prow: published records), 1 the force loop (Prow: 32-byte state-based records)
 template <int KIND, int QXY, int K, int ZX, int ZY>
 __device__ __forceinline__ void osb_row_bond(const StepArgsF32& a, float xx, float xy, float xx2,
-                                             float xy2, const float4* Prow, uint32_t rb,
-                                             uint32_t& rp, OsbNode& s)
+                                             float xy2, const float4* Prow, const float* Brow,
+                                             uint32_t rb, uint32_t& rp, OsbNode& s)
 {
     constexpr int OZ = stencil_row_oz(QXY, K);
     constexpr int Q = QXY + OZ * OZ;
-    float4 h, ab;
-    if constexpr (KIND == 0) {
-        h = ld_pub(Prow + OZ);
-    } else {
-        ld_rec(Prow + 2 * OZ, h, ab);
-    }
+    const float4 h = ld_pub(Prow + OZ);  // dilation: {h, 0}; force: {h, A_j}
     const float3 e = lat_eta(s.own, h);
     const float tx = ZX ? e.x : e.x + xx2;
     const float ty = ZY ? e.y : e.y + xy2;
@@ -94,7 +90,7 @@ __device__ __forceinline__ void osb_row_bond(const StepArgsF32& a, float xx, flo
         s.acc += c;
         rp |= (alive && cand) ? (1u << K) : 0u;
     } else {
-        const float t = (s.A + h.w) * a.lat_l[Q] + (s.B + ab.x) * ext;
+        const float t = (s.A + h.w) * a.lat_l[Q] + (s.B + ld_f32(Brow + OZ)) * ext;
         const float f = alive ? t * ry : 0.0f;
         const float yx = ZX ? e.x : e.x + xx, yy = ZY ? e.y : e.y + xy;
         const float yz = OZ ? e.z + a.lat_xi[OZ + 3] : e.z;
@@ -105,60 +101,65 @@ __device__ __forceinline__ void osb_row_bond(const StepArgsF32& a, float xx, flo
 }
 
 template <int KIND, int SG, int R, int... K>
-__device__ __forceinline__ void osb_row_fixed(const StepArgsF32& a, const float4* Pi, OsbNode& s,
+__device__ __forceinline__ void osb_row_fixed(const StepArgsF32& a, const float4* Pi,
+                                              const float* Bi, OsbNode& s,
                                               std::integer_sequence<int, K...>)
 {
     constexpr StencilSeg sg = stencil_seg(SG);
     constexpr Off3 o = stencil_row_xy(sg.qxy, sg.row0 + R);
     constexpr int b0 = sg.bit0 + stencil_row_len(sg.qxy) * R;
-    constexpr int rs = KIND == 0 ? 1 : 2;  // float4 per record
-    const float4* Prow = Pi + rs * (o.x * a.lat_sx + o.y * a.lat_sy);
+    const int off = o.x * a.lat_sx + o.y * a.lat_sy;
     const uint32_t rb = s.word[sg.word] >> b0;
     uint32_t rp = 0u;
     (osb_row_bond<KIND, sg.qxy, K, o.x == 0, o.y == 0>(a, a.lat_xi[o.x + 3], a.lat_xi[o.y + 3],
                                                        a.lat_xi2[o.x + 3], a.lat_xi2[o.y + 3],
-                                                       Prow, rb, rp, s),
+                                                       Pi + off, KIND == 1 ? Bi + off : nullptr,
+                                                       rb, rp, s),
      ...);
     if (KIND == 0) s.pend |= rp << b0;
 }
 
 template <int KIND, int SG, int... R>
-__device__ __forceinline__ void osb_rows_fixed(const StepArgsF32& a, const float4* Pi, OsbNode& s,
+__device__ __forceinline__ void osb_rows_fixed(const StepArgsF32& a, const float4* Pi,
+                                               const float* Bi, OsbNode& s,
                                                std::integer_sequence<int, R...>)
 {
     (osb_row_fixed<KIND, SG, R>(
-         a, Pi, s, std::make_integer_sequence<int, stencil_row_len(stencil_seg(SG).qxy)>{}),
+         a, Pi, Bi, s, std::make_integer_sequence<int, stencil_row_len(stencil_seg(SG).qxy)>{}),
      ...);
 }
 
 template <int KIND, int SG, int... K>
-__device__ __forceinline__ void osb_rows_loop(const StepArgsF32& a, const float4* Pi, OsbNode& s,
+__device__ __forceinline__ void osb_rows_loop(const StepArgsF32& a, const float4* Pi,
+                                              const float* Bi, OsbNode& s,
                                               std::integer_sequence<int, K...>)
 {
     constexpr StencilSeg sg = stencil_seg(SG);
     constexpr int len = stencil_row_len(sg.qxy);
-    constexpr int rs = KIND == 0 ? 1 : 2;
 #pragma unroll 1
     for (int r = 0; r < sg.nrows; ++r) {
         const float4 xr = a.lat_rxi[sg.first + r];
-        const float4* Prow = Pi + rs * a.lat_roff[sg.first + r];
+        const int off = a.lat_roff[sg.first + r];
         const int b0 = sg.bit0 + len * r;
         const uint32_t rb = s.word[sg.word] >> b0;
         uint32_t rp = 0u;
-        (osb_row_bond<KIND, sg.qxy, K, sg.zx, sg.zy>(a, xr.x, xr.y, xr.z, xr.w, Prow, rb, rp, s),
+        (osb_row_bond<KIND, sg.qxy, K, sg.zx, sg.zy>(a, xr.x, xr.y, xr.z, xr.w, Pi + off,
+                                                     KIND == 1 ? Bi + off : nullptr, rb, rp, s),
          ...);
         if (KIND == 0) s.pend |= rp << b0;
     }
 }
 
 template <int KIND, int SG>
-__device__ __forceinline__ void osb_seg(const StepArgsF32& a, const float4* Pi, OsbNode& s)
+__device__ __forceinline__ void osb_seg(const StepArgsF32& a, const float4* Pi, const float* Bi,
+                                        OsbNode& s)
 {
     constexpr StencilSeg sg = stencil_seg(SG);
     if constexpr (sg.unroll)
-        osb_rows_fixed<KIND, SG>(a, Pi, s, std::make_integer_sequence<int, sg.nrows>{});
+        osb_rows_fixed<KIND, SG>(a, Pi, Bi, s, std::make_integer_sequence<int, sg.nrows>{});
     else
-        osb_rows_loop<KIND, SG>(a, Pi, s, std::make_integer_sequence<int, stencil_row_len(sg.qxy)>{});
+        osb_rows_loop<KIND, SG>(a, Pi, Bi, s,
+                                std::make_integer_sequence<int, stencil_row_len(sg.qxy)>{});
 }
 
 // dilation loop: after flag word W, decide its near-s_c candidates
@@ -184,21 +185,21 @@ __device__ __forceinline__ void osb_word_end(const StepArgsF32& a, int cur, OsbN
 
 template <int KIND, int SCM>
 __device__ __forceinline__ void osb_walk(const StepArgsF32& a, int cur, const float4* Pi,
-                                         OsbNode& s)
+                                         const float* Bi, OsbNode& s)
 {
-    osb_seg<KIND, 0>(a, Pi, s);
-    osb_seg<KIND, 1>(a, Pi, s);
-    osb_seg<KIND, 2>(a, Pi, s);
+    osb_seg<KIND, 0>(a, Pi, Bi, s);
+    osb_seg<KIND, 1>(a, Pi, Bi, s);
+    osb_seg<KIND, 2>(a, Pi, Bi, s);
     if constexpr (KIND == 0) osb_word_end<SCM, 0>(a, cur, s);
-    osb_seg<KIND, 3>(a, Pi, s);
-    osb_seg<KIND, 4>(a, Pi, s);
-    osb_seg<KIND, 5>(a, Pi, s);
+    osb_seg<KIND, 3>(a, Pi, Bi, s);
+    osb_seg<KIND, 4>(a, Pi, Bi, s);
+    osb_seg<KIND, 5>(a, Pi, Bi, s);
     if constexpr (KIND == 0) osb_word_end<SCM, 1>(a, cur, s);
-    osb_seg<KIND, 6>(a, Pi, s);
-    osb_seg<KIND, 7>(a, Pi, s);
-    osb_seg<KIND, 8>(a, Pi, s);
+    osb_seg<KIND, 6>(a, Pi, Bi, s);
+    osb_seg<KIND, 7>(a, Pi, Bi, s);
+    osb_seg<KIND, 8>(a, Pi, Bi, s);
     if constexpr (KIND == 0) osb_word_end<SCM, 2>(a, cur, s);
-    osb_seg<KIND, 9>(a, Pi, s);
+    osb_seg<KIND, 9>(a, Pi, Bi, s);
     if constexpr (KIND == 0) osb_word_end<SCM, 3>(a, cur, s);
 }
 
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(PD_LAT_THREADS, PD_LAT_MIN_BLOCKS)
         s.acc = 0.f;
         s.pend = 0u;
         s.alive = 0;
-        osb_walk<0, SCM>(a, cur, P + s.i, s);
+        osb_walk<0, SCM>(a, cur, P + s.i, nullptr, s);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
             if (s.word[q] != w0[q]) bw[q * 32] = s.word[q];
@@ -236,8 +237,7 @@ __global__ void __launch_bounds__(PD_LAT_THREADS, PD_LAT_MIN_BLOCKS)
         const float4 c = o.coef[i];  // {3 / m~, (3K - 5G) / (delta m~), 15 G / (delta m~)}
         const float theta = c.x * a.w_const * s.acc;
         o.theta[i] = theta;
-        st_rec(o.rec + 2 * i, make_float4(hi.x, hi.y, hi.z, c.y * theta),
-               make_float4(c.z, 0.f, 0.f, 0.f));
+        o.rec[i] = make_float4(hi.x, hi.y, hi.z, c.y * theta);
         const float wi = a.wsum_inv[i];
         const float ws = a.w_const * (float)s.alive;
         a.damage[i] = wi > 0.0f ? fmaxf(0.0f, 1.0f - ws * wi) : 0.0f;
@@ -261,17 +261,16 @@ __global__ void __launch_bounds__(PD_LAT_THREADS, PD_LAT_MIN_BLOCKS)
     for (int64_t g = wid; g < nslices; g += nwarps) {
         OsbNode s;
         s.i = (g << 5) + lane;
-        float4 r0, r1;
-        ld_rec(S + 2 * s.i, r0, r1);
+        const float4 r0 = ld_pub(S + s.i);
         s.own.nxy = make_float2(-r0.x, -r0.y);
         s.own.nz = -r0.z;
         s.A = r0.w;
-        s.B = r1.x;
+        s.B = o.bco[s.i];
         const uint32_t* bw = a.bits + g * 4 * 32 + lane;
 #pragma unroll
         for (int q = 0; q < 4; ++q) s.word[q] = bw[q * 32];
         s.fx = s.fy = s.fz = 0.f;
-        osb_walk<1, 0>(a, cur, S + 2 * s.i, s);
+        osb_walk<1, 0>(a, cur, S + s.i, o.bco + s.i, s);
         const int64_t i = s.i;
         if (i >= a.n) continue;
         const float V = a.w_const;  // the volume (uniform)
