@@ -6,9 +6,11 @@
 Default workload: the notched three-point-bend beam, 300 x 58 x 58 = 1,009,200
 nodes, delta = pi dx, 117.7M directed bonds, per-bond critical stretch, FP32
 bulk arithmetic.  A step is one pass of the whole method over the model (one
-fused kernel launch).  Inputs are resident in HBM when the timed region starts;
-the 517 MB padded family index streamed every step is larger than L2, so no
-flush is needed between steps.  Rank 0 prints one JSON line.
+fused kernel launch).  Inputs are resident in HBM when the timed region starts.
+The beam is a regular lattice, so its step runs the stencil kernel, whose
+per-step footprint (about 120 MB of node state) fits in L2: every step is timed
+alone with CUDA events, and a 516 MB write between the timed intervals flushes
+L2.  Rank 0 prints one JSON line.
 
 Under torchrun (N > 1) every rank advances its own replica of the workload
 (the method has no exchange step on one model: replicas only, weak scaling);
@@ -81,6 +83,54 @@ DW_BYTES_PER_BOND = BYTES_PER_BOND + 8.0
 STEP_SRC = {32: "pd_step_f32.cu", 64: "pd_step_f64.cu", 48: "pd_step_dw.cu",
             "lat": "pd_step_f32_lat.cu"}
 STEP_TAG = {32: "f32", 64: "f64", 48: "dw", "lat": "f32_lat"}
+# Device memory one FP32 lattice step touches per node: FP64 displacement 24 B
+# read + 24 B written (double-buffered), the published record 16 B read + 16 B
+# written, velocity 12 B, bond flags 16 B, BC class 4 B, inverse weight sum 4 B,
+# damage 4 B; the state-based step adds its published record {h, A} 16 B, its
+# per-node coefficients 16 B, B 4 B and theta 4 B.
+LAT_FOOTPRINT_PER_NODE = 120.0
+LAT_OSB_FOOTPRINT_PER_NODE = LAT_FOOTPRINT_PER_NODE + 2 * 16.0 + 8.0
+L2_BYTES = 129e6
+# the L2 flush between timed steps: a write of four times the L2
+FLUSH_BYTES = int(4 * L2_BYTES)
+
+
+def step_footprint(n_nodes, n_bonds, precision, lattice, osb=False):
+    """Bytes of device memory one step touches (node state, and the family where
+    the kernel streams one)."""
+    if lattice:
+        return n_nodes * (LAT_OSB_FOOTPRINT_PER_NODE if osb else LAT_FOOTPRINT_PER_NODE)
+    per_bond = DW_BYTES_PER_BOND if precision == 48 else BYTES_PER_BOND
+    return n_bonds * per_bond + n_nodes * BYTES_PER_NODE[precision]
+
+
+def l2_flush_buffer(torch, device):
+    return torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=device)
+
+
+def timed_steps_flushed(torch, stream, m, steps, flush):
+    """`steps` steps, each timed alone with CUDA events on the launching stream,
+    with an L2 flush (a write of `flush`) between the timed intervals; returns the
+    summed device time in ms.  A device-side sleep first lets the host queue the
+    steps ahead of the device, so that no interval holds host launch latency."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        torch.cuda._sleep(4_000_000)
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            m.step(1)
+            e1.record(stream)
+        ev[-1][1].synchronize()
+    return sum(e0.elapsed_time(e1) for e0, e1 in ev)
+
+
+def l2_flush(torch, stream, flush):
+    """One L2 flush on `stream`, waited for (before a timed leg)."""
+    with torch.cuda.stream(stream):
+        flush.zero_()
+    stream.synchronize()
 
 
 def parse():
@@ -124,6 +174,7 @@ def make_workload(name, shape=None):
 
 
 def describe(w, n_bonds, precision, integrator="ec", lattice=None):
+    osb = getattr(w, "state_based", None) is not None
     return {
         "integrator": {"ec": "damped Euler-Cromer", "vv": "damped velocity-Verlet"}[integrator],
         "ramp_steps": int(getattr(w, "ramp_steps", 0)),
@@ -139,9 +190,10 @@ def describe(w, n_bonds, precision, integrator="ec", lattice=None):
                       48: "fp64-grade: double-word fp32 bonds, fp64 node state"}[precision],
         "n_nodes": w.n,
         "n_bonds": int(n_bonds),
-        "l2_policy": ("inputs larger than L2 (family index > 129 MB streamed per step)"
-                      if 4 * n_bonds > 129e6 else
-                      "inputs smaller than L2, no flush between steps (a parity-size case)"),
+        "l2_policy": (f"L2 flushed between timed steps: a {FLUSH_BYTES / 1e6:.0f} MB write on "
+                      f"the launching stream between per-step CUDA-event intervals (step "
+                      f"footprint {step_footprint(w.n, n_bonds, precision, lattice, osb) / 1e6:.0f}"
+                      f" MB, L2 {L2_BYTES / 1e6:.0f} MB)"),
     }
 
 
@@ -396,26 +448,34 @@ def run_ours(args):
     m.step(args.warmup)
     m.sync()
     barrier(group, dev_sync)
-    with torch.cuda.stream(stream):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        with ClockSampler(local) as clk:
-            time.sleep(0.5)  # let the sampler start
-            barrier(group, dev_sync)
-            t_on = time.time()
+    flush = l2_flush_buffer(torch, local)
+    with ClockSampler(local) as clk:
+        time.sleep(0.5)  # let the sampler start
+        barrier(group, dev_sync)
+        t_on = time.time()
+        ms = timed_steps_flushed(torch, stream, m, args.steps, flush)
+        t_off = time.time()
+        barrier(group, dev_sync)
+        time.sleep(0.25)
+    m.sync()
+    ms_max = aggregate_max(ms, group)
+    # each timed interval: the step's kernels (two passes for the state-based
+    # model) and the step-counter advance
+    launches = args.steps * ((2 if args.state_based is not None else 1) + 1)
+    # context: the same number of steps back to back in CUDA graphs of G steps,
+    # with no flush between them
+    unflushed = None
+    if G > 0:
+        with torch.cuda.stream(stream):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             m.step(args.steps)
             e1.record(stream)
             e1.synchronize()
-            t_off = time.time()
-            barrier(group, dev_sync)
-            time.sleep(0.25)
-    m.sync()
-    ms = e0.elapsed_time(e1)
-    ms_max = aggregate_max(ms, group)
-    n_graph = args.steps // G if G > 0 else 0
-    rem = args.steps - n_graph * G
-    launches = args.steps + n_graph + (1 if rem > 0 else 0)
+        unflushed = {"ms_per_step": e0.elapsed_time(e1) / args.steps, "graph_steps": G,
+                     "note": "the same steps replayed back to back in CUDA graphs, "
+                             "no L2 flush between them (context, not the line's value)"}
 
     # end to end through the public API with pinned host buffers: every step uploads
     # the state (u, v), advances one step and reads the new state back.
@@ -527,6 +587,8 @@ def run_ours(args):
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk.summary(t_on, t_off),
     }
+    if unflushed is not None:
+        line["unflushed_graph_replay"] = unflushed
     if world == 1 and not args.no_outer and args.workload == "beam":
         # the outer-loop forms, measured in the same process: the batched UQ sweep
         # (256 instances) and the sensitivity plate's adjoint (2000 steps,
@@ -704,7 +766,10 @@ def measure_batch(args, steps, warmup, with_cpu, with_e2e):
         "config": {"workload": f"batch of {n_inst} bars and notched beams, "
                                f"{n_nodes:,} nodes, {n_bonds:,} directed bonds",
                    "layout": "lattice stencil kernel" if lat else "sliced ELL",
-                   "autotuned_launch": {"block_threads": block, "blocks_per_sm": bps}},
+                   "autotuned_launch": {"block_threads": block, "blocks_per_sm": bps},
+                   "l2_policy": f"inputs larger than L2 (step footprint "
+                                f"{step_footprint(n_nodes, n_bonds, args.precision, lat) / 1e6:.0f}"
+                                f" MB over all instances, L2 {L2_BYTES / 1e6:.0f} MB)"},
         "instance_steps_per_s": n_inst / (ms_b * 1e-3),
         "loop": {"ms_per_step": ms_l, "instance_steps_per_s": n_inst / (ms_l * 1e-3),
                  "launches_per_step": loop_launches, "graph_steps": GL, "steps": reps * GL,
@@ -767,10 +832,12 @@ def measure_adjoint(args, N, C, fd_directions, warmup, with_cpu):
         m.step(steps)
         return cmod_loss(m.state()[0], above, below)[0]
 
-    def gradient(c_bond, load, steps=N, ck=C, times=None):
+    def gradient(c_bond, load, steps=N, ck=C, times=None, flush=None):
         m.set_params(c0, w.sc, load, w.disp_rate, c_bond)
         m.set_state(zero, zero, step=0)
         m.sync()
+        if flush is not None:
+            l2_flush(torch, stream, flush)
         t0 = time.perf_counter()
         pdgb.pd_adjoint_forward(m.h, steps, ck)
         L, g = cmod_loss(m.state()[0], above, below)
@@ -787,19 +854,21 @@ def measure_adjoint(args, N, C, fd_directions, warmup, with_cpu):
         gradient(cb, w.load)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    flush = l2_flush_buffer(torch, 0)
     with ClockSampler(0) as clk:
         time.sleep(0.5)
         t_on = time.time()
         m.set_params(c0, w.sc, w.load, w.disp_rate, cb)
         m.set_state(zero, zero, step=0)
         m.sync()
+        l2_flush(torch, stream, flush)
         e0.record(stream)
         m.step(N)
         e1.record(stream)
         e1.synchronize()
         ms_fwd = e0.elapsed_time(e1)
         parts = {}
-        L0, gc, gl = gradient(cb, w.load, times=parts)
+        L0, gc, gl = gradient(cb, w.load, times=parts, flush=flush)
         ms_grad = parts["forward_ms"] + parts["backward_ms"]
         t_off = time.time()
     broken = int((m.bonds() == 0).sum())
@@ -863,7 +932,10 @@ def measure_adjoint(args, N, C, fd_directions, warmup, with_cpu):
                                f"gradient of CMOD^2 after {N} steps w.r.t. per-bond stiffness "
                                f"and edge load, checkpoint every {C} steps",
                    "integrator": "damped velocity-Verlet" if vv else "damped Euler-Cromer",
-                   "load": w.load},
+                   "load": w.load,
+                   "l2_policy": "L2 flushed before each timed leg (the forward run and the "
+                                "gradient); within a trajectory the plate's state stays in L2, "
+                                "in both legs alike"},
         "gradient_ms": ms_grad, "gradient_parts_ms": parts, "forward_ms": ms_fwd,
         "adjoint_over_forward": ms_grad / ms_fwd, "bonds_broken": broken,
         "loss": L0, "dL_dload": gl,
