@@ -217,28 +217,33 @@ struct LatNode {
     float thr_t;        // batch: its near-s_c threshold per unit q
     int64_t i;
     int64_t slot0;      // index of slot 0 of this node in per-slot arrays
-    float fx, fy, fz;
+    float2 fxy;         // force sum: (x, y) as one register pair, z alone
+    float fz;
     uint32_t word[4];   // bond flags (stencil slot order)
     uint32_t pend;      // near-s_c candidates of the current flag word
     int alive;          // intact bonds after this step's decisions
 };
 
-// Bond K of a row with q_xy = QXY: o_z = stencil_row_oz(QXY, K); xx, xy and
-// xx2, xy2: xi and 2 xi of the row's o_x, o_y (ZX / ZY: that component is 0);
-// rb: the row's flags from bit 0, rp: the row's near-s_c candidates.
+// Bond K of a row with q_xy = QXY: o_z = stencil_row_oz(QXY, K); xi, xi2: the
+// (x, y) components of xi and 2 xi of the row's o_x, o_y (ZX / ZY: that
+// component is 0); rb: the row's flags from bit 0, rp: the row's near-s_c
+// candidates.  The (x, y) components go through paired FP32 instructions (each
+// half rounded as the scalar operation).
 template <int QXY, int K, int ZX, int ZY, bool PBC>
-__device__ __forceinline__ void lat_row_bond(const StepArgsF32& a, float xx, float xy, float xx2,
-                                             float xy2, const float4* Prow, const float* cbrow,
+__device__ __forceinline__ void lat_row_bond(const StepArgsF32& a, float2 xi, float2 xi2,
+                                             const float4* Prow, const float* cbrow,
                                              uint32_t rb, uint32_t& rp, LatNode& s)
 {
     constexpr int OZ = stencil_row_oz(QXY, K);
     constexpr int Q = QXY + OZ * OZ;
-    const float3 e = lat_eta(s.own, ld_pub(Prow + OZ));
-    const float yx = ZX ? e.x : e.x + xx, tx = ZX ? e.x : e.x + xx2;
-    const float yy = ZY ? e.y : e.y + xy, ty = ZY ? e.y : e.y + xy2;
-    const float yz = OZ ? e.z + a.lat_xi[OZ + 3] : e.z;
-    const float tz = OZ ? e.z + a.lat_xi2[OZ + 3] : e.z;
-    const float num = fmaf(e.x, tx, fmaf(e.y, ty, e.z * tz));
+    const float4 r = ld_pub(Prow + OZ);
+    const float2 exy = __fadd2_rn(make_float2(r.x, r.y), s.own.nxy);
+    const float ez = r.z + s.own.nz;
+    const float2 yxy = (ZX && ZY) ? exy : __fadd2_rn(exy, xi);
+    const float2 txy = (ZX && ZY) ? exy : __fadd2_rn(exy, xi2);
+    const float yz = OZ ? ez + a.lat_xi[OZ + 3] : ez;
+    const float tz = OZ ? ez + a.lat_xi2[OZ + 3] : ez;
+    const float num = fmaf(exy.x, txy.x, fmaf(exy.y, txy.y, ez * tz));
     const float y2 = num + a.lat_q[Q];
     const float ay = y2 * rsqrt_fast(y2);
     const float D = fmaf(ay, a.lat_q[Q], a.lat_l[Q] * y2);
@@ -248,8 +253,7 @@ __device__ __forceinline__ void lat_row_bond(const StepArgsF32& a, float xx, flo
     if (PBC) coef *= __ldg(cbrow + 32 * K);
     coef = (alive && !cand) ? coef : 0.0f;
     rp |= (alive && cand) ? (1u << K) : 0u;
-    s.fx = fmaf(coef, yx, s.fx);
-    s.fy = fmaf(coef, yy, s.fy);
+    s.fxy = __ffma2_rn(make_float2(coef, coef), yxy, s.fxy);
     s.fz = fmaf(coef, yz, s.fz);
 }
 
@@ -266,10 +270,9 @@ __device__ __forceinline__ void lat_row_fixed(const StepArgsF32& a, const float4
     const uint32_t rb = s.word[sg.word] >> b0;
     const float* cbrow = PBC ? a.cbond + s.slot0 + 32 * (32 * sg.word + b0) : nullptr;
     uint32_t rp = 0u;
-    (lat_row_bond<sg.qxy, K, o.x == 0, o.y == 0, PBC>(a, a.lat_xi[o.x + 3], a.lat_xi[o.y + 3],
-                                                      a.lat_xi2[o.x + 3], a.lat_xi2[o.y + 3],
-                                                      Prow, cbrow, rb, rp, s),
-     ...);
+    const float2 xi = make_float2(a.lat_xi[o.x + 3], a.lat_xi[o.y + 3]);
+    const float2 xi2 = make_float2(a.lat_xi2[o.x + 3], a.lat_xi2[o.y + 3]);
+    (lat_row_bond<sg.qxy, K, o.x == 0, o.y == 0, PBC>(a, xi, xi2, Prow, cbrow, rb, rp, s), ...);
     s.pend |= rp << b0;
 }
 
@@ -299,7 +302,8 @@ __device__ __forceinline__ void lat_rows_loop(const StepArgsF32& a, const float4
         const uint32_t rb = s.word[sg.word] >> b0;
         const float* cbrow = PBC ? a.cbond + s.slot0 + 32 * (32 * sg.word + b0) : nullptr;
         uint32_t rp = 0u;
-        (lat_row_bond<sg.qxy, K, sg.zx, sg.zy, PBC>(a, xr.x, xr.y, xr.z, xr.w, Prow, cbrow, rb,
+        (lat_row_bond<sg.qxy, K, sg.zx, sg.zy, PBC>(a, make_float2(xr.x, xr.y),
+                                                    make_float2(xr.z, xr.w), Prow, cbrow, rb,
                                                     rp, s),
          ...);
         s.pend |= rp << b0;
@@ -333,8 +337,8 @@ __device__ __forceinline__ void lat_word_end(const StepArgsF32& a, int cur, LatN
         if (broken) {
             nword &= ~(1u << bb);
         } else {
-            s.fx += f.x;
-            s.fy += f.y;
+            s.fxy.x += f.x;
+            s.fxy.y += f.y;
             s.fz += f.z;
         }
     }
@@ -400,7 +404,8 @@ __global__ void __launch_bounds__(PD_LAT_THREADS, PD_LAT_MIN_BLOCKS)
         uint32_t w0[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) w0[q] = s.word[q] = bw[q * 32];
-        s.fx = s.fy = s.fz = 0.f;
+        s.fxy = make_float2(0.f, 0.f);
+        s.fz = 0.f;
         s.pend = 0u;
         s.alive = 0;
         lat_walk<SCM, PBC>(a, cur, P + s.i, s);
@@ -424,7 +429,7 @@ __global__ void __launch_bounds__(PD_LAT_THREADS, PD_LAT_MIN_BLOCKS)
         const uint32_t cls = a.bcc[i];
         uint32_t mask = 0u;
         const BcClass* bc = nullptr;
-        float F[3] = {wc * s.fx, wc * s.fy, wc * s.fz};
+        float F[3] = {wc * s.fxy.x, wc * s.fxy.y, wc * s.fz};
         if (cls != 0u) {
             bc = a.bct + cls;
             mask = bc->mask;
