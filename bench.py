@@ -714,7 +714,8 @@ def measure_batch(args, steps, warmup, with_cpu, with_e2e):
     peak, peak_kind = hbm_peak()
     achieved = alg_bytes / (ms_b * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": profiled_traffic("lat", "batch") if lat else None,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "kernel": "k_step_f32_lat (batch)" if lat

@@ -27,7 +27,8 @@ struct OsbNode {
     LatOwn own;
     int64_t i;
     float acc;          // dilation: sum |xi~| e~ over intact bonds (x V at the end)
-    float fx, fy, fz;   // force: sum of the bonds' terms (x V at the end)
+    float2 fxy;         // force: sum of the bonds' terms (x V at the end), (x, y) paired
+    float fz;
     float A, B;         // force: the node's own coefficients
     uint32_t word[4];   // bond flags
     uint32_t pend;      // dilation: near-s_c candidates of the current flag word
@@ -65,20 +66,22 @@ __device__ __noinline__ float osb_resolve(const StepArgsF32& a, int cur, int64_t
 }
 
 // Bond K of a row with q_xy = QXY (see lat_row_bond): KIND 0 the dilation loop
-// (Prow: published records), 1 the force loop (Prow: 32-byte state-based records)
+// (Prow: published records), 1 the force loop (Prow: 16-byte state-based records
+// {h, A}, Brow: B); xi, xi2: the (x, y) components of xi and 2 xi of the row,
+// which go through paired FP32 instructions.
 template <int KIND, int QXY, int K, int ZX, int ZY>
-__device__ __forceinline__ void osb_row_bond(const StepArgsF32& a, float xx, float xy, float xx2,
-                                             float xy2, const float4* Prow, const float* Brow,
+__device__ __forceinline__ void osb_row_bond(const StepArgsF32& a, float2 xi, float2 xi2,
+                                             const float4* Prow, const float* Brow,
                                              uint32_t rb, uint32_t& rp, OsbNode& s)
 {
     constexpr int OZ = stencil_row_oz(QXY, K);
     constexpr int Q = QXY + OZ * OZ;
     const float4 h = ld_pub(Prow + OZ);  // dilation: {h, 0}; force: {h, A_j}
-    const float3 e = lat_eta(s.own, h);
-    const float tx = ZX ? e.x : e.x + xx2;
-    const float ty = ZY ? e.y : e.y + xy2;
-    const float tz = OZ ? e.z + a.lat_xi2[OZ + 3] : e.z;
-    const float num = fmaf(e.x, tx, fmaf(e.y, ty, e.z * tz));
+    const float2 exy = __fadd2_rn(make_float2(h.x, h.y), s.own.nxy);
+    const float ez = h.z + s.own.nz;
+    const float2 txy = (ZX && ZY) ? exy : __fadd2_rn(exy, xi2);
+    const float tz = OZ ? ez + a.lat_xi2[OZ + 3] : ez;
+    const float num = fmaf(exy.x, txy.x, fmaf(exy.y, txy.y, ez * tz));
     const float y2 = num + a.lat_q[Q];
     const float ry = rsqrt_fast(y2);
     const float ay = y2 * ry;
@@ -92,10 +95,9 @@ __device__ __forceinline__ void osb_row_bond(const StepArgsF32& a, float xx, flo
     } else {
         const float t = (s.A + h.w) * a.lat_l[Q] + (s.B + ld_f32(Brow + OZ)) * ext;
         const float f = alive ? t * ry : 0.0f;
-        const float yx = ZX ? e.x : e.x + xx, yy = ZY ? e.y : e.y + xy;
-        const float yz = OZ ? e.z + a.lat_xi[OZ + 3] : e.z;
-        s.fx = fmaf(f, yx, s.fx);
-        s.fy = fmaf(f, yy, s.fy);
+        const float2 yxy = (ZX && ZY) ? exy : __fadd2_rn(exy, xi);
+        const float yz = OZ ? ez + a.lat_xi[OZ + 3] : ez;
+        s.fxy = __ffma2_rn(make_float2(f, f), yxy, s.fxy);
         s.fz = fmaf(f, yz, s.fz);
     }
 }
@@ -111,10 +113,10 @@ __device__ __forceinline__ void osb_row_fixed(const StepArgsF32& a, const float4
     const int off = o.x * a.lat_sx + o.y * a.lat_sy;
     const uint32_t rb = s.word[sg.word] >> b0;
     uint32_t rp = 0u;
-    (osb_row_bond<KIND, sg.qxy, K, o.x == 0, o.y == 0>(a, a.lat_xi[o.x + 3], a.lat_xi[o.y + 3],
-                                                       a.lat_xi2[o.x + 3], a.lat_xi2[o.y + 3],
-                                                       Pi + off, KIND == 1 ? Bi + off : nullptr,
-                                                       rb, rp, s),
+    const float2 xi = make_float2(a.lat_xi[o.x + 3], a.lat_xi[o.y + 3]);
+    const float2 xi2 = make_float2(a.lat_xi2[o.x + 3], a.lat_xi2[o.y + 3]);
+    (osb_row_bond<KIND, sg.qxy, K, o.x == 0, o.y == 0>(a, xi, xi2, Pi + off,
+                                                       KIND == 1 ? Bi + off : nullptr, rb, rp, s),
      ...);
     if (KIND == 0) s.pend |= rp << b0;
 }
@@ -143,7 +145,8 @@ __device__ __forceinline__ void osb_rows_loop(const StepArgsF32& a, const float4
         const int b0 = sg.bit0 + len * r;
         const uint32_t rb = s.word[sg.word] >> b0;
         uint32_t rp = 0u;
-        (osb_row_bond<KIND, sg.qxy, K, sg.zx, sg.zy>(a, xr.x, xr.y, xr.z, xr.w, Pi + off,
+        (osb_row_bond<KIND, sg.qxy, K, sg.zx, sg.zy>(a, make_float2(xr.x, xr.y),
+                                                     make_float2(xr.z, xr.w), Pi + off,
                                                      KIND == 1 ? Bi + off : nullptr, rb, rp, s),
          ...);
         if (KIND == 0) s.pend |= rp << b0;
@@ -269,7 +272,8 @@ __global__ void __launch_bounds__(PD_LAT_THREADS, PD_LAT_MIN_BLOCKS)
         const uint32_t* bw = a.bits + g * 4 * 32 + lane;
 #pragma unroll
         for (int q = 0; q < 4; ++q) s.word[q] = bw[q * 32];
-        s.fx = s.fy = s.fz = 0.f;
+        s.fxy = make_float2(0.f, 0.f);
+        s.fz = 0.f;
         osb_walk<1, 0>(a, cur, S + s.i, o.bco + s.i, s);
         const int64_t i = s.i;
         if (i >= a.n) continue;
@@ -277,7 +281,7 @@ __global__ void __launch_bounds__(PD_LAT_THREADS, PD_LAT_MIN_BLOCKS)
         const uint32_t cls = a.bcc[i];
         uint32_t mask = 0u;
         const BcClass* bc = nullptr;
-        float F[3] = {V * s.fx, V * s.fy, V * s.fz};
+        float F[3] = {V * s.fxy.x, V * s.fxy.y, V * s.fz};
         if (cls != 0u) {
             bc = a.bct + cls;
             mask = bc->mask;

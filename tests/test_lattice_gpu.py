@@ -67,10 +67,12 @@ def test_which_models_take_the_lattice_kernel():
     assert _layout(p) == LAT
 
 
-@pytest.mark.parametrize("shape", [(13, 5, 6), (9, 4, 3), (25, 11, 2), (17, 9, 8)])
+@pytest.mark.parametrize("shape", [(13, 5, 6), (9, 4, 3), (25, 11, 2), (17, 9, 8), (25, 11, 3),
+                                   (7, 3, 3)])
 def test_short_axes_and_ragged_slices_match_oracle(shape):
     # Nz < 7: offsets of a warp wrap across several lattice lines; n not a
-    # multiple of 32; a random start state so that every component moves
+    # multiple of 32 (and odd for the last two shapes: 825 and 63 nodes); a
+    # random start state so that every component moves
     w = workloads.tensile_bar(*shape, rate=3e-7, slab=1, steps=80)
     u0, v0 = workloads.random_state(w.n, 7, 1e-7, 1e-2)
     o = oracle_run(w, w.steps, u0=u0, v0=v0)
