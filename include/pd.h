@@ -87,6 +87,14 @@ typedef struct {
     int32_t integrator;   /* PD_INTEGRATOR_EC (0) or PD_INTEGRATOR_VV (1), see below */
     int32_t general;      /* 0 = the regular-lattice stencil step where it applies (see
                              pd_info_t.layout); 1 = always the general sliced-ELL step */
+    int32_t lat_variant;  /* compiled variant of the stencil step (lattice handles; the
+                             same results bit for bit, pd_autotune searches them):
+                             0 = default, records read through L1 (64 registers);
+                             1 = the same for 3 resident blocks (80 registers);
+                             2, 3, 4 = records staged in shared memory by one TMA
+                             bulk tensor copy per block of 16x2x8, 8x4x8 or 32x2x4
+                             nodes (z, y, x), single bond-based models only.
+                             PD_ERR_ARG for other values or models */
 } pd_config;
 
 /*
@@ -189,6 +197,8 @@ typedef struct {
                              the bond arithmetic rounded to FP32) */
     int32_t step_registers; /* registers per thread of the step kernel the handle
                                launches (after pd_autotune: the variant it chose) */
+    int32_t lat_variant;    /* lattice handles: the stencil step's variant in use
+                               (pd_config.lat_variant); else 0 */
 } pd_info_t;
 #define PD_LAYOUT_SELL 0
 #define PD_LAYOUT_LATTICE 1
@@ -467,13 +477,25 @@ pd_status pd_batch_offsets(pd_handle* h, int32_t* n_inst, int64_t* node_offset);
 /*
  * pd_autotune - time `trial_steps` steps for each candidate launch shape
  * (threads per block 128 or 256, resident blocks per SM up to the kernel's
- * occupancy) and, on lattice models (PD_LAYOUT_LATTICE), for each compiled
- * register budget of the stencil kernel (64 registers for 4 blocks of 256
- * threads, 80 for 3), and keep the fastest.  The model state (u, v, bond
+ * occupancy) and, on bond-based lattice models (PD_LAYOUT_LATTICE), for each
+ * compiled variant of the stencil step (pd_config.lat_variant: both register
+ * budgets; on single models also the three shared-memory tile shapes, whose
+ * launch shape is fixed), and keep the fastest.  The model state (u, v, bond
  * flags, step counter) is saved before and restored after, so the simulation
- * is unchanged.  trial_steps in [1, 1000].  pd_info_t.step_registers tells
- * the variant kept.
+ * is unchanged.  trial_steps in [1, 1000].  pd_info_t.step_registers and
+ * pd_info_t.lat_variant tell the variant kept.
  */
+/*
+ * Test hook of the tile step's bounded wait (lat_variant 2..4): the barrier of
+ * every block's tile copy then waits for `bytes` more than the copy delivers,
+ * so the wait runs out (after about 0.5 s, then once more), the block leaves
+ * without updating its nodes and the next synchronising call returns
+ * PD_ERR_TIMEOUT; pd_set_state clears the error.  bytes = 0 restores the step.
+ * PD_ERR_ARG on handles not using the tile step or bytes outside [0, 65536].
+ * Host-only (takes effect from the next step launched).
+ */
+pd_status pd_test_tile_wait_extra(pd_handle* h, int32_t bytes);
+
 pd_status pd_autotune(pd_handle* h, int32_t trial_steps, int32_t* block_threads,
                       int32_t* blocks_per_sm);
 

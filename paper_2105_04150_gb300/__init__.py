@@ -24,7 +24,8 @@ __all__ = [
     "PdError", "build", "lib", "pd_micromodulus", "pd_critical_stretch", "pd_create", "pd_destroy", "pd_last_error",
     "pd_get_info", "pd_get_family", "pd_step", "pd_sync", "pd_get_state", "pd_set_state",
     "pd_get_bonds", "pd_set_bonds", "pd_remove_bonds", "pd_damage", "pd_set_params", "pd_batch_create",
-    "pd_batch_offsets", "pd_autotune", "pd_adjoint_forward", "pd_adjoint_backward",
+    "pd_batch_offsets", "pd_autotune", "pd_test_tile_wait_extra", "pd_adjoint_forward",
+    "pd_adjoint_backward",
     "pd_adjoint_backward_static", "pd_stiffness_factors", "pd_get_bond_integrity", "PD_STIFF_CONICAL",
     "PD_STIFF_SURFACE", "PD_STIFF_PARTIAL", "PD_INTEGRATOR_EC", "PD_INTEGRATOR_VV",
     "PD_LAYOUT_SELL", "PD_LAYOUT_LATTICE",
@@ -64,7 +65,7 @@ class _Config(ctypes.Structure):
                 ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("reorder", ctypes.c_int32), ("integrator", ctypes.c_int32),
-                ("general", ctypes.c_int32)]
+                ("general", ctypes.c_int32), ("lat_variant", ctypes.c_int32)]
 
 
 class _Material(ctypes.Structure):
@@ -93,7 +94,7 @@ class _Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("n_bonds", ctypes.c_int64), ("step", ctypes.c_int64),
                 ("precision", ctypes.c_int32), ("ell_width", ctypes.c_int32),
                 ("device_bytes", ctypes.c_int64), ("layout", ctypes.c_int32),
-                ("step_registers", ctypes.c_int32)]
+                ("step_registers", ctypes.c_int32), ("lat_variant", ctypes.c_int32)]
 
 
 _lib = None
@@ -131,6 +132,7 @@ def lib():
             "pd_batch_create": [I32, P, P, P],
             "pd_batch_offsets": [P, P, P],
             "pd_autotune": [P, I32, P, P],
+            "pd_test_tile_wait_extra": [P, I32],
             "pd_adjoint_forward": [P, I64, I64],
             "pd_adjoint_backward": [P, P, P, P, P, P, P],
             "pd_adjoint_backward_static": [P, P, P, P, P, P, P],
@@ -203,7 +205,8 @@ def pd_create(coords, volumes, horizon: float, *, c: float, sc: float = 0.0,
               graph_steps: int = 0, check_dt: bool = False, device: int = 0, stream=None,
               block_threads: int = 0, blocks_per_sm: int = 0, reorder: int = 0,
               integrator: int = 0, ramp_steps: int = 0, kr: float = 0.0,
-              state_based=None, trilinear=None, general: bool = False) -> int:
+              state_based=None, trilinear=None, general: bool = False,
+              lat_variant: int = 0) -> int:
     """Create a model; returns an opaque handle (int).  See pd.h for the semantics."""
     x, kx = _ptr(coords, np.float64)
     n = (kx.numel() if hasattr(kx, "numel") else kx.size) // 3
@@ -234,7 +237,7 @@ def pd_create(coords, volumes, horizon: float, *, c: float, sc: float = 0.0,
     bc = _Bc(type=bt, disp=bd, force=bf, no_fail=nf, disp_rate=float(disp_rate),
              load=float(load), ramp_steps=int(ramp_steps))
     cfg = _config(precision, graph_steps, dt, damping, density, check_dt, device, stream,
-                  block_threads, blocks_per_sm, reorder, integrator, general)
+                  block_threads, blocks_per_sm, reorder, integrator, general, lat_variant)
     h = ctypes.c_void_p()
     _check(lib().pd_create(n, x, vol, float(horizon), fo, fi, cp, ncut, ctypes.byref(mat),
                            ctypes.byref(bc), ctypes.byref(cfg), ctypes.byref(h)))
@@ -331,12 +334,13 @@ def pd_set_params(h: int, c: float, sc: float, load: float, disp_rate: float,
 
 
 def _config(precision, graph_steps, dt, damping, density, check_dt, device, stream,
-            block_threads, blocks_per_sm, reorder, integrator=0, general=0):
+            block_threads, blocks_per_sm, reorder, integrator=0, general=0, lat_variant=0):
     return _Config(precision=int(precision), graph_steps=int(graph_steps), dt=float(dt),
                    damping=float(damping), density=float(density), check_dt=int(bool(check_dt)),
                    device=int(device), stream=stream, block_threads=int(block_threads),
                    blocks_per_sm=int(blocks_per_sm), reorder=int(reorder),
-                   integrator=int(integrator), general=int(bool(general)))
+                   integrator=int(integrator), general=int(bool(general)),
+                   lat_variant=int(lat_variant))
 
 
 def pd_batch_create(instances, *, dt: float, damping: float, density: float,
@@ -394,8 +398,14 @@ def pd_batch_offsets(h: int) -> np.ndarray:
     return off
 
 
+def pd_test_tile_wait_extra(h: int, nbytes: int):
+    """Test hook of the tile step's bounded wait (see pd.h)."""
+    _check(lib().pd_test_tile_wait_extra(h, int(nbytes)))
+
+
 def pd_autotune(h: int, trial_steps: int = 20):
-    """Pick the fastest (threads per block, blocks per SM); the state is unchanged."""
+    """Pick the fastest (threads per block, blocks per SM and, on lattice models,
+    the stencil step's variant); the state is unchanged."""
     b, s = ctypes.c_int32(), ctypes.c_int32()
     _check(lib().pd_autotune(h, int(trial_steps), ctypes.byref(b), ctypes.byref(s)))
     return b.value, s.value

@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FAST_MATH = {"pd_step_f32.cu", "pd_step_f32_soft.cu", "pd_step_f32_ext.cu",
              "pd_step_f32_osb.cu", "pd_step_f32_lat.cu", "pd_step_f32_lat_batch.cu",
              "pd_step_f32_lat_r80.cu", "pd_step_f32_lat_batch_r80.cu",
-             "pd_step_f32_lat_osb.cu"}
+             "pd_step_f32_lat_osb.cu", "pd_step_f32_lat_tma.cu"}
 
 
 def _nvcc() -> str:

@@ -185,7 +185,9 @@ struct pd_handle {
     std::vector<Lattice> lats;      // one per instance (a single model: one)
     std::vector<int32_t> lat_of;    // batches: the lattice of each library position
     int64_t lat_halo = 0;
-    int lat_r80 = 0;                // 1: the stencil kernel built for 80 registers (autotune)
+    int lat_var = 0;                // the stencil step's variant (pd_config.lat_variant)
+    LatTmaArgs lat_tma{};           // variants 2..4: the tile copies' tensor maps and tiling
+    int lat_tma_shape = -1;         // the box shape lat_tma holds maps for
     double* lat_u[2] = {nullptr, nullptr};   // u / delta, FP64, 3 per node
     float4* lat_pub[2] = {nullptr, nullptr}; // FP32 copies the neighbours read
     // batches: instance of each node, instance-local ids, per-instance s_c table
@@ -371,13 +373,17 @@ cudaError_t launch_f32(pd_handle* h, const StepArgsF32& a)
 {
     // a regular-lattice model (created only for the Euler-Cromer PMB step with a
     // linear loading ramp and uniform volumes) has the stencil kernel's state
+    if (h->lattice && h->lat_var >= 2)
+        return launch_step_f32_lat_tma(a, h->lat_tma, h->lat_var - 2, h->sc_mode, h->grid,
+                                       h->stream);
     if (h->lattice && h->batch)
-        return h->lat_r80
+        return h->lat_var == 1
                    ? launch_step_f32_lat_batch_r80(a, h->sc_mode, h->grid, h->block, h->stream)
                    : launch_step_f32_lat_batch(a, h->sc_mode, h->grid, h->block, h->stream);
     if (h->lattice)
-        return h->lat_r80 ? launch_step_f32_lat_r80(a, h->sc_mode, h->grid, h->block, h->stream)
-                          : launch_step_f32_lat(a, h->sc_mode, h->grid, h->block, h->stream);
+        return h->lat_var == 1
+                   ? launch_step_f32_lat_r80(a, h->sc_mode, h->grid, h->block, h->stream)
+                   : launch_step_f32_lat(a, h->sc_mode, h->grid, h->block, h->stream);
     if (h->integ != nullptr) return launch_step_f32_soft(a, h->sc_mode, h->grid, h->block, h->stream);
     if (a.vv || a.ramp_steps > 0 || a.peek)
         return launch_step_f32_ext(a, h->sc_mode, h->grid, h->block, h->stream);
@@ -386,12 +392,14 @@ cudaError_t launch_f32(pd_handle* h, const StepArgsF32& a)
 
 const void* f32_kernel(pd_handle* h)
 {
+    if (h->lattice && h->lat_var >= 2)
+        return step_f32_kernel_lat_tma(h->lat_var - 2, h->sc_mode, h->per_bond_c);
     if (h->lattice && h->batch)
-        return h->lat_r80 ? step_f32_kernel_lat_batch_r80(h->sc_mode, h->per_bond_c)
-                          : step_f32_kernel_lat_batch(h->sc_mode, h->per_bond_c);
+        return h->lat_var == 1 ? step_f32_kernel_lat_batch_r80(h->sc_mode, h->per_bond_c)
+                               : step_f32_kernel_lat_batch(h->sc_mode, h->per_bond_c);
     if (h->lattice)
-        return h->lat_r80 ? step_f32_kernel_lat_r80(h->sc_mode, h->per_bond_c)
-                          : step_f32_kernel_lat(h->sc_mode, h->per_bond_c);
+        return h->lat_var == 1 ? step_f32_kernel_lat_r80(h->sc_mode, h->per_bond_c)
+                               : step_f32_kernel_lat(h->sc_mode, h->per_bond_c);
     return h->integ != nullptr ? step_f32_kernel_soft(h->sc_mode, h->uniform_vol, h->per_bond_c)
                                : step_f32_kernel(h->sc_mode, h->uniform_vol, h->per_bond_c);
 }
@@ -507,8 +515,76 @@ cudaError_t launch_one(pd_handle* h, int k)
     return launch_step_f64(args_f64(h, k), h->sc_mode, h->grid, h->block, h->stream);
 }
 
+// The tensor maps of the tile step's copies (both record buffers) for box shape
+// `shape`, and its tiling of the lattice.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+pd_status encode_lat_tma(pd_handle* h, int shape)
+{
+    if (h->lat_tma_shape == shape) return PD_OK;
+    static EncodeTiledFn encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return fail(PD_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+        encode = (EncodeTiledFn)fn;
+    }
+    const Lattice& L = h->lats[0];
+    const int64_t nx = L.N[0], ny = L.N[1], nz = L.N[2];
+    const int bz = lat_tma_dim(shape, 0), by = lat_tma_dim(shape, 1), bx = lat_tma_dim(shape, 2);
+    LatTmaArgs t{};
+    t.nz = (int32_t)nz;
+    t.ny = (int32_t)ny;
+    t.nx = (int32_t)nx;
+    t.tiles_z = (int32_t)((nz + bz - 1) / bz);
+    t.tiles_y = (int32_t)((ny + by - 1) / by);
+    t.tiles_x = (int32_t)((nx + bx - 1) / bx);
+    t.extra_tx = h->lat_tma.extra_tx;
+    // records {x, y, z, 0} of node (ix Ny + iy) Nz + iz: the innermost dimension
+    // is the record's 4 floats (16 bytes), then z, y, x
+    const cuuint64_t dims[4] = {4, (cuuint64_t)nz, (cuuint64_t)ny, (cuuint64_t)nx};
+    const cuuint64_t strides[3] = {16, (cuuint64_t)(16 * nz), (cuuint64_t)(16 * nz * ny)};
+    const cuuint32_t box[4] = {4, (cuuint32_t)(bz + 6), (cuuint32_t)(by + 6), (cuuint32_t)(bx + 6)};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    for (int k = 0; k < 2; ++k) {
+        const CUresult r =
+            encode(&t.map[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)h->lat_pub[k], dims,
+                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(PD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    }
+    h->lat_tma = t;
+    h->lat_tma_shape = shape;
+    return PD_OK;
+}
+
 pd_status choose_grid(pd_handle* h, int blocks_per_sm)
 {
+    if (h->lattice && h->lat_var >= 2) {  // the tile step: one block per box of the lattice
+        const int shape = h->lat_var - 2;
+        pd_status st = encode_lat_tma(h, shape);
+        if (st != PD_OK) return st;
+        const void* fn = step_kernel_fn(h);
+        PD_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)lat_tma_smem_bytes(shape)),
+                "shared memory size");
+        PD_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared),
+                "carveout");
+        h->block = lat_tma_dim(shape, 0) * lat_tma_dim(shape, 1) * lat_tma_dim(shape, 2);
+        const int64_t tiles = (int64_t)h->lat_tma.tiles_z * h->lat_tma.tiles_y * h->lat_tma.tiles_x;
+        if (tiles > 0x7fffffff) return fail(PD_ERR_ARG, "lattice too large for the tile step");
+        h->grid = (int)tiles;
+        h->grid_dil = h->grid;
+        h->grid_osbf = h->grid;
+        return PD_OK;
+    }
     int sms = 0;
     PD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "sm count");
     const void* fn = step_kernel_fn(h);
@@ -562,6 +638,8 @@ pd_status check_dev_err(pd_handle* h)
     PD_CUDA(cudaStreamSynchronize(h->stream), "synchronize");
     if (e & PD_DEVERR_NONFINITE)
         return fail(PD_ERR_NONFINITE, "a displacement became non-finite (check dt and loads)");
+    if (e & PD_DEVERR_TIMEOUT)
+        return fail(PD_ERR_TIMEOUT, "a bounded device wait ran out (the tile copy of the step)");
     return PD_OK;
 }
 
@@ -682,6 +760,8 @@ pd_status check_cfg(const pd_config* cfg)
     if (cfg->integrator != PD_INTEGRATOR_EC && cfg->integrator != PD_INTEGRATOR_VV)
         return fail(PD_ERR_ARG, "integrator must be PD_INTEGRATOR_EC or PD_INTEGRATOR_VV");
     if (cfg->general != 0 && cfg->general != 1) return fail(PD_ERR_ARG, "general must be 0 or 1");
+    if (cfg->lat_variant < 0 || cfg->lat_variant > 1 + kLatTmaShapes)
+        return fail(PD_ERR_ARG, "lat_variant must be in [0, %d]", 1 + kLatTmaShapes);
     return PD_OK;
 }
 
@@ -1069,6 +1149,12 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
         }
         if (e != cudaSuccess) return cuda_fail(e, "state-based set-up");
     }
+    if (cfg->lat_variant != 0 && !(h->lattice && h->model == 0))
+        return fail(PD_ERR_ARG, "lat_variant applies to bond-based lattice handles "
+                                "(pd_info_t.layout PD_LAYOUT_LATTICE)");
+    if (cfg->lat_variant >= 2 && h->batch)
+        return fail(PD_ERR_ARG, "the tile step (lat_variant 2..4) takes single models");
+    h->lat_var = cfg->lat_variant;
     h->blocks_per_sm = cfg->blocks_per_sm;
     if ((st = choose_grid(h, h->blocks_per_sm)) != PD_OK) return st;
     e = cudaStreamSynchronize(h->stream);
@@ -1347,6 +1433,7 @@ pd_status pd_get_info(pd_handle* h, pd_info_t* out)
     out->ell_width = 32 * h->Q;
     out->device_bytes = h->device_bytes;
     out->layout = h->lattice ? PD_LAYOUT_LATTICE : PD_LAYOUT_SELL;
+    out->lat_variant = h->lattice ? h->lat_var : 0;
     out->step_registers = 0;
     cudaFuncAttributes fa;
     if (cudaSetDevice(h->device) == cudaSuccess &&
@@ -2014,6 +2101,17 @@ pd_status pd_adjoint_backward(pd_handle* h, const double* dLdu, const double* dL
     return check_dev_err(h);
 }
 
+pd_status pd_test_tile_wait_extra(pd_handle* h, int32_t bytes)
+{
+    if (!h) return fail(PD_ERR_ARG, "NULL handle");
+    if (!(h->lattice && h->lat_var >= 2))
+        return fail(PD_ERR_ARG, "the handle does not use the tile step (lat_variant 2..4)");
+    if (bytes < 0 || bytes > 65536) return fail(PD_ERR_ARG, "bytes must be in [0, 65536]");
+    h->lat_tma.extra_tx = bytes;
+    h->drop_graph();  // captured launches hold the old value
+    return PD_OK;
+}
+
 pd_status pd_autotune(pd_handle* h, int32_t trial_steps, int32_t* block_threads,
                       int32_t* blocks_per_sm)
 {
@@ -2069,20 +2167,24 @@ pd_status pd_autotune(pd_handle* h, int32_t trial_steps, int32_t* block_threads,
                     "restore state");
         return PD_OK;
     };
-    const int old_block = h->block, old_bps = h->blocks_per_sm, old_r80 = h->lat_r80;
+    const int old_block = h->block, old_bps = h->blocks_per_sm, old_var = h->lat_var;
     const int64_t step0 = h->step;
     cudaEvent_t e0, e1;
     PD_CUDA(cudaEventCreate(&e0), "event");
     PD_CUDA(cudaEventCreate(&e1), "event");
     float best = 1e30f;
-    int best_block = old_block, best_bps = old_bps, best_r80 = old_r80;
+    int best_block = old_block, best_bps = old_bps, best_var = old_var;
     pd_status st = PD_OK;
     h->drop_graph();
-    // lattice models: both compiled register budgets of the stencil kernel too
-    for (int r80 = 0; r80 <= (h->lattice ? 1 : 0); ++r80)
+    // bond-based lattice models: the stencil step's compiled variants too (both
+    // register budgets; single models also the shared-memory tile shapes, whose
+    // block and grid are fixed by the shape)
+    const int n_var = !(h->lattice && h->model == 0) ? 1 : h->batch ? 2 : 2 + kLatTmaShapes;
+    for (int var = 0; var < n_var && st == PD_OK; ++var)
     for (int block : {128, 256}) {
+        if (var >= 2 && block != 256) continue;
         for (int bps = 1; bps <= 16 && st == PD_OK; ++bps) {
-            h->lat_r80 = r80;
+            h->lat_var = var;
             h->block = block;
             if ((st = choose_grid(h, bps)) != PD_OK) break;
             if ((st = restore()) != PD_OK) break;
@@ -2102,8 +2204,9 @@ pd_status pd_autotune(pd_handle* h, int32_t trial_steps, int32_t* block_threads,
                 best = ms;
                 best_block = block;
                 best_bps = bps;
-                best_r80 = r80;
+                best_var = var;
             }
+            if (var >= 2) break;  // the tile step's grid does not depend on bps
             int occ = 0;
             const void* fn = step_kernel_fn(h);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block, 0);
@@ -2114,7 +2217,7 @@ pd_status pd_autotune(pd_handle* h, int32_t trial_steps, int32_t* block_threads,
     cudaEventDestroy(e1);
     h->block = st == PD_OK ? best_block : old_block;
     h->blocks_per_sm = st == PD_OK ? best_bps : old_bps;
-    h->lat_r80 = st == PD_OK ? best_r80 : old_r80;
+    h->lat_var = st == PD_OK ? best_var : old_var;
     pd_status st2 = choose_grid(h, h->blocks_per_sm);
     pd_status st3 = restore();
     h->step = step0;

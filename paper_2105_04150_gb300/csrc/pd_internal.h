@@ -34,9 +34,11 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>  // CUtensorMap
 #include <cuda_runtime.h>
 
 #define PD_DEVERR_NONFINITE 1
+#define PD_DEVERR_TIMEOUT 2  // a bounded device wait ran out
 
 namespace pd {
 
@@ -300,6 +302,38 @@ struct OsbDwArgs {
 cudaError_t launch_osb_dw_setup(const StepArgsF64& a, const OsbDwArgs& o, cudaStream_t s);
 cudaError_t launch_osb_dw_step(const StepArgsF64& a, const DwArgs& d, const OsbDwArgs& o, int grid,
                                int block, cudaStream_t s);
+
+// Shared-memory tile step of single bond-based lattice models
+// (pd_step_f32_lat_tma.cu): a block per box of BZ x BY x BX nodes, the box's
+// records and a halo of 3 nodes copied by one tiled bulk tensor copy.  The
+// compiled box shapes (BZ, BY, BX): 0 = (16, 2, 8), 1 = (8, 4, 8), 2 = (32, 2, 4).
+constexpr int kLatTmaShapes = 3;
+__host__ __device__ constexpr int lat_tma_dim(int shape, int axis)
+{
+    constexpr int d[kLatTmaShapes][3] = {{16, 2, 8}, {8, 4, 8}, {32, 2, 4}};
+    return d[shape][axis];
+}
+__host__ __device__ constexpr uint32_t lat_tma_tile_bytes(int bz, int by, int bx)
+{
+    return 16u * (uint32_t)((bz + 6) * (by + 6) * (bx + 6));
+}
+// dynamic shared memory of a block: the tile, 128 bytes to align it, the barrier
+__host__ __device__ constexpr size_t lat_tma_smem_bytes(int shape)
+{
+    return lat_tma_tile_bytes(lat_tma_dim(shape, 0), lat_tma_dim(shape, 1), lat_tma_dim(shape, 2)) +
+           128 + 16;
+}
+struct LatTmaArgs {
+    CUtensorMap map[2];   // the published records of buffer 0 / 1 as the 4-D tensor
+                          // {4 floats, Nz, Ny, Nx}, box {4, BZ + 6, BY + 6, BX + 6}
+    int32_t nz, ny, nx;   // lattice dimensions
+    int32_t tiles_z, tiles_y, tiles_x;
+    int32_t extra_tx;     // bytes the barrier waits for beyond the copy's (0; a test
+                          // sets it to run the bounded wait out)
+};
+const void* step_f32_kernel_lat_tma(int shape, int sc_mode, bool per_bond_c);
+cudaError_t launch_step_f32_lat_tma(const StepArgsF32& a, const LatTmaArgs& t, int shape,
+                                    int sc_mode, int grid, cudaStream_t s);
 
 // Ordinary state-based arrays of FP32 lattice models (pd_step_f32_lat_osb.cu)
 struct OsbLatArgs {

@@ -54,10 +54,11 @@
 #ifndef PD_LAT_BATCH
 #define PD_LAT_BATCH 0
 #endif
-// State-based build (pd_step_f32_lat_osb.cu): this file's helpers without the
-// bond-based step's entry points.
-#ifndef PD_LAT_OSB
-#define PD_LAT_OSB 0
+// Helper builds (the state-based loops, pd_step_f32_lat_osb.cu, and the
+// shared-memory tile step, pd_step_f32_lat_tma.cu): this file's helpers without
+// the bond-based step's entry points.
+#ifndef PD_LAT_HELPERS
+#define PD_LAT_HELPERS 0
 #endif
 
 namespace pd {
@@ -224,19 +225,50 @@ struct LatNode {
     int alive;          // intact bonds after this step's decisions
 };
 
+// Where the walk reads the neighbours' published records.  SrcGlobal: the
+// record array itself (a row of offsets o_x, o_y starts o_x Sx + o_y Sy records
+// from the node's own); SrcTile: a shared-memory copy of the records of a box of
+// the lattice, z fastest, TZ x TY records per x plane (a row starts
+// TZ (o_y + TY o_x) records from the node's own).
+struct SrcGlobal {
+    __device__ static int64_t fixed_row(const StepArgsF32& a, const LatNode& s, int ox, int oy)
+    {
+        return kLatBatch ? (int64_t)(ox * s.sx + oy * s.sy) : (int64_t)(ox * a.lat_sx + oy * a.lat_sy);
+    }
+    __device__ static int64_t loop_row(const StepArgsF32& a, const LatNode& s, int r)
+    {
+        return kLatBatch ? (int64_t)(a.lat_rox[r] * s.sx + a.lat_roy[r] * s.sy)
+                         : (int64_t)a.lat_roff[r];
+    }
+    __device__ static float4 load(const float4* p) { return ld_pub(p); }
+};
+
+template <int TZ, int TY>
+struct SrcTile {
+    __device__ static int fixed_row(const StepArgsF32&, const LatNode&, int ox, int oy)
+    {
+        return TZ * (oy + TY * ox);
+    }
+    __device__ static int loop_row(const StepArgsF32& a, const LatNode&, int r)
+    {
+        return TZ * (a.lat_roy[r] + TY * a.lat_rox[r]);
+    }
+    __device__ static float4 load(const float4* p) { return *p; }
+};
+
 // Bond K of a row with q_xy = QXY: o_z = stencil_row_oz(QXY, K); xi, xi2: the
 // (x, y) components of xi and 2 xi of the row's o_x, o_y (ZX / ZY: that
 // component is 0); rb: the row's flags from bit 0, rp: the row's near-s_c
 // candidates.  The (x, y) components go through paired FP32 instructions (each
 // half rounded as the scalar operation).
-template <int QXY, int K, int ZX, int ZY, bool PBC>
+template <class Src, int QXY, int K, int ZX, int ZY, bool PBC>
 __device__ __forceinline__ void lat_row_bond(const StepArgsF32& a, float2 xi, float2 xi2,
                                              const float4* Prow, const float* cbrow,
                                              uint32_t rb, uint32_t& rp, LatNode& s)
 {
     constexpr int OZ = stencil_row_oz(QXY, K);
     constexpr int Q = QXY + OZ * OZ;
-    const float4 r = ld_pub(Prow + OZ);
+    const float4 r = Src::load(Prow + OZ);
     const float2 exy = __fadd2_rn(make_float2(r.x, r.y), s.own.nxy);
     const float ez = r.z + s.own.nz;
     const float2 yxy = (ZX && ZY) ? exy : __fadd2_rn(exy, xi);
@@ -258,35 +290,35 @@ __device__ __forceinline__ void lat_row_bond(const StepArgsF32& a, float2 xi, fl
 }
 
 // Row R (compile-time) of segment SG, unrolled, its offsets fixed
-template <bool PBC, int SG, int R, int... K>
+template <class Src, bool PBC, int SG, int R, int... K>
 __device__ __forceinline__ void lat_row_fixed(const StepArgsF32& a, const float4* Pi, LatNode& s,
                                               std::integer_sequence<int, K...>)
 {
     constexpr StencilSeg sg = stencil_seg(SG);
     constexpr Off3 o = stencil_row_xy(sg.qxy, sg.row0 + R);
     constexpr int b0 = sg.bit0 + stencil_row_len(sg.qxy) * R;
-    const float4* Prow = Pi + (kLatBatch ? o.x * s.sx + o.y * s.sy
-                                         : o.x * a.lat_sx + o.y * a.lat_sy);
+    const float4* Prow = Pi + Src::fixed_row(a, s, o.x, o.y);
     const uint32_t rb = s.word[sg.word] >> b0;
     const float* cbrow = PBC ? a.cbond + s.slot0 + 32 * (32 * sg.word + b0) : nullptr;
     uint32_t rp = 0u;
     const float2 xi = make_float2(a.lat_xi[o.x + 3], a.lat_xi[o.y + 3]);
     const float2 xi2 = make_float2(a.lat_xi2[o.x + 3], a.lat_xi2[o.y + 3]);
-    (lat_row_bond<sg.qxy, K, o.x == 0, o.y == 0, PBC>(a, xi, xi2, Prow, cbrow, rb, rp, s), ...);
+    (lat_row_bond<Src, sg.qxy, K, o.x == 0, o.y == 0, PBC>(a, xi, xi2, Prow, cbrow, rb, rp, s),
+     ...);
     s.pend |= rp << b0;
 }
 
-template <bool PBC, int SG, int... R>
+template <class Src, bool PBC, int SG, int... R>
 __device__ __forceinline__ void lat_rows_fixed(const StepArgsF32& a, const float4* Pi, LatNode& s,
                                                std::integer_sequence<int, R...>)
 {
-    (lat_row_fixed<PBC, SG, R>(a, Pi, s,
+    (lat_row_fixed<Src, PBC, SG, R>(a, Pi, s,
                                std::make_integer_sequence<int, stencil_row_len(stencil_seg(SG).qxy)>{}),
      ...);
 }
 
 // Segment SG as a loop over its rows (offsets of a row unrolled)
-template <bool PBC, int SG, int... K>
+template <class Src, bool PBC, int SG, int... K>
 __device__ __forceinline__ void lat_rows_loop(const StepArgsF32& a, const float4* Pi, LatNode& s,
                                               std::integer_sequence<int, K...>)
 {
@@ -295,14 +327,12 @@ __device__ __forceinline__ void lat_rows_loop(const StepArgsF32& a, const float4
 #pragma unroll 1
     for (int r = 0; r < sg.nrows; ++r) {
         const float4 xr = a.lat_rxi[sg.first + r];
-        const float4* Prow =
-            Pi + (kLatBatch ? a.lat_rox[sg.first + r] * s.sx + a.lat_roy[sg.first + r] * s.sy
-                            : a.lat_roff[sg.first + r]);
+        const float4* Prow = Pi + Src::loop_row(a, s, sg.first + r);
         const int b0 = sg.bit0 + len * r;
         const uint32_t rb = s.word[sg.word] >> b0;
         const float* cbrow = PBC ? a.cbond + s.slot0 + 32 * (32 * sg.word + b0) : nullptr;
         uint32_t rp = 0u;
-        (lat_row_bond<sg.qxy, K, sg.zx, sg.zy, PBC>(a, make_float2(xr.x, xr.y),
+        (lat_row_bond<Src, sg.qxy, K, sg.zx, sg.zy, PBC>(a, make_float2(xr.x, xr.y),
                                                     make_float2(xr.z, xr.w), Prow, cbrow, rb,
                                                     rp, s),
          ...);
@@ -310,14 +340,15 @@ __device__ __forceinline__ void lat_rows_loop(const StepArgsF32& a, const float4
     }
 }
 
-template <bool PBC, int SG>
+template <class Src, bool PBC, int SG>
 __device__ __forceinline__ void lat_seg(const StepArgsF32& a, const float4* Pi, LatNode& s)
 {
     constexpr StencilSeg sg = stencil_seg(SG);
     if constexpr (sg.unroll)
-        lat_rows_fixed<PBC, SG>(a, Pi, s, std::make_integer_sequence<int, sg.nrows>{});
+        lat_rows_fixed<Src, PBC, SG>(a, Pi, s, std::make_integer_sequence<int, sg.nrows>{});
     else
-        lat_rows_loop<PBC, SG>(a, Pi, s, std::make_integer_sequence<int, stencil_row_len(sg.qxy)>{});
+        lat_rows_loop<Src, PBC, SG>(a, Pi, s,
+                                    std::make_integer_sequence<int, stencil_row_len(sg.qxy)>{});
 }
 
 // After the last segment of flag word W: decide the word's near-s_c candidates.
@@ -349,28 +380,78 @@ __device__ __forceinline__ void lat_word_end(const StepArgsF32& a, int cur, LatN
 
 // the walk over the stencil: the segments of each flag word, then the word's
 // near-s_c candidates (the segment and word layout of stencil_seg)
-template <int SCM, bool PBC>
+template <class Src, int SCM, bool PBC>
 __device__ __forceinline__ void lat_walk(const StepArgsF32& a, int cur, const float4* Pi,
                                          LatNode& s)
 {
-    lat_seg<PBC, 0>(a, Pi, s);
-    lat_seg<PBC, 1>(a, Pi, s);
-    lat_seg<PBC, 2>(a, Pi, s);
+    lat_seg<Src, PBC, 0>(a, Pi, s);
+    lat_seg<Src, PBC, 1>(a, Pi, s);
+    lat_seg<Src, PBC, 2>(a, Pi, s);
     lat_word_end<SCM, PBC, 0>(a, cur, s);
-    lat_seg<PBC, 3>(a, Pi, s);
-    lat_seg<PBC, 4>(a, Pi, s);
-    lat_seg<PBC, 5>(a, Pi, s);
+    lat_seg<Src, PBC, 3>(a, Pi, s);
+    lat_seg<Src, PBC, 4>(a, Pi, s);
+    lat_seg<Src, PBC, 5>(a, Pi, s);
     lat_word_end<SCM, PBC, 1>(a, cur, s);
-    lat_seg<PBC, 6>(a, Pi, s);
-    lat_seg<PBC, 7>(a, Pi, s);
-    lat_seg<PBC, 8>(a, Pi, s);
+    lat_seg<Src, PBC, 6>(a, Pi, s);
+    lat_seg<Src, PBC, 7>(a, Pi, s);
+    lat_seg<Src, PBC, 8>(a, Pi, s);
     lat_word_end<SCM, PBC, 2>(a, cur, s);
-    lat_seg<PBC, 9>(a, Pi, s);
+    lat_seg<Src, PBC, 9>(a, Pi, s);
     lat_word_end<SCM, PBC, 3>(a, cur, s);
 }
 static_assert(stencil_seg(2).word == 0 && stencil_seg(3).word == 1 && stencil_seg(5).word == 1 &&
                   stencil_seg(6).word == 2 && stencil_seg(8).word == 2 && stencil_seg(9).word == 3,
               "lat_walk follows the segment layout");
+
+// The node's update: damped Euler-Cromer (Eq. 11) with the force in FP32 and
+// u accumulated in FP64, the linear displacement ramp, damage (Eq. 8) from the
+// intact-bond count; publishes the FP32 rounding of the new u / delta.
+__device__ __forceinline__ void lat_update(const StepArgsF32& a, const LatNode& s, int64_t step,
+                                           const double* __restrict__ U,
+                                           double* __restrict__ Uout, float4* __restrict__ Pout)
+{
+    const int64_t i = s.i;
+    float wc = a.w_const, dtd = a.dtd_f;
+    double inv_unit = a.inv_delta;
+    if (kLatBatch) {
+        const InstParams& ip = a.itab[a.inst[i]];
+        wc = ip.w_const;
+        dtd = ip.dtd;
+        inv_unit = ip.inv_unit;
+    }
+    const uint32_t cls = a.bcc[i];
+    uint32_t mask = 0u;
+    const BcClass* bc = nullptr;
+    float F[3] = {wc * s.fxy.x, wc * s.fxy.y, wc * s.fz};
+    if (cls != 0u) {
+        bc = a.bct + cls;
+        mask = bc->mask;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) F[c] += (float)(a.load * bc->force[c]);
+    }
+    double un[3];
+    bool finite = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float vi = a.v[3 * i + c];
+        float vn = vi + a.dt_f * (F[c] - a.eta_f * vi) / a.rho_f;
+        un[c] = fma((double)vn, (double)dtd, U[3 * i + c]);
+        if (mask & (1u << c)) {
+            const double s_now = a.disp_rate * (double)step;
+            const double s_next = a.disp_rate * (double)(step + 1);
+            un[c] = bc->disp[c] * s_next * inv_unit;
+            vn = (float)(bc->disp[c] * (s_next - s_now) / a.dt);
+        }
+        finite = finite && isfinite(un[c]);
+        a.v[3 * i + c] = vn;
+        Uout[3 * i + c] = un[c];
+    }
+    Pout[i] = make_float4((float)un[0], (float)un[1], (float)un[2], 0.0f);
+    const float wi = a.wsum_inv[i];
+    const float ws = wc * (float)s.alive;
+    a.damage[i] = wi > 0.0f ? fmaxf(0.0f, 1.0f - ws * wi) : 0.0f;
+    if (!finite) atomicOr(a.err, PD_DEVERR_NONFINITE);
+}
 
 template <int SCM, bool PBC>
 __global__ void __launch_bounds__(PD_LAT_THREADS, PD_LAT_MIN_BLOCKS)
@@ -408,62 +489,19 @@ __global__ void __launch_bounds__(PD_LAT_THREADS, PD_LAT_MIN_BLOCKS)
         s.fz = 0.f;
         s.pend = 0u;
         s.alive = 0;
-        lat_walk<SCM, PBC>(a, cur, P + s.i, s);
+        lat_walk<SrcGlobal, SCM, PBC>(a, cur, P + s.i, s);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
             if (s.word[q] != w0[q]) bw[q * 32] = s.word[q];
 
-        // ---- the node's update: damped Euler-Cromer (Eq. 11) with the force in
-        // FP32 and u accumulated in FP64, the linear displacement ramp, damage
-        // (Eq. 8) from the intact-bond count
-        const int64_t i = s.i;
-        if (i >= a.n) continue;
-        float wc = a.w_const, dtd = a.dtd_f;
-        double inv_unit = a.inv_delta;
-        if (kLatBatch) {
-            const InstParams& ip = a.itab[a.inst[i]];
-            wc = ip.w_const;
-            dtd = ip.dtd;
-            inv_unit = ip.inv_unit;
-        }
-        const uint32_t cls = a.bcc[i];
-        uint32_t mask = 0u;
-        const BcClass* bc = nullptr;
-        float F[3] = {wc * s.fxy.x, wc * s.fxy.y, wc * s.fz};
-        if (cls != 0u) {
-            bc = a.bct + cls;
-            mask = bc->mask;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) F[c] += (float)(a.load * bc->force[c]);
-        }
-        double un[3];
-        bool finite = true;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float vi = a.v[3 * i + c];
-            float vn = vi + a.dt_f * (F[c] - a.eta_f * vi) / a.rho_f;
-            un[c] = fma((double)vn, (double)dtd, U[3 * i + c]);
-            if (mask & (1u << c)) {
-                const double s_now = a.disp_rate * (double)step;
-                const double s_next = a.disp_rate * (double)(step + 1);
-                un[c] = bc->disp[c] * s_next * inv_unit;
-                vn = (float)(bc->disp[c] * (s_next - s_now) / a.dt);
-            }
-            finite = finite && isfinite(un[c]);
-            a.v[3 * i + c] = vn;
-            Uout[3 * i + c] = un[c];
-        }
-        Pout[i] = make_float4((float)un[0], (float)un[1], (float)un[2], 0.0f);
-        const float wi = a.wsum_inv[i];
-        const float ws = wc * (float)s.alive;
-        a.damage[i] = wi > 0.0f ? fmaxf(0.0f, 1.0f - ws * wi) : 0.0f;
-        if (!finite) atomicOr(a.err, PD_DEVERR_NONFINITE);
+        if (s.i >= a.n) continue;
+        lat_update(a, s, step, U, Uout, Pout);
     }
 }
 
 }  // namespace
 
-#if !PD_LAT_OSB
+#if !PD_LAT_HELPERS
 // entry points of this build: single model or batch, register budget
 #if PD_LAT_BATCH && PD_LAT_MIN_BLOCKS == 3
 #define PD_LAT_KERNEL_OF step_f32_kernel_lat_batch_r80
@@ -498,6 +536,6 @@ cudaError_t PD_LAT_LAUNCH(const StepArgsF32& a, int sc_mode, int grid, int block
     }
     return cudaGetLastError();
 }
-#endif  // !PD_LAT_OSB
+#endif  // !PD_LAT_HELPERS
 
 }  // namespace pd

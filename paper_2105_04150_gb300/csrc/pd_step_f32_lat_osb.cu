@@ -16,7 +16,7 @@
 // loop; the dilation kernel also writes the damage (Eq. 8) and, for the
 // force loop, a 16-byte record per node {h, A}; B, fixed, is read from a
 // per-node array beside it (16 + 4 bytes per neighbour).
-#define PD_LAT_OSB 1
+#define PD_LAT_HELPERS 1
 #include "pd_step_f32_lat.cu"
 
 namespace pd {

@@ -122,6 +122,117 @@ def test_lattice_kernel_agrees_with_general_kernel():
     assert (a["mu"] != b["mu"]).mean() < 1e-3
 
 
+def _tile_case(case):
+    """(w, steps, u0, v0, c_bond) for the tile-step comparisons."""
+    u0 = v0 = cb = None
+    if case == "beam":       # notch, per-bond s_c, no-fail strip: breaks resolved per node
+        w = workloads.notched_beam(40, 9, 10, length=0.07, rate=2e-7, steps=220)
+        nf = np.zeros(w.n, np.uint8)
+        nf[w.coords[:, 2] > w.coords[:, 2].max() - 1.5 * w.dx] = 1
+        w.no_fail = nf
+    elif case == "pbc":      # per-bond stiffness
+        w = workloads.tensile_bar(16, 6, 7, rate=5e-7, steps=100)
+        off, idx = oracle.cut_family(w.coords, w.horizon, w.cuts_array())
+        rows = np.repeat(np.arange(w.n), np.diff(off))
+        mid = 0.5 * (w.coords[rows] + w.coords[idx])
+        c = oracle.micromodulus(w.bulk_modulus, w.horizon)
+        cb = c * (1.0 + 0.1 * np.sin(mid[:, 0] / w.dx) * np.cos(mid[:, 1] / w.dx))
+    else:                    # short axes, ragged boxes, odd n, random start
+        shape = {"odd": (25, 11, 3), "short": (13, 5, 6), "tiny": (5, 3, 2)}[case]
+        w = workloads.tensile_bar(*shape, rate=3e-7, slab=1, steps=80)
+        u0, v0 = workloads.random_state(w.n, 7, 1e-7, 1e-2)
+    return w, w.steps, u0, v0, cb
+
+
+def _run_variant(w, steps, u0, v0, cb, variant, restart=False, tune=False):
+    c = oracle.micromodulus(w.bulk_modulus, w.horizon)
+    m = pdgb.Model.from_workload(w, precision=F32, c=c, lat_variant=variant, graph_steps=8)
+    info = m.info()
+    assert info["layout"] == LAT and info["lat_variant"] == variant
+    if cb is not None:
+        m.set_params(c, w.sc, w.load, w.disp_rate, cb)
+    if u0 is not None:
+        m.set_state(u0, v0)
+    if tune:
+        m.autotune(3)
+    if restart:
+        m.step(steps // 2)
+        u, v = m.state()
+        m.set_state(u, v)
+        m.step(steps - steps // 2)
+    else:
+        m.step(steps)
+    u, v = m.state()
+    out = (u, v, m.bonds(), m.damage(), m.info())
+    m.close()
+    return out
+
+
+@pytest.mark.parametrize("variant", [2, 3, 4])
+@pytest.mark.parametrize("case", ["odd", "short", "tiny", "beam", "pbc", "restart"])
+def test_tile_step_equals_l1_step_bitwise(case, variant):
+    # records staged in shared memory by one TMA copy per block (lat_variant
+    # 2..4) against the same step reading them through L1 (variant 0): the same
+    # operations per node, so the same bits
+    w, steps, u0, v0, cb = _tile_case("beam" if case == "restart" else case)
+    a = _run_variant(w, steps, u0, v0, cb, 0, restart=case == "restart")
+    b = _run_variant(w, steps, u0, v0, cb, variant, restart=case == "restart")
+    assert np.abs(a[0]).max() > 0
+    if case == "beam":
+        assert (a[2] == 0).sum() > 100
+    for x, y in zip(a[:4], b[:4]):
+        assert np.array_equal(x, y)
+
+
+def test_autotune_over_stencil_variants_keeps_results():
+    w, steps, u0, v0, cb = _tile_case("odd")
+    a = _run_variant(w, steps, u0, v0, cb, 0)
+    b = _run_variant(w, steps, u0, v0, cb, 0, tune=True)
+    assert 0 <= b[4]["lat_variant"] <= 4
+    for x, y in zip(a[:4], b[:4]):
+        assert np.array_equal(x, y)
+
+
+def test_tile_step_bounded_wait_reports_timeout_and_recovers():
+    # the test hook makes every block's barrier wait for bytes no copy delivers:
+    # the wait runs out, the next synchronising call reports PD_ERR_TIMEOUT, and
+    # after a state reset the handle steps as a fresh one
+    w, steps, u0, v0, _ = _tile_case("tiny")
+    c = oracle.micromodulus(w.bulk_modulus, w.horizon)
+    m = pdgb.Model.from_workload(w, precision=F32, c=c, lat_variant=2)
+    m.set_state(u0, v0)
+    pdgb.pd_test_tile_wait_extra(m.h, 16)
+    m.step(1)
+    with pytest.raises(pdgb.PdError) as e:
+        m.sync()
+    assert e.value.name == "PD_ERR_TIMEOUT"
+    pdgb.pd_test_tile_wait_extra(m.h, 0)
+    m.set_state(u0, v0, step=0)
+    m.step(steps)
+    u, v = m.state()
+    ref = _run_variant(w, steps, u0, v0, None, 0)
+    assert np.array_equal(u, ref[0]) and np.array_equal(v, ref[1])
+    m.close()
+
+
+def test_stencil_variants_only_on_bond_based_lattice_handles():
+    # lat_variant != 0 on a model that does not run the bond-based stencil step
+    # (the general layout, FP64, the state-based model) is refused
+    w = workloads.tensile_bar(12, 6, 6, rate=1e-6, steps=10)
+    for variant in (1, 2):
+        for kw in ({"precision": F32, "reorder": 1}, {"precision": F64}):
+            with pytest.raises(pdgb.PdError) as e:
+                pdgb.Model.from_workload(w, lat_variant=variant, **kw)
+            assert e.value.name == "PD_ERR_ARG"
+    s = workloads.tensile_bar(12, 6, 6, rate=1e-6, steps=10)
+    s.state_based = _moduli(s.bulk_modulus, 0.25)
+    with pytest.raises(pdgb.PdError):
+        pdgb.Model.from_workload(s, precision=F32, lat_variant=2)
+    m = pdgb.Model.from_workload(w, precision=F32, lat_variant=3)
+    assert m.info()["lat_variant"] == 3
+    m.close()
+
+
 def test_per_bond_stiffness_on_a_lattice_handle():
     # per-bond c read per stencil slot by the lattice kernel
     w = workloads.tensile_bar(16, 6, 7, rate=5e-7, steps=100)
