@@ -80,9 +80,10 @@ FP32_PEAK_TOPS = 35.1
 # 8 B, wsum_inv 8 B, BC class 1 B; per bond 8 B of double-word |xi| on top
 BYTES_PER_NODE[48] = 305.0
 DW_BYTES_PER_BOND = BYTES_PER_BOND + 8.0
-STEP_SRC = {32: "pd_step_f32.cu", 64: "pd_step_f64.cu", 48: "pd_step_dw.cu",
-            "lat": "pd_step_f32_lat.cu"}
-STEP_TAG = {32: "f32", 64: "f64", 48: "dw", "lat": "f32_lat"}
+STEP_SRC = {32: ["pd_step_f32.cu"], 64: ["pd_step_f64.cu"], 48: ["pd_step_dw.cu"],
+            "lat": ["pd_step_f32_lat.cu"], "lat_tma": ["pd_step_f32_lat_tma.cu", "pd_step_f32_lat.cu"]}
+STEP_TAG = {32: "f32", 64: "f64", 48: "dw", "lat": "f32_lat", "lat_tma": "f32_lat_tma"}
+TMA_BOX = ["16x2x8", "8x4x8", "32x2x4"]  # pd_config.lat_variant 2, 3, 4
 # Device memory one FP32 lattice step touches per node: FP64 displacement 24 B
 # read + 24 B written (double-buffered), the published record 16 B read + 16 B
 # written, velocity 12 B, bond flags 16 B, BC class 4 B, inverse weight sum 4 B,
@@ -158,6 +159,8 @@ def parse():
     p.add_argument("--graph-steps", type=int, default=50)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the default stencil variant and launch shape on lattice models")
     p.add_argument("--no-outer", action="store_true",
                    help="leave out the batch and adjoint sub-objects of the default line")
     return p.parse_args()
@@ -308,8 +311,10 @@ def profiled_traffic(precision, workload):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the
     current kernel source (matched by hash); else None.  precision: 32, 64, 48, or
     "lat" for the FP32 regular-lattice stencil kernel."""
-    src = os.path.join(ROOT, "paper_2105_04150_gb300", "csrc", STEP_SRC[precision])
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in STEP_SRC[precision]:
+        h.update(open(os.path.join(ROOT, "paper_2105_04150_gb300", "csrc", name), "rb").read())
+    sha = h.hexdigest()[:16]
     path = os.path.join(ROOT, "profiles", f"step_{STEP_TAG[precision]}_{workload}_traffic.txt")
     try:
         kv = dict(l.split(None, 1) for l in open(path) if l.strip() and not l.startswith("#"))
@@ -444,6 +449,15 @@ def run_ours(args):
     n_bonds = info["n_bonds"]
     # the FP32 step on a regular lattice runs the stencil kernel (FP64 displacement)
     lat = args.precision == 32 and info["layout"] == pdgb.PD_LAYOUT_LATTICE
+    # lattice models: the autotuner picks the stencil step's variant (records
+    # through L1, or staged in shared memory by TMA per box) and launch shape
+    tuned = None
+    if lat and not args.no_autotune:
+        block, bps = m.autotune(10)
+        info = m.info()
+        tuned = {"block_threads": block, "blocks_per_sm": bps,
+                 "lat_variant": info["lat_variant"], "step_registers": info["step_registers"]}
+    tma = lat and info["lat_variant"] >= 2
     # warm-up: W steps (also captures the graph)
     m.step(args.warmup)
     m.sync()
@@ -522,12 +536,14 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak,
                 "traffic": None if (args.kr or osb)
-                else profiled_traffic("lat" if lat else args.precision, args.workload),
+                else profiled_traffic(("lat_tma" if tma else "lat") if lat else args.precision,
+                                      args.workload),
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s", "algorithmic_bytes_per_launch": alg_bytes,
                 "kernel": ("k_osb_lat_dilation + k_osb_lat_force" if lat
                            else "k_osb32_dilation + k_osb32_force") if osb
-                else "k_step_f32_lat" if lat else f"k_step_f{args.precision}"}
+                else (f"k_step_f32_lat_tma (box {TMA_BOX[info['lat_variant'] - 2]}, z y x)" if tma
+                      else "k_step_f32_lat") if lat else f"k_step_f{args.precision}"}
     if lat:
         roofline["note"] = ("algorithmic bytes of the stored-family step (4.125 B per directed "
                             "bond, 93 B per node); the lattice stencil kernel reads no neighbour "
@@ -589,6 +605,8 @@ def run_ours(args):
     }
     if unflushed is not None:
         line["unflushed_graph_replay"] = unflushed
+    if tuned is not None:
+        line["autotuned_launch"] = tuned
     if world == 1 and not args.no_outer and args.workload == "beam":
         # the outer-loop forms, measured in the same process: the batched UQ sweep
         # (256 instances) and the sensitivity plate's adjoint (2000 steps,

@@ -138,7 +138,8 @@ def _tile_case(case):
         c = oracle.micromodulus(w.bulk_modulus, w.horizon)
         cb = c * (1.0 + 0.1 * np.sin(mid[:, 0] / w.dx) * np.cos(mid[:, 1] / w.dx))
     else:                    # short axes, ragged boxes, odd n, random start
-        shape = {"odd": (25, 11, 3), "short": (13, 5, 6), "tiny": (5, 3, 2)}[case]
+        shape = {"odd": (25, 11, 3), "short": (13, 5, 6), "tiny": (5, 3, 2),
+                 "fit": (32, 8, 16)}[case]  # fit: boxes of 16x2x8 and 8x4x8 tile it exactly
         w = workloads.tensile_bar(*shape, rate=3e-7, slab=1, steps=80)
         u0, v0 = workloads.random_state(w.n, 7, 1e-7, 1e-2)
     return w, w.steps, u0, v0, cb
@@ -169,7 +170,7 @@ def _run_variant(w, steps, u0, v0, cb, variant, restart=False, tune=False):
 
 
 @pytest.mark.parametrize("variant", [2, 3, 4])
-@pytest.mark.parametrize("case", ["odd", "short", "tiny", "beam", "pbc", "restart"])
+@pytest.mark.parametrize("case", ["odd", "short", "tiny", "fit", "beam", "pbc", "restart"])
 def test_tile_step_equals_l1_step_bitwise(case, variant):
     # records staged in shared memory by one TMA copy per block (lat_variant
     # 2..4) against the same step reading them through L1 (variant 0): the same
