@@ -176,8 +176,9 @@ __device__ __forceinline__ bool lat_breaks(const StepArgsF32& a, int cur, int64_
 }
 
 // A bond of slot m whose stretch reached the near-s_c band: the break decision
-// (lat_breaks) and its force term, zero when it breaks.  slot: the bond's index
-// in the per-slot arrays; sx, sy: a batch instance's strides.
+// (lat_breaks) and, when it breaks, the force term the walk added for it (to be
+// taken back), else zero.  slot: the bond's index in the per-slot arrays; sx,
+// sy: a batch instance's strides.
 template <int SCM, bool PBC>
 __device__ __noinline__ float3 lat_resolve(const StepArgsF32& a, int cur, int64_t i, int m,
                                            int64_t slot, int sx, int sy, bool* broken)
@@ -192,8 +193,8 @@ __device__ __noinline__ float3 lat_resolve(const StepArgsF32& a, int cur, int64_
     const double sc = SCM == 1 ? sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i], a.gid[j]) : a.sc;
     const bool brk = lat_breaks(a, cur, i, j, ox, oy, oz, q, sc);
     *broken = brk;
-    if (brk) return make_float3(0.f, 0.f, 0.f);
-    // the force term from the published displacements, formed as the fast path does
+    if (!brk) return make_float3(0.f, 0.f, 0.f);
+    // the force term from the published displacements, formed as the walk formed it
     const float xx = a.lat_xi[ox + 3], xy = a.lat_xi[oy + 3], xz = a.lat_xi[oz + 3];
     const float4* __restrict__ P = a.lat_pub[cur];
     const float4 hi = ld_pub(P + i), hj = ld_pub(P + j);
@@ -275,16 +276,18 @@ __device__ __forceinline__ void lat_row_bond(const StepArgsF32& a, float2 xi, fl
     const float2 txy = (ZX && ZY) ? exy : __fadd2_rn(exy, xi2);
     const float yz = OZ ? ez + a.lat_xi[OZ + 3] : ez;
     const float tz = OZ ? ez + a.lat_xi2[OZ + 3] : ez;
-    const float num = fmaf(exy.x, txy.x, fmaf(exy.y, txy.y, ez * tz));
+    // an absent or broken bond (flag 0) has num = 0: no force and no candidate
+    const float num =
+        ((rb >> K) & 1u) ? fmaf(exy.x, txy.x, fmaf(exy.y, txy.y, ez * tz)) : 0.0f;
     const float y2 = num + a.lat_q[Q];
     const float ay = y2 * rsqrt_fast(y2);
     const float D = fmaf(ay, a.lat_q[Q], a.lat_l[Q] * y2);
-    const bool alive = (rb >> K) & 1u;
+    // near-s_c candidates keep their force here; the ones that break give it
+    // back after the flag word (lat_word_end)
     const bool cand = num >= (kLatBatch ? (float)Q * s.thr_t : a.lat_thr[Q]);
     float coef = num * rcp_fast(D);
     if (PBC) coef *= __ldg(cbrow + 32 * K);
-    coef = (alive && !cand) ? coef : 0.0f;
-    rp |= (alive && cand) ? (1u << K) : 0u;
+    rp |= cand ? (1u << K) : 0u;
     s.fxy = __ffma2_rn(make_float2(coef, coef), yxy, s.fxy);
     s.fz = fmaf(coef, yz, s.fz);
 }
@@ -367,10 +370,9 @@ __device__ __forceinline__ void lat_word_end(const StepArgsF32& a, int cur, LatN
                                                &broken);
         if (broken) {
             nword &= ~(1u << bb);
-        } else {
-            s.fxy.x += f.x;
-            s.fxy.y += f.y;
-            s.fz += f.z;
+            s.fxy.x -= f.x;
+            s.fxy.y -= f.y;
+            s.fz -= f.z;
         }
     }
     s.word[W] = nword;
