@@ -49,7 +49,7 @@ __device__ __forceinline__ float osb_dil_term_rt(const StepArgsF32& a, const flo
                            fmaf(e.y, e.y + a.lat_xi2[oy + 3], e.z * (e.z + a.lat_xi2[oz + 3])));
     const float y2 = num + a.lat_q[q];
     const float ay = y2 * rsqrt_fast(y2);
-    return a.lat_l[q] * num * rcp_fast(a.lat_l[q] + ay);
+    return a.lat_l[q] * (num * rcp_fast(a.lat_l[q] + ay));  // |xi| e~, as the walk forms it
 }
 
 template <int SCM>
@@ -61,8 +61,8 @@ __device__ __noinline__ float osb_resolve(const StepArgsF32& a, int cur, int64_t
     const int64_t j = i + (int64_t)ox * a.lat_sx + (int64_t)oy * a.lat_sy + oz;
     const double sc = SCM == 1 ? sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i], a.gid[j]) : a.sc;
     const bool brk = lat_breaks(a, cur, i, j, ox, oy, oz, q, sc);
-    *broken = brk;
-    return brk ? 0.0f : osb_dil_term_rt(a, a.lat_pub[cur], i, j, ox, oy, oz, q);
+    *broken = brk;  // when it breaks: the term the walk added for it, to be taken back
+    return brk ? osb_dil_term_rt(a, a.lat_pub[cur], i, j, ox, oy, oz, q) : 0.0f;
 }
 
 // Bond K of a row with q_xy = QXY (see lat_row_bond): KIND 0 the dilation loop
@@ -81,17 +81,20 @@ __device__ __forceinline__ void osb_row_bond(const StepArgsF32& a, float2 xi, fl
     const float ez = h.z + s.own.nz;
     const float2 txy = (ZX && ZY) ? exy : __fadd2_rn(exy, xi2);
     const float tz = OZ ? ez + a.lat_xi2[OZ + 3] : ez;
-    const float num = fmaf(exy.x, txy.x, fmaf(exy.y, txy.y, ez * tz));
+    const bool alive = (rb >> K) & 1u;
+    // dilation loop: an absent or broken bond enters with num = 0 (no term and no
+    // candidate); near-s_c candidates keep their term, the ones that break give
+    // it back after the flag word
+    const float num0 = fmaf(exy.x, txy.x, fmaf(exy.y, txy.y, ez * tz));
+    const float num = (KIND == 0 && !alive) ? 0.0f : num0;
     const float y2 = num + a.lat_q[Q];
     const float ry = rsqrt_fast(y2);
     const float ay = y2 * ry;
     const float ext = num * rcp_fast(a.lat_l[Q] + ay);  // e~ = |y| - |xi|
-    const bool alive = (rb >> K) & 1u;
     if constexpr (KIND == 0) {
         const bool cand = num >= a.lat_thr[Q];
-        const float c = (alive && !cand) ? a.lat_l[Q] * ext : 0.0f;
-        s.acc += c;
-        rp |= (alive && cand) ? (1u << K) : 0u;
+        s.acc = fmaf(a.lat_l[Q], ext, s.acc);
+        rp |= cand ? (1u << K) : 0u;
     } else {
         const float t = (s.A + h.w) * a.lat_l[Q] + (s.B + ld_f32(Brow + OZ)) * ext;
         const float f = alive ? t * ry : 0.0f;
@@ -176,10 +179,10 @@ __device__ __forceinline__ void osb_word_end(const StepArgsF32& a, int cur, OsbN
         pend &= pend - 1u;
         bool broken;
         const float c = osb_resolve<SCM>(a, cur, s.i, 32 * W + bb, &broken);
-        if (broken)
+        if (broken) {
             nword &= ~(1u << bb);
-        else
-            s.acc += c;
+            s.acc -= c;
+        }
     }
     s.word[W] = nword;
     s.alive += __popc(nword);
