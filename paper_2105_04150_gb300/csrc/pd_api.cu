@@ -319,6 +319,16 @@ StepArgsF32 args_f32(pd_handle* h, int k)
             a.lat_q[q] = (float)(kap * kap * q);
             a.lat_l[q] = (float)(kap * std::sqrt((double)q));
             a.lat_thr[q] = (float)(f * (2.0 + f) * kap * kap * q);
+            if (q == 0) continue;  // no stencil offset
+            // num / D = num g(x) / |xi|^3 with g = 1/2 - 3x/8 + 5x^2/16 + O(x^3), x = num / |xi|^2
+            const double qq = kap * kap * q, L = kap * std::sqrt((double)q);
+            a.lat_pc[0][q] = (float)(0.5 / (L * qq));
+            a.lat_pc[1][q] = (float)(-0.375 / (L * qq * qq));
+            a.lat_pc[2][q] = (float)(0.3125 / (L * qq * qq * qq));
+            const double pt = kLatPolyX * qq, tu = std::min(f * (2.0 + f) * qq, pt);
+            a.lat_pt[q] = (float)pt;
+            a.lat_cc[q] = (float)(0.5 * (tu - pt));
+            a.lat_ch[q] = (float)(0.5 * (tu + pt));
         }
     }
     return a;
@@ -1367,6 +1377,9 @@ pd_status pd_batch_create(int32_t n_inst, const pd_instance* inst, const pd_conf
             ip.lat_sx = (int32_t)(L.N[1] * L.N[2]);
             ip.lat_sy = (int32_t)L.N[2];
             ip.lat_thr_t = (float)(f * (2.0 + f));
+            const double tu = std::min(f * (2.0 + f), kLatPolyX);  // per unit q (kappa = 1)
+            ip.lat_cc_t = (float)(0.5 * (tu - kLatPolyX));
+            ip.lat_ch_t = (float)(0.5 * (tu + kLatPolyX));
             ip.dtd = (float)(cfg->dt / L.dx);
             ip.unit = L.dx;
             ip.inv_unit = 1.0 / L.dx;

@@ -61,6 +61,8 @@ struct InstParams {
     // state in units of its own spacing dx, its node-order strides
     int32_t lat_sx, lat_sy;
     float lat_thr_t;           // fast_lo (2 + fast_lo): s >= fast_lo <=> num >= q lat_thr_t
+    float lat_cc_t, lat_ch_t;  // the stencil walk's candidate test |num - q cc_t| >= q ch_t
+                               // (lat_cc, lat_ch of StepArgsF32 per unit q)
     float dtd;                 // dt / dx
     double unit, inv_unit;     // dx, 1 / dx
 };
@@ -84,6 +86,9 @@ struct InstParams {
 // rows as a loop over its rows with the o_z offsets unrolled, and the short
 // rows (q_xy = 0, 8, 9) unrolled.
 constexpr int kStencil = 122;
+// |x| = |num| / |xi|^2 up to which the stencil walk's series coefficient is used
+// (truncation error below 0.25 ulp of FP32); bonds past it are corrected exactly
+constexpr double kLatPolyX = 3e-3;
 constexpr int kStencilSlots = 128;
 constexpr int kStencilR2 = 9;
 constexpr int kStencilSegs = 10;
@@ -218,6 +223,12 @@ struct StepArgsF32 {
     float lat_l[kStencilR2 + 1];    // |xi| = kappa sqrt(q)
     float lat_thr[kStencilR2 + 1];  // num threshold of the near-s_c band: s >= fast_lo
                                     // <=> num >= fast_lo (2 + fast_lo) |xi|^2
+    // the walk's force coefficient num / D as num (pc0 + pc1 num + pc2 num^2), the
+    // series of num / D in x = num / |xi|^2 to x^2 (kLatPolyX: its range); the
+    // candidates: |num - cc| >= ch, i.e. num >= min(thr, pt) or num <= -pt, with
+    // pt = kLatPolyX |xi|^2 (the near-s_c band and the bonds past the series)
+    float lat_pc[3][kStencilR2 + 1];
+    float lat_cc[kStencilR2 + 1], lat_ch[kStencilR2 + 1], lat_pt[kStencilR2 + 1];
     float dt_f, eta_f, rho_f;  // dt, eta, rho rounded to FP32 once, on the host
     float dtd_f;               // dt / delta (velocity to displacement in horizon units)
     // regular-lattice models keep their state differently (no rec / lo32):

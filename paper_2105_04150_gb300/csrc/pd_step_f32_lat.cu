@@ -175,10 +175,12 @@ __device__ __forceinline__ bool lat_breaks(const StepArgsF32& a, int cur, int64_
     return brk;
 }
 
-// A bond of slot m whose stretch reached the near-s_c band: the break decision
-// (lat_breaks) and, when it breaks, the force term the walk added for it (to be
-// taken back), else zero.  slot: the bond's index in the per-slot arrays; sx,
-// sy: a batch instance's strides.
+// A candidate bond of slot m (its stretch in the near-s_c band, or |x| past the
+// walk's series): the break decision (lat_breaks) and the correction of the
+// force term the walk added for it: minus that term when the bond breaks, the
+// exact term (num / D) minus the series one when |x| > kLatPolyX, else zero.
+// slot: the bond's index in the per-slot arrays; sx, sy: a batch instance's
+// strides.
 template <int SCM, bool PBC>
 __device__ __noinline__ float3 lat_resolve(const StepArgsF32& a, int cur, int64_t i, int m,
                                            int64_t slot, int sx, int sy, bool* broken)
@@ -193,8 +195,7 @@ __device__ __noinline__ float3 lat_resolve(const StepArgsF32& a, int cur, int64_
     const double sc = SCM == 1 ? sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i], a.gid[j]) : a.sc;
     const bool brk = lat_breaks(a, cur, i, j, ox, oy, oz, q, sc);
     *broken = brk;
-    if (!brk) return make_float3(0.f, 0.f, 0.f);
-    // the force term from the published displacements, formed as the walk formed it
+    // the walk's force term from the published displacements, formed as it formed it
     const float xx = a.lat_xi[ox + 3], xy = a.lat_xi[oy + 3], xz = a.lat_xi[oz + 3];
     const float4* __restrict__ P = a.lat_pub[cur];
     const float4 hi = ld_pub(P + i), hj = ld_pub(P + j);
@@ -204,19 +205,27 @@ __device__ __noinline__ float3 lat_resolve(const StepArgsF32& a, int cur, int64_
     const float3 e = lat_eta(own, hj);
     const float fx = e.x + xx, fy = e.y + xy, fz = e.z + xz;
     const float n2 = fmaf(e.x, e.x + 2.0f * xx, fmaf(e.y, e.y + 2.0f * xy, e.z * (e.z + 2.0f * xz)));
-    const float z2 = n2 + a.lat_q[q];
-    const float az = z2 * rsqrt_fast(z2);
-    const float Dz = fmaf(az, a.lat_q[q], a.lat_l[q] * z2);
-    float coef = n2 * rcp_fast(Dz);
-    if (PBC) coef *= a.cbond[slot];
-    return make_float3(coef * fx, coef * fy, coef * fz);
+    const float cs = n2 * fmaf(fmaf(a.lat_pc[2][q], n2, a.lat_pc[1][q]), n2, a.lat_pc[0][q]);
+    float dc;
+    if (brk) {
+        dc = -cs;
+    } else if (fabsf(n2) > a.lat_pt[q]) {  // past the series' range: the exact num / D
+        const float z2 = n2 + a.lat_q[q];
+        const float az = z2 * rsqrt_fast(z2);
+        const float Dz = fmaf(az, a.lat_q[q], a.lat_l[q] * z2);
+        dc = n2 * rcp_fast(Dz) - cs;
+    } else {
+        return make_float3(0.f, 0.f, 0.f);
+    }
+    if (PBC) dc *= a.cbond[slot];
+    return make_float3(dc * fx, dc * fy, dc * fz);
 }
 
 // One node's state over its stencil walk.
 struct LatNode {
     LatOwn own;
     int sx, sy;         // batch: the instance's node-order strides
-    float thr_t;        // batch: its near-s_c threshold per unit q
+    float cc_t, ch_t;   // batch: its candidate test per unit q
     int64_t i;
     int64_t slot0;      // index of slot 0 of this node in per-slot arrays
     float2 fxy;         // force sum: (x, y) as one register pair, z alone
@@ -279,14 +288,16 @@ __device__ __forceinline__ void lat_row_bond(const StepArgsF32& a, float2 xi, fl
     // an absent or broken bond (flag 0) has num = 0: no force and no candidate
     const float num =
         ((rb >> K) & 1u) ? fmaf(exy.x, txy.x, fmaf(exy.y, txy.y, ez * tz)) : 0.0f;
-    const float y2 = num + a.lat_q[Q];
-    const float ay = y2 * rsqrt_fast(y2);
-    const float D = fmaf(ay, a.lat_q[Q], a.lat_l[Q] * y2);
-    // near-s_c candidates keep their force here; the ones that break give it
-    // back after the flag word (lat_word_end)
-    const bool cand = num >= (kLatBatch ? (float)Q * s.thr_t : a.lat_thr[Q]);
-    float coef = num * rcp_fast(D);
+    // coefficient num / D = num g(x) / |xi|^3, x = num / |xi|^2, g(x) = 1 / (r (1 + r))
+    // with r = sqrt(1 + x): the series of g to x^2 (1/2 - 3x/8 + 5x^2/16), within
+    // 0.25 ulp for |x| <= kLatPolyX, in place of a square root and a division
+    float coef = num * fmaf(fmaf(a.lat_pc[2][Q], num, a.lat_pc[1][Q]), num, a.lat_pc[0][Q]);
     if (PBC) coef *= __ldg(cbrow + 32 * K);
+    // candidates: the near-s_c band and |x| past the series (num >= min(thr, pt)
+    // or num <= -pt), decided and corrected after the flag word (lat_word_end);
+    // they keep the series term here
+    const bool cand = kLatBatch ? fabsf(fmaf(-(float)Q, s.cc_t, num)) >= (float)Q * s.ch_t
+                                : fabsf(num - a.lat_cc[Q]) >= a.lat_ch[Q];
     rp |= cand ? (1u << K) : 0u;
     s.fxy = __ffma2_rn(make_float2(coef, coef), yxy, s.fxy);
     s.fz = fmaf(coef, yz, s.fz);
@@ -368,12 +379,10 @@ __device__ __forceinline__ void lat_word_end(const StepArgsF32& a, int cur, LatN
         const float3 f = lat_resolve<SCM, PBC>(a, cur, s.i, m, s.slot0 + 32 * m,
                                                kLatBatch ? s.sx : 0, kLatBatch ? s.sy : 0,
                                                &broken);
-        if (broken) {
-            nword &= ~(1u << bb);
-            s.fxy.x -= f.x;
-            s.fxy.y -= f.y;
-            s.fz -= f.z;
-        }
+        if (broken) nword &= ~(1u << bb);
+        s.fxy.x += f.x;  // the candidate's correction (lat_resolve)
+        s.fxy.y += f.y;
+        s.fz += f.z;
     }
     s.word[W] = nword;
     s.alive += __popc(nword);
@@ -478,7 +487,8 @@ __global__ void __launch_bounds__(PD_LAT_THREADS, PD_LAT_MIN_BLOCKS)
             const InstParams& ip = a.itab[a.inst[s.i]];
             s.sx = ip.lat_sx;
             s.sy = ip.lat_sy;
-            s.thr_t = ip.lat_thr_t;
+            s.cc_t = ip.lat_cc_t;
+            s.ch_t = ip.lat_ch_t;
         }
         const float4 hi = ld_pub(P + s.i);
         s.own.nxy = make_float2(-hi.x, -hi.y);
