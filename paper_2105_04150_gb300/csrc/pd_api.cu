@@ -325,6 +325,10 @@ StepArgsF32 args_f32(pd_handle* h, int k)
             a.lat_pc[0][q] = (float)(0.5 / (L * qq));
             a.lat_pc[1][q] = (float)(-0.375 / (L * qq * qq));
             a.lat_pc[2][q] = (float)(0.3125 / (L * qq * qq * qq));
+            // |xi| e~ = num (1/2 - x/8 + x^2/16 + O(x^3)) for the state-based dilation
+            a.lat_dc[0][q] = 0.5f;
+            a.lat_dc[1][q] = (float)(-0.125 / qq);
+            a.lat_dc[2][q] = (float)(0.0625 / (qq * qq));
             const double pt = kLatPolyX * qq, tu = std::min(f * (2.0 + f) * qq, pt);
             a.lat_pt[q] = (float)pt;
             a.lat_cc[q] = (float)(0.5 * (tu - pt));

@@ -228,6 +228,10 @@ struct StepArgsF32 {
     // candidates: |num - cc| >= ch, i.e. num >= min(thr, pt) or num <= -pt, with
     // pt = kLatPolyX |xi|^2 (the near-s_c band and the bonds past the series)
     float lat_pc[3][kStencilR2 + 1];
+    // the state-based dilation loop's |xi| e~ = |xi| (|y| - |xi|) as num (dc0 + dc1 num
+    // + dc2 num^2), its series in x to x^2 (dc0 = 1/2, dc1 = -1 / (8 |xi|^2),
+    // dc2 = 1 / (16 |xi|^4)), the same candidates
+    float lat_dc[3][kStencilR2 + 1];
     float lat_cc[kStencilR2 + 1], lat_ch[kStencilR2 + 1], lat_pt[kStencilR2 + 1];
     float dt_f, eta_f, rho_f;  // dt, eta, rho rounded to FP32 once, on the host
     float dtd_f;               // dt / delta (velocity to displacement in horizon units)

@@ -35,10 +35,12 @@ struct OsbNode {
     int alive;
 };
 
-// |xi~| e~ of the bond to offset (ox, oy, oz) from the published displacements
-// (run-time offset: a resolved near-s_c candidate that stays intact)
+// The dilation term |xi| e~ of a candidate bond to offset (ox, oy, oz), from the
+// published displacements: the walk's series term (as the walk forms it) and,
+// in *exact, the exact |xi| num / (|xi| + |y|)
 __device__ __forceinline__ float osb_dil_term_rt(const StepArgsF32& a, const float4* P, int64_t i,
-                                                 int64_t j, int ox, int oy, int oz, int q)
+                                                 int64_t j, int ox, int oy, int oz, int q,
+                                                 float* exact)
 {
     LatOwn own;
     const float4 hi = ld_pub(P + i);
@@ -49,7 +51,8 @@ __device__ __forceinline__ float osb_dil_term_rt(const StepArgsF32& a, const flo
                            fmaf(e.y, e.y + a.lat_xi2[oy + 3], e.z * (e.z + a.lat_xi2[oz + 3])));
     const float y2 = num + a.lat_q[q];
     const float ay = y2 * rsqrt_fast(y2);
-    return a.lat_l[q] * (num * rcp_fast(a.lat_l[q] + ay));  // |xi| e~, as the walk forms it
+    *exact = fabsf(num) > a.lat_pt[q] ? a.lat_l[q] * (num * rcp_fast(a.lat_l[q] + ay)) : 0.0f;
+    return num * fmaf(fmaf(a.lat_dc[2][q], num, a.lat_dc[1][q]), num, a.lat_dc[0][q]);
 }
 
 template <int SCM>
@@ -61,8 +64,13 @@ __device__ __noinline__ float osb_resolve(const StepArgsF32& a, int cur, int64_t
     const int64_t j = i + (int64_t)ox * a.lat_sx + (int64_t)oy * a.lat_sy + oz;
     const double sc = SCM == 1 ? sc_draw(a.sc_seed, a.sc_lo, a.sc_hi, a.gid[i], a.gid[j]) : a.sc;
     const bool brk = lat_breaks(a, cur, i, j, ox, oy, oz, q, sc);
-    *broken = brk;  // when it breaks: the term the walk added for it, to be taken back
-    return brk ? osb_dil_term_rt(a, a.lat_pub[cur], i, j, ox, oy, oz, q) : 0.0f;
+    *broken = brk;
+    // the correction of the term the walk added: all of it back when the bond
+    // breaks, exact minus series past the series' range (|num| > pt)
+    float exact;
+    const float ser = osb_dil_term_rt(a, a.lat_pub[cur], i, j, ox, oy, oz, q, &exact);
+    if (brk) return -ser;
+    return exact != 0.0f ? exact - ser : 0.0f;  // exact is formed past the range only
 }
 
 // Bond K of a row with q_xy = QXY (see lat_row_bond): KIND 0 the dilation loop
@@ -87,15 +95,18 @@ __device__ __forceinline__ void osb_row_bond(const StepArgsF32& a, float2 xi, fl
     // it back after the flag word
     const float num0 = fmaf(exy.x, txy.x, fmaf(exy.y, txy.y, ez * tz));
     const float num = (KIND == 0 && !alive) ? 0.0f : num0;
-    const float y2 = num + a.lat_q[Q];
-    const float ry = rsqrt_fast(y2);
-    const float ay = y2 * ry;
-    const float ext = num * rcp_fast(a.lat_l[Q] + ay);  // e~ = |y| - |xi|
     if constexpr (KIND == 0) {
-        const bool cand = num >= a.lat_thr[Q];
-        s.acc = fmaf(a.lat_l[Q], ext, s.acc);
+        // |xi| e~ from its series in x = num / |xi|^2 (no square root or division);
+        // the candidates (the near-s_c band and |x| past the series) are decided and
+        // corrected after the flag word
+        s.acc += num * fmaf(fmaf(a.lat_dc[2][Q], num, a.lat_dc[1][Q]), num, a.lat_dc[0][Q]);
+        const bool cand = fabsf(num - a.lat_cc[Q]) >= a.lat_ch[Q];
         rp |= cand ? (1u << K) : 0u;
     } else {
+        const float y2 = num + a.lat_q[Q];
+        const float ry = rsqrt_fast(y2);
+        const float ay = y2 * ry;
+        const float ext = num * rcp_fast(a.lat_l[Q] + ay);  // e~ = |y| - |xi|
         const float t = (s.A + h.w) * a.lat_l[Q] + (s.B + ld_f32(Brow + OZ)) * ext;
         const float f = alive ? t * ry : 0.0f;
         const float2 yxy = (ZX && ZY) ? exy : __fadd2_rn(exy, xi);
@@ -179,10 +190,8 @@ __device__ __forceinline__ void osb_word_end(const StepArgsF32& a, int cur, OsbN
         pend &= pend - 1u;
         bool broken;
         const float c = osb_resolve<SCM>(a, cur, s.i, 32 * W + bb, &broken);
-        if (broken) {
-            nword &= ~(1u << bb);
-            s.acc -= c;
-        }
+        if (broken) nword &= ~(1u << bb);
+        s.acc += c;  // the candidate's correction (osb_resolve)
     }
     s.word[W] = nword;
     s.alive += __popc(nword);
