@@ -49,10 +49,12 @@ def oracle_run(w, steps, c=None, c_bond=None, u0=None, v0=None, off_idx=None):
     return dict(u=u, v=v, mu=mu, margin=margin, phi=m.damage(mu), off=off, idx=idx, model=m)
 
 
-def gpu_run(w, steps, precision, c=None, c_bond=None, u0=None, v0=None, **kw):
+def gpu_run(w, steps, precision, c=None, c_bond=None, u0=None, v0=None, autotune=0, **kw):
     if c is None:
         c = oracle.micromodulus(w.bulk_modulus, w.horizon)
     m = pdgb.Model.from_workload(w, precision=precision, c=c, **kw)
+    if autotune:  # the launch shape and stencil variant bench.py times
+        m.autotune(autotune)
     if c_bond is not None:
         m.set_params(c, w.sc, w.load, w.disp_rate, c_bond)
     if u0 is not None or v0 is not None:
@@ -368,7 +370,7 @@ def test_full_size_notched_beam_200_steps(beam_full_run, prec):
     # every node and every bond compared at the bars of the module docstring
     w, o = beam_full_run
     assert (o["mu"] == 0).sum() > 10
-    g = gpu_run(w, 200, prec, graph_steps=50)
+    g = gpu_run(w, 200, prec, graph_steps=50, autotune=10 if prec == F32 else 0)
     assert g["info"]["n"] == 1009200 and g["info"]["step"] == 200
     if prec == F32:
         assert g["info"]["layout"] == pdgb.PD_LAYOUT_LATTICE
@@ -439,6 +441,7 @@ def test_full_size_plate_sampled_one_step():
     c = oracle.micromodulus(w.bulk_modulus, w.horizon)
     m = pdgb.Model.from_workload(w, precision=F32, c=c, graph_steps=20)
     assert m.info()["n"] == 16_000_000
+    m.autotune(10)  # as bench.py does: the stencil variant it times (the TMA tile step)
     rng = np.random.default_rng(11)
     u0 = 2.0e-4 * (w.coords - w.coords.mean(axis=0)) * np.array([0.2, 1.0, 0.3])
     u0 += rng.normal(0.0, 2e-8, size=u0.shape)
