@@ -346,7 +346,8 @@ def _config(precision, graph_steps, dt, damping, density, check_dt, device, stre
 def pd_batch_create(instances, *, dt: float, damping: float, density: float,
                     precision: int = PD_PREC_F64, graph_steps: int = 0, check_dt: bool = False,
                     device: int = 0, stream=None, block_threads: int = 0,
-                    blocks_per_sm: int = 0, reorder: int = 0, integrator: int = 0) -> int:
+                    blocks_per_sm: int = 0, reorder: int = 0, integrator: int = 0,
+                    lat_variant: int = 0) -> int:
     """Create a batch handle from a list of dicts with the keys of ``pd_create``'s
     body arguments: coords, volumes, horizon, c, sc / sc_hash, cuts, bc_type,
     bc_disp, bc_force, no_fail, disp_rate, load, ramp_steps, kr, trilinear,
@@ -384,7 +385,7 @@ def pd_batch_create(instances, *, dt: float, damping: float, density: float,
                                   load=float(I.get("load", 0.0)),
                                   ramp_steps=int(I.get("ramp_steps", 0))))
     cfg = _config(precision, graph_steps, dt, damping, density, check_dt, device, stream,
-                  block_threads, blocks_per_sm, reorder, integrator)
+                  block_threads, blocks_per_sm, reorder, integrator, lat_variant=lat_variant)
     h = ctypes.c_void_p()
     _check(lib().pd_batch_create(len(instances), arr, ctypes.byref(cfg), ctypes.byref(h)))
     return h.value

@@ -156,6 +156,7 @@ struct pd_handle {
     float4* osblat_coef = nullptr;  // FP32 state-based lattice models (pd_step_f32_lat_osb.cu)
     float4* osblat_rec = nullptr;
     float* osblat_b = nullptr;
+    uint8_t* osblat_exact = nullptr;
     void* wsum_inv = nullptr;
     void* damage = nullptr;
     int* err = nullptr;
@@ -315,6 +316,13 @@ StepArgsF32 args_f32(pd_handle* h, int k)
             a.lat_rox[j] = r.x;
             a.lat_roy[j] = r.y;
         }
+        for (int j = 0; j + 1 < kStencilRows; ++j) {
+            const Off3 r0 = stencil_row(j), r1 = stencil_row(j + 1);
+            a.lat_rxp[j][0] = make_float4(a.lat_xi[r0.x + 3], a.lat_xi[r1.x + 3],
+                                          a.lat_xi[r0.y + 3], a.lat_xi[r1.y + 3]);
+            a.lat_rxp[j][1] = make_float4(a.lat_xi2[r0.x + 3], a.lat_xi2[r1.x + 3],
+                                          a.lat_xi2[r0.y + 3], a.lat_xi2[r1.y + 3]);
+        }
         for (int q = 0; q <= kStencilR2; ++q) {
             a.lat_q[q] = (float)(kap * kap * q);
             a.lat_l[q] = (float)(kap * std::sqrt((double)q));
@@ -333,6 +341,22 @@ StepArgsF32 args_f32(pd_handle* h, int k)
             a.lat_pt[q] = (float)pt;
             a.lat_cc[q] = (float)(0.5 * (tu - pt));
             a.lat_ch[q] = (float)(0.5 * (tu + pt));
+            for (int t = 0; t < 3; ++t) {
+                a.lat_pcd[t][q] = make_float2(a.lat_pc[t][q], a.lat_pc[t][q]);
+                a.lat_dcd[t][q] = make_float2(a.lat_dc[t][q], a.lat_dc[t][q]);
+            }
+            a.lat_ccd[q] = make_float2(-a.lat_cc[q], -a.lat_cc[q]);
+            // (1 + x)^(-1/2) = 1 - x/2 + 3x^2/8 + O(x^3); 1 - (1 + x)^(-1/2) = x/2 - 3x^2/8
+            // + 5x^3/16 + O(x^4), x = num / |xi|^2
+            a.lat_fa[0][q] = (float)(-0.5 / qq);
+            a.lat_fa[1][q] = (float)(0.375 / (qq * qq));
+            a.lat_fb[0][q] = (float)(0.5 / qq);
+            a.lat_fb[1][q] = (float)(-0.375 / (qq * qq));
+            a.lat_fb[2][q] = (float)(0.3125 / (qq * qq * qq));
+            for (int t = 0; t < 3; ++t) {
+                if (t < 2) a.lat_fad[t][q] = make_float2(a.lat_fa[t][q], a.lat_fa[t][q]);
+                a.lat_fbd[t][q] = make_float2(a.lat_fb[t][q], a.lat_fb[t][q]);
+            }
         }
     }
     return a;
@@ -452,6 +476,7 @@ OsbLatArgs osblat_args(pd_handle* h)
     o.rec = h->osblat_rec;
     o.bco = h->osblat_b;
     o.theta = h->osb32_theta;
+    o.exact = h->osblat_exact;
     return o;
 }
 
@@ -519,7 +544,7 @@ cudaError_t launch_one(pd_handle* h, int k)
     if (h->model == 1 && h->precision == 32)
         return h->lattice
                    ? launch_osb_lat_step(args_f32(h, k), osblat_args(h), h->sc_mode, h->grid,
-                                         h->block, h->stream)
+                                         h->grid_osbf, h->block, h->stream)
                    : launch_osb32_step(args_f32(h, k), osb32_args(h), h->sc_mode, h->grid_osbf, h->grid_dil, h->block,
                                  h->stream);
     if (h->model == 1)
@@ -614,6 +639,15 @@ pd_status choose_grid(pd_handle* h, int blocks_per_sm)
     h->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * occ, need));
     h->grid_dil = h->grid;
     h->grid_osbf = h->grid;
+    if (h->model == 1 && h->precision == 32 && h->lattice) {  // the force loop's own grid
+        const void* ff = osb_lat_force_kernel();
+        PD_CUDA(cudaFuncSetAttribute(ff, cudaFuncAttributePreferredSharedMemoryCarveout, 0),
+                "carveout");
+        int o = 0;
+        PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, ff, h->block, 0), "occupancy");
+        if (blocks_per_sm > 0) o = std::min(o, blocks_per_sm);
+        h->grid_osbf = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(o, 1), need));
+    }
     if (h->model == 1 && h->precision == 32 && !h->lattice) {  // the state-based kernels' own grids
         auto grid_of_kernel = [&](const void* fn, int& out) -> pd_status {
             PD_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 0),
@@ -977,6 +1011,7 @@ pd_status build_device(pd_handle* h, const ModelDesc& d, const pd_config* cfg)
                 h->osblat_rec += h->lat_halo;
                 ALLOC(h->osblat_b, float, np + 2 * h->lat_halo);
                 h->osblat_b += h->lat_halo;
+                ALLOC(h->osblat_exact, uint8_t, h->n_slices);
             } else {
                 ALLOC(h->osb32_mvol, float, np);
                 ALLOC(h->osb32_ab, float2, np);

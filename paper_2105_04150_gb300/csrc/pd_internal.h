@@ -233,6 +233,18 @@ struct StepArgsF32 {
     // dc2 = 1 / (16 |xi|^4)), the same candidates
     float lat_dc[3][kStencilR2 + 1];
     float lat_cc[kStencilR2 + 1], lat_ch[kStencilR2 + 1], lat_pt[kStencilR2 + 1];
+    // the bond-based walk takes its bonds two at a time (paired FP32 instructions):
+    // per first row j of a row pair, kappa (o_x(j), o_x(j+1), o_y(j), o_y(j+1)) and
+    // twice that; per q, pc0, pc1, pc2 and -cc, each twice (one register pair)
+    float4 lat_rxp[kStencilRows][2];
+    float2 lat_pcd[3][kStencilR2 + 1];
+    float2 lat_ccd[kStencilR2 + 1];
+    float2 lat_dcd[3][kStencilR2 + 1];  // the state-based dilation loop's dc0..dc2
+    // the state-based force loop's |xi| / |y| = 1 + fa0 num + fa1 num^2 and
+    // e~ / |y| = num (fb0 + fb1 num + fb2 num^2), the series of (1 + x)^(-1/2) and of
+    // 1 - (1 + x)^(-1/2) in x = num / |xi|^2 to x^2 (within 0.25 ulp for |x| <= kLatPolyX)
+    float lat_fa[2][kStencilR2 + 1], lat_fb[3][kStencilR2 + 1];
+    float2 lat_fad[2][kStencilR2 + 1], lat_fbd[3][kStencilR2 + 1];  // each twice
     float dt_f, eta_f, rho_f;  // dt, eta, rho rounded to FP32 once, on the host
     float dtd_f;               // dt / delta (velocity to displacement in horizon units)
     // regular-lattice models keep their state differently (no rec / lo32):
@@ -356,9 +368,11 @@ struct OsbLatArgs {
     float4* rec;         // per node the force loop's record {h, A} (zero halo)
     const float* bco;    // per node B = 15 G / (delta m~) (zero halo)
     float* theta;        // per node dilation of the current step
+    uint8_t* exact;      // per slice of 32 nodes: 1 when a node of it has a dilation
+                         // candidate (the force loop then forms 1 / |y| and e~ exactly)
 };
 cudaError_t launch_osb_lat_step(const StepArgsF32& a, const OsbLatArgs& o, int sc_mode, int grid,
-                                int block, cudaStream_t s);
+                                int grid_force, int block, cudaStream_t s);
 const void* osb_lat_force_kernel();
 const void* osb_lat_dilation_kernel(int sc_mode);
 

@@ -18,7 +18,10 @@
 //   - the slot loop is unrolled over the stencil at compile time: flag bits,
 //     record offsets along z (immediates) and per-offset constants are fixed.
 // A lane owns one node and accumulates its force in registers; a warp walks 32
-// consecutive nodes.  Where the 32 nodes cross a lattice line the offsets of
+// consecutive nodes.  The walk takes the stencil's bonds two at a time (two
+// rows of a segment at the same position, or o_z and -o_z of the o_x = o_y = 0
+// row: the same |xi|), each quantity of the two bonds in one register pair
+// through paired FP32 instructions.  Where the 32 nodes cross a lattice line the offsets of
 // some lanes wrap to other nodes; those slots have flag 0 and are masked, and
 // the published records carry a zero halo so that every read stays in bounds.
 //
@@ -221,19 +224,33 @@ __device__ __noinline__ float3 lat_resolve(const StepArgsF32& a, int cur, int64_
     return make_float3(dc * fx, dc * fy, dc * fz);
 }
 
-// One node's state over its stencil walk.
+// One node's state over its stencil walk.  The walk takes its bonds two at a
+// time (lat_pair_bond): the first half of each register pair belongs to the
+// first bond of a pair, the second half to the second.
 struct LatNode {
-    LatOwn own;
+    float2 nx, ny, nz;  // the lane's own published displacement, negated, twice
     int sx, sy;         // batch: the instance's node-order strides
     float cc_t, ch_t;   // batch: its candidate test per unit q
     int64_t i;
     int64_t slot0;      // index of slot 0 of this node in per-slot arrays
-    float2 fxy;         // force sum: (x, y) as one register pair, z alone
-    float fz;
+    float2 fx, fy, fz;  // force sums over the first and the second bonds of the pairs
     uint32_t word[4];   // bond flags (stencil slot order)
     uint32_t pend;      // near-s_c candidates of the current flag word
     int alive;          // intact bonds after this step's decisions
 };
+
+// start of a node's walk from its own published record
+__device__ __forceinline__ void lat_node_begin(LatNode& s, const float4 hi)
+{
+    s.nx = make_float2(-hi.x, -hi.x);
+    s.ny = make_float2(-hi.y, -hi.y);
+    s.nz = make_float2(-hi.z, -hi.z);
+    s.fx = make_float2(0.f, 0.f);
+    s.fy = make_float2(0.f, 0.f);
+    s.fz = make_float2(0.f, 0.f);
+    s.pend = 0u;
+    s.alive = 0;
+}
 
 // Where the walk reads the neighbours' published records.  SrcGlobal: the
 // record array itself (a row of offsets o_x, o_y starts o_x Sx + o_y Sy records
@@ -266,91 +283,146 @@ struct SrcTile {
     __device__ static float4 load(const float4* p) { return *p; }
 };
 
-// Bond K of a row with q_xy = QXY: o_z = stencil_row_oz(QXY, K); xi, xi2: the
-// (x, y) components of xi and 2 xi of the row's o_x, o_y (ZX / ZY: that
-// component is 0); rb: the row's flags from bit 0, rp: the row's near-s_c
-// candidates.  The (x, y) components go through paired FP32 instructions (each
-// half rounded as the scalar operation).
-template <class Src, int QXY, int K, int ZX, int ZY, bool PBC>
-__device__ __forceinline__ void lat_row_bond(const StepArgsF32& a, float2 xi, float2 xi2,
-                                             const float4* Prow, const float* cbrow,
-                                             uint32_t rb, uint32_t& rp, LatNode& s)
+// Two bonds of equal |xi| walked together: bond K0 of the row at P0 (flags
+// from bit 0 in rb0, candidates into rp0) and bond K1 of the row at P1 (rb1,
+// rp1), both rows with q_xy = QXY: two rows of one segment at the same
+// position, or mirror positions of the o_x = o_y = 0 row.  xix, xiy, xi2x,
+// xi2y: the two rows' x and y components of xi and 2 xi (ZX / ZY: 0 in both).
+// Every quantity of the two bonds sits in one register pair and goes through
+// paired FP32 instructions, each half rounded as the scalar operation, so each
+// bond's terms are those of the one-bond formulas (lat_resolve re-forms them).
+template <class Src, int QXY, int K0, int K1, int ZX, int ZY, bool PBC>
+__device__ __forceinline__ void lat_pair_bond(const StepArgsF32& a, const float2 xix,
+                                              const float2 xiy, const float2 xi2x,
+                                              const float2 xi2y, const float4* P0,
+                                              const float4* P1, const float* cb0,
+                                              const float* cb1, uint32_t rb0, uint32_t rb1,
+                                              uint32_t& rp0, uint32_t& rp1, LatNode& s)
 {
-    constexpr int OZ = stencil_row_oz(QXY, K);
-    constexpr int Q = QXY + OZ * OZ;
-    const float4 r = Src::load(Prow + OZ);
-    const float2 exy = __fadd2_rn(make_float2(r.x, r.y), s.own.nxy);
-    const float ez = r.z + s.own.nz;
-    const float2 yxy = (ZX && ZY) ? exy : __fadd2_rn(exy, xi);
-    const float2 txy = (ZX && ZY) ? exy : __fadd2_rn(exy, xi2);
-    const float yz = OZ ? ez + a.lat_xi[OZ + 3] : ez;
-    const float tz = OZ ? ez + a.lat_xi2[OZ + 3] : ez;
-    // an absent or broken bond (flag 0) has num = 0: no force and no candidate
-    const float num =
-        ((rb >> K) & 1u) ? fmaf(exy.x, txy.x, fmaf(exy.y, txy.y, ez * tz)) : 0.0f;
+    constexpr int OZ0 = stencil_row_oz(QXY, K0), OZ1 = stencil_row_oz(QXY, K1);
+    static_assert(OZ0 * OZ0 == OZ1 * OZ1, "the two bonds of a pair have the same |xi|");
+    constexpr int Q = QXY + OZ0 * OZ0;
+    const float4 r0 = Src::load(P0 + OZ0), r1 = Src::load(P1 + OZ1);
+    const float2 ex = __fadd2_rn(make_float2(r0.x, r1.x), s.nx);
+    const float2 ey = __fadd2_rn(make_float2(r0.y, r1.y), s.ny);
+    const float2 ez = __fadd2_rn(make_float2(r0.z, r1.z), s.nz);
+    const float2 yx = ZX ? ex : __fadd2_rn(ex, xix);
+    const float2 tx = ZX ? ex : __fadd2_rn(ex, xi2x);
+    const float2 yy = ZY ? ey : __fadd2_rn(ey, xiy);
+    const float2 ty = ZY ? ey : __fadd2_rn(ey, xi2y);
+    const float2 yz = OZ0 ? __fadd2_rn(ez, make_float2(a.lat_xi[OZ0 + 3], a.lat_xi[OZ1 + 3])) : ez;
+    const float2 tz = OZ0 ? __fadd2_rn(ez, make_float2(a.lat_xi2[OZ0 + 3], a.lat_xi2[OZ1 + 3]))
+                          : ez;
+    // num = eta . (2 xi + eta); an absent or broken bond (flag 0) has num = 0: no
+    // force and no candidate
+    float2 num = __ffma2_rn(ex, tx, __ffma2_rn(ey, ty, __fmul2_rn(ez, tz)));
+    num.x = ((rb0 >> K0) & 1u) ? num.x : 0.0f;
+    num.y = ((rb1 >> K1) & 1u) ? num.y : 0.0f;
     // coefficient num / D = num g(x) / |xi|^3, x = num / |xi|^2, g(x) = 1 / (r (1 + r))
     // with r = sqrt(1 + x): the series of g to x^2 (1/2 - 3x/8 + 5x^2/16), within
     // 0.25 ulp for |x| <= kLatPolyX, in place of a square root and a division
-    float coef = num * fmaf(fmaf(a.lat_pc[2][Q], num, a.lat_pc[1][Q]), num, a.lat_pc[0][Q]);
-    if (PBC) coef *= __ldg(cbrow + 32 * K);
+    float2 coef = __fmul2_rn(
+        num, __ffma2_rn(__ffma2_rn(a.lat_pcd[2][Q], num, a.lat_pcd[1][Q]), num, a.lat_pcd[0][Q]));
+    if (PBC) {
+        coef.x *= __ldg(cb0 + 32 * K0);
+        coef.y *= __ldg(cb1 + 32 * K1);
+    }
     // candidates: the near-s_c band and |x| past the series (num >= min(thr, pt)
     // or num <= -pt), decided and corrected after the flag word (lat_word_end);
     // they keep the series term here
-    const bool cand = kLatBatch ? fabsf(fmaf(-(float)Q, s.cc_t, num)) >= (float)Q * s.ch_t
-                                : fabsf(num - a.lat_cc[Q]) >= a.lat_ch[Q];
-    rp |= cand ? (1u << K) : 0u;
-    s.fxy = __ffma2_rn(make_float2(coef, coef), yxy, s.fxy);
-    s.fz = fmaf(coef, yz, s.fz);
+    if (kLatBatch) {
+        const float ch = (float)Q * s.ch_t;
+        rp0 |= fabsf(fmaf(-(float)Q, s.cc_t, num.x)) >= ch ? (1u << K0) : 0u;
+        rp1 |= fabsf(fmaf(-(float)Q, s.cc_t, num.y)) >= ch ? (1u << K1) : 0u;
+    } else {
+        const float2 d = __fadd2_rn(num, a.lat_ccd[Q]);
+        rp0 |= fabsf(d.x) >= a.lat_ch[Q] ? (1u << K0) : 0u;
+        rp1 |= fabsf(d.y) >= a.lat_ch[Q] ? (1u << K1) : 0u;
+    }
+    s.fx = __ffma2_rn(coef, yx, s.fx);
+    s.fy = __ffma2_rn(coef, yy, s.fy);
+    s.fz = __ffma2_rn(coef, yz, s.fz);
 }
 
-// Row R (compile-time) of segment SG, unrolled, its offsets fixed
+// Rows R and R + 1 (compile-time) of segment SG, unrolled, their offsets fixed
 template <class Src, bool PBC, int SG, int R, int... K>
-__device__ __forceinline__ void lat_row_fixed(const StepArgsF32& a, const float4* Pi, LatNode& s,
-                                              std::integer_sequence<int, K...>)
+__device__ __forceinline__ void lat_rowpair_fixed(const StepArgsF32& a, const float4* Pi,
+                                                  LatNode& s, std::integer_sequence<int, K...>)
 {
     constexpr StencilSeg sg = stencil_seg(SG);
-    constexpr Off3 o = stencil_row_xy(sg.qxy, sg.row0 + R);
-    constexpr int b0 = sg.bit0 + stencil_row_len(sg.qxy) * R;
-    const float4* Prow = Pi + Src::fixed_row(a, s, o.x, o.y);
-    const uint32_t rb = s.word[sg.word] >> b0;
-    const float* cbrow = PBC ? a.cbond + s.slot0 + 32 * (32 * sg.word + b0) : nullptr;
-    uint32_t rp = 0u;
-    const float2 xi = make_float2(a.lat_xi[o.x + 3], a.lat_xi[o.y + 3]);
-    const float2 xi2 = make_float2(a.lat_xi2[o.x + 3], a.lat_xi2[o.y + 3]);
-    (lat_row_bond<Src, sg.qxy, K, o.x == 0, o.y == 0, PBC>(a, xi, xi2, Prow, cbrow, rb, rp, s),
+    constexpr int len = stencil_row_len(sg.qxy);
+    constexpr Off3 o0 = stencil_row_xy(sg.qxy, sg.row0 + R);
+    constexpr Off3 o1 = stencil_row_xy(sg.qxy, sg.row0 + R + 1);
+    constexpr int b0 = sg.bit0 + len * R;
+    const float4* P0 = Pi + Src::fixed_row(a, s, o0.x, o0.y);
+    const float4* P1 = Pi + Src::fixed_row(a, s, o1.x, o1.y);
+    const uint32_t rb0 = s.word[sg.word] >> b0, rb1 = rb0 >> len;
+    const float* cb0 = PBC ? a.cbond + s.slot0 + 32 * (32 * sg.word + b0) : nullptr;
+    const float* cb1 = PBC ? cb0 + 32 * len : nullptr;
+    uint32_t rp0 = 0u, rp1 = 0u;
+    const float2 xix = make_float2(a.lat_xi[o0.x + 3], a.lat_xi[o1.x + 3]);
+    const float2 xiy = make_float2(a.lat_xi[o0.y + 3], a.lat_xi[o1.y + 3]);
+    const float2 xi2x = make_float2(a.lat_xi2[o0.x + 3], a.lat_xi2[o1.x + 3]);
+    const float2 xi2y = make_float2(a.lat_xi2[o0.y + 3], a.lat_xi2[o1.y + 3]);
+    (lat_pair_bond<Src, sg.qxy, K, K, o0.x == 0 && o1.x == 0, o0.y == 0 && o1.y == 0, PBC>(
+         a, xix, xiy, xi2x, xi2y, P0, P1, cb0, cb1, rb0, rb1, rp0, rp1, s),
      ...);
-    s.pend |= rp << b0;
+    s.pend |= (rp0 | (rp1 << len)) << b0;
 }
 
 template <class Src, bool PBC, int SG, int... R>
 __device__ __forceinline__ void lat_rows_fixed(const StepArgsF32& a, const float4* Pi, LatNode& s,
                                                std::integer_sequence<int, R...>)
 {
-    (lat_row_fixed<Src, PBC, SG, R>(a, Pi, s,
-                               std::make_integer_sequence<int, stencil_row_len(stencil_seg(SG).qxy)>{}),
+    (lat_rowpair_fixed<Src, PBC, SG, 2 * R>(
+         a, Pi, s, std::make_integer_sequence<int, stencil_row_len(stencil_seg(SG).qxy)>{}),
      ...);
 }
 
-// Segment SG as a loop over its rows (offsets of a row unrolled)
+// The o_x = o_y = 0 row (a segment of one row, o_z = -3..-1, 1..3): its
+// positions K and len - 1 - K (o_z and -o_z) as pairs
+template <class Src, bool PBC, int SG, int... K>
+__device__ __forceinline__ void lat_row_mirror(const StepArgsF32& a, const float4* Pi, LatNode& s,
+                                               std::integer_sequence<int, K...>)
+{
+    constexpr StencilSeg sg = stencil_seg(SG);
+    constexpr int len = stencil_row_len(sg.qxy);
+    static_assert(sg.qxy == 0 && sg.nrows == 1 && len % 2 == 0, "the o_x = o_y = 0 row");
+    const uint32_t rb = s.word[sg.word] >> sg.bit0;
+    const float* cb = PBC ? a.cbond + s.slot0 + 32 * (32 * sg.word + sg.bit0) : nullptr;
+    uint32_t rp = 0u;
+    const float2 z = make_float2(0.f, 0.f);
+    (lat_pair_bond<Src, sg.qxy, K, len - 1 - K, 1, 1, PBC>(a, z, z, z, z, Pi, Pi, cb, cb, rb, rb,
+                                                          rp, rp, s),
+     ...);
+    s.pend |= rp << sg.bit0;
+}
+
+// Segment SG as a loop over its rows, two rows per iteration (offsets of a row
+// unrolled)
 template <class Src, bool PBC, int SG, int... K>
 __device__ __forceinline__ void lat_rows_loop(const StepArgsF32& a, const float4* Pi, LatNode& s,
                                               std::integer_sequence<int, K...>)
 {
     constexpr StencilSeg sg = stencil_seg(SG);
     constexpr int len = stencil_row_len(sg.qxy);
+    static_assert(sg.nrows % 2 == 0, "a loop segment walks its rows in pairs");
 #pragma unroll 1
-    for (int r = 0; r < sg.nrows; ++r) {
-        const float4 xr = a.lat_rxi[sg.first + r];
-        const float4* Prow = Pi + Src::loop_row(a, s, sg.first + r);
+    for (int r = 0; r < sg.nrows; r += 2) {
+        const int j = sg.first + r;
+        const float4 xa = a.lat_rxp[j][0], xb = a.lat_rxp[j][1];
+        const float4* P0 = Pi + Src::loop_row(a, s, j);
+        const float4* P1 = Pi + Src::loop_row(a, s, j + 1);
         const int b0 = sg.bit0 + len * r;
-        const uint32_t rb = s.word[sg.word] >> b0;
-        const float* cbrow = PBC ? a.cbond + s.slot0 + 32 * (32 * sg.word + b0) : nullptr;
-        uint32_t rp = 0u;
-        (lat_row_bond<Src, sg.qxy, K, sg.zx, sg.zy, PBC>(a, make_float2(xr.x, xr.y),
-                                                    make_float2(xr.z, xr.w), Prow, cbrow, rb,
-                                                    rp, s),
+        const uint32_t rb0 = s.word[sg.word] >> b0, rb1 = rb0 >> len;
+        const float* cb0 = PBC ? a.cbond + s.slot0 + 32 * (32 * sg.word + b0) : nullptr;
+        const float* cb1 = PBC ? cb0 + 32 * len : nullptr;
+        uint32_t rp0 = 0u, rp1 = 0u;
+        (lat_pair_bond<Src, sg.qxy, K, K, sg.zx, sg.zy, PBC>(
+             a, make_float2(xa.x, xa.y), make_float2(xa.z, xa.w), make_float2(xb.x, xb.y),
+             make_float2(xb.z, xb.w), P0, P1, cb0, cb1, rb0, rb1, rp0, rp1, s),
          ...);
-        s.pend |= rp << b0;
+        s.pend |= (rp0 | (rp1 << len)) << b0;
     }
 }
 
@@ -358,11 +430,13 @@ template <class Src, bool PBC, int SG>
 __device__ __forceinline__ void lat_seg(const StepArgsF32& a, const float4* Pi, LatNode& s)
 {
     constexpr StencilSeg sg = stencil_seg(SG);
-    if constexpr (sg.unroll)
-        lat_rows_fixed<Src, PBC, SG>(a, Pi, s, std::make_integer_sequence<int, sg.nrows>{});
+    constexpr int len = stencil_row_len(sg.qxy);
+    if constexpr (!sg.unroll)
+        lat_rows_loop<Src, PBC, SG>(a, Pi, s, std::make_integer_sequence<int, len>{});
+    else if constexpr (sg.nrows == 1)
+        lat_row_mirror<Src, PBC, SG>(a, Pi, s, std::make_integer_sequence<int, len / 2>{});
     else
-        lat_rows_loop<Src, PBC, SG>(a, Pi, s,
-                                    std::make_integer_sequence<int, stencil_row_len(sg.qxy)>{});
+        lat_rows_fixed<Src, PBC, SG>(a, Pi, s, std::make_integer_sequence<int, sg.nrows / 2>{});
 }
 
 // After the last segment of flag word W: decide the word's near-s_c candidates.
@@ -380,9 +454,9 @@ __device__ __forceinline__ void lat_word_end(const StepArgsF32& a, int cur, LatN
                                                kLatBatch ? s.sx : 0, kLatBatch ? s.sy : 0,
                                                &broken);
         if (broken) nword &= ~(1u << bb);
-        s.fxy.x += f.x;  // the candidate's correction (lat_resolve)
-        s.fxy.y += f.y;
-        s.fz += f.z;
+        s.fx.x += f.x;  // the candidate's correction (lat_resolve)
+        s.fy.x += f.y;
+        s.fz.x += f.z;
     }
     s.word[W] = nword;
     s.alive += __popc(nword);
@@ -433,7 +507,7 @@ __device__ __forceinline__ void lat_update(const StepArgsF32& a, const LatNode& 
     const uint32_t cls = a.bcc[i];
     uint32_t mask = 0u;
     const BcClass* bc = nullptr;
-    float F[3] = {wc * s.fxy.x, wc * s.fxy.y, wc * s.fz};
+    float F[3] = {wc * (s.fx.x + s.fx.y), wc * (s.fy.x + s.fy.y), wc * (s.fz.x + s.fz.y)};
     if (cls != 0u) {
         bc = a.bct + cls;
         mask = bc->mask;
@@ -490,17 +564,11 @@ __global__ void __launch_bounds__(PD_LAT_THREADS, PD_LAT_MIN_BLOCKS)
             s.cc_t = ip.lat_cc_t;
             s.ch_t = ip.lat_ch_t;
         }
-        const float4 hi = ld_pub(P + s.i);
-        s.own.nxy = make_float2(-hi.x, -hi.y);
-        s.own.nz = -hi.z;
+        lat_node_begin(s, ld_pub(P + s.i));
         uint32_t* bw = a.bits + g * 4 * 32 + lane;
         uint32_t w0[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) w0[q] = s.word[q] = bw[q * 32];
-        s.fxy = make_float2(0.f, 0.f);
-        s.fz = 0.f;
-        s.pend = 0u;
-        s.alive = 0;
         lat_walk<SrcGlobal, SCM, PBC>(a, cur, P + s.i, s);
 #pragma unroll
         for (int q = 0; q < 4; ++q)

@@ -137,17 +137,11 @@ __global__ void __launch_bounds__(BZ * BY * BX, PD_LAT_MIN_BLOCKS)
     s.i = ((int64_t)ix * t.ny + iy) * t.nz + iz;
     s.slot0 = (s.i >> 5) * (int64_t)(kStencilSlots * 32) + (s.i & 31);
     const float4* Ti = tile + ((tz + 3) + TZ * ((ty + 3) + TY * (tx + 3)));
-    const float4 hi = *Ti;
-    s.own.nxy = make_float2(-hi.x, -hi.y);
-    s.own.nz = -hi.z;
+    lat_node_begin(s, *Ti);
     uint32_t* bw = a.bits + (s.i >> 5) * (int64_t)kStencilSlots + (s.i & 31);
     uint32_t w0[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) w0[q] = s.word[q] = bw[q * 32];
-    s.fxy = make_float2(0.f, 0.f);
-    s.fz = 0.f;
-    s.pend = 0u;
-    s.alive = 0;
     lat_walk<SrcTile<TZ, TY>, SCM, PBC>(a, cur, Ti, s);
 #pragma unroll
     for (int q = 0; q < 4; ++q)

@@ -146,21 +146,28 @@ def test_lattice_kernel_agrees_with_general_kernel():
 
 
 @pytest.mark.parametrize("state_based", [False, True])
-@pytest.mark.parametrize("strain, no_fail", [(-0.01, False), (0.01, True), (-2e-3, False)])
-def test_large_strains_take_the_exact_coefficient(strain, no_fail, state_based):
+@pytest.mark.parametrize("strain, no_fail, half",
+                         [(-0.01, False, False), (0.01, True, False), (-2e-3, False, False),
+                          (-0.01, False, True)])
+def test_large_strains_take_the_exact_coefficient(strain, no_fail, half, state_based):
     # the walk forms num / D from its series in x = num / |xi|^2 up to |x| = 3e-3;
     # bonds past it (uniform 1 % compression, 1 % tension of a bar whose nodes are
     # all no-fail so that nothing breaks) are candidates corrected to the exact
     # coefficient, 0.2 % compression (|x| about 4e-3 and 1e-3 for the stencil's
     # offsets) mixes both: one step from that state, the force through v, against
     # the oracle.  The state-based dilation loop forms |xi| e~ from the same kind
-    # of series and corrects the same candidates.
+    # of series and corrects the same candidates; its force loop takes the series
+    # of |xi| / |y| and e~ / |y| on slices of nodes without a candidate, the exact
+    # form on the others ("half": only the nodes past mid-length strained, so that
+    # both kinds of slice meet).
     w = workloads.tensile_bar(16, 6, 7, rate=0.0, steps=1)
     if state_based:
         w.state_based = _moduli(w.bulk_modulus, 0.25)
     if no_fail:
         w.no_fail = np.ones(w.n, np.uint8)
     u0 = strain * (w.coords - w.coords.mean(axis=0))
+    if half:
+        u0 *= (w.coords[:, 0] > np.median(w.coords[:, 0]))[:, None]
     v0 = np.zeros_like(u0)
     o = oracle_run(w, 1, u0=u0, v0=v0)
     assert np.abs(o["v"]).max() > 0
