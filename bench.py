@@ -483,8 +483,9 @@ def run_ours(args):
     m.sync()
     ms_max = aggregate_max(ms, group)
     # each timed interval: the step's kernels (two passes for the state-based
-    # model) and the step-counter advance
-    launches = args.steps * ((2 if args.state_based is not None else 1) + 1)
+    # model) and, except on lattice models (whose step kernel advances the step
+    # counter itself when launched directly), the step-counter advance
+    launches = args.steps * ((2 if args.state_based is not None else 1) + (0 if lat else 1))
     # context: the same number of steps back to back in CUDA graphs of G steps,
     # with no flush between them
     unflushed = None

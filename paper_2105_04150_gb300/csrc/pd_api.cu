@@ -236,7 +236,7 @@ struct pd_handle {
 
 namespace {
 
-StepArgsF32 args_f32(pd_handle* h, int k)
+StepArgsF32 args_f32(pd_handle* h, int k, int64_t step_abs = -1)
 {
     StepArgsF32 a{};
     a.inst = h->inst;
@@ -263,6 +263,7 @@ StepArgsF32 args_f32(pd_handle* h, int k)
     a.step_ctr = h->step_ctr;
     a.n = h->n;
     a.k = k;
+    a.step_abs = h->lattice ? step_abs : -1;
     a.Q = h->Q;
     a.has_nofail = h->has_nofail ? 1 : 0;
     a.guard = (float)kGuard;
@@ -533,7 +534,10 @@ const void* step_kernel_fn(pd_handle* h)
     return step_f64_kernel(h->sc_mode);
 }
 
-cudaError_t launch_one(pd_handle* h, int k)
+// One step launch, k steps past the device counter; step_abs >= 0 (F32 lattice
+// handles, direct launches): the absolute step, the kernel then advancing the
+// counter itself
+cudaError_t launch_one(pd_handle* h, int k, int64_t step_abs = -1)
 {
     if (h->dw && h->model == 1)
         return launch_osb_dw_step(args_f64(h, k), dw_args(h), osbdw_args(h), h->grid, h->block,
@@ -543,14 +547,14 @@ cudaError_t launch_one(pd_handle* h, int k)
                               h->stream);
     if (h->model == 1 && h->precision == 32)
         return h->lattice
-                   ? launch_osb_lat_step(args_f32(h, k), osblat_args(h), h->sc_mode, h->grid,
+                   ? launch_osb_lat_step(args_f32(h, k, step_abs), osblat_args(h), h->sc_mode, h->grid,
                                          h->grid_osbf, h->block, h->stream)
                    : launch_osb32_step(args_f32(h, k), osb32_args(h), h->sc_mode, h->grid_osbf, h->grid_dil, h->block,
                                  h->stream);
     if (h->model == 1)
         return launch_osb_step(args_f64(h, k), osb_args(h), h->grid, h->block, h->stream);
     if (h->precision == 32)
-        return launch_f32(h, args_f32(h, k));
+        return launch_f32(h, args_f32(h, k, step_abs));
     return launch_step_f64(args_f64(h, k), h->sc_mode, h->grid, h->block, h->stream);
 }
 
@@ -1539,9 +1543,14 @@ pd_status pd_step(pd_handle* h, int64_t n_steps)
             h->step += G;
         }
     }
-    for (int64_t k = 0; k < left; ++k) PD_CUDA(launch_one(h, (int)k), "step launch");
+    // direct launches: the FP32 lattice kernels take their absolute step and
+    // advance the device counter themselves (one launch per step); the others
+    // read counter + k and one advance follows
+    const bool self_adv = h->lattice && h->precision == 32;
+    for (int64_t k = 0; k < left; ++k)
+        PD_CUDA(self_adv ? launch_one(h, 0, h->step + k) : launch_one(h, (int)k), "step launch");
     if (left > 0) {
-        PD_CUDA(launch_advance(h->step_ctr, left, h->stream), "advance");
+        if (!self_adv) PD_CUDA(launch_advance(h->step_ctr, left, h->stream), "advance");
         h->step += left;
     }
     h->damage_fresh = true;

@@ -195,6 +195,9 @@ struct StepArgsF32 {
     const int64_t* step_ctr;
     int64_t n;
     int32_t k;                 // offset of this launch from the device step counter
+    int64_t step_abs;          // lattice kernels: >= 0, the absolute step of a direct
+                               // launch, which then sets the counter to step_abs + 1
+                               // instead of reading it; -1: counter + k
     int32_t Q;
     int32_t has_nofail;
     int32_t pad0;

@@ -224,6 +224,20 @@ __device__ __noinline__ float3 lat_resolve(const StepArgsF32& a, int cur, int64_
     return make_float3(dc * fx, dc * fy, dc * fz);
 }
 
+// The step a launch computes: the device counter plus the launch's offset, or
+// the absolute step of a direct launch (a.step_abs >= 0), whose kernel then sets
+// the counter to the next step itself (block 0, thread 0: no thread of such a
+// launch reads it, and the stream orders it before the next launch)
+__device__ __forceinline__ int64_t lat_step_of(const StepArgsF32& a)
+{
+    return a.step_abs >= 0 ? a.step_abs : a.step_ctr[0] + a.k;
+}
+__device__ __forceinline__ void lat_advance_counter(const StepArgsF32& a)
+{
+    if (a.step_abs >= 0 && blockIdx.x == 0 && threadIdx.x == 0)
+        const_cast<int64_t*>(a.step_ctr)[0] = a.step_abs + 1;
+}
+
 // One node's state over its stencil walk.  The walk takes its bonds two at a
 // time (lat_pair_bond): the first half of each register pair belongs to the
 // first bond of a pair, the second half to the second.
@@ -545,7 +559,8 @@ __global__ void __launch_bounds__(PD_LAT_THREADS, PD_LAT_MIN_BLOCKS)
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t step = a.step_ctr[0] + a.k;
+    const int64_t step = lat_step_of(a);
+    lat_advance_counter(a);
     const int cur = (int)(step & 1);
     const int64_t nslices = (a.n + 31) >> 5;
     const float4* __restrict__ P = a.lat_pub[cur];

@@ -501,6 +501,7 @@ __global__ void __launch_bounds__(PD_LAT_THREADS, PD_LAT_MIN_BLOCKS)
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // a direct launch's counter still holds this step (the step's force kernel advances it)
     const int64_t step = a.step_ctr[0] + a.k;
     const int cur = (int)(step & 1);
     const int64_t nslices = (a.n + 31) >> 5;
@@ -547,7 +548,8 @@ __global__ void __launch_bounds__(PD_LAT_THREADS, 3)
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t step = a.step_ctr[0] + a.k;
+    const int64_t step = lat_step_of(a);
+    lat_advance_counter(a);  // the step's last kernel
     const int cur = (int)(step & 1);
     const int64_t nslices = (a.n + 31) >> 5;
     float4* __restrict__ Pout = const_cast<float4*>(a.lat_pub[cur ^ 1]);

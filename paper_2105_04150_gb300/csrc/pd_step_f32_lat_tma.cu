@@ -109,7 +109,8 @@ __global__ void __launch_bounds__(BZ * BY * BX, PD_LAT_MIN_BLOCKS)
     float4* tile = reinterpret_cast<float4*>(base);
     uint64_t* bar = reinterpret_cast<uint64_t*>(base + kBytes);
 
-    const int64_t step = a.step_ctr[0] + a.k;
+    const int64_t step = lat_step_of(a);
+    lat_advance_counter(a);
     const int cur = (int)(step & 1);
     const int b = blockIdx.x;
     const int bz = b % t.tiles_z, by = (b / t.tiles_z) % t.tiles_y, bx = b / (t.tiles_z * t.tiles_y);
