@@ -349,14 +349,12 @@ StepArgsF32 args_f32(pd_handle* h, int k, int64_t step_abs = -1)
             a.lat_ccd[q] = make_float2(-a.lat_cc[q], -a.lat_cc[q]);
             // (1 + x)^(-1/2) = 1 - x/2 + 3x^2/8 + O(x^3); 1 - (1 + x)^(-1/2) = x/2 - 3x^2/8
             // + 5x^3/16 + O(x^4), x = num / |xi|^2
-            a.lat_fa[0][q] = (float)(-0.5 / qq);
-            a.lat_fa[1][q] = (float)(0.375 / (qq * qq));
-            a.lat_fb[0][q] = (float)(0.5 / qq);
-            a.lat_fb[1][q] = (float)(-0.375 / (qq * qq));
-            a.lat_fb[2][q] = (float)(0.3125 / (qq * qq * qq));
+            const float fa[2] = {(float)(-0.5 / qq), (float)(0.375 / (qq * qq))};
+            const float fb[3] = {(float)(0.5 / qq), (float)(-0.375 / (qq * qq)),
+                                 (float)(0.3125 / (qq * qq * qq))};
             for (int t = 0; t < 3; ++t) {
-                if (t < 2) a.lat_fad[t][q] = make_float2(a.lat_fa[t][q], a.lat_fa[t][q]);
-                a.lat_fbd[t][q] = make_float2(a.lat_fb[t][q], a.lat_fb[t][q]);
+                if (t < 2) a.lat_fad[t][q] = make_float2(fa[t], fa[t]);
+                a.lat_fbd[t][q] = make_float2(fb[t], fb[t]);
             }
         }
     }

@@ -245,9 +245,9 @@ struct StepArgsF32 {
     float2 lat_dcd[3][kStencilR2 + 1];  // the state-based dilation loop's dc0..dc2
     // the state-based force loop's |xi| / |y| = 1 + fa0 num + fa1 num^2 and
     // e~ / |y| = num (fb0 + fb1 num + fb2 num^2), the series of (1 + x)^(-1/2) and of
-    // 1 - (1 + x)^(-1/2) in x = num / |xi|^2 to x^2 (within 0.25 ulp for |x| <= kLatPolyX)
-    float lat_fa[2][kStencilR2 + 1], lat_fb[3][kStencilR2 + 1];
-    float2 lat_fad[2][kStencilR2 + 1], lat_fbd[3][kStencilR2 + 1];  // each twice
+    // 1 - (1 + x)^(-1/2) in x = num / |xi|^2 to x^2 (within 0.25 ulp for |x| <= kLatPolyX),
+    // each coefficient twice (one register pair)
+    float2 lat_fad[2][kStencilR2 + 1], lat_fbd[3][kStencilR2 + 1];
     float dt_f, eta_f, rho_f;  // dt, eta, rho rounded to FP32 once, on the host
     float dtd_f;               // dt / delta (velocity to displacement in horizon units)
     // regular-lattice models keep their state differently (no rec / lo32):

@@ -256,14 +256,13 @@ __device__ __forceinline__ void osb_dil_walk(const StepArgsF32& a, int cur, cons
     osb_word_end<SCM, 3>(a, cur, s);
 }
 
-// Force loop: bond K of a row with q_xy = QXY (Prow: 16-byte state-based
-// records {h, A}, Brow: B); xi, xi2: the (x, y) components of xi and 2 xi of
-// the row, which go through paired FP32 instructions.  The bond's force factor
-// t / |y| = (A_i + A_j) |xi| / |y| + (B_i + B_j) e~ / |y|: SER, for slices of
-// nodes without a dilation candidate (every bond's |x| = |num| / |xi|^2 within
-// kLatPolyX), from the series of |xi| / |y| and e~ / |y| in x; else with the
+// Force loop, one bond at a time with the exact factors (the slices of nodes
+// with a dilation candidate): bond K of a row with q_xy = QXY (Prow: 16-byte
+// state-based records {h, A}, Brow: B); xi, xi2: the (x, y) components of xi
+// and 2 xi of the row, which go through paired FP32 instructions.  The bond's
+// force factor t / |y| = ((A_i + A_j) |xi| + (B_i + B_j) e~) / |y| with the
 // reciprocal square root and the division.
-template <bool SER, int QXY, int K, int ZX, int ZY>
+template <int QXY, int K, int ZX, int ZY>
 __device__ __forceinline__ void osb_force_bond(const StepArgsF32& a, float2 xi, float2 xi2,
                                                const float4* Prow, const float* Brow, uint32_t rb,
                                                OsbForceNode& s)
@@ -278,19 +277,11 @@ __device__ __forceinline__ void osb_force_bond(const StepArgsF32& a, float2 xi, 
     const bool alive = (rb >> K) & 1u;
     const float num = fmaf(exy.x, txy.x, fmaf(exy.y, txy.y, ez * tz));
     const float As = s.A + h.w, Bs = s.B + ld_f32(Brow + OZ);
-    float f0;
-    if constexpr (SER) {
-        const float p = fmaf(fmaf(a.lat_fa[1][Q], num, a.lat_fa[0][Q]), num, 1.0f);  // |xi| / |y|
-        const float r = num * fmaf(fmaf(a.lat_fb[2][Q], num, a.lat_fb[1][Q]), num,
-                                   a.lat_fb[0][Q]);  // e~ / |y|
-        f0 = fmaf(As, p, Bs * r);
-    } else {
-        const float y2 = num + a.lat_q[Q];
-        const float ry = rsqrt_fast(y2);
-        const float ay = y2 * ry;
-        const float ext = num * rcp_fast(a.lat_l[Q] + ay);  // e~ = |y| - |xi|
-        f0 = (As * a.lat_l[Q] + Bs * ext) * ry;
-    }
+    const float y2 = num + a.lat_q[Q];
+    const float ry = rsqrt_fast(y2);
+    const float ay = y2 * ry;
+    const float ext = num * rcp_fast(a.lat_l[Q] + ay);  // e~ = |y| - |xi|
+    const float f0 = (As * a.lat_l[Q] + Bs * ext) * ry;
     const float f = alive ? f0 : 0.0f;
     const float2 yxy = (ZX && ZY) ? exy : __fadd2_rn(exy, xi);
     const float yz = OZ ? ez + a.lat_xi[OZ + 3] : ez;
@@ -298,7 +289,7 @@ __device__ __forceinline__ void osb_force_bond(const StepArgsF32& a, float2 xi, 
     s.fzs = fmaf(f, yz, s.fzs);
 }
 
-template <bool SER, int SG, int R, int... K>
+template <int SG, int R, int... K>
 __device__ __forceinline__ void osb_force_row_fixed(const StepArgsF32& a, const float4* Pi,
                                                     const float* Bi, OsbForceNode& s,
                                                     std::integer_sequence<int, K...>)
@@ -310,21 +301,21 @@ __device__ __forceinline__ void osb_force_row_fixed(const StepArgsF32& a, const 
     const uint32_t rb = s.word[sg.word] >> b0;
     const float2 xi = make_float2(a.lat_xi[o.x + 3], a.lat_xi[o.y + 3]);
     const float2 xi2 = make_float2(a.lat_xi2[o.x + 3], a.lat_xi2[o.y + 3]);
-    (osb_force_bond<SER, sg.qxy, K, o.x == 0, o.y == 0>(a, xi, xi2, Pi + off, Bi + off, rb, s),
+    (osb_force_bond<sg.qxy, K, o.x == 0, o.y == 0>(a, xi, xi2, Pi + off, Bi + off, rb, s),
      ...);
 }
 
-template <bool SER, int SG, int... R>
+template <int SG, int... R>
 __device__ __forceinline__ void osb_force_rows_fixed(const StepArgsF32& a, const float4* Pi,
                                                      const float* Bi, OsbForceNode& s,
                                                      std::integer_sequence<int, R...>)
 {
-    (osb_force_row_fixed<SER, SG, R>(
+    (osb_force_row_fixed<SG, R>(
          a, Pi, Bi, s, std::make_integer_sequence<int, stencil_row_len(stencil_seg(SG).qxy)>{}),
      ...);
 }
 
-template <bool SER, int SG, int... K>
+template <int SG, int... K>
 __device__ __forceinline__ void osb_force_rows_loop(const StepArgsF32& a, const float4* Pi,
                                                     const float* Bi, OsbForceNode& s,
                                                     std::integer_sequence<int, K...>)
@@ -336,22 +327,22 @@ __device__ __forceinline__ void osb_force_rows_loop(const StepArgsF32& a, const 
         const float4 xr = a.lat_rxi[sg.first + r];
         const int off = a.lat_roff[sg.first + r];
         const uint32_t rb = s.word[sg.word] >> (sg.bit0 + len * r);
-        (osb_force_bond<SER, sg.qxy, K, sg.zx, sg.zy>(a, make_float2(xr.x, xr.y),
+        (osb_force_bond<sg.qxy, K, sg.zx, sg.zy>(a, make_float2(xr.x, xr.y),
                                                  make_float2(xr.z, xr.w), Pi + off, Bi + off, rb,
                                                  s),
          ...);
     }
 }
 
-template <bool SER, int SG>
+template <int SG>
 __device__ __forceinline__ void osb_force_seg(const StepArgsF32& a, const float4* Pi,
                                               const float* Bi, OsbForceNode& s)
 {
     constexpr StencilSeg sg = stencil_seg(SG);
     if constexpr (sg.unroll)
-        osb_force_rows_fixed<SER, SG>(a, Pi, Bi, s, std::make_integer_sequence<int, sg.nrows>{});
+        osb_force_rows_fixed<SG>(a, Pi, Bi, s, std::make_integer_sequence<int, sg.nrows>{});
     else
-        osb_force_rows_loop<SER, SG>(a, Pi, Bi, s,
+        osb_force_rows_loop<SG>(a, Pi, Bi, s,
                                 std::make_integer_sequence<int, stencil_row_len(sg.qxy)>{});
 }
 
@@ -485,12 +476,12 @@ __device__ __forceinline__ void osb_force_pairwalk(const StepArgsF32& a, const f
     (osb_force_pairseg<SG>(a, Pi, Bi, s), ...);
 }
 
-template <bool SER, int... SG>
+template <int... SG>
 __device__ __forceinline__ void osb_force_walk(const StepArgsF32& a, const float4* Pi,
                                                const float* Bi, OsbForceNode& s,
                                                std::integer_sequence<int, SG...>)
 {
-    (osb_force_seg<SER, SG>(a, Pi, Bi, s), ...);
+    (osb_force_seg<SG>(a, Pi, Bi, s), ...);
 }
 
 // the dilation loop: breaks, theta, damage and the force loop's records
@@ -574,8 +565,8 @@ __global__ void __launch_bounds__(PD_LAT_THREADS, 3)
             s.own.nz = -r0.z;
             s.fxy = make_float2(0.f, 0.f);
             s.fzs = 0.f;
-            osb_force_walk<false>(a, S + s.i, o.bco + s.i, s,
-                                  std::make_integer_sequence<int, kStencilSegs>{});
+            osb_force_walk(a, S + s.i, o.bco + s.i, s,
+                           std::make_integer_sequence<int, kStencilSegs>{});
             s.fx.x = s.fxy.x;
             s.fy.x = s.fxy.y;
             s.fz.x = s.fzs;
