@@ -307,7 +307,11 @@ pd_status pd_get_family(pd_handle* h, int64_t* off, int32_t* idx);
  * components with u = disp * disp_rate * (k+1), v = disp * disp_rate / dt,
  * and writes the damage.  Asynchronous on the handle's stream; a non-finite
  * displacement is reported by the next synchronising call (PD_ERR_NONFINITE).
- * n_steps >= 0.
+ * n_steps >= 0.  Whole groups of pd_config.graph_steps steps replay one CUDA
+ * graph (its kernels read the device step counter, one advance per graph);
+ * the rest are direct launches: on FP32 lattice handles one launch per step
+ * (two for the state-based model) whose kernel sets the counter itself, on
+ * the others the step kernels and one counter advance.
  */
 pd_status pd_step(pd_handle* h, int64_t n_steps);
 
