@@ -351,7 +351,9 @@ def pd_batch_create(instances, *, dt: float, damping: float, density: float,
     """Create a batch handle from a list of dicts with the keys of ``pd_create``'s
     body arguments: coords, volumes, horizon, c, sc / sc_hash, cuts, bc_type,
     bc_disp, bc_force, no_fail, disp_rate, load, ramp_steps, kr, trilinear,
-    state_based."""
+    state_based.  lat_variant (batches of bond-based FP32 lattice models): the
+    stencil kernel's register budget, 0 (64 registers) or 1 (80); pd_autotune
+    chooses between them."""
     keep = []
     arr = (_Instance * len(instances))()
     for k, I in enumerate(instances):
